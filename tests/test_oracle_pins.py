@@ -1,0 +1,424 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Nothing here compares the oracle with a retyped copy of itself:
+  * field operations against Python big integers (Sec. 6.1, p = 2^61 - 1);
+  * multilinear extensions against Boolean-point values and multilinearity;
+  * interpolation against polynomials evaluated directly;
+  * round messages and line values against a brute-force sum over the Boolean
+    hypercube of the layer polynomial built from add~/mult~ (tests/brute.py),
+    an independent definition of the GKR iteration (Sec. 3.1);
+  * the sum-check invariant g_j(0) + g_j(1) = running claim in every round;
+  * closed forms of the benchmark circuits' outputs (Sec. 6.2.1);
+  * completeness and soundness of the verifier (Sec. 2.1).
+"""
+import random
+
+import numpy as np
+import pytest
+
+import brute
+import oracle
+
+P = oracle.P
+
+
+# --- field ---------------------------------------------------------------------
+
+EDGE = [0, 1, 2, P - 1, P - 2, (1 << 60), (1 << 61) - 2, 12345678901234567]
+
+
+def test_field_ops_match_bigint():
+    rng = random.Random(1)
+    vals = EDGE + [rng.randrange(P) for _ in range(300)]
+    for a in vals:
+        for b in vals[:40]:
+            assert oracle.fe_add(a, b) == (a + b) % P
+            assert oracle.fe_sub(a, b) == (a - b) % P
+            assert oracle.fe_mul(a, b) == (a * b) % P
+
+
+def test_field_inverse_and_pow():
+    rng = random.Random(2)
+    for a in [1, 2, P - 1] + [rng.randrange(1, P) for _ in range(50)]:
+        ai = oracle.fe_inv(a)
+        assert a * ai % P == 1
+        e = rng.randrange(1 << 64)
+        assert oracle.fe_pow(a, e) == pow(a, e, P)
+    # Fermat: a^(p-1) = 1 for a != 0 (the identity the F0 circuit relies on)
+    assert oracle.fe_pow(0, P - 1) == 0
+    assert oracle.fe_pow(7, P - 1) == 1
+
+
+# --- multilinear extensions ------------------------------------------------------
+
+def test_mle_boolean_points_and_multilinearity():
+    rng = random.Random(3)
+    for n in range(0, 6):
+        V = [rng.randrange(P) for _ in range(1 << n)]
+        for b in range(1 << n):
+            assert oracle.mle(V, brute.bits(b, n)) == V[b]
+        for _ in range(4):
+            x = [rng.randrange(P) for _ in range(n)]
+            assert oracle.mle(V, x) == brute.mle(V, x)
+            for k in range(n):
+                # degree 1 in each coordinate: value at 2 = 2 * value(1) - value(0)
+                x0, x1, x2 = list(x), list(x), list(x)
+                x0[k], x1[k], x2[k] = 0, 1, 2
+                v0, v1, v2 = (oracle.mle(V, y) for y in (x0, x1, x2))
+                assert v2 == (2 * v1 - v0) % P
+
+
+def test_eq_definition():
+    rng = random.Random(4)
+    for n in range(0, 6):
+        x = [rng.randrange(P) for _ in range(n)]
+        y = [rng.randrange(P) for _ in range(n)]
+        assert oracle.eq(x, y) == brute.eq(x, y)
+        # eq(x, .) sums to 1 over the hypercube
+        assert sum(oracle.eq(x, brute.bits(b, n)) for b in range(1 << n)) % P == 1
+
+
+def test_interpolation_against_polynomials():
+    rng = random.Random(5)
+    for _ in range(20):
+        c = [rng.randrange(P) for _ in range(3)]
+        poly = lambda t: (c[0] + c[1] * t + c[2] * t * t) % P
+        r = rng.randrange(P)
+        assert oracle.interp3(poly(0), poly(1), poly(2), r) == poly(r)
+    for deg in range(0, 9):
+        c = [rng.randrange(P) for _ in range(deg + 1)]
+        poly = lambda t: sum(ci * pow(t, k, P) for k, ci in enumerate(c)) % P
+        x = rng.randrange(P)
+        assert oracle.lagrange([poly(t) for t in range(deg + 1)], x) == poly(x)
+
+
+# --- challenge generator (convention: restated from its published definition) ----
+
+def test_splitmix64_restatement_and_range():
+    def ref(seed, n):
+        s, out = seed, []
+        M = (1 << 64) - 1
+        for _ in range(n):
+            s = (s + 0x9E3779B97F4A7C15) & M
+            z = s
+            z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+            z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+            out.append(z ^ (z >> 31))
+        return out
+    for seed in (0, 1, 0xC0FFEE, (1 << 64) - 1):
+        assert [int(v) for v in oracle.splitmix64(seed, 16)] == ref(seed, 16)
+    ch = oracle.draw_challenges(9, 1000)
+    assert (ch < P).all()
+    assert [int(v) for v in ch[:8]] == [v >> 3 for v in ref(9, 8)]
+
+
+# --- circuit expansions -------------------------------------------------------------
+
+def expand_kind(kind, si, sn):
+    """Gate lists of the structured wiring kinds, written from their definitions."""
+    S = 1 << si
+    if kind == oracle.SQUARE:
+        return [(1, g, g) for g in range(S)]
+    if kind == oracle.TREE:
+        return [(0, 2 * g, 2 * g + 1) for g in range(S)]
+    if kind == oracle.MATMULT:
+        L = si // 3
+        n = 1 << L
+        gates = []
+        for i in range(n):
+            for j in range(n):
+                for k in range(n):
+                    gates.append(None)
+        for i in range(n):
+            for j in range(n):
+                for k in range(n):
+                    gates[i * n * n + j * n + k] = (1, i * n + k, n * n + k * n + j)
+        return gates
+    if kind == oracle.F0_FIRST:
+        return [(1, g // 2, g // 2) if g % 2 == 0 else (0, g // 2, g // 2) for g in range(S)]
+    if kind == oracle.F0_PAIR:
+        return [(1, g, g) if g % 2 == 0 else (1, g, g - 1) for g in range(S)]
+    if kind == oracle.F0_FINAL:
+        return [(1, 2 * g + 1, 2 * g + 1) for g in range(S)]
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("family,logn", [("f2", 3), ("f0", 2), ("matmult", 2), ("matmult", 1)])
+def test_structured_expansion(family, logn):
+    lw, kinds = getattr(oracle, f"{family}_layers")(logn)
+    c = oracle.Circuit(lw, kinds)
+    for i, k in enumerate(kinds):
+        ty, a, b = c.layer_gates(i)
+        ref = expand_kind(k, lw[i], lw[i + 1])
+        assert [(int(t), int(x), int(y)) for t, x, y in zip(ty, a, b)] == ref
+
+
+def test_bad_shapes_rejected():
+    with pytest.raises(ValueError):
+        oracle.Circuit([2, 2], [oracle.TREE])
+    with pytest.raises(ValueError):
+        oracle.Circuit([1, 3], [oracle.SQUARE])
+    with pytest.raises(ValueError):
+        oracle.Circuit([1, 1], [oracle.EXPLICIT],
+                       explicit=[(np.array([0, 1]), np.array([0, 2]), np.array([1, 1]))])
+
+
+# --- the protocol against brute force -----------------------------------------------
+
+def random_explicit(rng, log_width):
+    d = len(log_width) - 1
+    layers = []
+    for i in range(d):
+        S, Sn = 1 << log_width[i], 1 << log_width[i + 1]
+        ty = np.array([rng.randrange(2) for _ in range(S)], np.uint8)
+        a = np.array([rng.randrange(Sn) for _ in range(S)], np.uint32)
+        b = np.array([rng.randrange(Sn) for _ in range(S)], np.uint32)
+        layers.append((ty, a, b))
+    return layers
+
+
+TINY_SHAPES = [[0, 1], [1, 1], [1, 2], [2, 1], [0, 0], [1, 0], [2, 2, 1], [0, 2, 2], [1, 2, 2, 1]]
+
+
+def brute_case(c, gates_by_layer, inputs, seed):
+    vals = c.evaluate(inputs)
+    ch = oracle.draw_challenges(seed, c.num_challenges())
+    return brute.prove(gates_by_layer, c.log_width, vals, ch)
+
+
+@pytest.mark.parametrize("shape", TINY_SHAPES)
+def test_explicit_circuit_matches_brute_force(shape):
+    rng = random.Random(hash(tuple(shape)) & 0xFFFF)
+    layers = random_explicit(rng, shape)
+    c = oracle.Circuit(shape, [oracle.EXPLICIT] * (len(shape) - 1), explicit=layers)
+    x = [rng.randrange(P) for _ in range(1 << shape[-1])]
+    gates = [[(int(t), int(a), int(b)) for t, a, b in zip(*L)] for L in layers]
+    for seed in (1, 77):
+        ref = brute_case(c, gates, x, seed)
+        t1 = c.prove(x, seed, form=1)
+        t2 = c.prove(x, seed, form=2)
+        assert [int(v) for v in t1] == ref
+        assert [int(v) for v in t2] == ref
+        assert c.verify(x, seed, t2) == (True, -1)
+
+
+@pytest.mark.parametrize("family,logn", [("f2", 1), ("f2", 2), ("matmult", 1)])
+def test_structured_circuits_match_brute_force(family, logn):
+    lw, kinds = getattr(oracle, f"{family}_layers")(logn)
+    c = oracle.Circuit(lw, kinds)
+    gates = [expand_kind(k, lw[i], lw[i + 1]) for i, k in enumerate(kinds)]
+    rng = random.Random(logn)
+    x = [rng.randrange(1000) for _ in range(c.n_inputs)]
+    ref = brute_case(c, gates, x, 5)
+    assert [int(v) for v in c.prove(x, 5, form=1)] == ref
+    assert [int(v) for v in c.prove(x, 5, form=2)] == ref
+
+
+def test_f0_power_layers_match_brute_force():
+    """The F0 power layers (first, pair, final) against brute force, on a short
+    circuit that uses each kind once: input -> first -> pair -> final -> tree."""
+    lw = [0, 1, 2, 2, 1]
+    kinds = [oracle.TREE, oracle.F0_FINAL, oracle.F0_PAIR, oracle.F0_FIRST]
+    c = oracle.Circuit(lw, kinds)
+    gates = [expand_kind(k, lw[i], lw[i + 1]) for i, k in enumerate(kinds)]
+    x = [3, 0]
+    ref = brute_case(c, gates, x, 21)
+    assert [int(v) for v in c.prove(x, 21, form=1)] == ref
+    assert [int(v) for v in c.prove(x, 21, form=2)] == ref
+
+
+def replay(c, transcript, seed):
+    """Replay the verifier's claims in Python; returns per-round (g0+g1, claim)
+    pairs and per-layer line data, using only big-integer arithmetic."""
+    ch = [int(v) for v in oracle.draw_challenges(seed, c.num_challenges())]
+    t = [int(v) for v in transcript]
+    lw = c.log_width
+    pos = 1 << lw[0]
+    k = lw[0]
+    z = ch[:k]
+    claim = brute.mle(t[:pos], z)
+    rounds, lines = [], []
+    for i in range(c.d):
+        si, sn = lw[i], lw[i + 1]
+        r = []
+        for j in range(si + 2 * sn):
+            g0, g1, g2 = t[pos:pos + 3]
+            pos += 3
+            rounds.append(((g0 + g1) % P, claim))
+            rj = ch[k]
+            k += 1
+            r.append(rj)
+            # degree-2 interpolation through (0,g0),(1,g1),(2,g2)
+            claim = brute.lagrange([g0, g1, g2], rj)
+        q = t[pos:pos + sn + 1]
+        pos += sn + 1
+        tau = ch[k]
+        k += 1
+        lines.append((i, r[si:si + sn], r[si + sn:], q, tau))
+        z = [(a + tau * (b - a)) % P for a, b in zip(r[si:si + sn], r[si + sn:])]
+        claim = brute.lagrange(q, tau)
+    return rounds, lines
+
+
+@pytest.mark.parametrize("family,logn", [("f2", 5), ("f0", 2), ("matmult", 2)])
+def test_round_invariant_and_line_values(family, logn):
+    lw, kinds = getattr(oracle, f"{family}_layers")(logn)
+    c = oracle.Circuit(lw, kinds)
+    rng = random.Random(9)
+    x = [rng.randrange(50) for _ in range(c.n_inputs)]
+    vals = c.evaluate(x)
+    t = c.prove(x, 3)
+    rounds, lines = replay(c, t, 3)
+    for s, claim in rounds:
+        assert s == claim
+    for i, r1, r2, q, tau in lines:
+        Vn = [int(v) for v in vals[i + 1]]
+        assert q[0] == brute.mle(Vn, r1)
+        assert q[1] == brute.mle(Vn, r2)
+        # degree <= s_{i+1}: the interpolant through q(0..s) predicts V~ on the line
+        s = len(r1)
+        for tt in (s + 1, 12345):
+            pt = [(a + tt * (b - a)) % P for a, b in zip(r1, r2)]
+            assert brute.lagrange(q, tt) == brute.mle(Vn, pt)
+
+
+# --- closed forms (Sec. 6.2.1) --------------------------------------------------------
+
+def test_f2_output_is_sum_of_squares():
+    rng = random.Random(11)
+    for logn in (0, 1, 4, 8):
+        lw, kinds = oracle.f2_layers(logn)
+        c = oracle.Circuit(lw, kinds)
+        x = [rng.randrange(1 << 16) for _ in range(1 << logn)]
+        assert int(c.evaluate(x)[0][0]) == sum(v * v for v in x) % P
+    # large values wrap mod p
+    c = oracle.Circuit(*oracle.f2_layers(2))
+    x = [P - 1, P - 2, 1 << 60, 5]
+    assert int(c.evaluate(x)[0][0]) == sum(v * v for v in x) % P
+
+
+def test_f0_output_is_four_times_distinct_count():
+    rng = random.Random(12)
+    for logn in (1, 3, 6):
+        c = oracle.Circuit(*oracle.f0_layers(logn))
+        x = [rng.choice([0, 0, 1, 2, 1000, P - 1]) for _ in range(1 << logn)]
+        nz = sum(1 for v in x if v)
+        assert int(c.evaluate(x)[0][0]) == 4 * nz % P
+
+
+def test_matmult_output_is_product():
+    rng = np.random.default_rng(13)
+    for logn in (0, 1, 3):
+        n = 1 << logn
+        A = rng.integers(0, 1 << 10, (n, n))
+        B = rng.integers(0, 1 << 10, (n, n))
+        c = oracle.Circuit(*oracle.matmult_layers(logn))
+        out = c.evaluate(np.concatenate([A.reshape(-1), B.reshape(-1)]))[0]
+        assert (out.reshape(n, n).astype(np.int64) == A @ B).all()
+
+
+# --- wiring predicates: generic sum vs closed-form products ------------------------------
+
+def eq3(a, b, c):
+    return (a * b % P * c + (1 - a) * (1 - b) % P * (1 - c)) % P
+
+
+def closed_form(kind, si, sn, p, w1, w2):
+    """add~, mult~ of the structured kinds as products of per-coordinate factors."""
+    prod = lambda xs: __import__("functools").reduce(lambda u, v: u * v % P, xs, 1)
+    if kind == oracle.SQUARE:
+        return 0, prod(eq3(p[k], w1[k], w2[k]) for k in range(si))
+    if kind == oracle.TREE:
+        v = (1 - w1[0]) * w2[0] % P * prod(eq3(p[k], w1[k + 1], w2[k + 1]) for k in range(si))
+        return v % P, 0
+    if kind == oracle.F0_FIRST:
+        base = prod(eq3(p[k + 1], w1[k], w2[k]) for k in range(sn))
+        return p[0] * base % P, (1 - p[0]) * base % P
+    if kind == oracle.F0_PAIR:
+        v = brute.eq1(p[0], w1[0]) * (1 - w2[0]) % P * prod(eq3(p[k], w1[k], w2[k]) for k in range(1, si))
+        return 0, v % P
+    if kind == oracle.F0_FINAL:
+        v = w1[0] * w2[0] % P * prod(eq3(p[k], w1[k + 1], w2[k + 1]) for k in range(si))
+        return 0, v % P
+    if kind == oracle.MATMULT:
+        L = si // 3
+        v = prod(eq3(p[b], w1[b], w2[L + b]) for b in range(L))
+        v = v * prod(brute.eq1(p[L + b], w2[b]) for b in range(L)) % P
+        v = v * prod(brute.eq1(p[2 * L + b], w1[L + b]) for b in range(L)) % P
+        v = v * (1 - w1[2 * L]) % P * w2[2 * L] % P
+        return 0, v
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("kind,si,sn", [
+    (oracle.SQUARE, 3, 3), (oracle.TREE, 2, 3), (oracle.TREE, 0, 1), (oracle.F0_FIRST, 3, 2),
+    (oracle.F0_PAIR, 3, 3), (oracle.F0_FINAL, 2, 3), (oracle.MATMULT, 3, 3), (oracle.MATMULT, 6, 5)])
+def test_wiring_closed_forms(kind, si, sn):
+    c = oracle.Circuit([si, sn], [kind])
+    rng = random.Random(kind * 100 + si)
+    for _ in range(3):
+        p = [rng.randrange(P) for _ in range(si)]
+        w1 = [rng.randrange(P) for _ in range(sn)]
+        w2 = [rng.randrange(P) for _ in range(sn)]
+        assert c.wiring_eval(0, p, w1, w2) == closed_form(kind, si, sn, p, w1, w2)
+
+
+# --- completeness and soundness ----------------------------------------------------------
+
+@pytest.mark.parametrize("family,logn", [("f2", 6), ("f0", 3), ("matmult", 2)])
+def test_honest_prover_accepted(family, logn):
+    c = oracle.Circuit(*getattr(oracle, f"{family}_layers")(logn))
+    rng = random.Random(14)
+    x = [rng.randrange(1 << 16) for _ in range(c.n_inputs)]
+    for seed in range(1, 9):
+        assert c.verify(x, seed, c.prove(x, seed)) == (True, -1)
+
+
+def test_tampering_rejected():
+    c = oracle.Circuit(*oracle.f2_layers(5))
+    rng = random.Random(15)
+    x = [rng.randrange(1 << 16) for _ in range(c.n_inputs)]
+    seed = 4
+    t = c.prove(x, seed)
+    L = len(t)
+    # every single-element change of the transcript is caught
+    for k in range(L):
+        bad = t.copy()
+        bad[k] = (int(bad[k]) + 1 + rng.randrange(P - 1)) % P
+        assert c.verify(x, seed, bad)[0] is False, k
+    # non-canonical transcript values are rejected
+    bad = t.copy()
+    bad[3] = P
+    assert c.verify(x, seed, bad) == (False, -2)
+    # a claim about different inputs is rejected
+    y = list(x)
+    y[7] = (y[7] + 1) % P
+    assert c.verify(y, seed, t)[0] is False
+
+
+def test_wrong_gate_value_rejected():
+    """A prover whose evaluation has one wrong gate (at every layer in turn),
+    with the layers above recomputed from it, is rejected at that layer."""
+    c = oracle.Circuit(*oracle.f2_layers(4))
+    rng = random.Random(16)
+    x = [rng.randrange(1 << 16) for _ in range(c.n_inputs)]
+    ty_all = [c.layer_gates(i) for i in range(c.d)]
+    for layer in range(1, c.d):
+        vals = [v.astype(object) for v in c.evaluate(x)]
+        g = rng.randrange(len(vals[layer]))
+        vals[layer][g] = (int(vals[layer][g]) + 1) % P
+        for i in range(layer - 1, -1, -1):
+            ty, a, b = ty_all[i]
+            vals[i] = np.array([(int(vals[i + 1][a[k]]) * int(vals[i + 1][b[k]])) % P if ty[k]
+                                else (int(vals[i + 1][a[k]]) + int(vals[i + 1][b[k]])) % P
+                                for k in range(len(ty))], dtype=object)
+        t = c.prove_values([np.array(v, dtype=np.uint64) for v in vals], seed=8)
+        ok, where = c.verify(x, 8, t)
+        assert not ok
+        assert where == layer
+
+
+def test_noncanonical_input_rejected_by_evaluate():
+    c = oracle.Circuit(*oracle.f2_layers(2))
+    with pytest.raises(ValueError):
+        c.evaluate([1, 2, P, 3])
