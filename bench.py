@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Benchmark of the GKR/CMT prover on the F2 circuit, n = 2^20 (inputs uniform
+in [0, 2^16]): one step = one proof (evaluation, all sum-check rounds, all line
+reductions) plus its verification, on inputs already resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is whole-job non-input gates per
+second (device time, CUDA events around each step, L2 flushed between steps);
+`e2e` is the same metric through the C ABI with pinned host buffers (uploads
+and the transcript download inside the timed region); `roofline` covers the
+first sum-check wave, the dominant kernel; `cpu_baseline` is the CPU oracle
+timed on this host.  Under torchrun every rank proves its own independent
+instances (the proofs share nothing): weak scaling, no collective on the data
+path.  `--impl reference` times the CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GKR prover gates/s (F2, n=2^20); batched proofs/s and p50/p99 proof latency"
+UNIT = "gates/s"
+WORKLOAD = "f2_2^20"
+SC_CHUNK_LOG = 11
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+# ---- clocks during the timed region --------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---- algorithmic work of the first sum-check wave -----------------------------------------
+
+def sc0_work(widths, kinds):
+    """Field products and table bytes of the first sum-check wave: per pair of
+    entries 3 message products + one fold product per table (P, V and B when
+    the layer has addition gates); phase 1 also forms P = eq(z, x), one product
+    per entry.  Bytes: every table entry read once (8 B)."""
+    mul = 0
+    byts = 0
+    for i, k in enumerate(kinds):
+        has_add = k in (1, 3)
+        for ph, n in ((1, widths[i]), (2, widths[i + 1]), (3, widths[i + 1])):
+            if n == 0:
+                continue
+            nr = min(SC_CHUNK_LOG, n)
+            hasb = ph != 1 and has_add
+            for r in range(nr):
+                mul += (1 << (n - r - 1)) * (5 + (1 if hasb else 0))
+            if ph == 1:
+                mul += 1 << n
+            byts += 8 * (1 << n) * (1 + (0 if ph == 1 else 1) + (1 if hasb else 0))
+    return mul, byts
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---- the oracle on the host cores ---------------------------------------------------------
+
+def _oracle_job(args):
+    logn, seed = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_1202_1350_gb300 import inputs as I
+    c = oracle.Circuit(*oracle.f2_layers(logn))
+    x = I.f2_inputs(logn, 1 << 16, seed)
+    t0 = time.perf_counter()
+    tr = c.prove(x, 1)
+    ok, _ = c.verify(x, 1, tr)
+    return time.perf_counter() - t0, ok
+
+
+def cpu_baseline(logn: int = 20):
+    import oracle
+    oracle.build()
+    cores = max(1, min(8, os.cpu_count() or 1))
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_job, [(logn, 5000 + j) for j in range(cores)])
+    wall = time.perf_counter() - t0
+    gates = 2 * (1 << logn) - 1
+    assert all(ok for _, ok in res)
+    return {"value": cores * gates / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} independent F2 n=2^{logn} prove+verify runs of the C oracle, one per process "
+                      f"({wall:.1f} s wall, {sum(t for t, _ in res):.1f} s CPU)"}
+
+
+def run_reference(args):
+    rank, local, world = env_rank()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1202_1350_gb300 import inputs as I
+    oracle.build()
+    # size each step so the whole run stays within about two minutes
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    logn = 20
+    while logn > 10 and 5.5 * (1 << (logn - 20)) > budget:
+        logn -= 1
+    c = oracle.Circuit(*oracle.f2_layers(logn))
+    gates = 2 * (1 << logn) - 1
+    times = []
+    for k in range(args.warmup + args.steps):
+        x = I.f2_inputs(logn, 1 << 16, 7000 + k)
+        t0 = time.perf_counter()
+        tr = c.prove(x, k + 1)
+        ok, _ = c.verify(x, k + 1, tr)
+        dt = time.perf_counter() - t0
+        assert ok
+        if k >= args.warmup:
+            times.append(dt)
+    ms = 1000 * statistics.mean(times)
+    value = gates / (ms / 1000)
+    sample = f"F2 n=2^{logn} prove+verify per step, single thread of the C oracle"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"F2 n=2^{logn}, x uniform in [0, 2^16], prove + verify", "gates": gates},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- the CUDA path ------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    from paper_1202_1350_gb300 import build as vcbuild
+    from paper_1202_1350_gb300 import circuits, vc
+    from paper_1202_1350_gb300 import inputs as I
+
+    rank, local, world = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    vcbuild.build()
+    fam, logn, gen, seed0 = I.WORKLOADS[WORKLOAD]
+    widths, kinds = circuits.by_name(fam, logn)
+    gates = circuits.non_input_gates(widths)
+    h = vc.vc_circuit_create(widths, kinds, None, local)
+    info = vc.vc_circuit_get_info(h)
+    x = gen(seed0 + rank)
+    xd = torch.from_numpy(x.view(np.int64).copy()).cuda()
+    tr = torch.empty(info["transcript_len"], dtype=torch.int64, device="cuda")
+    acc = torch.zeros(1, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.int64, device="cuda")
+    stage_ev = [torch.cuda.Event(enable_timing=True) for _ in range(vc.NUM_STAGES + 1)]
+    vc.vc_circuit_set_stage_events(h, stage_ev)
+
+    def step(seed):
+        vc.vc_prove(h, xd, seed, tr)
+        vc.vc_verify(h, xd, seed, tr, accept=acc)
+
+    for w in range(args.warmup):
+        flush.zero_()
+        step(100 + w)
+    torch.cuda.synchronize()
+    vc.vc_circuit_sync(h)
+    assert int(acc.item()) == 1, "warm-up proof rejected"
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    step_ms, stage_ms = [], [[] for _ in range(vc.NUM_STAGES)]
+    oks = 0
+    for k in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step(1 + k)
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        for s in range(vc.NUM_STAGES):
+            stage_ms[s].append(stage_ev[s].elapsed_time(stage_ev[s + 1]))
+        oks += int(acc.item())
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    vc.vc_circuit_sync(h)
+    assert oks == args.steps, "a timed proof was rejected"
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * gates * args.steps / (total_ms / 1000)
+
+    # end to end through the C ABI with pinned host buffers
+    xh = torch.from_numpy(x.view(np.int64).copy()).pin_memory()
+    trh = torch.empty(info["transcript_len"], dtype=torch.int64).pin_memory()
+    vc.vc_circuit_set_stage_events(h, None)
+    vc.vc_prove(h, xh, 999, trh)
+    e2e_ms = []
+    for k in range(max(3, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        vc.vc_prove(h, xh, 500 + k, trh)
+        ok = vc.vc_verify(h, xh, 500 + k, trh)
+        e2e_ms.append(1000 * (time.perf_counter() - t0))
+        assert ok
+    e2e_ms_mean = statistics.mean(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e_ms_mean], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms_mean = float(t.item())
+    n_in = 1 << widths[-1]
+    e2e = {"value": world * gates / (e2e_ms_mean / 1000), "unit": UNIT,
+           "h2d_bytes_per_step": 2 * n_in * 8 + info["transcript_len"] * 8,
+           "d2h_bytes_per_step": info["transcript_len"] * 8 + 4 * 8,
+           "ms_per_step": e2e_ms_mean}
+
+    if rank != 0:
+        vc.vc_circuit_destroy(h)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the first sum-check wave (the dominant kernel)
+    sc0_ms = statistics.mean(stage_ms[vc.STAGES.index("sc0")])
+    mul, byts = sc0_work(widths, kinds)
+    rate = vc.vc_field_mul_rate(local, 0, 1 << 14)
+    achieved = mul / (sc0_ms / 1000)
+    stages = {name: round(statistics.mean(v), 4) for name, v in zip(vc.STAGES, stage_ms)}
+    launches = (info["prove_launches"] + info["verify_launches"]) * args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "F2 n=2^20, x uniform in [0, 2^16], prove + verify per step",
+                   "gates": gates, "transcript_u64": info["transcript_len"], "rounds": info["n_rounds"],
+                   "l2": "flushed between steps (256 MiB write outside the step events)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": e2e,
+        "roofline": {"bound": "alu", "kernel": "k_sc_wave (first sum-check wave)",
+                     "achieved": achieved / 1e12, "peak": rate / 1e12, "unit": "Tmulmod/s",
+                     "frac": achieved / rate, "traffic": None,
+                     "peak_source": "measured: vc_field_mul_rate microbenchmark (product + add chains) on this GPU",
+                     "algorithmic_mulmods": mul, "algorithmic_bytes": byts, "kernel_ms": sc0_ms,
+                     "bytes_frac_of_hbm": (byts / (sc0_ms / 1000)) / (measured_peaks().get("hbm_gbs", 6787.9) * 1e9)},
+        "stage_ms": stages,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    vc.vc_circuit_destroy(h)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

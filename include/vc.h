@@ -1,0 +1,202 @@
+/*
+ * vc.h -- C ABI of the GB300 prover/verifier for the GKR/CMT interactive proof
+ * over F_p, p = 2^61 - 1 (Thaler, Roberts, Mitzenmacher, Pfister, "Verifiable
+ * Computation with Massively Parallel Interactive Proofs").
+ *
+ * The calls follow the paper's statement of the problem (Sec. 3.1): prover and
+ * verifier agree on a layered arithmetic circuit of fan-in two; the prover
+ * evaluates it, sends the outputs and then answers the verifier's random
+ * challenges with polynomials; the verifier checks the answers for internal
+ * consistency and finally compares the prover's last claim with one symbol of
+ * the low-degree-extension encoding of the input (Sec. 2.2, Sec. 4.1.2).
+ *
+ * Conventions (the paper defers them to GKR/CMT; these are the readings taken):
+ *   - layer 0 is the output layer, layer d the input layer; layer i has
+ *     S_i = 2^{s_i} gates;
+ *   - multilinear coordinate k (k >= 1) is bit k-1 of a gate index;
+ *   - layer i's identity is summed over (p, w1, w2), bound in that order:
+ *       V~_i(z) = sum eq(z,p) [add~_i (V~_{i+1}(w1) + V~_{i+1}(w2)) + mult~_i V~_{i+1}(w1) V~_{i+1}(w2)];
+ *   - every round message is a degree-2 polynomial sent as its values at 0, 1, 2;
+ *   - two claims about layer i+1 are reduced to one along l(t) = r1 + t (r2 - r1):
+ *     the prover sends q(t) = V~_{i+1}(l(t)) for t = 0..s_{i+1};
+ *   - the verifier's coins come from splitmix64 seeded with `seed` (a challenge
+ *     is next() >> 3, redrawn while it equals p), drawn in this order: s_0
+ *     output coordinates, then for each layer its s_i + 2 s_{i+1} round
+ *     challenges and one line parameter tau.  Both parties replay the same
+ *     stream, so the verifier's coins are fixed by the seed.
+ *
+ * Transcript layout (u64, every entry a canonical field element < p):
+ *   [S_0 outputs]
+ *   ++ for each layer i = 0..d-1:
+ *        [3 (s_i + 2 s_{i+1}) round values: g_j(0), g_j(1), g_j(2) per round j]
+ *        ++ [s_{i+1} + 1 line values q(0) .. q(s_{i+1})]
+ *
+ * Memory: every pointer argument may be host memory or CUDA device memory of
+ * the circuit's device; the library detects which.  The caller owns inputs,
+ * outputs and transcripts; the library owns circuits and all their device
+ * scratch (allocated once by vc_circuit_create).  Device work is ordered on
+ * `stream` (a cudaStream_t, NULL = the legacy default stream).
+ *
+ * Threads: calls on different circuit handles may run concurrently from
+ * different host threads; calls on one handle must not overlap (they share
+ * the handle's scratch).
+ *
+ * Errors: every call returns a vc_status; nothing is thrown across the ABI.
+ * A verifier rejection is not an error: it is reported through *accept.
+ */
+#ifndef VC_H
+#define VC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VC_OK = 0,
+    VC_EINVAL = 1,    /* bad argument, bad circuit shape, non-canonical input */
+    VC_ENOMEM = 2,    /* device or host allocation failed */
+    VC_ECUDA = 3,     /* a CUDA runtime call failed */
+    VC_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+    VC_EBUSY = 5      /* no free capacity (serving admission) */
+} vc_status;
+
+/* How layer i is wired to layer i+1 (Sec. 5.1.4: in-neighbour indices computed
+ * from the gate index; Sec. 6.2.1: the benchmark circuits). */
+typedef enum {
+    VC_WIRE_SQUARE = 0,   /* gate g = MUL(g, g);                 s_i = s_{i+1}     */
+    VC_WIRE_TREE = 1,     /* gate g = ADD(2g, 2g+1);             s_{i+1} = s_i + 1 */
+    VC_WIRE_MATMULT = 2,  /* gate k + n j + n^2 i = MUL(i n + k, n^2 + k n + j);
+                             s_i = 3L, s_{i+1} = 2L + 1, n = 2^L                    */
+    VC_WIRE_F0_FIRST = 3, /* gate 2j = MUL(j, j), 2j+1 = ADD(j, j); s_i = s_{i+1} + 1 */
+    VC_WIRE_F0_PAIR = 4,  /* gate 2j = MUL(2j, 2j), 2j+1 = MUL(2j+1, 2j); s_i = s_{i+1} */
+    VC_WIRE_F0_FINAL = 5, /* gate j = MUL(2j+1, 2j+1);           s_{i+1} = s_i + 1 */
+    VC_WIRE_EXPLICIT = 6  /* gate arrays supplied in vc_circuit_desc                */
+} vc_wiring;
+
+/* Layered circuit description (Sec. 3.1).  Arrays are read during
+ * vc_circuit_create only and may be host memory. */
+typedef struct {
+    uint32_t n_layers;                 /* d >= 1: layers 0 (output) .. d (input)           */
+    const uint32_t *log_width;         /* d + 1 entries, s_0 .. s_d, each <= 30             */
+    const uint32_t *wiring;            /* d entries, vc_wiring of layer i -> i+1            */
+    const uint8_t *const *gate_type;   /* d entries; for EXPLICIT layers: S_i bytes,
+                                          0 = ADD, 1 = MUL; other entries may be NULL      */
+    const uint32_t *const *in1;        /* d entries; EXPLICIT: S_i first in-neighbours     */
+    const uint32_t *const *in2;        /* d entries; EXPLICIT: S_i second in-neighbours    */
+} vc_circuit_desc;
+
+typedef struct vc_circuit vc_circuit;
+
+/* Validate a description, build the launch plan and allocate all device
+ * scratch on `device`.  VC_EINVAL: widths do not fit a wiring kind, an
+ * in-neighbour is out of range, or d = 0.  VC_ENOMEM: not enough device memory.
+ * On success *out owns the circuit until vc_circuit_destroy. */
+vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, vc_circuit **out);
+
+/* Free the circuit and its device scratch (synchronises its device).  NULL is
+ * accepted. */
+vc_status vc_circuit_destroy(vc_circuit *c);
+
+/* Transcript length in u64 for this circuit (fixed by its shape). */
+vc_status vc_transcript_len(const vc_circuit *c, uint64_t *n_u64);
+
+/* Device bytes the circuit holds (scratch + plan). */
+vc_status vc_circuit_bytes(const vc_circuit *c, uint64_t *bytes);
+
+/* Layer-by-layer evaluation (Sec. 6.2.4: the prover's first step).
+ * inputs: S_d canonical field elements; outputs: S_0 elements.  Synchronous:
+ * returns after `outputs` is written.  VC_EINVAL if an input is >= p. */
+vc_status vc_evaluate(vc_circuit *c, const uint64_t *inputs, uint64_t *outputs, void *stream);
+
+/* Prover (Sec. 3.1, Sec. 4.1.1): evaluate the circuit on `inputs` (S_d
+ * canonical elements) and write the whole transcript for the verifier coins
+ * derived from `seed`.  transcript: vc_transcript_len() u64.
+ * If `inputs` and `transcript` are both device memory the call is
+ * asynchronous with respect to the host: a non-canonical input is then
+ * latched in the circuit and reported by the next vc_circuit_sync.
+ * Otherwise the call returns after the transcript is written and reports
+ * VC_EINVAL itself. */
+vc_status vc_prove(vc_circuit *c, const uint64_t *inputs, uint64_t seed,
+                   uint64_t *transcript, void *stream);
+
+/* Wait for the circuit's queued work on `stream` and return (and clear) any
+ * error latched by asynchronous calls. */
+vc_status vc_circuit_sync(vc_circuit *c, void *stream);
+
+/* Verifier (Sec. 2.2, Sec. 3.1, Sec. 4.1.2): replay the coins of `seed`,
+ * check every round (g(0) + g(1) = running claim), every layer's final claim
+ * against add~/mult~ at the bound point, and the last claim against the
+ * input's multilinear extension at the final point.  *accept = 1 or 0.
+ * A transcript entry >= p is a rejection, not an error.  If `accept`,
+ * `inputs` and `transcript` are all device memory the call is asynchronous
+ * (the int at `accept` is written on the stream; a non-canonical input is
+ * latched for vc_circuit_sync); otherwise it returns after *accept is set and
+ * reports VC_EINVAL for an input >= p itself. */
+vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t seed,
+                    const uint64_t *transcript, int *accept, void *stream);
+
+/* Launch sequence of a proof, for timing individual stages: a proof is the
+ * stages below in this order (some may be empty for small circuits). */
+typedef enum {
+    VC_STAGE_SETUP = 0,  /* coins, layer points, eq(z_i, r_P)                    */
+    VC_STAGE_EQ = 1,     /* split eq tables                                       */
+    VC_STAGE_EVAL = 2,   /* layer-by-layer evaluation                             */
+    VC_STAGE_LINE = 3,   /* line-reduction polynomials q_i                        */
+    VC_STAGE_BUILD = 4,  /* phase-2/3 tables from the wiring                      */
+    VC_STAGE_SC0 = 5,    /* first sum-check wave (the bulk of the arithmetic)     */
+    VC_STAGE_SC1 = 6,    /* remaining sum-check waves                             */
+    VC_STAGE_FINAL = 7,  /* per-round reductions into the transcript              */
+    VC_NUM_STAGES = 8
+} vc_stage;
+
+/* Record CUDA events at stage boundaries of every later vc_prove on this
+ * circuit: events[k] (a cudaEvent_t) just before stage k, events[VC_NUM_STAGES]
+ * after the last.  `events` must hold VC_NUM_STAGES + 1 events created on the
+ * circuit's device, owned by the caller; NULL turns recording off. */
+vc_status vc_circuit_set_stage_events(vc_circuit *c, void *const *events);
+
+/* Shape facts of a circuit. */
+typedef struct {
+    uint32_t n_layers;           /* d                                             */
+    uint32_t n_rounds;           /* sum-check rounds over all layers              */
+    uint64_t transcript_len;     /* u64 entries                                   */
+    uint64_t gates;              /* non-input gates                               */
+    uint64_t device_bytes;       /* scratch + plan held on the device             */
+    uint32_t prove_launches;     /* kernel launches per vc_prove                  */
+    uint32_t verify_launches;    /* kernel launches per vc_verify                 */
+    uint32_t sc0_ctas;           /* CTAs of the first sum-check wave              */
+    uint32_t pad;
+} vc_circuit_info;
+
+vc_status vc_circuit_get_info(const vc_circuit *c, vc_circuit_info *info);
+
+/* Batched proving: n independent (circuit, inputs, seed) jobs in one set of
+ * merged launches; circuits must be distinct handles on one device.
+ * Same pointer rules as vc_prove; synchronous unless every pointer is device
+ * memory. */
+vc_status vc_prove_batch(vc_circuit *const *circuits, const uint64_t *const *inputs,
+                         const uint64_t *seeds, uint64_t *const *transcripts, int n,
+                         void *stream);
+
+/* Elementwise field product out[k] = a[k] b[k] mod p on the device (device
+ * pointers, n elements, canonical inputs).  Used to check the device field
+ * arithmetic.  Asynchronous. */
+vc_status vc_field_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t n,
+                       void *stream);
+
+/* Field-multiply issue-rate microbenchmark: runs `iters` dependent products on
+ * `chains` independent chains per thread over a grid that fills the device,
+ * and returns the measured products per second (CUDA events) in *rate.
+ * variant 0: 32-bit-limb Mersenne product; 1: 64x64->128 product then fold. */
+vc_status vc_field_mul_rate(int device, int variant, uint64_t iters, double *rate);
+
+/* Human-readable name of a status code (static string). */
+const char *vc_status_string(vc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VC_H */

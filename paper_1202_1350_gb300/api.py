@@ -1,0 +1,86 @@
+"""Convenience wrapper over the C ABI: a circuit handle with torch-tensor I/O.
+
+Field elements travel as 64-bit torch tensors (int64 storage; every value is
+below p < 2^63, so the bits are the same as uint64).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import circuits as _circuits
+from . import vc as _vc
+
+
+def _as_tensor(x, device):
+    import torch
+    if isinstance(x, torch.Tensor):
+        return x
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.uint64)).view(np.int64)
+    return torch.from_numpy(a.copy()).to(device)
+
+
+class Circuit:
+    def __init__(self, log_width, wiring, explicit=None, device: int = 0):
+        self.log_width = [int(s) for s in log_width]
+        self.wiring = [int(k) for k in wiring]
+        self.device = device
+        self.handle = _vc.vc_circuit_create(self.log_width, self.wiring, explicit, device)
+        self.transcript_len = _vc.vc_transcript_len(self.handle)
+
+    @classmethod
+    def f2(cls, logn: int, device: int = 0):
+        return cls(*_circuits.f2(logn), device=device)
+
+    @classmethod
+    def f0(cls, logn: int, device: int = 0):
+        return cls(*_circuits.f0(logn), device=device)
+
+    @classmethod
+    def matmult(cls, logn: int, device: int = 0):
+        return cls(*_circuits.matmult(logn), device=device)
+
+    @property
+    def n_inputs(self) -> int:
+        return 1 << self.log_width[-1]
+
+    @property
+    def n_outputs(self) -> int:
+        return 1 << self.log_width[0]
+
+    @property
+    def gates(self) -> int:
+        return _circuits.non_input_gates(self.log_width)
+
+    def new_transcript(self):
+        import torch
+        return torch.empty(self.transcript_len, dtype=torch.int64, device=f"cuda:{self.device}")
+
+    def evaluate(self, inputs):
+        import torch
+        x = _as_tensor(inputs, f"cuda:{self.device}")
+        out = torch.empty(self.n_outputs, dtype=torch.int64, device=x.device)
+        _vc.vc_evaluate(self.handle, x, out, device=self.device)
+        return out
+
+    def prove(self, inputs, seed: int, transcript=None, sync: bool = True):
+        x = _as_tensor(inputs, f"cuda:{self.device}")
+        tr = self.new_transcript() if transcript is None else transcript
+        _vc.vc_prove(self.handle, x, seed, tr, device=self.device)
+        if sync:
+            _vc.vc_circuit_sync(self.handle, device=self.device)
+        return tr
+
+    def verify(self, inputs, seed: int, transcript) -> bool:
+        x = _as_tensor(inputs, f"cuda:{self.device}")
+        return _vc.vc_verify(self.handle, x, seed, transcript, device=self.device)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _vc.vc_circuit_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

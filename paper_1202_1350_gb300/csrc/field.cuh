@@ -1,0 +1,104 @@
+// field.cuh -- device arithmetic in F_p, p = 2^61 - 1 (Sec. 6.1 of the paper:
+// a Mersenne prime, so reduction is shifts and masks; Sec. 5.1.4: a product
+// costs a few machine multiplies).  Every value handled here is canonical,
+// i.e. in [0, p).
+#pragma once
+#include <stdint.h>
+
+typedef uint64_t u64;
+typedef unsigned int u32;
+
+#define FP_P 0x1FFFFFFFFFFFFFFFull
+
+__host__ __device__ __forceinline__ u64 f_add(u64 a, u64 b)
+{
+    u64 s = a + b;  // < 2^62, no wrap
+    return s >= FP_P ? s - FP_P : s;
+}
+
+__host__ __device__ __forceinline__ u64 f_sub(u64 a, u64 b)
+{
+    return a >= b ? a - b : a + (FP_P - b);
+}
+
+__host__ __device__ __forceinline__ u64 f_neg(u64 a) { return a ? FP_P - a : 0; }
+
+// 2a - b, the value at t = 2 of the line through (0, b) and (1, a).
+__host__ __device__ __forceinline__ u64 f_ext2(u64 a1, u64 a0) { return f_sub(f_add(a1, a1), a0); }
+
+// Product with 32-bit limbs.  a = a1 2^32 + a0 with a1, b1 < 2^29 (canonical
+// inputs), so
+//   a b = a1 b1 2^64 + (a1 b0 + a0 b1) 2^32 + a0 b0,   mid = a1 b0 + a0 b1 < 2^62.
+// Using 2^61 = 1 and 2^64 = 8 (mod p):
+//   mid 2^32 = (mid >> 29) 2^61 + (mid mod 2^29) 2^32 = (mid >> 29) + (mid mod 2^29) 2^32,
+//   a0 b0    = (a0 b0 mod 2^61) + (a0 b0 >> 61).
+// The five terms sum to less than 3 2^61 + 2^34 < 2^63; one more fold leaves
+// a value below p + 4, and one conditional subtraction makes it canonical.
+__device__ __forceinline__ u64 f_mul(u64 a, u64 b)
+{
+    const u32 a0 = (u32)a, a1 = (u32)(a >> 32);
+    const u32 b0 = (u32)b, b1 = (u32)(b >> 32);
+    const u64 lo = (u64)a0 * b0;
+    const u64 mid = (u64)a1 * b0 + (u64)a0 * b1;
+    const u64 hi = (u64)a1 * b1;
+    u64 s = (hi << 3) + (mid >> 29) + ((mid & 0x1FFFFFFFull) << 32) + (lo & FP_P) + (lo >> 61);
+    s = (s & FP_P) + (s >> 61);
+    return s >= FP_P ? s - FP_P : s;
+}
+
+// Product with a full 64x64 -> 128 multiply and one Mersenne fold:
+// a b = hi 2^64 + lo, (a b) mod 2^61 = lo & p, (a b) >> 61 = (hi << 3) | (lo >> 61);
+// both parts are below p because a b <= (p-1)^2 < p 2^61, so one conditional
+// subtraction suffices.
+__device__ __forceinline__ u64 f_mul_wide(u64 a, u64 b)
+{
+    const u64 lo = a * b;
+    const u64 hi = __umul64hi(a, b);
+    u64 s = (lo & FP_P) + ((lo >> 61) | (hi << 3));
+    return s >= FP_P ? s - FP_P : s;
+}
+
+// Host-side product for plan-time constants (never on the proof path).
+static inline u64 h_mul(u64 a, u64 b)
+{
+    unsigned __int128 x = (unsigned __int128)a * b;
+    u64 s = (u64)(x & FP_P) + (u64)(x >> 61);
+    return s >= FP_P ? s - FP_P : s;
+}
+
+// Sum of a and b where both are canonical: lazy-free add used in reductions.
+__device__ __forceinline__ u64 f_add3(u64 a, u64 b, u64 c) { return f_add(f_add(a, b), c); }
+
+// Fermat inverse a^(p-2) (a != 0): square-and-multiply over the bits of p - 2.
+__device__ __forceinline__ u64 f_inv(u64 a)
+{
+    u64 r = 1, b = a;
+    u64 e = FP_P - 2;
+    while (e) {
+        if (e & 1) r = f_mul(r, b);
+        b = f_mul(b, b);
+        e >>= 1;
+    }
+    return r;
+}
+
+// 1/2 = 2^60 mod p, since 2 * 2^60 = 2^61 = 1.
+#define FP_INV2 0x1000000000000000ull
+
+// splitmix64 (Steele, Lea, Flood 2014): output number k (k >= 1) of the
+// generator started at `seed` is mix(seed + k * gamma).
+__device__ __forceinline__ u64 splitmix64_at(u64 seed, u64 k)
+{
+    u64 z = seed + k * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Warp-wide field sum (all 32 lanes participate).
+__device__ __forceinline__ u64 warp_sum(u64 v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = f_add(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}

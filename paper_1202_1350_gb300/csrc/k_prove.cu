@@ -1,0 +1,669 @@
+// k_prove.cu -- prover kernels for the GKR/CMT protocol over F_p, p = 2^61 - 1.
+//
+// Paper: Thaler, Roberts, Mitzenmacher, Pfister, "Verifiable Computation with
+// Massively Parallel Interactive Proofs".
+//   Sec. 3.1   one iteration per layer, each touching two adjacent layers;
+//   Sec. 4.1.1 every gate contributes independently to each prover message,
+//              which is the field sum of the contributions (parallel reduction);
+//   Sec. 5.1.4 in-neighbour indices from the gate index; coalesced accesses.
+//
+// The prover here folds tables instead of recomputing per-gate contributions
+// from scratch each round (the folding form gives the same messages; each
+// round halves the tables), and runs every layer's sum-check phases and line
+// reduction concurrently, since all verifier coins follow from the seed.
+#include <cuda_runtime.h>
+#include "plan.h"
+
+// --------------------------------------------------------------------------------
+// Setup: verifier coins (splitmix64 stream), the layer points z_i, eq(z_i, r_P).
+// --------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(1024) k_setup(Globals G, u32 zd_off)
+{
+    __shared__ int s_rej;
+    if (threadIdx.x == 0) s_rej = 0;
+    __syncthreads();
+    // Challenge c is the (c+1)-th accepted draw; draws equal to p (probability
+    // 2^-61 each) are rejected, so in the common case draw c is output c+1.
+    for (u32 c = threadIdx.x; c < G.nchal; c += blockDim.x) {
+        u64 x = splitmix64_at(G.seed, (u64)c + 1) >> 3;
+        G.chal[c] = x;
+        if (x == FP_P) s_rej = 1;
+    }
+    __syncthreads();
+    if (s_rej) {
+        if (threadIdx.x == 0) {
+            u64 k = 1;
+            for (u32 c = 0; c < G.nchal; c++) {
+                u64 x;
+                do { x = splitmix64_at(G.seed, k++) >> 3; } while (x == FP_P);
+                G.chal[c] = x;
+            }
+        }
+        __syncthreads();
+    }
+    const LayerDev *L = G.layers;
+    // z_0: the first s_0 challenges.
+    for (u32 k = threadIdx.x; k < L[0].s; k += blockDim.x) G.pts[L[0].z_off + k] = G.chal[k];
+    // z_{i+1} = l_i(tau_i) = r1 + tau (r2 - r1).
+    for (u32 i = 0; i < G.d; i++) {
+        const u32 si = L[i].s, sn = L[i].sn, co = L[i].chal_off;
+        const u64 tau = G.chal[co + si + 2 * sn];
+        u64 *zn = G.pts + ((i + 1 < G.d) ? L[i + 1].z_off : zd_off);
+        for (u32 k = threadIdx.x; k < sn; k += blockDim.x) {
+            u64 r1 = G.chal[co + si + k], r2 = G.chal[co + si + sn + k];
+            zn[k] = f_add(r1, f_mul(tau, f_sub(r2, r1)));
+        }
+    }
+    __syncthreads();
+    // eq(z_i, r_P) per layer.
+    for (u32 i = threadIdx.x; i < G.d; i += blockDim.x) {
+        const u64 *z = G.pts + L[i].z_off;
+        const u64 *rp = G.chal + L[i].chal_off;
+        u64 e = 1;
+        for (u32 k = 0; k < L[i].s; k++)
+            e = f_mul(e, f_add(f_mul(z[k], rp[k]), f_mul(f_sub(1, z[k]), f_sub(1, rp[k]))));
+        G.scal[SCAL_EQZRP(i)] = e;
+    }
+}
+
+void launch_setup(const Globals &G, u32 zd_off, cudaStream_t st)
+{
+    k_setup<<<1, 1024, 0, st>>>(G, zd_off);
+}
+
+// --------------------------------------------------------------------------------
+// Split eq tables: lo[j] = prod_{k<h} eq(x_k, bit_k j), hi[j] = prod_{k<n-h} eq(x_{h+k}, bit_k j).
+// --------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_eqtabs(const EqJob *jobs)
+{
+    const EqTab t = jobs[blockIdx.x].t;
+    __shared__ u64 x[64], xm[64];
+    for (u32 k = threadIdx.x; k < t.n; k += blockDim.x) {
+        x[k] = t.pt[k];
+        xm[k] = f_sub(1, x[k]);
+    }
+    __syncthreads();
+    const u32 h = t.h, hh = t.n - t.h;
+    for (u32 j = threadIdx.x; j < (1u << h); j += blockDim.x) {
+        u64 e = 1;
+        for (u32 k = 0; k < h; k++) e = f_mul(e, ((j >> k) & 1) ? x[k] : xm[k]);
+        t.lo[j] = e;
+    }
+    for (u32 j = threadIdx.x; j < (1u << hh); j += blockDim.x) {
+        u64 e = 1;
+        for (u32 k = 0; k < hh; k++) e = f_mul(e, ((j >> k) & 1) ? x[h + k] : xm[h + k]);
+        t.hi[j] = e;
+    }
+}
+
+void launch_eqtabs(const EqJob *jobs, int njobs, cudaStream_t st)
+{
+    if (njobs > 0) k_eqtabs<<<njobs, 256, 0, st>>>(jobs);
+}
+
+// --------------------------------------------------------------------------------
+// Wiring: in-neighbours and gate type of gate g (Sec. 5.1.4, Sec. 6.2.1).
+// --------------------------------------------------------------------------------
+
+__device__ __forceinline__ void gate_wiring(const LayerDev &L, u64 g, u64 &a, u64 &b, u32 &mul)
+{
+    switch (L.kind) {
+    case W_SQUARE: a = g; b = g; mul = 1; break;
+    case W_TREE: a = 2 * g; b = 2 * g + 1; mul = 0; break;
+    case W_MATMULT: {
+        const u32 Lb = L.s / 3;
+        const u64 n = 1ull << Lb, m = n - 1;
+        const u64 k = g & m, j = (g >> Lb) & m, ii = g >> (2 * Lb);
+        a = (ii << Lb) | k;
+        b = (1ull << (2 * Lb)) | (k << Lb) | j;
+        mul = 1;
+        break;
+    }
+    case W_F0_FIRST: a = g >> 1; b = g >> 1; mul = (g & 1) ? 0 : 1; break;
+    case W_F0_PAIR: a = g; b = g & ~1ull; mul = 1; break;
+    case W_F0_FINAL: a = 2 * g + 1; b = 2 * g + 1; mul = 1; break;
+    default: a = L.in1[g]; b = L.in2[g]; mul = L.type[g]; break;
+    }
+}
+
+// Layer evaluation: V_i[g] = V_{i+1}[in1] op V_{i+1}[in2] (Sec. 6.2.4).
+__global__ void __launch_bounds__(256) k_eval_layer(const LayerDev L)
+{
+    const u64 S = 1ull << L.s;
+    for (u64 g = blockIdx.x * (u64)blockDim.x + threadIdx.x; g < S; g += (u64)gridDim.x * blockDim.x) {
+        u64 a, b;
+        u32 mul;
+        gate_wiring(L, g, a, b, mul);
+        const u64 x = L.Vn[a], y = L.Vn[b];
+        L.V[g] = mul ? f_mul(x, y) : f_add(x, y);
+    }
+}
+
+void launch_eval_layer(const Globals &G, const LayerDev &L, int i, cudaStream_t st)
+{
+    (void)G;
+    (void)i;
+    const u64 S = 1ull << L.s;
+    u64 blocks = (S + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_eval_layer<<<(unsigned)blocks, 256, 0, st>>>(L);
+}
+
+__global__ void k_check_canonical(const u64 *x, u64 n, u32 *status)
+{
+    bool bad = false;
+    for (u64 k = blockIdx.x * (u64)blockDim.x + threadIdx.x; k < n; k += (u64)gridDim.x * blockDim.x)
+        bad |= (x[k] >= FP_P);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_BAD_INPUT);
+}
+
+void launch_check_canonical(const u64 *x, u64 n, u32 *status, cudaStream_t st)
+{
+    u64 blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks == 0) blocks = 1;
+    k_check_canonical<<<(unsigned)blocks, 256, 0, st>>>(x, n, status);
+}
+
+// --------------------------------------------------------------------------------
+// Line reduction: q(t) = V~_{i+1}(l(t)), folding V_{i+1} with coordinates
+// a_k + b_k t in coefficient form (degree grows by one per folded coordinate).
+// --------------------------------------------------------------------------------
+
+#define LN_NT 256
+#define LN_E 3
+#define LN_SP 32  // coefficient stride in shared memory (degree <= 31)
+
+// One coefficient of the fold of polynomials A (lower) and B (upper) with
+// a + b t:  out_c = A_c + a (B_c - A_c) + b (B_{c-1} - A_{c-1}).
+__device__ __forceinline__ u64 poly_fold_coef(const u64 *A, const u64 *B, u32 deg, u32 c, u64 a, u64 b)
+{
+    u64 dc = (c <= deg) ? f_sub(B[c], A[c]) : 0;
+    u64 dm = (c >= 1) ? f_sub(B[c - 1], A[c - 1]) : 0;
+    u64 ac = (c <= deg) ? A[c] : 0;
+    return f_add(ac, f_add(f_mul(a, dc), f_mul(b, dm)));
+}
+
+extern __shared__ u64 ln_dyn[];
+
+__global__ void __launch_bounds__(LN_NT) k_line_wave(Globals G, const LineWaveDev *waves, const Item *items)
+{
+    const Item it = items[blockIdx.x];
+    const LineWaveDev W = waves[it.wave];
+    const u32 tid = threadIdx.x;
+    __shared__ u64 sa[32], sb[32];
+    if (tid < W.nl) {
+        u64 a = G.chal[W.a_off + W.l0 + tid];
+        sa[tid] = a;
+        sb[tid] = f_sub(G.chal[W.b_off + W.l0 + tid], a);
+    }
+    __syncthreads();
+    u64 *bufA = ln_dyn;                       // LN_NT polys
+    u64 *bufB = ln_dyn + LN_NT * LN_SP;       // LN_NT / 2 polys
+    u32 m;        // polys in the current level
+    u32 deg;      // their degree
+    u32 done;     // coordinates of this wave already folded
+    if (W.l0 == 0) {
+        // Entries are field values (degree 0).  Each thread folds a run of 2^e
+        // consecutive entries in registers.
+        const u32 e = (W.nl >= LN_E) ? LN_E : 0;
+        const u32 na = 1u << (W.nl - e);
+        const u64 base = (u64)it.chunk << W.nl;
+        bool bad = false;
+        if (tid < na) {
+            if (e == LN_E) {
+                u64 v[8];
+                const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(W.in + base + ((u64)tid << LN_E));
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    ulonglong2 w = src[q];
+                    v[2 * q] = w.x;
+                    v[2 * q + 1] = w.y;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; q++) bad |= (v[q] >= FP_P);
+                // level 1: 4 linear polys c0 + c1 t
+                u64 c1[4][2];
+                {
+                    const u64 a = sa[0], b = sb[0];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        u64 dd = f_sub(v[2 * q + 1], v[2 * q]);
+                        c1[q][0] = f_add(v[2 * q], f_mul(a, dd));
+                        c1[q][1] = f_mul(b, dd);
+                    }
+                }
+                u64 c2[2][3];
+                {
+                    const u64 a = sa[1], b = sb[1];
+#pragma unroll
+                    for (int q = 0; q < 2; q++) {
+                        const u64 *A = c1[2 * q], *B = c1[2 * q + 1];
+#pragma unroll
+                        for (int c = 0; c < 3; c++) c2[q][c] = poly_fold_coef(A, B, 1, c, a, b);
+                    }
+                }
+                u64 *dst = bufA + tid * LN_SP;
+                {
+                    const u64 a = sa[2], b = sb[2];
+#pragma unroll
+                    for (int c = 0; c < 4; c++) dst[c] = poly_fold_coef(c2[0], c2[1], 2, c, a, b);
+                }
+            } else {
+                u64 x = W.in[base + tid];
+                bad |= (x >= FP_P);
+                bufA[tid * LN_SP] = x;
+            }
+        }
+        if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(G.status, ST_BAD_INPUT);
+        m = na;
+        deg = e;
+        done = e;
+    } else {
+        // Entries are polynomials of degree l0 from the previous wave: each
+        // thread loads two and folds them with the first coordinate.
+        const u32 din = W.l0;
+        const u32 npoly = 1u << W.nl;
+        const u64 base = (u64)it.chunk << W.nl;
+        const u32 half = npoly >> 1;
+        for (u32 idx = tid; idx < half * (din + 2); idx += LN_NT) {
+            const u32 j = idx / (din + 2), c = idx % (din + 2);
+            const u64 *A = W.in + (base + 2 * j) * (din + 1);
+            const u64 *B = A + (din + 1);
+            bufA[j * LN_SP + c] = poly_fold_coef(A, B, din, c, sa[0], sb[0]);
+        }
+        m = half;
+        deg = din + 1;
+        done = 1;
+        if (W.nl == 0) {  // cannot happen (waves after the first fold >= 1 coordinate)
+            m = 1;
+        }
+    }
+    __syncthreads();
+    // Remaining coordinates of this wave, in shared memory (ping-pong A <-> B).
+    u64 *cur = bufA, *nxt = bufB;
+    for (u32 k = done; k < W.nl; k++) {
+        const u32 half = m >> 1;
+        for (u32 idx = tid; idx < half * (deg + 2); idx += LN_NT) {
+            const u32 j = idx / (deg + 2), c = idx % (deg + 2);
+            nxt[j * LN_SP + c] = poly_fold_coef(cur + (2 * j) * LN_SP, cur + (2 * j + 1) * LN_SP, deg, c, sa[k], sb[k]);
+        }
+        __syncthreads();
+        u64 *t = cur; cur = nxt; nxt = t;
+        m = half;
+        deg += 1;
+    }
+    // cur[0..deg] is this chunk's polynomial.
+    if (!W.last) {
+        for (u32 c = tid; c <= deg; c += LN_NT) W.out[(u64)it.chunk * (deg + 1) + c] = cur[c];
+    } else {
+        // q(t) for t = 0..n by Horner; q(0) = V~_{i+1}(r1) feeds phase 3.
+        for (u32 t = tid; t <= W.n; t += LN_NT) {
+            u64 acc = cur[deg];
+            for (int c = (int)deg - 1; c >= 0; c--) acc = f_add(f_mul(acc, (u64)t), cur[c]);
+            G.tr[W.tr_q + t] = acc;
+        }
+        if (tid == 0) G.scal[SCAL_V1(W.layer)] = cur[0];
+    }
+}
+
+void launch_line_wave(const Globals &G, const LineWaveDev *lw, const Item *items, int nitems, cudaStream_t st)
+{
+    if (nitems <= 0) return;
+    const size_t smem = (size_t)(LN_NT + LN_NT / 2) * LN_SP * sizeof(u64);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_line_wave, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    k_line_wave<<<nitems, LN_NT, smem, st>>>(G, lw, items);
+}
+
+// --------------------------------------------------------------------------------
+// Phase-2/3 tables over layer i+1, gathered per entry w (no atomics).
+//   w_g = eq(z, r_P) eq(r_P, g),   u_g = w_g eq(r1, in1(g))
+//   P2[w] = sum_{g: in1=w} w_g [ADD: 1, MUL: V(in2)],   B2[w] = sum_{ADD g: in1=w} w_g V(in2)
+//   A2[w] = sum_{ADD g: in2=w} u_g,   M2[w] = sum_{MUL g: in2=w} u_g
+//   P3 = A2 + v1 M2,   B3 = v1 A2,   v1 = V~_{i+1}(r1)
+// Phase-2 message: sum P2 V + B2; phase-3 message: sum P3 V + B3.
+// --------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_build23(Globals G, const u32 *blk_off, int nlayers)
+{
+    // which layer: last i with blk_off[i] <= blockIdx.x
+    int lo = 0, hi = nlayers;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (blk_off[mid] <= blockIdx.x) lo = mid; else hi = mid;
+    }
+    const int i = lo;
+    const LayerDev &L = G.layers[i];
+    const u64 w = (u64)(blockIdx.x - blk_off[i]) * blockDim.x + threadIdx.x;
+    const u64 Sn = 1ull << L.sn;
+    if (w >= Sn) return;
+    const u64 ez = G.scal[SCAL_EQZRP(i)];
+    const u64 v1 = G.scal[SCAL_V1(i)];
+    const u64 *V = L.Vn;
+    u64 P2 = 0, B2 = 0, A2 = 0, M2 = 0;
+    switch (L.kind) {
+    case W_SQUARE: {
+        const u64 wg = f_mul(ez, eq_at(L.trp, w));
+        P2 = f_mul(wg, V[w]);
+        M2 = f_mul(wg, eq_at(L.tr1, w));
+        break;
+    }
+    case W_TREE: {
+        if ((w & 1) == 0) {
+            const u64 wg = f_mul(ez, eq_at(L.trp, w >> 1));
+            P2 = wg;
+            B2 = f_mul(wg, V[w + 1]);
+        } else {
+            const u64 g = w >> 1;
+            const u64 wg = f_mul(ez, eq_at(L.trp, g));
+            A2 = f_mul(wg, eq_at(L.tr1, w - 1));
+        }
+        break;
+    }
+    case W_F0_FIRST: {
+        const u64 wm = f_mul(ez, eq_at(L.trp, 2 * w));      // MUL gate 2w
+        const u64 wa = f_mul(ez, eq_at(L.trp, 2 * w + 1));  // ADD gate 2w+1
+        const u64 e1 = eq_at(L.tr1, w);
+        P2 = f_add(f_mul(wm, V[w]), wa);
+        B2 = f_mul(wa, V[w]);
+        A2 = f_mul(wa, e1);
+        M2 = f_mul(wm, e1);
+        break;
+    }
+    case W_F0_PAIR: {
+        const u64 wg = f_mul(ez, eq_at(L.trp, w));
+        P2 = f_mul(wg, V[w & ~1ull]);
+        if ((w & 1) == 0) {
+            const u64 wg1 = f_mul(ez, eq_at(L.trp, w + 1));
+            M2 = f_add(f_mul(wg, eq_at(L.tr1, w)), f_mul(wg1, eq_at(L.tr1, w + 1)));
+        }
+        break;
+    }
+    case W_F0_FINAL: {
+        if (w & 1) {
+            const u64 g = w >> 1;
+            const u64 wg = f_mul(ez, eq_at(L.trp, g));
+            P2 = f_mul(wg, V[w]);
+            M2 = f_mul(wg, eq_at(L.tr1, w));
+        }
+        break;
+    }
+    case W_MATMULT: {
+        const u32 Lb = L.s / 3;
+        const u64 n = 1ull << Lb, msk = n - 1;
+        if (w < (1ull << (2 * Lb))) {
+            // gates with in1 = w: k = w mod n, i = w >> L, all j
+            const u64 k = w & msk, ii = w >> Lb;
+            u64 acc = 0;
+            for (u64 j = 0; j < n; j++) {
+                const u64 g = k | (j << Lb) | (ii << (2 * Lb));
+                const u64 bidx = (1ull << (2 * Lb)) | (k << Lb) | j;
+                acc = f_add(acc, f_mul(eq_at(L.trp, g), V[bidx]));
+            }
+            P2 = f_mul(ez, acc);
+        } else {
+            // gates with in2 = w: j = w mod n, k = (w >> L) mod n, all i
+            const u64 j = w & msk, k = (w >> Lb) & msk;
+            u64 acc = 0;
+            for (u64 ii = 0; ii < n; ii++) {
+                const u64 g = k | (j << Lb) | (ii << (2 * Lb));
+                acc = f_add(acc, f_mul(eq_at(L.trp, g), eq_at(L.tr1, (ii << Lb) | k)));
+            }
+            M2 = f_mul(ez, acc);
+        }
+        break;
+    }
+    default: {  // explicit wiring, gates grouped by in1 and by in2
+        for (u32 q = L.by1_off[w]; q < L.by1_off[w + 1]; q++) {
+            const u32 g = L.by1_g[q];
+            const u64 wg = f_mul(ez, eq_at(L.trp, g));
+            if (L.type[g]) {
+                P2 = f_add(P2, f_mul(wg, V[L.in2[g]]));
+            } else {
+                P2 = f_add(P2, wg);
+                B2 = f_add(B2, f_mul(wg, V[L.in2[g]]));
+            }
+        }
+        for (u32 q = L.by2_off[w]; q < L.by2_off[w + 1]; q++) {
+            const u32 g = L.by2_g[q];
+            const u64 ug = f_mul(f_mul(ez, eq_at(L.trp, g)), eq_at(L.tr1, L.in1[g]));
+            if (L.type[g]) M2 = f_add(M2, ug);
+            else A2 = f_add(A2, ug);
+        }
+        break;
+    }
+    }
+    L.P2[w] = P2;
+    L.P3[w] = f_add(A2, f_mul(v1, M2));
+    if (L.has_add) {
+        L.B2[w] = B2;
+        L.B3[w] = f_mul(v1, A2);
+    }
+}
+
+void launch_build23(const Globals &G, const u32 *blk_off, int nlayers, int nblocks, cudaStream_t st)
+{
+    if (nblocks > 0) k_build23<<<nblocks, 256, 0, st>>>(G, blk_off, nlayers);
+}
+
+// --------------------------------------------------------------------------------
+// Sum-check waves: sum_x P(x) V(x) + B(x).  Round message (values at 0, 1, 2):
+//   g(t) = sum_k P(t,k) V(t,k) + B(t,k),   X(t,k) = X[2k] + t (X[2k+1] - X[2k]),
+// then every table folds with the round's challenge.  A CTA takes a chunk of
+// 2^nr consecutive entries: each thread folds a run of 8 entries through 3
+// rounds in registers, the CTA folds the 256 results through the remaining
+// rounds in shared memory, and per-round partial messages go to `partials`.
+// --------------------------------------------------------------------------------
+
+#define SC_NT 256
+#define SC_M 3
+
+template <int NP>
+__device__ __forceinline__ void sc_level(u64 (&p)[8], u64 (&v)[8], u64 (&b)[8], const u64 r, u64 (&acc)[3],
+                                         const bool hasB)
+{
+#pragma unroll
+    for (int q = 0; q < NP; q++) {
+        const u64 p0 = p[2 * q], p1 = p[2 * q + 1], v0 = v[2 * q], v1 = v[2 * q + 1];
+        acc[0] = f_add(acc[0], f_mul(p0, v0));
+        acc[1] = f_add(acc[1], f_mul(p1, v1));
+        acc[2] = f_add(acc[2], f_mul(f_ext2(p1, p0), f_ext2(v1, v0)));
+        if (hasB) {
+            const u64 b0 = b[2 * q], b1 = b[2 * q + 1];
+            acc[0] = f_add(acc[0], b0);
+            acc[1] = f_add(acc[1], b1);
+            acc[2] = f_add(acc[2], f_ext2(b1, b0));
+            b[q] = f_add(b0, f_mul(r, f_sub(b1, b0)));
+        }
+        p[q] = f_add(p0, f_mul(r, f_sub(p1, p0)));
+        v[q] = f_add(v0, f_mul(r, f_sub(v1, v0)));
+    }
+}
+
+__global__ void __launch_bounds__(SC_NT) k_sc_wave(Globals G, const WaveDev *waves, const Item *items,
+                                                   u64 *partials)
+{
+    __shared__ u64 s_r[32];
+    __shared__ u64 s_lvl[3][SC_NT];
+    __shared__ u64 s_x[3][SC_NT / 2], s_y[3][SC_NT / 2];
+    __shared__ u64 s_ctr[3][SC_NT];
+    __shared__ u64 s_wsum[SC_NT / 32][3 * SC_M];
+
+    const Item it = items[blockIdx.x];
+    const WaveDev &W = waves[it.wave];
+    const u32 nr = W.nr;
+    const u32 chunk = it.chunk;
+    const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool hasB = (W.flags & WF_HASB) != 0;
+    const bool peq = (W.flags & WF_PEQ) != 0;
+    if (tid < nr) s_r[tid] = G.chal[W.chal_off + tid];
+    __syncthreads();
+
+    const u32 e = (nr >= SC_M) ? SC_M : 0;
+    const u32 na = 1u << (nr - e);
+    const u64 base = (u64)chunk << nr;
+
+    u64 acc[SC_M][3];
+#pragma unroll
+    for (int k = 0; k < SC_M; k++) acc[k][0] = acc[k][1] = acc[k][2] = 0;
+    u64 fp = 0, fv = 0, fb = 0;
+    if (tid < na) {
+        if (e == SC_M) {
+            u64 p[8], v[8], b[8];
+            const u64 x0 = base + ((u64)tid << SC_M);
+            const ulonglong2 *sv = reinterpret_cast<const ulonglong2 *>(W.inV + x0);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const ulonglong2 t = sv[q];
+                v[2 * q] = t.x;
+                v[2 * q + 1] = t.y;
+            }
+            if (peq) {
+#pragma unroll
+                for (int q = 0; q < 8; q++) p[q] = eq_at(W.peq, x0 + q);
+            } else {
+                const ulonglong2 *sp = reinterpret_cast<const ulonglong2 *>(W.inP + x0);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const ulonglong2 t = sp[q];
+                    p[2 * q] = t.x;
+                    p[2 * q + 1] = t.y;
+                }
+            }
+            if (hasB) {
+                const ulonglong2 *sb = reinterpret_cast<const ulonglong2 *>(W.inB + x0);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const ulonglong2 t = sb[q];
+                    b[2 * q] = t.x;
+                    b[2 * q + 1] = t.y;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; q++) b[q] = 0;
+            }
+            sc_level<4>(p, v, b, s_r[0], acc[0], hasB);
+            sc_level<2>(p, v, b, s_r[1], acc[1], hasB);
+            sc_level<1>(p, v, b, s_r[2], acc[2], hasB);
+            fp = p[0];
+            fv = v[0];
+            fb = b[0];
+        } else {
+            const u64 x = base + tid;
+            fv = W.inV[x];
+            fp = peq ? eq_at(W.peq, x) : W.inP[x];
+            fb = hasB ? W.inB[x] : 0;
+        }
+        s_lvl[0][tid] = fp;
+        s_lvl[1][tid] = fv;
+        s_lvl[2][tid] = fb;
+    }
+    if (e == SC_M) {
+#pragma unroll
+        for (int k = 0; k < SC_M; k++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const u64 s = warp_sum(acc[k][c]);
+                if (lane == 0) s_wsum[warp][k * 3 + c] = s;
+            }
+    }
+    __syncthreads();
+
+    // Remaining rounds over the na level values.
+    u64 *cP = s_lvl[0], *cV = s_lvl[1], *cB = s_lvl[2];
+    u32 m = na;
+    int flip = 0;
+    for (u32 k = e; k < nr; k++) {
+        const u32 half = m >> 1;
+        const u32 seg = na - (na >> (k - e));
+        u64 *nP = flip ? s_y[0] : s_x[0];
+        u64 *nV = flip ? s_y[1] : s_x[1];
+        u64 *nB = flip ? s_y[2] : s_x[2];
+        if (tid < half) {
+            const u64 r = s_r[k];
+            const u64 p0 = cP[2 * tid], p1 = cP[2 * tid + 1];
+            const u64 v0 = cV[2 * tid], v1 = cV[2 * tid + 1];
+            const u64 b0 = cB[2 * tid], b1 = cB[2 * tid + 1];
+            s_ctr[0][seg + tid] = f_add(f_mul(p0, v0), b0);
+            s_ctr[1][seg + tid] = f_add(f_mul(p1, v1), b1);
+            s_ctr[2][seg + tid] = f_add(f_mul(f_ext2(p1, p0), f_ext2(v1, v0)), f_ext2(b1, b0));
+            nP[tid] = f_add(p0, f_mul(r, f_sub(p1, p0)));
+            nV[tid] = f_add(v0, f_mul(r, f_sub(v1, v0)));
+            nB[tid] = f_add(b0, f_mul(r, f_sub(b1, b0)));
+        }
+        __syncthreads();
+        cP = nP;
+        cV = nV;
+        cB = nB;
+        m = half;
+        flip ^= 1;
+    }
+
+    // Per-round partial messages of this chunk.
+    const u32 nwarps = SC_NT / 32;
+    for (u32 k = warp; k < nr; k += nwarps) {
+        for (int c = 0; c < 3; c++) {
+            u64 s = 0;
+            if (k < e) {
+                if (lane < nwarps) s = s_wsum[lane][k * 3 + c];
+            } else {
+                const u32 seg = na - (na >> (k - e));
+                const u32 len = na >> (k - e + 1);
+                for (u32 q = lane; q < len; q += 32) s = f_add(s, s_ctr[c][seg + q]);
+            }
+            s = warp_sum(s);
+            if (lane == 0) partials[W.part + ((u64)k * W.nchunks + chunk) * 3 + c] = s;
+        }
+    }
+    if (!(W.flags & WF_LAST) && tid == 0) {
+        W.outP[chunk] = cP[0];
+        W.outV[chunk] = cV[0];
+        if (hasB) W.outB[chunk] = cB[0];
+    }
+}
+
+void launch_sc_wave(const Globals &G, const WaveDev *waves, const Item *items, int nitems, u64 *partials,
+                    cudaStream_t st)
+{
+    if (nitems > 0) k_sc_wave<<<nitems, SC_NT, 0, st>>>(G, waves, items, partials);
+}
+
+// --------------------------------------------------------------------------------
+// Final reduction: each round's value = sum over the chunks' partials; the
+// outputs open the transcript.
+// --------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_final(Globals G, const RoundRef *rounds, int nrounds,
+                                               const u64 *partials, const u64 *V0, u64 S0)
+{
+    const u32 lane = threadIdx.x & 31;
+    const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+    for (u64 gw = (blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5; gw < (u64)nrounds; gw += nwarps) {
+        const RoundRef R = rounds[gw];
+        for (int c = 0; c < 3; c++) {
+            u64 s = 0;
+            for (u32 q = lane; q < R.nchunks; q += 32) s = f_add(s, partials[R.part_pos + (u64)q * 3 + c]);
+            s = warp_sum(s);
+            if (lane == 0) G.tr[R.tr_pos + c] = s;
+        }
+    }
+    for (u64 x = blockIdx.x * (u64)blockDim.x + threadIdx.x; x < S0; x += (u64)gridDim.x * blockDim.x)
+        G.tr[x] = V0[x];
+}
+
+void launch_final(const Globals &G, const RoundRef *rounds, int nrounds, const u64 *partials, const u64 *V0,
+                  u64 S0, cudaStream_t st)
+{
+    u64 threads = (u64)nrounds * 32;
+    if (threads < S0) threads = S0;
+    u64 blocks = (threads + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks == 0) blocks = 1;
+    k_final<<<(unsigned)blocks, 256, 0, st>>>(G, rounds, nrounds, partials, V0, S0);
+}

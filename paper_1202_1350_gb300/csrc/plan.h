@@ -1,0 +1,169 @@
+// plan.h -- launch-plan descriptors shared by the host planner and the kernels.
+//
+// A proof is a fixed sequence of launches whose shapes depend only on the
+// circuit's shape, so vc_circuit_create computes every descriptor once and
+// uploads it; a proof only replays the plan with a new seed and new inputs.
+//
+// Because the verifier's coins are a function of the seed alone, every
+// challenge is known before the first message is computed.  The prover uses
+// this to run all d layer iterations, and within a layer its three sum-check
+// phases and its line reduction, concurrently: each is an independent
+// "sum-check instance" (SCI) or line job over its own tables.  The rounds of
+// one SCI stay in order (each round folds the tables with its challenge).
+#pragma once
+#include "field.cuh"
+
+enum : u32 {
+    W_SQUARE = 0, W_TREE = 1, W_MATMULT = 2, W_F0_FIRST = 3, W_F0_PAIR = 4, W_F0_FINAL = 5,
+    W_EXPLICIT = 6
+};
+
+// Split table of eq(x, .) over n coordinates: eq(x, b) = lo[b mod 2^h] * hi[b >> h]
+// with h = ceil(n/2) (Sec. 4.1.1's per-gate eq factor at one product per gate).
+struct EqTab {
+    u64 *lo;        // 2^h entries
+    u64 *hi;        // 2^(n-h) entries
+    const u64 *pt;  // the point, n coordinates (device)
+    u32 n, h;
+};
+
+__device__ __forceinline__ u64 eq_at(const EqTab &t, u64 b)
+{
+    return f_mul(t.lo[b & ((1ull << t.h) - 1)], t.hi[b >> t.h]);
+}
+
+// One layer iteration (layer i relates V_i to V_{i+1}).
+struct LayerDev {
+    u32 s, sn;        // s_i, s_{i+1}
+    u32 kind;         // W_*
+    u32 has_add;      // layer has ADD gates (else the B tables are zero)
+    u32 chal_off;     // first round challenge of this layer in chal[]
+    u32 z_off;        // z_i in pts[] (s_i coordinates)
+    u64 *V;           // layer i values
+    u64 *Vn;          // layer i+1 values
+    u64 tr_msg;       // transcript offset of the layer's round values
+    u64 tr_q;         // transcript offset of q(0..s_{i+1})
+    EqTab tz, trp, tr1, tr2;  // eq tables of z_i, r_P, r1, r2
+    u64 *P2, *B2, *P3, *B3;   // phase-2/3 tables over layer i+1 (B* NULL if !has_add)
+    const unsigned char *type;  // EXPLICIT only
+    const u32 *in1, *in2;
+    const u32 *by1_off, *by1_g;  // gates grouped by in1: offsets [S_{i+1}+1], gate ids [S_i]
+    const u32 *by2_off, *by2_g;  // gates grouped by in2
+};
+
+// Per-layer scalars written during a proof: scal[2 i] = eq(z_i, r_P),
+// scal[2 i + 1] = V~_{i+1}(r1) (= q_i(0)).
+#define SCAL_EQZRP(i) (2 * (i))
+#define SCAL_V1(i) (2 * (i) + 1)
+
+// Flags of a sum-check wave.
+enum : u32 { WF_PEQ = 1, WF_HASB = 2, WF_LAST = 4 };
+
+// Sum-check instance: sum_x P(x) V(x) + B(x) over n variables (Sec. 4.1.1's
+// message = field sum of per-entry contributions).  Phase 1 of layer i has
+// P = eq(z_i, .), V = V_i, B = 0; phases 2 and 3 use tables built from the
+// wiring (k_build23) with V = V_{i+1}.
+struct SciDev {
+    u32 n;        // rounds
+    u32 layer;
+    u32 phase;    // 1, 2, 3
+    u32 chal_off; // challenge of round k is chal[chal_off + k]
+    u64 tr_off;   // transcript offset of round 0's three values
+};
+
+// One wave of one SCI: each CTA folds a chunk of 2^nr entries down to one,
+// producing the partial messages of rounds r0..r0+nr-1 for its chunk.
+struct WaveDev {
+    u32 sci;
+    u32 r0, nr;
+    u32 nchunks;
+    u32 flags;
+    u32 pad;
+    const u64 *inP, *inV, *inB;
+    u64 *outP, *outV, *outB;  // nchunks entries each (unused on the last wave)
+    EqTab peq;                // P = eq(pt, .) when WF_PEQ
+    u64 part;                 // partials: part + (k * nchunks + chunk) * 3 + c
+    u64 chal_off;             // challenge of local round k: chal[chal_off + k]
+};
+
+// Line reduction of layer i (q(t) = V~_{i+1}(l(t)), l(t) = r1 + t (r2 - r1)),
+// computed by folding V_{i+1} with the coordinates a_k + b_k t in coefficient
+// form: after folding j coordinates each entry is a polynomial of degree j.
+struct LineWaveDev {
+    u32 layer;
+    u32 n;        // s_{i+1}
+    u32 l0, nl;   // coordinates [l0, l0 + nl) folded by this wave
+    u32 nchunks;
+    u32 last;
+    const u64 *in;  // l0 == 0: V_{i+1}; else polys [chunk][l0 + 1]
+    u64 *out;       // polys [nchunks][l0 + nl + 1] (unused on the last wave)
+    u32 a_off;      // a_k = chal[a_off + k] (= r1), b_k = chal[b_off + k] - a_k
+    u32 b_off;
+    u64 tr_q;
+};
+
+// Work item of a merged launch: which wave descriptor and which chunk.
+struct Item {
+    u32 wave;
+    u32 chunk;
+};
+
+// Final reduction of one round: sum nchunks partial triples into tr[tr_pos..+3].
+struct RoundRef {
+    u64 tr_pos;
+    u64 part_pos;
+    u32 nchunks;
+    u32 pad;
+};
+
+// Per-call globals passed by value to the prover's kernels.
+struct Globals {
+    u64 seed;
+    u32 d;
+    u32 nchal;
+    u64 *chal;        // nchal challenges
+    u64 *pts;         // z_0 .. z_d
+    u64 *scal;        // per-layer scalars (SCAL_*)
+    u64 *tr;          // transcript (device)
+    u32 *status;      // error flags (bit 0: non-canonical input)
+    LayerDev *layers;
+    u64 *invfact;     // 1/k! for k < 64 (verifier)
+};
+
+#define ST_BAD_INPUT 1u
+#define ST_TIMEOUT 2u
+
+// ---- launch entry points (implemented in the .cu files) -------------------------
+struct EqJob {
+    EqTab t;
+};
+
+void launch_setup(const Globals &G, u32 zd_off, cudaStream_t st);
+void launch_eqtabs(const EqJob *jobs, int njobs, cudaStream_t st);
+void launch_eval_layer(const Globals &G, const LayerDev &L, int i, cudaStream_t st);
+void launch_check_canonical(const u64 *x, u64 n, u32 *status, cudaStream_t st);
+void launch_line_wave(const Globals &G, const LineWaveDev *lw, const Item *items, int nitems,
+                      cudaStream_t st);
+void launch_build23(const Globals &G, const u32 *blk_off, int nlayers, int nblocks, cudaStream_t st);
+void launch_sc_wave(const Globals &G, const WaveDev *waves, const Item *items, int nitems,
+                    u64 *partials, cudaStream_t st);
+void launch_final(const Globals &G, const RoundRef *rounds, int nrounds, const u64 *partials,
+                  const u64 *V0, u64 S0, cudaStream_t st);
+
+// verifier
+struct VerifyDev {
+    u32 d;
+    u64 tr_len;
+    const u64 *tr;      // transcript (device)
+    const u64 *inputs;  // S_d inputs (device)
+    u64 *mle_part;      // partial sums of the input MLE
+    u32 mle_blocks;
+    u64 *result;        // [0] input MLE, [1] output MLE, [2] accept flag, [3] bad-value flag
+    u64 *wire;          // generic add~/mult~ per layer (EXPLICIT layers)
+    int *accept_out;    // optional device int receiving the accept bit
+};
+void launch_verify(const Globals &G, const VerifyDev &V, const EqTab &tzd, const EqTab &tz0,
+                   const u32 *explicit_layers, int n_explicit, cudaStream_t st);
+
+void launch_field_mul(const u64 *a, const u64 *b, u64 *out, u64 n, cudaStream_t st);
+float run_field_mul_rate(int variant, u64 iters, int blocks, int threads, u64 *sink);

@@ -1,0 +1,299 @@
+"""Thin ctypes binding of the C ABI in include/vc.h (argument marshalling only).
+
+Every function keeps the C name.  Array arguments may be torch tensors (int64
+or uint64, CPU or CUDA, contiguous) or numpy uint64 arrays; the library itself
+decides host vs device from the pointer.  `stream` defaults to PyTorch's
+current stream on the circuit's device.  There is no CPU fallback: if the CUDA
+library is missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+P = (1 << 61) - 1
+SQUARE, TREE, MATMULT, F0_FIRST, F0_PAIR, F0_FINAL, EXPLICIT = range(7)
+
+VC_OK, VC_EINVAL, VC_ENOMEM, VC_ECUDA, VC_ETIMEOUT, VC_EBUSY = range(6)
+_STATUS = {0: "VC_OK", 1: "VC_EINVAL", 2: "VC_ENOMEM", 3: "VC_ECUDA", 4: "VC_ETIMEOUT", 5: "VC_EBUSY"}
+
+
+class VcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}")
+        self.status = status
+
+
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("n_layers", ctypes.c_uint32),
+                ("log_width", _u32p),
+                ("wiring", _u32p),
+                ("gate_type", ctypes.POINTER(_u8p)),
+                ("in1", ctypes.POINTER(_u32p)),
+                ("in2", ctypes.POINTER(_u32p))]
+
+
+NUM_STAGES = 8
+STAGES = ("setup", "eq", "eval", "line", "build", "sc0", "sc1", "final")
+
+
+class CircuitInfo(ctypes.Structure):
+    _fields_ = [("n_layers", ctypes.c_uint32), ("n_rounds", ctypes.c_uint32),
+                ("transcript_len", ctypes.c_uint64), ("gates", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64), ("prove_launches", ctypes.c_uint32),
+                ("verify_launches", ctypes.c_uint32), ("sc0_ctas", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32)]
+
+
+_lock = threading.Lock()
+_lib = None
+_shapes = {}  # handle -> (inputs, outputs, transcript length), for size checks
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libvc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with `python -m paper_1202_1350_gb300.build` "
+                                   "(there is no CPU fallback)")
+            L = ctypes.CDLL(path)
+            vp = ctypes.c_void_p
+            st = ctypes.c_int
+            L.vc_circuit_create.argtypes = [ctypes.POINTER(_Desc), ctypes.c_int, ctypes.POINTER(vp)]
+            L.vc_circuit_destroy.argtypes = [vp]
+            L.vc_transcript_len.argtypes = [vp, _u64p]
+            L.vc_circuit_bytes.argtypes = [vp, _u64p]
+            L.vc_evaluate.argtypes = [vp, vp, vp, vp]
+            L.vc_prove.argtypes = [vp, vp, ctypes.c_uint64, vp, vp]
+            L.vc_circuit_sync.argtypes = [vp, vp]
+            L.vc_verify.argtypes = [vp, vp, ctypes.c_uint64, vp, ctypes.POINTER(ctypes.c_int), vp]
+            L.vc_prove_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), _u64p, ctypes.POINTER(vp),
+                                         ctypes.c_int, vp]
+            L.vc_field_mul.argtypes = [vp, vp, vp, ctypes.c_uint64, vp]
+            L.vc_field_mul_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                            ctypes.POINTER(ctypes.c_double)]
+            L.vc_circuit_set_stage_events.argtypes = [vp, ctypes.POINTER(vp)]
+            L.vc_circuit_get_info.argtypes = [vp, ctypes.POINTER(CircuitInfo)]
+            L.vc_status_string.argtypes = [ctypes.c_int]
+            L.vc_status_string.restype = ctypes.c_char_p
+            for name in ("vc_circuit_create", "vc_circuit_destroy", "vc_transcript_len", "vc_circuit_bytes",
+                         "vc_evaluate", "vc_prove", "vc_circuit_sync", "vc_verify", "vc_prove_batch",
+                         "vc_field_mul", "vc_field_mul_rate", "vc_circuit_set_stage_events",
+                         "vc_circuit_get_info"):
+                getattr(L, name).restype = st
+            _lib = L
+    return _lib
+
+
+def header_functions() -> list:
+    """Function names declared in include/vc.h."""
+    hdr = os.path.join(_build.INCLUDE, "vc.h")
+    text = open(hdr).read()
+    return sorted(set(re.findall(r"^\s*(?:vc_status|const\s+char\s*\*)\s*(vc_\w+)\s*\(", text, re.M)))
+
+
+def _check(status: int, where: str):
+    if status != VC_OK:
+        raise VcError(status, where)
+
+
+def _ptr(x):
+    """Raw address of a contiguous torch tensor or numpy array."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"] or x.dtype.itemsize != 8:
+            raise ValueError("numpy arrays must be contiguous 64-bit")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous() or x.element_size() != 8:
+            raise ValueError("tensors must be contiguous 64-bit")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _numel(x) -> int:
+    return int(x.size if isinstance(x, np.ndarray) else x.numel())
+
+
+def _stream(stream, device: int):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream(device).cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+# --- C ABI ----------------------------------------------------------------------------
+
+def vc_circuit_create(log_width, wiring, explicit=None, device: int = 0):
+    """Returns an opaque handle (int).  explicit: per-layer (type, in1, in2) or None."""
+    lw = [int(x) for x in log_width]
+    kinds = [int(k) for k in wiring]
+    d = len(kinds)
+    if len(lw) != d + 1:
+        raise ValueError("log_width must have len(wiring) + 1 entries")
+    keep = []
+    lw_a = (ctypes.c_uint32 * (d + 1))(*lw)
+    k_a = (ctypes.c_uint32 * max(d, 1))(*kinds)
+    desc = _Desc(d, ctypes.cast(lw_a, _u32p), ctypes.cast(k_a, _u32p), None, None, None)
+    if explicit is not None:
+        tys = (_u8p * d)()
+        i1s = (_u32p * d)()
+        i2s = (_u32p * d)()
+        for i, layer in enumerate(explicit):
+            if layer is None:
+                continue
+            ty = np.ascontiguousarray(layer[0], dtype=np.uint8)
+            a = np.ascontiguousarray(layer[1], dtype=np.uint32)
+            b = np.ascontiguousarray(layer[2], dtype=np.uint32)
+            keep += [ty, a, b]
+            tys[i] = ty.ctypes.data_as(_u8p)
+            i1s[i] = a.ctypes.data_as(_u32p)
+            i2s[i] = b.ctypes.data_as(_u32p)
+        desc.gate_type = tys
+        desc.in1 = i1s
+        desc.in2 = i2s
+    h = ctypes.c_void_p()
+    _check(lib().vc_circuit_create(ctypes.byref(desc), device, ctypes.byref(h)), "vc_circuit_create")
+    del keep
+    n = ctypes.c_uint64()
+    _check(lib().vc_transcript_len(h, ctypes.byref(n)), "vc_transcript_len")
+    _shapes[h.value] = (1 << lw[-1], 1 << lw[0], n.value)
+    return h.value
+
+
+def _need(x, n: int, what: str):
+    if x is None or _numel(x) < n:
+        raise ValueError(f"{what} needs at least {n} elements")
+
+
+def vc_circuit_destroy(h):
+    _check(lib().vc_circuit_destroy(h), "vc_circuit_destroy")
+    _shapes.pop(h, None)
+
+
+def vc_transcript_len(h) -> int:
+    n = ctypes.c_uint64()
+    _check(lib().vc_transcript_len(h, ctypes.byref(n)), "vc_transcript_len")
+    return n.value
+
+
+def vc_circuit_bytes(h) -> int:
+    n = ctypes.c_uint64()
+    _check(lib().vc_circuit_bytes(h, ctypes.byref(n)), "vc_circuit_bytes")
+    return n.value
+
+
+def vc_evaluate(h, inputs, outputs, stream=None, device: int = 0):
+    nin, nout, _ = _shapes[h]
+    _need(inputs, nin, "inputs")
+    _need(outputs, nout, "outputs")
+    _check(lib().vc_evaluate(h, _ptr(inputs), _ptr(outputs), _stream(stream, device)), "vc_evaluate")
+    return outputs
+
+
+def vc_prove(h, inputs, seed: int, transcript, stream=None, device: int = 0):
+    nin, _, ntr = _shapes[h]
+    _need(inputs, nin, "inputs")
+    _need(transcript, ntr, "transcript")
+    _check(lib().vc_prove(h, _ptr(inputs), seed & 0xFFFFFFFFFFFFFFFF, _ptr(transcript),
+                          _stream(stream, device)), "vc_prove")
+    return transcript
+
+
+def vc_circuit_sync(h, stream=None, device: int = 0):
+    _check(lib().vc_circuit_sync(h, _stream(stream, device)), "vc_circuit_sync")
+
+
+def vc_verify(h, inputs, seed: int, transcript, stream=None, device: int = 0, accept=None) -> bool:
+    """Returns the accept bit; with `accept` (a CUDA int32 tensor of >= 1
+    element) the call is asynchronous and the bit is written there instead."""
+    nin, _, ntr = _shapes[h]
+    _need(inputs, nin, "inputs")
+    _need(transcript, ntr, "transcript")
+    if accept is not None:
+        if accept.element_size() != 4 or accept.numel() < 1:
+            raise ValueError("accept must be an int32 tensor")
+        _check(lib().vc_verify(h, _ptr(inputs), seed & 0xFFFFFFFFFFFFFFFF, _ptr(transcript),
+                               ctypes.cast(ctypes.c_void_p(accept.data_ptr()), ctypes.POINTER(ctypes.c_int)),
+                               _stream(stream, device)), "vc_verify")
+        return None
+    acc = ctypes.c_int(0)
+    _check(lib().vc_verify(h, _ptr(inputs), seed & 0xFFFFFFFFFFFFFFFF, _ptr(transcript), ctypes.byref(acc),
+                           _stream(stream, device)), "vc_verify")
+    return bool(acc.value)
+
+
+def vc_circuit_set_stage_events(h, events):
+    """events: NUM_STAGES + 1 torch.cuda.Event objects (enable_timing=True), or None."""
+    if events is None:
+        _check(lib().vc_circuit_set_stage_events(h, None), "vc_circuit_set_stage_events")
+        return
+    if len(events) != NUM_STAGES + 1:
+        raise ValueError(f"need {NUM_STAGES + 1} events")
+    for e in events:  # make sure each event exists on the device
+        if getattr(e, "cuda_event", 0) == 0:
+            e.record()
+    arr = (ctypes.c_void_p * (NUM_STAGES + 1))(*[e.cuda_event for e in events])
+    _check(lib().vc_circuit_set_stage_events(h, arr), "vc_circuit_set_stage_events")
+
+
+def vc_circuit_get_info(h) -> dict:
+    info = CircuitInfo()
+    _check(lib().vc_circuit_get_info(h, ctypes.byref(info)), "vc_circuit_get_info")
+    return {name: getattr(info, name) for name, _ in CircuitInfo._fields_ if name != "pad"}
+
+
+def vc_prove_batch(handles, inputs, seeds, transcripts, stream=None, device: int = 0):
+    n = len(handles)
+    if not (len(inputs) == len(seeds) == len(transcripts) == n):
+        raise ValueError("one input, seed and transcript per circuit")
+    for h, x, t in zip(handles, inputs, transcripts):
+        _need(x, _shapes[h][0], "inputs")
+        _need(t, _shapes[h][2], "transcript")
+    hs = (ctypes.c_void_p * n)(*handles)
+    ins = (ctypes.c_void_p * n)(*[_ptr(x) for x in inputs])
+    sd = (ctypes.c_uint64 * n)(*[s & 0xFFFFFFFFFFFFFFFF for s in seeds])
+    trs = (ctypes.c_void_p * n)(*[_ptr(t) for t in transcripts])
+    _check(lib().vc_prove_batch(hs, ins, sd, trs, n, _stream(stream, device)), "vc_prove_batch")
+    return transcripts
+
+
+def vc_field_mul(a, b, out, stream=None, device: int = 0):
+    _need(a, _numel(out), "a")
+    _need(b, _numel(out), "b")
+    _check(lib().vc_field_mul(_ptr(a), _ptr(b), _ptr(out), _numel(out), _stream(stream, device)), "vc_field_mul")
+    return out
+
+
+def vc_field_mul_rate(device: int = 0, variant: int = 0, iters: int = 1 << 14) -> float:
+    r = ctypes.c_double(0)
+    _check(lib().vc_field_mul_rate(device, variant, iters, ctypes.byref(r)), "vc_field_mul_rate")
+    return r.value
+
+
+def vc_status_string(status: int) -> str:
+    return lib().vc_status_string(status).decode()

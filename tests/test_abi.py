@@ -1,0 +1,61 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports every
+function declared in include/vc.h, and rejects malformed circuits before it
+touches a device."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1202_1350_gb300 import build, circuits, vc
+
+
+@pytest.fixture(scope="module")
+def libvc():
+    build.build()
+    return vc.lib()
+
+
+def test_exports_every_declared_function(libvc):
+    names = vc.header_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(libvc, name), name
+        assert isinstance(getattr(libvc, name), ctypes._CFuncPtr)
+
+
+def test_status_strings(libvc):
+    assert vc.vc_status_string(0) == "ok"
+    assert vc.vc_status_string(1) == "invalid argument"
+
+
+@pytest.mark.parametrize("widths,kinds", [
+    ([2, 2], [vc.TREE]), ([1, 3], [vc.SQUARE]), ([3, 4], [vc.MATMULT]), ([4, 3], [vc.MATMULT]), ([1, 3], [vc.F0_FIRST]),
+    ([0, 0], [vc.F0_PAIR]), ([2, 2], [vc.F0_FINAL]), ([31, 31], [vc.SQUARE]), ([1, 1], [9])])
+def test_bad_shapes_rejected_without_device(libvc, widths, kinds):
+    with pytest.raises(vc.VcError) as e:
+        vc.vc_circuit_create(widths, kinds)
+    assert e.value.status == vc.VC_EINVAL
+
+
+def test_bad_explicit_wiring_rejected(libvc):
+    ex = [(np.array([0, 1]), np.array([0, 2]), np.array([1, 1]))]
+    with pytest.raises(vc.VcError) as e:
+        vc.vc_circuit_create([1, 1], [vc.EXPLICIT], explicit=ex)
+    assert e.value.status == vc.VC_EINVAL
+    ex = [(np.array([0, 2]), np.array([0, 1]), np.array([1, 1]))]
+    with pytest.raises(vc.VcError):
+        vc.vc_circuit_create([1, 1], [vc.EXPLICIT], explicit=ex)
+
+
+@pytest.mark.parametrize("family,logn", [("f2", 10), ("f2", 20), ("f0", 16), ("matmult", 7), ("matmult", 1)])
+def test_circuit_descriptions_agree_with_oracle(family, logn):
+    """The product's layer descriptions and the oracle's are written separately;
+    both must describe the same circuit."""
+    assert circuits.by_name(family, logn) == getattr(oracle, f"{family}_layers")(logn)
+
+
+def test_gate_counts():
+    # F2 at n = 2^20: 2^20 squaring gates and 2^20 - 1 addition gates
+    assert circuits.non_input_gates(circuits.f2(20)[0]) == 2 * (1 << 20) - 1
+    assert circuits.non_input_gates(circuits.matmult(7)[0]) == (1 << 21) + (1 << 21) - (1 << 14)

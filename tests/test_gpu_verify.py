@@ -1,0 +1,151 @@
+"""The CUDA verifier: accepts honest transcripts, rejects tampered ones, and
+agrees with the oracle verifier on every case (Sec. 2.1: completeness and
+soundness)."""
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import ensure_built, gpu_prove, to_np
+from paper_1202_1350_gb300 import circuits, vc
+from paper_1202_1350_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+P = (1 << 61) - 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(x, np.uint64)).view(np.int64).copy()).cuda()
+
+
+CASES = [("f2", 10), ("f2", 1), ("f0", 3), ("matmult", 2), ("matmult", 0)]
+
+
+@pytest.mark.parametrize("family,logn", CASES)
+def test_honest_accepted(family, logn):
+    widths, kinds = circuits.by_name(family, logn)
+    x = I.job_inputs(family, logn, 17)
+    h = vc.vc_circuit_create(widths, kinds)
+    try:
+        for seed in (1, 2, 3, 1 << 63):
+            tr = gpu_prove(widths, kinds, x, seed)
+            assert vc.vc_verify(h, dev(x), seed, dev(tr))
+            assert oracle.Circuit(widths, kinds).verify(x, seed, tr) == (True, -1)
+    finally:
+        vc.vc_circuit_destroy(h)
+
+
+def test_every_single_change_rejected():
+    widths, kinds = circuits.f2(5)
+    x = I.f2_inputs(5, 1 << 16, 5)
+    seed = 9
+    tr = gpu_prove(widths, kinds, x, seed)
+    h = vc.vc_circuit_create(widths, kinds)
+    rng = random.Random(1)
+    try:
+        xd = dev(x)
+        for k in range(len(tr)):
+            bad = tr.copy()
+            bad[k] = (int(bad[k]) + 1 + rng.randrange(P - 1)) % P
+            assert not vc.vc_verify(h, xd, seed, dev(bad)), k
+    finally:
+        vc.vc_circuit_destroy(h)
+
+
+@pytest.mark.parametrize("family,logn", CASES + [("explicit", 0)])
+def test_agrees_with_oracle_on_random_tampering(family, logn):
+    rng = random.Random(hash((family, logn)) & 0xFFFF)
+    if family == "explicit":
+        widths, kinds = [3, 4, 2], [6, 6]
+        ex = []
+        for i in range(2):
+            S, Sn = 1 << widths[i], 1 << widths[i + 1]
+            ex.append((np.array([rng.randrange(2) for _ in range(S)], np.uint8),
+                       np.array([rng.randrange(Sn) for _ in range(S)], np.uint32),
+                       np.array([rng.randrange(Sn) for _ in range(S)], np.uint32)))
+        x = np.array([rng.randrange(P) for _ in range(4)], np.uint64)
+    else:
+        widths, kinds = circuits.by_name(family, logn)
+        ex = None
+        x = I.job_inputs(family, logn, 23)
+    seed = 31
+    tr = gpu_prove(widths, kinds, x, seed, ex)
+    oc = oracle.Circuit(widths, kinds, explicit=ex)
+    h = vc.vc_circuit_create(widths, kinds, ex)
+    try:
+        xd = dev(x)
+        assert vc.vc_verify(h, xd, seed, dev(tr))
+        for _ in range(40):
+            bad = tr.copy()
+            k = rng.randrange(len(tr))
+            bad[k] = rng.randrange(P)
+            want = oc.verify(x, seed, bad)[0]
+            assert vc.vc_verify(h, xd, seed, dev(bad)) == want
+        # the right transcript for other inputs or another seed is rejected
+        y = x.copy()
+        y[0] = (int(y[0]) + 1) % P
+        assert not vc.vc_verify(h, dev(y), seed, dev(tr))
+        assert not vc.vc_verify(h, xd, seed + 1, dev(tr))
+    finally:
+        vc.vc_circuit_destroy(h)
+
+
+def test_wrong_evaluation_rejected():
+    """An oracle prover whose layer values carry one wrong gate (layers above
+    recomputed) is rejected by the CUDA verifier, as by the oracle's."""
+    widths, kinds = circuits.f2(6)
+    x = I.f2_inputs(6, 1 << 16, 41)
+    oc = oracle.Circuit(widths, kinds)
+    h = vc.vc_circuit_create(widths, kinds)
+    try:
+        for layer in (1, 3, 6):
+            vals = [v.astype(object) for v in oc.evaluate(x)]
+            vals[layer][2] = (int(vals[layer][2]) + 1) % P
+            for i in range(layer - 1, -1, -1):
+                ty, a, b = oc.layer_gates(i)
+                vals[i] = np.array([(int(vals[i + 1][a[k]]) * int(vals[i + 1][b[k]])) % P if ty[k]
+                                    else (int(vals[i + 1][a[k]]) + int(vals[i + 1][b[k]])) % P
+                                    for k in range(len(ty))], dtype=object)
+            tr = oc.prove_values([np.array(v, dtype=np.uint64) for v in vals], 12)
+            assert not vc.vc_verify(h, dev(x), 12, dev(tr))
+    finally:
+        vc.vc_circuit_destroy(h)
+
+
+def test_noncanonical_values():
+    widths, kinds = circuits.f2(4)
+    x = I.f2_inputs(4, 1 << 16, 3)
+    tr = gpu_prove(widths, kinds, x, 4)
+    h = vc.vc_circuit_create(widths, kinds)
+    try:
+        bad = tr.copy()
+        bad[5] = P
+        assert not vc.vc_verify(h, dev(x), 4, dev(bad))
+        y = x.copy()
+        y[1] = P
+        with pytest.raises(vc.VcError) as e:
+            vc.vc_verify(h, dev(y), 4, dev(tr))
+        assert e.value.status == vc.VC_EINVAL
+    finally:
+        vc.vc_circuit_destroy(h)
+
+
+def test_host_pointers():
+    widths, kinds = circuits.f2(8)
+    x = I.f2_inputs(8, 1 << 16, 8)
+    h = vc.vc_circuit_create(widths, kinds)
+    try:
+        tr = np.zeros(vc.vc_transcript_len(h), np.uint64)
+        vc.vc_prove(h, np.ascontiguousarray(x), 6, tr)
+        assert (tr == gpu_prove(widths, kinds, x, 6)).all()
+        assert vc.vc_verify(h, np.ascontiguousarray(x), 6, tr)
+        assert vc.vc_verify(h, dev(x), 6, tr)
+    finally:
+        vc.vc_circuit_destroy(h)
