@@ -192,6 +192,30 @@ vc_status vc_field_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, uint
  * variant 0: 32-bit-limb Mersenne product; 1: 64x64->128 product then fold. */
 vc_status vc_field_mul_rate(int device, int variant, uint64_t iters, double *rate);
 
+/* Circuit evaluation that allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library call.  It exists for callers that cannot allocate device
+ * memory, such as a process whose device memory is entirely reserved by
+ * another framework's caching allocator, or code that must not trigger the
+ * device-wide synchronisation a cudaMalloc or cudaFree can cause.  It has no
+ * counterpart in the paper: it is vc_evaluate without a circuit handle.
+ *
+ * desc: the circuit shape (host memory; structured wiring kinds only, an
+ * EXPLICIT layer is VC_EINVAL).  inputs: S_d canonical elements and outputs:
+ * S_0 elements, both device memory of the current device (VC_EINVAL
+ * otherwise).  The intermediate layers 1..d-1 are kept in one fixed device
+ * array of 2^20 field elements (8 MiB); a circuit whose intermediate layers
+ * need more is rejected with VC_EINVAL before any work is queued.  Every GPU on
+ * which this function has run keeps that array until the process exits.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array and it keeps the last call's contents, so calls that
+ * overlap on the GPU (other streams, other host threads) race: serialise them.
+ * Synchronous: returns after `outputs` is written; VC_EINVAL if an input is
+ * >= p. */
+vc_status vc_evaluate_noalloc(const vc_circuit_desc *desc, const uint64_t *inputs, uint64_t *outputs,
+                              void *stream);
+
 /* Human-readable name of a status code (static string). */
 const char *vc_status_string(vc_status s);
 

@@ -92,6 +92,8 @@ def lib():
                                             ctypes.POINTER(ctypes.c_double)]
             L.vc_circuit_set_stage_events.argtypes = [vp, ctypes.POINTER(vp)]
             L.vc_circuit_get_info.argtypes = [vp, ctypes.POINTER(CircuitInfo)]
+            L.vc_evaluate_noalloc.argtypes = [ctypes.POINTER(_Desc), vp, vp, vp]
+            L.vc_evaluate_noalloc.restype = st
             L.vc_status_string.argtypes = [ctypes.c_int]
             L.vc_status_string.restype = ctypes.c_char_p
             for name in ("vc_circuit_create", "vc_circuit_destroy", "vc_transcript_len", "vc_circuit_bytes",
@@ -293,6 +295,36 @@ def vc_field_mul_rate(device: int = 0, variant: int = 0, iters: int = 1 << 14) -
     r = ctypes.c_double(0)
     _check(lib().vc_field_mul_rate(device, variant, iters, ctypes.byref(r)), "vc_field_mul_rate")
     return r.value
+
+
+NOALLOC_MAX_VALUES = 1 << 20
+
+
+def vc_evaluate_noalloc(log_width, wiring, inputs, outputs, stream=None, device: int = 0):
+    """Evaluate a structured-wiring circuit without any device allocation.
+
+    For callers that cannot allocate device memory (their device memory is
+    owned by another allocator, or allocation's implicit synchronisation is
+    unacceptable).  inputs/outputs must be CUDA tensors on the current device;
+    intermediate layers live in the library's fixed 2^20-element device array,
+    shared by all calls (overlapping calls race)."""
+    lw = [int(x) for x in log_width]
+    kinds = [int(k) for k in wiring]
+    d = len(kinds)
+    if len(lw) != d + 1:
+        raise ValueError("log_width must have len(wiring) + 1 entries")
+    need = sum(1 << s for s in lw[1:d])
+    if need > NOALLOC_MAX_VALUES:
+        raise VcError(VC_EINVAL, f"vc_evaluate_noalloc: intermediate layers need {need} field elements, "
+                                 f"the fixed array holds {NOALLOC_MAX_VALUES}")
+    _need(inputs, 1 << lw[-1], "inputs")
+    _need(outputs, 1 << lw[0], "outputs")
+    lw_a = (ctypes.c_uint32 * (d + 1))(*lw)
+    k_a = (ctypes.c_uint32 * max(d, 1))(*kinds)
+    desc = _Desc(d, ctypes.cast(lw_a, _u32p), ctypes.cast(k_a, _u32p), None, None, None)
+    _check(lib().vc_evaluate_noalloc(ctypes.byref(desc), _ptr(inputs), _ptr(outputs), _stream(stream, device)),
+           "vc_evaluate_noalloc")
+    return outputs
 
 
 def vc_status_string(status: int) -> str:
