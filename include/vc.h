@@ -189,7 +189,10 @@ vc_status vc_field_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, uint
 /* Field-multiply issue-rate microbenchmark: runs `iters` dependent products on
  * `chains` independent chains per thread over a grid that fills the device,
  * and returns the measured products per second (CUDA events) in *rate.
- * variant 0: 32-bit-limb Mersenne product; 1: 64x64->128 product then fold. */
+ * variant 0: canonical 32-bit-limb Mersenne product + add; 1: canonical
+ * 64x64->128 product then fold + add; 2: the product-weighted sum-check pair
+ * step (two 128-bit multiply-adds and one lazily reduced fold, counted as three
+ * products), the arithmetic mix of the dominant kernel. */
 vc_status vc_field_mul_rate(int device, int variant, uint64_t iters, double *rate);
 
 /* Circuit evaluation that allocates nothing: no cudaMalloc, no cudaFree, no

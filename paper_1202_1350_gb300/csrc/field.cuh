@@ -102,3 +102,72 @@ __device__ __forceinline__ u64 warp_sum(u64 v)
     for (int o = 16; o > 0; o >>= 1) v = f_add(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
+
+// ---- Lazy arithmetic: values in W = [0, 2^61 + 8) ("weakly reduced"). -------
+// Canonical values are in W; only transcript entries must be canonical.
+
+// Any 64-bit x -> W, congruent mod p (2^61 = 1).
+__device__ __forceinline__ u64 wred(u64 x) { return (x & FP_P) + (x >> 61); }
+
+// W -> canonical.
+__device__ __forceinline__ u64 wcanon(u64 w) { return w >= FP_P ? w - FP_P : w; }
+
+// 128-bit accumulator of products of W values (at most 64 products).
+struct acc128 {
+    u64 lo, hi;
+};
+
+__device__ __forceinline__ void acc_zero(acc128 &a) { a.lo = 0; a.hi = 0; }
+
+// a += x y (exact 128-bit multiply-add).
+__device__ __forceinline__ void mac(acc128 &a, u64 x, u64 y)
+{
+    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\tmadc.hi.u64 %1, %2, %3, %1;" : "+l"(a.lo), "+l"(a.hi) : "l"(x), "l"(y));
+}
+
+// a += x (x < 2^64).
+__device__ __forceinline__ void acc_add(acc128 &a, u64 x)
+{
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(a.lo), "+l"(a.hi) : "l"(x));
+}
+
+// hi 2^64 + lo -> W: 2^64 = 8 (mod p), and 8 hi = (hi >> 58) 2^61 + (8 hi mod 2^61).
+__device__ __forceinline__ u64 acc_red(const acc128 &a)
+{
+    const u64 t = (a.lo & FP_P) + (a.lo >> 61) + ((a.hi << 3) & FP_P) + (a.hi >> 58);
+    return wred(t);
+}
+
+// Product of two W values, result in W.
+__device__ __forceinline__ u64 wmul(u64 x, u64 y)
+{
+    acc128 a;
+    a.lo = x * y;
+    a.hi = __umul64hi(x, y);
+    return acc_red(a);
+}
+
+// 2 a1 - a0 for W values, result in W (the value at t = 2 of the line
+// through (0, a0) and (1, a1)); 2 a1 + 2p - a0 < 2^63 + 16.
+__device__ __forceinline__ u64 wext2(u64 a1, u64 a0) { return wred(2 * a1 + (2 * FP_P) - a0); }
+
+// u0 + r (u1 - u0) for u0, u1 in W and canonical r given as 31/30-bit limbs
+// r = r1 2^31 + r0.  With d = u1 - u0 + 2p in (0, 2^63) split as d1 2^31 + d0:
+//   r d + u0 = r1 d1 2^62 + (r0 d1 + r1 d0) 2^31 + (r0 d0 + u0)
+// and 2^62 = 2, M 2^31 = (M >> 30) + (M mod 2^30) 2^31 (mod p).
+__device__ __forceinline__ u64 wfold(u64 u0, u64 u1, u32 r0, u32 r1)
+{
+    const u64 d = u1 + (2 * FP_P) - u0;
+    const u32 d0 = (u32)d & 0x7FFFFFFFu, d1 = (u32)(d >> 31);
+    const u64 A00 = u0 + (u64)r0 * d0;
+    const u64 AM = (u64)r0 * d1 + (u64)r1 * d0;
+    const u64 A11 = (u64)r1 * d1;
+    const u64 t = (A11 << 1) + (AM >> 30) + ((AM & 0x3FFFFFFFull) << 31) + (A00 & FP_P) + (A00 >> 61);
+    return wred(t);
+}
+
+__device__ __forceinline__ void limbs31(u64 r, u32 &r0, u32 &r1)
+{
+    r0 = (u32)r & 0x7FFFFFFFu;
+    r1 = (u32)(r >> 31);
+}

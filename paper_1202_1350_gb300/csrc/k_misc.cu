@@ -45,17 +45,58 @@ __global__ void __launch_bounds__(256) k_mul_rate(u64 iters, u64 *sink)
     if (s == 0x12345) sink[0] = s;  // keeps the chains alive
 }
 
+// The sum-check pair primitive of the product-weighted waves: per step two
+// multiply-adds into 128-bit accumulators and one lazy fold (3 products).
+template <int CH>
+__global__ void __launch_bounds__(256) k_pair_rate(u64 iters, u64 *sink)
+{
+    u64 x[CH], y[CH], w[CH];
+    const u64 t = blockIdx.x * (u64)blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+        x[c] = (t * 0x9E3779B97F4A7C15ull + c) & FP_P;
+        y[c] = ((t + 7) * 0xBF58476D1CE4E5B9ull + 3 * c) & FP_P;
+        w[c] = ((t + 11) * 0x94D049BB133111EBull + 5 * c) & FP_P;
+    }
+    u32 r0, r1;
+    limbs31(0x123456789ABCDEull + t, r0, r1);
+    acc128 a0, a1;
+    acc_zero(a0);
+    acc_zero(a1);
+    u64 s = 0;
+    for (u64 k = 0; k < iters; k++) {
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            mac(a0, w[c], x[c]);
+            mac(a1, w[c], y[c]);
+            const u64 f = wfold(x[c], y[c], r0, r1);
+            y[c] = x[c];
+            x[c] = f;
+        }
+        if ((k & 3) == 3) {
+            s += acc_red(a0) + acc_red(a1);
+            acc_zero(a0);
+            acc_zero(a1);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < CH; c++) s ^= x[c];
+    if (s == 0x12345) sink[0] = s;
+}
+
 float run_field_mul_rate(int variant, u64 iters, int blocks, int threads, u64 *sink)
 {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    // warm-up
-    if (variant == 0) k_mul_rate<0, 8><<<blocks, threads>>>(iters / 8 + 1, sink);
-    else k_mul_rate<1, 8><<<blocks, threads>>>(iters / 8 + 1, sink);
+    auto run = [&](u64 n) {
+        if (variant == 0) k_mul_rate<0, 8><<<blocks, threads>>>(n, sink);
+        else if (variant == 1) k_mul_rate<1, 8><<<blocks, threads>>>(n, sink);
+        else k_pair_rate<4><<<blocks, threads>>>(n, sink);
+    };
+    run(iters / 8 + 1);  // warm-up
     cudaEventRecord(e0);
-    if (variant == 0) k_mul_rate<0, 8><<<blocks, threads>>>(iters, sink);
-    else k_mul_rate<1, 8><<<blocks, threads>>>(iters, sink);
+    run(iters);
     cudaEventRecord(e1);
     cudaEventSynchronize(e1);
     float ms = 0;

@@ -45,15 +45,13 @@ __global__ void __launch_bounds__(1024) k_setup(Globals G, u32 zd_off)
     const LayerDev *L = G.layers;
     // z_0: the first s_0 challenges.
     for (u32 k = threadIdx.x; k < L[0].s; k += blockDim.x) G.pts[L[0].z_off + k] = G.chal[k];
-    // z_{i+1} = l_i(tau_i) = r1 + tau (r2 - r1).
-    for (u32 i = 0; i < G.d; i++) {
+    // z_{i+1} = l_i(tau_i) = r1 + tau (r2 - r1): one thread per layer.
+    for (u32 i = threadIdx.x; i < G.d; i += blockDim.x) {
         const u32 si = L[i].s, sn = L[i].sn, co = L[i].chal_off;
         const u64 tau = G.chal[co + si + 2 * sn];
         u64 *zn = G.pts + ((i + 1 < G.d) ? L[i + 1].z_off : zd_off);
-        for (u32 k = threadIdx.x; k < sn; k += blockDim.x) {
-            u64 r1 = G.chal[co + si + k], r2 = G.chal[co + si + sn + k];
-            zn[k] = f_add(r1, f_mul(tau, f_sub(r2, r1)));
-        }
+        const u64 *r1 = G.chal + co + si, *r2 = r1 + sn;
+        for (u32 k = 0; k < sn; k++) zn[k] = f_add(r1[k], f_mul(tau, f_sub(r2[k], r1[k])));
     }
     __syncthreads();
     // eq(z_i, r_P) per layer.
@@ -149,6 +147,72 @@ void launch_eval_layer(const Globals &G, const LayerDev &L, int i, cudaStream_t 
     u64 blocks = (S + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     k_eval_layer<<<(unsigned)blocks, 256, 0, st>>>(L);
+}
+
+// Fused evaluation of a run of block-local layers (every structured kind but
+// MATMULT): a CTA loads an aligned chunk of the run's input layer and
+// evaluates it upward through the run in shared memory, writing each layer.
+// Block size of layer i = chunk size * 2^(s_i - s_in); all stay <= EV_MAXB.
+#define EV_NT 256
+#define EV_MAXB 4096
+
+extern __shared__ u64 ev_dyn[];
+
+__global__ void __launch_bounds__(EV_NT) k_eval_seg(Globals G, EvalSeg S)
+{
+    u64 *bufA = ev_dyn, *bufB = ev_dyn + EV_MAXB;
+    const LayerDev *Ls = G.layers;
+    const u32 chunk = blockIdx.x;
+    const LayerDev &Lin = Ls[S.i_hi];
+    const u32 s_in = Lin.sn;
+    u32 B = 1u << S.c;  // block size of the current (upper) layer
+    {
+        const u64 *src = Lin.Vn + ((u64)chunk << S.c);
+        bool bad = false;
+        for (u32 k = threadIdx.x; k < B; k += EV_NT) {
+            const u64 v = src[k];
+            bad |= (v >= FP_P);
+            bufA[k] = v;
+        }
+        if (S.check_input && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
+            atomicOr(G.status, ST_BAD_INPUT);
+    }
+    __syncthreads();
+    u64 *cur = bufA, *nxt = bufB;
+    for (int i = (int)S.i_hi; i >= (int)S.i_lo; i--) {
+        const LayerDev &L = Ls[i];
+        const u32 Bo = (L.s >= L.sn) ? (B << (L.s - L.sn)) : (B >> (L.sn - L.s));
+        const u64 gbase = (u64)chunk * Bo;
+        for (u32 k = threadIdx.x; k < Bo; k += EV_NT) {
+            u32 a, b, mul = 1;
+            switch (L.kind) {
+            case W_SQUARE: a = k; b = k; break;
+            case W_TREE: a = 2 * k; b = 2 * k + 1; mul = 0; break;
+            case W_F0_FIRST: a = k >> 1; b = k >> 1; mul = (k & 1) ? 0 : 1; break;
+            case W_F0_PAIR: a = k; b = k & ~1u; break;
+            default: a = 2 * k + 1; b = 2 * k + 1; break;  // W_F0_FINAL
+            }
+            const u64 x = cur[a], y = cur[b];
+            const u64 v = mul ? f_mul(x, y) : f_add(x, y);
+            nxt[k] = v;
+            L.V[gbase + k] = v;
+        }
+        __syncthreads();
+        u64 *t = cur; cur = nxt; nxt = t;
+        B = Bo;
+    }
+    (void)s_in;
+}
+
+void launch_eval_seg(const Globals &G, const EvalSeg &S, cudaStream_t st)
+{
+    const size_t smem = 2 * EV_MAXB * sizeof(u64);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_eval_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    k_eval_seg<<<S.nchunks, EV_NT, smem, st>>>(G, S);
 }
 
 __global__ void k_check_canonical(const u64 *x, u64 n, u32 *status)
@@ -452,218 +516,3 @@ void launch_build23(const Globals &G, const u32 *blk_off, int nlayers, int nbloc
     if (nblocks > 0) k_build23<<<nblocks, 256, 0, st>>>(G, blk_off, nlayers);
 }
 
-// --------------------------------------------------------------------------------
-// Sum-check waves: sum_x P(x) V(x) + B(x).  Round message (values at 0, 1, 2):
-//   g(t) = sum_k P(t,k) V(t,k) + B(t,k),   X(t,k) = X[2k] + t (X[2k+1] - X[2k]),
-// then every table folds with the round's challenge.  A CTA takes a chunk of
-// 2^nr consecutive entries: each thread folds a run of 8 entries through 3
-// rounds in registers, the CTA folds the 256 results through the remaining
-// rounds in shared memory, and per-round partial messages go to `partials`.
-// --------------------------------------------------------------------------------
-
-#define SC_NT 256
-#define SC_M 3
-
-template <int NP>
-__device__ __forceinline__ void sc_level(u64 (&p)[8], u64 (&v)[8], u64 (&b)[8], const u64 r, u64 (&acc)[3],
-                                         const bool hasB)
-{
-#pragma unroll
-    for (int q = 0; q < NP; q++) {
-        const u64 p0 = p[2 * q], p1 = p[2 * q + 1], v0 = v[2 * q], v1 = v[2 * q + 1];
-        acc[0] = f_add(acc[0], f_mul(p0, v0));
-        acc[1] = f_add(acc[1], f_mul(p1, v1));
-        acc[2] = f_add(acc[2], f_mul(f_ext2(p1, p0), f_ext2(v1, v0)));
-        if (hasB) {
-            const u64 b0 = b[2 * q], b1 = b[2 * q + 1];
-            acc[0] = f_add(acc[0], b0);
-            acc[1] = f_add(acc[1], b1);
-            acc[2] = f_add(acc[2], f_ext2(b1, b0));
-            b[q] = f_add(b0, f_mul(r, f_sub(b1, b0)));
-        }
-        p[q] = f_add(p0, f_mul(r, f_sub(p1, p0)));
-        v[q] = f_add(v0, f_mul(r, f_sub(v1, v0)));
-    }
-}
-
-__global__ void __launch_bounds__(SC_NT) k_sc_wave(Globals G, const WaveDev *waves, const Item *items,
-                                                   u64 *partials)
-{
-    __shared__ u64 s_r[32];
-    __shared__ u64 s_lvl[3][SC_NT];
-    __shared__ u64 s_x[3][SC_NT / 2], s_y[3][SC_NT / 2];
-    __shared__ u64 s_ctr[3][SC_NT];
-    __shared__ u64 s_wsum[SC_NT / 32][3 * SC_M];
-
-    const Item it = items[blockIdx.x];
-    const WaveDev &W = waves[it.wave];
-    const u32 nr = W.nr;
-    const u32 chunk = it.chunk;
-    const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool hasB = (W.flags & WF_HASB) != 0;
-    const bool peq = (W.flags & WF_PEQ) != 0;
-    if (tid < nr) s_r[tid] = G.chal[W.chal_off + tid];
-    __syncthreads();
-
-    const u32 e = (nr >= SC_M) ? SC_M : 0;
-    const u32 na = 1u << (nr - e);
-    const u64 base = (u64)chunk << nr;
-
-    u64 acc[SC_M][3];
-#pragma unroll
-    for (int k = 0; k < SC_M; k++) acc[k][0] = acc[k][1] = acc[k][2] = 0;
-    u64 fp = 0, fv = 0, fb = 0;
-    if (tid < na) {
-        if (e == SC_M) {
-            u64 p[8], v[8], b[8];
-            const u64 x0 = base + ((u64)tid << SC_M);
-            const ulonglong2 *sv = reinterpret_cast<const ulonglong2 *>(W.inV + x0);
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const ulonglong2 t = sv[q];
-                v[2 * q] = t.x;
-                v[2 * q + 1] = t.y;
-            }
-            if (peq) {
-#pragma unroll
-                for (int q = 0; q < 8; q++) p[q] = eq_at(W.peq, x0 + q);
-            } else {
-                const ulonglong2 *sp = reinterpret_cast<const ulonglong2 *>(W.inP + x0);
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const ulonglong2 t = sp[q];
-                    p[2 * q] = t.x;
-                    p[2 * q + 1] = t.y;
-                }
-            }
-            if (hasB) {
-                const ulonglong2 *sb = reinterpret_cast<const ulonglong2 *>(W.inB + x0);
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const ulonglong2 t = sb[q];
-                    b[2 * q] = t.x;
-                    b[2 * q + 1] = t.y;
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < 8; q++) b[q] = 0;
-            }
-            sc_level<4>(p, v, b, s_r[0], acc[0], hasB);
-            sc_level<2>(p, v, b, s_r[1], acc[1], hasB);
-            sc_level<1>(p, v, b, s_r[2], acc[2], hasB);
-            fp = p[0];
-            fv = v[0];
-            fb = b[0];
-        } else {
-            const u64 x = base + tid;
-            fv = W.inV[x];
-            fp = peq ? eq_at(W.peq, x) : W.inP[x];
-            fb = hasB ? W.inB[x] : 0;
-        }
-        s_lvl[0][tid] = fp;
-        s_lvl[1][tid] = fv;
-        s_lvl[2][tid] = fb;
-    }
-    if (e == SC_M) {
-#pragma unroll
-        for (int k = 0; k < SC_M; k++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const u64 s = warp_sum(acc[k][c]);
-                if (lane == 0) s_wsum[warp][k * 3 + c] = s;
-            }
-    }
-    __syncthreads();
-
-    // Remaining rounds over the na level values.
-    u64 *cP = s_lvl[0], *cV = s_lvl[1], *cB = s_lvl[2];
-    u32 m = na;
-    int flip = 0;
-    for (u32 k = e; k < nr; k++) {
-        const u32 half = m >> 1;
-        const u32 seg = na - (na >> (k - e));
-        u64 *nP = flip ? s_y[0] : s_x[0];
-        u64 *nV = flip ? s_y[1] : s_x[1];
-        u64 *nB = flip ? s_y[2] : s_x[2];
-        if (tid < half) {
-            const u64 r = s_r[k];
-            const u64 p0 = cP[2 * tid], p1 = cP[2 * tid + 1];
-            const u64 v0 = cV[2 * tid], v1 = cV[2 * tid + 1];
-            const u64 b0 = cB[2 * tid], b1 = cB[2 * tid + 1];
-            s_ctr[0][seg + tid] = f_add(f_mul(p0, v0), b0);
-            s_ctr[1][seg + tid] = f_add(f_mul(p1, v1), b1);
-            s_ctr[2][seg + tid] = f_add(f_mul(f_ext2(p1, p0), f_ext2(v1, v0)), f_ext2(b1, b0));
-            nP[tid] = f_add(p0, f_mul(r, f_sub(p1, p0)));
-            nV[tid] = f_add(v0, f_mul(r, f_sub(v1, v0)));
-            nB[tid] = f_add(b0, f_mul(r, f_sub(b1, b0)));
-        }
-        __syncthreads();
-        cP = nP;
-        cV = nV;
-        cB = nB;
-        m = half;
-        flip ^= 1;
-    }
-
-    // Per-round partial messages of this chunk.
-    const u32 nwarps = SC_NT / 32;
-    for (u32 k = warp; k < nr; k += nwarps) {
-        for (int c = 0; c < 3; c++) {
-            u64 s = 0;
-            if (k < e) {
-                if (lane < nwarps) s = s_wsum[lane][k * 3 + c];
-            } else {
-                const u32 seg = na - (na >> (k - e));
-                const u32 len = na >> (k - e + 1);
-                for (u32 q = lane; q < len; q += 32) s = f_add(s, s_ctr[c][seg + q]);
-            }
-            s = warp_sum(s);
-            if (lane == 0) partials[W.part + ((u64)k * W.nchunks + chunk) * 3 + c] = s;
-        }
-    }
-    if (!(W.flags & WF_LAST) && tid == 0) {
-        W.outP[chunk] = cP[0];
-        W.outV[chunk] = cV[0];
-        if (hasB) W.outB[chunk] = cB[0];
-    }
-}
-
-void launch_sc_wave(const Globals &G, const WaveDev *waves, const Item *items, int nitems, u64 *partials,
-                    cudaStream_t st)
-{
-    if (nitems > 0) k_sc_wave<<<nitems, SC_NT, 0, st>>>(G, waves, items, partials);
-}
-
-// --------------------------------------------------------------------------------
-// Final reduction: each round's value = sum over the chunks' partials; the
-// outputs open the transcript.
-// --------------------------------------------------------------------------------
-
-__global__ void __launch_bounds__(256) k_final(Globals G, const RoundRef *rounds, int nrounds,
-                                               const u64 *partials, const u64 *V0, u64 S0)
-{
-    const u32 lane = threadIdx.x & 31;
-    const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
-    for (u64 gw = (blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5; gw < (u64)nrounds; gw += nwarps) {
-        const RoundRef R = rounds[gw];
-        for (int c = 0; c < 3; c++) {
-            u64 s = 0;
-            for (u32 q = lane; q < R.nchunks; q += 32) s = f_add(s, partials[R.part_pos + (u64)q * 3 + c]);
-            s = warp_sum(s);
-            if (lane == 0) G.tr[R.tr_pos + c] = s;
-        }
-    }
-    for (u64 x = blockIdx.x * (u64)blockDim.x + threadIdx.x; x < S0; x += (u64)gridDim.x * blockDim.x)
-        G.tr[x] = V0[x];
-}
-
-void launch_final(const Globals &G, const RoundRef *rounds, int nrounds, const u64 *partials, const u64 *V0,
-                  u64 S0, cudaStream_t st)
-{
-    u64 threads = (u64)nrounds * 32;
-    if (threads < S0) threads = S0;
-    u64 blocks = (threads + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    if (blocks == 0) blocks = 1;
-    k_final<<<(unsigned)blocks, 256, 0, st>>>(G, rounds, nrounds, partials, V0, S0);
-}

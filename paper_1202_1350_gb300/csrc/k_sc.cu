@@ -1,0 +1,572 @@
+// k_sc.cu -- sum-check waves of the prover (Sec. 4.1.1 of the paper: every
+// message is a field sum of independent per-gate contributions; Sec. 3.1:
+// messages are degree-2 polynomials given by their values at 0, 1, 2).
+//
+// Each sum-check instance (SCI) sums P(x) V(x) + B(x) over n variables bound
+// low bit first.  Two kinds of instance:
+//
+//  * product-weighted (PROD): P(x) = sigma prod_m L_m(x_m) with linear factors
+//    L_m(b) = c0_m (1-b) + c1_m b, B = gamma-multiple of P.  Folding P keeps the
+//    product form, so P is never stored: round j's message is
+//      g_j(t) = kappa_j L_j(t) h_j(t),  h_j(t) = sum_y E_j(y) V_j(t, y),
+//    with kappa_j = sigma prod_{m<j} L_m(r_m), E_j(y) = prod_{m>j} L_m(y_m) and
+//    V_j the value table folded with r_0..r_{j-1}; h_j is linear in t, so only
+//    h_j(0), h_j(1) are summed.  Per pair of entries: two multiply-adds and one
+//    fold.  Used for phase 1 of every layer (P = eq(z_i, .)) and for phase 3 of
+//    TREE and SQUARE layers.
+//  * general (GEN): P, V, B are tables folded every round; the message needs
+//    P(t)V(t) at t = 0, 1, 2.  The first wave builds P and B from the wiring on
+//    the fly (SQUARE, TREE phase 2) or reads tables built by k_build23.
+//
+// Arithmetic is lazy: table values stay in W = [0, 2^61 + 8), products
+// accumulate exactly in 128 bits and are reduced once per round per thread;
+// only transcript entries are made canonical.
+#include <cuda_runtime.h>
+#include "plan.h"
+
+// --------------------------------------------------------------------------------
+// Shared helpers
+// --------------------------------------------------------------------------------
+
+// Sum over the warp of 16 values per lane: afterwards lane l holds the total of
+// value index l >> 1.  Inputs in W; sums are brought back to W every two
+// halving steps (a sum of four W values is below 2^64).
+__device__ __forceinline__ u64 warp_sum16(u64 (&v)[16])
+{
+    const u32 lane = threadIdx.x & 31;
+#pragma unroll
+    for (int step = 0; step < 4; step++) {
+        const int o = 16 >> step, half = 8 >> step;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; i++) {
+            const u64 send = up ? v[i] : v[i + half];
+            const u64 keep = up ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            if (step & 1) v[i] = wred(v[i]);
+        }
+    }
+    u64 r = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+    return wred(r);
+}
+
+// Warp-wide sum of one W value per lane -> W.
+__device__ __forceinline__ u64 warp_wsum(u64 x)
+{
+    x += __shfl_xor_sync(0xffffffffu, x, 16);
+    x += __shfl_xor_sync(0xffffffffu, x, 8);
+    x = wred(x);
+    x += __shfl_xor_sync(0xffffffffu, x, 4);
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    x = wred(x);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    return wred(x);
+}
+
+// --------------------------------------------------------------------------------
+// PROD: per-wave weight tables (computed once per proof, shared by all CTAs)
+// --------------------------------------------------------------------------------
+
+// Linear factor L_m of a product-weighted instance, from the coins.
+__device__ __forceinline__ void prod_factor(const Globals &G, const SciDev &S, u32 m, u64 &c0, u64 &c1)
+{
+    const LayerDev &L = G.layers[S.layer];
+    const u64 *rP = G.chal + L.chal_off, *r1 = rP + L.s;
+    switch (S.kind) {
+    case PK_PH1: {
+        const u64 z = G.pts[L.z_off + m];
+        c0 = f_sub(1, z);
+        c1 = z;
+        break;
+    }
+    case PK_TREE3: {
+        if (m == 0) {
+            c0 = 0;
+            c1 = 1;
+        } else {
+            const u64 a = rP[m - 1], b = r1[m];
+            c0 = f_mul(f_sub(1, a), f_sub(1, b));
+            c1 = f_mul(a, b);
+        }
+        break;
+    }
+    default: {  // PK_SQ3
+        const u64 a = rP[m], b = r1[m];
+        c0 = f_mul(f_sub(1, a), f_sub(1, b));
+        c1 = f_mul(a, b);
+        break;
+    }
+    }
+}
+
+// One CTA per PROD wave.  Writes the wave's weight block
+//   Q_k(q) = prod_{m=k+1}^{e-1} L_{r0+m}(bit_{m-k-1} q)      k < e          (in-thread rounds)
+//   E_k(y) = prod_{m=k+1}^{nr-1} L_{r0+m}(bit_{m-k-1} y)     k = kb..nr-1   (per-thread / in-CTA rounds)
+//   outer lo / hi: split table of prod_{m >= r0+nr} L_m over the chunk index,
+// and, for the first wave of an SCI, its factors, kappa_j (without sigma) and
+// esum_j = prod_{m>j} (c0_m + c1_m).
+__global__ void __launch_bounds__(256) k_prep_prod(Globals G, const SciDev *scis, const ProdWave *waves)
+{
+    const ProdWave &W = waves[blockIdx.x];
+    const SciDev &S = scis[W.sci];
+    __shared__ u64 c0[32], c1[32];
+    const u32 tid = threadIdx.x;
+    if (tid < S.n) prod_factor(G, S, tid, c0[tid], c1[tid]);
+    __syncthreads();
+    if (W.r0 == 0 && tid == 0) {
+        const u64 *r = G.chal + S.chal_off;
+        u64 k = 1;
+        for (u32 j = 0; j < S.n; j++) {
+            S.Lc[2 * j] = c0[j];
+            S.Lc[2 * j + 1] = c1[j];
+            S.kap[j] = k;
+            k = f_mul(k, f_add(c0[j], f_mul(r[j], f_sub(c1[j], c0[j]))));
+        }
+        u64 es = 1;
+        for (int j = (int)S.n - 1; j >= 0; j--) {
+            S.esum[j] = es;
+            es = f_mul(es, f_add(c0[j], c1[j]));
+        }
+    }
+    const u32 e = W.e, nr = W.nr, r0 = W.r0;
+    u64 *blk = W.wblk;
+    // Q block
+    for (u32 idx = tid; idx + 1 < (1u << e); idx += blockDim.x) {
+        u32 k = 0;
+        while (idx >= (1u << e) - (1u << (e - k - 1))) k++;
+        const u32 q = idx - ((1u << e) - (1u << (e - k)));
+        u64 v = 1;
+        for (u32 m = k + 1; m < e; m++) v = f_mul(v, ((q >> (m - k - 1)) & 1) ? c1[r0 + m] : c0[r0 + m]);
+        blk[idx] = v;
+    }
+    // E block
+    const u32 kb = e ? e - 1 : 0;
+    u64 *E = blk + ((1u << e) - 1);
+    const u32 esize = (1u << (nr - kb)) - 1;
+    for (u32 idx = tid; idx < esize; idx += blockDim.x) {
+        u32 k = kb;
+        while (idx >= (1u << (nr - kb)) - (1u << (nr - k - 1))) k++;
+        const u32 y = idx - ((1u << (nr - kb)) - (1u << (nr - k)));
+        u64 v = 1;
+        for (u32 m = k + 1; m < nr; m++) v = f_mul(v, ((y >> (m - k - 1)) & 1) ? c1[r0 + m] : c0[r0 + m]);
+        E[idx] = v;
+    }
+    // outer split tables
+    u64 *olo = E + esize;
+    const u32 o0 = r0 + nr, no = W.no, ho = W.ho;
+    u64 *ohi = olo + (1u << ho);
+    for (u32 j = tid; j < (1u << ho); j += blockDim.x) {
+        u64 v = 1;
+        for (u32 m = 0; m < ho; m++) v = f_mul(v, ((j >> m) & 1) ? c1[o0 + m] : c0[o0 + m]);
+        olo[j] = v;
+    }
+    for (u32 j = tid; j < (1u << (no - ho)); j += blockDim.x) {
+        u64 v = 1;
+        for (u32 m = 0; m < no - ho; m++) v = f_mul(v, ((j >> m) & 1) ? c1[o0 + ho + m] : c0[o0 + ho + m]);
+        ohi[j] = v;
+    }
+}
+
+void launch_prep_prod(const Globals &G, const SciDev *scis, const ProdWave *waves, int nwaves, cudaStream_t st)
+{
+    if (nwaves > 0) k_prep_prod<<<nwaves, 256, 0, st>>>(G, scis, waves);
+}
+
+// --------------------------------------------------------------------------------
+// PROD waves
+// --------------------------------------------------------------------------------
+
+#define PR_NT 256
+
+__global__ void __launch_bounds__(PR_NT, 2) k_sc_prod(Globals G, const ProdWave *waves, const Item *items,
+                                                      u64 *partials)
+{
+    constexpr int M = PR_M;
+    __shared__ u32 s_r0[32], s_r1[32];
+    __shared__ u64 s_Q[1 << M];
+    __shared__ u64 s_E[512];
+    __shared__ u64 s_lvl[PR_NT], s_x[PR_NT / 2], s_y[PR_NT / 2];
+    __shared__ u64 s_c[2][PR_NT];
+    __shared__ u64 s_w[PR_NT / 32][16];
+    __shared__ u64 s_echunk;
+
+    const Item it = items[blockIdx.x];
+    const ProdWave &W = waves[it.wave];
+    const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const u32 nr = W.nr, e = W.e, chunk = it.chunk;
+    const u32 na = 1u << (nr - e);
+    const u64 base = (u64)chunk << nr;
+    if (tid < nr) limbs31(G.chal[W.chal_off + tid], s_r0[tid], s_r1[tid]);
+    const u64 *blk = W.wblk;
+    const u32 qsize = (1u << e) - 1;
+    const u32 kb = e ? e - 1 : 0;
+    const u32 esize = (1u << (nr - kb)) - 1;
+    if (tid < qsize) s_Q[tid] = blk[tid];
+    for (u32 k = tid; k < esize; k += PR_NT) s_E[k] = blk[qsize + k];
+    if (tid == 0) {
+        const u64 *olo = blk + qsize + esize;
+        const u64 *ohi = olo + (1u << W.ho);
+        s_echunk = f_mul(olo[chunk & ((1u << W.ho) - 1)], ohi[chunk >> W.ho]);
+    }
+    __syncthreads();
+
+    u64 hv[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) hv[i] = 0;
+    if (e == M) {
+        if (tid < na) {
+            u64 u[1 << M];
+            const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(W.in + base + ((u64)tid << M));
+#pragma unroll
+            for (int q = 0; q < (1 << (M - 1)); q++) {
+                const ulonglong2 t = src[q];
+                u[2 * q] = t.x;
+                u[2 * q + 1] = t.y;
+            }
+            const u64 T = s_E[tid];  // E_{e-1}(tid)
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+                acc128 a0, a1;
+                acc_zero(a0);
+                acc_zero(a1);
+                const u32 rr0 = s_r0[k], rr1 = s_r1[k];
+                const int qoff = (1 << M) - (1 << (M - k));
+#pragma unroll
+                for (int q = 0; q < (1 << (M - k - 1)); q++) {
+                    const u64 w = s_Q[qoff + q];
+                    const u64 u0 = u[2 * q], u1 = u[2 * q + 1];
+                    mac(a0, w, u0);
+                    mac(a1, w, u1);
+                    u[q] = wfold(u0, u1, rr0, rr1);
+                }
+                hv[2 * k] = wmul(T, acc_red(a0));
+                hv[2 * k + 1] = wmul(T, acc_red(a1));
+            }
+            s_lvl[tid] = u[0];
+        }
+    } else if (tid < na) {
+        s_lvl[tid] = W.in[base + tid];
+    }
+    if (e == M) {
+        const u64 s = warp_sum16(hv);
+        if ((lane & 1) == 0 && (lane >> 1) < 2 * M) s_w[warp][lane >> 1] = s;
+    }
+    __syncthreads();
+
+    // rounds e..nr-1 across the CTA's na level values
+    u64 *cur = s_lvl;
+    u32 m = na;
+    const u32 eoff0 = (1u << (nr - kb));
+    for (u32 k = e; k < nr; k++) {
+        const u32 half = m >> 1;
+        const u32 seg = na - (na >> (k - e));
+        u64 *nxt = ((k - e) & 1) ? s_y : s_x;
+        if (tid < half) {
+            const u64 w = s_E[eoff0 - (1u << (nr - k)) + tid];  // E_k(tid)
+            const u64 u0 = cur[2 * tid], u1 = cur[2 * tid + 1];
+            s_c[0][seg + tid] = wmul(w, u0);
+            s_c[1][seg + tid] = wmul(w, u1);
+            nxt[tid] = wfold(u0, u1, s_r0[k], s_r1[k]);
+        }
+        __syncthreads();
+        cur = nxt;
+        m = half;
+    }
+
+    // per-round sums of this chunk, times the chunk's outer weight
+    const u64 ech = s_echunk;
+    for (u32 idx = warp; idx < 2 * nr; idx += PR_NT / 32) {
+        const u32 k = idx >> 1, t = idx & 1;
+        u64 s = 0;
+        if (k < e) {
+            if (lane < PR_NT / 32) s = s_w[lane][idx];
+        } else {
+            const u32 seg = na - (na >> (k - e));
+            const u32 len = na >> (k - e + 1);
+            for (u32 q = lane; q < len; q += 32) s = wred(s + s_c[t][seg + q]);
+        }
+        s = warp_wsum(s);
+        if (lane == 0) partials[W.part + ((u64)k * W.nchunks + chunk) * 2 + t] = wmul(s, ech);
+    }
+    if (!(W.flags & WF_LAST) && tid == 0) W.out[chunk] = cur[0];
+}
+
+void launch_sc_prod(const Globals &G, const ProdWave *waves, const Item *items, int nitems, u64 *partials,
+                    cudaStream_t st)
+{
+    if (nitems > 0) k_sc_prod<<<nitems, PR_NT, 0, st>>>(G, waves, items, partials);
+}
+
+// --------------------------------------------------------------------------------
+// GEN waves: tables P, V, B folded every round; message values at t = 0, 1, 2.
+// --------------------------------------------------------------------------------
+
+#define GN_NT 256
+
+// P and B of the first wave for the on-the-fly kinds, for the run of 8
+// entries at x0 whose V values are v[].
+__device__ __forceinline__ void gen_source(const Globals &G, const GenWave &W, u64 x0, const u64 (&v)[8],
+                                           u64 (&p)[8], u64 (&b)[8])
+{
+    const LayerDev &L = G.layers[W.layer];
+    if (W.src == GS_SQ2) {
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            p[q] = wmul(eq_at(L.trp, x0 + q), v[q]);
+            b[q] = 0;
+        }
+    } else if (W.src == GS_TREE2) {
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+            const u64 w = eq_at(L.trp, (x0 + q) >> 1);
+            p[q] = w;
+            b[q] = wmul(w, v[q + 1]);
+            p[q + 1] = 0;
+            b[q + 1] = 0;
+        }
+    } else {
+        const ulonglong2 *sp = reinterpret_cast<const ulonglong2 *>(W.inP + x0);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const ulonglong2 t = sp[q];
+            p[2 * q] = t.x;
+            p[2 * q + 1] = t.y;
+        }
+        if (W.flags & WF_HASB) {
+            const ulonglong2 *sb = reinterpret_cast<const ulonglong2 *>(W.inB + x0);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const ulonglong2 t = sb[q];
+                b[2 * q] = t.x;
+                b[2 * q + 1] = t.y;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; q++) b[q] = 0;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(GN_NT, 2) k_sc_gen(Globals G, const GenWave *waves, const Item *items,
+                                                     u64 *partials)
+{
+    constexpr int M = GN_M;
+    __shared__ u32 s_r0[32], s_r1[32];
+    __shared__ u64 s_lvl[3][GN_NT], s_x[3][GN_NT / 2], s_y[3][GN_NT / 2];
+    __shared__ u64 s_c[3][GN_NT];
+    __shared__ u64 s_w[GN_NT / 32][16];
+
+    const Item it = items[blockIdx.x];
+    const GenWave &W = waves[it.wave];
+    const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const u32 nr = W.nr, e = W.e, chunk = it.chunk;
+    const u32 na = 1u << (nr - e);
+    const u64 base = (u64)chunk << nr;
+    const bool hasB = (W.flags & WF_HASB) != 0;
+    if (tid < nr) limbs31(G.chal[W.chal_off + tid], s_r0[tid], s_r1[tid]);
+    __syncthreads();
+
+    u64 hv[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) hv[i] = 0;
+    if (e == M) {
+        if (tid < na) {
+            u64 p[8], v[8], b[8];
+            const u64 x0 = base + ((u64)tid << M);
+            const ulonglong2 *sv = reinterpret_cast<const ulonglong2 *>(W.inV + x0);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const ulonglong2 t = sv[q];
+                v[2 * q] = t.x;
+                v[2 * q + 1] = t.y;
+            }
+            if (W.src != GS_NONE) {
+                gen_source(G, W, x0, v, p, b);
+            } else {
+                const ulonglong2 *sp = reinterpret_cast<const ulonglong2 *>(W.inP + x0);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const ulonglong2 t = sp[q];
+                    p[2 * q] = t.x;
+                    p[2 * q + 1] = t.y;
+                }
+                if (hasB) {
+                    const ulonglong2 *sb = reinterpret_cast<const ulonglong2 *>(W.inB + x0);
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const ulonglong2 t = sb[q];
+                        b[2 * q] = t.x;
+                        b[2 * q + 1] = t.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; q++) b[q] = 0;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < M; k++) {
+                acc128 a0, a1, a2;
+                acc_zero(a0);
+                acc_zero(a1);
+                acc_zero(a2);
+                const u32 rr0 = s_r0[k], rr1 = s_r1[k];
+#pragma unroll
+                for (int q = 0; q < (1 << (M - k - 1)); q++) {
+                    const u64 p0 = p[2 * q], p1 = p[2 * q + 1], v0 = v[2 * q], v1 = v[2 * q + 1];
+                    mac(a0, p0, v0);
+                    mac(a1, p1, v1);
+                    mac(a2, wext2(p1, p0), wext2(v1, v0));
+                    const u64 b0 = b[2 * q], b1 = b[2 * q + 1];
+                    acc_add(a0, b0);
+                    acc_add(a1, b1);
+                    acc_add(a2, wext2(b1, b0));
+                    p[q] = wfold(p0, p1, rr0, rr1);
+                    v[q] = wfold(v0, v1, rr0, rr1);
+                    b[q] = wfold(b0, b1, rr0, rr1);
+                }
+                hv[3 * k] = acc_red(a0);
+                hv[3 * k + 1] = acc_red(a1);
+                hv[3 * k + 2] = acc_red(a2);
+            }
+            s_lvl[0][tid] = p[0];
+            s_lvl[1][tid] = v[0];
+            s_lvl[2][tid] = b[0];
+        }
+    } else if (tid < na) {
+        const u64 x = base + tid;
+        s_lvl[1][tid] = W.inV[x];
+        if (W.src == GS_SQ2) {
+            s_lvl[0][tid] = wmul(eq_at(G.layers[W.layer].trp, x), s_lvl[1][tid]);
+            s_lvl[2][tid] = 0;
+        } else if (W.src == GS_TREE2) {
+            const u64 w = (x & 1) ? 0 : eq_at(G.layers[W.layer].trp, x >> 1);
+            s_lvl[0][tid] = w;
+            s_lvl[2][tid] = (x & 1) ? 0 : wmul(w, W.inV[x + 1]);
+        } else {
+            s_lvl[0][tid] = W.inP[x];
+            s_lvl[2][tid] = hasB ? W.inB[x] : 0;
+        }
+    }
+    if (e == M) {
+        const u64 s = warp_sum16(hv);
+        if ((lane & 1) == 0 && (lane >> 1) < 3 * M) s_w[warp][lane >> 1] = s;
+    }
+    __syncthreads();
+
+    u64 *cP = s_lvl[0], *cV = s_lvl[1], *cB = s_lvl[2];
+    u32 m = na;
+    for (u32 k = e; k < nr; k++) {
+        const u32 half = m >> 1;
+        const u32 seg = na - (na >> (k - e));
+        const bool odd = ((k - e) & 1) != 0;
+        u64 *nP = odd ? s_y[0] : s_x[0], *nV = odd ? s_y[1] : s_x[1], *nB = odd ? s_y[2] : s_x[2];
+        if (tid < half) {
+            const u64 p0 = cP[2 * tid], p1 = cP[2 * tid + 1];
+            const u64 v0 = cV[2 * tid], v1 = cV[2 * tid + 1];
+            const u64 b0 = cB[2 * tid], b1 = cB[2 * tid + 1];
+            s_c[0][seg + tid] = wred(wmul(p0, v0) + b0);
+            s_c[1][seg + tid] = wred(wmul(p1, v1) + b1);
+            s_c[2][seg + tid] = wred(wmul(wext2(p1, p0), wext2(v1, v0)) + wext2(b1, b0));
+            const u32 rr0 = s_r0[k], rr1 = s_r1[k];
+            nP[tid] = wfold(p0, p1, rr0, rr1);
+            nV[tid] = wfold(v0, v1, rr0, rr1);
+            nB[tid] = wfold(b0, b1, rr0, rr1);
+        }
+        __syncthreads();
+        cP = nP;
+        cV = nV;
+        cB = nB;
+        m = half;
+    }
+
+    for (u32 idx = warp; idx < 3 * nr; idx += GN_NT / 32) {
+        const u32 k = idx / 3, t = idx % 3;
+        u64 s = 0;
+        if (k < e) {
+            if (lane < GN_NT / 32) s = s_w[lane][idx];
+        } else {
+            const u32 seg = na - (na >> (k - e));
+            const u32 len = na >> (k - e + 1);
+            for (u32 q = lane; q < len; q += 32) s = wred(s + s_c[t][seg + q]);
+        }
+        s = warp_wsum(s);
+        if (lane == 0) partials[W.part + ((u64)k * W.nchunks + chunk) * 3 + t] = s;
+    }
+    if (!(W.flags & WF_LAST) && tid == 0) {
+        W.outP[chunk] = cP[0];
+        W.outV[chunk] = cV[0];
+        if (W.outB) W.outB[chunk] = cB[0];
+    }
+}
+
+void launch_sc_gen(const Globals &G, const GenWave *waves, const Item *items, int nitems, u64 *partials,
+                   cudaStream_t st)
+{
+    if (nitems > 0) k_sc_gen<<<nitems, GN_NT, 0, st>>>(G, waves, items, partials);
+}
+
+// --------------------------------------------------------------------------------
+// Final reduction into the transcript: a warp per round sums the chunks'
+// partials; the round's scalars turn the sums into g(0), g(1), g(2).
+// --------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_final(Globals G, const SciDev *scis, const RoundRef *rounds, int nrounds,
+                                               const u64 *partials, const u64 *V0, u64 S0)
+{
+    const u32 lane = threadIdx.x & 31;
+    const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
+    for (u64 gw = (blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5; gw < (u64)nrounds; gw += nwarps) {
+        const RoundRef R = rounds[gw];
+        const SciDev &S = scis[R.sci];
+        const u32 nv = (S.kind >= PK_GEN_FIRST) ? 3 : 2;
+        u64 h[3];
+        for (u32 t = 0; t < nv; t++) {
+            u64 s = 0;
+            for (u32 q = lane; q < R.nchunks; q += 32) s = wred(s + partials[R.part_pos + (u64)q * nv + t]);
+            h[t] = wcanon(warp_wsum(s));
+        }
+        if (lane == 0) {
+            const LayerDev &L = G.layers[S.layer];
+            const u64 ez = G.scal[SCAL_EQZRP(S.layer)], v1 = G.scal[SCAL_V1(S.layer)];
+            u64 g0, g1, g2;
+            if (nv == 3) {
+                const u64 sg = (S.kind == PK_GEN_TAB) ? 1 : ez;
+                g0 = f_mul(sg, h[0]);
+                g1 = f_mul(sg, h[1]);
+                g2 = f_mul(sg, h[2]);
+            } else {
+                u64 sigma = 1, c2u = 0;
+                if (S.kind == PK_TREE3) {
+                    sigma = f_mul(ez, f_sub(1, G.chal[L.chal_off + L.s]));
+                    c2u = v1;
+                } else if (S.kind == PK_SQ3) {
+                    sigma = f_mul(ez, v1);
+                }
+                const u32 j = R.j;
+                const u64 es = S.esum[j];
+                const u64 h0 = f_add(h[0], f_mul(c2u, es)), h1 = f_add(h[1], f_mul(c2u, es));
+                const u64 kj = f_mul(sigma, S.kap[j]);
+                const u64 c0 = S.Lc[2 * j], c1 = S.Lc[2 * j + 1];
+                g0 = f_mul(kj, f_mul(c0, h0));
+                g1 = f_mul(kj, f_mul(c1, h1));
+                g2 = f_mul(kj, f_mul(f_sub(f_add(c1, c1), c0), f_sub(f_add(h1, h1), h0)));
+            }
+            G.tr[R.tr_pos] = g0;
+            G.tr[R.tr_pos + 1] = g1;
+            G.tr[R.tr_pos + 2] = g2;
+        }
+    }
+    for (u64 x = blockIdx.x * (u64)blockDim.x + threadIdx.x; x < S0; x += (u64)gridDim.x * blockDim.x)
+        G.tr[x] = V0[x];
+}
+
+void launch_final(const Globals &G, const SciDev *scis, const RoundRef *rounds, int nrounds, const u64 *partials,
+                  const u64 *V0, u64 S0, cudaStream_t st)
+{
+    u64 threads = (u64)nrounds * 32;
+    if (threads < S0) threads = S0;
+    u64 blocks = (threads + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks == 0) blocks = 1;
+    k_final<<<(unsigned)blocks, 256, 0, st>>>(G, scis, rounds, nrounds, partials, V0, S0);
+}

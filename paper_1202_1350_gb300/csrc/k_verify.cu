@@ -160,9 +160,20 @@ __device__ u64 lagrange_at(const u64 *q, u32 n, u64 x, const u64 *invfact)
     return acc;
 }
 
-#define VC_NT 256
+#define VC_NT 1024
 
-__global__ void __launch_bounds__(VC_NT) k_vcheck(Globals G, VerifyDev V, EqTab tz0, u64 S0)
+// All checks of the verifier, concurrently (one CTA):
+//   phase 1: transcript entries canonical; claimed outputs' MLE at z_0; sum of
+//            the input-MLE partials;
+//   phase 2: per layer i, its starting claim (V~_0(z_0) for i = 0, else
+//            q_{i-1}(tau_{i-1})), its end check claim_n = eq(z_i, r_P)[add~ (v1+v2)
+//            + mult~ v1 v2] with claim_n = g_{n-1}(r_{n-1}) (or the starting
+//            claim when the layer has no rounds), and for the last layer
+//            q(tau) = input MLE;
+//   phase 3: per round j of layer i, g_j(0) + g_j(1) = g_{j-1}(r_{j-1}) (the
+//            starting claim for j = 0).
+__global__ void __launch_bounds__(VC_NT) k_vcheck(Globals G, VerifyDev V, EqTab tz0, u64 S0, const u32 *round_layer,
+                                                  u32 nrounds)
 {
     __shared__ u64 invfact[64];
     __shared__ u64 s_red[VC_NT / 32];
@@ -173,20 +184,18 @@ __global__ void __launch_bounds__(VC_NT) k_vcheck(Globals G, VerifyDev V, EqTab 
         s_bad = 0;
         s_fail = 0;
     }
-    if (tid < 64) {
-        u64 f = 1;
-        for (u32 j = 2; j <= tid; j++) f = f_mul(f, j);
-        invfact[tid] = f_inv(f);
-    }
-    __syncthreads();
-    // Transcript entries must be canonical.
+    if (tid < 64) invfact[tid] = G.invfact[tid];
+    // phase 1
     bool bad = false;
     for (u64 k = tid; k < V.tr_len; k += VC_NT) bad |= (V.tr[k] >= FP_P);
-    if (__any_sync(0xffffffffu, bad) && lane == 0) s_bad = 1;
-    // Claimed outputs' multilinear extension at z_0.
     u64 acc = 0;
     for (u64 b = tid; b < S0; b += VC_NT) acc = f_add(acc, f_mul(eq_at(tz0, b), V.tr[b] >= FP_P ? 0 : V.tr[b]));
+    u64 acc2 = 0;
+    for (u32 k = tid; k < V.mle_blocks; k += VC_NT) acc2 = f_add(acc2, V.mle_part[k]);
+    __syncthreads();
+    if (__any_sync(0xffffffffu, bad) && lane == 0) s_bad = 1;
     acc = warp_sum(acc);
+    acc2 = warp_sum(acc2);
     if (lane == 0) s_red[warp] = acc;
     __syncthreads();
     if (tid < 32) {
@@ -195,11 +204,7 @@ __global__ void __launch_bounds__(VC_NT) k_vcheck(Globals G, VerifyDev V, EqTab 
         if (tid == 0) s_out_mle = v;
     }
     __syncthreads();
-    // Input multilinear extension at z_d: sum of the grid's partials.
-    acc = 0;
-    for (u32 k = tid; k < V.mle_blocks; k += VC_NT) acc = f_add(acc, V.mle_part[k]);
-    acc = warp_sum(acc);
-    if (lane == 0) s_red[warp] = acc;
+    if (lane == 0) s_red[warp] = acc2;
     __syncthreads();
     if (tid < 32) {
         u64 v = tid < VC_NT / 32 ? s_red[tid] : 0;
@@ -207,46 +212,52 @@ __global__ void __launch_bounds__(VC_NT) k_vcheck(Globals G, VerifyDev V, EqTab 
         if (tid == 0) s_in_mle = v;
     }
     __syncthreads();
-    if (!s_bad) {
-        for (u32 i = tid; i < G.d; i += VC_NT) {
-            const LayerDev &L = G.layers[i];
-            const u32 si = L.s, sn = L.sn, n = si + 2 * sn;
-            const u64 *r = G.chal + L.chal_off;
-            u64 claim;
-            if (i == 0) {
-                claim = s_out_mle;
-            } else {
-                const LayerDev &Lp = G.layers[i - 1];
-                const u64 tau = G.chal[Lp.chal_off + Lp.s + 2 * Lp.sn];
-                claim = lagrange_at(V.tr + Lp.tr_q, Lp.sn, tau, invfact);
-            }
-            bool ok = true;
-            const u64 *m = V.tr + L.tr_msg;
-            for (u32 j = 0; j < n; j++) {
-                const u64 g0 = m[3 * j], g1 = m[3 * j + 1], g2 = m[3 * j + 2];
-                ok &= (f_add(g0, g1) == claim);
-                claim = interp3(g0, g1, g2, r[j]);
-            }
-            const u64 *q = V.tr + L.tr_q;
-            const u64 v1 = q[0], v2 = sn ? q[1] : q[0];
-            u64 add, mult;
-            if (L.kind == W_EXPLICIT) {
-                add = V.wire[2 * i];
-                mult = V.wire[2 * i + 1];
-            } else {
-                wiring_closed(L.kind, si, sn, r, r + si, r + si + sn, add, mult);
-            }
-            const u64 expect = f_mul(G.scal[SCAL_EQZRP(i)],
-                                     f_add(f_mul(add, f_add(v1, v2)), f_mul(mult, f_mul(v1, v2))));
-            ok &= (expect == claim);
-            if (i + 1 == G.d) {
-                const u64 tau = G.chal[L.chal_off + si + 2 * sn];
-                ok &= (lagrange_at(q, sn, tau, invfact) == s_in_mle);
-            }
-            if (!ok) atomicOr(&s_fail, 1);
+    if (s_bad) goto done;
+    // phase 2
+    for (u32 i = tid; i < G.d; i += VC_NT) {
+        const LayerDev &L = G.layers[i];
+        const u32 si = L.s, sn = L.sn, n = si + 2 * sn;
+        const u64 *r = G.chal + L.chal_off;
+        u64 start;
+        if (i == 0) {
+            start = s_out_mle;
+        } else {
+            const LayerDev &Lp = G.layers[i - 1];
+            start = lagrange_at(V.tr + Lp.tr_q, Lp.sn, G.chal[Lp.chal_off + Lp.s + 2 * Lp.sn], invfact);
         }
+        V.claims[i] = start;
+        u64 claim = start;
+        if (n > 0) {
+            const u64 *m = V.tr + L.tr_msg + 3ull * (n - 1);
+            claim = interp3(m[0], m[1], m[2], r[n - 1]);
+        }
+        const u64 *q = V.tr + L.tr_q;
+        const u64 v1 = q[0], v2 = sn ? q[1] : q[0];
+        u64 add, mult;
+        if (L.kind == W_EXPLICIT) {
+            add = V.wire[2 * i];
+            mult = V.wire[2 * i + 1];
+        } else {
+            wiring_closed(L.kind, si, sn, r, r + si, r + si + sn, add, mult);
+        }
+        const u64 expect = f_mul(G.scal[SCAL_EQZRP(i)], f_add(f_mul(add, f_add(v1, v2)), f_mul(mult, f_mul(v1, v2))));
+        bool ok = (expect == claim);
+        if (i + 1 == G.d) ok &= (lagrange_at(q, sn, G.chal[L.chal_off + n], invfact) == s_in_mle);
+        if (!ok) atomicOr(&s_fail, 1);
     }
     __syncthreads();
+    // phase 3
+    for (u32 g = tid; g < nrounds; g += VC_NT) {
+        const u32 i = round_layer[g] >> 8, j = round_layer[g] & 0xFF;
+        const LayerDev &L = G.layers[i];
+        const u64 *m = V.tr + L.tr_msg + 3ull * j;
+        u64 prev;
+        if (j == 0) prev = V.claims[i];
+        else prev = interp3(m[-3], m[-2], m[-1], G.chal[L.chal_off + j - 1]);
+        if (f_add(m[0], m[1]) != prev) atomicOr(&s_fail, 1);
+    }
+    __syncthreads();
+done:
     if (tid == 0) {
         V.result[0] = s_in_mle;
         V.result[1] = s_out_mle;
@@ -256,11 +267,23 @@ __global__ void __launch_bounds__(VC_NT) k_vcheck(Globals G, VerifyDev V, EqTab 
     }
 }
 
+__global__ void k_init_invfact(u64 *invfact)
+{
+    const u32 k = threadIdx.x;
+    if (k < 64) {
+        u64 f = 1;
+        for (u32 j = 2; j <= k; j++) f = f_mul(f, j);
+        invfact[k] = f_inv(f);
+    }
+}
+
+void launch_init_invfact(u64 *invfact, cudaStream_t st) { k_init_invfact<<<1, 64, 0, st>>>(invfact); }
+
 void launch_verify(const Globals &G, const VerifyDev &V, const EqTab &tzd, const EqTab &tz0,
                    const u32 *explicit_layers, int n_explicit, cudaStream_t st)
 {
     const u64 nin = 1ull << tzd.n;
     k_vmle<<<V.mle_blocks, VM_NT, 0, st>>>(tzd, V.inputs, nin, V.mle_part, G.status);
     if (n_explicit > 0) k_vwire<<<n_explicit, VM_NT, 0, st>>>(G, explicit_layers, V.wire);
-    k_vcheck<<<1, VC_NT, 0, st>>>(G, V, tz0, 1ull << tz0.n);
+    k_vcheck<<<1, VC_NT, 0, st>>>(G, V, tz0, 1ull << tz0.n, V.round_layer, V.nrounds);
 }

@@ -57,33 +57,66 @@ struct LayerDev {
 #define SCAL_V1(i) (2 * (i) + 1)
 
 // Flags of a sum-check wave.
-enum : u32 { WF_PEQ = 1, WF_HASB = 2, WF_LAST = 4 };
+enum : u32 { WF_HASB = 2, WF_LAST = 4 };
 
-// Sum-check instance: sum_x P(x) V(x) + B(x) over n variables (Sec. 4.1.1's
-// message = field sum of per-entry contributions).  Phase 1 of layer i has
-// P = eq(z_i, .), V = V_i, B = 0; phases 2 and 3 use tables built from the
-// wiring (k_build23) with V = V_{i+1}.
-struct SciDev {
-    u32 n;        // rounds
-    u32 layer;
-    u32 phase;    // 1, 2, 3
-    u32 chal_off; // challenge of round k is chal[chal_off + k]
-    u64 tr_off;   // transcript offset of round 0's three values
+// Kinds of sum-check instance (SCI).  Product-weighted ones (< PK_GEN_FIRST)
+// keep P = sigma prod_m L_m(x_m) implicit; general ones fold P, V, B tables.
+enum : u32 {
+    PK_PH1 = 0,        // phase 1 of any layer: P = eq(z_i, .), V = V_i
+    PK_TREE3 = 1,      // TREE phase 3: L_0 = (0,1), L_m = eq(rP_{m-1},.) eq(r1_m,.), U = V + v1
+    PK_SQ3 = 2,        // SQUARE phase 3: L_m = eq(rP_m,.) eq(r1_m,.), sigma = eq(z,rP) v1
+    PK_GEN_FIRST = 8,
+    PK_GEN_SQ2 = 8,    // SQUARE phase 2: P[x] = eq(rP, x) V[x] (times eq(z, rP))
+    PK_GEN_TREE2 = 9,  // TREE phase 2: P[2g] = eq(rP, g), B[2g] = P[2g] V[2g+1] (times eq(z, rP))
+    PK_GEN_TAB = 10    // tables built by k_build23
 };
 
-// One wave of one SCI: each CTA folds a chunk of 2^nr entries down to one,
-// producing the partial messages of rounds r0..r0+nr-1 for its chunk.
-struct WaveDev {
+// Source of the first GEN wave's P and B.
+enum : u32 { GS_NONE = 0, GS_SQ2 = 1, GS_TREE2 = 2 };
+
+#define PR_M 5  // PROD: each thread folds 2^5 entries through 5 rounds in registers
+#define GN_M 3  // GEN: 2^3 entries, 3 rounds
+
+struct SciDev {
+    u32 n;         // rounds
+    u32 kind;      // PK_*
+    u32 layer;
+    u32 chal_off;  // challenge of round k: chal[chal_off + k]
+    u64 tr_off;    // transcript offset of round 0's three values
+    u64 *Lc;       // PROD: factors c0_m, c1_m (2n), written by k_prep_prod
+    u64 *kap;      // PROD: prod_{m<j} L_m(r_m)
+    u64 *esum;     // PROD: prod_{m>j} (c0_m + c1_m)
+};
+
+// One wave of a PROD SCI: each CTA folds 2^nr entries (the first e rounds in
+// registers, 2^e entries per thread; the rest across the CTA).
+struct ProdWave {
     u32 sci;
-    u32 r0, nr;
+    u32 r0, nr, e;
     u32 nchunks;
     u32 flags;
+    u32 no, ho;        // coordinates beyond the chunk (r0+nr..n-1) and their split
+    u32 chal_off;      // challenge of local round k: chal[chal_off + k]
+    u32 pad;
+    const u64 *in;     // entries of this wave's table
+    u64 *out;          // one folded value per chunk (unused on the last wave)
+    u64 *wblk;         // weight block: Q, E, outer lo, outer hi
+    u64 part;          // partials: part + (k * nchunks + chunk) * 2 + t
+};
+
+// One wave of a GEN SCI.
+struct GenWave {
+    u32 sci;
+    u32 r0, nr, e;
+    u32 nchunks;
+    u32 flags;
+    u32 src;           // GS_* (first wave only)
+    u32 layer;
+    u32 chal_off;
     u32 pad;
     const u64 *inP, *inV, *inB;
-    u64 *outP, *outV, *outB;  // nchunks entries each (unused on the last wave)
-    EqTab peq;                // P = eq(pt, .) when WF_PEQ
-    u64 part;                 // partials: part + (k * nchunks + chunk) * 3 + c
-    u64 chal_off;             // challenge of local round k: chal[chal_off + k]
+    u64 *outP, *outV, *outB;
+    u64 part;          // partials: part + (k * nchunks + chunk) * 3 + t
 };
 
 // Line reduction of layer i (q(t) = V~_{i+1}(l(t)), l(t) = r1 + t (r2 - r1)),
@@ -108,11 +141,14 @@ struct Item {
     u32 chunk;
 };
 
-// Final reduction of one round: sum nchunks partial triples into tr[tr_pos..+3].
+// Final reduction of one round: sum the chunks' partials (2 per chunk for
+// PROD, 3 for GEN) and write g(0), g(1), g(2) at tr[tr_pos].
 struct RoundRef {
     u64 tr_pos;
     u64 part_pos;
     u32 nchunks;
+    u32 sci;
+    u32 j;  // round index within the SCI
     u32 pad;
 };
 
@@ -130,6 +166,15 @@ struct Globals {
     u64 *invfact;     // 1/k! for k < 64 (verifier)
 };
 
+// A run of block-local layers evaluated by one launch (k_eval_seg): layers
+// i_hi down to i_lo, chunks of 2^c entries of layer i_hi + 1 per CTA.
+struct EvalSeg {
+    u32 i_hi, i_lo;
+    u32 c;
+    u32 nchunks;
+    u32 check_input;  // the run's input layer is the circuit's input layer
+};
+
 #define ST_BAD_INPUT 1u
 #define ST_TIMEOUT 2u
 
@@ -141,13 +186,17 @@ struct EqJob {
 void launch_setup(const Globals &G, u32 zd_off, cudaStream_t st);
 void launch_eqtabs(const EqJob *jobs, int njobs, cudaStream_t st);
 void launch_eval_layer(const Globals &G, const LayerDev &L, int i, cudaStream_t st);
+void launch_eval_seg(const Globals &G, const EvalSeg &S, cudaStream_t st);
 void launch_check_canonical(const u64 *x, u64 n, u32 *status, cudaStream_t st);
 void launch_line_wave(const Globals &G, const LineWaveDev *lw, const Item *items, int nitems,
                       cudaStream_t st);
 void launch_build23(const Globals &G, const u32 *blk_off, int nlayers, int nblocks, cudaStream_t st);
-void launch_sc_wave(const Globals &G, const WaveDev *waves, const Item *items, int nitems,
-                    u64 *partials, cudaStream_t st);
-void launch_final(const Globals &G, const RoundRef *rounds, int nrounds, const u64 *partials,
+void launch_prep_prod(const Globals &G, const SciDev *scis, const ProdWave *waves, int nwaves, cudaStream_t st);
+void launch_sc_prod(const Globals &G, const ProdWave *waves, const Item *items, int nitems, u64 *partials,
+                    cudaStream_t st);
+void launch_sc_gen(const Globals &G, const GenWave *waves, const Item *items, int nitems, u64 *partials,
+                   cudaStream_t st);
+void launch_final(const Globals &G, const SciDev *scis, const RoundRef *rounds, int nrounds, const u64 *partials,
                   const u64 *V0, u64 S0, cudaStream_t st);
 
 // verifier
@@ -161,7 +210,11 @@ struct VerifyDev {
     u64 *result;        // [0] input MLE, [1] output MLE, [2] accept flag, [3] bad-value flag
     u64 *wire;          // generic add~/mult~ per layer (EXPLICIT layers)
     int *accept_out;    // optional device int receiving the accept bit
+    u64 *claims;        // starting claim of every layer (d entries)
+    const u32 *round_layer;  // per global round: layer << 8 | round within layer
+    u32 nrounds;
 };
+void launch_init_invfact(u64 *invfact, cudaStream_t st);
 void launch_verify(const Globals &G, const VerifyDev &V, const EqTab &tzd, const EqTab &tz0,
                    const u32 *explicit_layers, int n_explicit, cudaStream_t st);
 

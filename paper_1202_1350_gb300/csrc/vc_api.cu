@@ -19,7 +19,12 @@
 
 namespace {
 
-constexpr u32 SC_CHUNK_LOG = 11;   // entries folded by one sum-check CTA (256 threads x 8)
+constexpr u32 PR_CHUNK_LOG = PR_M + 8;  // entries folded by one PROD CTA (256 threads x 2^PR_M)
+constexpr u32 GN_CHUNK_LOG = GN_M + 8;  // entries folded by one GEN CTA (256 threads x 2^GN_M)
+
+// Which layers' phase-2/3 tables are built by k_build23 (the rest are formed
+// on the fly or never stored).
+static bool needs_tables(u32 kind) { return kind != W_SQUARE && kind != W_TREE; }
 constexpr u32 LN_CHUNK0_LOG = 11;  // coordinates folded by the first line wave
 constexpr u32 LN_CHUNKW_LOG = 9;   // coordinates folded by later line waves
 
@@ -83,10 +88,16 @@ struct vc_circuit {
     std::vector<u32> build_off;
     u32 *d_build_off = nullptr;
     int build_blocks = 0;
-    std::vector<WaveDev> waves;
-    WaveDev *d_waves = nullptr;
-    std::vector<std::vector<Item>> sc_items;
-    std::vector<Item *> d_sc_items;
+    std::vector<SciDev> scis;
+    SciDev *d_scis = nullptr;
+    std::vector<ProdWave> pwaves;
+    ProdWave *d_pwaves = nullptr;
+    std::vector<std::vector<Item>> p_items;
+    std::vector<Item *> d_p_items;
+    std::vector<GenWave> gwaves;
+    GenWave *d_gwaves = nullptr;
+    std::vector<std::vector<Item>> g_items;
+    std::vector<Item *> d_g_items;
     std::vector<RoundRef> rounds;
     RoundRef *d_rounds = nullptr;
     u64 *partials = nullptr;
@@ -96,6 +107,11 @@ struct vc_circuit {
     std::vector<u32> explicit_layers;
     u32 *d_explicit_layers = nullptr;
     u64 *h_pinned = nullptr;  // small pinned buffer for status/result readback
+    // evaluation steps: seg >= 0 -> eval_segs[seg]; else per-layer launch of layer (-seg - 1)
+    std::vector<EvalSeg> eval_segs;
+    std::vector<int> eval_steps;
+    std::vector<u32> round_layer;
+    u32 *d_round_layer = nullptr;
     cudaEvent_t stage_ev[VC_NUM_STAGES + 1] = {};
     bool stage_on = false;
 };
@@ -129,6 +145,67 @@ static EqTab take_eq(Arena &A, const u64 *pt, u32 n)
     return t;
 }
 
+// Evaluation plan: runs of block-local layers (every kind but MATMULT and
+// EXPLICIT) go to one k_eval_seg launch each; a CTA takes 2^c entries of the
+// run's input layer (about 256 CTAs for wide layers) and keeps going while its
+// block stays >= 32 entries (or while one CTA covers the whole layer) and
+// <= 4096 entries.
+static void plan_eval(vc_circuit *c)
+{
+    c->eval_segs.clear();
+    c->eval_steps.clear();
+    int i = (int)c->d - 1;
+    auto local = [&](int j) { return c->kind[j] != W_MATMULT && c->kind[j] != W_EXPLICIT; };
+    while (i >= 0) {
+        if (!local(i)) {
+            c->eval_steps.push_back(-i - 1);
+            i--;
+            continue;
+        }
+        const int s_in = (int)c->s[i + 1];
+        int cl = std::min(s_in, std::max(s_in - 8, 10));
+        cl = std::min(cl, 12);
+        int i_lo = i + 1;
+        while (true) {
+            int e = cl, j = i;
+            i_lo = i + 1;
+            const bool whole = (cl == s_in);
+            while (j >= 0 && local(j)) {
+                const int ne = e + (int)c->s[j] - (int)c->s[j + 1];
+                if (ne < 0 || ne > 12 || (!whole && ne < 5)) break;
+                if (c->kind[j] == W_F0_PAIR && ne < 1) break;
+                e = ne;
+                i_lo = j;
+                j--;
+            }
+            if (i_lo <= i || cl == 0) break;
+            cl--;  // the first layer did not fit: smaller chunks
+        }
+        if (i_lo > i) {  // no run possible: evaluate this layer alone
+            c->eval_steps.push_back(-i - 1);
+            i--;
+            continue;
+        }
+        EvalSeg S{};
+        S.i_hi = (u32)i;
+        S.i_lo = (u32)i_lo;
+        S.c = (u32)cl;
+        S.nchunks = 1u << (s_in - cl);
+        S.check_input = (u32)(i + 1 == (int)c->d);
+        c->eval_steps.push_back((int)c->eval_segs.size());
+        c->eval_segs.push_back(S);
+        i = i_lo - 1;
+    }
+}
+
+static void enqueue_eval(vc_circuit *c, const Globals &G, cudaStream_t st)
+{
+    for (int step : c->eval_steps) {
+        if (step >= 0) launch_eval_seg(G, c->eval_segs[step], st);
+        else launch_eval_layer(G, c->L[-step - 1], -step - 1, st);
+    }
+}
+
 // Lay out every buffer and descriptor relative to `base` (0 for sizing).
 static size_t layout(vc_circuit *c, uintptr_t base)
 {
@@ -148,7 +225,7 @@ static size_t layout(vc_circuit *c, uintptr_t base)
     G.pts = A.take<u64>(npts + 1);
     G.scal = A.take<u64>(2 * d + 2);
     G.status = A.take<u32>(16);
-    G.invfact = nullptr;
+    G.invfact = A.take<u64>(64);
     c->d_result = A.take<u64>(8);
     c->d_tr = A.take<u64>(c->tr_len);
 
@@ -177,10 +254,11 @@ static size_t layout(vc_circuit *c, uintptr_t base)
         c->eq_prove.push_back({L.tz});
         c->eq_prove.push_back({L.trp});
         c->eq_prove.push_back({L.tr1});
-        L.P2 = A.take<u64>(S(i + 1));
-        L.P3 = A.take<u64>(S(i + 1));
-        L.B2 = L.has_add ? A.take<u64>(S(i + 1)) : nullptr;
-        L.B3 = L.has_add ? A.take<u64>(S(i + 1)) : nullptr;
+        const bool tabs = needs_tables(L.kind);
+        L.P2 = tabs ? A.take<u64>(S(i + 1)) : nullptr;
+        L.P3 = tabs ? A.take<u64>(S(i + 1)) : nullptr;
+        L.B2 = (tabs && L.has_add) ? A.take<u64>(S(i + 1)) : nullptr;
+        L.B3 = (tabs && L.has_add) ? A.take<u64>(S(i + 1)) : nullptr;
         if (L.kind == W_EXPLICIT) {
             L.type = A.take<unsigned char>(S(i));
             L.in1 = A.take<u32>(S(i));
@@ -233,66 +311,129 @@ static size_t layout(vc_circuit *c, uintptr_t base)
 
     // phase-2/3 table builds: one thread per entry of layer i+1
     c->build_off.assign(d + 1, 0);
-    for (u32 i = 0; i < d; i++) c->build_off[i + 1] = c->build_off[i] + (u32)((S(i + 1) + 255) / 256);
+    for (u32 i = 0; i < d; i++)
+        c->build_off[i + 1] = c->build_off[i] + (needs_tables(c->kind[i]) ? (u32)((S(i + 1) + 255) / 256) : 0);
     c->build_blocks = (int)c->build_off[d];
 
     // sum-check instances and their waves
-    c->waves.clear();
-    c->sc_items.clear();
+    c->scis.clear();
+    c->pwaves.clear();
+    c->gwaves.clear();
+    c->p_items.clear();
+    c->g_items.clear();
     c->rounds.clear();
     u64 part_total = 0;
-    struct PendingOut { size_t wave; u32 n; bool b; };
-    std::vector<PendingOut> outs;
     for (u32 i = 0; i < d; i++) {
+        const LayerDev &L = c->L[i];
         for (u32 ph = 1; ph <= 3; ph++) {
             const u32 n = (ph == 1) ? c->s[i] : c->s[i + 1];
             if (n == 0) continue;
             const u32 roff = (ph == 1) ? 0 : (ph == 2) ? c->s[i] : c->s[i] + c->s[i + 1];
-            const bool hasB = (ph != 1) && c->has_add[i];
-            const LayerDev &L = c->L[i];
-            const u64 *inP = (ph == 1) ? nullptr : (ph == 2) ? L.P2 : L.P3;
-            const u64 *inV = (ph == 1) ? L.V : L.Vn;
-            const u64 *inB = !hasB ? nullptr : (ph == 2) ? L.B2 : L.B3;
-            u32 flags = (ph == 1 ? WF_PEQ : 0) | (hasB ? WF_HASB : 0);
+            SciDev Sc{};
+            Sc.n = n;
+            Sc.layer = i;
+            Sc.chal_off = c->chal_off[i] + roff;
+            Sc.tr_off = c->tr_msg[i] + 3ull * roff;
+            if (ph == 1) Sc.kind = PK_PH1;
+            else if (L.kind == W_SQUARE) Sc.kind = (ph == 2) ? PK_GEN_SQ2 : PK_SQ3;
+            else if (L.kind == W_TREE) Sc.kind = (ph == 2) ? PK_GEN_TREE2 : PK_TREE3;
+            else Sc.kind = PK_GEN_TAB;
+            const u32 sci = (u32)c->scis.size();
+            const bool prod = Sc.kind < PK_GEN_FIRST;
+            if (prod) {
+                Sc.Lc = A.take<u64>(2 * n);
+                Sc.kap = A.take<u64>(n);
+                Sc.esum = A.take<u64>(n);
+            }
+            c->scis.push_back(Sc);
             u32 r0 = 0;
-            for (u32 w = 0;; w++) {
-                const u32 nr = std::min(SC_CHUNK_LOG, n - r0);
-                WaveDev W{};
-                W.sci = 0;
-                W.r0 = r0;
-                W.nr = nr;
-                W.nchunks = u32(1) << (n - r0 - nr);
-                const bool last = (r0 + nr == n);
-                W.flags = flags | (last ? WF_LAST : 0);
-                W.inP = inP;
-                W.inV = inV;
-                W.inB = inB;
-                if (!last) {
-                    W.outP = A.take<u64>(W.nchunks);
-                    W.outV = A.take<u64>(W.nchunks);
-                    W.outB = hasB ? A.take<u64>(W.nchunks) : nullptr;
+            if (prod) {
+                const u64 *in = (ph == 1) ? L.V : L.Vn;
+                for (u32 w = 0;; w++) {
+                    const u32 nr = std::min(PR_CHUNK_LOG, n - r0);
+                    ProdWave W{};
+                    W.sci = sci;
+                    W.r0 = r0;
+                    W.nr = nr;
+                    W.e = (nr >= (u32)PR_M) ? (u32)PR_M : 0;
+                    W.nchunks = u32(1) << (n - r0 - nr);
+                    const bool last = (r0 + nr == n);
+                    W.flags = last ? WF_LAST : 0;
+                    W.no = n - r0 - nr;
+                    W.ho = (W.no + 1) / 2;
+                    W.chal_off = Sc.chal_off + r0;
+                    W.in = in;
+                    W.out = last ? nullptr : A.take<u64>(W.nchunks);
+                    const u32 kb = W.e ? W.e - 1 : 0;
+                    W.wblk = A.take<u64>(((1u << W.e) - 1) + ((1u << (nr - kb)) - 1) + (1u << W.ho) + (1u << (W.no - W.ho)));
+                    W.part = part_total;
+                    for (u32 k = 0; k < nr; k++) {
+                        RoundRef R{};
+                        R.tr_pos = Sc.tr_off + 3ull * (r0 + k);
+                        R.part_pos = part_total + u64(k) * W.nchunks * 2;
+                        R.nchunks = W.nchunks;
+                        R.sci = sci;
+                        R.j = r0 + k;
+                        c->rounds.push_back(R);
+                    }
+                    part_total += u64(nr) * W.nchunks * 2;
+                    if (c->p_items.size() <= w) c->p_items.resize(w + 1);
+                    const u32 idx = (u32)c->pwaves.size();
+                    c->pwaves.push_back(W);
+                    for (u32 ch = 0; ch < W.nchunks; ch++) c->p_items[w].push_back({idx, ch});
+                    if (last) break;
+                    in = W.out;
+                    r0 += nr;
                 }
-                W.peq = L.tz;
-                W.part = part_total;
-                W.chal_off = c->chal_off[i] + roff + r0;
-                for (u32 k = 0; k < nr; k++) {
-                    RoundRef R{};
-                    R.tr_pos = c->tr_msg[i] + 3ull * (roff + r0 + k);
-                    R.part_pos = part_total + u64(k) * W.nchunks * 3;
-                    R.nchunks = W.nchunks;
-                    c->rounds.push_back(R);
+            } else {
+                const bool tab = Sc.kind == PK_GEN_TAB;
+                const bool tabB = tab && L.has_add;
+                const u64 *inP = tab ? (ph == 2 ? L.P2 : L.P3) : nullptr;
+                const u64 *inB = tabB ? (ph == 2 ? L.B2 : L.B3) : nullptr;
+                const u64 *inV = L.Vn;
+                const bool anyB = tabB || Sc.kind == PK_GEN_TREE2;
+                for (u32 w = 0;; w++) {
+                    const u32 nr = std::min(GN_CHUNK_LOG, n - r0);
+                    GenWave W{};
+                    W.sci = sci;
+                    W.r0 = r0;
+                    W.nr = nr;
+                    W.e = (nr >= (u32)GN_M) ? (u32)GN_M : 0;
+                    W.nchunks = u32(1) << (n - r0 - nr);
+                    const bool last = (r0 + nr == n);
+                    W.src = (w > 0 || tab) ? GS_NONE : (Sc.kind == PK_GEN_SQ2 ? GS_SQ2 : GS_TREE2);
+                    W.flags = (last ? WF_LAST : 0) | (((w > 0 && anyB) || tabB) ? WF_HASB : 0);
+                    W.layer = i;
+                    W.chal_off = Sc.chal_off + r0;
+                    W.inP = inP;
+                    W.inV = inV;
+                    W.inB = inB;
+                    if (!last) {
+                        W.outP = A.take<u64>(W.nchunks);
+                        W.outV = A.take<u64>(W.nchunks);
+                        W.outB = anyB ? A.take<u64>(W.nchunks) : nullptr;
+                    }
+                    W.part = part_total;
+                    for (u32 k = 0; k < nr; k++) {
+                        RoundRef R{};
+                        R.tr_pos = Sc.tr_off + 3ull * (r0 + k);
+                        R.part_pos = part_total + u64(k) * W.nchunks * 3;
+                        R.nchunks = W.nchunks;
+                        R.sci = sci;
+                        R.j = r0 + k;
+                        c->rounds.push_back(R);
+                    }
+                    part_total += u64(nr) * W.nchunks * 3;
+                    if (c->g_items.size() <= w) c->g_items.resize(w + 1);
+                    const u32 idx = (u32)c->gwaves.size();
+                    c->gwaves.push_back(W);
+                    for (u32 ch = 0; ch < W.nchunks; ch++) c->g_items[w].push_back({idx, ch});
+                    if (last) break;
+                    inP = W.outP;
+                    inV = W.outV;
+                    inB = W.outB;
+                    r0 += nr;
                 }
-                part_total += u64(nr) * W.nchunks * 3;
-                if (c->sc_items.size() <= w) c->sc_items.resize(w + 1);
-                const u32 idx = (u32)c->waves.size();
-                c->waves.push_back(W);
-                for (u32 ch = 0; ch < W.nchunks; ch++) c->sc_items[w].push_back({idx, ch});
-                if (last) break;
-                inP = W.outP;
-                inV = W.outV;
-                inB = W.outB;
-                flags &= ~WF_PEQ;
-                r0 += nr;
             }
         }
     }
@@ -307,6 +448,13 @@ static size_t layout(vc_circuit *c, uintptr_t base)
     c->Vd.mle_blocks = (u32)mb;
     c->Vd.mle_part = A.take<u64>(mb);
     c->Vd.wire = A.take<u64>(2 * d + 2);
+    c->Vd.claims = A.take<u64>(d + 1);
+    c->round_layer.clear();
+    for (u32 i = 0; i < d; i++)
+        for (u32 j = 0; j < c->s[i] + 2 * c->s[i + 1]; j++) c->round_layer.push_back((i << 8) | j);
+    c->d_round_layer = A.take<u32>(c->round_layer.size() + 1);
+    c->Vd.round_layer = c->d_round_layer;
+    c->Vd.nrounds = (u32)c->round_layer.size();
     c->Vd.result = c->d_result;
     c->Vd.d = d;
     c->Vd.tr_len = c->tr_len;
@@ -319,9 +467,13 @@ static size_t layout(vc_circuit *c, uintptr_t base)
     c->d_line_items.assign(c->line_items.size(), nullptr);
     for (size_t w = 0; w < c->line_items.size(); w++) c->d_line_items[w] = A.take<Item>(c->line_items[w].size());
     c->d_build_off = A.take<u32>(d + 1);
-    c->d_waves = A.take<WaveDev>(c->waves.size());
-    c->d_sc_items.assign(c->sc_items.size(), nullptr);
-    for (size_t w = 0; w < c->sc_items.size(); w++) c->d_sc_items[w] = A.take<Item>(c->sc_items[w].size());
+    c->d_scis = A.take<SciDev>(c->scis.size() + 1);
+    c->d_pwaves = A.take<ProdWave>(c->pwaves.size() + 1);
+    c->d_gwaves = A.take<GenWave>(c->gwaves.size() + 1);
+    c->d_p_items.assign(c->p_items.size(), nullptr);
+    for (size_t w = 0; w < c->p_items.size(); w++) c->d_p_items[w] = A.take<Item>(c->p_items[w].size());
+    c->d_g_items.assign(c->g_items.size(), nullptr);
+    for (size_t w = 0; w < c->g_items.size(); w++) c->d_g_items[w] = A.take<Item>(c->g_items[w].size());
     c->d_rounds = A.take<RoundRef>(c->rounds.size() + 1);
     c->d_explicit_layers = A.take<u32>(c->explicit_layers.size() + 1);
     G.layers = c->d_layers;
@@ -411,6 +563,7 @@ extern "C" vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, 
     c->zd_off = zo;
     c->nchal = ch;
     c->tr_len = tp;
+    plan_eval(c);
 
     DevGuard guard(device);
     const size_t bytes = layout(c, 0);
@@ -426,10 +579,18 @@ extern "C" vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, 
     for (size_t w = 0; e == cudaSuccess && w < c->line_items.size(); w++)
         e = upload(c->d_line_items[w], c->line_items[w]);
     if (e == cudaSuccess) e = upload(c->d_build_off, c->build_off);
-    if (e == cudaSuccess) e = upload(c->d_waves, c->waves);
-    for (size_t w = 0; e == cudaSuccess && w < c->sc_items.size(); w++) e = upload(c->d_sc_items[w], c->sc_items[w]);
+    if (e == cudaSuccess) e = upload(c->d_scis, c->scis);
+    if (e == cudaSuccess) e = upload(c->d_pwaves, c->pwaves);
+    if (e == cudaSuccess) e = upload(c->d_gwaves, c->gwaves);
+    for (size_t w = 0; e == cudaSuccess && w < c->p_items.size(); w++) e = upload(c->d_p_items[w], c->p_items[w]);
+    for (size_t w = 0; e == cudaSuccess && w < c->g_items.size(); w++) e = upload(c->d_g_items[w], c->g_items[w]);
     if (e == cudaSuccess) e = upload(c->d_rounds, c->rounds);
     if (e == cudaSuccess) e = upload(c->d_explicit_layers, c->explicit_layers);
+    if (e == cudaSuccess) e = upload(c->d_round_layer, c->round_layer);
+    if (e == cudaSuccess) {
+        launch_init_invfact(c->G.invfact, 0);
+        e = cudaDeviceSynchronize();
+    }
     for (u32 i = 0; e == cudaSuccess && i < d; i++) {
         if (c->kind[i] != W_EXPLICIT) continue;
         const LayerDev &L = c->L[i];
@@ -515,20 +676,25 @@ static cudaError_t enqueue_prove(vc_circuit *c, u64 seed, u64 *tr, cudaStream_t 
     mark(VC_STAGE_EQ);
     launch_eqtabs(c->d_eq_prove, (int)c->eq_prove.size(), st);
     mark(VC_STAGE_EVAL);
-    for (int i = (int)c->d - 1; i >= 0; i--) launch_eval_layer(G, c->L[i], i, st);
+    enqueue_eval(c, G, st);
     mark(VC_STAGE_LINE);
     for (size_t w = 0; w < c->line_items.size(); w++)
         launch_line_wave(G, c->d_lw, c->d_line_items[w], (int)c->line_items[w].size(), st);
     mark(VC_STAGE_BUILD);
+    launch_prep_prod(G, c->d_scis, c->d_pwaves, (int)c->pwaves.size(), st);
     launch_build23(G, c->d_build_off, (int)c->d, c->build_blocks, st);
     mark(VC_STAGE_SC0);
-    for (size_t w = 0; w < c->sc_items.size(); w++) {
+    const size_t nw = std::max(c->p_items.size(), c->g_items.size());
+    for (size_t w = 0; w < nw; w++) {
         if (w == 1) mark(VC_STAGE_SC1);
-        launch_sc_wave(G, c->d_waves, c->d_sc_items[w], (int)c->sc_items[w].size(), c->partials, st);
+        if (w < c->p_items.size())
+            launch_sc_prod(G, c->d_pwaves, c->d_p_items[w], (int)c->p_items[w].size(), c->partials, st);
+        if (w < c->g_items.size())
+            launch_sc_gen(G, c->d_gwaves, c->d_g_items[w], (int)c->g_items[w].size(), c->partials, st);
     }
-    if (c->sc_items.size() < 2) mark(VC_STAGE_SC1);
+    if (nw < 2) mark(VC_STAGE_SC1);
     mark(VC_STAGE_FINAL);
-    launch_final(G, c->d_rounds, (int)c->rounds.size(), c->partials, c->V[0], u64(1) << c->s[0], st);
+    launch_final(G, c->d_scis, c->d_rounds, (int)c->rounds.size(), c->partials, c->V[0], u64(1) << c->s[0], st);
     mark(VC_NUM_STAGES);
     return cudaGetLastError();
 }
@@ -574,7 +740,7 @@ extern "C" vc_status vc_evaluate(vc_circuit *c, const uint64_t *inputs, uint64_t
                                     ki ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return VC_ECUDA;
     launch_check_canonical(c->V[c->d], nin, c->G.status, st);
-    for (int i = (int)c->d - 1; i >= 0; i--) launch_eval_layer(c->G, c->L[i], i, st);
+    enqueue_eval(c, c->G, st);
     e = cudaMemcpyAsync(outputs, c->V[0], (u64(1) << c->s[0]) * sizeof(u64),
                         ko ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -655,10 +821,12 @@ extern "C" vc_status vc_circuit_get_info(const vc_circuit *c, vc_circuit_info *i
     I.gates = gates;
     I.device_bytes = c->arena_bytes;
     // setup, eq tables, d evaluation layers, line waves, build, sum-check waves, final
-    I.prove_launches = (uint32_t)(3 + c->d + c->line_items.size() + (c->build_blocks > 0 ? 1 : 0) +
-                                  c->sc_items.size() + (c->eq_prove.empty() ? -1 : 0));
+    I.prove_launches = (uint32_t)(3 + c->eval_steps.size() + c->line_items.size() + (c->build_blocks > 0 ? 1 : 0) +
+                                  (c->pwaves.empty() ? 0 : 1) + c->p_items.size() + c->g_items.size() +
+                                  (c->eq_prove.empty() ? -1 : 0));
     I.verify_launches = (uint32_t)(3 + (c->explicit_layers.empty() ? 0 : 1) + 1);
-    I.sc0_ctas = c->sc_items.empty() ? 0 : (uint32_t)c->sc_items[0].size();
+    I.sc0_ctas = (uint32_t)((c->p_items.empty() ? 0 : c->p_items[0].size()) +
+                            (c->g_items.empty() ? 0 : c->g_items[0].size()));
     *info = I;
     return VC_OK;
 }
@@ -708,7 +876,7 @@ extern "C" vc_status vc_field_mul(const uint64_t *a, const uint64_t *b, uint64_t
 
 extern "C" vc_status vc_field_mul_rate(int device, int variant, uint64_t iters, double *rate)
 {
-    if (!rate || iters == 0 || (variant != 0 && variant != 1)) return VC_EINVAL;
+    if (!rate || iters == 0 || variant < 0 || variant > 2) return VC_EINVAL;
     DevGuard guard(device);
     cudaDeviceProp prop{};
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return VC_ECUDA;
@@ -719,7 +887,9 @@ extern "C" vc_status vc_field_mul_rate(int device, int variant, uint64_t iters, 
     cudaError_t e = cudaGetLastError();
     cudaFree(sink);
     if (e != cudaSuccess || ms <= 0.f) return VC_ECUDA;
-    *rate = double(blocks) * threads * 8.0 * double(iters) / (ms * 1e-3);
+    // variants 0, 1: 8 chains x one product per step; variant 2: 4 chains x 3 products per step
+    const double per_step = (variant == 2) ? 12.0 : 8.0;
+    *rate = double(blocks) * threads * per_step * double(iters) / (ms * 1e-3);
     return VC_OK;
 }
 
