@@ -137,24 +137,31 @@ vc_status vc_circuit_sync(vc_circuit *c, void *stream);
 vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t seed,
                     const uint64_t *transcript, int *accept, void *stream);
 
-/* Launch sequence of a proof, for timing individual stages: a proof is the
- * stages below in this order (some may be empty for small circuits). */
+/* Stages of a proof, for timing them.  A proof runs on the caller's stream
+ * and two helper streams owned by the circuit (forked from and joined back to
+ * the caller's stream): after evaluation, the line reductions, the
+ * product-weighted sum-check waves and the general sum-check waves run
+ * concurrently. */
 typedef enum {
-    VC_STAGE_SETUP = 0,  /* coins, layer points, eq(z_i, r_P)                    */
-    VC_STAGE_EQ = 1,     /* split eq tables                                       */
-    VC_STAGE_EVAL = 2,   /* layer-by-layer evaluation                             */
-    VC_STAGE_LINE = 3,   /* line-reduction polynomials q_i                        */
-    VC_STAGE_BUILD = 4,  /* phase-2/3 tables from the wiring                      */
-    VC_STAGE_SC0 = 5,    /* first sum-check wave (the bulk of the arithmetic)     */
-    VC_STAGE_SC1 = 6,    /* remaining sum-check waves                             */
-    VC_STAGE_FINAL = 7,  /* per-round reductions into the transcript              */
-    VC_NUM_STAGES = 8
+    VC_STAGE_PROOF = 0,   /* the whole proof                          (caller's stream) */
+    VC_STAGE_SETUP = 1,   /* coins, layer points, eq(z_i, r_P)        (caller's stream) */
+    VC_STAGE_TABLES = 2,  /* split eq tables, product weights         (helper stream A) */
+    VC_STAGE_EVAL = 3,    /* layer-by-layer evaluation                (caller's stream) */
+    VC_STAGE_LINE = 4,    /* line reductions q_i, wiring tables       (caller's stream) */
+    VC_STAGE_PROD0 = 5,   /* first product-weighted sum-check wave    (helper stream A) */
+    VC_STAGE_PRODN = 6,   /* later product-weighted waves             (helper stream A) */
+    VC_STAGE_GEN0 = 7,    /* first general sum-check wave             (helper stream B) */
+    VC_STAGE_GENN = 8,    /* later general waves                      (helper stream B) */
+    VC_STAGE_FINAL = 9,   /* per-round reductions into the transcript (caller's stream) */
+    VC_NUM_STAGES = 10
 } vc_stage;
 
-/* Record CUDA events at stage boundaries of every later vc_prove on this
- * circuit: events[k] (a cudaEvent_t) just before stage k, events[VC_NUM_STAGES]
- * after the last.  `events` must hold VC_NUM_STAGES + 1 events created on the
- * circuit's device, owned by the caller; NULL turns recording off. */
+/* Record CUDA events around the stages of every later vc_prove on this
+ * circuit: events[2k] when stage k starts and events[2k+1] when it ends, each
+ * on the stream that runs the stage (a stage with no work records both
+ * back to back).  `events` must hold 2 * VC_NUM_STAGES events (cudaEvent_t)
+ * created on the circuit's device and owned by the caller; NULL turns
+ * recording off. */
 vc_status vc_circuit_set_stage_events(vc_circuit *c, void *const *events);
 
 /* Shape facts of a circuit. */

@@ -241,13 +241,16 @@ void launch_check_canonical(const u64 *x, u64 n, u32 *status, cudaStream_t st)
 #define LN_SP 32  // coefficient stride in shared memory (degree <= 31)
 
 // One coefficient of the fold of polynomials A (lower) and B (upper) with
-// a + b t:  out_c = A_c + a (B_c - A_c) + b (B_{c-1} - A_{c-1}).
+// a + b t:  out_c = A_c + a (B_c - A_c) + b (B_{c-1} - A_{c-1}).  Coefficients
+// are in W (lazy); the two products accumulate exactly in 128 bits.
 __device__ __forceinline__ u64 poly_fold_coef(const u64 *A, const u64 *B, u32 deg, u32 c, u64 a, u64 b)
 {
-    u64 dc = (c <= deg) ? f_sub(B[c], A[c]) : 0;
-    u64 dm = (c >= 1) ? f_sub(B[c - 1], A[c - 1]) : 0;
-    u64 ac = (c <= deg) ? A[c] : 0;
-    return f_add(ac, f_add(f_mul(a, dc), f_mul(b, dm)));
+    acc128 acc;
+    acc.lo = (c <= deg) ? A[c] : 0;
+    acc.hi = 0;
+    if (c <= deg) mac(acc, a, B[c] + (2 * FP_P) - A[c]);
+    if (c >= 1) mac(acc, b, B[c - 1] + (2 * FP_P) - A[c - 1]);
+    return acc_red(acc);
 }
 
 extern __shared__ u64 ln_dyn[];
@@ -366,10 +369,10 @@ __global__ void __launch_bounds__(LN_NT) k_line_wave(Globals G, const LineWaveDe
         // q(t) for t = 0..n by Horner; q(0) = V~_{i+1}(r1) feeds phase 3.
         for (u32 t = tid; t <= W.n; t += LN_NT) {
             u64 acc = cur[deg];
-            for (int c = (int)deg - 1; c >= 0; c--) acc = f_add(f_mul(acc, (u64)t), cur[c]);
-            G.tr[W.tr_q + t] = acc;
+            for (int c = (int)deg - 1; c >= 0; c--) acc = wred(wmul(acc, (u64)t) + cur[c]);
+            G.tr[W.tr_q + t] = wcanon(acc);
         }
-        if (tid == 0) G.scal[SCAL_V1(W.layer)] = cur[0];
+        if (tid == 0) G.scal[SCAL_V1(W.layer)] = wcanon(cur[0]);
     }
 }
 

@@ -50,6 +50,26 @@ __device__ __forceinline__ u64 warp_sum16(u64 (&v)[16])
     return wred(r);
 }
 
+// Sum over the warp of 32 values per lane: afterwards lane l holds the total
+// of value index l.  Inputs in W.
+__device__ __forceinline__ u64 warp_sum32(u64 (&v)[32])
+{
+    const u32 lane = threadIdx.x & 31;
+#pragma unroll
+    for (int step = 0; step < 5; step++) {
+        const int o = 16 >> step, half = 16 >> step;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; i++) {
+            const u64 send = up ? v[i] : v[i + half];
+            const u64 keep = up ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            if (step & 1) v[i] = wred(v[i]);
+        }
+    }
+    return wred(v[0]);
+}
+
 // Warp-wide sum of one W value per lane -> W.
 __device__ __forceinline__ u64 warp_wsum(u64 x)
 {
@@ -178,6 +198,54 @@ void launch_prep_prod(const Globals &G, const SciDev *scis, const ProdWave *wave
 
 #define PR_NT 256
 
+// Rounds OFF.. of a product-weighted chunk across threads.  Thread t holds
+// level value t (t < na); a round pairs values 2y and 2y+1, which sit in the
+// threads t = y 2^(kk+1) and t + 2^kk, and the first of them keeps the folded
+// value, so rounds stay inside a warp for kk < 5 (shuffles) and continue in
+// warp 0 after one exchange through shared memory.  Each active thread adds
+// E_k(y) u0 and E_k(y) u1 to hv[2k], hv[2k+1].
+template <int OFF>
+__device__ __forceinline__ void prod_cross(u64 (&hv)[32], u64 uv, u32 tid, u32 na, u32 nr, const u64 *s_E,
+                                           u32 eoff0, const u32 *s_r0, const u32 *s_r1, u64 *s_lvl)
+{
+    const u32 lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int kk = 0; kk < 5; kk++) {
+        const u32 k = OFF + kk;
+        if (k < nr) {  // uniform
+            const u64 u1 = __shfl_down_sync(0xffffffffu, uv, 1u << kk);
+            if ((tid & ((2u << kk) - 1)) == 0 && tid < na) {
+                const u32 y = tid >> (kk + 1);
+                const u64 w = s_E[eoff0 - (1u << (nr - k)) + y];
+                hv[2 * (OFF + kk)] = wmul(w, uv);
+                hv[2 * (OFF + kk) + 1] = wmul(w, u1);
+                uv = wfold(uv, u1, s_r0[k], s_r1[k]);
+            }
+        }
+    }
+    if (lane == 0) s_lvl[warp] = uv;
+    __syncthreads();
+    if (OFF + 5 < nr && warp == 0) {
+        uv = (lane < PR_NT / 32) ? s_lvl[lane] : 0;
+#pragma unroll
+        for (int kk = 5; kk < 8; kk++) {
+            const u32 k = OFF + kk;
+            if (k < nr) {
+                const u64 u1 = __shfl_down_sync(0xffffffffu, uv, 1u << (kk - 5));
+                const u32 t = lane << 5;  // the thread index this lane stands for
+                if ((t & ((2u << kk) - 1)) == 0 && t < na) {
+                    const u32 y = t >> (kk + 1);
+                    const u64 w = s_E[eoff0 - (1u << (nr - k)) + y];
+                    hv[2 * (OFF + kk)] = wmul(w, uv);
+                    hv[2 * (OFF + kk) + 1] = wmul(w, u1);
+                    uv = wfold(uv, u1, s_r0[k], s_r1[k]);
+                }
+            }
+        }
+        if (lane == 0) s_lvl[0] = uv;
+    }
+}
+
 __global__ void __launch_bounds__(PR_NT, 2) k_sc_prod(Globals G, const ProdWave *waves, const Item *items,
                                                       u64 *partials)
 {
@@ -185,9 +253,8 @@ __global__ void __launch_bounds__(PR_NT, 2) k_sc_prod(Globals G, const ProdWave 
     __shared__ u32 s_r0[32], s_r1[32];
     __shared__ u64 s_Q[1 << M];
     __shared__ u64 s_E[512];
-    __shared__ u64 s_lvl[PR_NT], s_x[PR_NT / 2], s_y[PR_NT / 2];
-    __shared__ u64 s_c[2][PR_NT];
-    __shared__ u64 s_w[PR_NT / 32][16];
+    __shared__ u64 s_lvl[PR_NT / 32];
+    __shared__ u64 s_w[PR_NT / 32][32];
     __shared__ u64 s_echunk;
 
     const Item it = items[blockIdx.x];
@@ -210,9 +277,11 @@ __global__ void __launch_bounds__(PR_NT, 2) k_sc_prod(Globals G, const ProdWave 
     }
     __syncthreads();
 
-    u64 hv[16];
+    // hv[2k + t]: this thread's share of h_k(t), k < nr (at most 13 rounds)
+    u64 hv[32];
 #pragma unroll
-    for (int i = 0; i < 16; i++) hv[i] = 0;
+    for (int i = 0; i < 32; i++) hv[i] = 0;
+    u64 uv = 0;  // the thread's level value after its in-register rounds
     if (e == M) {
         if (tid < na) {
             u64 u[1 << M];
@@ -242,53 +311,29 @@ __global__ void __launch_bounds__(PR_NT, 2) k_sc_prod(Globals G, const ProdWave 
                 hv[2 * k] = wmul(T, acc_red(a0));
                 hv[2 * k + 1] = wmul(T, acc_red(a1));
             }
-            s_lvl[tid] = u[0];
+            uv = u[0];
         }
-    } else if (tid < na) {
-        s_lvl[tid] = W.in[base + tid];
+        prod_cross<M>(hv, uv, tid, na, nr, s_E, (1u << (nr - kb)), s_r0, s_r1, s_lvl);
+    } else {
+        if (tid < na) uv = W.in[base + tid];
+        prod_cross<0>(hv, uv, tid, na, nr, s_E, (1u << (nr - kb)), s_r0, s_r1, s_lvl);
     }
-    if (e == M) {
-        const u64 s = warp_sum16(hv);
-        if ((lane & 1) == 0 && (lane >> 1) < 2 * M) s_w[warp][lane >> 1] = s;
-    }
-    __syncthreads();
-
-    // rounds e..nr-1 across the CTA's na level values
-    u64 *cur = s_lvl;
-    u32 m = na;
-    const u32 eoff0 = (1u << (nr - kb));
-    for (u32 k = e; k < nr; k++) {
-        const u32 half = m >> 1;
-        const u32 seg = na - (na >> (k - e));
-        u64 *nxt = ((k - e) & 1) ? s_y : s_x;
-        if (tid < half) {
-            const u64 w = s_E[eoff0 - (1u << (nr - k)) + tid];  // E_k(tid)
-            const u64 u0 = cur[2 * tid], u1 = cur[2 * tid + 1];
-            s_c[0][seg + tid] = wmul(w, u0);
-            s_c[1][seg + tid] = wmul(w, u1);
-            nxt[tid] = wfold(u0, u1, s_r0[k], s_r1[k]);
-        }
-        __syncthreads();
-        cur = nxt;
-        m = half;
-    }
+    __syncthreads();  // s_lvl[0] written by prod_cross
 
     // per-round sums of this chunk, times the chunk's outer weight
-    const u64 ech = s_echunk;
-    for (u32 idx = warp; idx < 2 * nr; idx += PR_NT / 32) {
-        const u32 k = idx >> 1, t = idx & 1;
-        u64 s = 0;
-        if (k < e) {
-            if (lane < PR_NT / 32) s = s_w[lane][idx];
-        } else {
-            const u32 seg = na - (na >> (k - e));
-            const u32 len = na >> (k - e + 1);
-            for (u32 q = lane; q < len; q += 32) s = wred(s + s_c[t][seg + q]);
-        }
-        s = warp_wsum(s);
-        if (lane == 0) partials[W.part + ((u64)k * W.nchunks + chunk) * 2 + t] = wmul(s, ech);
+    {
+        const u64 s = warp_sum32(hv);
+        if (lane < 2 * nr) s_w[warp][lane] = s;
     }
-    if (!(W.flags & WF_LAST) && tid == 0) W.out[chunk] = cur[0];
+    __syncthreads();
+    if (tid < 2 * nr) {
+        // eight W values can exceed 2^64: add them in two groups of four
+        const u64 s = wred(wred(s_w[0][tid] + s_w[1][tid] + s_w[2][tid] + s_w[3][tid]) +
+                           wred(s_w[4][tid] + s_w[5][tid] + s_w[6][tid] + s_w[7][tid]));
+        const u32 k = tid >> 1, t = tid & 1;
+        partials[W.part + ((u64)k * W.nchunks + chunk) * 2 + t] = wmul(s, s_echunk);
+    }
+    if (!(W.flags & WF_LAST) && tid == 0) W.out[chunk] = s_lvl[0];
 }
 
 void launch_sc_prod(const Globals &G, const ProdWave *waves, const Item *items, int nitems, u64 *partials,
@@ -301,7 +346,7 @@ void launch_sc_prod(const Globals &G, const ProdWave *waves, const Item *items, 
 // GEN waves: tables P, V, B folded every round; message values at t = 0, 1, 2.
 // --------------------------------------------------------------------------------
 
-#define GN_NT 256
+#define GN_NT 128
 
 // P and B of the first wave for the on-the-fly kinds, for the run of 8
 // entries at x0 whose V values are v[].
@@ -315,7 +360,7 @@ __device__ __forceinline__ void gen_source(const Globals &G, const GenWave &W, u
             p[q] = wmul(eq_at(L.trp, x0 + q), v[q]);
             b[q] = 0;
         }
-    } else if (W.src == GS_TREE2) {
+    } else {  // GS_TREE2
 #pragma unroll
         for (int q = 0; q < 8; q += 2) {
             const u64 w = eq_at(L.trp, (x0 + q) >> 1);
@@ -324,37 +369,81 @@ __device__ __forceinline__ void gen_source(const Globals &G, const GenWave &W, u
             p[q + 1] = 0;
             b[q + 1] = 0;
         }
-    } else {
-        const ulonglong2 *sp = reinterpret_cast<const ulonglong2 *>(W.inP + x0);
+    }
+}
+
+// One general pair: message contributions at t = 0, 1, 2 and the folds.
+__device__ __forceinline__ void gen_pair(u64 p0, u64 p1, u64 v0, u64 v1, u64 b0, u64 b1, u32 rr0, u32 rr1,
+                                         u64 &c0, u64 &c1, u64 &c2, u64 &pn, u64 &vn, u64 &bn)
+{
+    c0 = wred(wmul(p0, v0) + b0);
+    c1 = wred(wmul(p1, v1) + b1);
+    c2 = wred(wmul(wext2(p1, p0), wext2(v1, v0)) + wext2(b1, b0));
+    pn = wfold(p0, p1, rr0, rr1);
+    vn = wfold(v0, v1, rr0, rr1);
+    bn = wfold(b0, b1, rr0, rr1);
+}
+
+// Rounds OFF.. of a general chunk across threads (same placement as
+// prod_cross: the first thread of each pair keeps the folded values).
+template <int OFF>
+__device__ __forceinline__ void gen_cross(u64 (&hv)[32], u64 &p, u64 &v, u64 &b, u32 tid, u32 na, u32 nr,
+                                          const u32 *s_r0, const u32 *s_r1, u64 (*s_lvl)[GN_NT / 32])
+{
+    const u32 lane = tid & 31, warp = tid >> 5;
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const ulonglong2 t = sp[q];
-            p[2 * q] = t.x;
-            p[2 * q + 1] = t.y;
+    for (int kk = 0; kk < 5; kk++) {
+        const u32 k = OFF + kk;
+        if (k < nr) {
+            const u32 d = 1u << kk;
+            const u64 p1 = __shfl_down_sync(0xffffffffu, p, d);
+            const u64 v1 = __shfl_down_sync(0xffffffffu, v, d);
+            const u64 b1 = __shfl_down_sync(0xffffffffu, b, d);
+            if ((tid & ((2u << kk) - 1)) == 0 && tid < na)
+                gen_pair(p, p1, v, v1, b, b1, s_r0[k], s_r1[k], hv[3 * (OFF + kk)], hv[3 * (OFF + kk) + 1],
+                         hv[3 * (OFF + kk) + 2], p, v, b);
         }
-        if (W.flags & WF_HASB) {
-            const ulonglong2 *sb = reinterpret_cast<const ulonglong2 *>(W.inB + x0);
+    }
+    if (lane == 0) {
+        s_lvl[0][warp] = p;
+        s_lvl[1][warp] = v;
+        s_lvl[2][warp] = b;
+    }
+    __syncthreads();
+    if (OFF + 5 < nr && warp == 0) {
+        const bool have = lane < GN_NT / 32;
+        p = have ? s_lvl[0][lane] : 0;
+        v = have ? s_lvl[1][lane] : 0;
+        b = have ? s_lvl[2][lane] : 0;
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const ulonglong2 t = sb[q];
-                b[2 * q] = t.x;
-                b[2 * q + 1] = t.y;
+        for (int kk = 5; kk < 7; kk++) {
+            const u32 k = OFF + kk;
+            if (k < nr) {
+                const u32 d = 1u << (kk - 5);
+                const u64 p1 = __shfl_down_sync(0xffffffffu, p, d);
+                const u64 v1 = __shfl_down_sync(0xffffffffu, v, d);
+                const u64 b1 = __shfl_down_sync(0xffffffffu, b, d);
+                const u32 t = lane << 5;
+                if ((t & ((2u << kk) - 1)) == 0 && t < na)
+                    gen_pair(p, p1, v, v1, b, b1, s_r0[k], s_r1[k], hv[3 * (OFF + kk)], hv[3 * (OFF + kk) + 1],
+                             hv[3 * (OFF + kk) + 2], p, v, b);
             }
-        } else {
-#pragma unroll
-            for (int q = 0; q < 8; q++) b[q] = 0;
+        }
+        if (lane == 0) {
+            s_lvl[0][0] = p;
+            s_lvl[1][0] = v;
+            s_lvl[2][0] = b;
         }
     }
 }
 
-__global__ void __launch_bounds__(GN_NT, 2) k_sc_gen(Globals G, const GenWave *waves, const Item *items,
+__global__ void __launch_bounds__(GN_NT, 4) k_sc_gen(Globals G, const GenWave *waves, const Item *items,
                                                      u64 *partials)
 {
     constexpr int M = GN_M;
     __shared__ u32 s_r0[32], s_r1[32];
-    __shared__ u64 s_lvl[3][GN_NT], s_x[3][GN_NT / 2], s_y[3][GN_NT / 2];
-    __shared__ u64 s_c[3][GN_NT];
-    __shared__ u64 s_w[GN_NT / 32][16];
+    __shared__ u64 s_lvl[3][GN_NT / 32];
+    __shared__ u64 s_w[GN_NT / 32][32];
 
     const Item it = items[blockIdx.x];
     const GenWave &W = waves[it.wave];
@@ -366,9 +455,10 @@ __global__ void __launch_bounds__(GN_NT, 2) k_sc_gen(Globals G, const GenWave *w
     if (tid < nr) limbs31(G.chal[W.chal_off + tid], s_r0[tid], s_r1[tid]);
     __syncthreads();
 
-    u64 hv[16];
+    u64 hv[32];
 #pragma unroll
-    for (int i = 0; i < 16; i++) hv[i] = 0;
+    for (int i = 0; i < 32; i++) hv[i] = 0;
+    u64 pv = 0, vv = 0, bv = 0;
     if (e == M) {
         if (tid < na) {
             u64 p[8], v[8], b[8];
@@ -428,74 +518,45 @@ __global__ void __launch_bounds__(GN_NT, 2) k_sc_gen(Globals G, const GenWave *w
                 hv[3 * k + 1] = acc_red(a1);
                 hv[3 * k + 2] = acc_red(a2);
             }
-            s_lvl[0][tid] = p[0];
-            s_lvl[1][tid] = v[0];
-            s_lvl[2][tid] = b[0];
+            pv = p[0];
+            vv = v[0];
+            bv = b[0];
         }
-    } else if (tid < na) {
-        const u64 x = base + tid;
-        s_lvl[1][tid] = W.inV[x];
-        if (W.src == GS_SQ2) {
-            s_lvl[0][tid] = wmul(eq_at(G.layers[W.layer].trp, x), s_lvl[1][tid]);
-            s_lvl[2][tid] = 0;
-        } else if (W.src == GS_TREE2) {
-            const u64 w = (x & 1) ? 0 : eq_at(G.layers[W.layer].trp, x >> 1);
-            s_lvl[0][tid] = w;
-            s_lvl[2][tid] = (x & 1) ? 0 : wmul(w, W.inV[x + 1]);
-        } else {
-            s_lvl[0][tid] = W.inP[x];
-            s_lvl[2][tid] = hasB ? W.inB[x] : 0;
+        gen_cross<M>(hv, pv, vv, bv, tid, na, nr, s_r0, s_r1, s_lvl);
+    } else {
+        if (tid < na) {
+            const u64 x = base + tid;
+            vv = W.inV[x];
+            if (W.src == GS_SQ2) {
+                pv = wmul(eq_at(G.layers[W.layer].trp, x), vv);
+                bv = 0;
+            } else if (W.src == GS_TREE2) {
+                const u64 w = (x & 1) ? 0 : eq_at(G.layers[W.layer].trp, x >> 1);
+                pv = w;
+                bv = (x & 1) ? 0 : wmul(w, W.inV[x + 1]);
+            } else {
+                pv = W.inP[x];
+                bv = hasB ? W.inB[x] : 0;
+            }
         }
-    }
-    if (e == M) {
-        const u64 s = warp_sum16(hv);
-        if ((lane & 1) == 0 && (lane >> 1) < 3 * M) s_w[warp][lane >> 1] = s;
+        gen_cross<0>(hv, pv, vv, bv, tid, na, nr, s_r0, s_r1, s_lvl);
     }
     __syncthreads();
 
-    u64 *cP = s_lvl[0], *cV = s_lvl[1], *cB = s_lvl[2];
-    u32 m = na;
-    for (u32 k = e; k < nr; k++) {
-        const u32 half = m >> 1;
-        const u32 seg = na - (na >> (k - e));
-        const bool odd = ((k - e) & 1) != 0;
-        u64 *nP = odd ? s_y[0] : s_x[0], *nV = odd ? s_y[1] : s_x[1], *nB = odd ? s_y[2] : s_x[2];
-        if (tid < half) {
-            const u64 p0 = cP[2 * tid], p1 = cP[2 * tid + 1];
-            const u64 v0 = cV[2 * tid], v1 = cV[2 * tid + 1];
-            const u64 b0 = cB[2 * tid], b1 = cB[2 * tid + 1];
-            s_c[0][seg + tid] = wred(wmul(p0, v0) + b0);
-            s_c[1][seg + tid] = wred(wmul(p1, v1) + b1);
-            s_c[2][seg + tid] = wred(wmul(wext2(p1, p0), wext2(v1, v0)) + wext2(b1, b0));
-            const u32 rr0 = s_r0[k], rr1 = s_r1[k];
-            nP[tid] = wfold(p0, p1, rr0, rr1);
-            nV[tid] = wfold(v0, v1, rr0, rr1);
-            nB[tid] = wfold(b0, b1, rr0, rr1);
-        }
-        __syncthreads();
-        cP = nP;
-        cV = nV;
-        cB = nB;
-        m = half;
+    {
+        const u64 s = warp_sum32(hv);
+        if (lane < 3 * nr) s_w[warp][lane] = s;
     }
-
-    for (u32 idx = warp; idx < 3 * nr; idx += GN_NT / 32) {
-        const u32 k = idx / 3, t = idx % 3;
-        u64 s = 0;
-        if (k < e) {
-            if (lane < GN_NT / 32) s = s_w[lane][idx];
-        } else {
-            const u32 seg = na - (na >> (k - e));
-            const u32 len = na >> (k - e + 1);
-            for (u32 q = lane; q < len; q += 32) s = wred(s + s_c[t][seg + q]);
-        }
-        s = warp_wsum(s);
-        if (lane == 0) partials[W.part + ((u64)k * W.nchunks + chunk) * 3 + t] = s;
+    __syncthreads();
+    if (tid < 3 * nr) {
+        const u64 s = wred(s_w[0][tid] + s_w[1][tid] + s_w[2][tid] + s_w[3][tid]);
+        const u32 k = tid / 3, t = tid % 3;
+        partials[W.part + ((u64)k * W.nchunks + chunk) * 3 + t] = s;
     }
     if (!(W.flags & WF_LAST) && tid == 0) {
-        W.outP[chunk] = cP[0];
-        W.outV[chunk] = cV[0];
-        if (W.outB) W.outB[chunk] = cB[0];
+        W.outP[chunk] = s_lvl[0][0];
+        W.outV[chunk] = s_lvl[1][0];
+        if (W.outB) W.outB[chunk] = s_lvl[2][0];
     }
 }
 

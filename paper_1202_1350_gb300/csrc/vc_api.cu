@@ -20,7 +20,7 @@
 namespace {
 
 constexpr u32 PR_CHUNK_LOG = PR_M + 8;  // entries folded by one PROD CTA (256 threads x 2^PR_M)
-constexpr u32 GN_CHUNK_LOG = GN_M + 8;  // entries folded by one GEN CTA (256 threads x 2^GN_M)
+constexpr u32 GN_CHUNK_LOG = GN_M + 7;  // entries folded by one GEN CTA (128 threads x 2^GN_M)
 
 // Which layers' phase-2/3 tables are built by k_build23 (the rest are formed
 // on the fly or never stored).
@@ -112,8 +112,13 @@ struct vc_circuit {
     std::vector<int> eval_steps;
     std::vector<u32> round_layer;
     u32 *d_round_layer = nullptr;
-    cudaEvent_t stage_ev[VC_NUM_STAGES + 1] = {};
+    cudaEvent_t stage_ev[2 * VC_NUM_STAGES] = {};
     bool stage_on = false;
+    // helper streams and the fork/join events of a proof
+    cudaStream_t aux[2] = {};
+    cudaEvent_t ev_fork = nullptr, ev_tables = nullptr, ev_eval = nullptr, ev_build = nullptr, ev_prod = nullptr,
+                ev_gen = nullptr;
+    bool has_tab = false;
 };
 
 static vc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? VC_OK : (e == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA); }
@@ -603,6 +608,10 @@ extern "C" vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, 
         if (e == cudaSuccess) e = upload(const_cast<u32 *>(L.by2_g), c->by2_g[i]);
     }
     if (e == cudaSuccess) e = cudaHostAlloc(&c->h_pinned, 64 * sizeof(u64), cudaHostAllocDefault);
+    for (int k = 0; e == cudaSuccess && k < 2; k++) e = cudaStreamCreateWithFlags(&c->aux[k], cudaStreamNonBlocking);
+    for (cudaEvent_t *ev : {&c->ev_fork, &c->ev_tables, &c->ev_eval, &c->ev_build, &c->ev_prod, &c->ev_gen})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    for (const SciDev &Sc : c->scis) c->has_tab = c->has_tab || Sc.kind == PK_GEN_TAB;
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (c->arena) cudaFree(c->arena);
@@ -618,6 +627,10 @@ extern "C" vc_status vc_circuit_destroy(vc_circuit *c)
     if (!c) return VC_OK;
     DevGuard guard(c->device);
     cudaDeviceSynchronize();
+    for (cudaEvent_t ev : {c->ev_fork, c->ev_tables, c->ev_eval, c->ev_build, c->ev_prod, c->ev_gen})
+        if (ev) cudaEventDestroy(ev);
+    for (cudaStream_t s : c->aux)
+        if (s) cudaStreamDestroy(s);
     if (c->arena) cudaFree(c->arena);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     delete c;
@@ -668,34 +681,63 @@ static cudaError_t enqueue_prove(vc_circuit *c, u64 seed, u64 *tr, cudaStream_t 
     Globals G = c->G;
     G.seed = seed;
     G.tr = tr;
-    auto mark = [&](int k) {
-        if (c->stage_on) cudaEventRecord(c->stage_ev[k], st);
+    cudaStream_t sa = c->aux[0], sb = c->aux[1];
+    auto mark = [&](int k, int end, cudaStream_t s) {
+        if (c->stage_on) cudaEventRecord(c->stage_ev[2 * k + end], s);
     };
-    mark(VC_STAGE_SETUP);
+    mark(VC_STAGE_PROOF, 0, st);
+    mark(VC_STAGE_SETUP, 0, st);
     launch_setup(G, c->zd_off, st);
-    mark(VC_STAGE_EQ);
-    launch_eqtabs(c->d_eq_prove, (int)c->eq_prove.size(), st);
-    mark(VC_STAGE_EVAL);
+    mark(VC_STAGE_SETUP, 1, st);
+    cudaEventRecord(c->ev_fork, st);
+    // helper A: eq tables and product weights (need the coins only)
+    cudaStreamWaitEvent(sa, c->ev_fork, 0);
+    mark(VC_STAGE_TABLES, 0, sa);
+    launch_eqtabs(c->d_eq_prove, (int)c->eq_prove.size(), sa);
+    launch_prep_prod(G, c->d_scis, c->d_pwaves, (int)c->pwaves.size(), sa);
+    mark(VC_STAGE_TABLES, 1, sa);
+    cudaEventRecord(c->ev_tables, sa);
+    // caller's stream: evaluation
+    mark(VC_STAGE_EVAL, 0, st);
     enqueue_eval(c, G, st);
-    mark(VC_STAGE_LINE);
+    mark(VC_STAGE_EVAL, 1, st);
+    cudaEventRecord(c->ev_eval, st);
+    // helper A: product-weighted waves
+    cudaStreamWaitEvent(sa, c->ev_eval, 0);
+    for (size_t w = 0; w < c->p_items.size() || w < 2; w++) {
+        if (w < 2) mark(w == 0 ? VC_STAGE_PROD0 : VC_STAGE_PRODN, 0, sa);
+        if (w < c->p_items.size())
+            launch_sc_prod(G, c->d_pwaves, c->d_p_items[w], (int)c->p_items[w].size(), c->partials, sa);
+        if (w == 0) mark(VC_STAGE_PROD0, 1, sa);
+    }
+    mark(VC_STAGE_PRODN, 1, sa);
+    cudaEventRecord(c->ev_prod, sa);
+    // caller's stream: line reductions, then the wiring tables (they need v1 = q(0))
+    mark(VC_STAGE_LINE, 0, st);
     for (size_t w = 0; w < c->line_items.size(); w++)
         launch_line_wave(G, c->d_lw, c->d_line_items[w], (int)c->line_items[w].size(), st);
-    mark(VC_STAGE_BUILD);
-    launch_prep_prod(G, c->d_scis, c->d_pwaves, (int)c->pwaves.size(), st);
     launch_build23(G, c->d_build_off, (int)c->d, c->build_blocks, st);
-    mark(VC_STAGE_SC0);
-    const size_t nw = std::max(c->p_items.size(), c->g_items.size());
-    for (size_t w = 0; w < nw; w++) {
-        if (w == 1) mark(VC_STAGE_SC1);
-        if (w < c->p_items.size())
-            launch_sc_prod(G, c->d_pwaves, c->d_p_items[w], (int)c->p_items[w].size(), c->partials, st);
+    mark(VC_STAGE_LINE, 1, st);
+    cudaEventRecord(c->ev_build, st);
+    // helper B: general waves (after the tables they read)
+    cudaStreamWaitEvent(sb, c->ev_eval, 0);
+    cudaStreamWaitEvent(sb, c->ev_tables, 0);
+    if (c->has_tab) cudaStreamWaitEvent(sb, c->ev_build, 0);
+    for (size_t w = 0; w < c->g_items.size() || w < 2; w++) {
+        if (w < 2) mark(w == 0 ? VC_STAGE_GEN0 : VC_STAGE_GENN, 0, sb);
         if (w < c->g_items.size())
-            launch_sc_gen(G, c->d_gwaves, c->d_g_items[w], (int)c->g_items[w].size(), c->partials, st);
+            launch_sc_gen(G, c->d_gwaves, c->d_g_items[w], (int)c->g_items[w].size(), c->partials, sb);
+        if (w == 0) mark(VC_STAGE_GEN0, 1, sb);
     }
-    if (nw < 2) mark(VC_STAGE_SC1);
-    mark(VC_STAGE_FINAL);
+    mark(VC_STAGE_GENN, 1, sb);
+    cudaEventRecord(c->ev_gen, sb);
+    // join
+    cudaStreamWaitEvent(st, c->ev_prod, 0);
+    cudaStreamWaitEvent(st, c->ev_gen, 0);
+    mark(VC_STAGE_FINAL, 0, st);
     launch_final(G, c->d_scis, c->d_rounds, (int)c->rounds.size(), c->partials, c->V[0], u64(1) << c->s[0], st);
-    mark(VC_NUM_STAGES);
+    mark(VC_STAGE_FINAL, 1, st);
+    mark(VC_STAGE_PROOF, 1, st);
     return cudaGetLastError();
 }
 
@@ -798,7 +840,7 @@ extern "C" vc_status vc_circuit_set_stage_events(vc_circuit *c, void *const *eve
         c->stage_on = false;
         return VC_OK;
     }
-    for (int k = 0; k <= VC_NUM_STAGES; k++) {
+    for (int k = 0; k < 2 * VC_NUM_STAGES; k++) {
         if (!events[k]) return VC_EINVAL;
         c->stage_ev[k] = (cudaEvent_t)events[k];
     }

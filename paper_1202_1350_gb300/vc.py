@@ -44,8 +44,8 @@ class _Desc(ctypes.Structure):
                 ("in2", ctypes.POINTER(_u32p))]
 
 
-NUM_STAGES = 8
-STAGES = ("setup", "eq", "eval", "line", "build", "sc0", "sc1", "final")
+NUM_STAGES = 10
+STAGES = ("proof", "setup", "tables", "eval", "line", "prod0", "prodn", "gen0", "genn", "final")
 
 
 class CircuitInfo(ctypes.Structure):
@@ -250,16 +250,17 @@ def vc_verify(h, inputs, seed: int, transcript, stream=None, device: int = 0, ac
 
 
 def vc_circuit_set_stage_events(h, events):
-    """events: NUM_STAGES + 1 torch.cuda.Event objects (enable_timing=True), or None."""
+    """events: 2 * NUM_STAGES torch.cuda.Event objects (enable_timing=True):
+    start and end of every stage; or None."""
     if events is None:
         _check(lib().vc_circuit_set_stage_events(h, None), "vc_circuit_set_stage_events")
         return
-    if len(events) != NUM_STAGES + 1:
-        raise ValueError(f"need {NUM_STAGES + 1} events")
+    if len(events) != 2 * NUM_STAGES:
+        raise ValueError(f"need {2 * NUM_STAGES} events")
     for e in events:  # make sure each event exists on the device
         if getattr(e, "cuda_event", 0) == 0:
             e.record()
-    arr = (ctypes.c_void_p * (NUM_STAGES + 1))(*[e.cuda_event for e in events])
+    arr = (ctypes.c_void_p * (2 * NUM_STAGES))(*[e.cuda_event for e in events])
     _check(lib().vc_circuit_set_stage_events(h, arr), "vc_circuit_set_stage_events")
 
 
