@@ -161,7 +161,10 @@ typedef enum {
  * on the stream that runs the stage (a stage with no work records both
  * back to back).  `events` must hold 2 * VC_NUM_STAGES events (cudaEvent_t)
  * created on the circuit's device and owned by the caller; NULL turns
- * recording off. */
+ * recording off.  A proof replays a CUDA graph of its launches, captured by
+ * the first vc_prove after the circuit's creation or after this call; the
+ * events are event-record nodes of that graph.  The call must not overlap a
+ * proof in flight on the circuit (it may replace the graph). */
 vc_status vc_circuit_set_stage_events(vc_circuit *c, void *const *events);
 
 /* Shape facts of a circuit. */
@@ -179,10 +182,48 @@ typedef struct {
 
 vc_status vc_circuit_get_info(const vc_circuit *c, vc_circuit_info *info);
 
-/* Batched proving: n independent (circuit, inputs, seed) jobs in one set of
- * merged launches; circuits must be distinct handles on one device.
- * Same pointer rules as vc_prove; synchronous unless every pointer is device
- * memory. */
+/* Batches (Sec. 6.2.3 runs many independent proofs; here they share launches).
+ * A batch is a fixed set of distinct circuit handles on one device whose
+ * proofs run as ONE set of merged launches: every evaluation step, line wave
+ * and sum-check wave of every member is one work list, so n small proofs cost
+ * about the launches of one.  A batch keeps its own launch plan and a small
+ * parameter table on the device; the members keep their scratch, so a member
+ * must not be used by another call while a batch proof that includes it is in
+ * flight.  The first vc_batch_prove captures the launches into a CUDA graph;
+ * later calls replay it. */
+typedef struct vc_batch vc_batch;
+
+/* circuits: n >= 1 distinct handles on one device (VC_EINVAL otherwise).  The
+ * handles must outlive the batch. */
+vc_status vc_batch_create(vc_circuit *const *circuits, int n, vc_batch **out);
+
+/* Free the batch (synchronises its device); the members are untouched.  NULL
+ * is accepted. */
+vc_status vc_batch_destroy(vc_batch *b);
+
+/* Prove every member: inputs[j], seeds[j], transcripts[j] for member j, with
+ * vc_prove's pointer rules.  Asynchronous when every pointer is device memory
+ * (errors latched, reported by vc_batch_sync); otherwise returns after all
+ * transcripts are written and reports VC_EINVAL for a non-canonical input. */
+vc_status vc_batch_prove(vc_batch *b, const uint64_t *const *inputs, const uint64_t *seeds,
+                         uint64_t *const *transcripts, void *stream);
+
+/* Wait for the batch's queued work on `stream`; return (and clear) the worst
+ * error latched by any member. */
+vc_status vc_batch_sync(vc_batch *b, void *stream);
+
+typedef struct {
+    uint32_t n_members;
+    uint32_t prove_launches;  /* kernel launches per vc_batch_prove (all members) */
+    uint64_t device_bytes;    /* plan + parameter table held by the batch         */
+    uint64_t gates;           /* non-input gates over all members                 */
+} vc_batch_info;
+
+vc_status vc_batch_get_info(const vc_batch *b, vc_batch_info *info);
+
+/* One-shot batch: vc_batch_create + vc_batch_prove + vc_batch_sync +
+ * vc_batch_destroy.  Synchronous.  For repeated batches of the same circuits
+ * keep a vc_batch instead (it skips the planning and the graph capture). */
 vc_status vc_prove_batch(vc_circuit *const *circuits, const uint64_t *const *inputs,
                          const uint64_t *seeds, uint64_t *const *transcripts, int n,
                          void *stream);

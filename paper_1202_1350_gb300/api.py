@@ -84,3 +84,35 @@ class Circuit:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """A fixed set of distinct circuits proved by one set of merged launches."""
+
+    def __init__(self, circuits):
+        self.circuits = list(circuits)
+        self.device = self.circuits[0].device
+        self.handle = _vc.vc_batch_create([c.handle for c in self.circuits])
+
+    def info(self) -> dict:
+        return _vc.vc_batch_get_info(self.handle)
+
+    def prove(self, inputs, seeds, transcripts=None, sync: bool = True):
+        dev = f"cuda:{self.device}"
+        xs = [_as_tensor(x, dev) for x in inputs]
+        trs = [c.new_transcript() for c in self.circuits] if transcripts is None else transcripts
+        _vc.vc_batch_prove(self.handle, xs, list(seeds), trs, device=self.device)
+        if sync:
+            _vc.vc_batch_sync(self.handle, device=self.device)
+        return trs
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _vc.vc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -171,3 +171,49 @@ __device__ __forceinline__ void limbs31(u64 r, u32 &r0, u32 &r1)
     r0 = (u32)r & 0x7FFFFFFFu;
     r1 = (u32)(r >> 31);
 }
+
+// Inclusive product scan over the warp (lane l gets prod_{j<=l} x_j).
+__device__ __forceinline__ u64 warp_scan_mul(u64 x)
+{
+    const u32 lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u64 y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (u32)o) x = f_mul(x, y);
+    }
+    return x;
+}
+
+// Inclusive suffix product scan (lane l gets prod_{j>=l} x_j).
+__device__ __forceinline__ u64 warp_rscan_mul(u64 x)
+{
+    const u32 lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u64 y = __shfl_down_sync(0xffffffffu, x, o);
+        if (lane + o < 32) x = f_mul(x, y);
+    }
+    return x;
+}
+
+// Product over the warp of one canonical value per lane.
+__device__ __forceinline__ u64 warp_prod(u64 x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = f_mul(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// Warp-wide sum of one W value per lane -> W (a sum of four W values stays
+// below 2^64, so reduce every two steps).
+__device__ __forceinline__ u64 warp_wsum(u64 x)
+{
+    x += __shfl_xor_sync(0xffffffffu, x, 16);
+    x += __shfl_xor_sync(0xffffffffu, x, 8);
+    x = wred(x);
+    x += __shfl_xor_sync(0xffffffffu, x, 4);
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    x = wred(x);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    return wred(x);
+}

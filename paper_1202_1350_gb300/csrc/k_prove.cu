@@ -18,8 +18,34 @@
 // Setup: verifier coins (splitmix64 stream), the layer points z_i, eq(z_i, r_P).
 // --------------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(1024) k_setup(Globals G, u32 zd_off)
+// Per-proof parameters of one circuit (seed, transcript pointer).
+__global__ void k_params(Globals *G, u64 seed, u64 *tr)
 {
+    G->seed = seed;
+    G->tr = tr;
+}
+
+__global__ void k_params_batch(Globals *Gs, const CallParams *cp, int n)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        Gs[j].seed = cp[j].seed;
+        Gs[j].tr = cp[j].tr;
+    }
+}
+
+void launch_params(Globals *G, u64 seed, u64 *tr, cudaStream_t st) { k_params<<<1, 1, 0, st>>>(G, seed, tr); }
+
+void launch_params_batch(Globals *Gs, const CallParams *cp, int n, cudaStream_t st)
+{
+    if (n > 0) k_params_batch<<<(n + 255) / 256, 256, 0, st>>>(Gs, cp, n);
+}
+
+// One CTA per circuit.
+__global__ void __launch_bounds__(1024) k_setup(const Globals *Gs)
+{
+    const Globals &G = Gs[blockIdx.x];
+    const u32 *zmap = G.zmap;
+    const u32 nz = G.nz, zd_off = G.zd_off;
     __shared__ int s_rej;
     if (threadIdx.x == 0) s_rej = 0;
     __syncthreads();
@@ -43,56 +69,72 @@ __global__ void __launch_bounds__(1024) k_setup(Globals G, u32 zd_off)
         __syncthreads();
     }
     const LayerDev *L = G.layers;
-    // z_0: the first s_0 challenges.
+    // z_0 and every z_{i+1} = l_i(tau_i) = r1 + tau (r2 - r1): one thread per
+    // coordinate (zmap[q] = layer << 8 | k for the flattened coordinates).
     for (u32 k = threadIdx.x; k < L[0].s; k += blockDim.x) G.pts[L[0].z_off + k] = G.chal[k];
-    // z_{i+1} = l_i(tau_i) = r1 + tau (r2 - r1): one thread per layer.
-    for (u32 i = threadIdx.x; i < G.d; i += blockDim.x) {
+    for (u32 qi = threadIdx.x; qi < nz; qi += blockDim.x) {
+        const u32 i = zmap[qi] >> 8, k = zmap[qi] & 0xFF;
         const u32 si = L[i].s, sn = L[i].sn, co = L[i].chal_off;
         const u64 tau = G.chal[co + si + 2 * sn];
-        u64 *zn = G.pts + ((i + 1 < G.d) ? L[i + 1].z_off : zd_off);
-        const u64 *r1 = G.chal + co + si, *r2 = r1 + sn;
-        for (u32 k = 0; k < sn; k++) zn[k] = f_add(r1[k], f_mul(tau, f_sub(r2[k], r1[k])));
+        const u64 r1 = G.chal[co + si + k], r2 = G.chal[co + si + sn + k];
+        G.pts[((i + 1 < G.d) ? L[i + 1].z_off : zd_off) + k] = f_add(r1, f_mul(tau, f_sub(r2, r1)));
     }
     __syncthreads();
-    // eq(z_i, r_P) per layer.
-    for (u32 i = threadIdx.x; i < G.d; i += blockDim.x) {
-        const u64 *z = G.pts + L[i].z_off;
-        const u64 *rp = G.chal + L[i].chal_off;
-        u64 e = 1;
-        for (u32 k = 0; k < L[i].s; k++)
-            e = f_mul(e, f_add(f_mul(z[k], rp[k]), f_mul(f_sub(1, z[k]), f_sub(1, rp[k]))));
-        G.scal[SCAL_EQZRP(i)] = e;
+    // eq(z_i, r_P) per layer: a warp per layer, a lane per coordinate (s_i <= 30).
+    const u32 lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (u32 i = warp; i < G.d; i += blockDim.x >> 5) {
+        u64 f = 1;
+        if (lane < L[i].s) {
+            const u64 z = G.pts[L[i].z_off + lane], rp = G.chal[L[i].chal_off + lane];
+            f = f_add(f_mul(z, rp), f_mul(f_sub(1, z), f_sub(1, rp)));
+        }
+        f = warp_prod(f);
+        if (lane == 0) G.scal[SCAL_EQZRP(i)] = f;
     }
 }
 
-void launch_setup(const Globals &G, u32 zd_off, cudaStream_t st)
+void launch_setup(const Globals *Gs, int ncirc, cudaStream_t st)
 {
-    k_setup<<<1, 1024, 0, st>>>(G, zd_off);
+    if (ncirc > 0) k_setup<<<ncirc, 1024, 0, st>>>(Gs);
 }
 
 // --------------------------------------------------------------------------------
 // Split eq tables: lo[j] = prod_{k<h} eq(x_k, bit_k j), hi[j] = prod_{k<n-h} eq(x_{h+k}, bit_k j).
 // --------------------------------------------------------------------------------
 
+// Each half (lo over coordinates [0, h), hi over [h, n)) is itself a product
+// of two sub-tables over its low and high coordinates, built by direct
+// products (at most 8 factors), so every entry costs one product.
 __global__ void __launch_bounds__(256) k_eqtabs(const EqJob *jobs)
 {
     const EqTab t = jobs[blockIdx.x].t;
     __shared__ u64 x[64], xm[64];
+    __shared__ u64 sub[4][256];
     for (u32 k = threadIdx.x; k < t.n; k += blockDim.x) {
         x[k] = t.pt[k];
         xm[k] = f_sub(1, x[k]);
     }
     __syncthreads();
-    const u32 h = t.h, hh = t.n - t.h;
-    for (u32 j = threadIdx.x; j < (1u << h); j += blockDim.x) {
-        u64 e = 1;
-        for (u32 k = 0; k < h; k++) e = f_mul(e, ((j >> k) & 1) ? x[k] : xm[k]);
-        t.lo[j] = e;
+    const u32 m[2] = {t.h, t.n - t.h};
+    const u32 c0[2] = {0, t.h};
+    // sub-tables: half j, part a (low m1 coordinates) / b (high)
+    for (u32 j = 0; j < 2; j++) {
+        const u32 m1 = m[j] / 2, m2 = m[j] - m1;
+        for (u32 e = threadIdx.x; e < (1u << m1) + (1u << m2); e += blockDim.x) {
+            const bool lowp = e < (1u << m1);
+            const u32 idx = lowp ? e : e - (1u << m1);
+            const u32 cnt = lowp ? m1 : m2, off = c0[j] + (lowp ? 0 : m1);
+            u64 v = 1;
+            for (u32 k = 0; k < cnt; k++) v = f_mul(v, ((idx >> k) & 1) ? x[off + k] : xm[off + k]);
+            sub[2 * j + (lowp ? 0 : 1)][idx] = v;
+        }
     }
-    for (u32 j = threadIdx.x; j < (1u << hh); j += blockDim.x) {
-        u64 e = 1;
-        for (u32 k = 0; k < hh; k++) e = f_mul(e, ((j >> k) & 1) ? x[h + k] : xm[h + k]);
-        t.hi[j] = e;
+    __syncthreads();
+    u64 *dst[2] = {t.lo, t.hi};
+    for (u32 j = 0; j < 2; j++) {
+        const u32 m1 = m[j] / 2;
+        for (u32 e = threadIdx.x; e < (1u << m[j]); e += blockDim.x)
+            dst[j][e] = f_mul(sub[2 * j][e & ((1u << m1) - 1)], sub[2 * j + 1][e >> m1]);
     }
 }
 
@@ -126,11 +168,15 @@ __device__ __forceinline__ void gate_wiring(const LayerDev &L, u64 g, u64 &a, u6
     }
 }
 
-// Layer evaluation: V_i[g] = V_{i+1}[in1] op V_{i+1}[in2] (Sec. 6.2.4).
-__global__ void __launch_bounds__(256) k_eval_layer(const LayerDev L)
+// Layer evaluation: V_i[g] = V_{i+1}[in1] op V_{i+1}[in2] (Sec. 6.2.4); an
+// item covers 256 gates of one layer of one circuit.
+__global__ void __launch_bounds__(256) k_eval_layer(const Globals *Gs, const LayerEval *le, const Item *items)
 {
-    const u64 S = 1ull << L.s;
-    for (u64 g = blockIdx.x * (u64)blockDim.x + threadIdx.x; g < S; g += (u64)gridDim.x * blockDim.x) {
+    const Item it = items[blockIdx.x];
+    const LayerEval E = le[it.wave];
+    const LayerDev &L = Gs[E.circ].layers[E.layer];
+    const u64 g = (u64)it.chunk * 256 + threadIdx.x;
+    if (g < (1ull << L.s)) {
         u64 a, b;
         u32 mul;
         gate_wiring(L, g, a, b, mul);
@@ -139,14 +185,9 @@ __global__ void __launch_bounds__(256) k_eval_layer(const LayerDev L)
     }
 }
 
-void launch_eval_layer(const Globals &G, const LayerDev &L, int i, cudaStream_t st)
+void launch_eval_layers(const Globals *Gs, const LayerEval *le, const Item *items, int nitems, cudaStream_t st)
 {
-    (void)G;
-    (void)i;
-    const u64 S = 1ull << L.s;
-    u64 blocks = (S + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    k_eval_layer<<<(unsigned)blocks, 256, 0, st>>>(L);
+    if (nitems > 0) k_eval_layer<<<nitems, 256, 0, st>>>(Gs, le, items);
 }
 
 // Fused evaluation of a run of block-local layers (every structured kind but
@@ -158,11 +199,14 @@ void launch_eval_layer(const Globals &G, const LayerDev &L, int i, cudaStream_t 
 
 extern __shared__ u64 ev_dyn[];
 
-__global__ void __launch_bounds__(EV_NT) k_eval_seg(Globals G, EvalSeg S)
+__global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const EvalSeg *segs, const Item *items)
 {
     u64 *bufA = ev_dyn, *bufB = ev_dyn + EV_MAXB;
+    const Item it = items[blockIdx.x];
+    const EvalSeg S = segs[it.wave];
+    const Globals &G = Gs[S.circ];
     const LayerDev *Ls = G.layers;
-    const u32 chunk = blockIdx.x;
+    const u32 chunk = it.chunk;
     const LayerDev &Lin = Ls[S.i_hi];
     const u32 s_in = Lin.sn;
     u32 B = 1u << S.c;  // block size of the current (upper) layer
@@ -204,15 +248,9 @@ __global__ void __launch_bounds__(EV_NT) k_eval_seg(Globals G, EvalSeg S)
     (void)s_in;
 }
 
-void launch_eval_seg(const Globals &G, const EvalSeg &S, cudaStream_t st)
+void launch_eval_segs(const Globals *Gs, const EvalSeg *segs, const Item *items, int nitems, cudaStream_t st)
 {
-    const size_t smem = 2 * EV_MAXB * sizeof(u64);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_eval_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
-    k_eval_seg<<<S.nchunks, EV_NT, smem, st>>>(G, S);
+    if (nitems > 0) k_eval_seg<<<nitems, EV_NT, 2 * EV_MAXB * sizeof(u64), st>>>(Gs, segs, items);
 }
 
 __global__ void k_check_canonical(const u64 *x, u64 n, u32 *status)
@@ -229,6 +267,25 @@ void launch_check_canonical(const u64 *x, u64 n, u32 *status, cudaStream_t st)
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks == 0) blocks = 1;
     k_check_canonical<<<(unsigned)blocks, 256, 0, st>>>(x, n, status);
+}
+
+// Canonical-input check inside a proof plan: an item covers 2048 inputs of
+// circuit item.wave (used where the first evaluation launch does not check).
+__global__ void __launch_bounds__(256) k_check_inputs(const Globals *Gs, const Item *items)
+{
+    const Item it = items[blockIdx.x];
+    const Globals &G = Gs[it.wave];
+    const LayerDev &L = G.layers[G.d - 1];
+    const u64 n = 1ull << L.sn;
+    bool bad = false;
+    for (u64 k = (u64)it.chunk * 2048 + threadIdx.x, e = min(n, (u64)(it.chunk + 1) * 2048); k < e; k += 256)
+        bad |= (L.Vn[k] >= FP_P);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(G.status, ST_BAD_INPUT);
+}
+
+void launch_check_inputs(const Globals *Gs, const Item *items, int nitems, cudaStream_t st)
+{
+    if (nitems > 0) k_check_inputs<<<nitems, 256, 0, st>>>(Gs, items);
 }
 
 // --------------------------------------------------------------------------------
@@ -255,10 +312,11 @@ __device__ __forceinline__ u64 poly_fold_coef(const u64 *A, const u64 *B, u32 de
 
 extern __shared__ u64 ln_dyn[];
 
-__global__ void __launch_bounds__(LN_NT) k_line_wave(Globals G, const LineWaveDev *waves, const Item *items)
+__global__ void __launch_bounds__(LN_NT) k_line_wave(const Globals *Gs, const LineWaveDev *waves, const Item *items)
 {
     const Item it = items[blockIdx.x];
     const LineWaveDev W = waves[it.wave];
+    const Globals &G = Gs[W.circ];
     const u32 tid = threadIdx.x;
     __shared__ u64 sa[32], sb[32];
     if (tid < W.nl) {
@@ -376,16 +434,17 @@ __global__ void __launch_bounds__(LN_NT) k_line_wave(Globals G, const LineWaveDe
     }
 }
 
-void launch_line_wave(const Globals &G, const LineWaveDev *lw, const Item *items, int nitems, cudaStream_t st)
+void launch_line_wave(const Globals *Gs, const LineWaveDev *lw, const Item *items, int nitems, cudaStream_t st)
 {
-    if (nitems <= 0) return;
-    const size_t smem = (size_t)(LN_NT + LN_NT / 2) * LN_SP * sizeof(u64);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_line_wave, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
-    k_line_wave<<<nitems, LN_NT, smem, st>>>(G, lw, items);
+    if (nitems > 0)
+        k_line_wave<<<nitems, LN_NT, (size_t)(LN_NT + LN_NT / 2) * LN_SP * sizeof(u64), st>>>(Gs, lw, items);
+}
+
+void prove_kernels_init()
+{
+    cudaFuncSetAttribute(k_line_wave, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)((LN_NT + LN_NT / 2) * LN_SP * sizeof(u64)));
+    cudaFuncSetAttribute(k_eval_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * EV_MAXB * sizeof(u64)));
 }
 
 // --------------------------------------------------------------------------------
@@ -397,17 +456,13 @@ void launch_line_wave(const Globals &G, const LineWaveDev *lw, const Item *items
 // Phase-2 message: sum P2 V + B2; phase-3 message: sum P3 V + B3.
 // --------------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_build23(Globals G, const u32 *blk_off, int nlayers)
+__global__ void __launch_bounds__(256) k_build23(const Globals *Gs, const BuildItem *items)
 {
-    // which layer: last i with blk_off[i] <= blockIdx.x
-    int lo = 0, hi = nlayers;
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (blk_off[mid] <= blockIdx.x) lo = mid; else hi = mid;
-    }
-    const int i = lo;
+    const BuildItem bi = items[blockIdx.x];
+    const Globals &G = Gs[bi.circ];
+    const u32 i = bi.layer;
     const LayerDev &L = G.layers[i];
-    const u64 w = (u64)(blockIdx.x - blk_off[i]) * blockDim.x + threadIdx.x;
+    const u64 w = (u64)bi.block * blockDim.x + threadIdx.x;
     const u64 Sn = 1ull << L.sn;
     if (w >= Sn) return;
     const u64 ez = G.scal[SCAL_EQZRP(i)];
@@ -514,8 +569,8 @@ __global__ void __launch_bounds__(256) k_build23(Globals G, const u32 *blk_off, 
     }
 }
 
-void launch_build23(const Globals &G, const u32 *blk_off, int nlayers, int nblocks, cudaStream_t st)
+void launch_build23(const Globals *Gs, const BuildItem *items, int nitems, cudaStream_t st)
 {
-    if (nblocks > 0) k_build23<<<nblocks, 256, 0, st>>>(G, blk_off, nlayers);
+    if (nitems > 0) k_build23<<<nitems, 256, 0, st>>>(Gs, items);
 }
 

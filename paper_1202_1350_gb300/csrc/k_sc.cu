@@ -70,19 +70,6 @@ __device__ __forceinline__ u64 warp_sum32(u64 (&v)[32])
     return wred(v[0]);
 }
 
-// Warp-wide sum of one W value per lane -> W.
-__device__ __forceinline__ u64 warp_wsum(u64 x)
-{
-    x += __shfl_xor_sync(0xffffffffu, x, 16);
-    x += __shfl_xor_sync(0xffffffffu, x, 8);
-    x = wred(x);
-    x += __shfl_xor_sync(0xffffffffu, x, 4);
-    x += __shfl_xor_sync(0xffffffffu, x, 2);
-    x = wred(x);
-    x += __shfl_xor_sync(0xffffffffu, x, 1);
-    return wred(x);
-}
-
 // --------------------------------------------------------------------------------
 // PROD: per-wave weight tables (computed once per proof, shared by all CTAs)
 // --------------------------------------------------------------------------------
@@ -125,27 +112,30 @@ __device__ __forceinline__ void prod_factor(const Globals &G, const SciDev &S, u
 //   outer lo / hi: split table of prod_{m >= r0+nr} L_m over the chunk index,
 // and, for the first wave of an SCI, its factors, kappa_j (without sigma) and
 // esum_j = prod_{m>j} (c0_m + c1_m).
-__global__ void __launch_bounds__(256) k_prep_prod(Globals G, const SciDev *scis, const ProdWave *waves)
+__global__ void __launch_bounds__(256) k_prep_prod(const Globals *Gs, const SciDev *scis, const ProdWave *waves)
 {
     const ProdWave &W = waves[blockIdx.x];
+    const Globals &G = Gs[W.circ];
     const SciDev &S = scis[W.sci];
     __shared__ u64 c0[32], c1[32];
     const u32 tid = threadIdx.x;
     if (tid < S.n) prod_factor(G, S, tid, c0[tid], c1[tid]);
     __syncthreads();
-    if (W.r0 == 0 && tid == 0) {
-        const u64 *r = G.chal + S.chal_off;
-        u64 k = 1;
-        for (u32 j = 0; j < S.n; j++) {
+    if (W.r0 == 0 && tid < 32) {
+        // kappa_j = prod_{m<j} L_m(r_m), esum_j = prod_{m>j} (c0_m + c1_m): warp scans
+        const u32 j = tid;
+        const bool in = j < S.n;
+        const u64 a = in ? f_add(c0[j], f_mul(G.chal[S.chal_off + j], f_sub(c1[j], c0[j]))) : 1;
+        const u64 b = in ? f_add(c0[j], c1[j]) : 1;
+        u64 pre = __shfl_up_sync(0xffffffffu, warp_scan_mul(a), 1);
+        u64 suf = __shfl_down_sync(0xffffffffu, warp_rscan_mul(b), 1);
+        if (j == 0) pre = 1;
+        if (j == 31) suf = 1;
+        if (in) {
             S.Lc[2 * j] = c0[j];
             S.Lc[2 * j + 1] = c1[j];
-            S.kap[j] = k;
-            k = f_mul(k, f_add(c0[j], f_mul(r[j], f_sub(c1[j], c0[j]))));
-        }
-        u64 es = 1;
-        for (int j = (int)S.n - 1; j >= 0; j--) {
-            S.esum[j] = es;
-            es = f_mul(es, f_add(c0[j], c1[j]));
+            S.kap[j] = pre;
+            S.esum[j] = suf;
         }
     }
     const u32 e = W.e, nr = W.nr, r0 = W.r0;
@@ -187,9 +177,9 @@ __global__ void __launch_bounds__(256) k_prep_prod(Globals G, const SciDev *scis
     }
 }
 
-void launch_prep_prod(const Globals &G, const SciDev *scis, const ProdWave *waves, int nwaves, cudaStream_t st)
+void launch_prep_prod(const Globals *Gs, const SciDev *scis, const ProdWave *waves, int nwaves, cudaStream_t st)
 {
-    if (nwaves > 0) k_prep_prod<<<nwaves, 256, 0, st>>>(G, scis, waves);
+    if (nwaves > 0) k_prep_prod<<<nwaves, 256, 0, st>>>(Gs, scis, waves);
 }
 
 // --------------------------------------------------------------------------------
@@ -246,8 +236,7 @@ __device__ __forceinline__ void prod_cross(u64 (&hv)[32], u64 uv, u32 tid, u32 n
     }
 }
 
-__global__ void __launch_bounds__(PR_NT, 2) k_sc_prod(Globals G, const ProdWave *waves, const Item *items,
-                                                      u64 *partials)
+__global__ void __launch_bounds__(PR_NT, 2) k_sc_prod(const Globals *Gs, const ProdWave *waves, const Item *items)
 {
     constexpr int M = PR_M;
     __shared__ u32 s_r0[32], s_r1[32];
@@ -259,6 +248,7 @@ __global__ void __launch_bounds__(PR_NT, 2) k_sc_prod(Globals G, const ProdWave 
 
     const Item it = items[blockIdx.x];
     const ProdWave &W = waves[it.wave];
+    const Globals &G = Gs[W.circ];
     const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const u32 nr = W.nr, e = W.e, chunk = it.chunk;
     const u32 na = 1u << (nr - e);
@@ -331,15 +321,14 @@ __global__ void __launch_bounds__(PR_NT, 2) k_sc_prod(Globals G, const ProdWave 
         const u64 s = wred(wred(s_w[0][tid] + s_w[1][tid] + s_w[2][tid] + s_w[3][tid]) +
                            wred(s_w[4][tid] + s_w[5][tid] + s_w[6][tid] + s_w[7][tid]));
         const u32 k = tid >> 1, t = tid & 1;
-        partials[W.part + ((u64)k * W.nchunks + chunk) * 2 + t] = wmul(s, s_echunk);
+        W.part[((u64)k * W.nchunks + chunk) * 2 + t] = wmul(s, s_echunk);
     }
     if (!(W.flags & WF_LAST) && tid == 0) W.out[chunk] = s_lvl[0];
 }
 
-void launch_sc_prod(const Globals &G, const ProdWave *waves, const Item *items, int nitems, u64 *partials,
-                    cudaStream_t st)
+void launch_sc_prod(const Globals *Gs, const ProdWave *waves, const Item *items, int nitems, cudaStream_t st)
 {
-    if (nitems > 0) k_sc_prod<<<nitems, PR_NT, 0, st>>>(G, waves, items, partials);
+    if (nitems > 0) k_sc_prod<<<nitems, PR_NT, 0, st>>>(Gs, waves, items);
 }
 
 // --------------------------------------------------------------------------------
@@ -437,8 +426,7 @@ __device__ __forceinline__ void gen_cross(u64 (&hv)[32], u64 &p, u64 &v, u64 &b,
     }
 }
 
-__global__ void __launch_bounds__(GN_NT, 4) k_sc_gen(Globals G, const GenWave *waves, const Item *items,
-                                                     u64 *partials)
+__global__ void __launch_bounds__(GN_NT, 4) k_sc_gen(const Globals *Gs, const GenWave *waves, const Item *items)
 {
     constexpr int M = GN_M;
     __shared__ u32 s_r0[32], s_r1[32];
@@ -447,6 +435,7 @@ __global__ void __launch_bounds__(GN_NT, 4) k_sc_gen(Globals G, const GenWave *w
 
     const Item it = items[blockIdx.x];
     const GenWave &W = waves[it.wave];
+    const Globals &G = Gs[W.circ];
     const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const u32 nr = W.nr, e = W.e, chunk = it.chunk;
     const u32 na = 1u << (nr - e);
@@ -551,7 +540,7 @@ __global__ void __launch_bounds__(GN_NT, 4) k_sc_gen(Globals G, const GenWave *w
     if (tid < 3 * nr) {
         const u64 s = wred(s_w[0][tid] + s_w[1][tid] + s_w[2][tid] + s_w[3][tid]);
         const u32 k = tid / 3, t = tid % 3;
-        partials[W.part + ((u64)k * W.nchunks + chunk) * 3 + t] = s;
+        W.part[((u64)k * W.nchunks + chunk) * 3 + t] = s;
     }
     if (!(W.flags & WF_LAST) && tid == 0) {
         W.outP[chunk] = s_lvl[0][0];
@@ -560,10 +549,9 @@ __global__ void __launch_bounds__(GN_NT, 4) k_sc_gen(Globals G, const GenWave *w
     }
 }
 
-void launch_sc_gen(const Globals &G, const GenWave *waves, const Item *items, int nitems, u64 *partials,
-                   cudaStream_t st)
+void launch_sc_gen(const Globals *Gs, const GenWave *waves, const Item *items, int nitems, cudaStream_t st)
 {
-    if (nitems > 0) k_sc_gen<<<nitems, GN_NT, 0, st>>>(G, waves, items, partials);
+    if (nitems > 0) k_sc_gen<<<nitems, GN_NT, 0, st>>>(Gs, waves, items);
 }
 
 // --------------------------------------------------------------------------------
@@ -571,19 +559,20 @@ void launch_sc_gen(const Globals &G, const GenWave *waves, const Item *items, in
 // partials; the round's scalars turn the sums into g(0), g(1), g(2).
 // --------------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_final(Globals G, const SciDev *scis, const RoundRef *rounds, int nrounds,
-                                               const u64 *partials, const u64 *V0, u64 S0)
+__global__ void __launch_bounds__(256) k_final(const Globals *Gs, const SciDev *scis, const RoundRef *rounds,
+                                               int nrounds, const u32 *outs, int nouts)
 {
     const u32 lane = threadIdx.x & 31;
     const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
     for (u64 gw = (blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5; gw < (u64)nrounds; gw += nwarps) {
         const RoundRef R = rounds[gw];
         const SciDev &S = scis[R.sci];
+        const Globals &G = Gs[S.circ];
         const u32 nv = (S.kind >= PK_GEN_FIRST) ? 3 : 2;
         u64 h[3];
         for (u32 t = 0; t < nv; t++) {
             u64 s = 0;
-            for (u32 q = lane; q < R.nchunks; q += 32) s = wred(s + partials[R.part_pos + (u64)q * nv + t]);
+            for (u32 q = lane; q < R.nchunks; q += 32) s = wred(s + R.part_pos[(u64)q * nv + t]);
             h[t] = wcanon(warp_wsum(s));
         }
         if (lane == 0) {
@@ -617,17 +606,19 @@ __global__ void __launch_bounds__(256) k_final(Globals G, const SciDev *scis, co
             G.tr[R.tr_pos + 2] = g2;
         }
     }
-    for (u64 x = blockIdx.x * (u64)blockDim.x + threadIdx.x; x < S0; x += (u64)gridDim.x * blockDim.x)
-        G.tr[x] = V0[x];
+    // the outputs open each transcript
+    const u64 gid = blockIdx.x * (u64)blockDim.x + threadIdx.x, gstride = (u64)gridDim.x * blockDim.x;
+    for (int j = 0; j < nouts; j++) {
+        const Globals &G = Gs[outs[j]];
+        for (u64 x = gid; x < G.S0; x += gstride) G.tr[x] = G.layers[0].V[x];
+    }
 }
 
-void launch_final(const Globals &G, const SciDev *scis, const RoundRef *rounds, int nrounds, const u64 *partials,
-                  const u64 *V0, u64 S0, cudaStream_t st)
+void launch_final(const Globals *Gs, const SciDev *scis, const RoundRef *rounds, int nrounds, const u32 *outs,
+                  int nouts, cudaStream_t st)
 {
-    u64 threads = (u64)nrounds * 32;
-    if (threads < S0) threads = S0;
-    u64 blocks = (threads + 255) / 256;
+    u64 blocks = ((u64)nrounds * 32 + 255) / 256;
+    if (blocks < 64) blocks = 64;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    if (blocks == 0) blocks = 1;
-    k_final<<<(unsigned)blocks, 256, 0, st>>>(G, scis, rounds, nrounds, partials, V0, S0);
+    k_final<<<(unsigned)blocks, 256, 0, st>>>(Gs, scis, rounds, nrounds, outs, nouts);
 }

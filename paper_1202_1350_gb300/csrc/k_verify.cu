@@ -12,24 +12,47 @@
 
 #define VM_NT 256
 
-__global__ void __launch_bounds__(VM_NT) k_vmle(const EqTab tz, const u64 *x, u64 n, u64 *part, u32 *status)
+// Partial sums of the two multilinear extensions the verifier needs: the
+// input's at z_d (blocks [0, nin_blocks)) and the claimed outputs' at z_0 (the
+// remaining blocks).  Every value contributes independently (Sec. 4.1.2);
+// products accumulate exactly in 128 bits.  A non-canonical input latches
+// ST_BAD_INPUT; a non-canonical output entry marks the transcript bad.
+__global__ void __launch_bounds__(VM_NT) k_vmle(const EqTab tzd, const u64 *x, u64 n, const EqTab tz0,
+                                                const u64 *out, u64 nout, u32 nin_blocks, u64 *part,
+                                                u32 *status, u64 *result)
 {
-    u64 acc = 0;
+    const bool inp = blockIdx.x < nin_blocks;
+    const EqTab &tz = inp ? tzd : tz0;
+    const u64 *src = inp ? x : out;
+    const u64 cnt = inp ? n : nout;
+    const u32 b = inp ? blockIdx.x : blockIdx.x - nin_blocks;
+    const u32 nb = inp ? nin_blocks : gridDim.x - nin_blocks;
+    acc128 acc;
+    acc_zero(acc);
     bool bad = false;
-    for (u64 k = blockIdx.x * (u64)VM_NT + threadIdx.x; k < n; k += (u64)gridDim.x * VM_NT) {
-        const u64 v = x[k];
+    u32 k = 0;
+    for (u64 i = b * (u64)VM_NT + threadIdx.x; i < cnt; i += (u64)nb * VM_NT, k++) {
+        const u64 v = src[i];
         bad |= (v >= FP_P);
-        acc = f_add(acc, f_mul(eq_at(tz, k), v >= FP_P ? 0 : v));
+        mac(acc, eq_at(tz, i), v >= FP_P ? 0 : v);
+        if ((k & 31) == 31) {  // keep the accumulator well below 2^128
+            const u64 r = acc_red(acc);
+            acc.lo = r;
+            acc.hi = 0;
+        }
     }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_BAD_INPUT);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) {
+        if (inp) atomicOr(status, ST_BAD_INPUT);
+        else atomicOr(reinterpret_cast<unsigned long long *>(&result[3]), 1ull);
+    }
     __shared__ u64 s[VM_NT / 32];
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    const u64 w = warp_wsum(acc_red(acc));
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = w;
     __syncthreads();
     if (threadIdx.x < 32) {
-        u64 v = threadIdx.x < VM_NT / 32 ? s[threadIdx.x] : 0;
-        v = warp_sum(v);
-        if (threadIdx.x == 0) part[blockIdx.x] = v;
+        const u64 v = threadIdx.x < VM_NT / 32 ? s[threadIdx.x] : 0;
+        const u64 t = warp_wsum(v);
+        if (threadIdx.x == 0) part[blockIdx.x] = wcanon(t);
     }
 }
 
@@ -142,128 +165,171 @@ __device__ __forceinline__ u64 interp3(u64 g0, u64 g1, u64 g2, u64 r)
     return f_add(f_sub(t0, t1), t2);
 }
 
-// Value at x of the polynomial with values q[0..n] at 0..n (Lagrange form):
-// weight_t = prod_{u != t}(x - u) / (t! (n-t)! (-1)^(n-t)).
-__device__ u64 lagrange_at(const u64 *q, u32 n, u64 x, const u64 *invfact)
+// Value at x of the polynomial with values q[0..n] at 0..n (n <= 31), by the
+// whole warp: lane t forms the Lagrange weight
+//   prod_{u != t} (x - u) / (t! (n-t)! (-1)^(n-t))
+// from warp prefix and suffix products of the factors (x - u).
+__device__ u64 lagrange_warp(const u64 *q, u32 n, u64 x, const u64 *invfact)
 {
-    u64 pre[33], suf[33];
-    pre[0] = 1;
-    for (u32 t = 0; t < n; t++) pre[t + 1] = f_mul(pre[t], f_sub(x, t));
-    suf[n] = 1;
-    for (int t = (int)n; t >= 1; t--) suf[t - 1] = f_mul(suf[t], f_sub(x, (u64)t));
-    u64 acc = 0;
-    for (u32 t = 0; t <= n; t++) {
-        u64 w = f_mul(f_mul(pre[t], suf[t]), f_mul(invfact[t], invfact[n - t]));
-        if ((n - t) & 1) w = f_neg(w);
-        acc = f_add(acc, f_mul(q[t], w));
+    const u32 lane = threadIdx.x & 31;
+    const bool in = lane <= n;
+    const u64 f = in ? f_sub(x, (u64)lane) : 1;
+    const u64 incl = warp_scan_mul(f);
+    u64 pre = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) pre = 1;
+    const u64 rincl = warp_rscan_mul(f);
+    u64 suf = __shfl_down_sync(0xffffffffu, rincl, 1);
+    if (lane == 31) suf = 1;
+    u64 term = 0;
+    if (in) {
+        u64 w = f_mul(f_mul(pre, suf), f_mul(invfact[lane], invfact[n - lane]));
+        if ((n - lane) & 1) w = f_neg(w);
+        term = f_mul(q[lane], w);
     }
-    return acc;
+    return wcanon(warp_wsum(term));
 }
 
-#define VC_NT 1024
-
-// All checks of the verifier, concurrently (one CTA):
-//   phase 1: transcript entries canonical; claimed outputs' MLE at z_0; sum of
-//            the input-MLE partials;
-//   phase 2: per layer i, its starting claim (V~_0(z_0) for i = 0, else
-//            q_{i-1}(tau_{i-1})), its end check claim_n = eq(z_i, r_P)[add~ (v1+v2)
-//            + mult~ v1 v2] with claim_n = g_{n-1}(r_{n-1}) (or the starting
-//            claim when the layer has no rounds), and for the last layer
-//            q(tau) = input MLE;
-//   phase 3: per round j of layer i, g_j(0) + g_j(1) = g_{j-1}(r_{j-1}) (the
-//            starting claim for j = 0).
-__global__ void __launch_bounds__(VC_NT) k_vcheck(Globals G, VerifyDev V, EqTab tz0, u64 S0, const u32 *round_layer,
-                                                  u32 nrounds)
+// add~, mult~ at (p, w1, w2) for a structured kind, by the whole warp: lane k
+// forms the factor of coordinate k, the warp multiplies them.
+__device__ void wiring_warp(u32 kind, u32 si, u32 sn, const u64 *p, const u64 *w1, const u64 *w2, u64 &add,
+                            u64 &mult)
 {
-    __shared__ u64 invfact[64];
-    __shared__ u64 s_red[VC_NT / 32];
-    __shared__ u64 s_out_mle, s_in_mle;
-    __shared__ int s_bad, s_fail;
-    const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        s_bad = 0;
-        s_fail = 0;
+    const u32 k = threadIdx.x & 31;
+    u64 f = 1, lead = 1;
+    bool is_add = false;
+    switch (kind) {
+    case W_SQUARE:
+        if (k < si) f = eq3(p[k], w1[k], w2[k]);
+        break;
+    case W_TREE:
+        is_add = true;
+        if (k < si) f = eq3(p[k], w1[k + 1], w2[k + 1]);
+        lead = f_mul(f_sub(1, w1[0]), w2[0]);
+        break;
+    case W_F0_FIRST:
+        if (k < sn) f = eq3(p[k + 1], w1[k], w2[k]);
+        break;
+    case W_F0_PAIR:
+        if (k >= 1 && k < si) f = eq3(p[k], w1[k], w2[k]);
+        lead = f_mul(eq2(p[0], w1[0]), f_sub(1, w2[0]));
+        break;
+    case W_F0_FINAL:
+        if (k < si) f = eq3(p[k], w1[k + 1], w2[k + 1]);
+        lead = f_mul(w1[0], w2[0]);
+        break;
+    case W_MATMULT: {
+        const u32 L = si / 3;
+        if (k < L) f = f_mul(eq3(p[k], w1[k], w2[L + k]), f_mul(eq2(p[L + k], w2[k]), eq2(p[2 * L + k], w1[L + k])));
+        lead = f_mul(f_sub(1, w1[2 * L]), w2[2 * L]);
+        break;
     }
-    if (tid < 64) invfact[tid] = G.invfact[tid];
-    // phase 1
-    bool bad = false;
-    for (u64 k = tid; k < V.tr_len; k += VC_NT) bad |= (V.tr[k] >= FP_P);
-    u64 acc = 0;
-    for (u64 b = tid; b < S0; b += VC_NT) acc = f_add(acc, f_mul(eq_at(tz0, b), V.tr[b] >= FP_P ? 0 : V.tr[b]));
-    u64 acc2 = 0;
-    for (u32 k = tid; k < V.mle_blocks; k += VC_NT) acc2 = f_add(acc2, V.mle_part[k]);
-    __syncthreads();
-    if (__any_sync(0xffffffffu, bad) && lane == 0) s_bad = 1;
-    acc = warp_sum(acc);
-    acc2 = warp_sum(acc2);
-    if (lane == 0) s_red[warp] = acc;
-    __syncthreads();
-    if (tid < 32) {
-        u64 v = tid < VC_NT / 32 ? s_red[tid] : 0;
-        v = warp_sum(v);
-        if (tid == 0) s_out_mle = v;
+    default:
+        break;
     }
-    __syncthreads();
-    if (lane == 0) s_red[warp] = acc2;
-    __syncthreads();
-    if (tid < 32) {
-        u64 v = tid < VC_NT / 32 ? s_red[tid] : 0;
-        v = warp_sum(v);
-        if (tid == 0) s_in_mle = v;
+    const u64 v = f_mul(warp_prod(f), lead);
+    add = 0;
+    mult = 0;
+    if (kind == W_F0_FIRST) {
+        add = f_mul(p[0], v);
+        mult = f_mul(f_sub(1, p[0]), v);
+    } else if (is_add) {
+        add = v;
+    } else {
+        mult = v;
     }
-    __syncthreads();
-    if (s_bad) goto done;
-    // phase 2
-    for (u32 i = tid; i < G.d; i += VC_NT) {
+}
+
+#define VC_NT 256
+
+// All checks of the verifier, concurrently.  Warp i < d checks layer i: its
+// starting claim (the claimed outputs' MLE at z_0 for i = 0, else
+// q_{i-1}(tau_{i-1})), round 0 (g_0(0) + g_0(1) = starting claim), the end of
+// the layer (g_{n-1}(r_{n-1}) = eq(z_i, r_P)[add~ (v1 + v2) + mult~ v1 v2], or the
+// starting claim itself when the layer has no rounds) and, for the last
+// layer, q(tau) = the input's MLE at z_d.  The remaining threads check rounds
+// j >= 1 (g_j(0) + g_j(1) = g_{j-1}(r_{j-1})) and that every transcript entry is
+// canonical.  The last CTA to finish turns the failure flags into the accept
+// bit.  The accept bit is the conjunction of exactly the sequential
+// verifier's checks.
+__global__ void __launch_bounds__(VC_NT) k_vcheck(Globals G, VerifyDev V, const u32 *round_layer, u32 nrounds)
+{
+    const u32 lane = threadIdx.x & 31;
+    const u64 g = blockIdx.x * (u64)VC_NT + threadIdx.x;
+    const u64 gw = g >> 5;
+    const u64 nthreads = (u64)gridDim.x * VC_NT;
+    u32 fail = 0;
+    if (gw < G.d) {
+        const u32 i = (u32)gw;
         const LayerDev &L = G.layers[i];
         const u32 si = L.s, sn = L.sn, n = si + 2 * sn;
         const u64 *r = G.chal + L.chal_off;
         u64 start;
         if (i == 0) {
-            start = s_out_mle;
+            u64 acc = 0;
+            for (u32 k = lane; k < V.mle_out_blocks; k += 32) acc = wred(acc + V.mle_part[V.mle_blocks + k]);
+            start = wcanon(warp_wsum(acc));
         } else {
             const LayerDev &Lp = G.layers[i - 1];
-            start = lagrange_at(V.tr + Lp.tr_q, Lp.sn, G.chal[Lp.chal_off + Lp.s + 2 * Lp.sn], invfact);
+            start = lagrange_warp(V.tr + Lp.tr_q, Lp.sn, G.chal[Lp.chal_off + Lp.s + 2 * Lp.sn], G.invfact);
         }
-        V.claims[i] = start;
-        u64 claim = start;
-        if (n > 0) {
-            const u64 *m = V.tr + L.tr_msg + 3ull * (n - 1);
-            claim = interp3(m[0], m[1], m[2], r[n - 1]);
-        }
-        const u64 *q = V.tr + L.tr_q;
-        const u64 v1 = q[0], v2 = sn ? q[1] : q[0];
-        u64 add, mult;
+        u64 add = 0, mult = 0;
         if (L.kind == W_EXPLICIT) {
             add = V.wire[2 * i];
             mult = V.wire[2 * i + 1];
         } else {
-            wiring_closed(L.kind, si, sn, r, r + si, r + si + sn, add, mult);
+            wiring_warp(L.kind, si, sn, r, r + si, r + si + sn, add, mult);
         }
-        const u64 expect = f_mul(G.scal[SCAL_EQZRP(i)], f_add(f_mul(add, f_add(v1, v2)), f_mul(mult, f_mul(v1, v2))));
-        bool ok = (expect == claim);
-        if (i + 1 == G.d) ok &= (lagrange_at(q, sn, G.chal[L.chal_off + n], invfact) == s_in_mle);
-        if (!ok) atomicOr(&s_fail, 1);
+        const u64 *q = V.tr + L.tr_q;
+        if (lane == 0) {
+            const u64 *m = V.tr + L.tr_msg;
+            if (n > 0 && f_add(m[0], m[1]) != start) fail = 1;
+            u64 claim = start;
+            if (n > 0) {
+                const u64 *ml = m + 3ull * (n - 1);
+                claim = interp3(ml[0], ml[1], ml[2], r[n - 1]);
+            }
+            const u64 v1 = q[0], v2 = sn ? q[1] : q[0];
+            const u64 expect = f_mul(G.scal[SCAL_EQZRP(i)], f_add(f_mul(add, f_add(v1, v2)), f_mul(mult, f_mul(v1, v2))));
+            if (expect != claim) fail = 1;
+        }
+        if (i + 1 == G.d) {
+            const u64 fin = lagrange_warp(q, sn, G.chal[L.chal_off + n], G.invfact);
+            u64 acc = 0;
+            for (u32 k = lane; k < V.mle_blocks; k += 32) acc = wred(acc + V.mle_part[k]);
+            const u64 in_mle = wcanon(warp_wsum(acc));
+            if (lane == 0 && fin != in_mle) fail = 1;
+        }
+    } else {
+        const u64 rho = g - 32ull * G.d;
+        if (rho < nrounds) {
+            const u32 i = round_layer[rho] >> 8, j = round_layer[rho] & 0xFF;
+            if (j > 0) {
+                const LayerDev &L = G.layers[i];
+                const u64 *m = V.tr + L.tr_msg + 3ull * j;
+                const u64 prev = interp3(m[-3], m[-2], m[-1], G.chal[L.chal_off + j - 1]);
+                if (f_add(m[0], m[1]) != prev) fail = 1;
+            }
+        }
+    }
+    for (u64 k = g; k < V.tr_len; k += nthreads)
+        if (V.tr[k] >= FP_P) fail = 1;
+    if (__any_sync(0xffffffffu, fail != 0) && lane == 0) atomicOr(reinterpret_cast<unsigned long long *>(&V.result[3]), 1ull);
+    // last CTA: publish the accept bit and reset the counter for the next call
+    __shared__ bool s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int done = atomicAdd(V.counter, 1u);
+        s_last = (done == gridDim.x - 1);
     }
     __syncthreads();
-    // phase 3
-    for (u32 g = tid; g < nrounds; g += VC_NT) {
-        const u32 i = round_layer[g] >> 8, j = round_layer[g] & 0xFF;
-        const LayerDev &L = G.layers[i];
-        const u64 *m = V.tr + L.tr_msg + 3ull * j;
-        u64 prev;
-        if (j == 0) prev = V.claims[i];
-        else prev = interp3(m[-3], m[-2], m[-1], G.chal[L.chal_off + j - 1]);
-        if (f_add(m[0], m[1]) != prev) atomicOr(&s_fail, 1);
-    }
-    __syncthreads();
-done:
-    if (tid == 0) {
-        V.result[0] = s_in_mle;
-        V.result[1] = s_out_mle;
-        V.result[2] = (!s_bad && !s_fail) ? 1 : 0;
-        V.result[3] = s_bad;
-        if (V.accept_out) *V.accept_out = (!s_bad && !s_fail) ? 1 : 0;
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        const u64 bad = atomicOr(reinterpret_cast<unsigned long long *>(&V.result[3]), 0ull);
+        const int acc = bad ? 0 : 1;
+        V.result[2] = (u64)acc;
+        if (V.accept_out) *V.accept_out = acc;
+        *V.counter = 0;
     }
 }
 
@@ -282,8 +348,12 @@ void launch_init_invfact(u64 *invfact, cudaStream_t st) { k_init_invfact<<<1, 64
 void launch_verify(const Globals &G, const VerifyDev &V, const EqTab &tzd, const EqTab &tz0,
                    const u32 *explicit_layers, int n_explicit, cudaStream_t st)
 {
-    const u64 nin = 1ull << tzd.n;
-    k_vmle<<<V.mle_blocks, VM_NT, 0, st>>>(tzd, V.inputs, nin, V.mle_part, G.status);
+    const u64 nin = 1ull << tzd.n, nout = 1ull << tz0.n;
+    k_vmle<<<V.mle_blocks + V.mle_out_blocks, VM_NT, 0, st>>>(tzd, V.inputs, nin, tz0, V.tr, nout, V.mle_blocks,
+                                                              V.mle_part, G.status, V.result);
     if (n_explicit > 0) k_vwire<<<n_explicit, VM_NT, 0, st>>>(G, explicit_layers, V.wire);
-    k_vcheck<<<1, VC_NT, 0, st>>>(G, V, tz0, 1ull << tz0.n, V.round_layer, V.nrounds);
+    const u64 threads = 32ull * G.d + V.nrounds;
+    u64 blocks = (threads + VC_NT - 1) / VC_NT;
+    if (blocks < 1) blocks = 1;
+    k_vcheck<<<(unsigned)blocks, VC_NT, 0, st>>>(G, V, V.round_layer, V.nrounds);
 }

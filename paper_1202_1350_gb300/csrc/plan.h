@@ -78,6 +78,7 @@ enum : u32 { GS_NONE = 0, GS_SQ2 = 1, GS_TREE2 = 2 };
 #define GN_M 3  // GEN: 2^3 entries, 3 rounds
 
 struct SciDev {
+    u32 circ;
     u32 n;         // rounds
     u32 kind;      // PK_*
     u32 layer;
@@ -91,6 +92,7 @@ struct SciDev {
 // One wave of a PROD SCI: each CTA folds 2^nr entries (the first e rounds in
 // registers, 2^e entries per thread; the rest across the CTA).
 struct ProdWave {
+    u32 circ;
     u32 sci;
     u32 r0, nr, e;
     u32 nchunks;
@@ -101,11 +103,12 @@ struct ProdWave {
     const u64 *in;     // entries of this wave's table
     u64 *out;          // one folded value per chunk (unused on the last wave)
     u64 *wblk;         // weight block: Q, E, outer lo, outer hi
-    u64 part;          // partials: part + (k * nchunks + chunk) * 2 + t
+    u64 *part;         // partials: part[(k * nchunks + chunk) * 2 + t]
 };
 
 // One wave of a GEN SCI.
 struct GenWave {
+    u32 circ;
     u32 sci;
     u32 r0, nr, e;
     u32 nchunks;
@@ -116,13 +119,14 @@ struct GenWave {
     u32 pad;
     const u64 *inP, *inV, *inB;
     u64 *outP, *outV, *outB;
-    u64 part;          // partials: part + (k * nchunks + chunk) * 3 + t
+    u64 *part;         // partials: part[(k * nchunks + chunk) * 3 + t]
 };
 
 // Line reduction of layer i (q(t) = V~_{i+1}(l(t)), l(t) = r1 + t (r2 - r1)),
 // computed by folding V_{i+1} with the coordinates a_k + b_k t in coefficient
 // form: after folding j coordinates each entry is a polynomial of degree j.
 struct LineWaveDev {
+    u32 circ;
     u32 layer;
     u32 n;        // s_{i+1}
     u32 l0, nl;   // coordinates [l0, l0 + nl) folded by this wave
@@ -145,14 +149,18 @@ struct Item {
 // PROD, 3 for GEN) and write g(0), g(1), g(2) at tr[tr_pos].
 struct RoundRef {
     u64 tr_pos;
-    u64 part_pos;
+    const u64 *part_pos;
     u32 nchunks;
     u32 sci;
     u32 j;  // round index within the SCI
     u32 pad;
 };
 
-// Per-call globals passed by value to the prover's kernels.
+// Per-circuit globals.  Each circuit keeps one copy in device memory (and a
+// batch keeps one per member); kernels find theirs through the `circ` index of
+// their work descriptor.  seed and tr change per proof and are written on the
+// stream by k_params (or from a parameter table for a batch) before the
+// proof's launches, so a captured launch sequence can be replayed.
 struct Globals {
     u64 seed;
     u32 d;
@@ -164,15 +172,40 @@ struct Globals {
     u32 *status;      // error flags (bit 0: non-canonical input)
     LayerDev *layers;
     u64 *invfact;     // 1/k! for k < 64 (verifier)
+    const u32 *zmap;  // flattened coordinates of z_1..z_d: layer << 8 | k
+    u32 nz;
+    u32 zd_off;       // z_d in pts[]
+    u64 S0;           // outputs
 };
 
 // A run of block-local layers evaluated by one launch (k_eval_seg): layers
 // i_hi down to i_lo, chunks of 2^c entries of layer i_hi + 1 per CTA.
 struct EvalSeg {
+    u32 circ;
     u32 i_hi, i_lo;
     u32 c;
     u32 nchunks;
     u32 check_input;  // the run's input layer is the circuit's input layer
+};
+
+// A layer evaluated on its own (MATMULT or EXPLICIT wiring).
+struct LayerEval {
+    u32 circ;
+    u32 layer;
+};
+
+// Work item of k_build23: 256 entries of layer i+1's phase-2/3 tables.
+struct BuildItem {
+    u32 circ;
+    u32 layer;
+    u32 block;
+    u32 pad;
+};
+
+// Parameters of one proof in a batch (written from the host each call).
+struct CallParams {
+    u64 seed;
+    u64 *tr;
 };
 
 #define ST_BAD_INPUT 1u
@@ -183,21 +216,22 @@ struct EqJob {
     EqTab t;
 };
 
-void launch_setup(const Globals &G, u32 zd_off, cudaStream_t st);
+void launch_params(Globals *G, u64 seed, u64 *tr, cudaStream_t st);
+void launch_params_batch(Globals *Gs, const CallParams *cp, int n, cudaStream_t st);
+void launch_setup(const Globals *Gs, int ncirc, cudaStream_t st);
 void launch_eqtabs(const EqJob *jobs, int njobs, cudaStream_t st);
-void launch_eval_layer(const Globals &G, const LayerDev &L, int i, cudaStream_t st);
-void launch_eval_seg(const Globals &G, const EvalSeg &S, cudaStream_t st);
+void launch_eval_layers(const Globals *Gs, const LayerEval *le, const Item *items, int nitems, cudaStream_t st);
+void launch_eval_segs(const Globals *Gs, const EvalSeg *segs, const Item *items, int nitems, cudaStream_t st);
 void launch_check_canonical(const u64 *x, u64 n, u32 *status, cudaStream_t st);
-void launch_line_wave(const Globals &G, const LineWaveDev *lw, const Item *items, int nitems,
-                      cudaStream_t st);
-void launch_build23(const Globals &G, const u32 *blk_off, int nlayers, int nblocks, cudaStream_t st);
-void launch_prep_prod(const Globals &G, const SciDev *scis, const ProdWave *waves, int nwaves, cudaStream_t st);
-void launch_sc_prod(const Globals &G, const ProdWave *waves, const Item *items, int nitems, u64 *partials,
-                    cudaStream_t st);
-void launch_sc_gen(const Globals &G, const GenWave *waves, const Item *items, int nitems, u64 *partials,
-                   cudaStream_t st);
-void launch_final(const Globals &G, const SciDev *scis, const RoundRef *rounds, int nrounds, const u64 *partials,
-                  const u64 *V0, u64 S0, cudaStream_t st);
+void launch_check_inputs(const Globals *Gs, const Item *items, int nitems, cudaStream_t st);
+void launch_line_wave(const Globals *Gs, const LineWaveDev *lw, const Item *items, int nitems, cudaStream_t st);
+void launch_build23(const Globals *Gs, const BuildItem *items, int nitems, cudaStream_t st);
+void launch_prep_prod(const Globals *Gs, const SciDev *scis, const ProdWave *waves, int nwaves, cudaStream_t st);
+void launch_sc_prod(const Globals *Gs, const ProdWave *waves, const Item *items, int nitems, cudaStream_t st);
+void launch_sc_gen(const Globals *Gs, const GenWave *waves, const Item *items, int nitems, cudaStream_t st);
+void launch_final(const Globals *Gs, const SciDev *scis, const RoundRef *rounds, int nrounds, const u32 *outs,
+                  int nouts, cudaStream_t st);
+void prove_kernels_init();
 
 // verifier
 struct VerifyDev {
@@ -211,6 +245,8 @@ struct VerifyDev {
     u64 *wire;          // generic add~/mult~ per layer (EXPLICIT layers)
     int *accept_out;    // optional device int receiving the accept bit
     u64 *claims;        // starting claim of every layer (d entries)
+    u32 mle_out_blocks; // blocks of the output-MLE partials (after the input's)
+    unsigned int *counter;  // CTAs of k_vcheck that finished (reset by the last)
     const u32 *round_layer;  // per global round: layer << 8 | round within layer
     u32 nrounds;
 };

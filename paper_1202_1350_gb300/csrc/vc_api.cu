@@ -4,29 +4,33 @@
 // Planning happens once per circuit: the widths and wiring kinds fix every
 // table size, every chunk of every sum-check wave, every transcript offset and
 // every challenge index, so vc_circuit_create lays all of it out in one device
-// arena and uploads the descriptors.  A proof then only replays the launches.
+// arena and uploads the descriptors.  A "plan" is the list of launches of one
+// proof over a set of circuits: one circuit, or the members of a batch, whose
+// work items then share every launch.  The first proof of a plan captures its
+// launches into a CUDA graph; later proofs replay the graph after writing the
+// new seed and transcript pointer into the device-resident globals.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
 #include "plan.h"
 #include "vc.h"
 
-
 namespace {
 
 constexpr u32 PR_CHUNK_LOG = PR_M + 8;  // entries folded by one PROD CTA (256 threads x 2^PR_M)
 constexpr u32 GN_CHUNK_LOG = GN_M + 7;  // entries folded by one GEN CTA (128 threads x 2^GN_M)
+constexpr u32 LN_CHUNK0_LOG = 11;       // coordinates folded by the first line wave
+constexpr u32 LN_CHUNKW_LOG = 9;        // coordinates folded by later line waves
 
 // Which layers' phase-2/3 tables are built by k_build23 (the rest are formed
 // on the fly or never stored).
-static bool needs_tables(u32 kind) { return kind != W_SQUARE && kind != W_TREE; }
-constexpr u32 LN_CHUNK0_LOG = 11;  // coordinates folded by the first line wave
-constexpr u32 LN_CHUNKW_LOG = 9;   // coordinates folded by later line waves
+bool needs_tables(u32 kind) { return kind != W_SQUARE && kind != W_TREE; }
 
 struct Arena {
     uintptr_t base = 0;
@@ -55,7 +59,81 @@ struct DevGuard {
     }
 };
 
+template <class T>
+cudaError_t upload(T *dst, const std::vector<T> &src)
+{
+    if (src.empty()) return cudaSuccess;
+    return cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// Kernel attributes, set once per device.
+void init_device_once(int device)
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    std::lock_guard<std::mutex> g(mu);
+    if (device < 0 || device >= 64) {
+        prove_kernels_init();
+        return;
+    }
+    if (!done[device]) {
+        prove_kernels_init();
+        done[device] = true;
+    }
+}
+
+vc_status cuda_status(cudaError_t e)
+{
+    return e == cudaSuccess ? VC_OK : (e == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA);
+}
+
 }  // namespace
+
+// The launches of one proof over a set of circuits.  Every descriptor carries
+// the index (circ) of its circuit in the plan's device array of globals; the
+// item lists of one evaluation step, line wave or sum-check wave hold the work
+// of every circuit, so one launch serves them all.
+struct Plan {
+    int ncirc = 0;
+    Globals *d_G = nullptr;
+    std::vector<Item> checks;  // canonical-input checks (circuit, 2048-input block)
+    std::vector<EqJob> eqjobs;
+    std::vector<EvalSeg> segs;
+    std::vector<LayerEval> levs;
+    std::vector<std::vector<Item>> seg_items, lev_items;  // per evaluation step
+    std::vector<LineWaveDev> lw;
+    std::vector<std::vector<Item>> line_items;  // per line wave
+    std::vector<BuildItem> builds;
+    std::vector<SciDev> scis;
+    std::vector<ProdWave> pw;
+    std::vector<GenWave> gw;
+    std::vector<std::vector<Item>> p_items, g_items;  // per sum-check wave
+    std::vector<RoundRef> rounds;
+    std::vector<u32> outs;
+    bool has_tab = false;
+    // device copies
+    Item *d_checks = nullptr;
+    EqJob *d_eqjobs = nullptr;
+    EvalSeg *d_segs = nullptr;
+    LayerEval *d_levs = nullptr;
+    std::vector<Item *> d_seg_items, d_lev_items, d_line_items, d_p_items, d_g_items;
+    LineWaveDev *d_lw = nullptr;
+    BuildItem *d_builds = nullptr;
+    SciDev *d_scis = nullptr;
+    ProdWave *d_pw = nullptr;
+    GenWave *d_gw = nullptr;
+    RoundRef *d_rounds = nullptr;
+    u32 *d_outs = nullptr;
+    // execution
+    cudaStream_t aux[2] = {};
+    cudaStream_t cap = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_tables = nullptr, ev_eval = nullptr, ev_build = nullptr, ev_prod = nullptr,
+                ev_gen = nullptr;
+    cudaEvent_t ev_params = nullptr;  // a batch's parameter table was copied
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t stage_ev[2 * VC_NUM_STAGES] = {};
+    bool stage_on = false;
+};
 
 struct vc_circuit {
     int device = 0;
@@ -70,58 +148,42 @@ struct vc_circuit {
     std::vector<u32> chal_off, z_off;
     std::vector<u64> tr_msg, tr_q;
 
-    // device arena and the descriptors that point into it
     char *arena = nullptr;
     size_t arena_bytes = 0;
-    Globals G{};
+    Globals G{};             // host copy of the circuit's globals
+    Globals *d_G = nullptr;  // device copy (seed and tr written per call)
     std::vector<u64 *> V;
     u64 *d_tr = nullptr;
     u64 *d_result = nullptr;
     std::vector<LayerDev> L;
     LayerDev *d_layers = nullptr;
-    std::vector<EqJob> eq_prove, eq_verify;
-    EqJob *d_eq_prove = nullptr, *d_eq_verify = nullptr;
-    std::vector<LineWaveDev> lw;
-    LineWaveDev *d_lw = nullptr;
-    std::vector<std::vector<Item>> line_items;
-    std::vector<Item *> d_line_items;
-    std::vector<u32> build_off;
-    u32 *d_build_off = nullptr;
-    int build_blocks = 0;
-    std::vector<SciDev> scis;
-    SciDev *d_scis = nullptr;
-    std::vector<ProdWave> pwaves;
-    ProdWave *d_pwaves = nullptr;
-    std::vector<std::vector<Item>> p_items;
-    std::vector<Item *> d_p_items;
-    std::vector<GenWave> gwaves;
-    GenWave *d_gwaves = nullptr;
-    std::vector<std::vector<Item>> g_items;
-    std::vector<Item *> d_g_items;
-    std::vector<RoundRef> rounds;
-    RoundRef *d_rounds = nullptr;
+    std::vector<EqJob> eq_verify;
+    EqJob *d_eq_verify = nullptr;
     u64 *partials = nullptr;
-    u64 n_partials = 0;
     VerifyDev Vd{};
     EqTab tzd{};
     std::vector<u32> explicit_layers;
     u32 *d_explicit_layers = nullptr;
-    u64 *h_pinned = nullptr;  // small pinned buffer for status/result readback
-    // evaluation steps: seg >= 0 -> eval_segs[seg]; else per-layer launch of layer (-seg - 1)
-    std::vector<EvalSeg> eval_segs;
-    std::vector<int> eval_steps;
-    std::vector<u32> round_layer;
-    u32 *d_round_layer = nullptr;
-    cudaEvent_t stage_ev[2 * VC_NUM_STAGES] = {};
-    bool stage_on = false;
-    // helper streams and the fork/join events of a proof
-    cudaStream_t aux[2] = {};
-    cudaEvent_t ev_fork = nullptr, ev_tables = nullptr, ev_eval = nullptr, ev_build = nullptr, ev_prod = nullptr,
-                ev_gen = nullptr;
-    bool has_tab = false;
+    std::vector<u32> round_layer, zmap;
+    u32 *d_round_layer = nullptr, *d_zmap = nullptr;
+    std::vector<int> eval_steps;  // >= 0: a segment; < 0: layer -step - 1 alone
+    Plan P;                       // this circuit alone (circ = 0)
+    u64 *h_pinned = nullptr;      // small pinned buffer for status/result readback
 };
 
-static vc_status cuda_status(cudaError_t e) { return e == cudaSuccess ? VC_OK : (e == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA); }
+struct vc_batch {
+    int device = 0;
+    std::vector<vc_circuit *> members;
+    Plan P;
+    char *arena = nullptr;
+    size_t arena_bytes = 0;
+    CallParams *d_cp = nullptr;
+    CallParams *h_cp = nullptr;  // pinned parameter table
+};
+
+// ---------------------------------------------------------------------------------------
+// Plan construction
+// ---------------------------------------------------------------------------------------
 
 // Validate the layer description against the wiring kinds (the same shape
 // rules as the header's vc_wiring comments).
@@ -154,10 +216,13 @@ static EqTab take_eq(Arena &A, const u64 *pt, u32 n)
 // EXPLICIT) go to one k_eval_seg launch each; a CTA takes 2^c entries of the
 // run's input layer (about 256 CTAs for wide layers) and keeps going while its
 // block stays >= 32 entries (or while one CTA covers the whole layer) and
-// <= 4096 entries.
+// <= 4096 entries.  Layers outside any run are evaluated alone (k_eval_layer).
 static void plan_eval(vc_circuit *c)
 {
-    c->eval_segs.clear();
+    Plan &P = c->P;
+    P.segs.clear();
+    P.levs.clear();
+    P.checks.clear();
     c->eval_steps.clear();
     int i = (int)c->d - 1;
     auto local = [&](int j) { return c->kind[j] != W_MATMULT && c->kind[j] != W_EXPLICIT; };
@@ -192,36 +257,51 @@ static void plan_eval(vc_circuit *c)
             continue;
         }
         EvalSeg S{};
+        S.circ = 0;
         S.i_hi = (u32)i;
         S.i_lo = (u32)i_lo;
         S.c = (u32)cl;
         S.nchunks = 1u << (s_in - cl);
         S.check_input = (u32)(i + 1 == (int)c->d);
-        c->eval_steps.push_back((int)c->eval_segs.size());
-        c->eval_segs.push_back(S);
+        c->eval_steps.push_back((int)P.segs.size());
+        P.segs.push_back(S);
         i = i_lo - 1;
     }
-}
-
-static void enqueue_eval(vc_circuit *c, const Globals &G, cudaStream_t st)
-{
-    for (int step : c->eval_steps) {
-        if (step >= 0) launch_eval_seg(G, c->eval_segs[step], st);
-        else launch_eval_layer(G, c->L[-step - 1], -step - 1, st);
+    P.seg_items.assign(c->eval_steps.size(), {});
+    P.lev_items.assign(c->eval_steps.size(), {});
+    for (size_t k = 0; k < c->eval_steps.size(); k++) {
+        const int step = c->eval_steps[k];
+        if (step >= 0) {
+            for (u32 ch = 0; ch < P.segs[step].nchunks; ch++) P.seg_items[k].push_back({(u32)step, ch});
+        } else {
+            const u32 layer = (u32)(-step - 1);
+            const u32 idx = (u32)P.levs.size();
+            P.levs.push_back({0u, layer});
+            const u64 blocks = ((u64(1) << c->s[layer]) + 255) / 256;
+            for (u64 b = 0; b < blocks; b++) P.lev_items[k].push_back({idx, (u32)b});
+        }
+    }
+    // the first step checks the inputs only if it is a segment that reads them all
+    if (c->eval_steps.empty() || c->eval_steps[0] < 0) {
+        const u64 blocks = ((u64(1) << c->s[c->d]) + 2047) / 2048;
+        for (u64 b = 0; b < blocks; b++) P.checks.push_back({0u, (u32)b});
     }
 }
 
-// Lay out every buffer and descriptor relative to `base` (0 for sizing).
+// Lay out every buffer and descriptor relative to `base` (0 for sizing) and
+// fill the circuit's single-circuit plan (circ = 0).
 static size_t layout(vc_circuit *c, uintptr_t base)
 {
     Arena A;
     A.base = base;
     const u32 d = c->d;
     auto S = [&](u32 i) { return u64(1) << c->s[i]; };
+    Plan &P = c->P;
 
     c->V.assign(d + 1, nullptr);
     for (u32 i = 0; i <= d; i++) c->V[i] = A.take<u64>(S(i));
     Globals &G = c->G;
+    G = Globals{};
     G.d = d;
     G.nchal = c->nchal;
     G.chal = A.take<u64>(c->nchal + 1);
@@ -231,12 +311,17 @@ static size_t layout(vc_circuit *c, uintptr_t base)
     G.scal = A.take<u64>(2 * d + 2);
     G.status = A.take<u32>(16);
     G.invfact = A.take<u64>(64);
+    G.zd_off = c->zd_off;
+    G.S0 = S(0);
+    c->d_G = A.take<Globals>(1);
+    P.d_G = c->d_G;
     c->d_result = A.take<u64>(8);
     c->d_tr = A.take<u64>(c->tr_len);
+    G.tr = c->d_tr;
 
     // layers and their eq tables
     c->L.assign(d, LayerDev{});
-    c->eq_prove.clear();
+    P.eqjobs.clear();
     c->eq_verify.clear();
     c->explicit_layers.clear();
     for (u32 i = 0; i < d; i++) {
@@ -256,9 +341,9 @@ static size_t layout(vc_circuit *c, uintptr_t base)
         L.trp = take_eq(A, r, L.s);
         L.tr1 = take_eq(A, r + L.s, L.sn);
         L.tr2 = take_eq(A, r + L.s + L.sn, L.sn);
-        c->eq_prove.push_back({L.tz});
-        c->eq_prove.push_back({L.trp});
-        c->eq_prove.push_back({L.tr1});
+        P.eqjobs.push_back({L.tz});
+        P.eqjobs.push_back({L.trp});
+        P.eqjobs.push_back({L.tr1});
         const bool tabs = needs_tables(L.kind);
         L.P2 = tabs ? A.take<u64>(S(i + 1)) : nullptr;
         L.P3 = tabs ? A.take<u64>(S(i + 1)) : nullptr;
@@ -283,8 +368,8 @@ static size_t layout(vc_circuit *c, uintptr_t base)
     c->eq_verify.push_back({c->L[0].tz});
 
     // line reduction waves
-    c->lw.clear();
-    c->line_items.clear();
+    P.lw.clear();
+    P.line_items.clear();
     for (u32 i = 0; i < d; i++) {
         const u32 n = c->s[i + 1];
         u32 l0 = 0;
@@ -293,6 +378,7 @@ static size_t layout(vc_circuit *c, uintptr_t base)
             const u32 cap = (w == 0) ? LN_CHUNK0_LOG : LN_CHUNKW_LOG;
             const u32 nl = std::min(cap, n - l0);
             LineWaveDev W{};
+            W.circ = 0;
             W.layer = i;
             W.n = n;
             W.l0 = l0;
@@ -304,10 +390,10 @@ static size_t layout(vc_circuit *c, uintptr_t base)
             W.a_off = c->chal_off[i] + c->s[i];
             W.b_off = c->chal_off[i] + c->s[i] + n;
             W.tr_q = c->tr_q[i];
-            if (c->line_items.size() <= w) c->line_items.resize(w + 1);
-            const u32 idx = (u32)c->lw.size();
-            c->lw.push_back(W);
-            for (u32 ch = 0; ch < W.nchunks; ch++) c->line_items[w].push_back({idx, ch});
+            if (P.line_items.size() <= w) P.line_items.resize(w + 1);
+            const u32 idx = (u32)P.lw.size();
+            P.lw.push_back(W);
+            for (u32 ch = 0; ch < W.nchunks; ch++) P.line_items[w].push_back({idx, ch});
             if (W.last) break;
             in = W.out;
             l0 += nl;
@@ -315,18 +401,21 @@ static size_t layout(vc_circuit *c, uintptr_t base)
     }
 
     // phase-2/3 table builds: one thread per entry of layer i+1
-    c->build_off.assign(d + 1, 0);
-    for (u32 i = 0; i < d; i++)
-        c->build_off[i + 1] = c->build_off[i] + (needs_tables(c->kind[i]) ? (u32)((S(i + 1) + 255) / 256) : 0);
-    c->build_blocks = (int)c->build_off[d];
+    P.builds.clear();
+    for (u32 i = 0; i < d; i++) {
+        if (!needs_tables(c->kind[i])) continue;
+        const u64 blocks = (S(i + 1) + 255) / 256;
+        for (u64 b = 0; b < blocks; b++) P.builds.push_back({0u, i, (u32)b, 0u});
+    }
 
-    // sum-check instances and their waves
-    c->scis.clear();
-    c->pwaves.clear();
-    c->gwaves.clear();
-    c->p_items.clear();
-    c->g_items.clear();
-    c->rounds.clear();
+    // sum-check instances and their waves; all partial sums go to one buffer
+    P.scis.clear();
+    P.pw.clear();
+    P.gw.clear();
+    P.p_items.clear();
+    P.g_items.clear();
+    P.rounds.clear();
+    std::vector<u64> pw_off, gw_off, round_off;
     u64 part_total = 0;
     for (u32 i = 0; i < d; i++) {
         const LayerDev &L = c->L[i];
@@ -335,6 +424,7 @@ static size_t layout(vc_circuit *c, uintptr_t base)
             if (n == 0) continue;
             const u32 roff = (ph == 1) ? 0 : (ph == 2) ? c->s[i] : c->s[i] + c->s[i + 1];
             SciDev Sc{};
+            Sc.circ = 0;
             Sc.n = n;
             Sc.layer = i;
             Sc.chal_off = c->chal_off[i] + roff;
@@ -343,69 +433,67 @@ static size_t layout(vc_circuit *c, uintptr_t base)
             else if (L.kind == W_SQUARE) Sc.kind = (ph == 2) ? PK_GEN_SQ2 : PK_SQ3;
             else if (L.kind == W_TREE) Sc.kind = (ph == 2) ? PK_GEN_TREE2 : PK_TREE3;
             else Sc.kind = PK_GEN_TAB;
-            const u32 sci = (u32)c->scis.size();
+            const u32 sci = (u32)P.scis.size();
             const bool prod = Sc.kind < PK_GEN_FIRST;
             if (prod) {
                 Sc.Lc = A.take<u64>(2 * n);
                 Sc.kap = A.take<u64>(n);
                 Sc.esum = A.take<u64>(n);
             }
-            c->scis.push_back(Sc);
+            P.scis.push_back(Sc);
+            const u32 nv = prod ? 2 : 3;
+            const u32 C = prod ? PR_CHUNK_LOG : GN_CHUNK_LOG;
+            const bool tab = Sc.kind == PK_GEN_TAB;
+            const bool tabB = tab && L.has_add;
+            const bool anyB = tabB || Sc.kind == PK_GEN_TREE2;
+            const u64 *inP = tab ? (ph == 2 ? L.P2 : L.P3) : nullptr;
+            const u64 *inB = tabB ? (ph == 2 ? L.B2 : L.B3) : nullptr;
+            const u64 *inV = (ph == 1) ? L.V : L.Vn;
             u32 r0 = 0;
-            if (prod) {
-                const u64 *in = (ph == 1) ? L.V : L.Vn;
-                for (u32 w = 0;; w++) {
-                    const u32 nr = std::min(PR_CHUNK_LOG, n - r0);
+            for (u32 w = 0;; w++) {
+                const u32 nr = std::min(C, n - r0);
+                const u32 nchunks = u32(1) << (n - r0 - nr);
+                const bool last = (r0 + nr == n);
+                for (u32 k = 0; k < nr; k++) {
+                    RoundRef R{};
+                    R.tr_pos = Sc.tr_off + 3ull * (r0 + k);
+                    R.nchunks = nchunks;
+                    R.sci = sci;
+                    R.j = r0 + k;
+                    round_off.push_back(part_total + u64(k) * nchunks * nv);
+                    P.rounds.push_back(R);
+                }
+                if (prod) {
                     ProdWave W{};
+                    W.circ = 0;
                     W.sci = sci;
                     W.r0 = r0;
                     W.nr = nr;
                     W.e = (nr >= (u32)PR_M) ? (u32)PR_M : 0;
-                    W.nchunks = u32(1) << (n - r0 - nr);
-                    const bool last = (r0 + nr == n);
+                    W.nchunks = nchunks;
                     W.flags = last ? WF_LAST : 0;
                     W.no = n - r0 - nr;
                     W.ho = (W.no + 1) / 2;
                     W.chal_off = Sc.chal_off + r0;
-                    W.in = in;
-                    W.out = last ? nullptr : A.take<u64>(W.nchunks);
+                    W.in = inV;
+                    W.out = last ? nullptr : A.take<u64>(nchunks);
                     const u32 kb = W.e ? W.e - 1 : 0;
-                    W.wblk = A.take<u64>(((1u << W.e) - 1) + ((1u << (nr - kb)) - 1) + (1u << W.ho) + (1u << (W.no - W.ho)));
-                    W.part = part_total;
-                    for (u32 k = 0; k < nr; k++) {
-                        RoundRef R{};
-                        R.tr_pos = Sc.tr_off + 3ull * (r0 + k);
-                        R.part_pos = part_total + u64(k) * W.nchunks * 2;
-                        R.nchunks = W.nchunks;
-                        R.sci = sci;
-                        R.j = r0 + k;
-                        c->rounds.push_back(R);
-                    }
-                    part_total += u64(nr) * W.nchunks * 2;
-                    if (c->p_items.size() <= w) c->p_items.resize(w + 1);
-                    const u32 idx = (u32)c->pwaves.size();
-                    c->pwaves.push_back(W);
-                    for (u32 ch = 0; ch < W.nchunks; ch++) c->p_items[w].push_back({idx, ch});
-                    if (last) break;
-                    in = W.out;
-                    r0 += nr;
-                }
-            } else {
-                const bool tab = Sc.kind == PK_GEN_TAB;
-                const bool tabB = tab && L.has_add;
-                const u64 *inP = tab ? (ph == 2 ? L.P2 : L.P3) : nullptr;
-                const u64 *inB = tabB ? (ph == 2 ? L.B2 : L.B3) : nullptr;
-                const u64 *inV = L.Vn;
-                const bool anyB = tabB || Sc.kind == PK_GEN_TREE2;
-                for (u32 w = 0;; w++) {
-                    const u32 nr = std::min(GN_CHUNK_LOG, n - r0);
+                    W.wblk = A.take<u64>(((1u << W.e) - 1) + ((1u << (nr - kb)) - 1) + (1u << W.ho) +
+                                         (1u << (W.no - W.ho)));
+                    pw_off.push_back(part_total);
+                    if (P.p_items.size() <= w) P.p_items.resize(w + 1);
+                    const u32 idx = (u32)P.pw.size();
+                    P.pw.push_back(W);
+                    for (u32 ch = 0; ch < nchunks; ch++) P.p_items[w].push_back({idx, ch});
+                    inV = W.out;
+                } else {
                     GenWave W{};
+                    W.circ = 0;
                     W.sci = sci;
                     W.r0 = r0;
                     W.nr = nr;
                     W.e = (nr >= (u32)GN_M) ? (u32)GN_M : 0;
-                    W.nchunks = u32(1) << (n - r0 - nr);
-                    const bool last = (r0 + nr == n);
+                    W.nchunks = nchunks;
                     W.src = (w > 0 || tab) ? GS_NONE : (Sc.kind == PK_GEN_SQ2 ? GS_SQ2 : GS_TREE2);
                     W.flags = (last ? WF_LAST : 0) | (((w > 0 && anyB) || tabB) ? WF_HASB : 0);
                     W.layer = i;
@@ -414,36 +502,32 @@ static size_t layout(vc_circuit *c, uintptr_t base)
                     W.inV = inV;
                     W.inB = inB;
                     if (!last) {
-                        W.outP = A.take<u64>(W.nchunks);
-                        W.outV = A.take<u64>(W.nchunks);
-                        W.outB = anyB ? A.take<u64>(W.nchunks) : nullptr;
+                        W.outP = A.take<u64>(nchunks);
+                        W.outV = A.take<u64>(nchunks);
+                        W.outB = anyB ? A.take<u64>(nchunks) : nullptr;
                     }
-                    W.part = part_total;
-                    for (u32 k = 0; k < nr; k++) {
-                        RoundRef R{};
-                        R.tr_pos = Sc.tr_off + 3ull * (r0 + k);
-                        R.part_pos = part_total + u64(k) * W.nchunks * 3;
-                        R.nchunks = W.nchunks;
-                        R.sci = sci;
-                        R.j = r0 + k;
-                        c->rounds.push_back(R);
-                    }
-                    part_total += u64(nr) * W.nchunks * 3;
-                    if (c->g_items.size() <= w) c->g_items.resize(w + 1);
-                    const u32 idx = (u32)c->gwaves.size();
-                    c->gwaves.push_back(W);
-                    for (u32 ch = 0; ch < W.nchunks; ch++) c->g_items[w].push_back({idx, ch});
-                    if (last) break;
+                    gw_off.push_back(part_total);
+                    if (P.g_items.size() <= w) P.g_items.resize(w + 1);
+                    const u32 idx = (u32)P.gw.size();
+                    P.gw.push_back(W);
+                    for (u32 ch = 0; ch < nchunks; ch++) P.g_items[w].push_back({idx, ch});
                     inP = W.outP;
                     inV = W.outV;
                     inB = W.outB;
-                    r0 += nr;
                 }
+                part_total += u64(nr) * nchunks * nv;
+                if (last) break;
+                r0 += nr;
             }
         }
     }
-    c->n_partials = part_total;
     c->partials = A.take<u64>(part_total + 1);
+    for (size_t k = 0; k < P.pw.size(); k++) P.pw[k].part = c->partials + pw_off[k];
+    for (size_t k = 0; k < P.gw.size(); k++) P.gw[k].part = c->partials + gw_off[k];
+    for (size_t k = 0; k < P.rounds.size(); k++) P.rounds[k].part_pos = c->partials + round_off[k];
+    P.outs.assign(1, 0u);
+    P.has_tab = false;
+    for (const SciDev &Sc : P.scis) P.has_tab = P.has_tab || Sc.kind == PK_GEN_TAB;
 
     // verifier scratch
     const u64 Sd = S(d);
@@ -451,7 +535,11 @@ static size_t layout(vc_circuit *c, uintptr_t base)
     if (mb > 152 * 4) mb = 152 * 4;
     if (mb == 0) mb = 1;
     c->Vd.mle_blocks = (u32)mb;
-    c->Vd.mle_part = A.take<u64>(mb);
+    u64 mbo = (S(0) + 255) / 256;
+    if (mbo > 64) mbo = 64;
+    c->Vd.mle_out_blocks = (u32)mbo;
+    c->Vd.mle_part = A.take<u64>(mb + mbo);
+    c->Vd.counter = A.take<unsigned int>(4);
     c->Vd.wire = A.take<u64>(2 * d + 2);
     c->Vd.claims = A.take<u64>(d + 1);
     c->round_layer.clear();
@@ -460,37 +548,329 @@ static size_t layout(vc_circuit *c, uintptr_t base)
     c->d_round_layer = A.take<u32>(c->round_layer.size() + 1);
     c->Vd.round_layer = c->d_round_layer;
     c->Vd.nrounds = (u32)c->round_layer.size();
+    c->zmap.clear();
+    for (u32 i = 0; i < d; i++)
+        for (u32 k = 0; k < c->s[i + 1]; k++) c->zmap.push_back((i << 8) | k);
+    c->d_zmap = A.take<u32>(c->zmap.size() + 1);
+    G.zmap = c->d_zmap;
+    G.nz = (u32)c->zmap.size();
     c->Vd.result = c->d_result;
     c->Vd.d = d;
     c->Vd.tr_len = c->tr_len;
 
     // descriptor arrays
     c->d_layers = A.take<LayerDev>(d);
-    c->d_eq_prove = A.take<EqJob>(c->eq_prove.size());
-    c->d_eq_verify = A.take<EqJob>(c->eq_verify.size());
-    c->d_lw = A.take<LineWaveDev>(c->lw.size());
-    c->d_line_items.assign(c->line_items.size(), nullptr);
-    for (size_t w = 0; w < c->line_items.size(); w++) c->d_line_items[w] = A.take<Item>(c->line_items[w].size());
-    c->d_build_off = A.take<u32>(d + 1);
-    c->d_scis = A.take<SciDev>(c->scis.size() + 1);
-    c->d_pwaves = A.take<ProdWave>(c->pwaves.size() + 1);
-    c->d_gwaves = A.take<GenWave>(c->gwaves.size() + 1);
-    c->d_p_items.assign(c->p_items.size(), nullptr);
-    for (size_t w = 0; w < c->p_items.size(); w++) c->d_p_items[w] = A.take<Item>(c->p_items[w].size());
-    c->d_g_items.assign(c->g_items.size(), nullptr);
-    for (size_t w = 0; w < c->g_items.size(); w++) c->d_g_items[w] = A.take<Item>(c->g_items[w].size());
-    c->d_rounds = A.take<RoundRef>(c->rounds.size() + 1);
-    c->d_explicit_layers = A.take<u32>(c->explicit_layers.size() + 1);
     G.layers = c->d_layers;
-    return A.off + 256;
+    c->d_eq_verify = A.take<EqJob>(c->eq_verify.size());
+    c->d_explicit_layers = A.take<u32>(c->explicit_layers.size() + 1);
+    return A.off;
 }
 
-template <class T>
-static cudaError_t upload(T *dst, const std::vector<T> &src)
+// Device arrays for a plan's descriptors, carved from an arena (own_G: the
+// plan holds its own array of globals, as a batch does).
+static void plan_take(Plan &P, Arena &A, bool own_G)
 {
-    if (src.empty()) return cudaSuccess;
-    return cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (own_G) P.d_G = A.take<Globals>(P.ncirc);
+    P.d_checks = A.take<Item>(P.checks.size() + 1);
+    P.d_eqjobs = A.take<EqJob>(P.eqjobs.size() + 1);
+    P.d_segs = A.take<EvalSeg>(P.segs.size() + 1);
+    P.d_levs = A.take<LayerEval>(P.levs.size() + 1);
+    auto items = [&](std::vector<std::vector<Item>> &v, std::vector<Item *> &dv) {
+        dv.assign(v.size(), nullptr);
+        for (size_t k = 0; k < v.size(); k++) dv[k] = A.take<Item>(v[k].size() + 1);
+    };
+    items(P.seg_items, P.d_seg_items);
+    items(P.lev_items, P.d_lev_items);
+    items(P.line_items, P.d_line_items);
+    items(P.p_items, P.d_p_items);
+    items(P.g_items, P.d_g_items);
+    P.d_lw = A.take<LineWaveDev>(P.lw.size() + 1);
+    P.d_builds = A.take<BuildItem>(P.builds.size() + 1);
+    P.d_scis = A.take<SciDev>(P.scis.size() + 1);
+    P.d_pw = A.take<ProdWave>(P.pw.size() + 1);
+    P.d_gw = A.take<GenWave>(P.gw.size() + 1);
+    P.d_rounds = A.take<RoundRef>(P.rounds.size() + 1);
+    P.d_outs = A.take<u32>(P.outs.size() + 1);
 }
+
+// Host-side consistency check of a plan before any of it reaches the device:
+// every item names an existing descriptor and one of its chunks, every
+// descriptor an existing circuit and sum-check instance.
+static bool plan_valid(const Plan &P)
+{
+    const u32 nc = (u32)P.ncirc;
+    for (const Item &it : P.checks)
+        if (it.wave >= nc) return false;
+    for (const EvalSeg &S : P.segs)
+        if (S.circ >= nc) return false;
+    for (const LayerEval &E : P.levs)
+        if (E.circ >= nc) return false;
+    for (const LineWaveDev &W : P.lw)
+        if (W.circ >= nc) return false;
+    for (const BuildItem &b : P.builds)
+        if (b.circ >= nc) return false;
+    for (const SciDev &S : P.scis)
+        if (S.circ >= nc) return false;
+    for (const ProdWave &W : P.pw)
+        if (W.circ >= nc || W.sci >= P.scis.size() || P.scis[W.sci].circ != W.circ) return false;
+    for (const GenWave &W : P.gw)
+        if (W.circ >= nc || W.sci >= P.scis.size() || P.scis[W.sci].circ != W.circ) return false;
+    for (const RoundRef &R : P.rounds)
+        if (R.sci >= P.scis.size() || R.j >= P.scis[R.sci].n) return false;
+    for (u32 o : P.outs)
+        if (o >= nc) return false;
+    for (const auto &v : P.seg_items)
+        for (const Item &it : v)
+            if (it.wave >= P.segs.size() || it.chunk >= P.segs[it.wave].nchunks) return false;
+    for (const auto &v : P.lev_items)
+        for (const Item &it : v)
+            if (it.wave >= P.levs.size()) return false;
+    for (const auto &v : P.line_items)
+        for (const Item &it : v)
+            if (it.wave >= P.lw.size() || it.chunk >= P.lw[it.wave].nchunks) return false;
+    for (const auto &v : P.p_items)
+        for (const Item &it : v)
+            if (it.wave >= P.pw.size() || it.chunk >= P.pw[it.wave].nchunks) return false;
+    for (const auto &v : P.g_items)
+        for (const Item &it : v)
+            if (it.wave >= P.gw.size() || it.chunk >= P.gw[it.wave].nchunks) return false;
+    return P.seg_items.size() == P.d_seg_items.size() && P.lev_items.size() == P.d_lev_items.size() &&
+           P.line_items.size() == P.d_line_items.size() && P.p_items.size() == P.d_p_items.size() &&
+           P.g_items.size() == P.d_g_items.size();
+}
+
+static cudaError_t plan_upload(Plan &P)
+{
+    if (!plan_valid(P)) return cudaErrorInvalidValue;
+    cudaError_t e = upload(P.d_checks, P.checks);
+    if (e == cudaSuccess) e = upload(P.d_eqjobs, P.eqjobs);
+    if (e == cudaSuccess) e = upload(P.d_segs, P.segs);
+    if (e == cudaSuccess) e = upload(P.d_levs, P.levs);
+    auto items = [&](std::vector<std::vector<Item>> &v, std::vector<Item *> &dv) {
+        for (size_t k = 0; e == cudaSuccess && k < v.size(); k++) e = upload(dv[k], v[k]);
+    };
+    items(P.seg_items, P.d_seg_items);
+    items(P.lev_items, P.d_lev_items);
+    items(P.line_items, P.d_line_items);
+    items(P.p_items, P.d_p_items);
+    items(P.g_items, P.d_g_items);
+    if (e == cudaSuccess) e = upload(P.d_lw, P.lw);
+    if (e == cudaSuccess) e = upload(P.d_builds, P.builds);
+    if (e == cudaSuccess) e = upload(P.d_scis, P.scis);
+    if (e == cudaSuccess) e = upload(P.d_pw, P.pw);
+    if (e == cudaSuccess) e = upload(P.d_gw, P.gw);
+    if (e == cudaSuccess) e = upload(P.d_rounds, P.rounds);
+    if (e == cudaSuccess) e = upload(P.d_outs, P.outs);
+    return e;
+}
+
+static cudaError_t plan_resources(Plan &P)
+{
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; e == cudaSuccess && k < 2; k++) e = cudaStreamCreateWithFlags(&P.aux[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P.cap, cudaStreamNonBlocking);
+    for (cudaEvent_t *ev : {&P.ev_fork, &P.ev_tables, &P.ev_eval, &P.ev_build, &P.ev_prod, &P.ev_gen, &P.ev_params})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    return e;
+}
+
+static void plan_release(Plan &P)
+{
+    if (P.exec) cudaGraphExecDestroy(P.exec);
+    P.exec = nullptr;
+    for (cudaEvent_t *ev : {&P.ev_fork, &P.ev_tables, &P.ev_eval, &P.ev_build, &P.ev_prod, &P.ev_gen, &P.ev_params}) {
+        if (*ev) cudaEventDestroy(*ev);
+        *ev = nullptr;
+    }
+    for (cudaStream_t *s : {&P.aux[0], &P.aux[1], &P.cap}) {
+        if (*s) cudaStreamDestroy(*s);
+        *s = nullptr;
+    }
+}
+
+// Merge the single-circuit plans of `cs` into one plan: every descriptor keeps
+// its circuit's buffers and gets circ = the member's index; the item lists of
+// the same evaluation step, line wave or sum-check wave are concatenated.
+// Steps of different circuits are independent, and the steps of one circuit
+// keep their order, so each merged launch is valid for every member.
+static void plan_merge(Plan &B, const std::vector<vc_circuit *> &cs)
+{
+    B = Plan{};
+    B.ncirc = (int)cs.size();
+    auto grow = [](std::vector<std::vector<Item>> &dst, size_t n) {
+        if (dst.size() < n) dst.resize(n);
+    };
+    auto append = [](std::vector<std::vector<Item>> &dst, const std::vector<std::vector<Item>> &src, u32 off) {
+        for (size_t k = 0; k < src.size(); k++)
+            for (Item it : src[k]) dst[k].push_back({it.wave + off, it.chunk});
+    };
+    for (size_t j = 0; j < cs.size(); j++) {
+        const Plan &P = cs[j]->P;
+        const u32 cj = (u32)j;
+        const u32 oseg = (u32)B.segs.size(), olev = (u32)B.levs.size(), olw = (u32)B.lw.size();
+        const u32 osci = (u32)B.scis.size(), opw = (u32)B.pw.size(), ogw = (u32)B.gw.size();
+        for (Item it : P.checks) B.checks.push_back({cj, it.chunk});
+        B.eqjobs.insert(B.eqjobs.end(), P.eqjobs.begin(), P.eqjobs.end());
+        for (EvalSeg S : P.segs) {
+            S.circ = cj;
+            B.segs.push_back(S);
+        }
+        for (LayerEval E : P.levs) {
+            E.circ = cj;
+            B.levs.push_back(E);
+        }
+        grow(B.seg_items, P.seg_items.size());
+        grow(B.lev_items, P.lev_items.size());
+        append(B.seg_items, P.seg_items, oseg);
+        append(B.lev_items, P.lev_items, olev);
+        for (LineWaveDev W : P.lw) {
+            W.circ = cj;
+            B.lw.push_back(W);
+        }
+        grow(B.line_items, P.line_items.size());
+        append(B.line_items, P.line_items, olw);
+        for (BuildItem b : P.builds) {
+            b.circ = cj;
+            B.builds.push_back(b);
+        }
+        for (SciDev Sc : P.scis) {
+            Sc.circ = cj;
+            B.scis.push_back(Sc);
+        }
+        for (ProdWave W : P.pw) {
+            W.circ = cj;
+            W.sci += osci;
+            B.pw.push_back(W);
+        }
+        for (GenWave W : P.gw) {
+            W.circ = cj;
+            W.sci += osci;
+            B.gw.push_back(W);
+        }
+        grow(B.p_items, P.p_items.size());
+        grow(B.g_items, P.g_items.size());
+        append(B.p_items, P.p_items, opw);
+        append(B.g_items, P.g_items, ogw);
+        for (RoundRef R : P.rounds) {
+            R.sci += osci;
+            B.rounds.push_back(R);
+        }
+        B.outs.push_back(cj);
+        B.has_tab = B.has_tab || P.has_tab;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Proof launch sequence
+// ---------------------------------------------------------------------------------------
+
+// The launches of one proof of every circuit of the plan, after the globals
+// hold the call's seeds.  Setup (coins, layer points) runs on `st`; then
+// helper stream A builds eq tables and product weights and, after the
+// evaluation, runs the product-weighted waves; `st` evaluates the circuit,
+// reduces the lines and builds the wiring tables; helper stream B runs the
+// general waves once the tables they read exist; the final reduction joins all.
+static void enqueue_plan(Plan &P, cudaStream_t st)
+{
+    cudaStream_t sa = P.aux[0], sb = P.aux[1];
+    const Globals *Gs = P.d_G;
+    // stage events become event-record nodes of the captured graph
+    auto mark = [&](int k, int end, cudaStream_t s) {
+        if (P.stage_on) cudaEventRecordWithFlags(P.stage_ev[2 * k + end], s, cudaEventRecordExternal);
+    };
+    mark(VC_STAGE_PROOF, 0, st);
+    mark(VC_STAGE_SETUP, 0, st);
+    launch_setup(Gs, P.ncirc, st);
+    mark(VC_STAGE_SETUP, 1, st);
+    cudaEventRecord(P.ev_fork, st);
+    cudaStreamWaitEvent(sa, P.ev_fork, 0);
+    mark(VC_STAGE_TABLES, 0, sa);
+    launch_eqtabs(P.d_eqjobs, (int)P.eqjobs.size(), sa);
+    launch_prep_prod(Gs, P.d_scis, P.d_pw, (int)P.pw.size(), sa);
+    mark(VC_STAGE_TABLES, 1, sa);
+    cudaEventRecord(P.ev_tables, sa);
+    mark(VC_STAGE_EVAL, 0, st);
+    launch_check_inputs(Gs, P.d_checks, (int)P.checks.size(), st);
+    for (size_t k = 0; k < P.seg_items.size(); k++) {
+        launch_eval_segs(Gs, P.d_segs, P.d_seg_items[k], (int)P.seg_items[k].size(), st);
+        launch_eval_layers(Gs, P.d_levs, P.d_lev_items[k], (int)P.lev_items[k].size(), st);
+    }
+    mark(VC_STAGE_EVAL, 1, st);
+    cudaEventRecord(P.ev_eval, st);
+    cudaStreamWaitEvent(sa, P.ev_eval, 0);
+    for (size_t w = 0; w < P.p_items.size() || w < 2; w++) {
+        if (w < 2) mark(w == 0 ? VC_STAGE_PROD0 : VC_STAGE_PRODN, 0, sa);
+        if (w < P.p_items.size()) launch_sc_prod(Gs, P.d_pw, P.d_p_items[w], (int)P.p_items[w].size(), sa);
+        if (w == 0) mark(VC_STAGE_PROD0, 1, sa);
+    }
+    mark(VC_STAGE_PRODN, 1, sa);
+    cudaEventRecord(P.ev_prod, sa);
+    mark(VC_STAGE_LINE, 0, st);
+    for (size_t w = 0; w < P.line_items.size(); w++)
+        launch_line_wave(Gs, P.d_lw, P.d_line_items[w], (int)P.line_items[w].size(), st);
+    launch_build23(Gs, P.d_builds, (int)P.builds.size(), st);
+    mark(VC_STAGE_LINE, 1, st);
+    cudaEventRecord(P.ev_build, st);
+    cudaStreamWaitEvent(sb, P.ev_eval, 0);
+    cudaStreamWaitEvent(sb, P.ev_tables, 0);
+    if (P.has_tab) cudaStreamWaitEvent(sb, P.ev_build, 0);
+    for (size_t w = 0; w < P.g_items.size() || w < 2; w++) {
+        if (w < 2) mark(w == 0 ? VC_STAGE_GEN0 : VC_STAGE_GENN, 0, sb);
+        if (w < P.g_items.size()) launch_sc_gen(Gs, P.d_gw, P.d_g_items[w], (int)P.g_items[w].size(), sb);
+        if (w == 0) mark(VC_STAGE_GEN0, 1, sb);
+    }
+    mark(VC_STAGE_GENN, 1, sb);
+    cudaEventRecord(P.ev_gen, sb);
+    cudaStreamWaitEvent(st, P.ev_prod, 0);
+    cudaStreamWaitEvent(st, P.ev_gen, 0);
+    mark(VC_STAGE_FINAL, 0, st);
+    launch_final(Gs, P.d_scis, P.d_rounds, (int)P.rounds.size(), P.d_outs, (int)P.outs.size(), st);
+    mark(VC_STAGE_FINAL, 1, st);
+    mark(VC_STAGE_PROOF, 1, st);
+}
+
+// Run the plan on `st`: replay its CUDA graph (captured on first use, and
+// again after the stage events change).
+static cudaError_t plan_launch(Plan &P, cudaStream_t st)
+{
+    if (!P.exec) {
+        cudaError_t e = cudaStreamBeginCapture(P.cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        enqueue_plan(P, P.cap);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(P.cap, &g);
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return e;
+        }
+        e = cudaGraphInstantiate(&P.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            P.exec = nullptr;
+            return e;
+        }
+    }
+    return cudaGraphLaunch(P.exec, st);
+}
+
+// Kernel launches of one proof (the parameter write included).
+static int count_launches(const Plan &P)
+{
+    int n = 2;  // parameters, setup
+    n += !P.eqjobs.empty();
+    n += !P.pw.empty();
+    n += !P.checks.empty();
+    for (size_t k = 0; k < P.seg_items.size(); k++) n += (!P.seg_items[k].empty()) + (!P.lev_items[k].empty());
+    for (const auto &v : P.line_items) n += !v.empty();
+    n += !P.builds.empty();
+    for (const auto &v : P.p_items) n += !v.empty();
+    for (const auto &v : P.g_items) n += !v.empty();
+    return n + 1;  // final
+}
+
+// ---------------------------------------------------------------------------------------
+// Circuits
+// ---------------------------------------------------------------------------------------
 
 extern "C" vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, vc_circuit **out)
 {
@@ -505,7 +885,10 @@ extern "C" vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, 
     c->s.assign(desc->log_width, desc->log_width + d + 1);
     c->kind.assign(desc->wiring, desc->wiring + d);
     for (u32 i = 0; i <= d; i++)
-        if (c->s[i] > 30) { delete c; return VC_EINVAL; }
+        if (c->s[i] > 30) {
+            delete c;
+            return VC_EINVAL;
+        }
     c->has_add.assign(d, 0);
     c->ex_type.resize(d);
     c->ex_in1.resize(d);
@@ -516,11 +899,11 @@ extern "C" vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, 
     c->by2_g.resize(d);
     for (u32 i = 0; i < d; i++) {
         const u32 si = c->s[i], sn = c->s[i + 1];
-        if (!shape_ok(c->kind[i], si, sn)) { delete c; return VC_EINVAL; }
-        switch (c->kind[i]) {
-        case W_TREE: case W_F0_FIRST: c->has_add[i] = 1; break;
-        default: break;
+        if (!shape_ok(c->kind[i], si, sn)) {
+            delete c;
+            return VC_EINVAL;
         }
+        if (c->kind[i] == W_TREE || c->kind[i] == W_F0_FIRST) c->has_add[i] = 1;
         if (c->kind[i] == W_EXPLICIT) {
             if (!desc->gate_type || !desc->in1 || !desc->in2 || !desc->gate_type[i] || !desc->in1[i] || !desc->in2[i]) {
                 delete c;
@@ -531,7 +914,10 @@ extern "C" vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, 
             c->ex_in1[i].assign(desc->in1[i], desc->in1[i] + Sg);
             c->ex_in2[i].assign(desc->in2[i], desc->in2[i] + Sg);
             for (u64 g = 0; g < Sg; g++) {
-                if (c->ex_type[i][g] > 1 || c->ex_in1[i][g] >= Sn || c->ex_in2[i][g] >= Sn) { delete c; return VC_EINVAL; }
+                if (c->ex_type[i][g] > 1 || c->ex_in1[i][g] >= Sn || c->ex_in2[i][g] >= Sn) {
+                    delete c;
+                    return VC_EINVAL;
+                }
                 if (c->ex_type[i][g] == 0) c->has_add[i] = 1;
             }
             // gates grouped by in1 and by in2 (counting sort keeps gate order)
@@ -569,33 +955,38 @@ extern "C" vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, 
     c->nchal = ch;
     c->tr_len = tp;
     plan_eval(c);
+    c->P.ncirc = 1;
 
     DevGuard guard(device);
-    const size_t bytes = layout(c, 0);
+    init_device_once(device);
+    size_t bytes = 0;
+    {
+        Arena A;
+        A.off = layout(c, 0);
+        plan_take(c->P, A, false);
+        bytes = A.off + 256;
+    }
     cudaError_t e = cudaMalloc(&c->arena, bytes);
-    if (e != cudaSuccess) { cudaGetLastError(); delete c; return e == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA; }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return e == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA;
+    }
     c->arena_bytes = bytes;
-    layout(c, reinterpret_cast<uintptr_t>(c->arena));
+    {
+        Arena A;
+        A.base = reinterpret_cast<uintptr_t>(c->arena);
+        A.off = layout(c, A.base);
+        plan_take(c->P, A, false);
+    }
     e = cudaMemset(c->arena, 0, bytes);
     if (e == cudaSuccess) e = upload(c->d_layers, c->L);
-    if (e == cudaSuccess) e = upload(c->d_eq_prove, c->eq_prove);
     if (e == cudaSuccess) e = upload(c->d_eq_verify, c->eq_verify);
-    if (e == cudaSuccess) e = upload(c->d_lw, c->lw);
-    for (size_t w = 0; e == cudaSuccess && w < c->line_items.size(); w++)
-        e = upload(c->d_line_items[w], c->line_items[w]);
-    if (e == cudaSuccess) e = upload(c->d_build_off, c->build_off);
-    if (e == cudaSuccess) e = upload(c->d_scis, c->scis);
-    if (e == cudaSuccess) e = upload(c->d_pwaves, c->pwaves);
-    if (e == cudaSuccess) e = upload(c->d_gwaves, c->gwaves);
-    for (size_t w = 0; e == cudaSuccess && w < c->p_items.size(); w++) e = upload(c->d_p_items[w], c->p_items[w]);
-    for (size_t w = 0; e == cudaSuccess && w < c->g_items.size(); w++) e = upload(c->d_g_items[w], c->g_items[w]);
-    if (e == cudaSuccess) e = upload(c->d_rounds, c->rounds);
     if (e == cudaSuccess) e = upload(c->d_explicit_layers, c->explicit_layers);
     if (e == cudaSuccess) e = upload(c->d_round_layer, c->round_layer);
-    if (e == cudaSuccess) {
-        launch_init_invfact(c->G.invfact, 0);
-        e = cudaDeviceSynchronize();
-    }
+    if (e == cudaSuccess) e = upload(c->d_zmap, c->zmap);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_G, &c->G, sizeof(Globals), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = plan_upload(c->P);
     for (u32 i = 0; e == cudaSuccess && i < d; i++) {
         if (c->kind[i] != W_EXPLICIT) continue;
         const LayerDev &L = c->L[i];
@@ -607,14 +998,17 @@ extern "C" vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, 
         if (e == cudaSuccess) e = upload(const_cast<u32 *>(L.by2_off), c->by2_off[i]);
         if (e == cudaSuccess) e = upload(const_cast<u32 *>(L.by2_g), c->by2_g[i]);
     }
+    if (e == cudaSuccess) {
+        launch_init_invfact(c->G.invfact, 0);
+        e = cudaDeviceSynchronize();
+    }
     if (e == cudaSuccess) e = cudaHostAlloc(&c->h_pinned, 64 * sizeof(u64), cudaHostAllocDefault);
-    for (int k = 0; e == cudaSuccess && k < 2; k++) e = cudaStreamCreateWithFlags(&c->aux[k], cudaStreamNonBlocking);
-    for (cudaEvent_t *ev : {&c->ev_fork, &c->ev_tables, &c->ev_eval, &c->ev_build, &c->ev_prod, &c->ev_gen})
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
-    for (const SciDev &Sc : c->scis) c->has_tab = c->has_tab || Sc.kind == PK_GEN_TAB;
+    if (e == cudaSuccess) e = plan_resources(c->P);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        if (c->arena) cudaFree(c->arena);
+        plan_release(c->P);
+        if (c->h_pinned) cudaFreeHost(c->h_pinned);
+        cudaFree(c->arena);
         delete c;
         return cuda_status(e);
     }
@@ -627,10 +1021,7 @@ extern "C" vc_status vc_circuit_destroy(vc_circuit *c)
     if (!c) return VC_OK;
     DevGuard guard(c->device);
     cudaDeviceSynchronize();
-    for (cudaEvent_t ev : {c->ev_fork, c->ev_tables, c->ev_eval, c->ev_build, c->ev_prod, c->ev_gen})
-        if (ev) cudaEventDestroy(ev);
-    for (cudaStream_t s : c->aux)
-        if (s) cudaStreamDestroy(s);
+    plan_release(c->P);
     if (c->arena) cudaFree(c->arena);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     delete c;
@@ -663,82 +1054,28 @@ static int ptr_kind(const void *p, int device)
     return 0;
 }
 
-static vc_status read_status_and_clear(vc_circuit *c, cudaStream_t st)
+// Queue the readback of the circuit's error flags (and their reset) on `st`.
+static cudaError_t queue_status(vc_circuit *c, cudaStream_t st)
 {
     cudaError_t e = cudaMemcpyAsync(c->h_pinned, c->G.status, sizeof(u32), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->G.status, 0, sizeof(u32), st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return VC_ECUDA;
-    const u32 s = *reinterpret_cast<u32 *>(c->h_pinned);
+    return e;
+}
+
+static vc_status decode_status(const vc_circuit *c)
+{
+    const u32 s = *reinterpret_cast<const u32 *>(c->h_pinned);
     if (s & ST_BAD_INPUT) return VC_EINVAL;
     if (s & ST_TIMEOUT) return VC_ETIMEOUT;
     return VC_OK;
 }
 
-// Enqueue evaluation + proof for inputs already in V_d; transcript -> G.tr.
-static cudaError_t enqueue_prove(vc_circuit *c, u64 seed, u64 *tr, cudaStream_t st)
+static vc_status read_status_and_clear(vc_circuit *c, cudaStream_t st)
 {
-    Globals G = c->G;
-    G.seed = seed;
-    G.tr = tr;
-    cudaStream_t sa = c->aux[0], sb = c->aux[1];
-    auto mark = [&](int k, int end, cudaStream_t s) {
-        if (c->stage_on) cudaEventRecord(c->stage_ev[2 * k + end], s);
-    };
-    mark(VC_STAGE_PROOF, 0, st);
-    mark(VC_STAGE_SETUP, 0, st);
-    launch_setup(G, c->zd_off, st);
-    mark(VC_STAGE_SETUP, 1, st);
-    cudaEventRecord(c->ev_fork, st);
-    // helper A: eq tables and product weights (need the coins only)
-    cudaStreamWaitEvent(sa, c->ev_fork, 0);
-    mark(VC_STAGE_TABLES, 0, sa);
-    launch_eqtabs(c->d_eq_prove, (int)c->eq_prove.size(), sa);
-    launch_prep_prod(G, c->d_scis, c->d_pwaves, (int)c->pwaves.size(), sa);
-    mark(VC_STAGE_TABLES, 1, sa);
-    cudaEventRecord(c->ev_tables, sa);
-    // caller's stream: evaluation
-    mark(VC_STAGE_EVAL, 0, st);
-    enqueue_eval(c, G, st);
-    mark(VC_STAGE_EVAL, 1, st);
-    cudaEventRecord(c->ev_eval, st);
-    // helper A: product-weighted waves
-    cudaStreamWaitEvent(sa, c->ev_eval, 0);
-    for (size_t w = 0; w < c->p_items.size() || w < 2; w++) {
-        if (w < 2) mark(w == 0 ? VC_STAGE_PROD0 : VC_STAGE_PRODN, 0, sa);
-        if (w < c->p_items.size())
-            launch_sc_prod(G, c->d_pwaves, c->d_p_items[w], (int)c->p_items[w].size(), c->partials, sa);
-        if (w == 0) mark(VC_STAGE_PROD0, 1, sa);
-    }
-    mark(VC_STAGE_PRODN, 1, sa);
-    cudaEventRecord(c->ev_prod, sa);
-    // caller's stream: line reductions, then the wiring tables (they need v1 = q(0))
-    mark(VC_STAGE_LINE, 0, st);
-    for (size_t w = 0; w < c->line_items.size(); w++)
-        launch_line_wave(G, c->d_lw, c->d_line_items[w], (int)c->line_items[w].size(), st);
-    launch_build23(G, c->d_build_off, (int)c->d, c->build_blocks, st);
-    mark(VC_STAGE_LINE, 1, st);
-    cudaEventRecord(c->ev_build, st);
-    // helper B: general waves (after the tables they read)
-    cudaStreamWaitEvent(sb, c->ev_eval, 0);
-    cudaStreamWaitEvent(sb, c->ev_tables, 0);
-    if (c->has_tab) cudaStreamWaitEvent(sb, c->ev_build, 0);
-    for (size_t w = 0; w < c->g_items.size() || w < 2; w++) {
-        if (w < 2) mark(w == 0 ? VC_STAGE_GEN0 : VC_STAGE_GENN, 0, sb);
-        if (w < c->g_items.size())
-            launch_sc_gen(G, c->d_gwaves, c->d_g_items[w], (int)c->g_items[w].size(), c->partials, sb);
-        if (w == 0) mark(VC_STAGE_GEN0, 1, sb);
-    }
-    mark(VC_STAGE_GENN, 1, sb);
-    cudaEventRecord(c->ev_gen, sb);
-    // join
-    cudaStreamWaitEvent(st, c->ev_prod, 0);
-    cudaStreamWaitEvent(st, c->ev_gen, 0);
-    mark(VC_STAGE_FINAL, 0, st);
-    launch_final(G, c->d_scis, c->d_rounds, (int)c->rounds.size(), c->partials, c->V[0], u64(1) << c->s[0], st);
-    mark(VC_STAGE_FINAL, 1, st);
-    mark(VC_STAGE_PROOF, 1, st);
-    return cudaGetLastError();
+    cudaError_t e = queue_status(c, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return VC_ECUDA;
+    return decode_status(c);
 }
 
 extern "C" vc_status vc_prove(vc_circuit *c, const uint64_t *inputs, uint64_t seed, uint64_t *transcript,
@@ -753,7 +1090,9 @@ extern "C" vc_status vc_prove(vc_circuit *c, const uint64_t *inputs, uint64_t se
     cudaError_t e = cudaMemcpyAsync(c->V[c->d], inputs, nin * sizeof(u64),
                                     ki ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return VC_ECUDA;
-    e = enqueue_prove(c, seed, kt ? transcript : c->d_tr, st);
+    launch_params(c->d_G, seed, kt ? transcript : c->d_tr, st);
+    e = plan_launch(c->P, st);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return VC_ECUDA;
     if (!kt) {
         e = cudaMemcpyAsync(transcript, c->d_tr, c->tr_len * sizeof(u64), cudaMemcpyDeviceToHost, st);
@@ -782,7 +1121,11 @@ extern "C" vc_status vc_evaluate(vc_circuit *c, const uint64_t *inputs, uint64_t
                                     ki ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return VC_ECUDA;
     launch_check_canonical(c->V[c->d], nin, c->G.status, st);
-    enqueue_eval(c, c->G, st);
+    const Plan &P = c->P;
+    for (size_t k = 0; k < P.seg_items.size(); k++) {
+        launch_eval_segs(P.d_G, P.d_segs, P.d_seg_items[k], (int)P.seg_items[k].size(), st);
+        launch_eval_layers(P.d_G, P.d_levs, P.d_lev_items[k], (int)P.lev_items[k].size(), st);
+    }
     e = cudaMemcpyAsync(outputs, c->V[0], (u64(1) << c->s[0]) * sizeof(u64),
                         ko ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -813,16 +1156,16 @@ extern "C" vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t s
         dtr = c->d_tr;
     }
     if (e != cudaSuccess) return VC_ECUDA;
-    Globals G = c->G;
-    G.seed = seed;
-    G.tr = nullptr;
-    launch_setup(G, c->zd_off, st);
+    launch_params(c->d_G, seed, c->d_tr, st);
+    launch_setup(c->d_G, 1, st);
     launch_eqtabs(c->d_eq_verify, (int)c->eq_verify.size(), st);
     VerifyDev Vd = c->Vd;
     Vd.tr = dtr;
     Vd.inputs = din;
+    e = cudaMemsetAsync(c->d_result, 0, 8 * sizeof(u64), st);
+    if (e != cudaSuccess) return VC_ECUDA;
     Vd.accept_out = ka ? accept : nullptr;
-    launch_verify(G, Vd, c->tzd, c->L[0].tz, c->d_explicit_layers, (int)c->explicit_layers.size(), st);
+    launch_verify(c->G, Vd, c->tzd, c->L[0].tz, c->d_explicit_layers, (int)c->explicit_layers.size(), st);
     if (ka && ki && kt) return cudaGetLastError() == cudaSuccess ? VC_OK : VC_ECUDA;
     e = cudaMemcpyAsync(c->h_pinned + 8, c->d_result, 4 * sizeof(u64), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -836,15 +1179,17 @@ extern "C" vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t s
 extern "C" vc_status vc_circuit_set_stage_events(vc_circuit *c, void *const *events)
 {
     if (!c) return VC_EINVAL;
-    if (!events) {
-        c->stage_on = false;
-        return VC_OK;
+    if (events)
+        for (int k = 0; k < 2 * VC_NUM_STAGES; k++)
+            if (!events[k]) return VC_EINVAL;
+    DevGuard guard(c->device);
+    if (c->P.exec) {  // the events are part of the captured graph: capture again
+        cudaGraphExecDestroy(c->P.exec);
+        c->P.exec = nullptr;
     }
-    for (int k = 0; k < 2 * VC_NUM_STAGES; k++) {
-        if (!events[k]) return VC_EINVAL;
-        c->stage_ev[k] = (cudaEvent_t)events[k];
-    }
-    c->stage_on = true;
+    c->P.stage_on = events != nullptr;
+    if (events)
+        for (int k = 0; k < 2 * VC_NUM_STAGES; k++) c->P.stage_ev[k] = (cudaEvent_t)events[k];
     return VC_OK;
 }
 
@@ -862,13 +1207,159 @@ extern "C" vc_status vc_circuit_get_info(const vc_circuit *c, vc_circuit_info *i
     I.transcript_len = c->tr_len;
     I.gates = gates;
     I.device_bytes = c->arena_bytes;
-    // setup, eq tables, d evaluation layers, line waves, build, sum-check waves, final
-    I.prove_launches = (uint32_t)(3 + c->eval_steps.size() + c->line_items.size() + (c->build_blocks > 0 ? 1 : 0) +
-                                  (c->pwaves.empty() ? 0 : 1) + c->p_items.size() + c->g_items.size() +
-                                  (c->eq_prove.empty() ? -1 : 0));
-    I.verify_launches = (uint32_t)(3 + (c->explicit_layers.empty() ? 0 : 1) + 1);
-    I.sc0_ctas = (uint32_t)((c->p_items.empty() ? 0 : c->p_items[0].size()) +
-                            (c->g_items.empty() ? 0 : c->g_items[0].size()));
+    I.prove_launches = (uint32_t)count_launches(c->P);
+    // parameters, setup, eq tables, input/output MLE, wiring (EXPLICIT only), checks
+    I.verify_launches = (uint32_t)(5 + (c->explicit_layers.empty() ? 0 : 1));
+    I.sc0_ctas = (uint32_t)((c->P.p_items.empty() ? 0 : c->P.p_items[0].size()) +
+                            (c->P.g_items.empty() ? 0 : c->P.g_items[0].size()));
+    *info = I;
+    return VC_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------------------------
+
+extern "C" vc_status vc_batch_create(vc_circuit *const *circuits, int n, vc_batch **out)
+{
+    if (!out) return VC_EINVAL;
+    *out = nullptr;
+    if (n <= 0 || !circuits) return VC_EINVAL;
+    for (int j = 0; j < n; j++) {
+        if (!circuits[j] || circuits[j]->device != circuits[0]->device) return VC_EINVAL;
+        for (int k = 0; k < j; k++)
+            if (circuits[k] == circuits[j]) return VC_EINVAL;
+    }
+    vc_batch *b = new (std::nothrow) vc_batch();
+    if (!b) return VC_ENOMEM;
+    b->device = circuits[0]->device;
+    b->members.assign(circuits, circuits + n);
+    DevGuard guard(b->device);
+    plan_merge(b->P, b->members);
+    size_t bytes = 0;
+    {
+        Arena A;
+        plan_take(b->P, A, true);
+        A.take<CallParams>(n);
+        bytes = A.off + 256;
+    }
+    cudaError_t e = cudaMalloc(&b->arena, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return e == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA;
+    }
+    b->arena_bytes = bytes;
+    {
+        Arena A;
+        A.base = reinterpret_cast<uintptr_t>(b->arena);
+        plan_take(b->P, A, true);
+        b->d_cp = A.take<CallParams>(n);
+    }
+    std::vector<Globals> Gs;
+    for (vc_circuit *c : b->members) Gs.push_back(c->G);
+    e = upload(b->P.d_G, Gs);
+    if (e == cudaSuccess) e = plan_upload(b->P);
+    if (e == cudaSuccess) e = cudaHostAlloc(&b->h_cp, n * sizeof(CallParams), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = plan_resources(b->P);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        plan_release(b->P);
+        if (b->h_cp) cudaFreeHost(b->h_cp);
+        cudaFree(b->arena);
+        delete b;
+        return cuda_status(e);
+    }
+    *out = b;
+    return VC_OK;
+}
+
+extern "C" vc_status vc_batch_destroy(vc_batch *b)
+{
+    if (!b) return VC_OK;
+    DevGuard guard(b->device);
+    cudaDeviceSynchronize();
+    plan_release(b->P);
+    if (b->arena) cudaFree(b->arena);
+    if (b->h_cp) cudaFreeHost(b->h_cp);
+    delete b;
+    return VC_OK;
+}
+
+extern "C" vc_status vc_batch_prove(vc_batch *b, const uint64_t *const *inputs, const uint64_t *seeds,
+                                    uint64_t *const *transcripts, void *stream)
+{
+    if (!b || !inputs || !seeds || !transcripts) return VC_EINVAL;
+    DevGuard guard(b->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)b->members.size();
+    std::vector<int> kt(n);
+    bool all_dev = true;
+    for (int j = 0; j < n; j++) {
+        vc_circuit *c = b->members[j];
+        if (!inputs[j] || !transcripts[j]) return VC_EINVAL;
+        const int ki = ptr_kind(inputs[j], c->device);
+        kt[j] = ptr_kind(transcripts[j], c->device);
+        if (ki < 0 || kt[j] < 0) return VC_EINVAL;
+        all_dev = all_dev && ki && kt[j];
+    }
+    // the pinned parameter table is rewritten only after the previous call's copy of it finished
+    if (cudaEventSynchronize(b->P.ev_params) != cudaSuccess) return VC_ECUDA;
+    for (int j = 0; j < n; j++) {
+        vc_circuit *c = b->members[j];
+        const u64 nin = u64(1) << c->s[c->d];
+        if (cudaMemcpyAsync(c->V[c->d], inputs[j], nin * sizeof(u64),
+                            ptr_kind(inputs[j], c->device) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            st) != cudaSuccess)
+            return VC_ECUDA;
+        b->h_cp[j].seed = seeds[j];
+        b->h_cp[j].tr = kt[j] ? transcripts[j] : c->d_tr;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_cp, b->h_cp, n * sizeof(CallParams), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->P.ev_params, st);
+    if (e != cudaSuccess) return VC_ECUDA;
+    launch_params_batch(b->P.d_G, b->d_cp, n, st);
+    e = plan_launch(b->P, st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return VC_ECUDA;
+    for (int j = 0; j < n; j++) {
+        if (kt[j]) continue;
+        vc_circuit *c = b->members[j];
+        if (cudaMemcpyAsync(transcripts[j], c->d_tr, c->tr_len * sizeof(u64), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess)
+            return VC_ECUDA;
+    }
+    if (all_dev) return VC_OK;
+    return vc_batch_sync(b, stream);
+}
+
+extern "C" vc_status vc_batch_sync(vc_batch *b, void *stream)
+{
+    if (!b) return VC_EINVAL;
+    DevGuard guard(b->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    for (vc_circuit *c : b->members)
+        if (queue_status(c, st) != cudaSuccess) return VC_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return VC_ECUDA;
+    vc_status worst = VC_OK;
+    for (vc_circuit *c : b->members) {
+        const vc_status s = decode_status(c);
+        if (s != VC_OK) worst = s;
+    }
+    return worst;
+}
+
+extern "C" vc_status vc_batch_get_info(const vc_batch *b, vc_batch_info *info)
+{
+    if (!b || !info) return VC_EINVAL;
+    vc_batch_info I{};
+    I.n_members = (uint32_t)b->members.size();
+    I.prove_launches = (uint32_t)count_launches(b->P);
+    I.device_bytes = b->arena_bytes;
+    u64 gates = 0;
+    for (const vc_circuit *c : b->members)
+        for (u32 i = 0; i < c->d; i++) gates += u64(1) << c->s[i];
+    I.gates = gates;
     *info = I;
     return VC_OK;
 }
@@ -877,37 +1368,19 @@ extern "C" vc_status vc_prove_batch(vc_circuit *const *circuits, const uint64_t 
                                     const uint64_t *seeds, uint64_t *const *transcripts, int n, void *stream)
 {
     if (n < 0 || (n > 0 && (!circuits || !inputs || !seeds || !transcripts))) return VC_EINVAL;
-    bool all_dev = true;
-    for (int j = 0; j < n; j++) {
-        vc_circuit *c = circuits[j];
-        if (!c || !inputs[j] || !transcripts[j]) return VC_EINVAL;
-        for (int k = 0; k < j; k++)
-            if (circuits[k] == c) return VC_EINVAL;
-    }
-    cudaStream_t st = (cudaStream_t)stream;
-    for (int j = 0; j < n; j++) {
-        vc_circuit *c = circuits[j];
-        DevGuard guard(c->device);
-        const int ki = ptr_kind(inputs[j], c->device), kt = ptr_kind(transcripts[j], c->device);
-        if (ki < 0 || kt < 0) return VC_EINVAL;
-        all_dev = all_dev && ki && kt;
-        const u64 nin = u64(1) << c->s[c->d];
-        cudaError_t e = cudaMemcpyAsync(c->V[c->d], inputs[j], nin * sizeof(u64),
-                                        ki ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = enqueue_prove(c, seeds[j], kt ? transcripts[j] : c->d_tr, st);
-        if (e == cudaSuccess && !kt)
-            e = cudaMemcpyAsync(transcripts[j], c->d_tr, c->tr_len * sizeof(u64), cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) return VC_ECUDA;
-    }
-    if (all_dev) return VC_OK;
-    vc_status worst = VC_OK;
-    for (int j = 0; j < n; j++) {
-        DevGuard guard(circuits[j]->device);
-        vc_status s = read_status_and_clear(circuits[j], st);
-        if (s != VC_OK) worst = s;
-    }
-    return worst;
+    if (n == 0) return VC_OK;
+    vc_batch *b = nullptr;
+    vc_status s = vc_batch_create(circuits, n, &b);
+    if (s != VC_OK) return s;
+    s = vc_batch_prove(b, inputs, seeds, transcripts, stream);
+    if (s == VC_OK) s = vc_batch_sync(b, stream);
+    vc_batch_destroy(b);
+    return s;
 }
+
+// ---------------------------------------------------------------------------------------
+// Field arithmetic checks
+// ---------------------------------------------------------------------------------------
 
 extern "C" vc_status vc_field_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t n, void *stream)
 {

@@ -56,6 +56,11 @@ class CircuitInfo(ctypes.Structure):
                 ("pad", ctypes.c_uint32)]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n_members", ctypes.c_uint32), ("prove_launches", ctypes.c_uint32),
+                ("device_bytes", ctypes.c_uint64), ("gates", ctypes.c_uint64)]
+
+
 _lock = threading.Lock()
 _lib = None
 _shapes = {}  # handle -> (inputs, outputs, transcript length), for size checks
@@ -87,6 +92,11 @@ def lib():
             L.vc_verify.argtypes = [vp, vp, ctypes.c_uint64, vp, ctypes.POINTER(ctypes.c_int), vp]
             L.vc_prove_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), _u64p, ctypes.POINTER(vp),
                                          ctypes.c_int, vp]
+            L.vc_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
+            L.vc_batch_destroy.argtypes = [vp]
+            L.vc_batch_prove.argtypes = [vp, ctypes.POINTER(vp), _u64p, ctypes.POINTER(vp), vp]
+            L.vc_batch_sync.argtypes = [vp, vp]
+            L.vc_batch_get_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
             L.vc_field_mul.argtypes = [vp, vp, vp, ctypes.c_uint64, vp]
             L.vc_field_mul_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                             ctypes.POINTER(ctypes.c_double)]
@@ -99,7 +109,8 @@ def lib():
             for name in ("vc_circuit_create", "vc_circuit_destroy", "vc_transcript_len", "vc_circuit_bytes",
                          "vc_evaluate", "vc_prove", "vc_circuit_sync", "vc_verify", "vc_prove_batch",
                          "vc_field_mul", "vc_field_mul_rate", "vc_circuit_set_stage_events",
-                         "vc_circuit_get_info"):
+                         "vc_circuit_get_info", "vc_batch_create", "vc_batch_destroy", "vc_batch_prove",
+                         "vc_batch_sync", "vc_batch_get_info"):
                 getattr(L, name).restype = st
             _lib = L
     return _lib
@@ -283,6 +294,49 @@ def vc_prove_batch(handles, inputs, seeds, transcripts, stream=None, device: int
     trs = (ctypes.c_void_p * n)(*[_ptr(t) for t in transcripts])
     _check(lib().vc_prove_batch(hs, ins, sd, trs, n, _stream(stream, device)), "vc_prove_batch")
     return transcripts
+
+
+_batches = {}  # batch handle -> member handles
+
+
+def vc_batch_create(handles):
+    """Returns an opaque batch handle (int) over distinct circuit handles."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * max(n, 1))(*handles)
+    b = ctypes.c_void_p()
+    _check(lib().vc_batch_create(hs, n, ctypes.byref(b)), "vc_batch_create")
+    _batches[b.value] = list(handles)
+    return b.value
+
+
+def vc_batch_destroy(b):
+    _check(lib().vc_batch_destroy(b), "vc_batch_destroy")
+    _batches.pop(b, None)
+
+
+def vc_batch_prove(b, inputs, seeds, transcripts, stream=None, device: int = 0):
+    handles = _batches[b]
+    n = len(handles)
+    if not (len(inputs) == len(seeds) == len(transcripts) == n):
+        raise ValueError("one input, seed and transcript per member")
+    for h, x, t in zip(handles, inputs, transcripts):
+        _need(x, _shapes[h][0], "inputs")
+        _need(t, _shapes[h][2], "transcript")
+    ins = (ctypes.c_void_p * n)(*[_ptr(x) for x in inputs])
+    sd = (ctypes.c_uint64 * n)(*[s & 0xFFFFFFFFFFFFFFFF for s in seeds])
+    trs = (ctypes.c_void_p * n)(*[_ptr(t) for t in transcripts])
+    _check(lib().vc_batch_prove(b, ins, sd, trs, _stream(stream, device)), "vc_batch_prove")
+    return transcripts
+
+
+def vc_batch_sync(b, stream=None, device: int = 0):
+    _check(lib().vc_batch_sync(b, _stream(stream, device)), "vc_batch_sync")
+
+
+def vc_batch_get_info(b) -> dict:
+    info = BatchInfo()
+    _check(lib().vc_batch_get_info(b, ctypes.byref(info)), "vc_batch_get_info")
+    return {name: getattr(info, name) for name, _ in BatchInfo._fields_}
 
 
 def vc_field_mul(a, b, out, stream=None, device: int = 0):

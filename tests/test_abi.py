@@ -59,3 +59,18 @@ def test_gate_counts():
     # F2 at n = 2^20: 2^20 squaring gates and 2^20 - 1 addition gates
     assert circuits.non_input_gates(circuits.f2(20)[0]) == 2 * (1 << 20) - 1
     assert circuits.non_input_gates(circuits.matmult(7)[0]) == (1 << 21) + (1 << 21) - (1 << 14)
+
+
+def test_batch_arguments_rejected_without_device(libvc):
+    with pytest.raises(vc.VcError) as e:
+        vc.vc_batch_create([])
+    assert e.value.status == vc.VC_EINVAL
+    with pytest.raises(vc.VcError) as e:
+        vc.vc_batch_create([None])
+    assert e.value.status == vc.VC_EINVAL
+    assert libvc.vc_batch_get_info(None, None) == vc.VC_EINVAL
+    assert libvc.vc_batch_sync(None, None) == vc.VC_EINVAL
+    assert libvc.vc_batch_prove(None, None, None, None, None) == vc.VC_EINVAL
+    assert libvc.vc_batch_destroy(None) == vc.VC_OK
+    assert libvc.vc_prove_batch(None, None, None, None, 0, None) == vc.VC_OK
+    assert libvc.vc_prove_batch(None, None, None, None, -1, None) == vc.VC_EINVAL
