@@ -166,6 +166,32 @@ __device__ __forceinline__ u64 wfold(u64 u0, u64 u1, u32 r0, u32 r1)
     return wred(t);
 }
 
+// u0 + a d for u0 in W, d < 2^62.6 (a lazy difference u1 + 2p - u0 of W
+// values) and canonical a = a1 2^31 + a0: the limb scheme of wfold.
+__device__ __forceinline__ u64 wlin1(u64 u0, u64 d, u32 a0, u32 a1)
+{
+    const u32 d0 = (u32)d & 0x7FFFFFFFu, d1 = (u32)(d >> 31);
+    const u64 A00 = u0 + (u64)a0 * d0;
+    const u64 AM = (u64)a0 * d1 + (u64)a1 * d0;
+    const u64 A11 = (u64)a1 * d1;
+    const u64 t = (A11 << 1) + (AM >> 30) + ((AM & 0x3FFFFFFFull) << 31) + (A00 & FP_P) + (A00 >> 61);
+    return wred(t);
+}
+
+// u0 + a d + b e (d, e < 2^62.6; a, b canonical as 31/30-bit limbs).  Bounds:
+// A00 < 2^61 + 8 + 2^63.6; AM < 2 (2^62.6 + 2^61) < 2^64; 2 A11 < 2^63.6;
+// the sum t stays below 2^64.
+__device__ __forceinline__ u64 wlin2(u64 u0, u64 d, u64 e, u32 a0, u32 a1, u32 b0, u32 b1)
+{
+    const u32 d0 = (u32)d & 0x7FFFFFFFu, d1 = (u32)(d >> 31);
+    const u32 e0 = (u32)e & 0x7FFFFFFFu, e1 = (u32)(e >> 31);
+    const u64 A00 = wred(u0 + (u64)a0 * d0) + (u64)b0 * e0;
+    const u64 AM = (u64)a0 * d1 + (u64)a1 * d0 + (u64)b0 * e1 + (u64)b1 * e0;
+    const u64 A11 = (u64)a1 * d1 + (u64)b1 * e1;
+    const u64 t = (A11 << 1) + (AM >> 30) + ((AM & 0x3FFFFFFFull) << 31) + (A00 & FP_P) + (A00 >> 61);
+    return wred(t);
+}
+
 __device__ __forceinline__ void limbs31(u64 r, u32 &r0, u32 &r1)
 {
     r0 = (u32)r & 0x7FFFFFFFu;

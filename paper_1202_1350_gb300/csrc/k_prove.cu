@@ -199,6 +199,20 @@ void launch_eval_layers(const Globals *Gs, const LayerEval *le, const Item *item
 
 extern __shared__ u64 ev_dyn[];
 
+// Gate k of a block-local layer: operand positions within the block below
+// and the operation.
+__device__ __forceinline__ void local_gate(u32 kind, u32 k, u32 &a, u32 &b, u32 &mul)
+{
+    mul = 1;
+    switch (kind) {
+    case W_SQUARE: a = k; b = k; break;
+    case W_TREE: a = 2 * k; b = 2 * k + 1; mul = 0; break;
+    case W_F0_FIRST: a = k >> 1; b = k >> 1; mul = (k & 1) ? 0 : 1; break;
+    case W_F0_PAIR: a = k; b = k & ~1u; break;
+    default: a = 2 * k + 1; b = 2 * k + 1; break;  // W_F0_FINAL
+    }
+}
+
 __global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const EvalSeg *segs, const Item *items)
 {
     u64 *bufA = ev_dyn, *bufB = ev_dyn + EV_MAXB;
@@ -210,13 +224,24 @@ __global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const Eva
     const LayerDev &Lin = Ls[S.i_hi];
     const u32 s_in = Lin.sn;
     u32 B = 1u << S.c;  // block size of the current (upper) layer
+    constexpr int R = EV_MAXB / EV_NT;
     {
+        // all loads of the chunk are issued before any store
         const u64 *src = Lin.Vn + ((u64)chunk << S.c);
+        u64 r[R];
+#pragma unroll
+        for (int j = 0; j < R; j++) {
+            const u32 k = threadIdx.x + j * EV_NT;
+            r[j] = (k < B) ? src[k] : 0;
+        }
         bool bad = false;
-        for (u32 k = threadIdx.x; k < B; k += EV_NT) {
-            const u64 v = src[k];
-            bad |= (v >= FP_P);
-            bufA[k] = v;
+#pragma unroll
+        for (int j = 0; j < R; j++) {
+            const u32 k = threadIdx.x + j * EV_NT;
+            if (k < B) {
+                bad |= (r[j] >= FP_P);
+                bufA[k] = r[j];
+            }
         }
         if (S.check_input && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
             atomicOr(G.status, ST_BAD_INPUT);
@@ -228,14 +253,8 @@ __global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const Eva
         const u32 Bo = (L.s >= L.sn) ? (B << (L.s - L.sn)) : (B >> (L.sn - L.s));
         const u64 gbase = (u64)chunk * Bo;
         for (u32 k = threadIdx.x; k < Bo; k += EV_NT) {
-            u32 a, b, mul = 1;
-            switch (L.kind) {
-            case W_SQUARE: a = k; b = k; break;
-            case W_TREE: a = 2 * k; b = 2 * k + 1; mul = 0; break;
-            case W_F0_FIRST: a = k >> 1; b = k >> 1; mul = (k & 1) ? 0 : 1; break;
-            case W_F0_PAIR: a = k; b = k & ~1u; break;
-            default: a = 2 * k + 1; b = 2 * k + 1; break;  // W_F0_FINAL
-            }
+            u32 a, b, mul;
+            local_gate(L.kind, k, a, b, mul);
             const u64 x = cur[a], y = cur[b];
             const u64 v = mul ? f_mul(x, y) : f_add(x, y);
             nxt[k] = v;
@@ -246,6 +265,55 @@ __global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const Eva
         B = Bo;
     }
     (void)s_in;
+    if (S.tail_lo >= S.i_lo) return;
+    // Last-CTA tail: every CTA publishes its writes and counts itself; the
+    // last one evaluates the narrow layers below the run from the whole
+    // layer i_lo (no CTA waits for another).
+    __shared__ u32 s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(S.counter, 1u) == S.nchunks - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) *S.counter = 0;
+    for (int i = (int)S.i_lo - 1; i >= (int)S.tail_lo; i--) {
+        const LayerDev &L = Ls[i];
+        const u32 Bo = 1u << L.s;
+        if (i == (int)S.i_lo - 1) {
+            // operands from the whole layer i_lo in global memory, all loads first
+            u64 xa[R], xb[R];
+#pragma unroll
+            for (int j = 0; j < R; j++) {
+                const u32 k = threadIdx.x + j * EV_NT;
+                u32 a, b, mul;
+                local_gate(L.kind, k, a, b, mul);
+                xa[j] = (k < Bo) ? __ldcg(L.Vn + a) : 0;
+                xb[j] = (k < Bo) ? __ldcg(L.Vn + b) : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < R; j++) {
+                const u32 k = threadIdx.x + j * EV_NT;
+                if (k < Bo) {
+                    u32 a, b, mul;
+                    local_gate(L.kind, k, a, b, mul);
+                    const u64 v = mul ? f_mul(xa[j], xb[j]) : f_add(xa[j], xb[j]);
+                    nxt[k] = v;
+                    L.V[k] = v;
+                }
+            }
+        } else {
+            for (u32 k = threadIdx.x; k < Bo; k += EV_NT) {
+                u32 a, b, mul;
+                local_gate(L.kind, k, a, b, mul);
+                const u64 v = mul ? f_mul(cur[a], cur[b]) : f_add(cur[a], cur[b]);
+                nxt[k] = v;
+                L.V[k] = v;
+            }
+        }
+        __syncthreads();
+        u64 *t = cur; cur = nxt; nxt = t;
+    }
 }
 
 void launch_eval_segs(const Globals *Gs, const EvalSeg *segs, const Item *items, int nitems, cudaStream_t st)
@@ -290,141 +358,150 @@ void launch_check_inputs(const Globals *Gs, const Item *items, int nitems, cudaS
 
 // --------------------------------------------------------------------------------
 // Line reduction: q(t) = V~_{i+1}(l(t)), folding V_{i+1} with coordinates
-// a_k + b_k t in coefficient form (degree grows by one per folded coordinate).
+// a_k + b_k t in coefficient form (degree grows by one per folded coordinate):
+//   out_c = A_c + a (B_c - A_c) + b (B_{c-1} - A_{c-1}),  c = 0 .. deg + 1.
+// A first-wave CTA folds LN_C0 coordinates of 2^LN_C0 entries: LN_E in
+// registers (2^LN_E consecutive entries per thread), the rest in shared
+// memory.  A later wave folds up to LN_CW coordinates of one polynomial per
+// thread.  A wave whose successor is a single chunk runs that successor in
+// the CTA that finishes last.
 // --------------------------------------------------------------------------------
 
 #define LN_NT 256
-#define LN_E 3
-#define LN_SP 32  // coefficient stride in shared memory (degree <= 31)
+#define LN_E 5
+#define LN_BUFA 4096  // shared-memory polynomial buffers (coefficients)
+#define LN_BUFB 2048
 
-// One coefficient of the fold of polynomials A (lower) and B (upper) with
-// a + b t:  out_c = A_c + a (B_c - A_c) + b (B_{c-1} - A_{c-1}).  Coefficients
-// are in W (lazy); the two products accumulate exactly in 128 bits.
-__device__ __forceinline__ u64 poly_fold_coef(const u64 *A, const u64 *B, u32 deg, u32 c, u64 a, u64 b)
+// One level of coefficient folding in registers: D+1 -> D+2 coefficients.
+template <int D>
+__device__ __forceinline__ void line_fold(const u64 (&A)[D + 1], const u64 (&B)[D + 1], u32 a0, u32 a1, u32 b0,
+                                          u32 b1, u64 (&out)[D + 2])
 {
-    acc128 acc;
-    acc.lo = (c <= deg) ? A[c] : 0;
-    acc.hi = 0;
-    if (c <= deg) mac(acc, a, B[c] + (2 * FP_P) - A[c]);
-    if (c >= 1) mac(acc, b, B[c - 1] + (2 * FP_P) - A[c - 1]);
-    return acc_red(acc);
+    u64 d[D + 1];
+#pragma unroll
+    for (int c = 0; c <= D; c++) d[c] = B[c] + (2 * FP_P) - A[c];
+    out[0] = wlin1(A[0], d[0], a0, a1);
+#pragma unroll
+    for (int c = 1; c <= D; c++) out[c] = wlin2(A[c], d[c], d[c - 1], a0, a1, b0, b1);
+    out[D + 1] = wlin1(0, d[D], b0, b1);
 }
 
-extern __shared__ u64 ln_dyn[];
-
-__global__ void __launch_bounds__(LN_NT) k_line_wave(const Globals *Gs, const LineWaveDev *waves, const Item *items)
+// 8 consecutive entries -> one cubic (coordinates 0, 1, 2 of the run).
+__device__ __forceinline__ void line_run8(const u64 *v, const u32 *la, const u32 *lb, u64 (&out)[4])
 {
-    const Item it = items[blockIdx.x];
-    const LineWaveDev W = waves[it.wave];
-    const Globals &G = Gs[W.circ];
+    u64 l1[4][2];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const u64 dd = v[2 * q + 1] + (2 * FP_P) - v[2 * q];
+        l1[q][0] = wlin1(v[2 * q], dd, la[0], la[1]);
+        l1[q][1] = wlin1(0, dd, lb[0], lb[1]);
+    }
+    u64 l2[2][3];
+    line_fold<1>(l1[0], l1[1], la[2], la[3], lb[2], lb[3], l2[0]);
+    line_fold<1>(l1[2], l1[3], la[2], la[3], lb[2], lb[3], l2[1]);
+    line_fold<2>(l2[0], l2[1], la[4], la[5], lb[4], lb[5], out);
+}
+
+// Coefficient `c` of the fold of polynomials A, B (degree deg, W values).
+__device__ __forceinline__ u64 line_coef(const u64 *A, const u64 *B, u32 deg, u32 c, const u32 *la, const u32 *lb)
+{
+    const u64 dc = (c <= deg) ? B[c] + (2 * FP_P) - A[c] : 0;
+    const u64 dm = (c >= 1) ? B[c - 1] + (2 * FP_P) - A[c - 1] : 0;
+    const u64 ac = (c <= deg) ? A[c] : 0;
+    return wlin2(ac, dc, dm, la[0], la[1], lb[0], lb[1]);
+}
+
+// One chunk of one line wave, by the whole CTA.
+__device__ void line_chunk(const Globals &G, const LineWaveDev &W, u32 chunk, u64 *bufA, u64 *bufB)
+{
+    __shared__ u32 s_la[32][2], s_lb[32][2];  // limbs of a_k and b_k for this wave's coordinates
     const u32 tid = threadIdx.x;
-    __shared__ u64 sa[32], sb[32];
     if (tid < W.nl) {
-        u64 a = G.chal[W.a_off + W.l0 + tid];
-        sa[tid] = a;
-        sb[tid] = f_sub(G.chal[W.b_off + W.l0 + tid], a);
+        const u64 a = G.chal[W.a_off + W.l0 + tid];
+        const u64 b = f_sub(G.chal[W.b_off + W.l0 + tid], a);
+        limbs31(a, s_la[tid][0], s_la[tid][1]);
+        limbs31(b, s_lb[tid][0], s_lb[tid][1]);
     }
     __syncthreads();
-    u64 *bufA = ln_dyn;                       // LN_NT polys
-    u64 *bufB = ln_dyn + LN_NT * LN_SP;       // LN_NT / 2 polys
-    u32 m;        // polys in the current level
-    u32 deg;      // their degree
-    u32 done;     // coordinates of this wave already folded
+    u32 m, deg, k0;  // polynomials in bufA, their degree, coordinates already folded
     if (W.l0 == 0) {
-        // Entries are field values (degree 0).  Each thread folds a run of 2^e
-        // consecutive entries in registers.
         const u32 e = (W.nl >= LN_E) ? LN_E : 0;
         const u32 na = 1u << (W.nl - e);
-        const u64 base = (u64)it.chunk << W.nl;
-        bool bad = false;
+        const u64 base = (u64)chunk << W.nl;
         if (tid < na) {
             if (e == LN_E) {
-                u64 v[8];
+                u64 v[32];
                 const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(W.in + base + ((u64)tid << LN_E));
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    ulonglong2 w = src[q];
+                for (int q = 0; q < 16; q++) {
+                    const ulonglong2 w = src[q];
                     v[2 * q] = w.x;
                     v[2 * q + 1] = w.y;
                 }
+                u32 la[10], lb[10];
 #pragma unroll
-                for (int q = 0; q < 8; q++) bad |= (v[q] >= FP_P);
-                // level 1: 4 linear polys c0 + c1 t
-                u64 c1[4][2];
-                {
-                    const u64 a = sa[0], b = sb[0];
-#pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        u64 dd = f_sub(v[2 * q + 1], v[2 * q]);
-                        c1[q][0] = f_add(v[2 * q], f_mul(a, dd));
-                        c1[q][1] = f_mul(b, dd);
-                    }
+                for (int k = 0; k < 5; k++) {
+                    la[2 * k] = s_la[k][0];
+                    la[2 * k + 1] = s_la[k][1];
+                    lb[2 * k] = s_lb[k][0];
+                    lb[2 * k + 1] = s_lb[k][1];
                 }
-                u64 c2[2][3];
-                {
-                    const u64 a = sa[1], b = sb[1];
+                u64 c0[4], c1[4], c2[4], c3[4];
+                line_run8(v, la, lb, c0);
+                line_run8(v + 8, la, lb, c1);
+                line_run8(v + 16, la, lb, c2);
+                line_run8(v + 24, la, lb, c3);
+                u64 q01[5], q23[5], p[6];
+                line_fold<3>(c0, c1, la[6], la[7], lb[6], lb[7], q01);
+                line_fold<3>(c2, c3, la[6], la[7], lb[6], lb[7], q23);
+                line_fold<4>(q01, q23, la[8], la[9], lb[8], lb[9], p);
 #pragma unroll
-                    for (int q = 0; q < 2; q++) {
-                        const u64 *A = c1[2 * q], *B = c1[2 * q + 1];
-#pragma unroll
-                        for (int c = 0; c < 3; c++) c2[q][c] = poly_fold_coef(A, B, 1, c, a, b);
-                    }
-                }
-                u64 *dst = bufA + tid * LN_SP;
-                {
-                    const u64 a = sa[2], b = sb[2];
-#pragma unroll
-                    for (int c = 0; c < 4; c++) dst[c] = poly_fold_coef(c2[0], c2[1], 2, c, a, b);
-                }
+                for (int c = 0; c < 6; c++) bufA[tid * 6 + c] = p[c];
             } else {
-                u64 x = W.in[base + tid];
-                bad |= (x >= FP_P);
-                bufA[tid * LN_SP] = x;
+                bufA[tid] = W.in[base + tid];
             }
         }
-        if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(G.status, ST_BAD_INPUT);
         m = na;
         deg = e;
-        done = e;
+        k0 = e;
     } else {
-        // Entries are polynomials of degree l0 from the previous wave: each
-        // thread loads two and folds them with the first coordinate.
-        const u32 din = W.l0;
-        const u32 npoly = 1u << W.nl;
-        const u64 base = (u64)it.chunk << W.nl;
-        const u32 half = npoly >> 1;
-        for (u32 idx = tid; idx < half * (din + 2); idx += LN_NT) {
-            const u32 j = idx / (din + 2), c = idx % (din + 2);
-            const u64 *A = W.in + (base + 2 * j) * (din + 1);
-            const u64 *B = A + (din + 1);
-            bufA[j * LN_SP + c] = poly_fold_coef(A, B, din, c, sa[0], sb[0]);
+        // polynomials of degree l0 from the previous wave (written by other
+        // CTAs of this launch when run as a tail: read through L2)
+        const u32 din = W.l0, npoly = 1u << W.nl, half = npoly >> 1, C = din + 2;
+        const u64 *in = W.in + ((u64)chunk << W.nl) * (din + 1);
+        for (u32 idx = tid; idx < half * C; idx += LN_NT) {
+            const u32 j = idx / C, c = idx - j * C;
+            const u64 *A = in + (u64)(2 * j) * (din + 1), *B = A + (din + 1);
+            const u64 dc = (c <= din) ? __ldcg(B + c) + (2 * FP_P) - __ldcg(A + c) : 0;
+            const u64 dm = (c >= 1) ? __ldcg(B + c - 1) + (2 * FP_P) - __ldcg(A + c - 1) : 0;
+            const u64 ac = (c <= din) ? __ldcg(A + c) : 0;
+            bufA[j * C + c] = wlin2(ac, dc, dm, s_la[0][0], s_la[0][1], s_lb[0][0], s_lb[0][1]);
         }
         m = half;
         deg = din + 1;
-        done = 1;
-        if (W.nl == 0) {  // cannot happen (waves after the first fold >= 1 coordinate)
-            m = 1;
-        }
+        k0 = 1;
     }
     __syncthreads();
-    // Remaining coordinates of this wave, in shared memory (ping-pong A <-> B).
     u64 *cur = bufA, *nxt = bufB;
-    for (u32 k = done; k < W.nl; k++) {
-        const u32 half = m >> 1;
-        for (u32 idx = tid; idx < half * (deg + 2); idx += LN_NT) {
-            const u32 j = idx / (deg + 2), c = idx % (deg + 2);
-            nxt[j * LN_SP + c] = poly_fold_coef(cur + (2 * j) * LN_SP, cur + (2 * j + 1) * LN_SP, deg, c, sa[k], sb[k]);
+    for (u32 k = k0; k < W.nl; k++) {
+        const u32 half = m >> 1, C = deg + 2;
+        for (u32 idx = tid; idx < half * C; idx += LN_NT) {
+            const u32 j = idx / C, c = idx - j * C;
+            nxt[j * C + c] = line_coef(cur + (2 * j) * (deg + 1), cur + (2 * j + 1) * (deg + 1), deg, c, s_la[k],
+                                       s_lb[k]);
         }
         __syncthreads();
-        u64 *t = cur; cur = nxt; nxt = t;
+        u64 *t = cur;
+        cur = nxt;
+        nxt = t;
         m = half;
         deg += 1;
     }
-    // cur[0..deg] is this chunk's polynomial.
+    // cur[0..deg] is this chunk's polynomial
     if (!W.last) {
-        for (u32 c = tid; c <= deg; c += LN_NT) W.out[(u64)it.chunk * (deg + 1) + c] = cur[c];
+        for (u32 c = tid; c <= deg; c += LN_NT) W.out[(u64)chunk * (deg + 1) + c] = cur[c];
     } else {
-        // q(t) for t = 0..n by Horner; q(0) = V~_{i+1}(r1) feeds phase 3.
+        // q(t) for t = 0..n by Horner; q(0) = V~_{i+1}(r1) feeds phase 3
         for (u32 t = tid; t <= W.n; t += LN_NT) {
             u64 acc = cur[deg];
             for (int c = (int)deg - 1; c >= 0; c--) acc = wred(wmul(acc, (u64)t) + cur[c]);
@@ -434,16 +511,38 @@ __global__ void __launch_bounds__(LN_NT) k_line_wave(const Globals *Gs, const Li
     }
 }
 
+extern __shared__ u64 ln_dyn[];
+
+__global__ void __launch_bounds__(LN_NT, 2) k_line_wave(const Globals *Gs, const LineWaveDev *waves, const Item *items)
+{
+    const Item it = items[blockIdx.x];
+    const LineWaveDev &W = waves[it.wave];
+    const Globals &G = Gs[W.circ];
+    u64 *bufA = ln_dyn, *bufB = ln_dyn + LN_BUFA;
+    line_chunk(G, W, it.chunk, bufA, bufB);
+    if (!W.tail) return;
+    // the CTA that finishes last runs the next wave (one chunk); no CTA waits
+    __shared__ u32 s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(W.counter, 1u) == W.nchunks - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) *W.counter = 0;
+    line_chunk(G, waves[it.wave + 1], 0, bufA, bufB);
+}
+
 void launch_line_wave(const Globals *Gs, const LineWaveDev *lw, const Item *items, int nitems, cudaStream_t st)
 {
     if (nitems > 0)
-        k_line_wave<<<nitems, LN_NT, (size_t)(LN_NT + LN_NT / 2) * LN_SP * sizeof(u64), st>>>(Gs, lw, items);
+        k_line_wave<<<nitems, LN_NT, (size_t)(LN_BUFA + LN_BUFB) * sizeof(u64), st>>>(Gs, lw, items);
 }
 
 void prove_kernels_init()
 {
     cudaFuncSetAttribute(k_line_wave, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)((LN_NT + LN_NT / 2) * LN_SP * sizeof(u64)));
+                         (int)((LN_BUFA + LN_BUFB) * sizeof(u64)));
     cudaFuncSetAttribute(k_eval_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * EV_MAXB * sizeof(u64)));
 }
 

@@ -137,6 +137,9 @@ struct LineWaveDev {
     u32 a_off;      // a_k = chal[a_off + k] (= r1), b_k = chal[b_off + k] - a_k
     u32 b_off;
     u64 tr_q;
+    u32 tail;       // the next descriptor (one chunk) is run by this wave's last CTA
+    u32 pad;
+    u32 *counter;   // CTAs of this wave that finished (tail only; reset by the last)
 };
 
 // Work item of a merged launch: which wave descriptor and which chunk.
@@ -179,13 +182,19 @@ struct Globals {
 };
 
 // A run of block-local layers evaluated by one launch (k_eval_seg): layers
-// i_hi down to i_lo, chunks of 2^c entries of layer i_hi + 1 per CTA.
+// i_hi down to i_lo, chunks of 2^c entries of layer i_hi + 1 per CTA.  The
+// CTA that finishes last then evaluates layers i_lo - 1 down to tail_lo
+// alone (tail_lo == i_lo: no tail); `counter` counts finished CTAs and is
+// reset by the last one.
 struct EvalSeg {
     u32 circ;
     u32 i_hi, i_lo;
     u32 c;
     u32 nchunks;
     u32 check_input;  // the run's input layer is the circuit's input layer
+    u32 tail_lo;
+    u32 pad;
+    u32 *counter;
 };
 
 // A layer evaluated on its own (MATMULT or EXPLICIT wiring).

@@ -25,8 +25,8 @@ namespace {
 
 constexpr u32 PR_CHUNK_LOG = PR_M + 8;  // entries folded by one PROD CTA (256 threads x 2^PR_M)
 constexpr u32 GN_CHUNK_LOG = GN_M + 7;  // entries folded by one GEN CTA (128 threads x 2^GN_M)
-constexpr u32 LN_CHUNK0_LOG = 11;       // coordinates folded by the first line wave
-constexpr u32 LN_CHUNKW_LOG = 9;        // coordinates folded by later line waves
+constexpr u32 LN_CHUNK0_LOG = 13;       // coordinates folded by the first line wave (LN_E + 8)
+constexpr u32 LN_CHUNKW_LOG = 8;        // coordinates folded by later line waves (one polynomial per thread)
 
 // Which layers' phase-2/3 tables are built by k_build23 (the rest are formed
 // on the fly or never stored).
@@ -263,9 +263,14 @@ static void plan_eval(vc_circuit *c)
         S.c = (u32)cl;
         S.nchunks = 1u << (s_in - cl);
         S.check_input = (u32)(i + 1 == (int)c->d);
+        // tail: narrow local layers below the run (outputs <= EV_MAXB, first
+        // input <= 2^16) go to the CTA that finishes last
+        S.tail_lo = S.i_lo;
+        if (S.nchunks > 1 && c->s[i_lo] <= 16)
+            for (int j = i_lo - 1; j >= 0 && local(j) && c->s[j] <= 12; j--) S.tail_lo = (u32)j;
         c->eval_steps.push_back((int)P.segs.size());
         P.segs.push_back(S);
-        i = i_lo - 1;
+        i = (int)S.tail_lo - 1;
     }
     P.seg_items.assign(c->eval_steps.size(), {});
     P.lev_items.assign(c->eval_steps.size(), {});
@@ -319,6 +324,8 @@ static size_t layout(vc_circuit *c, uintptr_t base)
     c->d_tr = A.take<u64>(c->tr_len);
     G.tr = c->d_tr;
 
+    for (EvalSeg &Sg : P.segs) Sg.counter = A.take<u32>(1);
+
     // layers and their eq tables
     c->L.assign(d, LayerDev{});
     P.eqjobs.clear();
@@ -367,13 +374,15 @@ static size_t layout(vc_circuit *c, uintptr_t base)
     c->eq_verify.push_back({c->tzd});
     c->eq_verify.push_back({c->L[0].tz});
 
-    // line reduction waves
+    // line reduction waves; a single-chunk wave after another wave is run by
+    // that wave's last CTA (its descriptor follows directly, no launch)
     P.lw.clear();
     P.line_items.clear();
     for (u32 i = 0; i < d; i++) {
         const u32 n = c->s[i + 1];
         u32 l0 = 0;
         const u64 *in = c->V[i + 1];
+        bool tail = false;
         for (u32 w = 0;; w++) {
             const u32 cap = (w == 0) ? LN_CHUNK0_LOG : LN_CHUNKW_LOG;
             const u32 nl = std::min(cap, n - l0);
@@ -390,10 +399,17 @@ static size_t layout(vc_circuit *c, uintptr_t base)
             W.a_off = c->chal_off[i] + c->s[i];
             W.b_off = c->chal_off[i] + c->s[i] + n;
             W.tr_q = c->tr_q[i];
-            if (P.line_items.size() <= w) P.line_items.resize(w + 1);
             const u32 idx = (u32)P.lw.size();
+            if (!W.last && (n - l0 - nl) <= LN_CHUNKW_LOG) {  // the next wave is one chunk
+                W.tail = 1;
+                W.counter = A.take<u32>(1);
+            }
             P.lw.push_back(W);
-            for (u32 ch = 0; ch < W.nchunks; ch++) P.line_items[w].push_back({idx, ch});
+            if (!tail) {
+                if (P.line_items.size() <= w) P.line_items.resize(w + 1);
+                for (u32 ch = 0; ch < W.nchunks; ch++) P.line_items[w].push_back({idx, ch});
+            }
+            tail = W.tail != 0;
             if (W.last) break;
             in = W.out;
             l0 += nl;
@@ -605,8 +621,13 @@ static bool plan_valid(const Plan &P)
         if (S.circ >= nc) return false;
     for (const LayerEval &E : P.levs)
         if (E.circ >= nc) return false;
-    for (const LineWaveDev &W : P.lw)
+    for (size_t k = 0; k < P.lw.size(); k++) {
+        const LineWaveDev &W = P.lw[k];
         if (W.circ >= nc) return false;
+        if (W.tail && (k + 1 >= P.lw.size() || P.lw[k + 1].nchunks != 1 || P.lw[k + 1].layer != W.layer ||
+                       P.lw[k + 1].circ != W.circ || P.lw[k + 1].l0 != W.l0 + W.nl || !W.counter))
+            return false;
+    }
     for (const BuildItem &b : P.builds)
         if (b.circ >= nc) return false;
     for (const SciDev &S : P.scis)

@@ -1,11 +1,12 @@
 """Transcript parity of the CUDA prover with the CPU oracle (bit-exact: every
 transcript entry is an exact field element).
 
-Sizes sweep every tiling boundary of the device plan: sum-check CTAs fold 2^11
-entries, line-reduction waves fold 11 then 9 coordinates, so widths 2^0..2^13,
-2^16, 2^20 and 2^21 cover single-CTA, multi-CTA, two-wave and three-wave
-shapes; each benchmark workload runs at its full size with its own input
-recipe."""
+Sizes sweep every tiling boundary of the device plan: product-weighted
+sum-check CTAs fold 2^13 entries and general ones 2^10; line-reduction waves
+fold 13 coordinates, then 8 per later wave, and a single-chunk wave runs as the
+tail of the wave before it.  Widths 2^0..2^13, 2^16, 2^20, 2^21 and 2^22 cover
+single-CTA, multi-CTA, tail and two-launch-plus-tail shapes; each benchmark
+workload runs at its full size with its own input recipe."""
 import random
 
 import numpy as np
@@ -96,9 +97,15 @@ def test_workload_f2_2e20():
     check(*circuits.f2(logn), gen(seed), seeds=(1,))
 
 
-def test_f2_2e21_three_line_waves():
+def test_f2_2e21_line_tail():
     x = I.f2_inputs(21, 1 << 16, 77)
     check(*circuits.f2(21), x, seeds=(5,))
+
+
+def test_f2_2e22_second_line_wave_and_tail():
+    """n = 22: line waves of 13, 8 (two chunks) and 1 coordinate (tail)."""
+    x = I.f2_inputs(22, 1 << 16, 78)
+    check(*circuits.f2(22), x, seeds=(6,))
 
 
 def test_workload_f0_2e16():
