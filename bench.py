@@ -95,7 +95,7 @@ class ClockSampler:
 # ---- algorithmic work of the first sum-check wave -----------------------------------------
 
 PR_CHUNK_LOG = 13  # rounds folded by the first product-weighted wave
-GN_CHUNK_LOG = 10  # rounds folded by the first general wave
+GN_CHUNK_LOG = 12  # rounds folded by the first general wave
 
 
 def sc0_work(widths, kinds):

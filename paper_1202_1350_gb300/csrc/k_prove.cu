@@ -213,21 +213,61 @@ __device__ __forceinline__ void local_gate(u32 kind, u32 k, u32 &a, u32 &b, u32 
     }
 }
 
+#define EV_LC 64  // layer descriptors cached in shared memory per launch
+
+// Descriptor of layer i = i_hi - j of a run: from the shared cache (j < EV_LC)
+// or from global memory.
+struct EvLayer {
+    u32 kind, s, sn;
+    u64 *V;
+};
+
 __global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const EvalSeg *segs, const Item *items)
 {
     u64 *bufA = ev_dyn, *bufB = ev_dyn + EV_MAXB;
+    __shared__ u32 s_kind[EV_LC], s_s[EV_LC], s_sn[EV_LC];
+    __shared__ u64 *s_V[EV_LC];
+    __shared__ const u64 *s_in;
     const Item it = items[blockIdx.x];
     const EvalSeg S = segs[it.wave];
     const Globals &G = Gs[S.circ];
     const LayerDev *Ls = G.layers;
+    u32 *const status = G.status;
     const u32 chunk = it.chunk;
-    const LayerDev &Lin = Ls[S.i_hi];
-    const u32 s_in = Lin.sn;
+    // every field the loops need, read once (stores to the layers' values
+    // would otherwise force the compiler to re-read descriptors per element)
+    const u32 nl = S.i_hi - S.tail_lo + 1;
+    for (u32 j = threadIdx.x; j < nl && j < EV_LC; j += EV_NT) {
+        const LayerDev &L = Ls[S.i_hi - j];
+        s_kind[j] = L.kind;
+        s_s[j] = L.s;
+        s_sn[j] = L.sn;
+        s_V[j] = L.V;
+    }
+    if (threadIdx.x == 0) s_in = Ls[S.i_hi].Vn;
+    __syncthreads();
+    auto layer = [&](u32 i) {
+        const u32 j = S.i_hi - i;
+        EvLayer e;
+        if (j < EV_LC) {
+            e.kind = s_kind[j];
+            e.s = s_s[j];
+            e.sn = s_sn[j];
+            e.V = s_V[j];
+        } else {
+            const LayerDev &L = Ls[i];
+            e.kind = L.kind;
+            e.s = L.s;
+            e.sn = L.sn;
+            e.V = L.V;
+        }
+        return e;
+    };
     u32 B = 1u << S.c;  // block size of the current (upper) layer
     constexpr int R = EV_MAXB / EV_NT;
     {
         // all loads of the chunk are issued before any store
-        const u64 *src = Lin.Vn + ((u64)chunk << S.c);
+        const u64 *__restrict__ src = s_in + ((u64)chunk << S.c);
         u64 r[R];
 #pragma unroll
         for (int j = 0; j < R; j++) {
@@ -243,28 +283,26 @@ __global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const Eva
                 bufA[k] = r[j];
             }
         }
-        if (S.check_input && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
-            atomicOr(G.status, ST_BAD_INPUT);
+        if (S.check_input && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_BAD_INPUT);
     }
     __syncthreads();
     u64 *cur = bufA, *nxt = bufB;
     for (int i = (int)S.i_hi; i >= (int)S.i_lo; i--) {
-        const LayerDev &L = Ls[i];
+        const EvLayer L = layer((u32)i);
         const u32 Bo = (L.s >= L.sn) ? (B << (L.s - L.sn)) : (B >> (L.sn - L.s));
-        const u64 gbase = (u64)chunk * Bo;
+        u64 *__restrict__ out = L.V + (u64)chunk * Bo;
         for (u32 k = threadIdx.x; k < Bo; k += EV_NT) {
             u32 a, b, mul;
             local_gate(L.kind, k, a, b, mul);
             const u64 x = cur[a], y = cur[b];
             const u64 v = mul ? f_mul(x, y) : f_add(x, y);
             nxt[k] = v;
-            L.V[gbase + k] = v;
+            out[k] = v;
         }
         __syncthreads();
         u64 *t = cur; cur = nxt; nxt = t;
         B = Bo;
     }
-    (void)s_in;
     if (S.tail_lo >= S.i_lo) return;
     // Last-CTA tail: every CTA publishes its writes and counts itself; the
     // last one evaluates the narrow layers below the run from the whole
@@ -278,18 +316,20 @@ __global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const Eva
     __threadfence();
     if (threadIdx.x == 0) *S.counter = 0;
     for (int i = (int)S.i_lo - 1; i >= (int)S.tail_lo; i--) {
-        const LayerDev &L = Ls[i];
+        const EvLayer L = layer((u32)i);
         const u32 Bo = 1u << L.s;
+        u64 *__restrict__ out = L.V;
         if (i == (int)S.i_lo - 1) {
             // operands from the whole layer i_lo in global memory, all loads first
+            const u64 *__restrict__ vin = layer((u32)i + 1).V;
             u64 xa[R], xb[R];
 #pragma unroll
             for (int j = 0; j < R; j++) {
                 const u32 k = threadIdx.x + j * EV_NT;
                 u32 a, b, mul;
                 local_gate(L.kind, k, a, b, mul);
-                xa[j] = (k < Bo) ? __ldcg(L.Vn + a) : 0;
-                xb[j] = (k < Bo) ? __ldcg(L.Vn + b) : 0;
+                xa[j] = (k < Bo) ? __ldcg(vin + a) : 0;
+                xb[j] = (k < Bo) ? __ldcg(vin + b) : 0;
             }
 #pragma unroll
             for (int j = 0; j < R; j++) {
@@ -299,7 +339,7 @@ __global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const Eva
                     local_gate(L.kind, k, a, b, mul);
                     const u64 v = mul ? f_mul(xa[j], xb[j]) : f_add(xa[j], xb[j]);
                     nxt[k] = v;
-                    L.V[k] = v;
+                    out[k] = v;
                 }
             }
         } else {
@@ -308,7 +348,7 @@ __global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const Eva
                 local_gate(L.kind, k, a, b, mul);
                 const u64 v = mul ? f_mul(cur[a], cur[b]) : f_add(cur[a], cur[b]);
                 nxt[k] = v;
-                L.V[k] = v;
+                out[k] = v;
             }
         }
         __syncthreads();

@@ -186,49 +186,49 @@ void launch_prep_prod(const Globals *Gs, const SciDev *scis, const ProdWave *wav
 // PROD waves
 // --------------------------------------------------------------------------------
 
-#define PR_NT 256
+#define PR_NT 128
+#define PR_SUB 16  // a thread's 2^PR_M entries are processed as runs of PR_SUB
 
 // Rounds OFF.. of a product-weighted chunk across threads.  Thread t holds
 // level value t (t < na); a round pairs values 2y and 2y+1, which sit in the
 // threads t = y 2^(kk+1) and t + 2^kk, and the first of them keeps the folded
 // value, so rounds stay inside a warp for kk < 5 (shuffles) and continue in
 // warp 0 after one exchange through shared memory.  Each active thread adds
-// E_k(y) u0 and E_k(y) u1 to hv[2k], hv[2k+1].
-template <int OFF>
-__device__ __forceinline__ void prod_cross(u64 (&hv)[32], u64 uv, u32 tid, u32 na, u32 nr, const u64 *s_E,
-                                           u32 eoff0, const u32 *s_r0, const u32 *s_r1, u64 *s_lvl)
+// E_k(y) u0 and E_k(y) u1 to hv[2 kk], hv[2 kk + 1].
+__device__ __forceinline__ void prod_cross(u64 (&hv)[16], u64 uv, u32 off, u32 tid, u32 na, u32 nr,
+                                           const u64 *s_E, u32 eoff0, const u32 (*s_r)[2], u64 *s_lvl)
 {
     const u32 lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int kk = 0; kk < 5; kk++) {
-        const u32 k = OFF + kk;
+        const u32 k = off + kk;
         if (k < nr) {  // uniform
             const u64 u1 = __shfl_down_sync(0xffffffffu, uv, 1u << kk);
             if ((tid & ((2u << kk) - 1)) == 0 && tid < na) {
                 const u32 y = tid >> (kk + 1);
                 const u64 w = s_E[eoff0 - (1u << (nr - k)) + y];
-                hv[2 * (OFF + kk)] = wmul(w, uv);
-                hv[2 * (OFF + kk) + 1] = wmul(w, u1);
-                uv = wfold(uv, u1, s_r0[k], s_r1[k]);
+                hv[2 * kk] = wmul(w, uv);
+                hv[2 * kk + 1] = wmul(w, u1);
+                uv = wfold(uv, u1, s_r[k][0], s_r[k][1]);
             }
         }
     }
     if (lane == 0) s_lvl[warp] = uv;
     __syncthreads();
-    if (OFF + 5 < nr && warp == 0) {
+    if (off + 5 < nr && warp == 0) {
         uv = (lane < PR_NT / 32) ? s_lvl[lane] : 0;
 #pragma unroll
-        for (int kk = 5; kk < 8; kk++) {
-            const u32 k = OFF + kk;
+        for (int kk = 5; kk < 7; kk++) {
+            const u32 k = off + kk;
             if (k < nr) {
                 const u64 u1 = __shfl_down_sync(0xffffffffu, uv, 1u << (kk - 5));
                 const u32 t = lane << 5;  // the thread index this lane stands for
                 if ((t & ((2u << kk) - 1)) == 0 && t < na) {
                     const u32 y = t >> (kk + 1);
                     const u64 w = s_E[eoff0 - (1u << (nr - k)) + y];
-                    hv[2 * (OFF + kk)] = wmul(w, uv);
-                    hv[2 * (OFF + kk) + 1] = wmul(w, u1);
-                    uv = wfold(uv, u1, s_r0[k], s_r1[k]);
+                    hv[2 * kk] = wmul(w, uv);
+                    hv[2 * kk + 1] = wmul(w, u1);
+                    uv = wfold(uv, u1, s_r[k][0], s_r[k][1]);
                 }
             }
         }
@@ -236,12 +236,51 @@ __device__ __forceinline__ void prod_cross(u64 (&hv)[32], u64 uv, u32 tid, u32 n
     }
 }
 
-__global__ void __launch_bounds__(PR_NT, 2) k_sc_prod(const Globals *Gs, const ProdWave *waves, const Item *items)
+// Rounds 0..3 of one run of 16 entries (run index sub within the thread):
+// pair weights Q_k(q), q = pair index + (sub << (3 - k)); adds the sums to
+// hv[2k], hv[2k+1] and returns the folded value.
+__device__ __forceinline__ u64 prod_run16(u64 (&u)[16], u32 sub, const u64 *s_Q, const u32 (*s_r)[2], u64 (&hv)[12])
+{
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        acc128 a0, a1, b0, b1;  // two chains per value for instruction-level parallelism
+        acc_zero(a0);
+        acc_zero(a1);
+        acc_zero(b0);
+        acc_zero(b1);
+        const u32 rr0 = s_r[k][0], rr1 = s_r[k][1];
+        const u32 qoff = (1u << PR_M) - (1u << (PR_M - k)) + (sub << (3 - k));
+#pragma unroll
+        for (int q = 0; q < (8 >> k); q++) {
+            const u64 w = s_Q[qoff + q];
+            const u64 u0 = u[2 * q], u1 = u[2 * q + 1];
+            if (q & 1) {
+                mac(b0, w, u0);
+                mac(b1, w, u1);
+            } else {
+                mac(a0, w, u0);
+                mac(a1, w, u1);
+            }
+            u[q] = wfold(u0, u1, rr0, rr1);
+        }
+        hv[2 * k] = wred(hv[2 * k] + acc_red(a0) + acc_red(b0));
+        hv[2 * k + 1] = wred(hv[2 * k + 1] + acc_red(a1) + acc_red(b1));
+    }
+    return u[0];
+}
+
+// Sum over the CTA's warps of per-warp round sums s_w[warp][i] (W values).
+__device__ __forceinline__ u64 cta_sum4(const u64 (*s_w)[32], u32 i)
+{
+    return wred(s_w[0][i] + s_w[1][i] + s_w[2][i] + s_w[3][i]);
+}
+
+__global__ void __launch_bounds__(PR_NT, 4) k_sc_prod(const Globals *Gs, const ProdWave *waves, const Item *items)
 {
     constexpr int M = PR_M;
-    __shared__ u32 s_r0[32], s_r1[32];
+    __shared__ u32 s_r[32][2];
     __shared__ u64 s_Q[1 << M];
-    __shared__ u64 s_E[512];
+    __shared__ u64 s_E[256];
     __shared__ u64 s_lvl[PR_NT / 32];
     __shared__ u64 s_w[PR_NT / 32][32];
     __shared__ u64 s_echunk;
@@ -253,7 +292,7 @@ __global__ void __launch_bounds__(PR_NT, 2) k_sc_prod(const Globals *Gs, const P
     const u32 nr = W.nr, e = W.e, chunk = it.chunk;
     const u32 na = 1u << (nr - e);
     const u64 base = (u64)chunk << nr;
-    if (tid < nr) limbs31(G.chal[W.chal_off + tid], s_r0[tid], s_r1[tid]);
+    if (tid < nr) limbs31(G.chal[W.chal_off + tid], s_r[tid][0], s_r[tid][1]);
     const u64 *blk = W.wblk;
     const u32 qsize = (1u << e) - 1;
     const u32 kb = e ? e - 1 : 0;
@@ -267,61 +306,77 @@ __global__ void __launch_bounds__(PR_NT, 2) k_sc_prod(const Globals *Gs, const P
     }
     __syncthreads();
 
-    // hv[2k + t]: this thread's share of h_k(t), k < nr (at most 13 rounds)
-    u64 hv[32];
-#pragma unroll
-    for (int i = 0; i < 32; i++) hv[i] = 0;
+    const u32 eoff0 = 1u << (nr - kb);
     u64 uv = 0;  // the thread's level value after its in-register rounds
+    u64 hv[16];  // cross-thread rounds: hv[2 kk + t]
+#pragma unroll
+    for (int i = 0; i < 16; i++) hv[i] = 0;
     if (e == M) {
+        // rounds 0..M-1 in registers: four runs of 16 entries (rounds 0..3
+        // each), then rounds 4 and 5 on the runs' folded values
+        u64 h0[12];
+#pragma unroll
+        for (int i = 0; i < 12; i++) h0[i] = 0;
         if (tid < na) {
-            u64 u[1 << M];
-            const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(W.in + base + ((u64)tid << M));
+            const u64 *src = W.in + base + ((u64)tid << M);
+            const u32 q4 = (1u << M) - 4, q5 = (1u << M) - 2;
+            u64 f0 = 0, g0 = 0;
+            // a rolled loop keeps the kernel small (instruction-cache bound when unrolled)
+#pragma unroll 1
+            for (u32 sub = 0; sub < 4; sub++) {
+                u64 u[16];
+                const ulonglong2 *sv = reinterpret_cast<const ulonglong2 *>(src + sub * PR_SUB);
 #pragma unroll
-            for (int q = 0; q < (1 << (M - 1)); q++) {
-                const ulonglong2 t = src[q];
-                u[2 * q] = t.x;
-                u[2 * q + 1] = t.y;
-            }
-            const u64 T = s_E[tid];  // E_{e-1}(tid)
-#pragma unroll
-            for (int k = 0; k < M; k++) {
-                acc128 a0, a1;
-                acc_zero(a0);
-                acc_zero(a1);
-                const u32 rr0 = s_r0[k], rr1 = s_r1[k];
-                const int qoff = (1 << M) - (1 << (M - k));
-#pragma unroll
-                for (int q = 0; q < (1 << (M - k - 1)); q++) {
-                    const u64 w = s_Q[qoff + q];
-                    const u64 u0 = u[2 * q], u1 = u[2 * q + 1];
-                    mac(a0, w, u0);
-                    mac(a1, w, u1);
-                    u[q] = wfold(u0, u1, rr0, rr1);
+                for (int q = 0; q < 8; q++) {
+                    const ulonglong2 t = sv[q];
+                    u[2 * q] = t.x;
+                    u[2 * q + 1] = t.y;
                 }
-                hv[2 * k] = wmul(T, acc_red(a0));
-                hv[2 * k + 1] = wmul(T, acc_red(a1));
+                const u64 fs = prod_run16(u, sub, s_Q, s_r, h0);
+                if (sub & 1) {
+                    // round 4 on runs (sub-1, sub); round 5 on the two results
+                    const u64 w = s_Q[q4 + (sub >> 1)];
+                    h0[8] = wred(h0[8] + wmul(w, f0));
+                    h0[9] = wred(h0[9] + wmul(w, fs));
+                    const u64 g = wfold(f0, fs, s_r[4][0], s_r[4][1]);
+                    if (sub == 1) {
+                        g0 = g;
+                    } else {
+                        const u64 w5 = s_Q[q5];
+                        h0[10] = wmul(w5, g0);
+                        h0[11] = wmul(w5, g);
+                        uv = wfold(g0, g, s_r[5][0], s_r[5][1]);
+                    }
+                } else {
+                    f0 = fs;
+                }
             }
-            uv = u[0];
+            const u64 T = s_E[tid];  // E_{M-1}(tid): the weight of the chunk bits above the thread's run
+#pragma unroll
+            for (int i = 0; i < 12; i++) h0[i] = wmul(T, h0[i]);
         }
-        prod_cross<M>(hv, uv, tid, na, nr, s_E, (1u << (nr - kb)), s_r0, s_r1, s_lvl);
+        // per-warp sums of the in-register rounds
+        u64 h16[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) h16[i] = (i < 12) ? h0[i] : 0;
+        const u64 s = warp_sum16(h16);
+        if ((lane & 1) == 0 && (lane >> 1) < 12) s_w[warp][lane >> 1] = s;
+        prod_cross(hv, uv, M, tid, na, nr, s_E, eoff0, s_r, s_lvl);
     } else {
         if (tid < na) uv = W.in[base + tid];
-        prod_cross<0>(hv, uv, tid, na, nr, s_E, (1u << (nr - kb)), s_r0, s_r1, s_lvl);
+        prod_cross(hv, uv, 0, tid, na, nr, s_E, eoff0, s_r, s_lvl);
     }
-    __syncthreads();  // s_lvl[0] written by prod_cross
-
-    // per-round sums of this chunk, times the chunk's outer weight
+    // per-warp sums of the cross-thread rounds (after the register rounds' 12 slots when e = M)
     {
-        const u64 s = warp_sum32(hv);
-        if (lane < 2 * nr) s_w[warp][lane] = s;
+        const u64 s = warp_sum16(hv);
+        const u32 o = e ? 12 : 0;
+        if ((lane & 1) == 0 && (lane >> 1) < 2 * (nr - e) && (lane >> 1) < 14) s_w[warp][o + (lane >> 1)] = s;
     }
     __syncthreads();
     if (tid < 2 * nr) {
-        // eight W values can exceed 2^64: add them in two groups of four
-        const u64 s = wred(wred(s_w[0][tid] + s_w[1][tid] + s_w[2][tid] + s_w[3][tid]) +
-                           wred(s_w[4][tid] + s_w[5][tid] + s_w[6][tid] + s_w[7][tid]));
+        const u64 sum = cta_sum4(s_w, tid);
         const u32 k = tid >> 1, t = tid & 1;
-        W.part[((u64)k * W.nchunks + chunk) * 2 + t] = wmul(s, s_echunk);
+        W.part[((u64)k * W.nchunks + chunk) * 2 + t] = wmul(sum, s_echunk);
     }
     if (!(W.flags & WF_LAST) && tid == 0) W.out[chunk] = s_lvl[0];
 }
@@ -373,24 +428,23 @@ __device__ __forceinline__ void gen_pair(u64 p0, u64 p1, u64 v0, u64 v1, u64 b0,
     bn = wfold(b0, b1, rr0, rr1);
 }
 
-// Rounds OFF.. of a general chunk across threads (same placement as
+// Rounds off.. of a general chunk across threads (same placement as
 // prod_cross: the first thread of each pair keeps the folded values).
-template <int OFF>
-__device__ __forceinline__ void gen_cross(u64 (&hv)[32], u64 &p, u64 &v, u64 &b, u32 tid, u32 na, u32 nr,
-                                          const u32 *s_r0, const u32 *s_r1, u64 (*s_lvl)[GN_NT / 32])
+__device__ __forceinline__ void gen_cross(u64 (&hv)[21], u64 &p, u64 &v, u64 &b, u32 off, u32 tid, u32 na, u32 nr,
+                                          const u32 (*s_r)[2], u64 (*s_lvl)[GN_NT / 32])
 {
     const u32 lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int kk = 0; kk < 5; kk++) {
-        const u32 k = OFF + kk;
+        const u32 k = off + kk;
         if (k < nr) {
             const u32 d = 1u << kk;
             const u64 p1 = __shfl_down_sync(0xffffffffu, p, d);
             const u64 v1 = __shfl_down_sync(0xffffffffu, v, d);
             const u64 b1 = __shfl_down_sync(0xffffffffu, b, d);
             if ((tid & ((2u << kk) - 1)) == 0 && tid < na)
-                gen_pair(p, p1, v, v1, b, b1, s_r0[k], s_r1[k], hv[3 * (OFF + kk)], hv[3 * (OFF + kk) + 1],
-                         hv[3 * (OFF + kk) + 2], p, v, b);
+                gen_pair(p, p1, v, v1, b, b1, s_r[k][0], s_r[k][1], hv[3 * kk], hv[3 * kk + 1], hv[3 * kk + 2], p,
+                         v, b);
         }
     }
     if (lane == 0) {
@@ -399,14 +453,14 @@ __device__ __forceinline__ void gen_cross(u64 (&hv)[32], u64 &p, u64 &v, u64 &b,
         s_lvl[2][warp] = b;
     }
     __syncthreads();
-    if (OFF + 5 < nr && warp == 0) {
+    if (off + 5 < nr && warp == 0) {
         const bool have = lane < GN_NT / 32;
         p = have ? s_lvl[0][lane] : 0;
         v = have ? s_lvl[1][lane] : 0;
         b = have ? s_lvl[2][lane] : 0;
 #pragma unroll
         for (int kk = 5; kk < 7; kk++) {
-            const u32 k = OFF + kk;
+            const u32 k = off + kk;
             if (k < nr) {
                 const u32 d = 1u << (kk - 5);
                 const u64 p1 = __shfl_down_sync(0xffffffffu, p, d);
@@ -414,8 +468,8 @@ __device__ __forceinline__ void gen_cross(u64 (&hv)[32], u64 &p, u64 &v, u64 &b,
                 const u64 b1 = __shfl_down_sync(0xffffffffu, b, d);
                 const u32 t = lane << 5;
                 if ((t & ((2u << kk) - 1)) == 0 && t < na)
-                    gen_pair(p, p1, v, v1, b, b1, s_r0[k], s_r1[k], hv[3 * (OFF + kk)], hv[3 * (OFF + kk) + 1],
-                             hv[3 * (OFF + kk) + 2], p, v, b);
+                    gen_pair(p, p1, v, v1, b, b1, s_r[k][0], s_r[k][1], hv[3 * kk], hv[3 * kk + 1], hv[3 * kk + 2],
+                             p, v, b);
             }
         }
         if (lane == 0) {
@@ -426,12 +480,68 @@ __device__ __forceinline__ void gen_cross(u64 (&hv)[32], u64 &p, u64 &v, u64 &b,
     }
 }
 
+// Cross-thread rounds from round off, then the per-warp sums of their
+// message values into s_w[warp][off * 3 ..] (after the register rounds' slots).
+__device__ __forceinline__ void gen_cross_sum(u64 &p, u64 &v, u64 &b, u32 off, u32 tid, u32 na, u32 nr,
+                                              const u32 (*s_r)[2], u64 (*s_lvl)[GN_NT / 32], u64 (*s_w)[40])
+{
+    u64 hv[32];
+#pragma unroll
+    for (int i = 0; i < 32; i++) hv[i] = 0;
+    gen_cross(reinterpret_cast<u64(&)[21]>(hv), p, v, b, off, tid, na, nr, s_r, s_lvl);
+    const u64 s = warp_sum32(hv);
+    const u32 lane = tid & 31;
+    if (lane < 3 * (nr - off) && lane < 21) s_w[tid >> 5][3 * off + lane] = s;
+}
+
+// Rounds 0..2 of one run of 8 entries; adds to h[0..8] and leaves the folded
+// values in p[0], v[0], b[0].
+__device__ __forceinline__ void gen_run8(u64 (&p)[8], u64 (&v)[8], u64 (&b)[8], const u32 (*s_r)[2], u64 (&h)[15])
+{
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        acc128 a0, a1, a2;
+        acc_zero(a0);
+        acc_zero(a1);
+        acc_zero(a2);
+        const u32 rr0 = s_r[k][0], rr1 = s_r[k][1];
+#pragma unroll
+        for (int q = 0; q < (4 >> k); q++) {
+            const u64 p0 = p[2 * q], p1 = p[2 * q + 1], v0 = v[2 * q], v1 = v[2 * q + 1];
+            const u64 b0 = b[2 * q], b1 = b[2 * q + 1];
+            mac(a0, p0, v0);
+            mac(a1, p1, v1);
+            mac(a2, wext2(p1, p0), wext2(v1, v0));
+            acc_add(a0, b0);
+            acc_add(a1, b1);
+            acc_add(a2, wext2(b1, b0));
+            p[q] = wfold(p0, p1, rr0, rr1);
+            v[q] = wfold(v0, v1, rr0, rr1);
+            b[q] = wfold(b0, b1, rr0, rr1);
+        }
+        h[3 * k] = wred(h[3 * k] + acc_red(a0));
+        h[3 * k + 1] = wred(h[3 * k + 1] + acc_red(a1));
+        h[3 * k + 2] = wred(h[3 * k + 2] + acc_red(a2));
+    }
+}
+
+// Round k (3 or 4) on two folded triples held by one thread.
+__device__ __forceinline__ void gen_pair_acc(u64 p0, u64 p1, u64 v0, u64 v1, u64 b0, u64 b1, u32 rr0, u32 rr1,
+                                             u64 *h, u64 &pn, u64 &vn, u64 &bn)
+{
+    u64 c0, c1, c2;
+    gen_pair(p0, p1, v0, v1, b0, b1, rr0, rr1, c0, c1, c2, pn, vn, bn);
+    h[0] = wred(h[0] + c0);
+    h[1] = wred(h[1] + c1);
+    h[2] = wred(h[2] + c2);
+}
+
 __global__ void __launch_bounds__(GN_NT, 4) k_sc_gen(const Globals *Gs, const GenWave *waves, const Item *items)
 {
     constexpr int M = GN_M;
-    __shared__ u32 s_r0[32], s_r1[32];
+    __shared__ u32 s_r[32][2];
     __shared__ u64 s_lvl[3][GN_NT / 32];
-    __shared__ u64 s_w[GN_NT / 32][32];
+    __shared__ u64 s_w[GN_NT / 32][40];
 
     const Item it = items[blockIdx.x];
     const GenWave &W = waves[it.wave];
@@ -441,77 +551,77 @@ __global__ void __launch_bounds__(GN_NT, 4) k_sc_gen(const Globals *Gs, const Ge
     const u32 na = 1u << (nr - e);
     const u64 base = (u64)chunk << nr;
     const bool hasB = (W.flags & WF_HASB) != 0;
-    if (tid < nr) limbs31(G.chal[W.chal_off + tid], s_r0[tid], s_r1[tid]);
+    if (tid < nr) limbs31(G.chal[W.chal_off + tid], s_r[tid][0], s_r[tid][1]);
     __syncthreads();
 
-    u64 hv[32];
-#pragma unroll
-    for (int i = 0; i < 32; i++) hv[i] = 0;
     u64 pv = 0, vv = 0, bv = 0;
     if (e == M) {
-        if (tid < na) {
-            u64 p[8], v[8], b[8];
-            const u64 x0 = base + ((u64)tid << M);
-            const ulonglong2 *sv = reinterpret_cast<const ulonglong2 *>(W.inV + x0);
+        // rounds 0..4 in registers: four runs of 8 entries (rounds 0..2
+        // each), round 3 on pairs of runs, round 4 on the two results
+        u64 h0[15];
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const ulonglong2 t = sv[q];
-                v[2 * q] = t.x;
-                v[2 * q + 1] = t.y;
-            }
-            if (W.src != GS_NONE) {
-                gen_source(G, W, x0, v, p, b);
-            } else {
-                const ulonglong2 *sp = reinterpret_cast<const ulonglong2 *>(W.inP + x0);
+        for (int i = 0; i < 15; i++) h0[i] = 0;
+        if (tid < na) {
+            u64 fp = 0, fv = 0, fb = 0, gp = 0, gv = 0, gb = 0;
+            // a rolled loop keeps the kernel small (instruction-cache bound when unrolled)
+#pragma unroll 1
+            for (u32 sub = 0; sub < 4; sub++) {
+                u64 p[8], v[8], b[8];
+                const u64 x0 = base + ((u64)tid << M) + 8 * sub;
+                const ulonglong2 *sv = reinterpret_cast<const ulonglong2 *>(W.inV + x0);
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
-                    const ulonglong2 t = sp[q];
-                    p[2 * q] = t.x;
-                    p[2 * q + 1] = t.y;
+                    const ulonglong2 t = sv[q];
+                    v[2 * q] = t.x;
+                    v[2 * q + 1] = t.y;
                 }
-                if (hasB) {
-                    const ulonglong2 *sb = reinterpret_cast<const ulonglong2 *>(W.inB + x0);
+                if (W.src != GS_NONE) {
+                    gen_source(G, W, x0, v, p, b);
+                } else {
+                    const ulonglong2 *sp = reinterpret_cast<const ulonglong2 *>(W.inP + x0);
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
-                        const ulonglong2 t = sb[q];
-                        b[2 * q] = t.x;
-                        b[2 * q + 1] = t.y;
+                        const ulonglong2 t = sp[q];
+                        p[2 * q] = t.x;
+                        p[2 * q + 1] = t.y;
+                    }
+                    if (hasB) {
+                        const ulonglong2 *sb = reinterpret_cast<const ulonglong2 *>(W.inB + x0);
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            const ulonglong2 t = sb[q];
+                            b[2 * q] = t.x;
+                            b[2 * q + 1] = t.y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 8; q++) b[q] = 0;
+                    }
+                }
+                gen_run8(p, v, b, s_r, h0);
+                if (sub & 1) {
+                    u64 np, nv, nb;
+                    gen_pair_acc(fp, p[0], fv, v[0], fb, b[0], s_r[3][0], s_r[3][1], h0 + 9, np, nv, nb);
+                    if (sub == 1) {
+                        gp = np;
+                        gv = nv;
+                        gb = nb;
+                    } else {
+                        gen_pair_acc(gp, np, gv, nv, gb, nb, s_r[4][0], s_r[4][1], h0 + 12, pv, vv, bv);
                     }
                 } else {
-#pragma unroll
-                    for (int q = 0; q < 8; q++) b[q] = 0;
+                    fp = p[0];
+                    fv = v[0];
+                    fb = b[0];
                 }
             }
-#pragma unroll
-            for (int k = 0; k < M; k++) {
-                acc128 a0, a1, a2;
-                acc_zero(a0);
-                acc_zero(a1);
-                acc_zero(a2);
-                const u32 rr0 = s_r0[k], rr1 = s_r1[k];
-#pragma unroll
-                for (int q = 0; q < (1 << (M - k - 1)); q++) {
-                    const u64 p0 = p[2 * q], p1 = p[2 * q + 1], v0 = v[2 * q], v1 = v[2 * q + 1];
-                    mac(a0, p0, v0);
-                    mac(a1, p1, v1);
-                    mac(a2, wext2(p1, p0), wext2(v1, v0));
-                    const u64 b0 = b[2 * q], b1 = b[2 * q + 1];
-                    acc_add(a0, b0);
-                    acc_add(a1, b1);
-                    acc_add(a2, wext2(b1, b0));
-                    p[q] = wfold(p0, p1, rr0, rr1);
-                    v[q] = wfold(v0, v1, rr0, rr1);
-                    b[q] = wfold(b0, b1, rr0, rr1);
-                }
-                hv[3 * k] = acc_red(a0);
-                hv[3 * k + 1] = acc_red(a1);
-                hv[3 * k + 2] = acc_red(a2);
-            }
-            pv = p[0];
-            vv = v[0];
-            bv = b[0];
         }
-        gen_cross<M>(hv, pv, vv, bv, tid, na, nr, s_r0, s_r1, s_lvl);
+        u64 h16[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) h16[i] = (i < 15) ? h0[i] : 0;
+        const u64 s = warp_sum16(h16);
+        if ((lane & 1) == 0 && (lane >> 1) < 15) s_w[warp][lane >> 1] = s;
+        gen_cross_sum(pv, vv, bv, M, tid, na, nr, s_r, s_lvl, s_w);
     } else {
         if (tid < na) {
             const u64 x = base + tid;
@@ -528,19 +638,13 @@ __global__ void __launch_bounds__(GN_NT, 4) k_sc_gen(const Globals *Gs, const Ge
                 bv = hasB ? W.inB[x] : 0;
             }
         }
-        gen_cross<0>(hv, pv, vv, bv, tid, na, nr, s_r0, s_r1, s_lvl);
-    }
-    __syncthreads();
-
-    {
-        const u64 s = warp_sum32(hv);
-        if (lane < 3 * nr) s_w[warp][lane] = s;
+        gen_cross_sum(pv, vv, bv, 0, tid, na, nr, s_r, s_lvl, s_w);
     }
     __syncthreads();
     if (tid < 3 * nr) {
-        const u64 s = wred(s_w[0][tid] + s_w[1][tid] + s_w[2][tid] + s_w[3][tid]);
+        const u64 sum = wred(s_w[0][tid] + s_w[1][tid] + s_w[2][tid] + s_w[3][tid]);
         const u32 k = tid / 3, t = tid % 3;
-        W.part[((u64)k * W.nchunks + chunk) * 3 + t] = s;
+        W.part[((u64)k * W.nchunks + chunk) * 3 + t] = sum;
     }
     if (!(W.flags & WF_LAST) && tid == 0) {
         W.outP[chunk] = s_lvl[0][0];
@@ -610,7 +714,10 @@ __global__ void __launch_bounds__(256) k_final(const Globals *Gs, const SciDev *
     const u64 gid = blockIdx.x * (u64)blockDim.x + threadIdx.x, gstride = (u64)gridDim.x * blockDim.x;
     for (int j = 0; j < nouts; j++) {
         const Globals &G = Gs[outs[j]];
-        for (u64 x = gid; x < G.S0; x += gstride) G.tr[x] = G.layers[0].V[x];
+        const u64 n = G.S0;
+        const u64 *__restrict__ src = G.layers[0].V;
+        u64 *__restrict__ dst = G.tr;
+        for (u64 x = gid; x < n; x += gstride) dst[x] = src[x];
     }
 }
 

@@ -74,8 +74,8 @@ enum : u32 {
 // Source of the first GEN wave's P and B.
 enum : u32 { GS_NONE = 0, GS_SQ2 = 1, GS_TREE2 = 2 };
 
-#define PR_M 5  // PROD: each thread folds 2^5 entries through 5 rounds in registers
-#define GN_M 3  // GEN: 2^3 entries, 3 rounds
+#define PR_M 6  // PROD: each thread folds 2^6 entries through 6 rounds in registers (128 threads per CTA)
+#define GN_M 5  // GEN: 2^5 entries, 5 rounds (128 threads per CTA)
 
 struct SciDev {
     u32 circ;

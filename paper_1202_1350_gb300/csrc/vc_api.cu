@@ -23,7 +23,7 @@
 
 namespace {
 
-constexpr u32 PR_CHUNK_LOG = PR_M + 8;  // entries folded by one PROD CTA (256 threads x 2^PR_M)
+constexpr u32 PR_CHUNK_LOG = PR_M + 7;  // entries folded by one PROD CTA (128 threads x 2^PR_M)
 constexpr u32 GN_CHUNK_LOG = GN_M + 7;  // entries folded by one GEN CTA (128 threads x 2^GN_M)
 constexpr u32 LN_CHUNK0_LOG = 13;       // coordinates folded by the first line wave (LN_E + 8)
 constexpr u32 LN_CHUNKW_LOG = 8;        // coordinates folded by later line waves (one polynomial per thread)
