@@ -341,6 +341,8 @@ def run_ours(args):
     }
     if not args.no_batch:
         line["batched"] = run_batch(local)
+    if not args.no_serve:
+        line["serving"] = run_serving(local)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -419,6 +421,74 @@ def run_batch(local: int, reps: int = 5):
             "reps": reps}
 
 
+# ---- serving: Poisson arrivals into the proof server ---------------------------------------
+
+def run_serving(local: int, seconds_per_rate: float = 1.5):
+    """70% F2 (log2 n uniform in [10, 22]) and 30% MatMult (n in {32, 64, 128})
+    jobs submitted to vc_server (admission cap 150 GB, continuous batching);
+    inputs resident in HBM, one input vector per shape.  First a saturating
+    burst gives the sustained throughput; then Poisson arrivals at 0.5x, 0.9x
+    and 1.2x of it give proofs/s and p50/p99 latency (submit to transcript
+    written, the server's own clock)."""
+    import torch
+    from paper_1202_1350_gb300 import Server, circuits
+    from paper_1202_1350_gb300 import inputs as I
+
+    shapes = {}
+    for logn in range(10, 23):
+        shapes[("f2", logn)] = circuits.f2(logn)
+    for logn in (5, 6, 7):
+        shapes[("matmult", logn)] = circuits.matmult(logn)
+    xin = {k: torch.from_numpy(I.job_inputs(k[0], k[1], 11 + k[1]).view(np.int64).copy()).cuda() for k in shapes}
+    trl = {k: circuits.transcript_len(w) for k, (w, _) in shapes.items()}
+    gates = {k: circuits.non_input_gates(w) for k, (w, _) in shapes.items()}
+    srv = Server(local, mem_cap_bytes=150 << 30)
+
+    def run(jobs, arrivals):
+        trbuf = torch.empty(sum(trl[(f, n)] for f, n, _ in jobs), dtype=torch.int64, device="cuda")
+        ids, off = [], 0
+        t0 = time.perf_counter()
+        for k, (fam, logn, seed) in enumerate(jobs):
+            if arrivals is not None:
+                while time.perf_counter() - t0 < arrivals[k]:
+                    pass
+            w, kinds = shapes[(fam, logn)]
+            n = trl[(fam, logn)]
+            ids.append(srv.submit(w, kinds, xin[(fam, logn)], seed, trbuf[off:off + n]))
+            off += n
+        infos = [srv.wait(j) for j in ids]
+        assert all(i["status"] == 0 for i in infos)
+        lat = np.array([(i["done_ns"] - i["submit_ns"]) / 1e6 for i in infos])
+        span = (max(i["done_ns"] for i in infos) - min(i["submit_ns"] for i in infos)) / 1e9
+        g = sum(gates[(f, n)] for f, n, _ in jobs)
+        return {"proofs_per_s": len(jobs) / span, "gates_per_s": g / span, "jobs": len(jobs),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean())}
+
+    try:
+        burst = I.serving_mix(0xC0FFEE + 5, 1500)
+        run(burst, None)  # warm-up: fills the circuit pool
+        sat = run(burst, None)
+        rates = []
+        for mult in (0.5, 0.9, 1.2):
+            rate = mult * sat["proofs_per_s"]
+            n = int(min(20000, max(200, rate * seconds_per_rate)))
+            jobs = I.serving_mix(0xC0FFEE + 5 + int(mult * 10), n)
+            arr = I.poisson_arrivals(0xC0FFEE + int(mult * 10), n, rate)
+            r = run(jobs, arr)
+            r["offered_per_s"] = rate
+            r["load"] = mult
+            rates.append(r)
+        st = srv.stats()
+    finally:
+        srv.close()
+    return {"workload": "Poisson arrivals; 70% F2 (log2 n uniform in [10,22], x uniform in [0,2^16]), "
+                        "30% MatMult (n in {32,64,128}); admission cap 150 GB; inputs resident in HBM",
+            "saturated": sat, "rates": rates,
+            "server": {"launch_sets": st["launch_sets"], "max_jobs_in_flight": st["max_jobs_in_flight"],
+                       "circuits": st["circuits_created"], "peak_held_gb": st["peak_held_bytes"] / 1e9}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -427,6 +497,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

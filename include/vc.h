@@ -228,6 +228,62 @@ vc_status vc_prove_batch(vc_circuit *const *circuits, const uint64_t *const *inp
                          const uint64_t *seeds, uint64_t *const *transcripts, int n,
                          void *stream);
 
+/* Proof server (serving form of the prover; the paper has no counterpart).
+ * A request loop owned by one worker thread: submitted jobs are admitted in
+ * arrival order while the circuits they need fit under a device-memory cap,
+ * admitted jobs are merged into launch sets (one set of merged launches for
+ * all of them, as for vc_batch), and up to `max_inflight` sets run at once on
+ * their own streams, so jobs that arrive while others are on the GPU are
+ * admitted as slots and memory free up and their work overlaps on the device
+ * (continuous batching).  Circuits are pooled by shape and stay resident
+ * between jobs.  Structured wirings only (EXPLICIT layers: VC_EINVAL). */
+typedef struct vc_server vc_server;
+
+typedef struct {
+    uint64_t mem_cap_bytes;  /* device bytes for resident circuits (0 = 150 GiB) */
+    uint32_t max_batch;      /* jobs per launch set (0 = 64)                     */
+    uint32_t max_inflight;   /* launch sets on the device at once (0 = 2, max 8) */
+} vc_server_config;
+
+typedef struct {
+    int done;                /* 1 once the transcript is written                 */
+    vc_status status;        /* the job's result (VC_EINVAL: non-canonical input) */
+    uint64_t submit_ns;      /* steady-clock times: submitted, admitted, finished */
+    uint64_t start_ns;
+    uint64_t done_ns;
+} vc_job_info;
+
+typedef struct {
+    uint64_t submitted, completed, launch_sets;
+    uint64_t circuits_created, circuits_evicted;
+    uint64_t held_bytes, peak_held_bytes, pending;
+    uint32_t max_jobs_in_flight;
+    uint32_t pad;
+} vc_server_stats;
+
+/* Start a server on `device` (cfg may be NULL for the defaults). */
+vc_status vc_server_create(int device, const vc_server_config *cfg, vc_server **out);
+
+/* Finish every submitted job, then stop the worker and free everything. */
+vc_status vc_server_destroy(vc_server *s);
+
+/* Queue one proof: circuit shape `desc` (host memory, read during the call),
+ * S_d canonical inputs and a transcript buffer of the shape's length, each
+ * host or device memory; both must stay valid until the job is done.  Returns
+ * at once with *job_id.  VC_EINVAL: bad shape or pointer; VC_EBUSY: one
+ * circuit of this shape alone exceeds the memory cap. */
+vc_status vc_server_submit(vc_server *s, const vc_circuit_desc *desc, const uint64_t *inputs,
+                           uint64_t seed, uint64_t *transcript, uint64_t *job_id);
+
+/* Job state without blocking.  Once a call reports done = 1 the job is
+ * forgotten (its id becomes invalid). */
+vc_status vc_server_poll(vc_server *s, uint64_t job_id, vc_job_info *info);
+
+/* Block until the job is done, report it and forget it. */
+vc_status vc_server_wait(vc_server *s, uint64_t job_id, vc_job_info *info);
+
+vc_status vc_server_get_stats(vc_server *s, vc_server_stats *stats);
+
 /* Elementwise field product out[k] = a[k] b[k] mod p on the device (device
  * pointers, n elements, canonical inputs).  Used to check the device field
  * arithmetic.  Asynchronous. */

@@ -11,4 +11,4 @@ from .vc import (EXPLICIT, F0_FINAL, F0_FIRST, F0_PAIR, MATMULT, P, SQUARE, TREE
                  vc_circuit_bytes, vc_circuit_create, vc_circuit_get_info, vc_circuit_set_stage_events, vc_circuit_destroy, vc_circuit_sync, vc_evaluate,
                  vc_field_mul, vc_field_mul_rate, vc_prove, vc_prove_batch, vc_status_string,
                  vc_transcript_len, vc_verify)
-from .api import Batch, Circuit  # noqa: F401
+from .api import Batch, Circuit, Server  # noqa: F401

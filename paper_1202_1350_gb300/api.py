@@ -116,3 +116,45 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Proof server: submit jobs (circuit shape, inputs, seed); results are
+    written into the caller's transcript buffers (continuous batching under a
+    device-memory cap)."""
+
+    def __init__(self, device: int = 0, mem_cap_bytes: int = 0, max_batch: int = 0, max_inflight: int = 0):
+        self.device = device
+        self.handle = _vc.vc_server_create(device, mem_cap_bytes, max_batch, max_inflight)
+        self._keep = {}  # job id -> buffers that must outlive the job
+
+    def submit(self, log_width, wiring, inputs, seed: int, transcript) -> int:
+        jid = _vc.vc_server_submit(self.handle, log_width, wiring, inputs, seed, transcript)
+        self._keep[jid] = (inputs, transcript)
+        return jid
+
+    def wait(self, job_id: int) -> dict:
+        info = _vc.vc_server_wait(self.handle, job_id)
+        self._keep.pop(job_id, None)
+        return info
+
+    def poll(self, job_id: int) -> dict:
+        info = _vc.vc_server_poll(self.handle, job_id)
+        if info["done"]:
+            self._keep.pop(job_id, None)
+        return info
+
+    def stats(self) -> dict:
+        return _vc.vc_server_get_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _vc.vc_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

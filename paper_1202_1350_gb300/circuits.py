@@ -40,3 +40,13 @@ def by_name(family: str, logn: int):
 def non_input_gates(log_width) -> int:
     """Gates outside the input layer (the count behind gates/s)."""
     return sum(1 << s for s in log_width[:-1])
+
+
+def transcript_len(log_width) -> int:
+    """u64 entries of a proof transcript: the outputs, three values per
+    sum-check round and s_{i+1} + 1 line values per layer."""
+    s = [int(v) for v in log_width]
+    n = 1 << s[0]
+    for i in range(len(s) - 1):
+        n += 3 * (s[i] + 2 * s[i + 1]) + s[i + 1] + 1
+    return n

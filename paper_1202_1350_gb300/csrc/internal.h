@@ -1,0 +1,180 @@
+// internal.h -- definitions shared by the C ABI (vc_api.cu) and the proof
+// server (server.cu): device arenas, launch plans, circuit and batch handles.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "plan.h"
+#include "vc.h"
+
+constexpr u32 PR_CHUNK_LOG = PR_M + 7;  // entries folded by one PROD CTA (128 threads x 2^PR_M)
+constexpr u32 GN_CHUNK_LOG = GN_M + 7;  // entries folded by one GEN CTA (128 threads x 2^GN_M)
+constexpr u32 LN_CHUNK0_LOG = 13;       // coordinates folded by the first line wave (LN_E + 8)
+constexpr u32 LN_CHUNKW_LOG = 8;        // coordinates folded by later line waves (one polynomial per thread)
+
+// Which layers' phase-2/3 tables are built by k_build23 (the rest are formed
+// on the fly or never stored).
+inline bool needs_tables(u32 kind) { return kind != W_SQUARE && kind != W_TREE; }
+
+// Bump allocator over one device allocation (base 0: sizing pass).
+struct Arena {
+    uintptr_t base = 0;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t n)
+    {
+        off = (off + 255) & ~size_t(255);
+        T *p = reinterpret_cast<T *>(base + off);
+        off += n * sizeof(T) + 16;
+        return p;
+    }
+};
+
+// Makes `d` the current device for the guard's lifetime.
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int d)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DevGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+cudaError_t upload(T *dst, const std::vector<T> &src)
+{
+    if (src.empty()) return cudaSuccess;
+    return cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+template <class T>
+cudaError_t upload_async(T *dst, const std::vector<T> &src, cudaStream_t st)
+{
+    if (src.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+// The launches of one proof over a set of circuits.  Every descriptor carries
+// the index (circ) of its circuit in the plan's device array of globals; the
+// item lists of one evaluation step, line wave or sum-check wave hold the work
+// of every circuit, so one launch serves them all.
+struct Plan {
+    int ncirc = 0;
+    Globals *d_G = nullptr;
+    std::vector<Globals> h_G;  // members' globals (merged plans: uploaded to d_G)
+    std::vector<Item> checks;  // canonical-input checks (circuit, 2048-input block)
+    std::vector<EqJob> eqjobs;
+    std::vector<EvalSeg> segs;
+    std::vector<LayerEval> levs;
+    std::vector<std::vector<Item>> seg_items, lev_items;  // per evaluation step
+    std::vector<LineWaveDev> lw;
+    std::vector<std::vector<Item>> line_items;  // per line wave
+    std::vector<BuildItem> builds;
+    std::vector<SciDev> scis;
+    std::vector<ProdWave> pw;
+    std::vector<GenWave> gw;
+    std::vector<std::vector<Item>> p_items, g_items;  // per sum-check wave
+    std::vector<RoundRef> rounds;
+    std::vector<u32> outs;
+    bool has_tab = false;
+    // device copies
+    Item *d_checks = nullptr;
+    EqJob *d_eqjobs = nullptr;
+    EvalSeg *d_segs = nullptr;
+    LayerEval *d_levs = nullptr;
+    std::vector<Item *> d_seg_items, d_lev_items, d_line_items, d_p_items, d_g_items;
+    LineWaveDev *d_lw = nullptr;
+    BuildItem *d_builds = nullptr;
+    SciDev *d_scis = nullptr;
+    ProdWave *d_pw = nullptr;
+    GenWave *d_gw = nullptr;
+    RoundRef *d_rounds = nullptr;
+    u32 *d_outs = nullptr;
+    // execution
+    cudaStream_t aux[2] = {};
+    cudaStream_t cap = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_tables = nullptr, ev_eval = nullptr, ev_build = nullptr, ev_prod = nullptr,
+                ev_gen = nullptr;
+    cudaEvent_t ev_params = nullptr;  // a batch's parameter table was copied
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t stage_ev[2 * VC_NUM_STAGES] = {};
+    bool stage_on = false;
+};
+
+struct vc_circuit {
+    int device = 0;
+    u32 d = 0;
+    std::vector<u32> s, kind, has_add;
+    std::vector<std::vector<unsigned char>> ex_type;
+    std::vector<std::vector<u32>> ex_in1, ex_in2;
+    std::vector<std::vector<u32>> by1_off, by1_g, by2_off, by2_g;
+    u64 tr_len = 0;
+    u32 nchal = 0;
+    u32 zd_off = 0;
+    std::vector<u32> chal_off, z_off;
+    std::vector<u64> tr_msg, tr_q;
+
+    char *arena = nullptr;
+    size_t arena_bytes = 0;
+    Globals G{};             // host copy of the circuit's globals
+    Globals *d_G = nullptr;  // device copy (seed and tr written per call)
+    std::vector<u64 *> V;
+    u64 *d_tr = nullptr;
+    u64 *d_result = nullptr;
+    std::vector<LayerDev> L;
+    LayerDev *d_layers = nullptr;
+    std::vector<EqJob> eq_verify;
+    EqJob *d_eq_verify = nullptr;
+    u64 *partials = nullptr;
+    VerifyDev Vd{};
+    EqTab tzd{};
+    std::vector<u32> explicit_layers;
+    u32 *d_explicit_layers = nullptr;
+    std::vector<u32> round_layer, zmap;
+    u32 *d_round_layer = nullptr, *d_zmap = nullptr;
+    std::vector<int> eval_steps;  // >= 0: a segment; < 0: layer -step - 1 alone
+    Plan P;                       // this circuit alone (circ = 0)
+    u64 *h_pinned = nullptr;      // small pinned buffer for status/result readback
+};
+
+struct vc_batch {
+    int device = 0;
+    std::vector<vc_circuit *> members;
+    Plan P;
+    char *arena = nullptr;
+    size_t arena_bytes = 0;
+    CallParams *d_cp = nullptr;
+    CallParams *h_cp = nullptr;  // pinned parameter table
+};
+
+vc_status cuda_status(cudaError_t e);
+void init_device_once(int device);
+
+// Host-side circuit construction: validation, offsets and the single-circuit
+// plan, sized but not allocated (c->arena_bytes set).  circuit_allocate then
+// takes the device memory and uploads everything.
+vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **out);
+vc_status circuit_allocate(vc_circuit *c);
+void circuit_free(vc_circuit *c);
+
+void plan_take(Plan &P, Arena &A, bool own_G);
+bool plan_valid(const Plan &P);
+cudaError_t plan_upload(Plan &P);                       // synchronous copies
+cudaError_t plan_upload_async(Plan &P, cudaStream_t st);  // host vectors must stay unchanged until done
+cudaError_t plan_resources(Plan &P);
+void plan_release(Plan &P);
+void plan_merge(Plan &B, const std::vector<vc_circuit *> &cs);
+void enqueue_plan(Plan &P, cudaStream_t st);
+int count_launches(const Plan &P);
+size_t plan_bytes(Plan &P, bool own_G);  // device bytes of the plan's descriptors
+
+int ptr_kind(const void *p, int device);
+cudaError_t queue_status(vc_circuit *c, cudaStream_t st);
+vc_status decode_status(const vc_circuit *c);

@@ -18,52 +18,11 @@
 #include <new>
 #include <vector>
 
-#include "plan.h"
-#include "vc.h"
+#include "internal.h"
 
-namespace {
-
-constexpr u32 PR_CHUNK_LOG = PR_M + 7;  // entries folded by one PROD CTA (128 threads x 2^PR_M)
-constexpr u32 GN_CHUNK_LOG = GN_M + 7;  // entries folded by one GEN CTA (128 threads x 2^GN_M)
-constexpr u32 LN_CHUNK0_LOG = 13;       // coordinates folded by the first line wave (LN_E + 8)
-constexpr u32 LN_CHUNKW_LOG = 8;        // coordinates folded by later line waves (one polynomial per thread)
-
-// Which layers' phase-2/3 tables are built by k_build23 (the rest are formed
-// on the fly or never stored).
-bool needs_tables(u32 kind) { return kind != W_SQUARE && kind != W_TREE; }
-
-struct Arena {
-    uintptr_t base = 0;
-    size_t off = 0;
-    template <class T>
-    T *take(size_t n)
-    {
-        off = (off + 255) & ~size_t(255);
-        T *p = reinterpret_cast<T *>(base + off);
-        off += n * sizeof(T) + 16;
-        return p;
-    }
-};
-
-struct DevGuard {
-    int prev = -1;
-    explicit DevGuard(int d)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != d) cudaSetDevice(d);
-    }
-    ~DevGuard()
-    {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-template <class T>
-cudaError_t upload(T *dst, const std::vector<T> &src)
+vc_status cuda_status(cudaError_t e)
 {
-    if (src.empty()) return cudaSuccess;
-    return cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? VC_OK : (e == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA);
 }
 
 // Kernel attributes, set once per device.
@@ -82,104 +41,7 @@ void init_device_once(int device)
     }
 }
 
-vc_status cuda_status(cudaError_t e)
-{
-    return e == cudaSuccess ? VC_OK : (e == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA);
-}
 
-}  // namespace
-
-// The launches of one proof over a set of circuits.  Every descriptor carries
-// the index (circ) of its circuit in the plan's device array of globals; the
-// item lists of one evaluation step, line wave or sum-check wave hold the work
-// of every circuit, so one launch serves them all.
-struct Plan {
-    int ncirc = 0;
-    Globals *d_G = nullptr;
-    std::vector<Item> checks;  // canonical-input checks (circuit, 2048-input block)
-    std::vector<EqJob> eqjobs;
-    std::vector<EvalSeg> segs;
-    std::vector<LayerEval> levs;
-    std::vector<std::vector<Item>> seg_items, lev_items;  // per evaluation step
-    std::vector<LineWaveDev> lw;
-    std::vector<std::vector<Item>> line_items;  // per line wave
-    std::vector<BuildItem> builds;
-    std::vector<SciDev> scis;
-    std::vector<ProdWave> pw;
-    std::vector<GenWave> gw;
-    std::vector<std::vector<Item>> p_items, g_items;  // per sum-check wave
-    std::vector<RoundRef> rounds;
-    std::vector<u32> outs;
-    bool has_tab = false;
-    // device copies
-    Item *d_checks = nullptr;
-    EqJob *d_eqjobs = nullptr;
-    EvalSeg *d_segs = nullptr;
-    LayerEval *d_levs = nullptr;
-    std::vector<Item *> d_seg_items, d_lev_items, d_line_items, d_p_items, d_g_items;
-    LineWaveDev *d_lw = nullptr;
-    BuildItem *d_builds = nullptr;
-    SciDev *d_scis = nullptr;
-    ProdWave *d_pw = nullptr;
-    GenWave *d_gw = nullptr;
-    RoundRef *d_rounds = nullptr;
-    u32 *d_outs = nullptr;
-    // execution
-    cudaStream_t aux[2] = {};
-    cudaStream_t cap = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_tables = nullptr, ev_eval = nullptr, ev_build = nullptr, ev_prod = nullptr,
-                ev_gen = nullptr;
-    cudaEvent_t ev_params = nullptr;  // a batch's parameter table was copied
-    cudaGraphExec_t exec = nullptr;
-    cudaEvent_t stage_ev[2 * VC_NUM_STAGES] = {};
-    bool stage_on = false;
-};
-
-struct vc_circuit {
-    int device = 0;
-    u32 d = 0;
-    std::vector<u32> s, kind, has_add;
-    std::vector<std::vector<unsigned char>> ex_type;
-    std::vector<std::vector<u32>> ex_in1, ex_in2;
-    std::vector<std::vector<u32>> by1_off, by1_g, by2_off, by2_g;
-    u64 tr_len = 0;
-    u32 nchal = 0;
-    u32 zd_off = 0;
-    std::vector<u32> chal_off, z_off;
-    std::vector<u64> tr_msg, tr_q;
-
-    char *arena = nullptr;
-    size_t arena_bytes = 0;
-    Globals G{};             // host copy of the circuit's globals
-    Globals *d_G = nullptr;  // device copy (seed and tr written per call)
-    std::vector<u64 *> V;
-    u64 *d_tr = nullptr;
-    u64 *d_result = nullptr;
-    std::vector<LayerDev> L;
-    LayerDev *d_layers = nullptr;
-    std::vector<EqJob> eq_verify;
-    EqJob *d_eq_verify = nullptr;
-    u64 *partials = nullptr;
-    VerifyDev Vd{};
-    EqTab tzd{};
-    std::vector<u32> explicit_layers;
-    u32 *d_explicit_layers = nullptr;
-    std::vector<u32> round_layer, zmap;
-    u32 *d_round_layer = nullptr, *d_zmap = nullptr;
-    std::vector<int> eval_steps;  // >= 0: a segment; < 0: layer -step - 1 alone
-    Plan P;                       // this circuit alone (circ = 0)
-    u64 *h_pinned = nullptr;      // small pinned buffer for status/result readback
-};
-
-struct vc_batch {
-    int device = 0;
-    std::vector<vc_circuit *> members;
-    Plan P;
-    char *arena = nullptr;
-    size_t arena_bytes = 0;
-    CallParams *d_cp = nullptr;
-    CallParams *h_cp = nullptr;  // pinned parameter table
-};
 
 // ---------------------------------------------------------------------------------------
 // Plan construction
@@ -584,7 +446,7 @@ static size_t layout(vc_circuit *c, uintptr_t base)
 
 // Device arrays for a plan's descriptors, carved from an arena (own_G: the
 // plan holds its own array of globals, as a batch does).
-static void plan_take(Plan &P, Arena &A, bool own_G)
+void plan_take(Plan &P, Arena &A, bool own_G)
 {
     if (own_G) P.d_G = A.take<Globals>(P.ncirc);
     P.d_checks = A.take<Item>(P.checks.size() + 1);
@@ -612,7 +474,7 @@ static void plan_take(Plan &P, Arena &A, bool own_G)
 // Host-side consistency check of a plan before any of it reaches the device:
 // every item names an existing descriptor and one of its chunks, every
 // descriptor an existing circuit and sum-check instance.
-static bool plan_valid(const Plan &P)
+bool plan_valid(const Plan &P)
 {
     const u32 nc = (u32)P.ncirc;
     for (const Item &it : P.checks)
@@ -660,7 +522,7 @@ static bool plan_valid(const Plan &P)
            P.g_items.size() == P.d_g_items.size();
 }
 
-static cudaError_t plan_upload(Plan &P)
+cudaError_t plan_upload(Plan &P)
 {
     if (!plan_valid(P)) return cudaErrorInvalidValue;
     cudaError_t e = upload(P.d_checks, P.checks);
@@ -685,7 +547,40 @@ static cudaError_t plan_upload(Plan &P)
     return e;
 }
 
-static cudaError_t plan_resources(Plan &P)
+cudaError_t plan_upload_async(Plan &P, cudaStream_t st)
+{
+    if (!plan_valid(P)) return cudaErrorInvalidValue;
+    cudaError_t e = upload_async(P.d_G, P.h_G, st);
+    if (e == cudaSuccess) e = upload_async(P.d_checks, P.checks, st);
+    if (e == cudaSuccess) e = upload_async(P.d_eqjobs, P.eqjobs, st);
+    if (e == cudaSuccess) e = upload_async(P.d_segs, P.segs, st);
+    if (e == cudaSuccess) e = upload_async(P.d_levs, P.levs, st);
+    auto items = [&](std::vector<std::vector<Item>> &v, std::vector<Item *> &dv) {
+        for (size_t k = 0; e == cudaSuccess && k < v.size(); k++) e = upload_async(dv[k], v[k], st);
+    };
+    items(P.seg_items, P.d_seg_items);
+    items(P.lev_items, P.d_lev_items);
+    items(P.line_items, P.d_line_items);
+    items(P.p_items, P.d_p_items);
+    items(P.g_items, P.d_g_items);
+    if (e == cudaSuccess) e = upload_async(P.d_lw, P.lw, st);
+    if (e == cudaSuccess) e = upload_async(P.d_builds, P.builds, st);
+    if (e == cudaSuccess) e = upload_async(P.d_scis, P.scis, st);
+    if (e == cudaSuccess) e = upload_async(P.d_pw, P.pw, st);
+    if (e == cudaSuccess) e = upload_async(P.d_gw, P.gw, st);
+    if (e == cudaSuccess) e = upload_async(P.d_rounds, P.rounds, st);
+    if (e == cudaSuccess) e = upload_async(P.d_outs, P.outs, st);
+    return e;
+}
+
+size_t plan_bytes(Plan &P, bool own_G)
+{
+    Arena A;
+    plan_take(P, A, own_G);
+    return A.off + 256;
+}
+
+cudaError_t plan_resources(Plan &P)
 {
     cudaError_t e = cudaSuccess;
     for (int k = 0; e == cudaSuccess && k < 2; k++) e = cudaStreamCreateWithFlags(&P.aux[k], cudaStreamNonBlocking);
@@ -695,7 +590,7 @@ static cudaError_t plan_resources(Plan &P)
     return e;
 }
 
-static void plan_release(Plan &P)
+void plan_release(Plan &P)
 {
     if (P.exec) cudaGraphExecDestroy(P.exec);
     P.exec = nullptr;
@@ -714,7 +609,7 @@ static void plan_release(Plan &P)
 // the same evaluation step, line wave or sum-check wave are concatenated.
 // Steps of different circuits are independent, and the steps of one circuit
 // keep their order, so each merged launch is valid for every member.
-static void plan_merge(Plan &B, const std::vector<vc_circuit *> &cs)
+void plan_merge(Plan &B, const std::vector<vc_circuit *> &cs)
 {
     B = Plan{};
     B.ncirc = (int)cs.size();
@@ -778,6 +673,7 @@ static void plan_merge(Plan &B, const std::vector<vc_circuit *> &cs)
         }
         B.outs.push_back(cj);
         B.has_tab = B.has_tab || P.has_tab;
+        B.h_G.push_back(cs[j]->G);
     }
 }
 
@@ -791,7 +687,7 @@ static void plan_merge(Plan &B, const std::vector<vc_circuit *> &cs)
 // evaluation, runs the product-weighted waves; `st` evaluates the circuit,
 // reduces the lines and builds the wiring tables; helper stream B runs the
 // general waves once the tables they read exist; the final reduction joins all.
-static void enqueue_plan(Plan &P, cudaStream_t st)
+void enqueue_plan(Plan &P, cudaStream_t st)
 {
     cudaStream_t sa = P.aux[0], sb = P.aux[1];
     const Globals *Gs = P.d_G;
@@ -875,7 +771,7 @@ static cudaError_t plan_launch(Plan &P, cudaStream_t st)
 }
 
 // Kernel launches of one proof (the parameter write included).
-static int count_launches(const Plan &P)
+int count_launches(const Plan &P)
 {
     int n = 2;  // parameters, setup
     n += !P.eqjobs.empty();
@@ -893,7 +789,7 @@ static int count_launches(const Plan &P)
 // Circuits
 // ---------------------------------------------------------------------------------------
 
-extern "C" vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, vc_circuit **out)
+vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **out)
 {
     if (!desc || !out || desc->n_layers < 1 || desc->n_layers > 4096 || !desc->log_width || !desc->wiring)
         return VC_EINVAL;
@@ -977,23 +873,35 @@ extern "C" vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, 
     c->tr_len = tp;
     plan_eval(c);
     c->P.ncirc = 1;
+    Arena A;
+    A.off = layout(c, 0);
+    plan_take(c->P, A, false);
+    c->arena_bytes = A.off + 256;
+    *out = c;
+    return VC_OK;
+}
 
-    DevGuard guard(device);
-    init_device_once(device);
-    size_t bytes = 0;
-    {
-        Arena A;
-        A.off = layout(c, 0);
-        plan_take(c->P, A, false);
-        bytes = A.off + 256;
-    }
+void circuit_free(vc_circuit *c)
+{
+    if (!c) return;
+    plan_release(c->P);
+    if (c->arena) cudaFree(c->arena);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    delete c;
+}
+
+vc_status circuit_allocate(vc_circuit *c)
+{
+    const u32 d = c->d;
+    const size_t bytes = c->arena_bytes;
+    DevGuard guard(c->device);
+    init_device_once(c->device);
     cudaError_t e = cudaMalloc(&c->arena, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        delete c;
+        c->arena = nullptr;
         return e == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA;
     }
-    c->arena_bytes = bytes;
     {
         Arena A;
         A.base = reinterpret_cast<uintptr_t>(c->arena);
@@ -1019,19 +927,32 @@ extern "C" vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, 
         if (e == cudaSuccess) e = upload(const_cast<u32 *>(L.by2_off), c->by2_off[i]);
         if (e == cudaSuccess) e = upload(const_cast<u32 *>(L.by2_g), c->by2_g[i]);
     }
+    if (e == cudaSuccess) e = plan_resources(c->P);
     if (e == cudaSuccess) {
-        launch_init_invfact(c->G.invfact, 0);
-        e = cudaDeviceSynchronize();
+        // on a private stream: creation does not wait for other work on the device
+        launch_init_invfact(c->G.invfact, c->P.cap);
+        e = cudaStreamSynchronize(c->P.cap);
     }
     if (e == cudaSuccess) e = cudaHostAlloc(&c->h_pinned, 64 * sizeof(u64), cudaHostAllocDefault);
-    if (e == cudaSuccess) e = plan_resources(c->P);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        plan_release(c->P);
-        if (c->h_pinned) cudaFreeHost(c->h_pinned);
-        cudaFree(c->arena);
-        delete c;
         return cuda_status(e);
+    }
+    return VC_OK;
+}
+
+extern "C" vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, vc_circuit **out)
+{
+    if (!out) return VC_EINVAL;
+    *out = nullptr;
+    vc_circuit *c = nullptr;
+    vc_status st = circuit_prepare(desc, device, &c);
+    if (st != VC_OK) return st;
+    st = circuit_allocate(c);
+    if (st != VC_OK) {
+        DevGuard guard(device);
+        circuit_free(c);
+        return st;
     }
     *out = c;
     return VC_OK;
@@ -1042,10 +963,7 @@ extern "C" vc_status vc_circuit_destroy(vc_circuit *c)
     if (!c) return VC_OK;
     DevGuard guard(c->device);
     cudaDeviceSynchronize();
-    plan_release(c->P);
-    if (c->arena) cudaFree(c->arena);
-    if (c->h_pinned) cudaFreeHost(c->h_pinned);
-    delete c;
+    circuit_free(c);
     return VC_OK;
 }
 
@@ -1064,7 +982,7 @@ extern "C" vc_status vc_circuit_bytes(const vc_circuit *c, uint64_t *bytes)
 }
 
 // Pointer kind: 1 = device memory of `device`, 0 = host, -1 = device memory of another device.
-static int ptr_kind(const void *p, int device)
+int ptr_kind(const void *p, int device)
 {
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -1076,14 +994,14 @@ static int ptr_kind(const void *p, int device)
 }
 
 // Queue the readback of the circuit's error flags (and their reset) on `st`.
-static cudaError_t queue_status(vc_circuit *c, cudaStream_t st)
+cudaError_t queue_status(vc_circuit *c, cudaStream_t st)
 {
     cudaError_t e = cudaMemcpyAsync(c->h_pinned, c->G.status, sizeof(u32), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->G.status, 0, sizeof(u32), st);
     return e;
 }
 
-static vc_status decode_status(const vc_circuit *c)
+vc_status decode_status(const vc_circuit *c)
 {
     const u32 s = *reinterpret_cast<const u32 *>(c->h_pinned);
     if (s & ST_BAD_INPUT) return VC_EINVAL;
@@ -1277,9 +1195,7 @@ extern "C" vc_status vc_batch_create(vc_circuit *const *circuits, int n, vc_batc
         plan_take(b->P, A, true);
         b->d_cp = A.take<CallParams>(n);
     }
-    std::vector<Globals> Gs;
-    for (vc_circuit *c : b->members) Gs.push_back(c->G);
-    e = upload(b->P.d_G, Gs);
+    e = upload(b->P.d_G, b->P.h_G);
     if (e == cudaSuccess) e = plan_upload(b->P);
     if (e == cudaSuccess) e = cudaHostAlloc(&b->h_cp, n * sizeof(CallParams), cudaHostAllocDefault);
     if (e == cudaSuccess) e = plan_resources(b->P);

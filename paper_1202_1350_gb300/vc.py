@@ -61,6 +61,23 @@ class BatchInfo(ctypes.Structure):
                 ("device_bytes", ctypes.c_uint64), ("gates", ctypes.c_uint64)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("mem_cap_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_uint32),
+                ("max_inflight", ctypes.c_uint32)]
+
+
+class JobInfo(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int), ("status", ctypes.c_int), ("submit_ns", ctypes.c_uint64),
+                ("start_ns", ctypes.c_uint64), ("done_ns", ctypes.c_uint64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("launch_sets", ctypes.c_uint64),
+                ("circuits_created", ctypes.c_uint64), ("circuits_evicted", ctypes.c_uint64),
+                ("held_bytes", ctypes.c_uint64), ("peak_held_bytes", ctypes.c_uint64),
+                ("pending", ctypes.c_uint64), ("max_jobs_in_flight", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+
+
 _lock = threading.Lock()
 _lib = None
 _shapes = {}  # handle -> (inputs, outputs, transcript length), for size checks
@@ -97,6 +114,13 @@ def lib():
             L.vc_batch_prove.argtypes = [vp, ctypes.POINTER(vp), _u64p, ctypes.POINTER(vp), vp]
             L.vc_batch_sync.argtypes = [vp, vp]
             L.vc_batch_get_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
+            L.vc_server_create.argtypes = [ctypes.c_int, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+            L.vc_server_destroy.argtypes = [vp]
+            L.vc_server_submit.argtypes = [vp, ctypes.POINTER(_Desc), vp, ctypes.c_uint64, vp,
+                                           ctypes.POINTER(ctypes.c_uint64)]
+            L.vc_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(JobInfo)]
+            L.vc_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(JobInfo)]
+            L.vc_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
             L.vc_field_mul.argtypes = [vp, vp, vp, ctypes.c_uint64, vp]
             L.vc_field_mul_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                             ctypes.POINTER(ctypes.c_double)]
@@ -110,7 +134,8 @@ def lib():
                          "vc_evaluate", "vc_prove", "vc_circuit_sync", "vc_verify", "vc_prove_batch",
                          "vc_field_mul", "vc_field_mul_rate", "vc_circuit_set_stage_events",
                          "vc_circuit_get_info", "vc_batch_create", "vc_batch_destroy", "vc_batch_prove",
-                         "vc_batch_sync", "vc_batch_get_info"):
+                         "vc_batch_sync", "vc_batch_get_info", "vc_server_create", "vc_server_destroy",
+                         "vc_server_submit", "vc_server_poll", "vc_server_wait", "vc_server_get_stats"):
                 getattr(L, name).restype = st
             _lib = L
     return _lib
@@ -337,6 +362,62 @@ def vc_batch_get_info(b) -> dict:
     info = BatchInfo()
     _check(lib().vc_batch_get_info(b, ctypes.byref(info)), "vc_batch_get_info")
     return {name: getattr(info, name) for name, _ in BatchInfo._fields_}
+
+
+def _desc_struct(log_width, wiring):
+    lw = [int(x) for x in log_width]
+    kinds = [int(k) for k in wiring]
+    d = len(kinds)
+    if len(lw) != d + 1:
+        raise ValueError("log_width must have len(wiring) + 1 entries")
+    lw_a = (ctypes.c_uint32 * (d + 1))(*lw)
+    k_a = (ctypes.c_uint32 * max(d, 1))(*kinds)
+    return _Desc(d, ctypes.cast(lw_a, _u32p), ctypes.cast(k_a, _u32p), None, None, None), (lw_a, k_a)
+
+
+def vc_server_create(device: int = 0, mem_cap_bytes: int = 0, max_batch: int = 0, max_inflight: int = 0):
+    cfg = ServerConfig(mem_cap_bytes, max_batch, max_inflight)
+    h = ctypes.c_void_p()
+    _check(lib().vc_server_create(device, ctypes.byref(cfg), ctypes.byref(h)), "vc_server_create")
+    return h.value
+
+
+def vc_server_destroy(s):
+    _check(lib().vc_server_destroy(s), "vc_server_destroy")
+
+
+def vc_server_submit(s, log_width, wiring, inputs, seed: int, transcript) -> int:
+    """Queue a proof; `inputs` and `transcript` must stay alive until the job is done."""
+    desc, keep = _desc_struct(log_width, wiring)
+    _need(inputs, 1 << int(log_width[-1]), "inputs")
+    jid = ctypes.c_uint64()
+    _check(lib().vc_server_submit(s, ctypes.byref(desc), _ptr(inputs), seed & 0xFFFFFFFFFFFFFFFF, _ptr(transcript),
+                                  ctypes.byref(jid)), "vc_server_submit")
+    del keep
+    return jid.value
+
+
+def _job(info: JobInfo) -> dict:
+    return {"done": bool(info.done), "status": info.status, "submit_ns": info.submit_ns,
+            "start_ns": info.start_ns, "done_ns": info.done_ns}
+
+
+def vc_server_poll(s, job_id: int) -> dict:
+    info = JobInfo()
+    _check(lib().vc_server_poll(s, job_id, ctypes.byref(info)), "vc_server_poll")
+    return _job(info)
+
+
+def vc_server_wait(s, job_id: int) -> dict:
+    info = JobInfo()
+    _check(lib().vc_server_wait(s, job_id, ctypes.byref(info)), "vc_server_wait")
+    return _job(info)
+
+
+def vc_server_get_stats(s) -> dict:
+    st = ServerStats()
+    _check(lib().vc_server_get_stats(s, ctypes.byref(st)), "vc_server_get_stats")
+    return {name: getattr(st, name) for name, _ in ServerStats._fields_ if name != "pad"}
 
 
 def vc_field_mul(a, b, out, stream=None, device: int = 0):

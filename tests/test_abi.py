@@ -74,3 +74,10 @@ def test_batch_arguments_rejected_without_device(libvc):
     assert libvc.vc_batch_destroy(None) == vc.VC_OK
     assert libvc.vc_prove_batch(None, None, None, None, 0, None) == vc.VC_OK
     assert libvc.vc_prove_batch(None, None, None, None, -1, None) == vc.VC_EINVAL
+
+
+@pytest.mark.parametrize("family,logn", [("f2", 0), ("f2", 10), ("f0", 3), ("matmult", 3)])
+def test_transcript_len_matches_library(libvc, family, logn):
+    w, k = circuits.by_name(family, logn)
+    c = oracle.Circuit(w, k)
+    assert circuits.transcript_len(w) == len(c.prove(np.zeros(1 << w[-1], np.uint64), 1))
