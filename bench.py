@@ -92,45 +92,37 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# ---- algorithmic work of the first sum-check wave -----------------------------------------
+# ---- algorithmic work of the dominant launch ----------------------------------------------
 
-PR_CHUNK_LOG = 13  # rounds folded by the first product-weighted wave
-GN_CHUNK_LOG = 12  # rounds folded by the first general wave
-
-
-def sc0_work(widths, kinds):
-    """Field products and table bytes of the first sum-check wave (the dominant
-    launch), counted from the method: per pair of entries, a product-weighted
-    instance (phase 1 of every layer, phase 3 of SQUARE and TREE layers) needs
-    2 products for h(0), h(1) and 1 for the fold of V; a general instance needs
-    3 message products and one fold per table (P, V and B when present), plus
-    forming P (and B) from the wiring in its first round (SQUARE: 2 per entry,
-    TREE: 2 per even entry).  Bytes: every V entry read once (8 B), plus P/B
-    reads for layers whose tables are built beforehand."""
+def wave_work(widths, kinds):
+    """Field multiplications of the first persistent wave launch, counted from
+    the method (the folding prover), for circuits of SQUARE and TREE layers,
+    whose every sum-check and line reduction runs in that launch:
+      * product-weighted instance over n variables (phase 1 of every layer,
+        phase 3 of SQUARE and TREE layers): per pair of entries of every round
+        h(0), h(1) and the fold of V: 3 (2^n - 1);
+      * general instance (phase 2): per pair P V at t = 0, 1, 2 and the folds
+        of P and V (and B for TREE): 5 (6) (2^n - 1), plus forming P (and B)
+        from eq(r_P, .): 2 per entry (SQUARE) or per even entry (TREE);
+      * line reduction over n = s_{i+1} coordinates: folding coordinate j turns
+        pairs of degree-j polynomials into one of degree j + 1 at 2 (j + 1)
+        multiplications: sum_j 2^(n-j-1) 2 (j + 1).
+    Bytes: every V entry of every instance and line reduction read once."""
     mul = 0
     byts = 0
     for i, k in enumerate(kinds):
         si, sn = widths[i], widths[i + 1]
+        assert k in (0, 1), "counted for SQUARE and TREE layers"
         for ph, n in ((1, si), (2, sn), (3, sn)):
             if n == 0:
                 continue
-            prod = ph == 1 or (ph == 3 and k in (0, 1))
-            if prod:
-                nr = min(PR_CHUNK_LOG, n)
-                mul += sum((1 << (n - r - 1)) * 3 for r in range(nr))
-                byts += 8 * (1 << n)
+            if ph == 2:
+                mul += (6 if k == 1 else 5) * ((1 << n) - 1) + (2 if k == 0 else 1) * (1 << n)
             else:
-                nr = min(GN_CHUNK_LOG, n)
-                hasb = k in (1, 3)
-                mul += sum((1 << (n - r - 1)) * (5 + (1 if hasb else 0)) for r in range(nr))
-                if k == 0:
-                    mul += 2 * (1 << n)
-                    byts += 8 * (1 << n)
-                elif k == 1:
-                    mul += 2 * (1 << (n - 1))
-                    byts += 8 * (1 << n)
-                else:
-                    byts += 8 * (1 << n) * (2 + (1 if hasb else 0))
+                mul += 3 * ((1 << n) - 1)
+            byts += 8 * (1 << n)
+        mul += sum((1 << (sn - j - 1)) * 2 * (j + 1) for j in range(sn))
+        byts += 8 * (1 << sn)
     return mul, byts
 
 
@@ -312,9 +304,8 @@ def run_ours(args):
     # the dominant launch: the first product-weighted and general waves run
     # concurrently on two streams; the roofline covers the longer of the two
     # spans, with both launches' work
-    sc0_ms = max(statistics.mean(stage_ms[vc.STAGES.index("prod0")]),
-                 statistics.mean(stage_ms[vc.STAGES.index("gen0")]))
-    mul, byts = sc0_work(widths, kinds)
+    sc0_ms = statistics.mean(stage_ms[vc.STAGES.index("waves")])
+    mul, byts = wave_work(widths, kinds)
     rate = vc.vc_field_mul_rate(local, 2, 1 << 12)
     achieved = mul / (sc0_ms / 1000)
     stages = {name: round(statistics.mean(v), 4) for name, v in zip(vc.STAGES, stage_ms)}
@@ -328,7 +319,8 @@ def run_ours(args):
                    "l2": "flushed between steps (256 MiB write outside the step events)",
                    "parallelism": f"replicas x{world}"},
         "e2e": e2e,
-        "roofline": {"bound": "alu", "kernel": "k_sc_prod + k_sc_gen (first sum-check waves, concurrent)",
+        "roofline": {"bound": "alu", "kernel": "k_waves (persistent launch: every sum-check round and line "
+                                                "reduction of the F2 circuit)",
                      "achieved": achieved / 1e12, "peak": rate / 1e12, "unit": "Tmulmod/s",
                      "frac": achieved / rate, "traffic": None,
                      "peak_source": "measured on this GPU: vc_field_mul_rate variant 2, the kernel's own "

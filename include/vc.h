@@ -137,23 +137,25 @@ vc_status vc_circuit_sync(vc_circuit *c, void *stream);
 vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t seed,
                     const uint64_t *transcript, int *accept, void *stream);
 
-/* Stages of a proof, for timing them.  A proof runs on the caller's stream
- * and two helper streams owned by the circuit (forked from and joined back to
- * the caller's stream): after evaluation, the line reductions, the
- * product-weighted sum-check waves and the general sum-check waves run
- * concurrently. */
+/* Stages of a proof, for timing them.  A proof runs on the caller's stream;
+ * the eq tables and product weights run on a helper stream owned by the
+ * circuit (forked from and joined back to the caller's stream), concurrently
+ * with the evaluation.  The sum-check waves and line reductions of all
+ * layers run as persistent launches that take their chunks from a shared
+ * task counter. */
 typedef enum {
-    VC_STAGE_PROOF = 0,   /* the whole proof                          (caller's stream) */
-    VC_STAGE_SETUP = 1,   /* coins, layer points, eq(z_i, r_P)        (caller's stream) */
-    VC_STAGE_TABLES = 2,  /* split eq tables, product weights         (helper stream A) */
-    VC_STAGE_EVAL = 3,    /* layer-by-layer evaluation                (caller's stream) */
-    VC_STAGE_LINE = 4,    /* line reductions q_i, wiring tables       (caller's stream) */
-    VC_STAGE_PROD0 = 5,   /* first product-weighted sum-check wave    (helper stream A) */
-    VC_STAGE_PRODN = 6,   /* later product-weighted waves             (helper stream A) */
-    VC_STAGE_GEN0 = 7,    /* first general sum-check wave             (helper stream B) */
-    VC_STAGE_GENN = 8,    /* later general waves                      (helper stream B) */
-    VC_STAGE_FINAL = 9,   /* per-round reductions into the transcript (caller's stream) */
-    VC_NUM_STAGES = 10
+    VC_STAGE_PROOF = 0,     /* the whole proof                                          */
+    VC_STAGE_SETUP = 1,     /* coins, layer points, eq(z_i, r_P)                        */
+    VC_STAGE_TABLES = 2,    /* split eq tables, product weights          (helper stream) */
+    VC_STAGE_EVAL = 3,      /* layer-by-layer evaluation                                 */
+    VC_STAGE_WAVES = 4,     /* first persistent launch: line reductions, product-weighted
+                               and on-the-fly general sum-checks (their single-chunk
+                               later waves run inside it)                                */
+    VC_STAGE_WAVESN = 5,    /* later persistent launches of the same kinds (wide layers) */
+    VC_STAGE_BUILD = 6,     /* phase-2/3 wiring tables (MATMULT, F0, EXPLICIT layers)    */
+    VC_STAGE_TABWAVES = 7,  /* general sum-checks over the built tables                  */
+    VC_STAGE_FINAL = 8,     /* per-round reductions into the transcript                  */
+    VC_NUM_STAGES = 9
 } vc_stage;
 
 /* Record CUDA events around the stages of every later vc_prove on this
@@ -176,7 +178,7 @@ typedef struct {
     uint64_t device_bytes;       /* scratch + plan held on the device             */
     uint32_t prove_launches;     /* kernel launches per vc_prove                  */
     uint32_t verify_launches;    /* kernel launches per vc_verify                 */
-    uint32_t sc0_ctas;           /* CTAs of the first sum-check wave              */
+    uint32_t wave_tasks;         /* chunks in the first persistent wave launch    */
     uint32_t pad;
 } vc_circuit_info;
 

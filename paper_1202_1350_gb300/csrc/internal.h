@@ -9,10 +9,11 @@
 #include "plan.h"
 #include "vc.h"
 
-constexpr u32 PR_CHUNK_LOG = PR_M + 7;  // entries folded by one PROD CTA (128 threads x 2^PR_M)
-constexpr u32 GN_CHUNK_LOG = GN_M + 7;  // entries folded by one GEN CTA (128 threads x 2^GN_M)
-constexpr u32 LN_CHUNK0_LOG = 13;       // coordinates folded by the first line wave (LN_E + 8)
-constexpr u32 LN_CHUNKW_LOG = 8;        // coordinates folded by later line waves (one polynomial per thread)
+constexpr u32 WV_LOG = 7;                  // log2 of the threads of a wave CTA
+constexpr u32 PR_CHUNK_LOG = PR_M + WV_LOG;  // rounds of one PROD chunk (2^PR_M entries per thread)
+constexpr u32 GN_CHUNK_LOG = GN_M + WV_LOG;  // rounds of one GEN chunk (2^GN_M entries per thread)
+constexpr u32 LN_CHUNK0_LOG = 6 + WV_LOG;    // coordinates of a first line-wave chunk (64 entries per thread)
+constexpr u32 LN_CHUNKW_LOG = WV_LOG;        // coordinates of a later line-wave chunk (one polynomial per thread)
 
 // Which layers' phase-2/3 tables are built by k_build23 (the rest are formed
 // on the fly or never stored).
@@ -75,21 +76,23 @@ struct Plan {
     std::vector<LayerEval> levs;
     std::vector<std::vector<Item>> seg_items, lev_items;  // per evaluation step
     std::vector<LineWaveDev> lw;
-    std::vector<std::vector<Item>> line_items;  // per line wave
     std::vector<BuildItem> builds;
     std::vector<SciDev> scis;
     std::vector<ProdWave> pw;
     std::vector<GenWave> gw;
-    std::vector<std::vector<Item>> p_items, g_items;  // per sum-check wave
+    // persistent wave launches: groups A (before the wiring tables are built)
+    // and B (general waves over built tables), each one launch
+    std::vector<std::vector<Task>> groupsA, groupsB;
     std::vector<RoundRef> rounds;
     std::vector<u32> outs;
-    bool has_tab = false;
     // device copies
     Item *d_checks = nullptr;
     EqJob *d_eqjobs = nullptr;
     EvalSeg *d_segs = nullptr;
     LayerEval *d_levs = nullptr;
-    std::vector<Item *> d_seg_items, d_lev_items, d_line_items, d_p_items, d_g_items;
+    std::vector<Item *> d_seg_items, d_lev_items;
+    std::vector<Task *> d_groupsA, d_groupsB;
+    u32 *d_ctr = nullptr;  // two task counters per wave launch (A groups, then B groups)
     LineWaveDev *d_lw = nullptr;
     BuildItem *d_builds = nullptr;
     SciDev *d_scis = nullptr;
@@ -98,10 +101,9 @@ struct Plan {
     RoundRef *d_rounds = nullptr;
     u32 *d_outs = nullptr;
     // execution
-    cudaStream_t aux[2] = {};
-    cudaStream_t cap = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_tables = nullptr, ev_eval = nullptr, ev_build = nullptr, ev_prod = nullptr,
-                ev_gen = nullptr;
+    cudaStream_t aux = nullptr;  // eq tables and product weights, concurrent with evaluation
+    cudaStream_t cap = nullptr;  // private stream: graph capture, creation work
+    cudaEvent_t ev_fork = nullptr, ev_tables = nullptr;
     cudaEvent_t ev_params = nullptr;  // a batch's parameter table was copied
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t stage_ev[2 * VC_NUM_STAGES] = {};
@@ -172,6 +174,7 @@ cudaError_t plan_resources(Plan &P);
 void plan_release(Plan &P);
 void plan_merge(Plan &B, const std::vector<vc_circuit *> &cs);
 void enqueue_plan(Plan &P, cudaStream_t st);
+void sort_tasks(Plan &P);
 int count_launches(const Plan &P);
 size_t plan_bytes(Plan &P, bool own_G);  // device bytes of the plan's descriptors
 

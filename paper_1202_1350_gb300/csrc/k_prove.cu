@@ -396,193 +396,8 @@ void launch_check_inputs(const Globals *Gs, const Item *items, int nitems, cudaS
     if (nitems > 0) k_check_inputs<<<nitems, 256, 0, st>>>(Gs, items);
 }
 
-// --------------------------------------------------------------------------------
-// Line reduction: q(t) = V~_{i+1}(l(t)), folding V_{i+1} with coordinates
-// a_k + b_k t in coefficient form (degree grows by one per folded coordinate):
-//   out_c = A_c + a (B_c - A_c) + b (B_{c-1} - A_{c-1}),  c = 0 .. deg + 1.
-// A first-wave CTA folds LN_C0 coordinates of 2^LN_C0 entries: LN_E in
-// registers (2^LN_E consecutive entries per thread), the rest in shared
-// memory.  A later wave folds up to LN_CW coordinates of one polynomial per
-// thread.  A wave whose successor is a single chunk runs that successor in
-// the CTA that finishes last.
-// --------------------------------------------------------------------------------
-
-#define LN_NT 256
-#define LN_E 5
-#define LN_BUFA 4096  // shared-memory polynomial buffers (coefficients)
-#define LN_BUFB 2048
-
-// One level of coefficient folding in registers: D+1 -> D+2 coefficients.
-template <int D>
-__device__ __forceinline__ void line_fold(const u64 (&A)[D + 1], const u64 (&B)[D + 1], u32 a0, u32 a1, u32 b0,
-                                          u32 b1, u64 (&out)[D + 2])
-{
-    u64 d[D + 1];
-#pragma unroll
-    for (int c = 0; c <= D; c++) d[c] = B[c] + (2 * FP_P) - A[c];
-    out[0] = wlin1(A[0], d[0], a0, a1);
-#pragma unroll
-    for (int c = 1; c <= D; c++) out[c] = wlin2(A[c], d[c], d[c - 1], a0, a1, b0, b1);
-    out[D + 1] = wlin1(0, d[D], b0, b1);
-}
-
-// 8 consecutive entries -> one cubic (coordinates 0, 1, 2 of the run).
-__device__ __forceinline__ void line_run8(const u64 *v, const u32 *la, const u32 *lb, u64 (&out)[4])
-{
-    u64 l1[4][2];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        const u64 dd = v[2 * q + 1] + (2 * FP_P) - v[2 * q];
-        l1[q][0] = wlin1(v[2 * q], dd, la[0], la[1]);
-        l1[q][1] = wlin1(0, dd, lb[0], lb[1]);
-    }
-    u64 l2[2][3];
-    line_fold<1>(l1[0], l1[1], la[2], la[3], lb[2], lb[3], l2[0]);
-    line_fold<1>(l1[2], l1[3], la[2], la[3], lb[2], lb[3], l2[1]);
-    line_fold<2>(l2[0], l2[1], la[4], la[5], lb[4], lb[5], out);
-}
-
-// Coefficient `c` of the fold of polynomials A, B (degree deg, W values).
-__device__ __forceinline__ u64 line_coef(const u64 *A, const u64 *B, u32 deg, u32 c, const u32 *la, const u32 *lb)
-{
-    const u64 dc = (c <= deg) ? B[c] + (2 * FP_P) - A[c] : 0;
-    const u64 dm = (c >= 1) ? B[c - 1] + (2 * FP_P) - A[c - 1] : 0;
-    const u64 ac = (c <= deg) ? A[c] : 0;
-    return wlin2(ac, dc, dm, la[0], la[1], lb[0], lb[1]);
-}
-
-// One chunk of one line wave, by the whole CTA.
-__device__ void line_chunk(const Globals &G, const LineWaveDev &W, u32 chunk, u64 *bufA, u64 *bufB)
-{
-    __shared__ u32 s_la[32][2], s_lb[32][2];  // limbs of a_k and b_k for this wave's coordinates
-    const u32 tid = threadIdx.x;
-    if (tid < W.nl) {
-        const u64 a = G.chal[W.a_off + W.l0 + tid];
-        const u64 b = f_sub(G.chal[W.b_off + W.l0 + tid], a);
-        limbs31(a, s_la[tid][0], s_la[tid][1]);
-        limbs31(b, s_lb[tid][0], s_lb[tid][1]);
-    }
-    __syncthreads();
-    u32 m, deg, k0;  // polynomials in bufA, their degree, coordinates already folded
-    if (W.l0 == 0) {
-        const u32 e = (W.nl >= LN_E) ? LN_E : 0;
-        const u32 na = 1u << (W.nl - e);
-        const u64 base = (u64)chunk << W.nl;
-        if (tid < na) {
-            if (e == LN_E) {
-                u64 v[32];
-                const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(W.in + base + ((u64)tid << LN_E));
-#pragma unroll
-                for (int q = 0; q < 16; q++) {
-                    const ulonglong2 w = src[q];
-                    v[2 * q] = w.x;
-                    v[2 * q + 1] = w.y;
-                }
-                u32 la[10], lb[10];
-#pragma unroll
-                for (int k = 0; k < 5; k++) {
-                    la[2 * k] = s_la[k][0];
-                    la[2 * k + 1] = s_la[k][1];
-                    lb[2 * k] = s_lb[k][0];
-                    lb[2 * k + 1] = s_lb[k][1];
-                }
-                u64 c0[4], c1[4], c2[4], c3[4];
-                line_run8(v, la, lb, c0);
-                line_run8(v + 8, la, lb, c1);
-                line_run8(v + 16, la, lb, c2);
-                line_run8(v + 24, la, lb, c3);
-                u64 q01[5], q23[5], p[6];
-                line_fold<3>(c0, c1, la[6], la[7], lb[6], lb[7], q01);
-                line_fold<3>(c2, c3, la[6], la[7], lb[6], lb[7], q23);
-                line_fold<4>(q01, q23, la[8], la[9], lb[8], lb[9], p);
-#pragma unroll
-                for (int c = 0; c < 6; c++) bufA[tid * 6 + c] = p[c];
-            } else {
-                bufA[tid] = W.in[base + tid];
-            }
-        }
-        m = na;
-        deg = e;
-        k0 = e;
-    } else {
-        // polynomials of degree l0 from the previous wave (written by other
-        // CTAs of this launch when run as a tail: read through L2)
-        const u32 din = W.l0, npoly = 1u << W.nl, half = npoly >> 1, C = din + 2;
-        const u64 *in = W.in + ((u64)chunk << W.nl) * (din + 1);
-        for (u32 idx = tid; idx < half * C; idx += LN_NT) {
-            const u32 j = idx / C, c = idx - j * C;
-            const u64 *A = in + (u64)(2 * j) * (din + 1), *B = A + (din + 1);
-            const u64 dc = (c <= din) ? __ldcg(B + c) + (2 * FP_P) - __ldcg(A + c) : 0;
-            const u64 dm = (c >= 1) ? __ldcg(B + c - 1) + (2 * FP_P) - __ldcg(A + c - 1) : 0;
-            const u64 ac = (c <= din) ? __ldcg(A + c) : 0;
-            bufA[j * C + c] = wlin2(ac, dc, dm, s_la[0][0], s_la[0][1], s_lb[0][0], s_lb[0][1]);
-        }
-        m = half;
-        deg = din + 1;
-        k0 = 1;
-    }
-    __syncthreads();
-    u64 *cur = bufA, *nxt = bufB;
-    for (u32 k = k0; k < W.nl; k++) {
-        const u32 half = m >> 1, C = deg + 2;
-        for (u32 idx = tid; idx < half * C; idx += LN_NT) {
-            const u32 j = idx / C, c = idx - j * C;
-            nxt[j * C + c] = line_coef(cur + (2 * j) * (deg + 1), cur + (2 * j + 1) * (deg + 1), deg, c, s_la[k],
-                                       s_lb[k]);
-        }
-        __syncthreads();
-        u64 *t = cur;
-        cur = nxt;
-        nxt = t;
-        m = half;
-        deg += 1;
-    }
-    // cur[0..deg] is this chunk's polynomial
-    if (!W.last) {
-        for (u32 c = tid; c <= deg; c += LN_NT) W.out[(u64)chunk * (deg + 1) + c] = cur[c];
-    } else {
-        // q(t) for t = 0..n by Horner; q(0) = V~_{i+1}(r1) feeds phase 3
-        for (u32 t = tid; t <= W.n; t += LN_NT) {
-            u64 acc = cur[deg];
-            for (int c = (int)deg - 1; c >= 0; c--) acc = wred(wmul(acc, (u64)t) + cur[c]);
-            G.tr[W.tr_q + t] = wcanon(acc);
-        }
-        if (tid == 0) G.scal[SCAL_V1(W.layer)] = wcanon(cur[0]);
-    }
-}
-
-extern __shared__ u64 ln_dyn[];
-
-__global__ void __launch_bounds__(LN_NT, 2) k_line_wave(const Globals *Gs, const LineWaveDev *waves, const Item *items)
-{
-    const Item it = items[blockIdx.x];
-    const LineWaveDev &W = waves[it.wave];
-    const Globals &G = Gs[W.circ];
-    u64 *bufA = ln_dyn, *bufB = ln_dyn + LN_BUFA;
-    line_chunk(G, W, it.chunk, bufA, bufB);
-    if (!W.tail) return;
-    // the CTA that finishes last runs the next wave (one chunk); no CTA waits
-    __shared__ u32 s_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(W.counter, 1u) == W.nchunks - 1) ? 1u : 0u;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (threadIdx.x == 0) *W.counter = 0;
-    line_chunk(G, waves[it.wave + 1], 0, bufA, bufB);
-}
-
-void launch_line_wave(const Globals *Gs, const LineWaveDev *lw, const Item *items, int nitems, cudaStream_t st)
-{
-    if (nitems > 0)
-        k_line_wave<<<nitems, LN_NT, (size_t)(LN_BUFA + LN_BUFB) * sizeof(u64), st>>>(Gs, lw, items);
-}
-
 void prove_kernels_init()
 {
-    cudaFuncSetAttribute(k_line_wave, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)((LN_BUFA + LN_BUFB) * sizeof(u64)));
     cudaFuncSetAttribute(k_eval_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * EV_MAXB * sizeof(u64)));
 }
 

@@ -22,6 +22,9 @@
 // accumulate exactly in 128 bits and are reduced once per round per thread;
 // only transcript entries are made canonical.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+
 #include "plan.h"
 
 // --------------------------------------------------------------------------------
@@ -183,63 +186,133 @@ void launch_prep_prod(const Globals *Gs, const SciDev *scis, const ProdWave *wav
 }
 
 // --------------------------------------------------------------------------------
-// PROD waves
+// One persistent launch for the waves of every instance: CTAs of WV_NT threads
+// take tasks (one chunk of one line, PROD or GEN wave) from a shared counter,
+// so the whole device stays busy until the last task; a wave whose successor
+// is a single chunk runs that successor in the CTA that finishes the wave's
+// last chunk (no CTA ever waits for another).
 // --------------------------------------------------------------------------------
 
-#define PR_NT 128
-#define PR_SUB 16  // a thread's 2^PR_M entries are processed as runs of PR_SUB
+#define WV_NT 128
+#define PR_SUB 16  // PROD runs of 16 entries (rounds 0..3 per run)
 
-// Rounds OFF.. of a product-weighted chunk across threads.  Thread t holds
+struct ProdSmem {
+    u32 r[32][2];
+    u64 Q[64];
+    u64 E[256];
+    u64 lvl[WV_NT / 32];
+    u64 w[WV_NT / 32][32];
+    u64 echunk;
+};
+
+struct GenSmem {
+    u32 r[32][2];
+    u64 lvl[3][WV_NT / 32];
+    u64 w[WV_NT / 32][40];
+    u64 hs[9][WV_NT];  // per-thread sums of in-register rounds 2..4 (kept out of registers)
+};
+
+#define LN_E 6        // line: coordinates folded per thread in registers (first wave)
+#define LN_BUFA 2048  // line: shared-memory polynomial buffers (coefficients): a later
+#define LN_BUFB 1024  // wave's first level is 64 pairs x <= 32 coefficients
+
+struct LineSmem {
+    u32 la[32][2], lb[32][2];  // limbs of a_k and b_k for the wave's coordinates
+    u64 bufA[LN_BUFA];
+    u64 bufB[LN_BUFB];
+};
+
+union WaveSmem {
+    ProdSmem prod;
+    GenSmem gen;
+    LineSmem line;
+};
+
+// Bring the line holding p into L1 ahead of its load (no register cost).
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
+// Sum of the four warps' per-warp round sums (W values).
+__device__ __forceinline__ u64 cta_sum4(const u64 *a, const u64 *b, const u64 *c, const u64 *d)
+{
+    return wred(*a + *b + *c + *d);
+}
+
+// ---- PROD -----------------------------------------------------------------------
+
+// Sum over the lanes l = 0 mod 2^(kk+1) of a warp (the lanes holding a
+// contribution in cross round kk; the others hold 0), written by lane 0.
+__device__ __forceinline__ void prod_round_sum(u64 c0, u64 c1, u32 kk, u64 *out)
+{
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        if ((u32)o < (2u << kk)) break;
+        c0 = wred(c0 + __shfl_xor_sync(0xffffffffu, c0, o));
+        c1 = wred(c1 + __shfl_xor_sync(0xffffffffu, c1, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        out[0] = c0;
+        out[1] = c1;
+    }
+}
+
+// Rounds off.. of a product-weighted chunk across threads.  Thread t holds
 // level value t (t < na); a round pairs values 2y and 2y+1, which sit in the
 // threads t = y 2^(kk+1) and t + 2^kk, and the first of them keeps the folded
 // value, so rounds stay inside a warp for kk < 5 (shuffles) and continue in
-// warp 0 after one exchange through shared memory.  Each active thread adds
-// E_k(y) u0 and E_k(y) u1 to hv[2 kk], hv[2 kk + 1].
-__device__ __forceinline__ void prod_cross(u64 (&hv)[16], u64 uv, u32 off, u32 tid, u32 na, u32 nr,
-                                           const u64 *s_E, u32 eoff0, const u32 (*s_r)[2], u64 *s_lvl)
+// warp 0 after one exchange through shared memory.  The active thread of a
+// pair contributes E_k(y) u0 and E_k(y) u1; the per-warp sums of round k go
+// to sm.w[warp][2k..2k+1] (CTA-level rounds: warp 0's row, zeros elsewhere).
+__device__ __forceinline__ void prod_cross(u64 uv, u32 off, u32 tid, u32 na, u32 nr, ProdSmem &sm, u32 eoff0)
 {
     const u32 lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-    for (int kk = 0; kk < 5; kk++) {
+    // rolled: one copy of the round body keeps the kernel small
+#pragma unroll 1
+    for (u32 kk = 0; kk < 5; kk++) {
         const u32 k = off + kk;
         if (k < nr) {  // uniform
             const u64 u1 = __shfl_down_sync(0xffffffffu, uv, 1u << kk);
+            u64 c0 = 0, c1 = 0;
             if ((tid & ((2u << kk) - 1)) == 0 && tid < na) {
                 const u32 y = tid >> (kk + 1);
-                const u64 w = s_E[eoff0 - (1u << (nr - k)) + y];
-                hv[2 * kk] = wmul(w, uv);
-                hv[2 * kk + 1] = wmul(w, u1);
-                uv = wfold(uv, u1, s_r[k][0], s_r[k][1]);
+                const u64 w = sm.E[eoff0 - (1u << (nr - k)) + y];
+                c0 = wmul(w, uv);
+                c1 = wmul(w, u1);
+                uv = wfold(uv, u1, sm.r[k][0], sm.r[k][1]);
             }
+            prod_round_sum(c0, c1, kk, &sm.w[warp][2 * k]);
         }
     }
-    if (lane == 0) s_lvl[warp] = uv;
+    if (lane == 0) {
+        sm.lvl[warp] = uv;
+        for (u32 k = off + 5; k < nr && k < off + 7; k++)
+            if (warp) sm.w[warp][2 * k] = sm.w[warp][2 * k + 1] = 0;
+    }
     __syncthreads();
     if (off + 5 < nr && warp == 0) {
-        uv = (lane < PR_NT / 32) ? s_lvl[lane] : 0;
-#pragma unroll
-        for (int kk = 5; kk < 7; kk++) {
+        uv = (lane < WV_NT / 32) ? sm.lvl[lane] : 0;
+        for (u32 kk = 5; kk < 7; kk++) {
             const u32 k = off + kk;
             if (k < nr) {
                 const u64 u1 = __shfl_down_sync(0xffffffffu, uv, 1u << (kk - 5));
                 const u32 t = lane << 5;  // the thread index this lane stands for
+                u64 c0 = 0, c1 = 0;
                 if ((t & ((2u << kk) - 1)) == 0 && t < na) {
                     const u32 y = t >> (kk + 1);
-                    const u64 w = s_E[eoff0 - (1u << (nr - k)) + y];
-                    hv[2 * kk] = wmul(w, uv);
-                    hv[2 * kk + 1] = wmul(w, u1);
-                    uv = wfold(uv, u1, s_r[k][0], s_r[k][1]);
+                    const u64 w = sm.E[eoff0 - (1u << (nr - k)) + y];
+                    c0 = wmul(w, uv);
+                    c1 = wmul(w, u1);
+                    uv = wfold(uv, u1, sm.r[k][0], sm.r[k][1]);
                 }
+                prod_round_sum(c0, c1, kk - 5, &sm.w[0][2 * k]);
             }
         }
-        if (lane == 0) s_lvl[0] = uv;
+        if (lane == 0) sm.lvl[0] = uv;
     }
 }
 
-// Rounds 0..3 of one run of 16 entries (run index sub within the thread):
-// pair weights Q_k(q), q = pair index + (sub << (3 - k)); adds the sums to
-// hv[2k], hv[2k+1] and returns the folded value.
-__device__ __forceinline__ u64 prod_run16(u64 (&u)[16], u32 sub, const u64 *s_Q, const u32 (*s_r)[2], u64 (&hv)[12])
+// Rounds 0..3 of one run of 16 entries (run `sub` of the thread's 2^e):
+// pair weights Q_k(q), q = pair index + (sub << (3 - k)).
+__device__ __forceinline__ u64 prod_run16(u64 (&u)[16], u32 sub, u32 e, const ProdSmem &sm, u64 (&h)[12])
 {
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -248,11 +321,11 @@ __device__ __forceinline__ u64 prod_run16(u64 (&u)[16], u32 sub, const u64 *s_Q,
         acc_zero(a1);
         acc_zero(b0);
         acc_zero(b1);
-        const u32 rr0 = s_r[k][0], rr1 = s_r[k][1];
-        const u32 qoff = (1u << PR_M) - (1u << (PR_M - k)) + (sub << (3 - k));
+        const u32 rr0 = sm.r[k][0], rr1 = sm.r[k][1];
+        const u32 qoff = (1u << e) - (1u << (e - k)) + (sub << (3 - k));
 #pragma unroll
         for (int q = 0; q < (8 >> k); q++) {
-            const u64 w = s_Q[qoff + q];
+            const u64 w = sm.Q[qoff + q];
             const u64 u0 = u[2 * q], u1 = u[2 * q + 1];
             if (q & 1) {
                 mac(b0, w, u0);
@@ -263,156 +336,169 @@ __device__ __forceinline__ u64 prod_run16(u64 (&u)[16], u32 sub, const u64 *s_Q,
             }
             u[q] = wfold(u0, u1, rr0, rr1);
         }
-        hv[2 * k] = wred(hv[2 * k] + acc_red(a0) + acc_red(b0));
-        hv[2 * k + 1] = wred(hv[2 * k + 1] + acc_red(a1) + acc_red(b1));
+        h[2 * k] = wred(h[2 * k] + acc_red(a0) + acc_red(b0));
+        h[2 * k + 1] = wred(h[2 * k + 1] + acc_red(a1) + acc_red(b1));
     }
     return u[0];
 }
 
-// Sum over the CTA's warps of per-warp round sums s_w[warp][i] (W values).
-__device__ __forceinline__ u64 cta_sum4(const u64 (*s_w)[32], u32 i)
+// In-register rounds for e in 4..6: runs of 16, then rounds 4 and 5 on the
+// runs' folded values.
+__device__ __forceinline__ u64 prod_regs_runs(const u64 *src, u32 e, const ProdSmem &sm, u64 (&h)[12])
 {
-    return wred(s_w[0][i] + s_w[1][i] + s_w[2][i] + s_w[3][i]);
+    const u32 nruns = 1u << (e - 4);
+    const u32 q4 = (1u << e) - (1u << (e - 4)), q5 = (1u << e) - 2;
+    u64 f0 = 0, g0 = 0, uv = 0;
+    // a rolled loop keeps the kernel small (instruction-cache bound when unrolled)
+#pragma unroll 1
+    for (u32 sub = 0; sub < nruns; sub++) {
+        if (sub + 1 < nruns) prefetch_l1(src + (sub + 1) * PR_SUB);
+        u64 u[16];
+        const ulonglong2 *sv = reinterpret_cast<const ulonglong2 *>(src + sub * PR_SUB);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const ulonglong2 t = __ldcg(sv + q);
+            u[2 * q] = t.x;
+            u[2 * q + 1] = t.y;
+        }
+        const u64 fs = prod_run16(u, sub, e, sm, h);
+        if (nruns == 1) {
+            uv = fs;
+        } else if (sub & 1) {
+            const u64 w = sm.Q[q4 + (sub >> 1)];
+            h[8] = wred(h[8] + wmul(w, f0));
+            h[9] = wred(h[9] + wmul(w, fs));
+            const u64 g = wfold(f0, fs, sm.r[4][0], sm.r[4][1]);
+            if (nruns == 2) {
+                uv = g;
+            } else if (sub == 1) {
+                g0 = g;
+            } else {
+                const u64 w5 = sm.Q[q5];
+                h[10] = wmul(w5, g0);
+                h[11] = wmul(w5, g);
+                uv = wfold(g0, g, sm.r[5][0], sm.r[5][1]);
+            }
+        } else {
+            f0 = fs;
+        }
+    }
+    return uv;
 }
 
-__global__ void __launch_bounds__(PR_NT, 4) k_sc_prod(const Globals *Gs, const ProdWave *waves, const Item *items)
+// One chunk of a PROD wave.
+__device__ void prod_chunk(const Globals &G, const ProdWave &W, u32 chunk, ProdSmem &sm)
 {
-    constexpr int M = PR_M;
-    __shared__ u32 s_r[32][2];
-    __shared__ u64 s_Q[1 << M];
-    __shared__ u64 s_E[256];
-    __shared__ u64 s_lvl[PR_NT / 32];
-    __shared__ u64 s_w[PR_NT / 32][32];
-    __shared__ u64 s_echunk;
-
-    const Item it = items[blockIdx.x];
-    const ProdWave &W = waves[it.wave];
-    const Globals &G = Gs[W.circ];
     const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const u32 nr = W.nr, e = W.e, chunk = it.chunk;
+    const u32 nr = W.nr, e = W.e;
     const u32 na = 1u << (nr - e);
     const u64 base = (u64)chunk << nr;
-    if (tid < nr) limbs31(G.chal[W.chal_off + tid], s_r[tid][0], s_r[tid][1]);
+    if (tid < nr) limbs31(G.chal[W.chal_off + tid], sm.r[tid][0], sm.r[tid][1]);
     const u64 *blk = W.wblk;
     const u32 qsize = (1u << e) - 1;
     const u32 kb = e ? e - 1 : 0;
     const u32 esize = (1u << (nr - kb)) - 1;
-    if (tid < qsize) s_Q[tid] = blk[tid];
-    for (u32 k = tid; k < esize; k += PR_NT) s_E[k] = blk[qsize + k];
+    if (tid < qsize) sm.Q[tid] = blk[tid];
+    for (u32 k = tid; k < esize; k += WV_NT) sm.E[k] = blk[qsize + k];
     if (tid == 0) {
         const u64 *olo = blk + qsize + esize;
         const u64 *ohi = olo + (1u << W.ho);
-        s_echunk = f_mul(olo[chunk & ((1u << W.ho) - 1)], ohi[chunk >> W.ho]);
+        sm.echunk = f_mul(olo[chunk & ((1u << W.ho) - 1)], ohi[chunk >> W.ho]);
     }
     __syncthreads();
-
     const u32 eoff0 = 1u << (nr - kb);
-    u64 uv = 0;  // the thread's level value after its in-register rounds
-    u64 hv[16];  // cross-thread rounds: hv[2 kk + t]
+    u64 uv = 0;
+    if (e > 0) {
+        u64 h[12];
 #pragma unroll
-    for (int i = 0; i < 16; i++) hv[i] = 0;
-    if (e == M) {
-        // rounds 0..M-1 in registers: four runs of 16 entries (rounds 0..3
-        // each), then rounds 4 and 5 on the runs' folded values
-        u64 h0[12];
-#pragma unroll
-        for (int i = 0; i < 12; i++) h0[i] = 0;
+        for (int i = 0; i < 12; i++) h[i] = 0;
         if (tid < na) {
-            const u64 *src = W.in + base + ((u64)tid << M);
-            const u32 q4 = (1u << M) - 4, q5 = (1u << M) - 2;
-            u64 f0 = 0, g0 = 0;
-            // a rolled loop keeps the kernel small (instruction-cache bound when unrolled)
-#pragma unroll 1
-            for (u32 sub = 0; sub < 4; sub++) {
-                u64 u[16];
-                const ulonglong2 *sv = reinterpret_cast<const ulonglong2 *>(src + sub * PR_SUB);
+            const u64 *src = W.in + base + ((u64)tid << e);
+            uv = prod_regs_runs(src, e, sm, h);
+            const u64 T = sm.E[tid];  // E_{e-1}(tid): weight of the chunk bits above the thread's run
 #pragma unroll
-                for (int q = 0; q < 8; q++) {
-                    const ulonglong2 t = sv[q];
-                    u[2 * q] = t.x;
-                    u[2 * q + 1] = t.y;
-                }
-                const u64 fs = prod_run16(u, sub, s_Q, s_r, h0);
-                if (sub & 1) {
-                    // round 4 on runs (sub-1, sub); round 5 on the two results
-                    const u64 w = s_Q[q4 + (sub >> 1)];
-                    h0[8] = wred(h0[8] + wmul(w, f0));
-                    h0[9] = wred(h0[9] + wmul(w, fs));
-                    const u64 g = wfold(f0, fs, s_r[4][0], s_r[4][1]);
-                    if (sub == 1) {
-                        g0 = g;
-                    } else {
-                        const u64 w5 = s_Q[q5];
-                        h0[10] = wmul(w5, g0);
-                        h0[11] = wmul(w5, g);
-                        uv = wfold(g0, g, s_r[5][0], s_r[5][1]);
-                    }
-                } else {
-                    f0 = fs;
-                }
-            }
-            const u64 T = s_E[tid];  // E_{M-1}(tid): the weight of the chunk bits above the thread's run
-#pragma unroll
-            for (int i = 0; i < 12; i++) h0[i] = wmul(T, h0[i]);
+            for (int i = 0; i < 12; i++) h[i] = wmul(T, h[i]);
         }
-        // per-warp sums of the in-register rounds
         u64 h16[16];
 #pragma unroll
-        for (int i = 0; i < 16; i++) h16[i] = (i < 12) ? h0[i] : 0;
+        for (int i = 0; i < 16; i++) h16[i] = (i < 12) ? h[i] : 0;
         const u64 s = warp_sum16(h16);
-        if ((lane & 1) == 0 && (lane >> 1) < 12) s_w[warp][lane >> 1] = s;
-        prod_cross(hv, uv, M, tid, na, nr, s_E, eoff0, s_r, s_lvl);
-    } else {
-        if (tid < na) uv = W.in[base + tid];
-        prod_cross(hv, uv, 0, tid, na, nr, s_E, eoff0, s_r, s_lvl);
+        if ((lane & 1) == 0 && (lane >> 1) < 2 * e) sm.w[warp][lane >> 1] = s;
+    } else if (tid < na) {
+        uv = __ldcg(W.in + base + tid);
     }
-    // per-warp sums of the cross-thread rounds (after the register rounds' 12 slots when e = M)
-    {
-        const u64 s = warp_sum16(hv);
-        const u32 o = e ? 12 : 0;
-        if ((lane & 1) == 0 && (lane >> 1) < 2 * (nr - e) && (lane >> 1) < 14) s_w[warp][o + (lane >> 1)] = s;
-    }
+    prod_cross(uv, e, tid, na, nr, sm, eoff0);
     __syncthreads();
     if (tid < 2 * nr) {
-        const u64 sum = cta_sum4(s_w, tid);
+        const u64 sum = wred(sm.w[0][tid] + sm.w[1][tid] + sm.w[2][tid] + sm.w[3][tid]);
         const u32 k = tid >> 1, t = tid & 1;
-        W.part[((u64)k * W.nchunks + chunk) * 2 + t] = wmul(sum, s_echunk);
+        W.part[((u64)k * W.nchunks + chunk) * 2 + t] = wmul(sum, sm.echunk);
     }
-    if (!(W.flags & WF_LAST) && tid == 0) W.out[chunk] = s_lvl[0];
+    if (!(W.flags & WF_LAST) && tid == 0) W.out[chunk] = sm.lvl[0];
 }
 
-void launch_sc_prod(const Globals *Gs, const ProdWave *waves, const Item *items, int nitems, cudaStream_t st)
-{
-    if (nitems > 0) k_sc_prod<<<nitems, PR_NT, 0, st>>>(Gs, waves, items);
-}
+// ---- GEN ------------------------------------------------------------------------
 
-// --------------------------------------------------------------------------------
-// GEN waves: tables P, V, B folded every round; message values at t = 0, 1, 2.
-// --------------------------------------------------------------------------------
-
-#define GN_NT 128
-
-// P and B of the first wave for the on-the-fly kinds, for the run of 8
-// entries at x0 whose V values are v[].
-__device__ __forceinline__ void gen_source(const Globals &G, const GenWave &W, u64 x0, const u64 (&v)[8],
-                                           u64 (&p)[8], u64 (&b)[8])
+// P and B of the first wave for the on-the-fly kinds, for N consecutive
+// entries at x0 (x0 even) whose V values are v[].
+template <int N>
+__device__ __forceinline__ void gen_source(const Globals &G, const GenWave &W, u64 x0, const u64 (&v)[N],
+                                           u64 (&p)[N], u64 (&b)[N])
 {
     const LayerDev &L = G.layers[W.layer];
     if (W.src == GS_SQ2) {
 #pragma unroll
-        for (int q = 0; q < 8; q++) {
+        for (int q = 0; q < N; q++) {
             p[q] = wmul(eq_at(L.trp, x0 + q), v[q]);
             b[q] = 0;
         }
     } else {  // GS_TREE2
 #pragma unroll
-        for (int q = 0; q < 8; q += 2) {
+        for (int q = 0; q < N; q += 2) {
             const u64 w = eq_at(L.trp, (x0 + q) >> 1);
             p[q] = w;
             b[q] = wmul(w, v[q + 1]);
             p[q + 1] = 0;
             b[q + 1] = 0;
         }
+    }
+}
+
+// N consecutive entries of a GEN wave's tables at x0 (first wave: P, B formed
+// from the wiring; later waves: read).
+template <int N>
+__device__ __forceinline__ void gen_load(const Globals &G, const GenWave &W, u64 x0, bool hasB, u64 (&p)[N],
+                                         u64 (&v)[N], u64 (&b)[N])
+{
+    const ulonglong2 *sv = reinterpret_cast<const ulonglong2 *>(W.inV + x0);
+#pragma unroll
+    for (int q = 0; q < N / 2; q++) {
+        const ulonglong2 t = __ldcg(sv + q);
+        v[2 * q] = t.x;
+        v[2 * q + 1] = t.y;
+    }
+    if (W.src != GS_NONE) {
+        gen_source<N>(G, W, x0, v, p, b);
+        return;
+    }
+    const ulonglong2 *sp = reinterpret_cast<const ulonglong2 *>(W.inP + x0);
+#pragma unroll
+    for (int q = 0; q < N / 2; q++) {
+        const ulonglong2 t = __ldcg(sp + q);
+        p[2 * q] = t.x;
+        p[2 * q + 1] = t.y;
+    }
+    if (hasB) {
+        const ulonglong2 *sb = reinterpret_cast<const ulonglong2 *>(W.inB + x0);
+#pragma unroll
+        for (int q = 0; q < N / 2; q++) {
+            const ulonglong2 t = __ldcg(sb + q);
+            b[2 * q] = t.x;
+            b[2 * q + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; q++) b[q] = 0;
     }
 }
 
@@ -428,85 +514,34 @@ __device__ __forceinline__ void gen_pair(u64 p0, u64 p1, u64 v0, u64 v1, u64 b0,
     bn = wfold(b0, b1, rr0, rr1);
 }
 
-// Rounds off.. of a general chunk across threads (same placement as
-// prod_cross: the first thread of each pair keeps the folded values).
-__device__ __forceinline__ void gen_cross(u64 (&hv)[21], u64 &p, u64 &v, u64 &b, u32 off, u32 tid, u32 na, u32 nr,
-                                          const u32 (*s_r)[2], u64 (*s_lvl)[GN_NT / 32])
+// Round k on two folded triples held by one thread, summed into the
+// thread's shared-memory slots hs[3j..3j+2].
+__device__ __forceinline__ void gen_pair_acc(u64 p0, u64 p1, u64 v0, u64 v1, u64 b0, u64 b1, u32 rr0, u32 rr1,
+                                             GenSmem &sm, u32 j, u64 &pn, u64 &vn, u64 &bn)
 {
-    const u32 lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-    for (int kk = 0; kk < 5; kk++) {
-        const u32 k = off + kk;
-        if (k < nr) {
-            const u32 d = 1u << kk;
-            const u64 p1 = __shfl_down_sync(0xffffffffu, p, d);
-            const u64 v1 = __shfl_down_sync(0xffffffffu, v, d);
-            const u64 b1 = __shfl_down_sync(0xffffffffu, b, d);
-            if ((tid & ((2u << kk) - 1)) == 0 && tid < na)
-                gen_pair(p, p1, v, v1, b, b1, s_r[k][0], s_r[k][1], hv[3 * kk], hv[3 * kk + 1], hv[3 * kk + 2], p,
-                         v, b);
-        }
-    }
-    if (lane == 0) {
-        s_lvl[0][warp] = p;
-        s_lvl[1][warp] = v;
-        s_lvl[2][warp] = b;
-    }
-    __syncthreads();
-    if (off + 5 < nr && warp == 0) {
-        const bool have = lane < GN_NT / 32;
-        p = have ? s_lvl[0][lane] : 0;
-        v = have ? s_lvl[1][lane] : 0;
-        b = have ? s_lvl[2][lane] : 0;
-#pragma unroll
-        for (int kk = 5; kk < 7; kk++) {
-            const u32 k = off + kk;
-            if (k < nr) {
-                const u32 d = 1u << (kk - 5);
-                const u64 p1 = __shfl_down_sync(0xffffffffu, p, d);
-                const u64 v1 = __shfl_down_sync(0xffffffffu, v, d);
-                const u64 b1 = __shfl_down_sync(0xffffffffu, b, d);
-                const u32 t = lane << 5;
-                if ((t & ((2u << kk) - 1)) == 0 && t < na)
-                    gen_pair(p, p1, v, v1, b, b1, s_r[k][0], s_r[k][1], hv[3 * kk], hv[3 * kk + 1], hv[3 * kk + 2],
-                             p, v, b);
-            }
-        }
-        if (lane == 0) {
-            s_lvl[0][0] = p;
-            s_lvl[1][0] = v;
-            s_lvl[2][0] = b;
-        }
-    }
+    u64 c0, c1, c2;
+    gen_pair(p0, p1, v0, v1, b0, b1, rr0, rr1, c0, c1, c2, pn, vn, bn);
+    const u32 t = threadIdx.x;
+    sm.hs[3 * j][t] = wred(sm.hs[3 * j][t] + c0);
+    sm.hs[3 * j + 1][t] = wred(sm.hs[3 * j + 1][t] + c1);
+    sm.hs[3 * j + 2][t] = wred(sm.hs[3 * j + 2][t] + c2);
 }
 
-// Cross-thread rounds from round off, then the per-warp sums of their
-// message values into s_w[warp][off * 3 ..] (after the register rounds' slots).
-__device__ __forceinline__ void gen_cross_sum(u64 &p, u64 &v, u64 &b, u32 off, u32 tid, u32 na, u32 nr,
-                                              const u32 (*s_r)[2], u64 (*s_lvl)[GN_NT / 32], u64 (*s_w)[40])
-{
-    u64 hv[32];
-#pragma unroll
-    for (int i = 0; i < 32; i++) hv[i] = 0;
-    gen_cross(reinterpret_cast<u64(&)[21]>(hv), p, v, b, off, tid, na, nr, s_r, s_lvl);
-    const u64 s = warp_sum32(hv);
-    const u32 lane = tid & 31;
-    if (lane < 3 * (nr - off) && lane < 21) s_w[tid >> 5][3 * off + lane] = s;
-}
-
-// Rounds 0..2 of one run of 8 entries; adds to h[0..8] and leaves the folded
-// values in p[0], v[0], b[0].
-__device__ __forceinline__ void gen_run8(u64 (&p)[8], u64 (&v)[8], u64 (&b)[8], const u32 (*s_r)[2], u64 (&h)[15])
+// Rounds 0..R-1 of N = 2^R entries held by one thread; adds to h[0..3R) and
+// leaves the folded values in p[0], v[0], b[0].
+template <int R>
+__device__ __forceinline__ void gen_regs(u64 (&p)[1 << R], u64 (&v)[1 << R], u64 (&b)[1 << R], const GenSmem &sm,
+                                         u64 (&h)[15])
 {
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
+    for (int k = 0; k < R; k++) {
         acc128 a0, a1, a2;
         acc_zero(a0);
         acc_zero(a1);
         acc_zero(a2);
-        const u32 rr0 = s_r[k][0], rr1 = s_r[k][1];
+        const u32 rr0 = sm.r[k][0], rr1 = sm.r[k][1];
 #pragma unroll
-        for (int q = 0; q < (4 >> k); q++) {
+        for (int q = 0; q < (1 << (R - k - 1)); q++) {
             const u64 p0 = p[2 * q], p1 = p[2 * q + 1], v0 = v[2 * q], v1 = v[2 * q + 1];
             const u64 b0 = b[2 * q], b1 = b[2 * q + 1];
             mac(a0, p0, v0);
@@ -525,137 +560,451 @@ __device__ __forceinline__ void gen_run8(u64 (&p)[8], u64 (&v)[8], u64 (&b)[8], 
     }
 }
 
-// Round k (3 or 4) on two folded triples held by one thread.
-__device__ __forceinline__ void gen_pair_acc(u64 p0, u64 p1, u64 v0, u64 v1, u64 b0, u64 b1, u32 rr0, u32 rr1,
-                                             u64 *h, u64 &pn, u64 &vn, u64 &bn)
+// In-register rounds for e in 3..5: runs of 4 entries (rounds 0, 1), then
+// rounds 2.. on the runs' folded triples, combined like a binary counter.
+__device__ __forceinline__ void gen_regs_runs(const Globals &G, const GenWave &W, u64 x0, u32 e, bool hasB,
+                                              GenSmem &sm, u64 (&h)[15], u64 &pv, u64 &vv, u64 &bv)
 {
-    u64 c0, c1, c2;
-    gen_pair(p0, p1, v0, v1, b0, b1, rr0, rr1, c0, c1, c2, pn, vn, bn);
-    h[0] = wred(h[0] + c0);
-    h[1] = wred(h[1] + c1);
-    h[2] = wred(h[2] + c2);
+    const u32 nruns = 1u << (e - 2);
+#pragma unroll
+    for (int j = 0; j < 9; j++) sm.hs[j][threadIdx.x] = 0;
+    u64 p0 = 0, v0 = 0, b0 = 0, p1 = 0, v1 = 0, b1 = 0, p2 = 0, v2 = 0, b2 = 0;  // pending: rounds 2, 3, 4
+    u64 tp = 0, tv = 0, tb = 0;
+    // a rolled loop keeps the kernel small (instruction-cache bound when unrolled)
+#pragma unroll 1
+    for (u32 sub = 0; sub < nruns; sub++) {
+        if (sub + 1 < nruns) {
+            const u64 xn = x0 + 4 * (sub + 1);
+            prefetch_l1(W.inV + xn);
+            if (W.src == GS_NONE) {
+                prefetch_l1(W.inP + xn);
+                if (hasB) prefetch_l1(W.inB + xn);
+            }
+        }
+        u64 p[4], v[4], b[4];
+        gen_load<4>(G, W, x0 + 4 * sub, hasB, p, v, b);
+        gen_regs<2>(p, v, b, sm, h);
+        tp = p[0];
+        tv = v[0];
+        tb = b[0];
+        if (!(sub & 1)) {  // wait for the partner run
+            p0 = tp, v0 = tv, b0 = tb;
+            continue;
+        }
+        gen_pair_acc(p0, tp, v0, tv, b0, tb, sm.r[2][0], sm.r[2][1], sm, 0, tp, tv, tb);
+        if (nruns == 2) continue;
+        if (!(sub & 2)) {
+            p1 = tp, v1 = tv, b1 = tb;
+            continue;
+        }
+        gen_pair_acc(p1, tp, v1, tv, b1, tb, sm.r[3][0], sm.r[3][1], sm, 1, tp, tv, tb);
+        if (nruns == 4) continue;
+        if (!(sub & 4)) {
+            p2 = tp, v2 = tv, b2 = tb;
+            continue;
+        }
+        gen_pair_acc(p2, tp, v2, tv, b2, tb, sm.r[4][0], sm.r[4][1], sm, 2, tp, tv, tb);
+    }
+    pv = tp;
+    vv = tv;
+    bv = tb;
+#pragma unroll
+    for (int j = 0; j < 9; j++) h[6 + j] = sm.hs[j][threadIdx.x];
 }
 
-__global__ void __launch_bounds__(GN_NT, 4) k_sc_gen(const Globals *Gs, const GenWave *waves, const Item *items)
+// Sum over the lanes l = 0 mod 2^(kk+1) of a warp (the only lanes holding a
+// contribution in cross round kk; the others hold 0), written by lane 0 to
+// out[0..2].
+__device__ __forceinline__ void gen_round_sum(u64 c0, u64 c1, u64 c2, u32 kk, u64 *out)
 {
-    constexpr int M = GN_M;
-    __shared__ u32 s_r[32][2];
-    __shared__ u64 s_lvl[3][GN_NT / 32];
-    __shared__ u64 s_w[GN_NT / 32][40];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        if ((u32)o < (2u << kk)) break;
+        c0 = wred(c0 + __shfl_xor_sync(0xffffffffu, c0, o));
+        c1 = wred(c1 + __shfl_xor_sync(0xffffffffu, c1, o));
+        c2 = wred(c2 + __shfl_xor_sync(0xffffffffu, c2, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        out[0] = c0;
+        out[1] = c1;
+        out[2] = c2;
+    }
+}
 
-    const Item it = items[blockIdx.x];
-    const GenWave &W = waves[it.wave];
-    const Globals &G = Gs[W.circ];
+// Rounds off.. of a general chunk across threads (same placement as
+// prod_cross: the first thread of each pair keeps the folded values).  The
+// per-warp sums of round k go to sm.w[warp][3k..3k+2] (CTA-level rounds: warp
+// 0's row, zeros in the other rows).
+__device__ __forceinline__ void gen_cross(u64 &p, u64 &v, u64 &b, u32 off, u32 tid, u32 na, u32 nr, GenSmem &sm)
+{
+    const u32 lane = tid & 31, warp = tid >> 5;
+    // rolled: one copy of the round body keeps the kernel small
+#pragma unroll 1
+    for (int kk = 0; kk < 5; kk++) {
+        const u32 k = off + kk;
+        if (k < nr) {
+            const u32 d = 1u << kk;
+            const u64 p1 = __shfl_down_sync(0xffffffffu, p, d);
+            const u64 v1 = __shfl_down_sync(0xffffffffu, v, d);
+            const u64 b1 = __shfl_down_sync(0xffffffffu, b, d);
+            u64 c0 = 0, c1 = 0, c2 = 0;
+            if ((tid & ((2u << kk) - 1)) == 0 && tid < na)
+                gen_pair(p, p1, v, v1, b, b1, sm.r[k][0], sm.r[k][1], c0, c1, c2, p, v, b);
+            gen_round_sum(c0, c1, c2, kk, &sm.w[warp][3 * k]);
+        }
+    }
+    if (lane == 0) {
+        sm.lvl[0][warp] = p;
+        sm.lvl[1][warp] = v;
+        sm.lvl[2][warp] = b;
+        for (u32 k = off + 5; k < nr && k < off + 7; k++)
+            if (warp) sm.w[warp][3 * k] = sm.w[warp][3 * k + 1] = sm.w[warp][3 * k + 2] = 0;
+    }
+    __syncthreads();
+    if (off + 5 < nr && warp == 0) {
+        const bool have = lane < WV_NT / 32;
+        p = have ? sm.lvl[0][lane] : 0;
+        v = have ? sm.lvl[1][lane] : 0;
+        b = have ? sm.lvl[2][lane] : 0;
+#pragma unroll
+        for (int kk = 5; kk < 7; kk++) {
+            const u32 k = off + kk;
+            if (k < nr) {
+                const u32 d = 1u << (kk - 5);
+                const u64 p1 = __shfl_down_sync(0xffffffffu, p, d);
+                const u64 v1 = __shfl_down_sync(0xffffffffu, v, d);
+                const u64 b1 = __shfl_down_sync(0xffffffffu, b, d);
+                const u32 t = lane << 5;
+                u64 c0 = 0, c1 = 0, c2 = 0;
+                if ((t & ((2u << kk) - 1)) == 0 && t < na)
+                    gen_pair(p, p1, v, v1, b, b1, sm.r[k][0], sm.r[k][1], c0, c1, c2, p, v, b);
+                gen_round_sum(c0, c1, c2, kk - 5, &sm.w[0][3 * k]);
+            }
+        }
+        if (lane == 0) {
+            sm.lvl[0][0] = p;
+            sm.lvl[1][0] = v;
+            sm.lvl[2][0] = b;
+        }
+    }
+}
+
+// One chunk of a GEN wave.
+__device__ void gen_chunk(const Globals &G, const GenWave &W, u32 chunk, GenSmem &sm)
+{
     const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const u32 nr = W.nr, e = W.e, chunk = it.chunk;
+    const u32 nr = W.nr, e = W.e;
     const u32 na = 1u << (nr - e);
     const u64 base = (u64)chunk << nr;
     const bool hasB = (W.flags & WF_HASB) != 0;
-    if (tid < nr) limbs31(G.chal[W.chal_off + tid], s_r[tid][0], s_r[tid][1]);
+    if (tid < nr) limbs31(G.chal[W.chal_off + tid], sm.r[tid][0], sm.r[tid][1]);
     __syncthreads();
-
     u64 pv = 0, vv = 0, bv = 0;
-    if (e == M) {
-        // rounds 0..4 in registers: four runs of 8 entries (rounds 0..2
-        // each), round 3 on pairs of runs, round 4 on the two results
-        u64 h0[15];
+    if (e > 0) {
+        u64 h[15];
 #pragma unroll
-        for (int i = 0; i < 15; i++) h0[i] = 0;
+        for (int i = 0; i < 15; i++) h[i] = 0;
         if (tid < na) {
-            u64 fp = 0, fv = 0, fb = 0, gp = 0, gv = 0, gb = 0;
-            // a rolled loop keeps the kernel small (instruction-cache bound when unrolled)
-#pragma unroll 1
-            for (u32 sub = 0; sub < 4; sub++) {
-                u64 p[8], v[8], b[8];
-                const u64 x0 = base + ((u64)tid << M) + 8 * sub;
-                const ulonglong2 *sv = reinterpret_cast<const ulonglong2 *>(W.inV + x0);
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const ulonglong2 t = sv[q];
-                    v[2 * q] = t.x;
-                    v[2 * q + 1] = t.y;
-                }
-                if (W.src != GS_NONE) {
-                    gen_source(G, W, x0, v, p, b);
-                } else {
-                    const ulonglong2 *sp = reinterpret_cast<const ulonglong2 *>(W.inP + x0);
-#pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        const ulonglong2 t = sp[q];
-                        p[2 * q] = t.x;
-                        p[2 * q + 1] = t.y;
-                    }
-                    if (hasB) {
-                        const ulonglong2 *sb = reinterpret_cast<const ulonglong2 *>(W.inB + x0);
-#pragma unroll
-                        for (int q = 0; q < 4; q++) {
-                            const ulonglong2 t = sb[q];
-                            b[2 * q] = t.x;
-                            b[2 * q + 1] = t.y;
-                        }
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 8; q++) b[q] = 0;
-                    }
-                }
-                gen_run8(p, v, b, s_r, h0);
-                if (sub & 1) {
-                    u64 np, nv, nb;
-                    gen_pair_acc(fp, p[0], fv, v[0], fb, b[0], s_r[3][0], s_r[3][1], h0 + 9, np, nv, nb);
-                    if (sub == 1) {
-                        gp = np;
-                        gv = nv;
-                        gb = nb;
-                    } else {
-                        gen_pair_acc(gp, np, gv, nv, gb, nb, s_r[4][0], s_r[4][1], h0 + 12, pv, vv, bv);
-                    }
-                } else {
-                    fp = p[0];
-                    fv = v[0];
-                    fb = b[0];
-                }
-            }
+            const u64 x0 = base + ((u64)tid << e);
+            gen_regs_runs(G, W, x0, e, hasB, sm, h, pv, vv, bv);
         }
         u64 h16[16];
 #pragma unroll
-        for (int i = 0; i < 16; i++) h16[i] = (i < 15) ? h0[i] : 0;
+        for (int i = 0; i < 16; i++) h16[i] = (i < 15) ? h[i] : 0;
         const u64 s = warp_sum16(h16);
-        if ((lane & 1) == 0 && (lane >> 1) < 15) s_w[warp][lane >> 1] = s;
-        gen_cross_sum(pv, vv, bv, M, tid, na, nr, s_r, s_lvl, s_w);
-    } else {
-        if (tid < na) {
-            const u64 x = base + tid;
-            vv = W.inV[x];
-            if (W.src == GS_SQ2) {
-                pv = wmul(eq_at(G.layers[W.layer].trp, x), vv);
-                bv = 0;
-            } else if (W.src == GS_TREE2) {
-                const u64 w = (x & 1) ? 0 : eq_at(G.layers[W.layer].trp, x >> 1);
-                pv = w;
-                bv = (x & 1) ? 0 : wmul(w, W.inV[x + 1]);
-            } else {
-                pv = W.inP[x];
-                bv = hasB ? W.inB[x] : 0;
-            }
+        if ((lane & 1) == 0 && (lane >> 1) < 3 * e) sm.w[warp][lane >> 1] = s;
+    } else if (tid < na) {
+        const u64 x = base + tid;
+        vv = __ldcg(W.inV + x);
+        if (W.src == GS_SQ2) {
+            pv = wmul(eq_at(G.layers[W.layer].trp, x), vv);
+        } else if (W.src == GS_TREE2) {
+            const u64 w = (x & 1) ? 0 : eq_at(G.layers[W.layer].trp, x >> 1);
+            pv = w;
+            bv = (x & 1) ? 0 : wmul(w, __ldcg(W.inV + x + 1));
+        } else {
+            pv = __ldcg(W.inP + x);
+            bv = hasB ? __ldcg(W.inB + x) : 0;
         }
-        gen_cross_sum(pv, vv, bv, 0, tid, na, nr, s_r, s_lvl, s_w);
     }
+    gen_cross(pv, vv, bv, e, tid, na, nr, sm);
     __syncthreads();
     if (tid < 3 * nr) {
-        const u64 sum = wred(s_w[0][tid] + s_w[1][tid] + s_w[2][tid] + s_w[3][tid]);
+        const u64 sum = wred(sm.w[0][tid] + sm.w[1][tid] + sm.w[2][tid] + sm.w[3][tid]);
         const u32 k = tid / 3, t = tid % 3;
         W.part[((u64)k * W.nchunks + chunk) * 3 + t] = sum;
     }
     if (!(W.flags & WF_LAST) && tid == 0) {
-        W.outP[chunk] = s_lvl[0][0];
-        W.outV[chunk] = s_lvl[1][0];
-        if (W.outB) W.outB[chunk] = s_lvl[2][0];
+        W.outP[chunk] = sm.lvl[0][0];
+        W.outV[chunk] = sm.lvl[1][0];
+        if (W.outB) W.outB[chunk] = sm.lvl[2][0];
     }
 }
 
-void launch_sc_gen(const Globals *Gs, const GenWave *waves, const Item *items, int nitems, cudaStream_t st)
+// ---- line reduction -----------------------------------------------------------------
+// q(t) = V~_{i+1}(l(t)), folding V_{i+1} with coordinates a_k + b_k t in
+// coefficient form (degree grows by one per folded coordinate):
+//   out_c = A_c + a (B_c - A_c) + b (B_{c-1} - A_{c-1}),  c = 0 .. deg + 1.
+// A first-wave chunk folds LN_E coordinates per thread in registers (2^LN_E
+// consecutive entries) and the rest in shared memory; a later wave folds up
+// to 7 coordinates of one polynomial per thread.
+
+// One level of coefficient folding in registers: D+1 -> D+2 coefficients.
+template <int D>
+__device__ __forceinline__ void line_fold(const u64 (&A)[D + 1], const u64 (&B)[D + 1], u32 a0, u32 a1, u32 b0,
+                                          u32 b1, u64 (&out)[D + 2])
 {
-    if (nitems > 0) k_sc_gen<<<nitems, GN_NT, 0, st>>>(Gs, waves, items);
+    u64 d[D + 1];
+#pragma unroll
+    for (int c = 0; c <= D; c++) d[c] = B[c] + (2 * FP_P) - A[c];
+    out[0] = wlin1(A[0], d[0], a0, a1);
+#pragma unroll
+    for (int c = 1; c <= D; c++) out[c] = wlin2(A[c], d[c], d[c - 1], a0, a1, b0, b1);
+    out[D + 1] = wlin1(0, d[D], b0, b1);
+}
+
+// 8 consecutive entries -> one cubic (coordinates 0, 1, 2 of the run).
+__device__ __forceinline__ void line_run8(const u64 *v, const u32 *la, const u32 *lb, u64 (&out)[4])
+{
+    u64 l1[4][2];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const u64 dd = v[2 * q + 1] + (2 * FP_P) - v[2 * q];
+        l1[q][0] = wlin1(v[2 * q], dd, la[0], la[1]);
+        l1[q][1] = wlin1(0, dd, lb[0], lb[1]);
+    }
+    u64 l2[2][3];
+    line_fold<1>(l1[0], l1[1], la[2], la[3], lb[2], lb[3], l2[0]);
+    line_fold<1>(l1[2], l1[3], la[2], la[3], lb[2], lb[3], l2[1]);
+    line_fold<2>(l2[0], l2[1], la[4], la[5], lb[4], lb[5], out);
+}
+
+// Coefficient `c` of the fold of polynomials A, B (degree deg, W values).
+__device__ __forceinline__ u64 line_coef(const u64 *A, const u64 *B, u32 deg, u32 c, const u32 *la, const u32 *lb)
+{
+    const u64 dc = (c <= deg) ? B[c] + (2 * FP_P) - A[c] : 0;
+    const u64 dm = (c >= 1) ? B[c - 1] + (2 * FP_P) - A[c - 1] : 0;
+    const u64 ac = (c <= deg) ? A[c] : 0;
+    return wlin2(ac, dc, dm, la[0], la[1], lb[0], lb[1]);
+}
+
+// One chunk of one line wave, by the whole CTA.
+__device__ void line_chunk(const Globals &G, const LineWaveDev &W, u32 chunk, LineSmem &sm)
+{
+    const u32 tid = threadIdx.x;
+    if (tid < W.nl) {
+        const u64 a = G.chal[W.a_off + W.l0 + tid];
+        const u64 b = f_sub(G.chal[W.b_off + W.l0 + tid], a);
+        limbs31(a, sm.la[tid][0], sm.la[tid][1]);
+        limbs31(b, sm.lb[tid][0], sm.lb[tid][1]);
+    }
+    __syncthreads();
+    u32 m, deg, k0;  // polynomials in bufA, their degree, coordinates already folded
+    if (W.l0 == 0) {
+        const u32 e = (W.nl >= LN_E) ? LN_E : 0;
+        const u32 na = 1u << (W.nl - e);
+        const u64 base = (u64)chunk << W.nl;
+        if (tid < na) {
+            if (e == LN_E) {
+                const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(W.in + base + ((u64)tid << LN_E));
+                u32 la[12], lb[12];
+#pragma unroll
+                for (int k = 0; k < 6; k++) {
+                    la[2 * k] = sm.la[k][0];
+                    la[2 * k + 1] = sm.la[k][1];
+                    lb[2 * k] = sm.lb[k][0];
+                    lb[2 * k + 1] = sm.lb[k][1];
+                }
+                // eight runs of 8 entries (cubics over coordinates 0..2), combined
+                // like a binary counter over coordinates 3, 4, 5; a rolled loop
+                // keeps one copy of the run code
+                u64 c0[4] = {0, 0, 0, 0}, q0[5] = {0, 0, 0, 0, 0};
+                u64 s0[6] = {0, 0, 0, 0, 0, 0}, s1[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll 1
+                for (int run = 0; run < 8; run++) {
+                    if (run < 7) prefetch_l1(src + 4 * (run + 1));
+                    u64 v[8];
+#pragma unroll
+                    for (int t = 0; t < 4; t++) {
+                        const ulonglong2 w = __ldcg(src + 4 * run + t);
+                        v[2 * t] = w.x;
+                        v[2 * t + 1] = w.y;
+                    }
+                    u64 c[4];
+                    line_run8(v, la, lb, c);
+                    if (!(run & 1)) {
+#pragma unroll
+                        for (int i = 0; i < 4; i++) c0[i] = c[i];
+                        continue;
+                    }
+                    u64 q[5];
+                    line_fold<3>(c0, c, la[6], la[7], lb[6], lb[7], q);
+                    if (!(run & 2)) {
+#pragma unroll
+                        for (int i = 0; i < 5; i++) q0[i] = q[i];
+                        continue;
+                    }
+                    u64 t5[6];
+                    line_fold<4>(q0, q, la[8], la[9], lb[8], lb[9], t5);
+#pragma unroll
+                    for (int i = 0; i < 6; i++) {
+                        if (run & 4) s1[i] = t5[i];
+                        else s0[i] = t5[i];
+                    }
+                }
+                u64 p[7];
+                line_fold<5>(s0, s1, la[10], la[11], lb[10], lb[11], p);
+#pragma unroll
+                for (int c = 0; c < 7; c++) sm.bufA[tid * 7 + c] = p[c];
+            } else {
+                sm.bufA[tid] = __ldcg(W.in + base + tid);
+            }
+        }
+        m = na;
+        deg = e;
+        k0 = e;
+    } else {
+        // polynomials of degree l0 from the previous wave (written by other
+        // CTAs of this launch when run as a tail: read through L2)
+        const u32 din = W.l0, npoly = 1u << W.nl, half = npoly >> 1, C = din + 2;
+        const u64 *in = W.in + ((u64)chunk << W.nl) * (din + 1);
+        for (u32 idx = tid; idx < half * C; idx += WV_NT) {
+            const u32 j = idx / C, c = idx - j * C;
+            const u64 *A = in + (u64)(2 * j) * (din + 1), *B = A + (din + 1);
+            const u64 dc = (c <= din) ? __ldcg(B + c) + (2 * FP_P) - __ldcg(A + c) : 0;
+            const u64 dm = (c >= 1) ? __ldcg(B + c - 1) + (2 * FP_P) - __ldcg(A + c - 1) : 0;
+            const u64 ac = (c <= din) ? __ldcg(A + c) : 0;
+            sm.bufA[j * C + c] = wlin2(ac, dc, dm, sm.la[0][0], sm.la[0][1], sm.lb[0][0], sm.lb[0][1]);
+        }
+        m = half;
+        deg = din + 1;
+        k0 = 1;
+    }
+    __syncthreads();
+    u64 *cur = sm.bufA, *nxt = sm.bufB;
+    for (u32 k = k0; k < W.nl; k++) {
+        const u32 half = m >> 1, C = deg + 2;
+        for (u32 idx = tid; idx < half * C; idx += WV_NT) {
+            const u32 j = idx / C, c = idx - j * C;
+            nxt[j * C + c] =
+                line_coef(cur + (2 * j) * (deg + 1), cur + (2 * j + 1) * (deg + 1), deg, c, sm.la[k], sm.lb[k]);
+        }
+        __syncthreads();
+        u64 *t = cur;
+        cur = nxt;
+        nxt = t;
+        m = half;
+        deg += 1;
+    }
+    // cur[0..deg] is this chunk's polynomial
+    if (!W.last) {
+        u64 *out = W.out + (u64)chunk * (deg + 1);
+        for (u32 c = tid; c <= deg; c += WV_NT) out[c] = cur[c];
+    } else {
+        // q(t) for t = 0..n by Horner; q(0) = V~_{i+1}(r1) feeds phase 3
+        const u32 n = W.n;
+        u64 *tr = G.tr + W.tr_q;
+        for (u32 t = tid; t <= n; t += WV_NT) {
+            u64 acc = cur[deg];
+            for (int c = (int)deg - 1; c >= 0; c--) acc = wred(wmul(acc, (u64)t) + cur[c]);
+            tr[t] = wcanon(acc);
+        }
+        if (tid == 0) G.scal[SCAL_V1(W.layer)] = wcanon(cur[0]);
+    }
+}
+
+// ---- the persistent launch ------------------------------------------------------------
+
+// After a chunk of a wave with a tail: count the chunk; the CTA that counts
+// the last one returns true (and resets the counter for the next proof).
+__device__ __forceinline__ bool wave_done(u32 *counter, u32 nchunks, u32 &s_flag)
+{
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_flag = (atomicAdd(counter, 1u) == nchunks - 1) ? 1u : 0u;
+    __syncthreads();
+    const bool last = s_flag != 0;
+    if (last) {
+        __threadfence();
+        if (threadIdx.x == 0) *counter = 0;
+    }
+    return last;
+}
+
+extern __shared__ __align__(16) unsigned char wv_dyn[];
+
+__global__ void __launch_bounds__(WV_NT, 4) k_waves(const Globals *Gs, const LineWaveDev *lw, const ProdWave *pw,
+                                                   const GenWave *gw, const Task *tasks, int ntasks, u32 *ctr)
+{
+    WaveSmem &sm = *reinterpret_cast<WaveSmem *>(wv_dyn);
+    __shared__ int s_task;
+    __shared__ u32 s_flag;
+    for (;;) {
+        __syncthreads();  // the previous task is done with shared memory
+        if (threadIdx.x == 0) s_task = (int)atomicAdd(&ctr[0], 1u);
+        __syncthreads();
+        const int ti = s_task;
+        if (ti >= ntasks) break;
+        const Task tk = tasks[ti];
+        if (tk.type == TK_LINE) {
+            const LineWaveDev &W = lw[tk.wave];
+            const Globals &G = Gs[W.circ];
+            line_chunk(G, W, tk.chunk, sm.line);
+            if (W.tail && wave_done(W.counter, W.nchunks, s_flag)) line_chunk(G, lw[tk.wave + 1], 0, sm.line);
+        } else if (tk.type == TK_PROD) {
+            const ProdWave &W = pw[tk.wave];
+            const Globals &G = Gs[W.circ];
+            prod_chunk(G, W, tk.chunk, sm.prod);
+            if ((W.flags & WF_TAIL) && wave_done(W.counter, W.nchunks, s_flag)) {
+                __syncthreads();
+                prod_chunk(G, pw[tk.wave + 1], 0, sm.prod);
+            }
+        } else {
+            const GenWave &W = gw[tk.wave];
+            const Globals &G = Gs[W.circ];
+            gen_chunk(G, W, tk.chunk, sm.gen);
+            if ((W.flags & WF_TAIL) && wave_done(W.counter, W.nchunks, s_flag)) {
+                __syncthreads();
+                gen_chunk(G, gw[tk.wave + 1], 0, sm.gen);
+            }
+        }
+    }
+    // the CTA that exits last resets the task counter for the next launch
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctr[1], 1u) == gridDim.x - 1) {
+            ctr[0] = 0;
+            ctr[1] = 0;
+        }
+    }
+}
+
+static int g_sm_count[64];
+
+// SM count of the current device, cached (called outside stream capture).
+void waves_init()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (dev >= 0 && dev < 64 && sms > 0) g_sm_count[dev] = sms;
+    cudaFuncSetAttribute(k_waves, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(WaveSmem));
+}
+
+void launch_waves(const Globals *Gs, const LineWaveDev *lw, const ProdWave *pw, const GenWave *gw, const Task *tasks,
+                  int ntasks, u32 *ctr, cudaStream_t st)
+{
+    if (ntasks <= 0) return;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int sms = (dev >= 0 && dev < 64) ? g_sm_count[dev] : 0;
+    if (sms <= 0) {
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+        if (dev >= 0 && dev < 64) g_sm_count[dev] = sms;
+    }
+    const int grid = std::min(ntasks, sms * 4);
+    k_waves<<<grid, WV_NT, sizeof(WaveSmem), st>>>(Gs, lw, pw, gw, tasks, ntasks, ctr);
 }
 
 // --------------------------------------------------------------------------------

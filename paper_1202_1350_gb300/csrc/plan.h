@@ -56,8 +56,9 @@ struct LayerDev {
 #define SCAL_EQZRP(i) (2 * (i))
 #define SCAL_V1(i) (2 * (i) + 1)
 
-// Flags of a sum-check wave.
-enum : u32 { WF_HASB = 2, WF_LAST = 4 };
+// Flags of a sum-check wave.  WF_TAIL: the next descriptor (a single chunk)
+// is run by the CTA that finishes this wave's last chunk.
+enum : u32 { WF_HASB = 2, WF_LAST = 4, WF_TAIL = 8 };
 
 // Kinds of sum-check instance (SCI).  Product-weighted ones (< PK_GEN_FIRST)
 // keep P = sigma prod_m L_m(x_m) implicit; general ones fold P, V, B tables.
@@ -74,8 +75,8 @@ enum : u32 {
 // Source of the first GEN wave's P and B.
 enum : u32 { GS_NONE = 0, GS_SQ2 = 1, GS_TREE2 = 2 };
 
-#define PR_M 6  // PROD: each thread folds 2^6 entries through 6 rounds in registers (128 threads per CTA)
-#define GN_M 5  // GEN: 2^5 entries, 5 rounds (128 threads per CTA)
+#define PR_M 6  // PROD: at most 2^6 entries per thread, folded in registers (128 threads per CTA)
+#define GN_M 5  // GEN: at most 2^5 entries per thread (128 threads per CTA)
 
 struct SciDev {
     u32 circ;
@@ -104,6 +105,7 @@ struct ProdWave {
     u64 *out;          // one folded value per chunk (unused on the last wave)
     u64 *wblk;         // weight block: Q, E, outer lo, outer hi
     u64 *part;         // partials: part[(k * nchunks + chunk) * 2 + t]
+    u32 *counter;      // chunks finished (WF_TAIL only; reset by the last)
 };
 
 // One wave of a GEN SCI.
@@ -120,6 +122,7 @@ struct GenWave {
     const u64 *inP, *inV, *inB;
     u64 *outP, *outV, *outB;
     u64 *part;         // partials: part[(k * nchunks + chunk) * 3 + t]
+    u32 *counter;      // chunks finished (WF_TAIL only; reset by the last)
 };
 
 // Line reduction of layer i (q(t) = V~_{i+1}(l(t)), l(t) = r1 + t (r2 - r1)),
@@ -146,6 +149,15 @@ struct LineWaveDev {
 struct Item {
     u32 wave;
     u32 chunk;
+};
+
+// Task of the persistent wave launch: one chunk of a line, PROD or GEN wave.
+enum : u32 { TK_LINE = 0, TK_PROD = 1, TK_GEN = 2 };
+struct Task {
+    u32 type;
+    u32 wave;   // index into the plan's line, PROD or GEN wave descriptors
+    u32 chunk;
+    u32 pad;
 };
 
 // Final reduction of one round: sum the chunks' partials (2 per chunk for
@@ -233,14 +245,15 @@ void launch_eval_layers(const Globals *Gs, const LayerEval *le, const Item *item
 void launch_eval_segs(const Globals *Gs, const EvalSeg *segs, const Item *items, int nitems, cudaStream_t st);
 void launch_check_canonical(const u64 *x, u64 n, u32 *status, cudaStream_t st);
 void launch_check_inputs(const Globals *Gs, const Item *items, int nitems, cudaStream_t st);
-void launch_line_wave(const Globals *Gs, const LineWaveDev *lw, const Item *items, int nitems, cudaStream_t st);
 void launch_build23(const Globals *Gs, const BuildItem *items, int nitems, cudaStream_t st);
 void launch_prep_prod(const Globals *Gs, const SciDev *scis, const ProdWave *waves, int nwaves, cudaStream_t st);
-void launch_sc_prod(const Globals *Gs, const ProdWave *waves, const Item *items, int nitems, cudaStream_t st);
-void launch_sc_gen(const Globals *Gs, const GenWave *waves, const Item *items, int nitems, cudaStream_t st);
+// One persistent launch over `tasks` (ctr: two zeroed counters, left zeroed).
+void launch_waves(const Globals *Gs, const LineWaveDev *lw, const ProdWave *pw, const GenWave *gw, const Task *tasks,
+                  int ntasks, u32 *ctr, cudaStream_t st);
 void launch_final(const Globals *Gs, const SciDev *scis, const RoundRef *rounds, int nrounds, const u32 *outs,
                   int nouts, cudaStream_t st);
 void prove_kernels_init();
+void waves_init();
 
 // verifier
 struct VerifyDev {

@@ -172,14 +172,10 @@ vc_status launch(vc_server *s, Slot &sl)
     // merged plan; the slot's streams and events are kept across sets
     Plan res = sl.P;
     plan_merge(sl.P, cs);
-    for (int k = 0; k < 2; k++) sl.P.aux[k] = res.aux[k];
+    sl.P.aux = res.aux;
     sl.P.cap = res.cap;
     sl.P.ev_fork = res.ev_fork;
     sl.P.ev_tables = res.ev_tables;
-    sl.P.ev_eval = res.ev_eval;
-    sl.P.ev_build = res.ev_build;
-    sl.P.ev_prod = res.ev_prod;
-    sl.P.ev_gen = res.ev_gen;
     sl.P.ev_params = res.ev_params;
     const int n = (int)cs.size();
     const size_t need = plan_bytes(sl.P, true) + (size_t)n * sizeof(CallParams) + 512;

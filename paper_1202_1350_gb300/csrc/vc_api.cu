@@ -33,10 +33,12 @@ void init_device_once(int device)
     std::lock_guard<std::mutex> g(mu);
     if (device < 0 || device >= 64) {
         prove_kernels_init();
+        waves_init();
         return;
     }
     if (!done[device]) {
         prove_kernels_init();
+        waves_init();
         done[device] = true;
     }
 }
@@ -236,13 +238,23 @@ static size_t layout(vc_circuit *c, uintptr_t base)
     c->eq_verify.push_back({c->tzd});
     c->eq_verify.push_back({c->L[0].tz});
 
-    // line reduction waves; a single-chunk wave after another wave is run by
-    // that wave's last CTA (its descriptor follows directly, no launch)
+    // Waves.  A wave is one launch's share of an instance: chunks of 2^nr
+    // entries (2^nl coordinates for the line reduction).  A wave followed by a
+    // single-chunk wave gets WF_TAIL / tail: its last CTA runs the successor,
+    // whose descriptor follows directly.  Every other wave is a task list of
+    // a persistent launch: group A[g] (g = waves before it in its instance)
+    // or, for general waves over tables built by k_build23, group B[g].
     P.lw.clear();
-    P.line_items.clear();
+    P.groupsA.clear();
+    P.groupsB.clear();
+    auto add_tasks = [&](bool groupB, u32 g, u32 type, u32 idx, u32 nchunks) {
+        auto &grp = groupB ? P.groupsB : P.groupsA;
+        if (grp.size() <= g) grp.resize(g + 1);
+        for (u32 ch = 0; ch < nchunks; ch++) grp[g].push_back({type, idx, ch, 0u});
+    };
     for (u32 i = 0; i < d; i++) {
         const u32 n = c->s[i + 1];
-        u32 l0 = 0;
+        u32 l0 = 0, g = 0;
         const u64 *in = c->V[i + 1];
         bool tail = false;
         for (u32 w = 0;; w++) {
@@ -267,10 +279,7 @@ static size_t layout(vc_circuit *c, uintptr_t base)
                 W.counter = A.take<u32>(1);
             }
             P.lw.push_back(W);
-            if (!tail) {
-                if (P.line_items.size() <= w) P.line_items.resize(w + 1);
-                for (u32 ch = 0; ch < W.nchunks; ch++) P.line_items[w].push_back({idx, ch});
-            }
+            if (!tail) add_tasks(false, g++, TK_LINE, idx, W.nchunks);
             tail = W.tail != 0;
             if (W.last) break;
             in = W.out;
@@ -290,8 +299,6 @@ static size_t layout(vc_circuit *c, uintptr_t base)
     P.scis.clear();
     P.pw.clear();
     P.gw.clear();
-    P.p_items.clear();
-    P.g_items.clear();
     P.rounds.clear();
     std::vector<u64> pw_off, gw_off, round_off;
     u64 part_total = 0;
@@ -321,17 +328,25 @@ static size_t layout(vc_circuit *c, uintptr_t base)
             P.scis.push_back(Sc);
             const u32 nv = prod ? 2 : 3;
             const u32 C = prod ? PR_CHUNK_LOG : GN_CHUNK_LOG;
+            const u32 M = prod ? (u32)PR_M : (u32)GN_M;
             const bool tab = Sc.kind == PK_GEN_TAB;
             const bool tabB = tab && L.has_add;
             const bool anyB = tabB || Sc.kind == PK_GEN_TREE2;
             const u64 *inP = tab ? (ph == 2 ? L.P2 : L.P3) : nullptr;
             const u64 *inB = tabB ? (ph == 2 ? L.B2 : L.B3) : nullptr;
             const u64 *inV = (ph == 1) ? L.V : L.Vn;
-            u32 r0 = 0;
+            u32 r0 = 0, g = 0;
+            bool tail = false;
             for (u32 w = 0;; w++) {
                 const u32 nr = std::min(C, n - r0);
                 const u32 nchunks = u32(1) << (n - r0 - nr);
                 const bool last = (r0 + nr == n);
+                // entries per thread: all WV threads busy, at most 2^M each; the
+                // register phase works on runs (16 entries PROD, 4 GEN), so a
+                // wave of more than WV threads' entries takes at least one run
+                const u32 run = prod ? 4u : 2u;
+                const u32 e = nr > WV_LOG ? std::min(M, std::max(run, nr - WV_LOG)) : 0u;
+                const bool has_tail = !last && (n - r0 - nr) <= C;  // the next wave is one chunk
                 for (u32 k = 0; k < nr; k++) {
                     RoundRef R{};
                     R.tr_pos = Sc.tr_off + 3ull * (r0 + k);
@@ -341,15 +356,16 @@ static size_t layout(vc_circuit *c, uintptr_t base)
                     round_off.push_back(part_total + u64(k) * nchunks * nv);
                     P.rounds.push_back(R);
                 }
+                u32 idx;
                 if (prod) {
                     ProdWave W{};
                     W.circ = 0;
                     W.sci = sci;
                     W.r0 = r0;
                     W.nr = nr;
-                    W.e = (nr >= (u32)PR_M) ? (u32)PR_M : 0;
+                    W.e = e;
                     W.nchunks = nchunks;
-                    W.flags = last ? WF_LAST : 0;
+                    W.flags = (last ? WF_LAST : 0) | (has_tail ? WF_TAIL : 0);
                     W.no = n - r0 - nr;
                     W.ho = (W.no + 1) / 2;
                     W.chal_off = Sc.chal_off + r0;
@@ -358,11 +374,10 @@ static size_t layout(vc_circuit *c, uintptr_t base)
                     const u32 kb = W.e ? W.e - 1 : 0;
                     W.wblk = A.take<u64>(((1u << W.e) - 1) + ((1u << (nr - kb)) - 1) + (1u << W.ho) +
                                          (1u << (W.no - W.ho)));
+                    W.counter = has_tail ? A.take<u32>(1) : nullptr;
                     pw_off.push_back(part_total);
-                    if (P.p_items.size() <= w) P.p_items.resize(w + 1);
-                    const u32 idx = (u32)P.pw.size();
+                    idx = (u32)P.pw.size();
                     P.pw.push_back(W);
-                    for (u32 ch = 0; ch < nchunks; ch++) P.p_items[w].push_back({idx, ch});
                     inV = W.out;
                 } else {
                     GenWave W{};
@@ -370,10 +385,11 @@ static size_t layout(vc_circuit *c, uintptr_t base)
                     W.sci = sci;
                     W.r0 = r0;
                     W.nr = nr;
-                    W.e = (nr >= (u32)GN_M) ? (u32)GN_M : 0;
+                    W.e = e;
                     W.nchunks = nchunks;
                     W.src = (w > 0 || tab) ? GS_NONE : (Sc.kind == PK_GEN_SQ2 ? GS_SQ2 : GS_TREE2);
-                    W.flags = (last ? WF_LAST : 0) | (((w > 0 && anyB) || tabB) ? WF_HASB : 0);
+                    W.flags = (last ? WF_LAST : 0) | (((w > 0 && anyB) || tabB) ? WF_HASB : 0) |
+                              (has_tail ? WF_TAIL : 0);
                     W.layer = i;
                     W.chal_off = Sc.chal_off + r0;
                     W.inP = inP;
@@ -384,15 +400,16 @@ static size_t layout(vc_circuit *c, uintptr_t base)
                         W.outV = A.take<u64>(nchunks);
                         W.outB = anyB ? A.take<u64>(nchunks) : nullptr;
                     }
+                    W.counter = has_tail ? A.take<u32>(1) : nullptr;
                     gw_off.push_back(part_total);
-                    if (P.g_items.size() <= w) P.g_items.resize(w + 1);
-                    const u32 idx = (u32)P.gw.size();
+                    idx = (u32)P.gw.size();
                     P.gw.push_back(W);
-                    for (u32 ch = 0; ch < nchunks; ch++) P.g_items[w].push_back({idx, ch});
                     inP = W.outP;
                     inV = W.outV;
                     inB = W.outB;
                 }
+                if (!tail) add_tasks(tab, g++, prod ? TK_PROD : TK_GEN, idx, nchunks);
+                tail = has_tail;
                 part_total += u64(nr) * nchunks * nv;
                 if (last) break;
                 r0 += nr;
@@ -404,8 +421,7 @@ static size_t layout(vc_circuit *c, uintptr_t base)
     for (size_t k = 0; k < P.gw.size(); k++) P.gw[k].part = c->partials + gw_off[k];
     for (size_t k = 0; k < P.rounds.size(); k++) P.rounds[k].part_pos = c->partials + round_off[k];
     P.outs.assign(1, 0u);
-    P.has_tab = false;
-    for (const SciDev &Sc : P.scis) P.has_tab = P.has_tab || Sc.kind == PK_GEN_TAB;
+    sort_tasks(P);
 
     // verifier scratch
     const u64 Sd = S(d);
@@ -459,9 +475,13 @@ void plan_take(Plan &P, Arena &A, bool own_G)
     };
     items(P.seg_items, P.d_seg_items);
     items(P.lev_items, P.d_lev_items);
-    items(P.line_items, P.d_line_items);
-    items(P.p_items, P.d_p_items);
-    items(P.g_items, P.d_g_items);
+    auto tasks = [&](std::vector<std::vector<Task>> &v, std::vector<Task *> &dv) {
+        dv.assign(v.size(), nullptr);
+        for (size_t k = 0; k < v.size(); k++) dv[k] = A.take<Task>(v[k].size() + 1);
+    };
+    tasks(P.groupsA, P.d_groupsA);
+    tasks(P.groupsB, P.d_groupsB);
+    P.d_ctr = A.take<u32>(2 * (P.groupsA.size() + P.groupsB.size()) + 2);
     P.d_lw = A.take<LineWaveDev>(P.lw.size() + 1);
     P.d_builds = A.take<BuildItem>(P.builds.size() + 1);
     P.d_scis = A.take<SciDev>(P.scis.size() + 1);
@@ -494,10 +514,26 @@ bool plan_valid(const Plan &P)
         if (b.circ >= nc) return false;
     for (const SciDev &S : P.scis)
         if (S.circ >= nc) return false;
-    for (const ProdWave &W : P.pw)
+    for (size_t k = 0; k < P.pw.size(); k++) {
+        const ProdWave &W = P.pw[k];
         if (W.circ >= nc || W.sci >= P.scis.size() || P.scis[W.sci].circ != W.circ) return false;
-    for (const GenWave &W : P.gw)
+        if (W.nr > PR_CHUNK_LOG || W.e > (u32)PR_M || W.e > W.nr || W.nr - W.e > WV_LOG || (W.e && W.e < 4))
+            return false;
+        if ((W.flags & WF_TAIL) && (k + 1 >= P.pw.size() || P.pw[k + 1].nchunks != 1 || P.pw[k + 1].sci != W.sci ||
+                                    P.pw[k + 1].r0 != W.r0 + W.nr || !W.counter))
+            return false;
+    }
+    for (size_t k = 0; k < P.gw.size(); k++) {
+        const GenWave &W = P.gw[k];
         if (W.circ >= nc || W.sci >= P.scis.size() || P.scis[W.sci].circ != W.circ) return false;
+        if (W.nr > GN_CHUNK_LOG || W.e > (u32)GN_M || W.e > W.nr || W.nr - W.e > WV_LOG || (W.e && W.e < 2))
+            return false;
+        if ((W.flags & WF_TAIL) && (k + 1 >= P.gw.size() || P.gw[k + 1].nchunks != 1 || P.gw[k + 1].sci != W.sci ||
+                                    P.gw[k + 1].r0 != W.r0 + W.nr || !W.counter))
+            return false;
+    }
+    for (const LineWaveDev &W : P.lw)
+        if (W.nl > (W.l0 ? LN_CHUNKW_LOG : LN_CHUNK0_LOG) || W.n > 30) return false;
     for (const RoundRef &R : P.rounds)
         if (R.sci >= P.scis.size() || R.j >= P.scis[R.sci].n) return false;
     for (u32 o : P.outs)
@@ -508,18 +544,39 @@ bool plan_valid(const Plan &P)
     for (const auto &v : P.lev_items)
         for (const Item &it : v)
             if (it.wave >= P.levs.size()) return false;
-    for (const auto &v : P.line_items)
-        for (const Item &it : v)
-            if (it.wave >= P.lw.size() || it.chunk >= P.lw[it.wave].nchunks) return false;
-    for (const auto &v : P.p_items)
-        for (const Item &it : v)
-            if (it.wave >= P.pw.size() || it.chunk >= P.pw[it.wave].nchunks) return false;
-    for (const auto &v : P.g_items)
-        for (const Item &it : v)
-            if (it.wave >= P.gw.size() || it.chunk >= P.gw[it.wave].nchunks) return false;
+    auto task_ok = [&](const Task &t) {
+        switch (t.type) {
+        case TK_LINE: return t.wave < P.lw.size() && t.chunk < P.lw[t.wave].nchunks;
+        case TK_PROD: return t.wave < P.pw.size() && t.chunk < P.pw[t.wave].nchunks;
+        case TK_GEN: return t.wave < P.gw.size() && t.chunk < P.gw[t.wave].nchunks;
+        default: return false;
+        }
+    };
+    for (const auto *grp : {&P.groupsA, &P.groupsB})
+        for (const auto &v : *grp)
+            for (const Task &t : v)
+                if (!task_ok(t)) return false;
     return P.seg_items.size() == P.d_seg_items.size() && P.lev_items.size() == P.d_lev_items.size() &&
-           P.line_items.size() == P.d_line_items.size() && P.p_items.size() == P.d_p_items.size() &&
-           P.g_items.size() == P.d_g_items.size();
+           P.groupsA.size() == P.d_groupsA.size() && P.groupsB.size() == P.d_groupsB.size();
+}
+
+// Task order inside a launch: line chunks first (their tails are the
+// longest serial work), then general, then product-weighted; within a kind,
+// chunks of larger waves first.
+void sort_tasks(Plan &P)
+{
+    auto rank = [&](const Task &t) { return t.type == TK_LINE ? 0 : (t.type == TK_GEN ? 1 : 2); };
+    auto chunks = [&](const Task &t) {
+        return t.type == TK_LINE ? P.lw[t.wave].nchunks : (t.type == TK_PROD ? P.pw[t.wave].nchunks
+                                                                              : P.gw[t.wave].nchunks);
+    };
+    for (auto *grp : {&P.groupsA, &P.groupsB})
+        for (auto &v : *grp)
+            std::stable_sort(v.begin(), v.end(), [&](const Task &a, const Task &b) {
+                const int ra = rank(a), rb = rank(b);
+                if (ra != rb) return ra < rb;
+                return chunks(a) > chunks(b);
+            });
 }
 
 cudaError_t plan_upload(Plan &P)
@@ -534,9 +591,9 @@ cudaError_t plan_upload(Plan &P)
     };
     items(P.seg_items, P.d_seg_items);
     items(P.lev_items, P.d_lev_items);
-    items(P.line_items, P.d_line_items);
-    items(P.p_items, P.d_p_items);
-    items(P.g_items, P.d_g_items);
+    for (size_t k = 0; e == cudaSuccess && k < P.groupsA.size(); k++) e = upload(P.d_groupsA[k], P.groupsA[k]);
+    for (size_t k = 0; e == cudaSuccess && k < P.groupsB.size(); k++) e = upload(P.d_groupsB[k], P.groupsB[k]);
+    if (e == cudaSuccess) e = cudaMemset(P.d_ctr, 0, sizeof(u32) * (2 * (P.groupsA.size() + P.groupsB.size()) + 2));
     if (e == cudaSuccess) e = upload(P.d_lw, P.lw);
     if (e == cudaSuccess) e = upload(P.d_builds, P.builds);
     if (e == cudaSuccess) e = upload(P.d_scis, P.scis);
@@ -560,9 +617,12 @@ cudaError_t plan_upload_async(Plan &P, cudaStream_t st)
     };
     items(P.seg_items, P.d_seg_items);
     items(P.lev_items, P.d_lev_items);
-    items(P.line_items, P.d_line_items);
-    items(P.p_items, P.d_p_items);
-    items(P.g_items, P.d_g_items);
+    for (size_t k = 0; e == cudaSuccess && k < P.groupsA.size(); k++)
+        e = upload_async(P.d_groupsA[k], P.groupsA[k], st);
+    for (size_t k = 0; e == cudaSuccess && k < P.groupsB.size(); k++)
+        e = upload_async(P.d_groupsB[k], P.groupsB[k], st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(P.d_ctr, 0, sizeof(u32) * (2 * (P.groupsA.size() + P.groupsB.size()) + 2), st);
     if (e == cudaSuccess) e = upload_async(P.d_lw, P.lw, st);
     if (e == cudaSuccess) e = upload_async(P.d_builds, P.builds, st);
     if (e == cudaSuccess) e = upload_async(P.d_scis, P.scis, st);
@@ -582,10 +642,9 @@ size_t plan_bytes(Plan &P, bool own_G)
 
 cudaError_t plan_resources(Plan &P)
 {
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; e == cudaSuccess && k < 2; k++) e = cudaStreamCreateWithFlags(&P.aux[k], cudaStreamNonBlocking);
+    cudaError_t e = cudaStreamCreateWithFlags(&P.aux, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P.cap, cudaStreamNonBlocking);
-    for (cudaEvent_t *ev : {&P.ev_fork, &P.ev_tables, &P.ev_eval, &P.ev_build, &P.ev_prod, &P.ev_gen, &P.ev_params})
+    for (cudaEvent_t *ev : {&P.ev_fork, &P.ev_tables, &P.ev_params})
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     return e;
 }
@@ -594,11 +653,11 @@ void plan_release(Plan &P)
 {
     if (P.exec) cudaGraphExecDestroy(P.exec);
     P.exec = nullptr;
-    for (cudaEvent_t *ev : {&P.ev_fork, &P.ev_tables, &P.ev_eval, &P.ev_build, &P.ev_prod, &P.ev_gen, &P.ev_params}) {
+    for (cudaEvent_t *ev : {&P.ev_fork, &P.ev_tables, &P.ev_params}) {
         if (*ev) cudaEventDestroy(*ev);
         *ev = nullptr;
     }
-    for (cudaStream_t *s : {&P.aux[0], &P.aux[1], &P.cap}) {
+    for (cudaStream_t *s : {&P.aux, &P.cap}) {
         if (*s) cudaStreamDestroy(*s);
         *s = nullptr;
     }
@@ -643,8 +702,16 @@ void plan_merge(Plan &B, const std::vector<vc_circuit *> &cs)
             W.circ = cj;
             B.lw.push_back(W);
         }
-        grow(B.line_items, P.line_items.size());
-        append(B.line_items, P.line_items, olw);
+        auto tasks = [&](std::vector<std::vector<Task>> &dst, const std::vector<std::vector<Task>> &src) {
+            if (dst.size() < src.size()) dst.resize(src.size());
+            for (size_t k = 0; k < src.size(); k++)
+                for (Task t : src[k]) {
+                    t.wave += (t.type == TK_LINE) ? olw : (t.type == TK_PROD ? opw : ogw);
+                    dst[k].push_back(t);
+                }
+        };
+        tasks(B.groupsA, P.groupsA);
+        tasks(B.groupsB, P.groupsB);
         for (BuildItem b : P.builds) {
             b.circ = cj;
             B.builds.push_back(b);
@@ -663,18 +730,14 @@ void plan_merge(Plan &B, const std::vector<vc_circuit *> &cs)
             W.sci += osci;
             B.gw.push_back(W);
         }
-        grow(B.p_items, P.p_items.size());
-        grow(B.g_items, P.g_items.size());
-        append(B.p_items, P.p_items, opw);
-        append(B.g_items, P.g_items, ogw);
         for (RoundRef R : P.rounds) {
             R.sci += osci;
             B.rounds.push_back(R);
         }
         B.outs.push_back(cj);
-        B.has_tab = B.has_tab || P.has_tab;
         B.h_G.push_back(cs[j]->G);
     }
+    sort_tasks(B);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -689,16 +752,21 @@ void plan_merge(Plan &B, const std::vector<vc_circuit *> &cs)
 // general waves once the tables they read exist; the final reduction joins all.
 void enqueue_plan(Plan &P, cudaStream_t st)
 {
-    cudaStream_t sa = P.aux[0], sb = P.aux[1];
+    cudaStream_t sa = P.aux;
     const Globals *Gs = P.d_G;
     // stage events become event-record nodes of the captured graph
     auto mark = [&](int k, int end, cudaStream_t s) {
         if (P.stage_on) cudaEventRecordWithFlags(P.stage_ev[2 * k + end], s, cudaEventRecordExternal);
     };
+    const size_t nA = P.groupsA.size();
+    auto waves = [&](std::vector<Task> &tasks, Task *d_tasks, size_t g) {
+        launch_waves(Gs, P.d_lw, P.d_pw, P.d_gw, d_tasks, (int)tasks.size(), P.d_ctr + 2 * g, st);
+    };
     mark(VC_STAGE_PROOF, 0, st);
     mark(VC_STAGE_SETUP, 0, st);
     launch_setup(Gs, P.ncirc, st);
     mark(VC_STAGE_SETUP, 1, st);
+    // helper stream: eq tables and product weights (they need the coins only)
     cudaEventRecord(P.ev_fork, st);
     cudaStreamWaitEvent(sa, P.ev_fork, 0);
     mark(VC_STAGE_TABLES, 0, sa);
@@ -713,33 +781,21 @@ void enqueue_plan(Plan &P, cudaStream_t st)
         launch_eval_layers(Gs, P.d_levs, P.d_lev_items[k], (int)P.lev_items[k].size(), st);
     }
     mark(VC_STAGE_EVAL, 1, st);
-    cudaEventRecord(P.ev_eval, st);
-    cudaStreamWaitEvent(sa, P.ev_eval, 0);
-    for (size_t w = 0; w < P.p_items.size() || w < 2; w++) {
-        if (w < 2) mark(w == 0 ? VC_STAGE_PROD0 : VC_STAGE_PRODN, 0, sa);
-        if (w < P.p_items.size()) launch_sc_prod(Gs, P.d_pw, P.d_p_items[w], (int)P.p_items[w].size(), sa);
-        if (w == 0) mark(VC_STAGE_PROD0, 1, sa);
-    }
-    mark(VC_STAGE_PRODN, 1, sa);
-    cudaEventRecord(P.ev_prod, sa);
-    mark(VC_STAGE_LINE, 0, st);
-    for (size_t w = 0; w < P.line_items.size(); w++)
-        launch_line_wave(Gs, P.d_lw, P.d_line_items[w], (int)P.line_items[w].size(), st);
+    cudaStreamWaitEvent(st, P.ev_tables, 0);
+    // line reductions, product-weighted and on-the-fly general waves
+    mark(VC_STAGE_WAVES, 0, st);
+    if (nA) waves(P.groupsA[0], P.d_groupsA[0], 0);
+    mark(VC_STAGE_WAVES, 1, st);
+    mark(VC_STAGE_WAVESN, 0, st);
+    for (size_t g = 1; g < nA; g++) waves(P.groupsA[g], P.d_groupsA[g], g);
+    mark(VC_STAGE_WAVESN, 1, st);
+    // wiring tables (they need q(0) of every line reduction), then their waves
+    mark(VC_STAGE_BUILD, 0, st);
     launch_build23(Gs, P.d_builds, (int)P.builds.size(), st);
-    mark(VC_STAGE_LINE, 1, st);
-    cudaEventRecord(P.ev_build, st);
-    cudaStreamWaitEvent(sb, P.ev_eval, 0);
-    cudaStreamWaitEvent(sb, P.ev_tables, 0);
-    if (P.has_tab) cudaStreamWaitEvent(sb, P.ev_build, 0);
-    for (size_t w = 0; w < P.g_items.size() || w < 2; w++) {
-        if (w < 2) mark(w == 0 ? VC_STAGE_GEN0 : VC_STAGE_GENN, 0, sb);
-        if (w < P.g_items.size()) launch_sc_gen(Gs, P.d_gw, P.d_g_items[w], (int)P.g_items[w].size(), sb);
-        if (w == 0) mark(VC_STAGE_GEN0, 1, sb);
-    }
-    mark(VC_STAGE_GENN, 1, sb);
-    cudaEventRecord(P.ev_gen, sb);
-    cudaStreamWaitEvent(st, P.ev_prod, 0);
-    cudaStreamWaitEvent(st, P.ev_gen, 0);
+    mark(VC_STAGE_BUILD, 1, st);
+    mark(VC_STAGE_TABWAVES, 0, st);
+    for (size_t g = 0; g < P.groupsB.size(); g++) waves(P.groupsB[g], P.d_groupsB[g], nA + g);
+    mark(VC_STAGE_TABWAVES, 1, st);
     mark(VC_STAGE_FINAL, 0, st);
     launch_final(Gs, P.d_scis, P.d_rounds, (int)P.rounds.size(), P.d_outs, (int)P.outs.size(), st);
     mark(VC_STAGE_FINAL, 1, st);
@@ -778,10 +834,9 @@ int count_launches(const Plan &P)
     n += !P.pw.empty();
     n += !P.checks.empty();
     for (size_t k = 0; k < P.seg_items.size(); k++) n += (!P.seg_items[k].empty()) + (!P.lev_items[k].empty());
-    for (const auto &v : P.line_items) n += !v.empty();
+    for (const auto &v : P.groupsA) n += !v.empty();
     n += !P.builds.empty();
-    for (const auto &v : P.p_items) n += !v.empty();
-    for (const auto &v : P.g_items) n += !v.empty();
+    for (const auto &v : P.groupsB) n += !v.empty();
     return n + 1;  // final
 }
 
@@ -1149,8 +1204,7 @@ extern "C" vc_status vc_circuit_get_info(const vc_circuit *c, vc_circuit_info *i
     I.prove_launches = (uint32_t)count_launches(c->P);
     // parameters, setup, eq tables, input/output MLE, wiring (EXPLICIT only), checks
     I.verify_launches = (uint32_t)(5 + (c->explicit_layers.empty() ? 0 : 1));
-    I.sc0_ctas = (uint32_t)((c->P.p_items.empty() ? 0 : c->P.p_items[0].size()) +
-                            (c->P.g_items.empty() ? 0 : c->P.g_items[0].size()));
+    I.wave_tasks = (uint32_t)(c->P.groupsA.empty() ? 0 : c->P.groupsA[0].size());
     *info = I;
     return VC_OK;
 }

@@ -44,15 +44,15 @@ class _Desc(ctypes.Structure):
                 ("in2", ctypes.POINTER(_u32p))]
 
 
-NUM_STAGES = 10
-STAGES = ("proof", "setup", "tables", "eval", "line", "prod0", "prodn", "gen0", "genn", "final")
+NUM_STAGES = 9
+STAGES = ("proof", "setup", "tables", "eval", "waves", "wavesn", "build", "tabwaves", "final")
 
 
 class CircuitInfo(ctypes.Structure):
     _fields_ = [("n_layers", ctypes.c_uint32), ("n_rounds", ctypes.c_uint32),
                 ("transcript_len", ctypes.c_uint64), ("gates", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64), ("prove_launches", ctypes.c_uint32),
-                ("verify_launches", ctypes.c_uint32), ("sc0_ctas", ctypes.c_uint32),
+                ("verify_launches", ctypes.c_uint32), ("wave_tasks", ctypes.c_uint32),
                 ("pad", ctypes.c_uint32)]
 
 
