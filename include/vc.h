@@ -138,14 +138,14 @@ vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t seed,
                     const uint64_t *transcript, int *accept, void *stream);
 
 /* Stages of a proof, for timing them.  A proof runs on the caller's stream;
- * the eq tables and product weights run on a helper stream owned by the
- * circuit (forked from and joined back to the caller's stream), concurrently
- * with the evaluation.  The sum-check waves and line reductions of all
+ * the coins, eq tables and product weights run on a helper stream owned by
+ * the circuit (forked from and joined back to the caller's stream),
+ * concurrently with the evaluation.  The sum-check waves and line reductions of all
  * layers run as persistent launches that take their chunks from a shared
  * task counter. */
 typedef enum {
     VC_STAGE_PROOF = 0,     /* the whole proof                                          */
-    VC_STAGE_SETUP = 1,     /* coins, layer points, eq(z_i, r_P)                        */
+    VC_STAGE_SETUP = 1,     /* coins, layer points, eq(z_i, r_P)         (helper stream) */
     VC_STAGE_TABLES = 2,    /* split eq tables, product weights          (helper stream) */
     VC_STAGE_EVAL = 3,      /* layer-by-layer evaluation                                 */
     VC_STAGE_WAVES = 4,     /* first persistent launch: line reductions, product-weighted

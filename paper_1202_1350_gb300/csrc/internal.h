@@ -136,6 +136,8 @@ struct vc_circuit {
     EqJob *d_eq_verify = nullptr;
     u64 *partials = nullptr;
     VerifyDev Vd{};
+    VerifyPtrs *d_vp = nullptr;        // per-call verifier pointers (device)
+    cudaGraphExec_t vexec = nullptr;   // the verifier's captured launches
     EqTab tzd{};
     std::vector<u32> explicit_layers;
     u32 *d_explicit_layers = nullptr;

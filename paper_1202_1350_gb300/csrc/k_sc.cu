@@ -933,7 +933,11 @@ __device__ __forceinline__ bool wave_done(u32 *counter, u32 nchunks, u32 &s_flag
 
 extern __shared__ __align__(16) unsigned char wv_dyn[];
 
-__global__ void __launch_bounds__(WV_NT, 4) k_waves(const Globals *Gs, const LineWaveDev *lw, const ProdWave *pw,
+#ifndef WV_MINB
+#define WV_MINB 3  // resident CTAs per SM the register allocation is sized for (3: 168 registers, no spills)
+#endif
+
+__global__ void __launch_bounds__(WV_NT, WV_MINB) k_waves(const Globals *Gs, const LineWaveDev *lw, const ProdWave *pw,
                                                    const GenWave *gw, const Task *tasks, int ntasks, u32 *ctr)
 {
     WaveSmem &sm = *reinterpret_cast<WaveSmem *>(wv_dyn);
@@ -1003,7 +1007,7 @@ void launch_waves(const Globals *Gs, const LineWaveDev *lw, const ProdWave *pw, 
         if (sms <= 0) sms = 152;
         if (dev >= 0 && dev < 64) g_sm_count[dev] = sms;
     }
-    const int grid = std::min(ntasks, sms * 4);
+    const int grid = std::min(ntasks, sms * WV_MINB);
     k_waves<<<grid, WV_NT, sizeof(WaveSmem), st>>>(Gs, lw, pw, gw, tasks, ntasks, ctr);
 }
 

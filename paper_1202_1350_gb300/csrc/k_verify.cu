@@ -17,13 +17,12 @@
 // remaining blocks).  Every value contributes independently (Sec. 4.1.2);
 // products accumulate exactly in 128 bits.  A non-canonical input latches
 // ST_BAD_INPUT; a non-canonical output entry marks the transcript bad.
-__global__ void __launch_bounds__(VM_NT) k_vmle(const EqTab tzd, const u64 *x, u64 n, const EqTab tz0,
-                                                const u64 *out, u64 nout, u32 nin_blocks, u64 *part,
-                                                u32 *status, u64 *result)
+__global__ void __launch_bounds__(VM_NT) k_vmle(const EqTab tzd, const VerifyPtrs *vp, u64 n, const EqTab tz0,
+                                                u64 nout, u32 nin_blocks, u64 *part, u32 *status, u64 *result)
 {
     const bool inp = blockIdx.x < nin_blocks;
     const EqTab &tz = inp ? tzd : tz0;
-    const u64 *src = inp ? x : out;
+    const u64 *src = inp ? vp->inputs : vp->tr;  // the claimed outputs open the transcript
     const u64 cnt = inp ? n : nout;
     const u32 b = inp ? blockIdx.x : blockIdx.x - nin_blocks;
     const u32 nb = inp ? nin_blocks : gridDim.x - nin_blocks;
@@ -253,6 +252,7 @@ __device__ void wiring_warp(u32 kind, u32 si, u32 sn, const u64 *p, const u64 *w
 // verifier's checks.
 __global__ void __launch_bounds__(VC_NT) k_vcheck(Globals G, VerifyDev V, const u32 *round_layer, u32 nrounds)
 {
+    const u64 *const tr = V.vp->tr;
     const u32 lane = threadIdx.x & 31;
     const u64 g = blockIdx.x * (u64)VC_NT + threadIdx.x;
     const u64 gw = g >> 5;
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(VC_NT) k_vcheck(Globals G, VerifyDev V, const 
             start = wcanon(warp_wsum(acc));
         } else {
             const LayerDev &Lp = G.layers[i - 1];
-            start = lagrange_warp(V.tr + Lp.tr_q, Lp.sn, G.chal[Lp.chal_off + Lp.s + 2 * Lp.sn], G.invfact);
+            start = lagrange_warp(tr + Lp.tr_q, Lp.sn, G.chal[Lp.chal_off + Lp.s + 2 * Lp.sn], G.invfact);
         }
         u64 add = 0, mult = 0;
         if (L.kind == W_EXPLICIT) {
@@ -279,9 +279,9 @@ __global__ void __launch_bounds__(VC_NT) k_vcheck(Globals G, VerifyDev V, const 
         } else {
             wiring_warp(L.kind, si, sn, r, r + si, r + si + sn, add, mult);
         }
-        const u64 *q = V.tr + L.tr_q;
+        const u64 *q = tr + L.tr_q;
         if (lane == 0) {
-            const u64 *m = V.tr + L.tr_msg;
+            const u64 *m = tr + L.tr_msg;
             if (n > 0 && f_add(m[0], m[1]) != start) fail = 1;
             u64 claim = start;
             if (n > 0) {
@@ -305,14 +305,14 @@ __global__ void __launch_bounds__(VC_NT) k_vcheck(Globals G, VerifyDev V, const 
             const u32 i = round_layer[rho] >> 8, j = round_layer[rho] & 0xFF;
             if (j > 0) {
                 const LayerDev &L = G.layers[i];
-                const u64 *m = V.tr + L.tr_msg + 3ull * j;
+                const u64 *m = tr + L.tr_msg + 3ull * j;
                 const u64 prev = interp3(m[-3], m[-2], m[-1], G.chal[L.chal_off + j - 1]);
                 if (f_add(m[0], m[1]) != prev) fail = 1;
             }
         }
     }
     for (u64 k = g; k < V.tr_len; k += nthreads)
-        if (V.tr[k] >= FP_P) fail = 1;
+        if (tr[k] >= FP_P) fail = 1;
     if (__any_sync(0xffffffffu, fail != 0) && lane == 0) atomicOr(reinterpret_cast<unsigned long long *>(&V.result[3]), 1ull);
     // last CTA: publish the accept bit and reset the counter for the next call
     __shared__ bool s_last;
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(VC_NT) k_vcheck(Globals G, VerifyDev V, const 
         const u64 bad = atomicOr(reinterpret_cast<unsigned long long *>(&V.result[3]), 0ull);
         const int acc = bad ? 0 : 1;
         V.result[2] = (u64)acc;
-        if (V.accept_out) *V.accept_out = acc;
+        if (V.vp->accept_out) *V.vp->accept_out = acc;
         *V.counter = 0;
     }
 }
@@ -345,12 +345,26 @@ __global__ void k_init_invfact(u64 *invfact)
 
 void launch_init_invfact(u64 *invfact, cudaStream_t st) { k_init_invfact<<<1, 64, 0, st>>>(invfact); }
 
+__global__ void k_vparams(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *tr, const u64 *inputs, int *accept)
+{
+    G->seed = seed;
+    vp->tr = tr;
+    vp->inputs = inputs;
+    vp->accept_out = accept;
+}
+
+void launch_vparams(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *tr, const u64 *inputs, int *accept,
+                    cudaStream_t st)
+{
+    k_vparams<<<1, 1, 0, st>>>(G, vp, seed, tr, inputs, accept);
+}
+
 void launch_verify(const Globals &G, const VerifyDev &V, const EqTab &tzd, const EqTab &tz0,
                    const u32 *explicit_layers, int n_explicit, cudaStream_t st)
 {
     const u64 nin = 1ull << tzd.n, nout = 1ull << tz0.n;
-    k_vmle<<<V.mle_blocks + V.mle_out_blocks, VM_NT, 0, st>>>(tzd, V.inputs, nin, tz0, V.tr, nout, V.mle_blocks,
-                                                              V.mle_part, G.status, V.result);
+    k_vmle<<<V.mle_blocks + V.mle_out_blocks, VM_NT, 0, st>>>(tzd, V.vp, nin, tz0, nout, V.mle_blocks, V.mle_part,
+                                                              G.status, V.result);
     if (n_explicit > 0) k_vwire<<<n_explicit, VM_NT, 0, st>>>(G, explicit_layers, V.wire);
     const u64 threads = 32ull * G.d + V.nrounds;
     u64 blocks = (threads + VC_NT - 1) / VC_NT;

@@ -256,16 +256,23 @@ void prove_kernels_init();
 void waves_init();
 
 // verifier
+// Per-call pointers of a verification, written on the stream before the
+// verifier's captured launches (so that the launches can be replayed).
+struct VerifyPtrs {
+    const u64 *tr;      // transcript (device)
+    const u64 *inputs;  // S_d inputs (device)
+    int *accept_out;    // optional device int receiving the accept bit
+    u64 pad;
+};
+
 struct VerifyDev {
     u32 d;
     u64 tr_len;
-    const u64 *tr;      // transcript (device)
-    const u64 *inputs;  // S_d inputs (device)
+    const VerifyPtrs *vp;  // device
     u64 *mle_part;      // partial sums of the input MLE
     u32 mle_blocks;
     u64 *result;        // [0] input MLE, [1] output MLE, [2] accept flag, [3] bad-value flag
     u64 *wire;          // generic add~/mult~ per layer (EXPLICIT layers)
-    int *accept_out;    // optional device int receiving the accept bit
     u64 *claims;        // starting claim of every layer (d entries)
     u32 mle_out_blocks; // blocks of the output-MLE partials (after the input's)
     unsigned int *counter;  // CTAs of k_vcheck that finished (reset by the last)
@@ -273,6 +280,8 @@ struct VerifyDev {
     u32 nrounds;
 };
 void launch_init_invfact(u64 *invfact, cudaStream_t st);
+void launch_vparams(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *tr, const u64 *inputs, int *accept,
+                    cudaStream_t st);
 void launch_verify(const Globals &G, const VerifyDev &V, const EqTab &tzd, const EqTab &tz0,
                    const u32 *explicit_layers, int n_explicit, cudaStream_t st);
 

@@ -451,6 +451,7 @@ static size_t layout(vc_circuit *c, uintptr_t base)
     c->Vd.result = c->d_result;
     c->Vd.d = d;
     c->Vd.tr_len = c->tr_len;
+    c->Vd.vp = c->d_vp = A.take<VerifyPtrs>(1);
 
     // descriptor arrays
     c->d_layers = A.take<LayerDev>(d);
@@ -763,12 +764,13 @@ void enqueue_plan(Plan &P, cudaStream_t st)
         launch_waves(Gs, P.d_lw, P.d_pw, P.d_gw, d_tasks, (int)tasks.size(), P.d_ctr + 2 * g, st);
     };
     mark(VC_STAGE_PROOF, 0, st);
-    mark(VC_STAGE_SETUP, 0, st);
-    launch_setup(Gs, P.ncirc, st);
-    mark(VC_STAGE_SETUP, 1, st);
-    // helper stream: eq tables and product weights (they need the coins only)
+    // helper stream: coins, points, eq tables and product weights (they do not
+    // depend on the circuit's values), concurrently with the evaluation
     cudaEventRecord(P.ev_fork, st);
     cudaStreamWaitEvent(sa, P.ev_fork, 0);
+    mark(VC_STAGE_SETUP, 0, sa);
+    launch_setup(Gs, P.ncirc, sa);
+    mark(VC_STAGE_SETUP, 1, sa);
     mark(VC_STAGE_TABLES, 0, sa);
     launch_eqtabs(P.d_eqjobs, (int)P.eqjobs.size(), sa);
     launch_prep_prod(Gs, P.d_scis, P.d_pw, (int)P.pw.size(), sa);
@@ -939,6 +941,7 @@ vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **
 void circuit_free(vc_circuit *c)
 {
     if (!c) return;
+    if (c->vexec) cudaGraphExecDestroy(c->vexec);
     plan_release(c->P);
     if (c->arena) cudaFree(c->arena);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -1150,16 +1153,28 @@ extern "C" vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t s
         dtr = c->d_tr;
     }
     if (e != cudaSuccess) return VC_ECUDA;
-    launch_params(c->d_G, seed, c->d_tr, st);
-    launch_setup(c->d_G, 1, st);
-    launch_eqtabs(c->d_eq_verify, (int)c->eq_verify.size(), st);
-    VerifyDev Vd = c->Vd;
-    Vd.tr = dtr;
-    Vd.inputs = din;
-    e = cudaMemsetAsync(c->d_result, 0, 8 * sizeof(u64), st);
+    // the verifier's launches are one captured graph; the per-call pointers
+    // and seed are written on the stream ahead of it
+    launch_vparams(c->d_G, c->d_vp, seed, dtr, din, ka ? accept : nullptr, st);
+    if (!c->vexec) {
+        e = cudaStreamBeginCapture(c->P.cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return VC_ECUDA;
+        cudaStream_t cs = c->P.cap;
+        cudaMemsetAsync(c->d_result, 0, 8 * sizeof(u64), cs);
+        launch_setup(c->d_G, 1, cs);
+        launch_eqtabs(c->d_eq_verify, (int)c->eq_verify.size(), cs);
+        launch_verify(c->G, c->Vd, c->tzd, c->L[0].tz, c->d_explicit_layers, (int)c->explicit_layers.size(), cs);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->vexec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->vexec = nullptr;
+            return VC_ECUDA;
+        }
+    }
+    e = cudaGraphLaunch(c->vexec, st);
     if (e != cudaSuccess) return VC_ECUDA;
-    Vd.accept_out = ka ? accept : nullptr;
-    launch_verify(c->G, Vd, c->tzd, c->L[0].tz, c->d_explicit_layers, (int)c->explicit_layers.size(), st);
     if (ka && ki && kt) return cudaGetLastError() == cudaSuccess ? VC_OK : VC_ECUDA;
     e = cudaMemcpyAsync(c->h_pinned + 8, c->d_result, 4 * sizeof(u64), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaGetLastError();
