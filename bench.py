@@ -38,8 +38,8 @@ SC_CHUNK_LOG = 11
 
 
 def env_rank():
-    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
-            int(os.environ.get("WORLD_SIZE", "1")))
+    from paper_1202_1350_gb300 import replicas
+    return replicas.rank_env()
 
 
 # ---- clocks during the timed region --------------------------------------------------
@@ -221,7 +221,8 @@ def run_ours(args):
     gates = circuits.non_input_gates(widths)
     h = vc.vc_circuit_create(widths, kinds, None, local)
     info = vc.vc_circuit_get_info(h)
-    x = gen(seed0 + rank)
+    from paper_1202_1350_gb300 import replicas
+    x = gen(replicas.replica_seed(seed0, rank))
     xd = torch.from_numpy(x.view(np.int64).copy()).cuda()
     tr = torch.empty(info["transcript_len"], dtype=torch.int64, device="cuda")
     acc = torch.zeros(1, dtype=torch.int32, device="cuda")
@@ -262,13 +263,9 @@ def run_ours(args):
     clocks = sampler.stop()
     vc.vc_circuit_sync(h)
     assert oks == args.steps, "a timed proof was rejected"
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replicas.max_over_ranks(sum(step_ms), dist, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * gates * args.steps / (total_ms / 1000)
+    value = replicas.whole_job_rate(gates * args.steps, world, total_ms / 1000)
 
     # end to end through the C ABI with pinned host buffers
     xh = torch.from_numpy(x.view(np.int64).copy()).pin_memory()
@@ -283,11 +280,7 @@ def run_ours(args):
         ok = vc.vc_verify(h, xh, 500 + k, trh)
         e2e_ms.append(1000 * (time.perf_counter() - t0))
         assert ok
-    e2e_ms_mean = statistics.mean(e2e_ms)
-    if dist:
-        t = torch.tensor([e2e_ms_mean], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms_mean = float(t.item())
+    e2e_ms_mean = replicas.max_over_ranks(statistics.mean(e2e_ms), dist, "cuda")
     n_in = 1 << widths[-1]
     e2e = {"value": world * gates / (e2e_ms_mean / 1000), "unit": UNIT,
            "h2d_bytes_per_step": 2 * n_in * 8 + info["transcript_len"] * 8,
