@@ -75,6 +75,7 @@ struct Plan {
     std::vector<EvalSeg> segs;
     std::vector<LayerEval> levs;
     std::vector<std::vector<Item>> seg_items, lev_items;  // per evaluation step
+    std::vector<u32> seg_maxblock;                         // per step: largest block of its runs
     std::vector<LineWaveDev> lw;
     std::vector<BuildItem> builds;
     std::vector<SciDev> scis;
@@ -144,6 +145,7 @@ struct vc_circuit {
     std::vector<u32> round_layer, zmap;
     u32 *d_round_layer = nullptr, *d_zmap = nullptr;
     std::vector<int> eval_steps;  // >= 0: a segment; < 0: layer -step - 1 alone
+    std::vector<u32> seg_maxblock;  // per segment: largest block of its run and tail
     Plan P;                       // this circuit alone (circ = 0)
     u64 *h_pinned = nullptr;      // small pinned buffer for status/result readback
 };

@@ -195,7 +195,7 @@ void launch_eval_layers(const Globals *Gs, const LayerEval *le, const Item *item
 // evaluates it upward through the run in shared memory, writing each layer.
 // Block size of layer i = chunk size * 2^(s_i - s_in); all stay <= EV_MAXB.
 #define EV_NT 256
-#define EV_MAXB 4096
+#define EV_MAXB 2048
 
 extern __shared__ u64 ev_dyn[];
 
@@ -222,9 +222,74 @@ struct EvLayer {
     u64 *V;
 };
 
-__global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const EvalSeg *segs, const Item *items)
+// One layer of a block in shared memory, the gate kind's loop hoisted out of
+// the switch.
+__device__ __forceinline__ void eval_block_smem(u32 kind, const u64 *cur, u64 *nxt, u64 *__restrict__ out, u32 Bo)
 {
-    u64 *bufA = ev_dyn, *bufB = ev_dyn + EV_MAXB;
+    const u32 t = threadIdx.x;
+    switch (kind) {
+    case W_SQUARE:
+        for (u32 k = t; k < Bo; k += EV_NT) {
+            const u64 v = f_mul(cur[k], cur[k]);
+            nxt[k] = v;
+            out[k] = v;
+        }
+        break;
+    case W_TREE:
+        for (u32 k = t; k < Bo; k += EV_NT) {
+            const u64 v = f_add(cur[2 * k], cur[2 * k + 1]);
+            nxt[k] = v;
+            out[k] = v;
+        }
+        break;
+    default:
+        for (u32 k = t; k < Bo; k += EV_NT) {
+            u32 a, b, mul;
+            local_gate(kind, k, a, b, mul);
+            const u64 x = cur[a], y = cur[b];
+            const u64 v = mul ? f_mul(x, y) : f_add(x, y);
+            nxt[k] = v;
+            out[k] = v;
+        }
+        break;
+    }
+}
+
+// Layers whose blocks all fit in one warp (<= 64 entries in and out): warp 0
+// holds the block in registers (two entries per lane) and exchanges operands
+// with shuffles, without block-wide barriers.
+template <class LayerFn>
+__device__ __forceinline__ void eval_warp_layers(LayerFn layer, int hi, int lo, const u64 *cur, u32 B, bool chunked,
+                                                 u32 chunk)
+{
+    const u32 lane = threadIdx.x & 31;
+    u64 v0 = (lane < B) ? cur[lane] : 0, v1 = (lane + 32 < B) ? cur[lane + 32] : 0;
+    for (int i = hi; i >= lo; i--) {
+        const EvLayer L = layer((u32)i);
+        const u32 Bo = chunked ? ((L.s >= L.sn) ? (B << (L.s - L.sn)) : (B >> (L.sn - L.s))) : (1u << L.s);
+        u64 *__restrict__ out = L.V + (chunked ? (u64)chunk * Bo : 0);
+        u64 nv[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const u32 k = lane + 32 * h;
+            u32 a, b, mul;
+            local_gate(L.kind, k < Bo ? k : 0, a, b, mul);
+            const u64 xa0 = __shfl_sync(0xffffffffu, v0, a & 31), xa1 = __shfl_sync(0xffffffffu, v1, a & 31);
+            const u64 xb0 = __shfl_sync(0xffffffffu, v0, b & 31), xb1 = __shfl_sync(0xffffffffu, v1, b & 31);
+            const u64 x = (a < 32) ? xa0 : xa1, y = (b < 32) ? xb0 : xb1;
+            nv[h] = mul ? f_mul(x, y) : f_add(x, y);
+            if (k < Bo) out[k] = nv[h];
+        }
+        v0 = (lane < Bo) ? nv[0] : 0;
+        v1 = (lane + 32 < Bo) ? nv[1] : 0;
+        B = Bo;
+    }
+}
+
+__global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const EvalSeg *segs, const Item *items,
+                                                    u32 bufsz)
+{
+    u64 *bufA = ev_dyn, *bufB = ev_dyn + bufsz;  // bufsz >= every block of the launch's runs and tails
     __shared__ u32 s_kind[EV_LC], s_s[EV_LC], s_sn[EV_LC];
     __shared__ u64 *s_V[EV_LC];
     __shared__ const u64 *s_in;
@@ -263,6 +328,16 @@ __global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const Eva
         }
         return e;
     };
+    // do all layers hi..lo keep blocks of at most 64 entries (input B)?
+    auto warp_fits = [&](int hi, int lo, u32 B, bool chunked) {
+        if (B > 64) return false;
+        for (int i = hi; i >= lo; i--) {
+            const EvLayer L = layer((u32)i);
+            B = chunked ? ((L.s >= L.sn) ? (B << (L.s - L.sn)) : (B >> (L.sn - L.s))) : (1u << L.s);
+            if (B > 64) return false;
+        }
+        return true;
+    };
     u32 B = 1u << S.c;  // block size of the current (upper) layer
     constexpr int R = EV_MAXB / EV_NT;
     {
@@ -287,22 +362,17 @@ __global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const Eva
     }
     __syncthreads();
     u64 *cur = bufA, *nxt = bufB;
-    for (int i = (int)S.i_hi; i >= (int)S.i_lo; i--) {
+    int i = (int)S.i_hi;
+    for (; i >= (int)S.i_lo; i--) {
+        if (warp_fits(i, (int)S.i_lo, B, true)) break;
         const EvLayer L = layer((u32)i);
         const u32 Bo = (L.s >= L.sn) ? (B << (L.s - L.sn)) : (B >> (L.sn - L.s));
-        u64 *__restrict__ out = L.V + (u64)chunk * Bo;
-        for (u32 k = threadIdx.x; k < Bo; k += EV_NT) {
-            u32 a, b, mul;
-            local_gate(L.kind, k, a, b, mul);
-            const u64 x = cur[a], y = cur[b];
-            const u64 v = mul ? f_mul(x, y) : f_add(x, y);
-            nxt[k] = v;
-            out[k] = v;
-        }
+        eval_block_smem(L.kind, cur, nxt, L.V + (u64)chunk * Bo, Bo);
         __syncthreads();
         u64 *t = cur; cur = nxt; nxt = t;
         B = Bo;
     }
+    if (i >= (int)S.i_lo && threadIdx.x < 32) eval_warp_layers(layer, i, (int)S.i_lo, cur, B, true, chunk);
     if (S.tail_lo >= S.i_lo) return;
     // Last-CTA tail: every CTA publishes its writes and counts itself; the
     // last one evaluates the narrow layers below the run from the whole
@@ -315,50 +385,55 @@ __global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const Eva
     if (!s_last) return;
     __threadfence();
     if (threadIdx.x == 0) *S.counter = 0;
-    for (int i = (int)S.i_lo - 1; i >= (int)S.tail_lo; i--) {
+    {
+        // first tail layer: operands from the whole layer i_lo in global memory, all loads first
+        i = (int)S.i_lo - 1;
         const EvLayer L = layer((u32)i);
         const u32 Bo = 1u << L.s;
         u64 *__restrict__ out = L.V;
-        if (i == (int)S.i_lo - 1) {
-            // operands from the whole layer i_lo in global memory, all loads first
-            const u64 *__restrict__ vin = layer((u32)i + 1).V;
-            u64 xa[R], xb[R];
+        const u64 *__restrict__ vin = layer((u32)i + 1).V;
+        u64 xa[R], xb[R];
 #pragma unroll
-            for (int j = 0; j < R; j++) {
-                const u32 k = threadIdx.x + j * EV_NT;
+        for (int j = 0; j < R; j++) {
+            const u32 k = threadIdx.x + j * EV_NT;
+            u32 a, b, mul;
+            local_gate(L.kind, k, a, b, mul);
+            xa[j] = (k < Bo) ? __ldcg(vin + a) : 0;
+            xb[j] = (k < Bo) ? __ldcg(vin + b) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < R; j++) {
+            const u32 k = threadIdx.x + j * EV_NT;
+            if (k < Bo) {
                 u32 a, b, mul;
                 local_gate(L.kind, k, a, b, mul);
-                xa[j] = (k < Bo) ? __ldcg(vin + a) : 0;
-                xb[j] = (k < Bo) ? __ldcg(vin + b) : 0;
-            }
-#pragma unroll
-            for (int j = 0; j < R; j++) {
-                const u32 k = threadIdx.x + j * EV_NT;
-                if (k < Bo) {
-                    u32 a, b, mul;
-                    local_gate(L.kind, k, a, b, mul);
-                    const u64 v = mul ? f_mul(xa[j], xb[j]) : f_add(xa[j], xb[j]);
-                    nxt[k] = v;
-                    out[k] = v;
-                }
-            }
-        } else {
-            for (u32 k = threadIdx.x; k < Bo; k += EV_NT) {
-                u32 a, b, mul;
-                local_gate(L.kind, k, a, b, mul);
-                const u64 v = mul ? f_mul(cur[a], cur[b]) : f_add(cur[a], cur[b]);
+                const u64 v = mul ? f_mul(xa[j], xb[j]) : f_add(xa[j], xb[j]);
                 nxt[k] = v;
                 out[k] = v;
             }
         }
         __syncthreads();
         u64 *t = cur; cur = nxt; nxt = t;
+        B = Bo;
+        i--;
     }
+    for (; i >= (int)S.tail_lo; i--) {
+        if (warp_fits(i, (int)S.tail_lo, B, false)) break;
+        const EvLayer L = layer((u32)i);
+        const u32 Bo = 1u << L.s;
+        eval_block_smem(L.kind, cur, nxt, L.V, Bo);
+        __syncthreads();
+        u64 *t = cur; cur = nxt; nxt = t;
+        B = Bo;
+    }
+    if (i >= (int)S.tail_lo && threadIdx.x < 32) eval_warp_layers(layer, i, (int)S.tail_lo, cur, B, false, 0);
 }
 
-void launch_eval_segs(const Globals *Gs, const EvalSeg *segs, const Item *items, int nitems, cudaStream_t st)
+void launch_eval_segs(const Globals *Gs, const EvalSeg *segs, const Item *items, int nitems, u32 maxblock,
+                      cudaStream_t st)
 {
-    if (nitems > 0) k_eval_seg<<<nitems, EV_NT, 2 * EV_MAXB * sizeof(u64), st>>>(Gs, segs, items);
+    if (maxblock > EV_MAXB) maxblock = EV_MAXB;
+    if (nitems > 0) k_eval_seg<<<nitems, EV_NT, 2 * maxblock * sizeof(u64), st>>>(Gs, segs, items, maxblock);
 }
 
 __global__ void k_check_canonical(const u64 *x, u64 n, u32 *status)

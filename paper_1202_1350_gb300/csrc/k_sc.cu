@@ -1019,13 +1019,27 @@ void launch_waves(const Globals *Gs, const LineWaveDev *lw, const ProdWave *pw, 
 __global__ void __launch_bounds__(256) k_final(const Globals *Gs, const SciDev *scis, const RoundRef *rounds,
                                                int nrounds, const u32 *outs, int nouts)
 {
+    (void)scis;
     const u32 lane = threadIdx.x & 31;
     const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
     for (u64 gw = (blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5; gw < (u64)nrounds; gw += nwarps) {
         const RoundRef R = rounds[gw];
-        const SciDev &S = scis[R.sci];
-        const Globals &G = Gs[S.circ];
-        const u32 nv = (S.kind >= PK_GEN_FIRST) ? 3 : 2;
+        const bool gen = R.kind >= PK_GEN_FIRST;
+        const u32 nv = gen ? 3 : 2;
+        // the round's scalars, loaded while the partials are summed
+        u64 ez = 0, v1 = 0, ch = 0, es = 0, kap = 0, c0 = 0, c1 = 0;
+        if (lane == 0) {
+            ez = *R.ez;
+            if (!gen) {
+                v1 = *R.v1;
+                ch = *R.ch;
+                es = *R.esum;
+                kap = *R.kap;
+                c0 = R.lc[0];
+                c1 = R.lc[1];
+            }
+        }
+        u64 *tr = Gs[R.circ].tr;
         u64 h[3];
         for (u32 t = 0; t < nv; t++) {
             u64 s = 0;
@@ -1033,34 +1047,29 @@ __global__ void __launch_bounds__(256) k_final(const Globals *Gs, const SciDev *
             h[t] = wcanon(warp_wsum(s));
         }
         if (lane == 0) {
-            const LayerDev &L = G.layers[S.layer];
-            const u64 ez = G.scal[SCAL_EQZRP(S.layer)], v1 = G.scal[SCAL_V1(S.layer)];
             u64 g0, g1, g2;
-            if (nv == 3) {
-                const u64 sg = (S.kind == PK_GEN_TAB) ? 1 : ez;
+            if (gen) {
+                const u64 sg = (R.kind == PK_GEN_TAB) ? 1 : ez;
                 g0 = f_mul(sg, h[0]);
                 g1 = f_mul(sg, h[1]);
                 g2 = f_mul(sg, h[2]);
             } else {
                 u64 sigma = 1, c2u = 0;
-                if (S.kind == PK_TREE3) {
-                    sigma = f_mul(ez, f_sub(1, G.chal[L.chal_off + L.s]));
+                if (R.kind == PK_TREE3) {
+                    sigma = f_mul(ez, f_sub(1, ch));
                     c2u = v1;
-                } else if (S.kind == PK_SQ3) {
+                } else if (R.kind == PK_SQ3) {
                     sigma = f_mul(ez, v1);
                 }
-                const u32 j = R.j;
-                const u64 es = S.esum[j];
                 const u64 h0 = f_add(h[0], f_mul(c2u, es)), h1 = f_add(h[1], f_mul(c2u, es));
-                const u64 kj = f_mul(sigma, S.kap[j]);
-                const u64 c0 = S.Lc[2 * j], c1 = S.Lc[2 * j + 1];
+                const u64 kj = f_mul(sigma, kap);
                 g0 = f_mul(kj, f_mul(c0, h0));
                 g1 = f_mul(kj, f_mul(c1, h1));
                 g2 = f_mul(kj, f_mul(f_sub(f_add(c1, c1), c0), f_sub(f_add(h1, h1), h0)));
             }
-            G.tr[R.tr_pos] = g0;
-            G.tr[R.tr_pos + 1] = g1;
-            G.tr[R.tr_pos + 2] = g2;
+            tr[R.tr_pos] = g0;
+            tr[R.tr_pos + 1] = g1;
+            tr[R.tr_pos + 2] = g2;
         }
     }
     // the outputs open each transcript

@@ -161,14 +161,24 @@ struct Task {
 };
 
 // Final reduction of one round: sum the chunks' partials (2 per chunk for
-// PROD, 3 for GEN) and write g(0), g(1), g(2) at tr[tr_pos].
+// PROD, 3 for GEN) and write g(0), g(1), g(2) at tr[tr_pos].  Every scalar
+// the round needs is reached through its own pointer, so the loads are
+// independent of one another.
 struct RoundRef {
     u64 tr_pos;
     const u64 *part_pos;
     u32 nchunks;
+    u32 kind;         // PK_* of the instance
+    u32 circ;
     u32 sci;
-    u32 j;  // round index within the SCI
+    u32 j;            // round index within the SCI
     u32 pad;
+    const u64 *ez;    // eq(z_i, r_P) of the layer
+    const u64 *v1;    // V~_{i+1}(r1) of the layer
+    const u64 *ch;    // TREE phase 3: the first challenge of phase 2
+    const u64 *lc;    // PROD: c0, c1 of round j
+    const u64 *kap;   // PROD: kappa_j
+    const u64 *esum;  // PROD: esum_j
 };
 
 // Per-circuit globals.  Each circuit keeps one copy in device memory (and a
@@ -242,7 +252,10 @@ void launch_params_batch(Globals *Gs, const CallParams *cp, int n, cudaStream_t 
 void launch_setup(const Globals *Gs, int ncirc, cudaStream_t st);
 void launch_eqtabs(const EqJob *jobs, int njobs, cudaStream_t st);
 void launch_eval_layers(const Globals *Gs, const LayerEval *le, const Item *items, int nitems, cudaStream_t st);
-void launch_eval_segs(const Globals *Gs, const EvalSeg *segs, const Item *items, int nitems, cudaStream_t st);
+// maxblock: the largest block (entries) of any run layer or tail output in
+// the launch (<= 2048); it sizes the two shared-memory buffers.
+void launch_eval_segs(const Globals *Gs, const EvalSeg *segs, const Item *items, int nitems, u32 maxblock,
+                      cudaStream_t st);
 void launch_check_canonical(const u64 *x, u64 n, u32 *status, cudaStream_t st);
 void launch_check_inputs(const Globals *Gs, const Item *items, int nitems, cudaStream_t st);
 void launch_build23(const Globals *Gs, const BuildItem *items, int nitems, cudaStream_t st);

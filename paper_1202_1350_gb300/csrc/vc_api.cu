@@ -88,6 +88,7 @@ static void plan_eval(vc_circuit *c)
     P.levs.clear();
     P.checks.clear();
     c->eval_steps.clear();
+    c->seg_maxblock.clear();
     int i = (int)c->d - 1;
     auto local = [&](int j) { return c->kind[j] != W_MATMULT && c->kind[j] != W_EXPLICIT; };
     while (i >= 0) {
@@ -96,20 +97,24 @@ static void plan_eval(vc_circuit *c)
             i--;
             continue;
         }
+        // chunks of 2^cl entries of the run's input layer: about 1024 CTAs for
+        // wide layers, blocks of at most 2^11 entries
         const int s_in = (int)c->s[i + 1];
-        int cl = std::min(s_in, std::max(s_in - 8, 10));
-        cl = std::min(cl, 12);
+        int cl = std::min(s_in, std::max(10, s_in - 10));
+        cl = std::min(cl, 11);
         int i_lo = i + 1;
+        u32 maxblock = 1;
         while (true) {
             int e = cl, j = i;
             i_lo = i + 1;
-            const bool whole = (cl == s_in);
+            maxblock = 1u << cl;
             while (j >= 0 && local(j)) {
                 const int ne = e + (int)c->s[j] - (int)c->s[j + 1];
-                if (ne < 0 || ne > 12 || (!whole && ne < 5)) break;
+                if (ne < 0 || ne > 11) break;
                 if (c->kind[j] == W_F0_PAIR && ne < 1) break;
                 e = ne;
                 i_lo = j;
+                maxblock = std::max(maxblock, 1u << ne);
                 j--;
             }
             if (i_lo <= i || cl == 0) break;
@@ -127,19 +132,25 @@ static void plan_eval(vc_circuit *c)
         S.c = (u32)cl;
         S.nchunks = 1u << (s_in - cl);
         S.check_input = (u32)(i + 1 == (int)c->d);
-        // tail: narrow local layers below the run (outputs <= EV_MAXB, first
+        // tail: narrow local layers below the run (outputs <= 2^11, first
         // input <= 2^16) go to the CTA that finishes last
         S.tail_lo = S.i_lo;
         if (S.nchunks > 1 && c->s[i_lo] <= 16)
-            for (int j = i_lo - 1; j >= 0 && local(j) && c->s[j] <= 12; j--) S.tail_lo = (u32)j;
+            for (int j = i_lo - 1; j >= 0 && local(j) && c->s[j] <= 11; j--) {
+                S.tail_lo = (u32)j;
+                maxblock = std::max(maxblock, 1u << c->s[j]);
+            }
         c->eval_steps.push_back((int)P.segs.size());
+        c->seg_maxblock.push_back(maxblock);
         P.segs.push_back(S);
         i = (int)S.tail_lo - 1;
     }
     P.seg_items.assign(c->eval_steps.size(), {});
     P.lev_items.assign(c->eval_steps.size(), {});
+    P.seg_maxblock.assign(c->eval_steps.size(), 1u);
     for (size_t k = 0; k < c->eval_steps.size(); k++) {
         const int step = c->eval_steps[k];
+        if (step >= 0) P.seg_maxblock[k] = c->seg_maxblock[step];
         if (step >= 0) {
             for (u32 ch = 0; ch < P.segs[step].nchunks; ch++) P.seg_items[k].push_back({(u32)step, ch});
         } else {
@@ -351,8 +362,18 @@ static size_t layout(vc_circuit *c, uintptr_t base)
                     RoundRef R{};
                     R.tr_pos = Sc.tr_off + 3ull * (r0 + k);
                     R.nchunks = nchunks;
+                    R.kind = Sc.kind;
+                    R.circ = 0;
                     R.sci = sci;
                     R.j = r0 + k;
+                    R.ez = G.scal + SCAL_EQZRP(i);
+                    R.v1 = G.scal + SCAL_V1(i);
+                    R.ch = G.chal + c->chal_off[i] + c->s[i];
+                    if (prod) {
+                        R.lc = Sc.Lc + 2 * R.j;
+                        R.kap = Sc.kap + R.j;
+                        R.esum = Sc.esum + R.j;
+                    }
                     round_off.push_back(part_total + u64(k) * nchunks * nv);
                     P.rounds.push_back(R);
                 }
@@ -536,7 +557,9 @@ bool plan_valid(const Plan &P)
     for (const LineWaveDev &W : P.lw)
         if (W.nl > (W.l0 ? LN_CHUNKW_LOG : LN_CHUNK0_LOG) || W.n > 30) return false;
     for (const RoundRef &R : P.rounds)
-        if (R.sci >= P.scis.size() || R.j >= P.scis[R.sci].n) return false;
+        if (R.sci >= P.scis.size() || R.j >= P.scis[R.sci].n || R.circ >= nc || P.scis[R.sci].circ != R.circ ||
+            !R.ez || !R.v1 || !R.ch || (R.kind < PK_GEN_FIRST && (!R.lc || !R.kap || !R.esum)))
+            return false;
     for (u32 o : P.outs)
         if (o >= nc) return false;
     for (const auto &v : P.seg_items)
@@ -697,6 +720,9 @@ void plan_merge(Plan &B, const std::vector<vc_circuit *> &cs)
         }
         grow(B.seg_items, P.seg_items.size());
         grow(B.lev_items, P.lev_items.size());
+        if (B.seg_maxblock.size() < P.seg_maxblock.size()) B.seg_maxblock.resize(P.seg_maxblock.size(), 1u);
+        for (size_t k = 0; k < P.seg_maxblock.size(); k++)
+            B.seg_maxblock[k] = std::max(B.seg_maxblock[k], P.seg_maxblock[k]);
         append(B.seg_items, P.seg_items, oseg);
         append(B.lev_items, P.lev_items, olev);
         for (LineWaveDev W : P.lw) {
@@ -733,6 +759,7 @@ void plan_merge(Plan &B, const std::vector<vc_circuit *> &cs)
         }
         for (RoundRef R : P.rounds) {
             R.sci += osci;
+            R.circ = cj;
             B.rounds.push_back(R);
         }
         B.outs.push_back(cj);
@@ -779,7 +806,7 @@ void enqueue_plan(Plan &P, cudaStream_t st)
     mark(VC_STAGE_EVAL, 0, st);
     launch_check_inputs(Gs, P.d_checks, (int)P.checks.size(), st);
     for (size_t k = 0; k < P.seg_items.size(); k++) {
-        launch_eval_segs(Gs, P.d_segs, P.d_seg_items[k], (int)P.seg_items[k].size(), st);
+        launch_eval_segs(Gs, P.d_segs, P.d_seg_items[k], (int)P.seg_items[k].size(), P.seg_maxblock[k], st);
         launch_eval_layers(Gs, P.d_levs, P.d_lev_items[k], (int)P.lev_items[k].size(), st);
     }
     mark(VC_STAGE_EVAL, 1, st);
@@ -1120,7 +1147,7 @@ extern "C" vc_status vc_evaluate(vc_circuit *c, const uint64_t *inputs, uint64_t
     launch_check_canonical(c->V[c->d], nin, c->G.status, st);
     const Plan &P = c->P;
     for (size_t k = 0; k < P.seg_items.size(); k++) {
-        launch_eval_segs(P.d_G, P.d_segs, P.d_seg_items[k], (int)P.seg_items[k].size(), st);
+        launch_eval_segs(P.d_G, P.d_segs, P.d_seg_items[k], (int)P.seg_items[k].size(), P.seg_maxblock[k], st);
         launch_eval_layers(P.d_G, P.d_levs, P.d_lev_items[k], (int)P.lev_items[k].size(), st);
     }
     e = cudaMemcpyAsync(outputs, c->V[0], (u64(1) << c->s[0]) * sizeof(u64),
