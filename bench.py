@@ -227,8 +227,13 @@ def run_ours(args):
     tr = torch.empty(info["transcript_len"], dtype=torch.int64, device="cuda")
     acc = torch.zeros(1, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.int64, device="cuda")
-    stage_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * vc.NUM_STAGES)]
-    vc.vc_circuit_set_stage_events(h, stage_ev)
+    # the timed region records only the dominant launch's two events (each
+    # recorded event costs device time); the stage breakdown is a separate pass
+    iw = vc.STAGES.index("waves")
+    wave_ev = [None] * (2 * vc.NUM_STAGES)
+    wave_ev[2 * iw] = torch.cuda.Event(enable_timing=True)
+    wave_ev[2 * iw + 1] = torch.cuda.Event(enable_timing=True)
+    vc.vc_circuit_set_stage_events(h, wave_ev)
 
     def step(seed):
         vc.vc_prove(h, xd, seed, tr)
@@ -246,7 +251,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
-    step_ms, stage_ms = [], [[] for _ in range(vc.NUM_STAGES)]
+    step_ms, wave_ms = [], []
     oks = 0
     for k in range(args.steps):
         flush.zero_()
@@ -256,8 +261,7 @@ def run_ours(args):
         e1.record()
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        for s in range(vc.NUM_STAGES):
-            stage_ms[s].append(stage_ev[2 * s].elapsed_time(stage_ev[2 * s + 1]))
+        wave_ms.append(wave_ev[2 * iw].elapsed_time(wave_ev[2 * iw + 1]))
         oks += int(acc.item())
     torch.cuda.synchronize()
     clocks = sampler.stop()
@@ -270,6 +274,22 @@ def run_ours(args):
     # end to end through the C ABI with pinned host buffers
     xh = torch.from_numpy(x.view(np.int64).copy()).pin_memory()
     trh = torch.empty(info["transcript_len"], dtype=torch.int64).pin_memory()
+    # stage breakdown (diagnostic, outside the timed region): every stage's events
+    stage_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * vc.NUM_STAGES)]
+    vc.vc_circuit_set_stage_events(h, stage_ev)
+    stage_ms = {}
+    for k in range(5):
+        flush.zero_()
+        vc.vc_prove(h, xd, 900 + k, tr)
+        torch.cuda.synchronize()
+        if k >= 2:
+            for i, name in enumerate(vc.STAGES):
+                if name in ("wavesn", "build", "tabwaves"):  # no work in SQUARE/TREE circuits
+                    continue
+                try:
+                    stage_ms.setdefault(name, []).append(stage_ev[2 * i].elapsed_time(stage_ev[2 * i + 1]))
+                except RuntimeError:  # a stage with no work records nothing
+                    pass
     vc.vc_circuit_set_stage_events(h, None)
     vc.vc_prove(h, xh, 999, trh)
     e2e_ms = []
@@ -297,11 +317,11 @@ def run_ours(args):
     # the dominant launch: the first product-weighted and general waves run
     # concurrently on two streams; the roofline covers the longer of the two
     # spans, with both launches' work
-    sc0_ms = statistics.mean(stage_ms[vc.STAGES.index("waves")])
+    sc0_ms = statistics.mean(wave_ms)
     mul, byts = wave_work(widths, kinds)
     rate = vc.vc_field_mul_rate(local, 2, 1 << 12)
     achieved = mul / (sc0_ms / 1000)
-    stages = {name: round(statistics.mean(v), 4) for name, v in zip(vc.STAGES, stage_ms)}
+    stages = {name: round(statistics.mean(v), 4) for name, v in stage_ms.items()}
     launches = (info["prove_launches"] + info["verify_launches"]) * args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -144,26 +144,27 @@ vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t seed,
  * layers run as persistent launches that take their chunks from a shared
  * task counter. */
 typedef enum {
-    VC_STAGE_PROOF = 0,     /* the whole proof                                          */
-    VC_STAGE_SETUP = 1,     /* coins, layer points, eq(z_i, r_P)         (helper stream) */
-    VC_STAGE_TABLES = 2,    /* split eq tables, product weights          (helper stream) */
-    VC_STAGE_EVAL = 3,      /* layer-by-layer evaluation                                 */
-    VC_STAGE_WAVES = 4,     /* first persistent launch: line reductions, product-weighted
+    VC_STAGE_PROOF = 0,     /* the whole proof                                           */
+    VC_STAGE_TABLES = 1,    /* one launch: coins, layer points, eq(z_i, r_P), split eq
+                               tables, product weights                   (helper stream) */
+    VC_STAGE_EVAL = 2,      /* layer-by-layer evaluation                                  */
+    VC_STAGE_WAVES = 3,     /* first persistent launch: line reductions, product-weighted
                                and on-the-fly general sum-checks (their single-chunk
                                later waves run inside it)                                */
-    VC_STAGE_WAVESN = 5,    /* later persistent launches of the same kinds (wide layers) */
-    VC_STAGE_BUILD = 6,     /* phase-2/3 wiring tables (MATMULT, F0, EXPLICIT layers)    */
-    VC_STAGE_TABWAVES = 7,  /* general sum-checks over the built tables                  */
-    VC_STAGE_FINAL = 8,     /* per-round reductions into the transcript                  */
-    VC_NUM_STAGES = 9
+    VC_STAGE_WAVESN = 4,    /* later persistent launches of the same kinds (wide layers) */
+    VC_STAGE_BUILD = 5,     /* phase-2/3 wiring tables (MATMULT, F0, EXPLICIT layers)    */
+    VC_STAGE_TABWAVES = 6,  /* general sum-checks over the built tables                  */
+    VC_STAGE_FINAL = 7,     /* per-round reductions into the transcript                  */
+    VC_NUM_STAGES = 8
 } vc_stage;
 
 /* Record CUDA events around the stages of every later vc_prove on this
  * circuit: events[2k] when stage k starts and events[2k+1] when it ends, each
- * on the stream that runs the stage (a stage with no work records both
- * back to back).  `events` must hold 2 * VC_NUM_STAGES events (cudaEvent_t)
- * created on the circuit's device and owned by the caller; NULL turns
- * recording off.  A proof replays a CUDA graph of its launches, captured by
+ * on the stream that runs the stage; a stage with no work for this circuit
+ * records nothing.  `events` must hold 2 * VC_NUM_STAGES entries: cudaEvent_t
+ * created on the circuit's device and owned by the caller, or NULL to skip
+ * that mark (each recorded event costs a little device time: record only the
+ * stages you time).  events == NULL turns recording off.  A proof replays a CUDA graph of its launches, captured by
  * the first vc_prove after the circuit's creation or after this call; the
  * events are event-record nodes of that graph.  The call must not overlap a
  * proof in flight on the circuit (it may replace the graph). */

@@ -40,108 +40,6 @@ void launch_params_batch(Globals *Gs, const CallParams *cp, int n, cudaStream_t 
     if (n > 0) k_params_batch<<<(n + 255) / 256, 256, 0, st>>>(Gs, cp, n);
 }
 
-// One CTA per circuit.
-__global__ void __launch_bounds__(1024) k_setup(const Globals *Gs)
-{
-    const Globals &G = Gs[blockIdx.x];
-    const u32 *zmap = G.zmap;
-    const u32 nz = G.nz, zd_off = G.zd_off;
-    __shared__ int s_rej;
-    if (threadIdx.x == 0) s_rej = 0;
-    __syncthreads();
-    // Challenge c is the (c+1)-th accepted draw; draws equal to p (probability
-    // 2^-61 each) are rejected, so in the common case draw c is output c+1.
-    for (u32 c = threadIdx.x; c < G.nchal; c += blockDim.x) {
-        u64 x = splitmix64_at(G.seed, (u64)c + 1) >> 3;
-        G.chal[c] = x;
-        if (x == FP_P) s_rej = 1;
-    }
-    __syncthreads();
-    if (s_rej) {
-        if (threadIdx.x == 0) {
-            u64 k = 1;
-            for (u32 c = 0; c < G.nchal; c++) {
-                u64 x;
-                do { x = splitmix64_at(G.seed, k++) >> 3; } while (x == FP_P);
-                G.chal[c] = x;
-            }
-        }
-        __syncthreads();
-    }
-    const LayerDev *L = G.layers;
-    // z_0 and every z_{i+1} = l_i(tau_i) = r1 + tau (r2 - r1): one thread per
-    // coordinate (zmap[q] = layer << 8 | k for the flattened coordinates).
-    for (u32 k = threadIdx.x; k < L[0].s; k += blockDim.x) G.pts[L[0].z_off + k] = G.chal[k];
-    for (u32 qi = threadIdx.x; qi < nz; qi += blockDim.x) {
-        const u32 i = zmap[qi] >> 8, k = zmap[qi] & 0xFF;
-        const u32 si = L[i].s, sn = L[i].sn, co = L[i].chal_off;
-        const u64 tau = G.chal[co + si + 2 * sn];
-        const u64 r1 = G.chal[co + si + k], r2 = G.chal[co + si + sn + k];
-        G.pts[((i + 1 < G.d) ? L[i + 1].z_off : zd_off) + k] = f_add(r1, f_mul(tau, f_sub(r2, r1)));
-    }
-    __syncthreads();
-    // eq(z_i, r_P) per layer: a warp per layer, a lane per coordinate (s_i <= 30).
-    const u32 lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (u32 i = warp; i < G.d; i += blockDim.x >> 5) {
-        u64 f = 1;
-        if (lane < L[i].s) {
-            const u64 z = G.pts[L[i].z_off + lane], rp = G.chal[L[i].chal_off + lane];
-            f = f_add(f_mul(z, rp), f_mul(f_sub(1, z), f_sub(1, rp)));
-        }
-        f = warp_prod(f);
-        if (lane == 0) G.scal[SCAL_EQZRP(i)] = f;
-    }
-}
-
-void launch_setup(const Globals *Gs, int ncirc, cudaStream_t st)
-{
-    if (ncirc > 0) k_setup<<<ncirc, 1024, 0, st>>>(Gs);
-}
-
-// --------------------------------------------------------------------------------
-// Split eq tables: lo[j] = prod_{k<h} eq(x_k, bit_k j), hi[j] = prod_{k<n-h} eq(x_{h+k}, bit_k j).
-// --------------------------------------------------------------------------------
-
-// Each half (lo over coordinates [0, h), hi over [h, n)) is itself a product
-// of two sub-tables over its low and high coordinates, built by direct
-// products (at most 8 factors), so every entry costs one product.
-__global__ void __launch_bounds__(256) k_eqtabs(const EqJob *jobs)
-{
-    const EqTab t = jobs[blockIdx.x].t;
-    __shared__ u64 x[64], xm[64];
-    __shared__ u64 sub[4][256];
-    for (u32 k = threadIdx.x; k < t.n; k += blockDim.x) {
-        x[k] = t.pt[k];
-        xm[k] = f_sub(1, x[k]);
-    }
-    __syncthreads();
-    const u32 m[2] = {t.h, t.n - t.h};
-    const u32 c0[2] = {0, t.h};
-    // sub-tables: half j, part a (low m1 coordinates) / b (high)
-    for (u32 j = 0; j < 2; j++) {
-        const u32 m1 = m[j] / 2, m2 = m[j] - m1;
-        for (u32 e = threadIdx.x; e < (1u << m1) + (1u << m2); e += blockDim.x) {
-            const bool lowp = e < (1u << m1);
-            const u32 idx = lowp ? e : e - (1u << m1);
-            const u32 cnt = lowp ? m1 : m2, off = c0[j] + (lowp ? 0 : m1);
-            u64 v = 1;
-            for (u32 k = 0; k < cnt; k++) v = f_mul(v, ((idx >> k) & 1) ? x[off + k] : xm[off + k]);
-            sub[2 * j + (lowp ? 0 : 1)][idx] = v;
-        }
-    }
-    __syncthreads();
-    u64 *dst[2] = {t.lo, t.hi};
-    for (u32 j = 0; j < 2; j++) {
-        const u32 m1 = m[j] / 2;
-        for (u32 e = threadIdx.x; e < (1u << m[j]); e += blockDim.x)
-            dst[j][e] = f_mul(sub[2 * j][e & ((1u << m1) - 1)], sub[2 * j + 1][e >> m1]);
-    }
-}
-
-void launch_eqtabs(const EqJob *jobs, int njobs, cudaStream_t st)
-{
-    if (njobs > 0) k_eqtabs<<<njobs, 256, 0, st>>>(jobs);
-}
 
 // --------------------------------------------------------------------------------
 // Wiring: in-neighbours and gate type of gate g (Sec. 5.1.4, Sec. 6.2.1).
@@ -328,16 +226,6 @@ __global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const Eva
         }
         return e;
     };
-    // do all layers hi..lo keep blocks of at most 64 entries (input B)?
-    auto warp_fits = [&](int hi, int lo, u32 B, bool chunked) {
-        if (B > 64) return false;
-        for (int i = hi; i >= lo; i--) {
-            const EvLayer L = layer((u32)i);
-            B = chunked ? ((L.s >= L.sn) ? (B << (L.s - L.sn)) : (B >> (L.sn - L.s))) : (1u << L.s);
-            if (B > 64) return false;
-        }
-        return true;
-    };
     u32 B = 1u << S.c;  // block size of the current (upper) layer
     constexpr int R = EV_MAXB / EV_NT;
     {
@@ -364,7 +252,7 @@ __global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const Eva
     u64 *cur = bufA, *nxt = bufB;
     int i = (int)S.i_hi;
     for (; i >= (int)S.i_lo; i--) {
-        if (warp_fits(i, (int)S.i_lo, B, true)) break;
+        if (i == (int)S.warp_from) break;
         const EvLayer L = layer((u32)i);
         const u32 Bo = (L.s >= L.sn) ? (B << (L.s - L.sn)) : (B >> (L.sn - L.s));
         eval_block_smem(L.kind, cur, nxt, L.V + (u64)chunk * Bo, Bo);
@@ -418,7 +306,7 @@ __global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const Eva
         i--;
     }
     for (; i >= (int)S.tail_lo; i--) {
-        if (warp_fits(i, (int)S.tail_lo, B, false)) break;
+        if (i == (int)S.tail_warp_from) break;
         const EvLayer L = layer((u32)i);
         const u32 Bo = 1u << L.s;
         eval_block_smem(L.kind, cur, nxt, L.V, Bo);

@@ -73,117 +73,9 @@ __device__ __forceinline__ u64 warp_sum32(u64 (&v)[32])
     return wred(v[0]);
 }
 
-// --------------------------------------------------------------------------------
-// PROD: per-wave weight tables (computed once per proof, shared by all CTAs)
-// --------------------------------------------------------------------------------
+// (The per-wave weight tables of the PROD waves are built with the coins, in
+// k_coins.cu.)
 
-// Linear factor L_m of a product-weighted instance, from the coins.
-__device__ __forceinline__ void prod_factor(const Globals &G, const SciDev &S, u32 m, u64 &c0, u64 &c1)
-{
-    const LayerDev &L = G.layers[S.layer];
-    const u64 *rP = G.chal + L.chal_off, *r1 = rP + L.s;
-    switch (S.kind) {
-    case PK_PH1: {
-        const u64 z = G.pts[L.z_off + m];
-        c0 = f_sub(1, z);
-        c1 = z;
-        break;
-    }
-    case PK_TREE3: {
-        if (m == 0) {
-            c0 = 0;
-            c1 = 1;
-        } else {
-            const u64 a = rP[m - 1], b = r1[m];
-            c0 = f_mul(f_sub(1, a), f_sub(1, b));
-            c1 = f_mul(a, b);
-        }
-        break;
-    }
-    default: {  // PK_SQ3
-        const u64 a = rP[m], b = r1[m];
-        c0 = f_mul(f_sub(1, a), f_sub(1, b));
-        c1 = f_mul(a, b);
-        break;
-    }
-    }
-}
-
-// One CTA per PROD wave.  Writes the wave's weight block
-//   Q_k(q) = prod_{m=k+1}^{e-1} L_{r0+m}(bit_{m-k-1} q)      k < e          (in-thread rounds)
-//   E_k(y) = prod_{m=k+1}^{nr-1} L_{r0+m}(bit_{m-k-1} y)     k = kb..nr-1   (per-thread / in-CTA rounds)
-//   outer lo / hi: split table of prod_{m >= r0+nr} L_m over the chunk index,
-// and, for the first wave of an SCI, its factors, kappa_j (without sigma) and
-// esum_j = prod_{m>j} (c0_m + c1_m).
-__global__ void __launch_bounds__(256) k_prep_prod(const Globals *Gs, const SciDev *scis, const ProdWave *waves)
-{
-    const ProdWave &W = waves[blockIdx.x];
-    const Globals &G = Gs[W.circ];
-    const SciDev &S = scis[W.sci];
-    __shared__ u64 c0[32], c1[32];
-    const u32 tid = threadIdx.x;
-    if (tid < S.n) prod_factor(G, S, tid, c0[tid], c1[tid]);
-    __syncthreads();
-    if (W.r0 == 0 && tid < 32) {
-        // kappa_j = prod_{m<j} L_m(r_m), esum_j = prod_{m>j} (c0_m + c1_m): warp scans
-        const u32 j = tid;
-        const bool in = j < S.n;
-        const u64 a = in ? f_add(c0[j], f_mul(G.chal[S.chal_off + j], f_sub(c1[j], c0[j]))) : 1;
-        const u64 b = in ? f_add(c0[j], c1[j]) : 1;
-        u64 pre = __shfl_up_sync(0xffffffffu, warp_scan_mul(a), 1);
-        u64 suf = __shfl_down_sync(0xffffffffu, warp_rscan_mul(b), 1);
-        if (j == 0) pre = 1;
-        if (j == 31) suf = 1;
-        if (in) {
-            S.Lc[2 * j] = c0[j];
-            S.Lc[2 * j + 1] = c1[j];
-            S.kap[j] = pre;
-            S.esum[j] = suf;
-        }
-    }
-    const u32 e = W.e, nr = W.nr, r0 = W.r0;
-    u64 *blk = W.wblk;
-    // Q block
-    for (u32 idx = tid; idx + 1 < (1u << e); idx += blockDim.x) {
-        u32 k = 0;
-        while (idx >= (1u << e) - (1u << (e - k - 1))) k++;
-        const u32 q = idx - ((1u << e) - (1u << (e - k)));
-        u64 v = 1;
-        for (u32 m = k + 1; m < e; m++) v = f_mul(v, ((q >> (m - k - 1)) & 1) ? c1[r0 + m] : c0[r0 + m]);
-        blk[idx] = v;
-    }
-    // E block
-    const u32 kb = e ? e - 1 : 0;
-    u64 *E = blk + ((1u << e) - 1);
-    const u32 esize = (1u << (nr - kb)) - 1;
-    for (u32 idx = tid; idx < esize; idx += blockDim.x) {
-        u32 k = kb;
-        while (idx >= (1u << (nr - kb)) - (1u << (nr - k - 1))) k++;
-        const u32 y = idx - ((1u << (nr - kb)) - (1u << (nr - k)));
-        u64 v = 1;
-        for (u32 m = k + 1; m < nr; m++) v = f_mul(v, ((y >> (m - k - 1)) & 1) ? c1[r0 + m] : c0[r0 + m]);
-        E[idx] = v;
-    }
-    // outer split tables
-    u64 *olo = E + esize;
-    const u32 o0 = r0 + nr, no = W.no, ho = W.ho;
-    u64 *ohi = olo + (1u << ho);
-    for (u32 j = tid; j < (1u << ho); j += blockDim.x) {
-        u64 v = 1;
-        for (u32 m = 0; m < ho; m++) v = f_mul(v, ((j >> m) & 1) ? c1[o0 + m] : c0[o0 + m]);
-        olo[j] = v;
-    }
-    for (u32 j = tid; j < (1u << (no - ho)); j += blockDim.x) {
-        u64 v = 1;
-        for (u32 m = 0; m < no - ho; m++) v = f_mul(v, ((j >> m) & 1) ? c1[o0 + ho + m] : c0[o0 + ho + m]);
-        ohi[j] = v;
-    }
-}
-
-void launch_prep_prod(const Globals *Gs, const SciDev *scis, const ProdWave *waves, int nwaves, cudaStream_t st)
-{
-    if (nwaves > 0) k_prep_prod<<<nwaves, 256, 0, st>>>(Gs, scis, waves);
-}
 
 // --------------------------------------------------------------------------------
 // One persistent launch for the waves of every instance: CTAs of WV_NT threads

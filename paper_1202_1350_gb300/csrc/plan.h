@@ -215,8 +215,10 @@ struct EvalSeg {
     u32 nchunks;
     u32 check_input;  // the run's input layer is the circuit's input layer
     u32 tail_lo;
-    u32 pad;
+    u32 warp_from;       // first run layer whose blocks all fit one warp (i_lo - 1: none)
     u32 *counter;
+    u32 tail_warp_from;  // first tail layer from which all fit one warp (tail_lo - 1: none)
+    u32 pad2;
 };
 
 // A layer evaluated on its own (MATMULT or EXPLICIT wiring).
@@ -243,14 +245,23 @@ struct CallParams {
 #define ST_TIMEOUT 2u
 
 // ---- launch entry points (implemented in the .cu files) -------------------------
+// An eq table to build and where its point comes from: challenges
+// chal[off ..] (EQ_SRC_CHAL) or the point z_layer (EQ_SRC_Z).
+enum : u32 { EQ_SRC_CHAL = 0, EQ_SRC_Z = 1 };
 struct EqJob {
     EqTab t;
+    u32 circ;
+    u32 src;
+    u32 off;
+    u32 layer;
 };
 
 void launch_params(Globals *G, u64 seed, u64 *tr, cudaStream_t st);
 void launch_params_batch(Globals *Gs, const CallParams *cp, int n, cudaStream_t st);
-void launch_setup(const Globals *Gs, int ncirc, cudaStream_t st);
-void launch_eqtabs(const EqJob *jobs, int njobs, cudaStream_t st);
+// One launch: setup of every circuit (challenges, points, eq(z_i, r_P)),
+// the eq tables and the product weights of the PROD waves.
+void launch_coins(const Globals *Gs, int ncirc, const EqJob *eqjobs, int neq, const SciDev *scis,
+                  const ProdWave *pw, int npw, cudaStream_t st);
 void launch_eval_layers(const Globals *Gs, const LayerEval *le, const Item *items, int nitems, cudaStream_t st);
 // maxblock: the largest block (entries) of any run layer or tail output in
 // the launch (<= 2048); it sizes the two shared-memory buffers.
@@ -259,7 +270,6 @@ void launch_eval_segs(const Globals *Gs, const EvalSeg *segs, const Item *items,
 void launch_check_canonical(const u64 *x, u64 n, u32 *status, cudaStream_t st);
 void launch_check_inputs(const Globals *Gs, const Item *items, int nitems, cudaStream_t st);
 void launch_build23(const Globals *Gs, const BuildItem *items, int nitems, cudaStream_t st);
-void launch_prep_prod(const Globals *Gs, const SciDev *scis, const ProdWave *waves, int nwaves, cudaStream_t st);
 // One persistent launch over `tasks` (ctr: two zeroed counters, left zeroed).
 void launch_waves(const Globals *Gs, const LineWaveDev *lw, const ProdWave *pw, const GenWave *gw, const Task *tasks,
                   int ntasks, u32 *ctr, cudaStream_t st);

@@ -140,6 +140,30 @@ static void plan_eval(vc_circuit *c)
                 S.tail_lo = (u32)j;
                 maxblock = std::max(maxblock, 1u << c->s[j]);
             }
+        // where the blocks start to fit one warp (<= 64 entries in and out to
+        // the end of the run / tail): from there warp 0 continues alone
+        {
+            auto fits_from = [&](int hi, int lo, u32 Bin, bool chunked) {
+                int from = lo - 1;  // none
+                u32 B = Bin;
+                std::vector<u32> bin(hi - lo + 2);
+                for (int j = hi; j >= lo; j--) {
+                    bin[hi - j] = B;
+                    const int sj = (int)c->s[j], snj = (int)c->s[j + 1];
+                    B = chunked ? (sj >= snj ? (B << (sj - snj)) : (B >> (snj - sj))) : (1u << sj);
+                    bin[hi - j + 1] = B;
+                }
+                for (int j = lo; j <= hi; j++) {  // the longest suffix of layers with blocks <= 64
+                    if (bin[hi - j] > 64 || bin[hi - j + 1] > 64) break;
+                    from = j;
+                }
+                return from;
+            };
+            S.warp_from = (u32)fits_from(i, i_lo, 1u << cl, true);
+            S.tail_warp_from = (S.tail_lo < S.i_lo) ? (u32)fits_from(i_lo - 2, (int)S.tail_lo,
+                                                                      1u << c->s[i_lo - 1], false)
+                                                    : S.tail_lo - 1;
+        }
         c->eval_steps.push_back((int)P.segs.size());
         c->seg_maxblock.push_back(maxblock);
         P.segs.push_back(S);
@@ -223,9 +247,9 @@ static size_t layout(vc_circuit *c, uintptr_t base)
         L.trp = take_eq(A, r, L.s);
         L.tr1 = take_eq(A, r + L.s, L.sn);
         L.tr2 = take_eq(A, r + L.s + L.sn, L.sn);
-        P.eqjobs.push_back({L.tz});
-        P.eqjobs.push_back({L.trp});
-        P.eqjobs.push_back({L.tr1});
+        P.eqjobs.push_back({L.tz, 0u, EQ_SRC_Z, 0u, i});
+        P.eqjobs.push_back({L.trp, 0u, EQ_SRC_CHAL, L.chal_off, 0u});
+        P.eqjobs.push_back({L.tr1, 0u, EQ_SRC_CHAL, L.chal_off + L.s, 0u});
         const bool tabs = needs_tables(L.kind);
         L.P2 = tabs ? A.take<u64>(S(i + 1)) : nullptr;
         L.P3 = tabs ? A.take<u64>(S(i + 1)) : nullptr;
@@ -240,14 +264,14 @@ static size_t layout(vc_circuit *c, uintptr_t base)
             L.by2_off = A.take<u32>(S(i + 1) + 1);
             L.by2_g = A.take<u32>(S(i));
             c->explicit_layers.push_back(i);
-            c->eq_verify.push_back({L.trp});
-            c->eq_verify.push_back({L.tr1});
-            c->eq_verify.push_back({L.tr2});
+            c->eq_verify.push_back({L.trp, 0u, EQ_SRC_CHAL, L.chal_off, 0u});
+            c->eq_verify.push_back({L.tr1, 0u, EQ_SRC_CHAL, L.chal_off + L.s, 0u});
+            c->eq_verify.push_back({L.tr2, 0u, EQ_SRC_CHAL, L.chal_off + L.s + L.sn, 0u});
         }
     }
     c->tzd = take_eq(A, G.pts + c->zd_off, c->s[d]);
-    c->eq_verify.push_back({c->tzd});
-    c->eq_verify.push_back({c->L[0].tz});
+    c->eq_verify.push_back({c->tzd, 0u, EQ_SRC_Z, 0u, d});
+    c->eq_verify.push_back({c->L[0].tz, 0u, EQ_SRC_Z, 0u, 0u});
 
     // Waves.  A wave is one launch's share of an instance: chunks of 2^nr
     // entries (2^nl coordinates for the line reduction).  A wave followed by a
@@ -521,6 +545,8 @@ bool plan_valid(const Plan &P)
     const u32 nc = (u32)P.ncirc;
     for (const Item &it : P.checks)
         if (it.wave >= nc) return false;
+    for (const EqJob &J : P.eqjobs)
+        if (J.circ >= nc || J.t.n > 30 || (J.src != EQ_SRC_CHAL && J.src != EQ_SRC_Z)) return false;
     for (const EvalSeg &S : P.segs)
         if (S.circ >= nc) return false;
     for (const LayerEval &E : P.levs)
@@ -709,7 +735,10 @@ void plan_merge(Plan &B, const std::vector<vc_circuit *> &cs)
         const u32 oseg = (u32)B.segs.size(), olev = (u32)B.levs.size(), olw = (u32)B.lw.size();
         const u32 osci = (u32)B.scis.size(), opw = (u32)B.pw.size(), ogw = (u32)B.gw.size();
         for (Item it : P.checks) B.checks.push_back({cj, it.chunk});
-        B.eqjobs.insert(B.eqjobs.end(), P.eqjobs.begin(), P.eqjobs.end());
+        for (EqJob J : P.eqjobs) {
+            J.circ = cj;
+            B.eqjobs.push_back(J);
+        }
         for (EvalSeg S : P.segs) {
             S.circ = cj;
             B.segs.push_back(S);
@@ -784,8 +813,16 @@ void enqueue_plan(Plan &P, cudaStream_t st)
     const Globals *Gs = P.d_G;
     // stage events become event-record nodes of the captured graph
     auto mark = [&](int k, int end, cudaStream_t s) {
-        if (P.stage_on) cudaEventRecordWithFlags(P.stage_ev[2 * k + end], s, cudaEventRecordExternal);
+        if (P.stage_on && P.stage_ev[2 * k + end])
+            cudaEventRecordWithFlags(P.stage_ev[2 * k + end], s, cudaEventRecordExternal);
     };
+    auto any_tasks = [](const std::vector<std::vector<Task>> &g, size_t from) {
+        for (size_t k = from; k < g.size(); k++)
+            if (!g[k].empty()) return true;
+        return false;
+    };
+    const bool has_wavesn = any_tasks(P.groupsA, 1), has_build = !P.builds.empty(),
+               has_tabwaves = any_tasks(P.groupsB, 0);
     const size_t nA = P.groupsA.size();
     auto waves = [&](std::vector<Task> &tasks, Task *d_tasks, size_t g) {
         launch_waves(Gs, P.d_lw, P.d_pw, P.d_gw, d_tasks, (int)tasks.size(), P.d_ctr + 2 * g, st);
@@ -795,12 +832,8 @@ void enqueue_plan(Plan &P, cudaStream_t st)
     // depend on the circuit's values), concurrently with the evaluation
     cudaEventRecord(P.ev_fork, st);
     cudaStreamWaitEvent(sa, P.ev_fork, 0);
-    mark(VC_STAGE_SETUP, 0, sa);
-    launch_setup(Gs, P.ncirc, sa);
-    mark(VC_STAGE_SETUP, 1, sa);
     mark(VC_STAGE_TABLES, 0, sa);
-    launch_eqtabs(P.d_eqjobs, (int)P.eqjobs.size(), sa);
-    launch_prep_prod(Gs, P.d_scis, P.d_pw, (int)P.pw.size(), sa);
+    launch_coins(Gs, P.ncirc, P.d_eqjobs, (int)P.eqjobs.size(), P.d_scis, P.d_pw, (int)P.pw.size(), sa);
     mark(VC_STAGE_TABLES, 1, sa);
     cudaEventRecord(P.ev_tables, sa);
     mark(VC_STAGE_EVAL, 0, st);
@@ -815,16 +848,22 @@ void enqueue_plan(Plan &P, cudaStream_t st)
     mark(VC_STAGE_WAVES, 0, st);
     if (nA) waves(P.groupsA[0], P.d_groupsA[0], 0);
     mark(VC_STAGE_WAVES, 1, st);
-    mark(VC_STAGE_WAVESN, 0, st);
-    for (size_t g = 1; g < nA; g++) waves(P.groupsA[g], P.d_groupsA[g], g);
-    mark(VC_STAGE_WAVESN, 1, st);
+    if (has_wavesn) {
+        mark(VC_STAGE_WAVESN, 0, st);
+        for (size_t g = 1; g < nA; g++) waves(P.groupsA[g], P.d_groupsA[g], g);
+        mark(VC_STAGE_WAVESN, 1, st);
+    }
     // wiring tables (they need q(0) of every line reduction), then their waves
-    mark(VC_STAGE_BUILD, 0, st);
-    launch_build23(Gs, P.d_builds, (int)P.builds.size(), st);
-    mark(VC_STAGE_BUILD, 1, st);
-    mark(VC_STAGE_TABWAVES, 0, st);
-    for (size_t g = 0; g < P.groupsB.size(); g++) waves(P.groupsB[g], P.d_groupsB[g], nA + g);
-    mark(VC_STAGE_TABWAVES, 1, st);
+    if (has_build) {
+        mark(VC_STAGE_BUILD, 0, st);
+        launch_build23(Gs, P.d_builds, (int)P.builds.size(), st);
+        mark(VC_STAGE_BUILD, 1, st);
+    }
+    if (has_tabwaves) {
+        mark(VC_STAGE_TABWAVES, 0, st);
+        for (size_t g = 0; g < P.groupsB.size(); g++) waves(P.groupsB[g], P.d_groupsB[g], nA + g);
+        mark(VC_STAGE_TABWAVES, 1, st);
+    }
     mark(VC_STAGE_FINAL, 0, st);
     launch_final(Gs, P.d_scis, P.d_rounds, (int)P.rounds.size(), P.d_outs, (int)P.outs.size(), st);
     mark(VC_STAGE_FINAL, 1, st);
@@ -858,9 +897,7 @@ static cudaError_t plan_launch(Plan &P, cudaStream_t st)
 // Kernel launches of one proof (the parameter write included).
 int count_launches(const Plan &P)
 {
-    int n = 2;  // parameters, setup
-    n += !P.eqjobs.empty();
-    n += !P.pw.empty();
+    int n = 2;  // parameters; coins, eq tables and product weights
     n += !P.checks.empty();
     for (size_t k = 0; k < P.seg_items.size(); k++) n += (!P.seg_items[k].empty()) + (!P.lev_items[k].empty());
     for (const auto &v : P.groupsA) n += !v.empty();
@@ -1188,8 +1225,7 @@ extern "C" vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t s
         if (e != cudaSuccess) return VC_ECUDA;
         cudaStream_t cs = c->P.cap;
         cudaMemsetAsync(c->d_result, 0, 8 * sizeof(u64), cs);
-        launch_setup(c->d_G, 1, cs);
-        launch_eqtabs(c->d_eq_verify, (int)c->eq_verify.size(), cs);
+        launch_coins(c->d_G, 1, c->d_eq_verify, (int)c->eq_verify.size(), nullptr, nullptr, 0, cs);
         launch_verify(c->G, c->Vd, c->tzd, c->L[0].tz, c->d_explicit_layers, (int)c->explicit_layers.size(), cs);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(cs, &g);
@@ -1215,9 +1251,6 @@ extern "C" vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t s
 extern "C" vc_status vc_circuit_set_stage_events(vc_circuit *c, void *const *events)
 {
     if (!c) return VC_EINVAL;
-    if (events)
-        for (int k = 0; k < 2 * VC_NUM_STAGES; k++)
-            if (!events[k]) return VC_EINVAL;
     DevGuard guard(c->device);
     if (c->P.exec) {  // the events are part of the captured graph: capture again
         cudaGraphExecDestroy(c->P.exec);
@@ -1244,8 +1277,8 @@ extern "C" vc_status vc_circuit_get_info(const vc_circuit *c, vc_circuit_info *i
     I.gates = gates;
     I.device_bytes = c->arena_bytes;
     I.prove_launches = (uint32_t)count_launches(c->P);
-    // parameters, setup, eq tables, input/output MLE, wiring (EXPLICIT only), checks
-    I.verify_launches = (uint32_t)(5 + (c->explicit_layers.empty() ? 0 : 1));
+    // parameters, coins and eq tables, input/output MLE, wiring (EXPLICIT only), checks
+    I.verify_launches = (uint32_t)(4 + (c->explicit_layers.empty() ? 0 : 1));
     I.wave_tasks = (uint32_t)(c->P.groupsA.empty() ? 0 : c->P.groupsA[0].size());
     *info = I;
     return VC_OK;

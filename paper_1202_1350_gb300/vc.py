@@ -44,8 +44,8 @@ class _Desc(ctypes.Structure):
                 ("in2", ctypes.POINTER(_u32p))]
 
 
-NUM_STAGES = 9
-STAGES = ("proof", "setup", "tables", "eval", "waves", "wavesn", "build", "tabwaves", "final")
+NUM_STAGES = 8
+STAGES = ("proof", "tables", "eval", "waves", "wavesn", "build", "tabwaves", "final")
 
 
 class CircuitInfo(ctypes.Structure):
@@ -286,17 +286,17 @@ def vc_verify(h, inputs, seed: int, transcript, stream=None, device: int = 0, ac
 
 
 def vc_circuit_set_stage_events(h, events):
-    """events: 2 * NUM_STAGES torch.cuda.Event objects (enable_timing=True):
-    start and end of every stage; or None."""
+    """events: 2 * NUM_STAGES entries, torch.cuda.Event (enable_timing=True)
+    or None to skip that mark: start and end of every stage; or None."""
     if events is None:
         _check(lib().vc_circuit_set_stage_events(h, None), "vc_circuit_set_stage_events")
         return
     if len(events) != 2 * NUM_STAGES:
         raise ValueError(f"need {2 * NUM_STAGES} events")
     for e in events:  # make sure each event exists on the device
-        if getattr(e, "cuda_event", 0) == 0:
+        if e is not None and getattr(e, "cuda_event", 0) == 0:
             e.record()
-    arr = (ctypes.c_void_p * (2 * NUM_STAGES))(*[e.cuda_event for e in events])
+    arr = (ctypes.c_void_p * (2 * NUM_STAGES))(*[None if e is None else e.cuda_event for e in events])
     _check(lib().vc_circuit_set_stage_events(h, arr), "vc_circuit_set_stage_events")
 
 
