@@ -368,6 +368,12 @@ def run_batch(local: int, reps: int = 5):
     from paper_1202_1350_gb300 import inputs as I
 
     jobs = I.batch_mix()
+    # the autotuner picks tile shapes per size class before the circuits are built
+    tuned = {}
+    for fam, logn, _ in jobs:
+        if (fam, logn) not in tuned:
+            w, k = circuits.by_name(fam, logn)
+            tuned[(fam, logn)] = vc.vc_autotune(w, k, local, reps=3)
     hs, xs, trs = [], [], []
     gates = 0
     for fam, logn, seed in jobs:
@@ -423,7 +429,8 @@ def run_batch(local: int, reps: int = 5):
             "launches_per_batch": info["prove_launches"],
             "one_at_a_time_proofs_per_s": n / (single_ms / 1000), "one_at_a_time_ms": single_ms,
             "speedup_vs_one_at_a_time": single_ms / batch_ms, "batched_equals_standalone": same,
-            "reps": reps}
+            "reps": reps,
+            "autotuned_tiles": {f"{f} 2^{n}": t[0] for (f, n), t in sorted(tuned.items())}}
 
 
 # ---- serving: Poisson arrivals into the proof server ---------------------------------------

@@ -185,6 +185,35 @@ typedef struct {
 
 vc_status vc_circuit_get_info(const vc_circuit *c, vc_circuit_info *info);
 
+/* Tile shapes of a circuit's launch plan: rounds folded by a first
+ * product-weighted / general sum-check chunk (<= 13 / <= 12), coordinates
+ * folded by a first line-reduction chunk (<= 13), and the smallest
+ * evaluation chunk (log2 entries, <= 11).  Any choice gives the same
+ * transcript; they only change speed. */
+typedef struct {
+    uint32_t pr_chunk_log;
+    uint32_t gn_chunk_log;
+    uint32_t line_chunk_log;
+    uint32_t eval_chunk_log;
+} vc_tile_config;
+
+/* Autotuner: times `reps` proofs of a circuit of shape `desc` (structured
+ * wirings only) with candidate tile shapes (coordinate descent from the
+ * current choice, on this device), records the fastest for the shape's size
+ * class (depth, widest layer, its wiring kind) and returns it with its mean
+ * proof time in ms.  Circuits created later in this process with a shape of
+ * that class use the recorded tiles (circuits that exist keep theirs).
+ * Allocates and frees scratch; synchronous. */
+vc_status vc_autotune(const vc_circuit_desc *desc, int device, int reps, vc_tile_config *best, double *best_ms);
+
+/* vc_circuit_create with explicit tile shapes (VC_EINVAL outside the
+ * bounds above). */
+vc_status vc_circuit_create_tiles(const vc_circuit_desc *desc, int device, const vc_tile_config *tiles,
+                                  vc_circuit **out);
+
+/* The tile shapes a circuit was planned with. */
+vc_status vc_circuit_get_tiles(const vc_circuit *c, vc_tile_config *tiles);
+
 /* Batches (Sec. 6.2.3 runs many independent proofs; here they share launches).
  * A batch is a fixed set of distinct circuit handles on one device whose
  * proofs run as ONE set of merged launches: every evaluation step, line wave

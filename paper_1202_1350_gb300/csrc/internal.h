@@ -15,6 +15,16 @@ constexpr u32 GN_CHUNK_LOG = GN_M + WV_LOG;  // rounds of one GEN chunk (2^GN_M 
 constexpr u32 LN_CHUNK0_LOG = 6 + WV_LOG;    // coordinates of a first line-wave chunk (64 entries per thread)
 constexpr u32 LN_CHUNKW_LOG = WV_LOG;        // coordinates of a later line-wave chunk (one polynomial per thread)
 
+// Tile shapes of a circuit's plan (the autotuner's knobs): rounds folded
+// by a first PROD / GEN chunk, coordinates folded by a first line-wave chunk,
+// and the smallest evaluation chunk (log2 entries).
+struct PlanConfig {
+    u32 pr_chunk = PR_CHUNK_LOG;
+    u32 gn_chunk = GN_CHUNK_LOG;
+    u32 ln_chunk0 = LN_CHUNK0_LOG;
+    u32 ev_chunk = 10;
+};
+
 // Which layers' phase-2/3 tables are built by k_build23 (the rest are formed
 // on the fly or never stored).
 inline bool needs_tables(u32 kind) { return kind != W_SQUARE && kind != W_TREE; }
@@ -113,6 +123,7 @@ struct Plan {
 
 struct vc_circuit {
     int device = 0;
+    PlanConfig cfg;
     u32 d = 0;
     std::vector<u32> s, kind, has_add;
     std::vector<std::vector<unsigned char>> ex_type;
@@ -166,7 +177,8 @@ void init_device_once(int device);
 // Host-side circuit construction: validation, offsets and the single-circuit
 // plan, sized but not allocated (c->arena_bytes set).  circuit_allocate then
 // takes the device memory and uploads everything.
-vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **out);
+vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **out,
+                          const PlanConfig *cfg = nullptr);
 vc_status circuit_allocate(vc_circuit *c);
 void circuit_free(vc_circuit *c);
 

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -100,7 +101,7 @@ static void plan_eval(vc_circuit *c)
         // chunks of 2^cl entries of the run's input layer: about 1024 CTAs for
         // wide layers, blocks of at most 2^11 entries
         const int s_in = (int)c->s[i + 1];
-        int cl = std::min(s_in, std::max(10, s_in - 10));
+        int cl = std::min(s_in, std::max((int)c->cfg.ev_chunk, s_in - 10));
         cl = std::min(cl, 11);
         int i_lo = i + 1;
         u32 maxblock = 1;
@@ -293,7 +294,7 @@ static size_t layout(vc_circuit *c, uintptr_t base)
         const u64 *in = c->V[i + 1];
         bool tail = false;
         for (u32 w = 0;; w++) {
-            const u32 cap = (w == 0) ? LN_CHUNK0_LOG : LN_CHUNKW_LOG;
+            const u32 cap = (w == 0) ? c->cfg.ln_chunk0 : LN_CHUNKW_LOG;
             const u32 nl = std::min(cap, n - l0);
             LineWaveDev W{};
             W.circ = 0;
@@ -362,7 +363,7 @@ static size_t layout(vc_circuit *c, uintptr_t base)
             }
             P.scis.push_back(Sc);
             const u32 nv = prod ? 2 : 3;
-            const u32 C = prod ? PR_CHUNK_LOG : GN_CHUNK_LOG;
+            const u32 C = prod ? c->cfg.pr_chunk : c->cfg.gn_chunk;
             const u32 M = prod ? (u32)PR_M : (u32)GN_M;
             const bool tab = Sc.kind == PK_GEN_TAB;
             const bool tabB = tab && L.has_add;
@@ -910,13 +911,43 @@ int count_launches(const Plan &P)
 // Circuits
 // ---------------------------------------------------------------------------------------
 
-vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **out)
+// ---- tile-shape autotuning -------------------------------------------------------
+// Size class of a circuit: depth, widest layer, and that layer's wiring kind.
+static std::vector<u32> size_class(const vc_circuit_desc *desc)
+{
+    u32 smax = 0, kmax = 0;
+    for (u32 i = 0; i < desc->n_layers; i++)
+        if (desc->log_width[i] >= smax) {
+            smax = desc->log_width[i];
+            kmax = desc->wiring[i];
+        }
+    return {desc->n_layers, smax, kmax};
+}
+
+static std::mutex g_tune_mu;
+static std::map<std::vector<u32>, PlanConfig> g_tuned;  // size class -> fastest measured tile shapes
+
+static bool config_ok(const PlanConfig &f)
+{
+    return f.pr_chunk >= 1 && f.pr_chunk <= PR_CHUNK_LOG && f.gn_chunk >= 1 && f.gn_chunk <= GN_CHUNK_LOG &&
+           f.ln_chunk0 >= 1 && f.ln_chunk0 <= LN_CHUNK0_LOG && f.ev_chunk >= 1 && f.ev_chunk <= 11;
+}
+
+vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **out, const PlanConfig *cfg)
 {
     if (!desc || !out || desc->n_layers < 1 || desc->n_layers > 4096 || !desc->log_width || !desc->wiring)
         return VC_EINVAL;
     *out = nullptr;
+    if (cfg && !config_ok(*cfg)) return VC_EINVAL;
     vc_circuit *c = new (std::nothrow) vc_circuit();
     if (!c) return VC_ENOMEM;
+    if (cfg) {
+        c->cfg = *cfg;
+    } else {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tuned.find(size_class(desc));
+        if (it != g_tuned.end()) c->cfg = it->second;
+    }
     c->device = device;
     c->d = desc->n_layers;
     const u32 d = c->d;
@@ -1281,6 +1312,121 @@ extern "C" vc_status vc_circuit_get_info(const vc_circuit *c, vc_circuit_info *i
     I.verify_launches = (uint32_t)(4 + (c->explicit_layers.empty() ? 0 : 1));
     I.wave_tasks = (uint32_t)(c->P.groupsA.empty() ? 0 : c->P.groupsA[0].size());
     *info = I;
+    return VC_OK;
+}
+
+// Mean time of `reps` proofs of a circuit of shape `desc` built with tiles `f`
+// (inputs all zero, device buffers, after two warm-up proofs).
+static vc_status time_config(const vc_circuit_desc *desc, int device, const PlanConfig &f, int reps, u64 *din,
+                             u64 *dtr, cudaStream_t st, double *ms)
+{
+    vc_circuit *c = nullptr;
+    vc_status s = circuit_prepare(desc, device, &c, &f);
+    if (s != VC_OK) return s;
+    s = circuit_allocate(c);
+    if (s == VC_OK) {
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (int k = 0; k < 2 && s == VC_OK; k++) s = vc_prove(c, din, 1 + k, dtr, st);
+        cudaEventRecord(e0, st);
+        for (int k = 0; k < reps && s == VC_OK; k++) s = vc_prove(c, din, 10 + k, dtr, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess && s == VC_OK) s = VC_ECUDA;
+        float t = 0;
+        cudaEventElapsedTime(&t, e0, e1);
+        *ms = t / reps;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (s == VC_OK) s = read_status_and_clear(c, st);
+    }
+    cudaStreamSynchronize(st);
+    circuit_free(c);
+    return s;
+}
+
+extern "C" vc_status vc_autotune(const vc_circuit_desc *desc, int device, int reps, vc_tile_config *best,
+                                 double *best_ms)
+{
+    if (!desc || !desc->log_width || !desc->wiring || desc->n_layers < 1 || reps < 1) return VC_EINVAL;
+    for (u32 i = 0; i < desc->n_layers; i++)
+        if (desc->wiring[i] == W_EXPLICIT) return VC_EINVAL;  // tuned per structured shape
+    DevGuard guard(device);
+    init_device_once(device);
+    const u64 nin = u64(1) << desc->log_width[desc->n_layers];
+    vc_circuit *probe = nullptr;
+    vc_status s = circuit_prepare(desc, device, &probe, nullptr);
+    if (s != VC_OK) return s;
+    const u64 trl = probe->tr_len;
+    PlanConfig cur = probe->cfg;
+    circuit_free(probe);
+    u64 *din = nullptr, *dtr = nullptr;
+    cudaStream_t st = nullptr;
+    if (cudaMalloc(&din, nin * sizeof(u64)) != cudaSuccess || cudaMalloc(&dtr, trl * sizeof(u64)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        if (din) cudaFree(din);
+        if (dtr) cudaFree(dtr);
+        return VC_ENOMEM;
+    }
+    cudaMemsetAsync(din, 0, nin * sizeof(u64), st);
+    double cur_ms = 0;
+    s = time_config(desc, device, cur, reps, din, dtr, st, &cur_ms);
+    // coordinate descent over the four knobs
+    const u32 cand[4][4] = {{11, 12, 13, 0}, {10, 11, 12, 0}, {11, 12, 13, 0}, {8, 9, 10, 11}};
+    for (int knob = 0; knob < 4 && s == VC_OK; knob++)
+        for (int j = 0; j < 4 && cand[knob][j]; j++) {
+            PlanConfig f = cur;
+            u32 *field = knob == 0 ? &f.pr_chunk : knob == 1 ? &f.gn_chunk : knob == 2 ? &f.ln_chunk0 : &f.ev_chunk;
+            if (*field == cand[knob][j]) continue;
+            *field = cand[knob][j];
+            double ms = 0;
+            s = time_config(desc, device, f, reps, din, dtr, st, &ms);
+            if (s == VC_OK && ms < 0.98 * cur_ms) {
+                cur = f;
+                cur_ms = ms;
+            }
+        }
+    cudaFree(din);
+    cudaFree(dtr);
+    cudaStreamDestroy(st);
+    if (s != VC_OK) return s;
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tuned[size_class(desc)] = cur;
+    }
+    if (best) *best = {cur.pr_chunk, cur.gn_chunk, cur.ln_chunk0, cur.ev_chunk};
+    if (best_ms) *best_ms = cur_ms;
+    return VC_OK;
+}
+
+extern "C" vc_status vc_circuit_create_tiles(const vc_circuit_desc *desc, int device, const vc_tile_config *tiles,
+                                            vc_circuit **out)
+{
+    if (!out || !tiles) return VC_EINVAL;
+    *out = nullptr;
+    PlanConfig f;
+    f.pr_chunk = tiles->pr_chunk_log;
+    f.gn_chunk = tiles->gn_chunk_log;
+    f.ln_chunk0 = tiles->line_chunk_log;
+    f.ev_chunk = tiles->eval_chunk_log;
+    vc_circuit *c = nullptr;
+    vc_status st = circuit_prepare(desc, device, &c, &f);
+    if (st != VC_OK) return st;
+    st = circuit_allocate(c);
+    if (st != VC_OK) {
+        DevGuard guard(device);
+        circuit_free(c);
+        return st;
+    }
+    *out = c;
+    return VC_OK;
+}
+
+extern "C" vc_status vc_circuit_get_tiles(const vc_circuit *c, vc_tile_config *tiles)
+{
+    if (!c || !tiles) return VC_EINVAL;
+    *tiles = {c->cfg.pr_chunk, c->cfg.gn_chunk, c->cfg.ln_chunk0, c->cfg.ev_chunk};
     return VC_OK;
 }
 

@@ -78,6 +78,11 @@ class ServerStats(ctypes.Structure):
                 ("pending", ctypes.c_uint64), ("max_jobs_in_flight", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
+class TileConfig(ctypes.Structure):
+    _fields_ = [("pr_chunk_log", ctypes.c_uint32), ("gn_chunk_log", ctypes.c_uint32),
+                ("line_chunk_log", ctypes.c_uint32), ("eval_chunk_log", ctypes.c_uint32)]
+
+
 _lock = threading.Lock()
 _lib = None
 _shapes = {}  # handle -> (inputs, outputs, transcript length), for size checks
@@ -121,6 +126,11 @@ def lib():
             L.vc_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(JobInfo)]
             L.vc_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(JobInfo)]
             L.vc_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+            L.vc_autotune.argtypes = [ctypes.POINTER(_Desc), ctypes.c_int, ctypes.c_int, ctypes.POINTER(TileConfig),
+                                      ctypes.POINTER(ctypes.c_double)]
+            L.vc_circuit_create_tiles.argtypes = [ctypes.POINTER(_Desc), ctypes.c_int, ctypes.POINTER(TileConfig),
+                                                  ctypes.POINTER(vp)]
+            L.vc_circuit_get_tiles.argtypes = [vp, ctypes.POINTER(TileConfig)]
             L.vc_field_mul.argtypes = [vp, vp, vp, ctypes.c_uint64, vp]
             L.vc_field_mul_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                             ctypes.POINTER(ctypes.c_double)]
@@ -135,7 +145,8 @@ def lib():
                          "vc_field_mul", "vc_field_mul_rate", "vc_circuit_set_stage_events",
                          "vc_circuit_get_info", "vc_batch_create", "vc_batch_destroy", "vc_batch_prove",
                          "vc_batch_sync", "vc_batch_get_info", "vc_server_create", "vc_server_destroy",
-                         "vc_server_submit", "vc_server_poll", "vc_server_wait", "vc_server_get_stats"):
+                         "vc_server_submit", "vc_server_poll", "vc_server_wait", "vc_server_get_stats",
+                         "vc_autotune", "vc_circuit_create_tiles", "vc_circuit_get_tiles"):
                 getattr(L, name).restype = st
             _lib = L
     return _lib
@@ -418,6 +429,41 @@ def vc_server_get_stats(s) -> dict:
     st = ServerStats()
     _check(lib().vc_server_get_stats(s, ctypes.byref(st)), "vc_server_get_stats")
     return {name: getattr(st, name) for name, _ in ServerStats._fields_ if name != "pad"}
+
+
+def _tiles(t: TileConfig) -> dict:
+    return {name: getattr(t, name) for name, _ in TileConfig._fields_}
+
+
+def vc_autotune(log_width, wiring, device: int = 0, reps: int = 5):
+    """Time candidate tile shapes for this circuit shape; the fastest is
+    recorded for its size class and used by later vc_circuit_create calls.
+    Returns (tiles dict, mean proof ms)."""
+    desc, keep = _desc_struct(log_width, wiring)
+    best = TileConfig()
+    ms = ctypes.c_double(0)
+    _check(lib().vc_autotune(ctypes.byref(desc), device, reps, ctypes.byref(best), ctypes.byref(ms)), "vc_autotune")
+    del keep
+    return _tiles(best), ms.value
+
+
+def vc_circuit_create_tiles(log_width, wiring, tiles: dict, device: int = 0):
+    desc, keep = _desc_struct(log_width, wiring)
+    t = TileConfig(tiles["pr_chunk_log"], tiles["gn_chunk_log"], tiles["line_chunk_log"], tiles["eval_chunk_log"])
+    h = ctypes.c_void_p()
+    _check(lib().vc_circuit_create_tiles(ctypes.byref(desc), device, ctypes.byref(t), ctypes.byref(h)),
+           "vc_circuit_create_tiles")
+    del keep
+    n = ctypes.c_uint64()
+    _check(lib().vc_transcript_len(h, ctypes.byref(n)), "vc_transcript_len")
+    _shapes[h.value] = (1 << int(log_width[-1]), 1 << int(log_width[0]), n.value)
+    return h.value
+
+
+def vc_circuit_get_tiles(h) -> dict:
+    t = TileConfig()
+    _check(lib().vc_circuit_get_tiles(h, ctypes.byref(t)), "vc_circuit_get_tiles")
+    return _tiles(t)
 
 
 def vc_field_mul(a, b, out, stream=None, device: int = 0):

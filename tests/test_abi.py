@@ -81,3 +81,18 @@ def test_transcript_len_matches_library(libvc, family, logn):
     w, k = circuits.by_name(family, logn)
     c = oracle.Circuit(w, k)
     assert circuits.transcript_len(w) == len(c.prove(np.zeros(1 << w[-1], np.uint64), 1))
+
+
+def test_tile_arguments_rejected_without_device(libvc):
+    w, k = circuits.f2(6)
+    for bad in ({"pr_chunk_log": 14, "gn_chunk_log": 12, "line_chunk_log": 13, "eval_chunk_log": 10},
+                {"pr_chunk_log": 13, "gn_chunk_log": 13, "line_chunk_log": 13, "eval_chunk_log": 10},
+                {"pr_chunk_log": 13, "gn_chunk_log": 12, "line_chunk_log": 14, "eval_chunk_log": 10},
+                {"pr_chunk_log": 13, "gn_chunk_log": 12, "line_chunk_log": 13, "eval_chunk_log": 12},
+                {"pr_chunk_log": 0, "gn_chunk_log": 12, "line_chunk_log": 13, "eval_chunk_log": 10}):
+        with pytest.raises(vc.VcError) as e:
+            vc.vc_circuit_create_tiles(w, k, bad)
+        assert e.value.status == vc.VC_EINVAL
+    with pytest.raises(vc.VcError) as e:
+        vc.vc_autotune([1, 1], [vc.EXPLICIT])
+    assert e.value.status == vc.VC_EINVAL
