@@ -422,3 +422,20 @@ def test_noncanonical_input_rejected_by_evaluate():
     c = oracle.Circuit(*oracle.f2_layers(2))
     with pytest.raises(ValueError):
         c.evaluate([1, 2, P, 3])
+
+
+def test_f2_circuit_size_matches_the_paper_table():
+    """The paper's results table prints the F2 circuit at 8.4 million input
+    entries as 25.2 million gates (inputs counted).  The oracle's F2 layering
+    (a squaring layer, then a binary addition tree) at n = 2^23 inputs has
+    n + n + (n - 1) gates, which rounds to the printed figures."""
+    import os
+    rows = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "paper_circuit_sizes.txt")):
+        if line.strip() and not line.startswith("#"):
+            name, inputs, gates = line.split()
+            rows[name] = (float(inputs), float(gates))
+    inputs, gates = rows["F2"]
+    widths, kinds = oracle.f2_layers(23)
+    assert round((1 << widths[-1]) / 1e5) == round(inputs / 1e5)
+    assert round(sum(1 << s for s in widths) / 1e5) == round(gates / 1e5)
