@@ -92,38 +92,59 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# ---- algorithmic work of the dominant launch ----------------------------------------------
+# ---- work of the dominant launch ---------------------------------------------------------
 
-def wave_work(widths, kinds):
-    """Field multiplications of the first persistent wave launch, counted from
-    the method (the folding prover), for circuits of SQUARE and TREE layers,
-    whose every sum-check and line reduction runs in that launch:
-      * product-weighted instance over n variables (phase 1 of every layer,
-        phase 3 of SQUARE and TREE layers): per pair of entries of every round
-        h(0), h(1) and the fold of V: 3 (2^n - 1);
-      * general instance (phase 2): per pair P V at t = 0, 1, 2 and the folds
-        of P and V (and B for TREE): 5 (6) (2^n - 1), plus forming P (and B)
-        from eq(r_P, .): 2 per entry (SQUARE) or per even entry (TREE);
-      * line reduction over n = s_{i+1} coordinates: folding coordinate j turns
-        pairs of degree-j polynomials into one of degree j + 1 at 2 (j + 1)
-        multiplications: sum_j 2^(n-j-1) 2 (j + 1).
-    Bytes: every V entry of every instance and line reduction read once."""
+def algorithmic_work(widths, kinds):
+    """Field multiplications the folding prover needs for what the wave launch
+    computes, per layer i with S_i = 2^{s_i} gates over S_{i+1} = 2^{s_{i+1}}:
+      phase 1 (three values and two folds per pair, over halving rounds)  5 S_i
+      phase-2/3 P and B tables (formed from eq(r_P, .) and the wiring)     2 S_i
+      phases 2 and 3 (A V, B, M V at t = 0, 1, 2 and four folds per pair) 20 S_{i+1}
+      line polynomial (coefficient-form folding)                           4 S_{i+1}
+    i.e. 7 S_i + 24 S_{i+1}.  (The eq tables themselves are built by the coin
+    launch and not counted here.)  Bytes: the value tables the launch reads,
+    each once: V_i for phase 1, V_{i+1} for phases 2 and 3 and the line,
+    8 (S_i + 3 S_{i+1}) per layer."""
     mul = 0
     byts = 0
+    for i in range(len(kinds)):
+        S, Sn = 1 << widths[i], 1 << widths[i + 1]
+        mul += 7 * S + 24 * Sn
+        byts += 8 * (S + 3 * Sn)
+    return mul, byts
+
+
+def executed_work(widths, kinds, first_wave_log=12):
+    """Field multiplications the wave launch actually performs on circuits of
+    SQUARE and TREE layers (products of W values, 64-bit or in 31-bit limbs):
+      * product-weighted instance over n variables (phase 1 of every layer,
+        phase 3 of SQUARE and TREE layers; P stays implicit): per pair of
+        entries of every round h(0), h(1) and the fold of V: 3 (2^n - 1);
+      * general instance (phase 2): per pair P V at t = 0, 1, 2 and the folds
+        of P and V (and B for TREE): 5 (6) per pair; SQUARE forms P = eq V at
+        2 per entry; TREE with a first wave in registers (n > 7) does its
+        round 0 at 5 per pair (eq(r_P, g), w (v0 + v1), w (3 v1 - v0), the V
+        fold and B = w v1), smaller TREE instances form P and B at 2 per gate;
+      * line reduction over n = s_{i+1} coordinates: folding coordinate j turns
+        pairs of degree-j polynomials into one of degree j + 1 at 2 (j + 1)
+        multiplications: sum_j 2^(n-j-1) 2 (j + 1)."""
+    mul = 0
     for i, k in enumerate(kinds):
         si, sn = widths[i], widths[i + 1]
         assert k in (0, 1), "counted for SQUARE and TREE layers"
         for ph, n in ((1, si), (2, sn), (3, sn)):
             if n == 0:
                 continue
-            if ph == 2:
-                mul += (6 if k == 1 else 5) * ((1 << n) - 1) + (2 if k == 0 else 1) * (1 << n)
+            if ph == 2 and k == 0:
+                mul += 5 * ((1 << n) - 1) + 2 * (1 << n)
+            elif ph == 2 and min(n, first_wave_log) > 7:
+                mul += 5 * (1 << (n - 1)) + 6 * ((1 << (n - 1)) - 1)
+            elif ph == 2:
+                mul += 6 * ((1 << n) - 1) + (1 << n)
             else:
                 mul += 3 * ((1 << n) - 1)
-            byts += 8 * (1 << n)
         mul += sum((1 << (sn - j - 1)) * 2 * (j + 1) for j in range(sn))
-        byts += 8 * (1 << sn)
-    return mul, byts
+    return mul
 
 
 # DRAM bytes (read + write) of one k_waves launch on this workload, from an ncu
@@ -322,7 +343,8 @@ def run_ours(args):
     # roofline of the dominant kernel: the first persistent wave launch,
     # which runs every sum-check round and line reduction of the F2 circuit
     sc0_ms = statistics.mean(wave_ms)
-    mul, byts = wave_work(widths, kinds)
+    mul, byts = algorithmic_work(widths, kinds)
+    executed = executed_work(widths, kinds, vc.vc_circuit_get_tiles(h)["gn_chunk_log"])
     rate = vc.vc_field_mul_rate(local, 2, 1 << 12)
     achieved = mul / (sc0_ms / 1000)
     stages = {name: round(statistics.mean(v), 4) for name, v in stage_ms.items()}
@@ -343,7 +365,9 @@ def run_ours(args):
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "peak_source": "measured on this GPU: vc_field_mul_rate variant 2, the kernel's own "
                                     "pair step (2 multiply-adds + 1 lazy fold) over 1216x256 threads",
-                     "algorithmic_mulmods": mul, "algorithmic_bytes": byts, "kernel_ms": sc0_ms,
+                     "algorithmic_mulmods": mul, "algorithmic_rule": "7 S_i + 24 S_{i+1} per layer (folding prover)",
+                     "executed_mulmods": executed, "executed_frac": executed / (sc0_ms / 1000) / rate,
+                     "algorithmic_bytes": byts, "kernel_ms": sc0_ms,
                      "bytes_frac_of_hbm": (byts / (sc0_ms / 1000)) / (measured_peaks().get("hbm_gbs", 6787.9) * 1e9)},
         "stage_ms": stages,
         "gpu_launches": launches,

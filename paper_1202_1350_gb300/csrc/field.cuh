@@ -147,10 +147,6 @@ __device__ __forceinline__ u64 wmul(u64 x, u64 y)
     return acc_red(a);
 }
 
-// 2 a1 - a0 for W values, result in W (the value at t = 2 of the line
-// through (0, a0) and (1, a1)); 2 a1 + 2p - a0 < 2^63 + 16.
-__device__ __forceinline__ u64 wext2(u64 a1, u64 a0) { return wred(2 * a1 + (2 * FP_P) - a0); }
-
 // u0 + r (u1 - u0) for u0, u1 in W and canonical r given as 31/30-bit limbs
 // r = r1 2^31 + r0.  With d = u1 - u0 + 2p in (0, 2^63) split as d1 2^31 + d0:
 //   r d + u0 = r1 d1 2^62 + (r0 d1 + r1 d0) 2^31 + (r0 d0 + u0)

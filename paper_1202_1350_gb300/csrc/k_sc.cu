@@ -15,8 +15,11 @@
 //    fold.  Used for phase 1 of every layer (P = eq(z_i, .)) and for phase 3 of
 //    TREE and SQUARE layers.
 //  * general (GEN): P, V, B are tables folded every round; the message needs
-//    P(t)V(t) at t = 0, 1, 2.  The first wave builds P and B from the wiring on
-//    the fly (SQUARE, TREE phase 2) or reads tables built by k_build23.
+//    P(t)V(t) + B(t) at t = 0, 1, 2.  Chunks sum the values at 0 and 1 and the
+//    leading coefficient (P1 - P0)(V1 - V0) of each pair, which shares its
+//    differences with the folds; k_final turns the three sums into the value
+//    at 2.  The first wave builds P and B from the wiring on the fly (SQUARE,
+//    TREE phase 2) or reads tables built by k_build23.
 //
 // Arithmetic is lazy: table values stay in W = [0, 2^61 + 8), products
 // accumulate exactly in 128 bits and are reduced once per round per thread;
@@ -119,6 +122,13 @@ union WaveSmem {
     GenSmem gen;
     LineSmem line;
 };
+
+// Load of a wave's input.  A first wave's input (layer values, or tables built
+// by an earlier launch) is read-only for the whole launch and goes through
+// L1, where the prefetch of the next run lands; a later wave's input is
+// written by other CTAs of this launch and is read through L2.
+__device__ __forceinline__ ulonglong2 ld_in(const ulonglong2 *p, bool ext) { return ext ? __ldg(p) : __ldcg(p); }
+__device__ __forceinline__ u64 ld_in(const u64 *p, bool ext) { return ext ? __ldg(p) : __ldcg(p); }
 
 // Bring the line holding p into L1 ahead of its load (no register cost).
 __device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
@@ -236,7 +246,7 @@ __device__ __forceinline__ u64 prod_run16(u64 (&u)[16], u32 sub, u32 e, const Pr
 
 // In-register rounds for e in 4..6: runs of 16, then rounds 4 and 5 on the
 // runs' folded values.
-__device__ __forceinline__ u64 prod_regs_runs(const u64 *src, u32 e, const ProdSmem &sm, u64 (&h)[12])
+__device__ __forceinline__ u64 prod_regs_runs(const u64 *src, u32 e, bool ext, const ProdSmem &sm, u64 (&h)[12])
 {
     const u32 nruns = 1u << (e - 4);
     const u32 q4 = (1u << e) - (1u << (e - 4)), q5 = (1u << e) - 2;
@@ -249,7 +259,7 @@ __device__ __forceinline__ u64 prod_regs_runs(const u64 *src, u32 e, const ProdS
         const ulonglong2 *sv = reinterpret_cast<const ulonglong2 *>(src + sub * PR_SUB);
 #pragma unroll
         for (int q = 0; q < 8; q++) {
-            const ulonglong2 t = __ldcg(sv + q);
+            const ulonglong2 t = ld_in(sv + q, ext);
             u[2 * q] = t.x;
             u[2 * q + 1] = t.y;
         }
@@ -306,7 +316,7 @@ __device__ void prod_chunk(const Globals &G, const ProdWave &W, u32 chunk, ProdS
         for (int i = 0; i < 12; i++) h[i] = 0;
         if (tid < na) {
             const u64 *src = W.in + base + ((u64)tid << e);
-            uv = prod_regs_runs(src, e, sm, h);
+            uv = prod_regs_runs(src, e, W.r0 == 0, sm, h);
             const u64 T = sm.E[tid];  // E_{e-1}(tid): weight of the chunk bits above the thread's run
 #pragma unroll
             for (int i = 0; i < 12; i++) h[i] = wmul(T, h[i]);
@@ -317,7 +327,7 @@ __device__ void prod_chunk(const Globals &G, const ProdWave &W, u32 chunk, ProdS
         const u64 s = warp_sum16(h16);
         if ((lane & 1) == 0 && (lane >> 1) < 2 * e) sm.w[warp][lane >> 1] = s;
     } else if (tid < na) {
-        uv = __ldcg(W.in + base + tid);
+        uv = ld_in(W.in + base + tid, W.r0 == 0);
     }
     prod_cross(uv, e, tid, na, nr, sm, eoff0);
     __syncthreads();
@@ -331,52 +341,24 @@ __device__ void prod_chunk(const Globals &G, const ProdWave &W, u32 chunk, ProdS
 
 // ---- GEN ------------------------------------------------------------------------
 
-// P and B of the first wave for the on-the-fly kinds, for N consecutive
-// entries at x0 (x0 even) whose V values are v[].
+// N consecutive entries of a GEN wave's P, V, B tables at x0 (tables built
+// by k_build23, or the previous wave's outputs; the first waves of SQUARE and
+// TREE phase 2 form P and B themselves: sq2_run, tree2_run).
 template <int N>
-__device__ __forceinline__ void gen_source(const Globals &G, const GenWave &W, u64 x0, const u64 (&v)[N],
-                                           u64 (&p)[N], u64 (&b)[N])
+__device__ __forceinline__ void gen_load(const GenWave &W, u64 x0, bool hasB, u64 (&p)[N], u64 (&v)[N], u64 (&b)[N])
 {
-    const LayerDev &L = G.layers[W.layer];
-    if (W.src == GS_SQ2) {
-#pragma unroll
-        for (int q = 0; q < N; q++) {
-            p[q] = wmul(eq_at(L.trp, x0 + q), v[q]);
-            b[q] = 0;
-        }
-    } else {  // GS_TREE2
-#pragma unroll
-        for (int q = 0; q < N; q += 2) {
-            const u64 w = eq_at(L.trp, (x0 + q) >> 1);
-            p[q] = w;
-            b[q] = wmul(w, v[q + 1]);
-            p[q + 1] = 0;
-            b[q + 1] = 0;
-        }
-    }
-}
-
-// N consecutive entries of a GEN wave's tables at x0 (first wave: P, B formed
-// from the wiring; later waves: read).
-template <int N>
-__device__ __forceinline__ void gen_load(const Globals &G, const GenWave &W, u64 x0, bool hasB, u64 (&p)[N],
-                                         u64 (&v)[N], u64 (&b)[N])
-{
+    const bool ext = W.r0 == 0;
     const ulonglong2 *sv = reinterpret_cast<const ulonglong2 *>(W.inV + x0);
 #pragma unroll
     for (int q = 0; q < N / 2; q++) {
-        const ulonglong2 t = __ldcg(sv + q);
+        const ulonglong2 t = ld_in(sv + q, ext);
         v[2 * q] = t.x;
         v[2 * q + 1] = t.y;
-    }
-    if (W.src != GS_NONE) {
-        gen_source<N>(G, W, x0, v, p, b);
-        return;
     }
     const ulonglong2 *sp = reinterpret_cast<const ulonglong2 *>(W.inP + x0);
 #pragma unroll
     for (int q = 0; q < N / 2; q++) {
-        const ulonglong2 t = __ldcg(sp + q);
+        const ulonglong2 t = ld_in(sp + q, ext);
         p[2 * q] = t.x;
         p[2 * q + 1] = t.y;
     }
@@ -384,7 +366,7 @@ __device__ __forceinline__ void gen_load(const Globals &G, const GenWave &W, u64
         const ulonglong2 *sb = reinterpret_cast<const ulonglong2 *>(W.inB + x0);
 #pragma unroll
         for (int q = 0; q < N / 2; q++) {
-            const ulonglong2 t = __ldcg(sb + q);
+            const ulonglong2 t = ld_in(sb + q, ext);
             b[2 * q] = t.x;
             b[2 * q + 1] = t.y;
         }
@@ -394,16 +376,20 @@ __device__ __forceinline__ void gen_load(const Globals &G, const GenWave &W, u64
     }
 }
 
-// One general pair: message contributions at t = 0, 1, 2 and the folds.
+// One general pair: the message's values at t = 0, 1 (c0, c1) and its
+// leading coefficient c2 = (P1 - P0)(V1 - V0), from which the value at 2 is
+// 2 c1 - c0 + 2 c2 (B is linear in t); then the folds, which share the
+// differences P1 - P0, V1 - V0, B1 - B0 (lazy, below 2^62.6).
 __device__ __forceinline__ void gen_pair(u64 p0, u64 p1, u64 v0, u64 v1, u64 b0, u64 b1, u32 rr0, u32 rr1,
                                          u64 &c0, u64 &c1, u64 &c2, u64 &pn, u64 &vn, u64 &bn)
 {
+    const u64 dp = p1 + (2 * FP_P) - p0, dv = v1 + (2 * FP_P) - v0, db = b1 + (2 * FP_P) - b0;
     c0 = wred(wmul(p0, v0) + b0);
     c1 = wred(wmul(p1, v1) + b1);
-    c2 = wred(wmul(wext2(p1, p0), wext2(v1, v0)) + wext2(b1, b0));
-    pn = wfold(p0, p1, rr0, rr1);
-    vn = wfold(v0, v1, rr0, rr1);
-    bn = wfold(b0, b1, rr0, rr1);
+    c2 = wmul(wred(dp), wred(dv));
+    pn = wlin1(p0, dp, rr0, rr1);
+    vn = wlin1(v0, dv, rr0, rr1);
+    bn = wlin1(b0, db, rr0, rr1);
 }
 
 // Round k on two folded triples held by one thread, summed into the
@@ -436,20 +422,92 @@ __device__ __forceinline__ void gen_regs(u64 (&p)[1 << R], u64 (&v)[1 << R], u64
         for (int q = 0; q < (1 << (R - k - 1)); q++) {
             const u64 p0 = p[2 * q], p1 = p[2 * q + 1], v0 = v[2 * q], v1 = v[2 * q + 1];
             const u64 b0 = b[2 * q], b1 = b[2 * q + 1];
+            const u64 dp = p1 + (2 * FP_P) - p0, dv = v1 + (2 * FP_P) - v0, db = b1 + (2 * FP_P) - b0;
             mac(a0, p0, v0);
             mac(a1, p1, v1);
-            mac(a2, wext2(p1, p0), wext2(v1, v0));
+            mac(a2, wred(dp), wred(dv));  // leading coefficient (see gen_pair)
             acc_add(a0, b0);
             acc_add(a1, b1);
-            acc_add(a2, wext2(b1, b0));
-            p[q] = wfold(p0, p1, rr0, rr1);
-            v[q] = wfold(v0, v1, rr0, rr1);
-            b[q] = wfold(b0, b1, rr0, rr1);
+            p[q] = wlin1(p0, dp, rr0, rr1);
+            v[q] = wlin1(v0, dv, rr0, rr1);
+            b[q] = wlin1(b0, db, rr0, rr1);
         }
         h[3 * k] = wred(h[3 * k] + acc_red(a0));
         h[3 * k + 1] = wred(h[3 * k + 1] + acc_red(a1));
         h[3 * k + 2] = wred(h[3 * k + 2] + acc_red(a2));
     }
+}
+
+// Rounds 0 and 1 of the first wave of a TREE phase-2 instance on the 4
+// entries at x0 (gates g = x0/2 and x0/2 + 1 of layer i).  P and B vanish at
+// odd entries and P[2g] = eq(r_P, g) = w, B[2g] = w V[2g+1], so round 0 needs
+// per gate only w: its message is c0 = sum w (v0 + v1), c1 = 0 and leading
+// coefficient c2 = -sum w (v1 - v0), and the folds are P' = (1 - r_0) w,
+// V' = V folded, B' = (1 - r_0) w v1.  The common factor 1 - r_0 of P' and B'
+// is left out here: it multiplies the message of every later round of the
+// instance and is applied in the final reduction.  h[2] collects the c2 sum
+// with its sign flipped (restored by the caller).
+__device__ __forceinline__ void tree2_run(const Globals &G, const GenWave &W, u64 x0, const GenSmem &sm,
+                                          u64 (&h)[15], u64 &pn, u64 &vn, u64 &bn)
+{
+    const ulonglong2 *sv = reinterpret_cast<const ulonglong2 *>(W.inV + x0);
+    const ulonglong2 va = __ldg(sv), vb = __ldg(sv + 1);
+    const EqTab &T = G.layers[W.layer].trp;
+    const u64 wa = eq_at(T, x0 >> 1), wb = eq_at(T, (x0 >> 1) + 1);
+    const u64 da = va.y + (2 * FP_P) - va.x, db = vb.y + (2 * FP_P) - vb.x;  // below 2^62.6
+    acc128 s, t;
+    acc_zero(s);
+    acc_zero(t);
+    mac(s, wa, va.x + va.y);  // operands below 2^62 + 16
+    mac(s, wb, vb.x + vb.y);
+    mac(t, wa, da);
+    mac(t, wb, db);
+    h[0] = wred(h[0] + acc_red(s));
+    h[2] = wred(h[2] + acc_red(t));
+    const u32 a0 = sm.r[0][0], a1 = sm.r[0][1];
+    const u64 v0 = wlin1(va.x, da, a0, a1), v1 = wlin1(vb.x, db, a0, a1);
+    const u64 b0 = wmul(wa, va.y), b1 = wmul(wb, vb.y);
+    u64 c0, c1, c2;
+    gen_pair(wa, wb, v0, v1, b0, b1, sm.r[1][0], sm.r[1][1], c0, c1, c2, pn, vn, bn);
+    h[3] = wred(h[3] + c0);
+    h[4] = wred(h[4] + c1);
+    h[5] = wred(h[5] + c2);
+}
+
+// Rounds 0 and 1 of the first wave of a SQUARE phase-2 instance on the 4
+// entries at x0: P[x] = eq(r_P, x) V[x] and B = 0, so the B terms drop out.
+__device__ __forceinline__ void sq2_run(const Globals &G, const GenWave &W, u64 x0, const GenSmem &sm, u64 (&h)[15],
+                                        u64 &pn, u64 &vn)
+{
+    const ulonglong2 *sv = reinterpret_cast<const ulonglong2 *>(W.inV + x0);
+    const ulonglong2 va = __ldg(sv), vb = __ldg(sv + 1);
+    const EqTab &T = G.layers[W.layer].trp;
+    u64 v[4] = {va.x, va.y, vb.x, vb.y}, p[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) p[q] = wmul(eq_at(T, x0 + q), v[q]);
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        acc128 a0, a1, a2;
+        acc_zero(a0);
+        acc_zero(a1);
+        acc_zero(a2);
+        const u32 rr0 = sm.r[k][0], rr1 = sm.r[k][1];
+#pragma unroll
+        for (int q = 0; q < (2 >> k); q++) {
+            const u64 p0 = p[2 * q], p1 = p[2 * q + 1], v0 = v[2 * q], v1 = v[2 * q + 1];
+            const u64 dp = p1 + (2 * FP_P) - p0, dv = v1 + (2 * FP_P) - v0;
+            mac(a0, p0, v0);
+            mac(a1, p1, v1);
+            mac(a2, wred(dp), wred(dv));
+            p[q] = wlin1(p0, dp, rr0, rr1);
+            v[q] = wlin1(v0, dv, rr0, rr1);
+        }
+        h[3 * k] = wred(h[3 * k] + acc_red(a0));
+        h[3 * k + 1] = wred(h[3 * k + 1] + acc_red(a1));
+        h[3 * k + 2] = wred(h[3 * k + 2] + acc_red(a2));
+    }
+    pn = p[0];
+    vn = v[0];
 }
 
 // In-register rounds for e in 3..5: runs of 4 entries (rounds 0, 1), then
@@ -462,6 +520,7 @@ __device__ __forceinline__ void gen_regs_runs(const Globals &G, const GenWave &W
     for (int j = 0; j < 9; j++) sm.hs[j][threadIdx.x] = 0;
     u64 p0 = 0, v0 = 0, b0 = 0, p1 = 0, v1 = 0, b1 = 0, p2 = 0, v2 = 0, b2 = 0;  // pending: rounds 2, 3, 4
     u64 tp = 0, tv = 0, tb = 0;
+    const bool tree2 = W.src == GS_TREE2;
     // a rolled loop keeps the kernel small (instruction-cache bound when unrolled)
 #pragma unroll 1
     for (u32 sub = 0; sub < nruns; sub++) {
@@ -473,12 +532,19 @@ __device__ __forceinline__ void gen_regs_runs(const Globals &G, const GenWave &W
                 if (hasB) prefetch_l1(W.inB + xn);
             }
         }
-        u64 p[4], v[4], b[4];
-        gen_load<4>(G, W, x0 + 4 * sub, hasB, p, v, b);
-        gen_regs<2>(p, v, b, sm, h);
-        tp = p[0];
-        tv = v[0];
-        tb = b[0];
+        if (tree2) {
+            tree2_run(G, W, x0 + 4 * sub, sm, h, tp, tv, tb);
+        } else if (W.src == GS_SQ2) {
+            sq2_run(G, W, x0 + 4 * sub, sm, h, tp, tv);
+            tb = 0;
+        } else {
+            u64 p[4], v[4], b[4];
+            gen_load<4>(W, x0 + 4 * sub, hasB, p, v, b);
+            gen_regs<2>(p, v, b, sm, h);
+            tp = p[0];
+            tv = v[0];
+            tb = b[0];
+        }
         if (!(sub & 1)) {  // wait for the partner run
             p0 = tp, v0 = tv, b0 = tb;
             continue;
@@ -500,6 +566,7 @@ __device__ __forceinline__ void gen_regs_runs(const Globals &G, const GenWave &W
     pv = tp;
     vv = tv;
     bv = tb;
+    if (tree2) h[2] = wred((2 * FP_P) - h[2]);
 #pragma unroll
     for (int j = 0; j < 9; j++) h[6 + j] = sm.hs[j][threadIdx.x];
 }
@@ -607,16 +674,17 @@ __device__ void gen_chunk(const Globals &G, const GenWave &W, u32 chunk, GenSmem
         if ((lane & 1) == 0 && (lane >> 1) < 3 * e) sm.w[warp][lane >> 1] = s;
     } else if (tid < na) {
         const u64 x = base + tid;
-        vv = __ldcg(W.inV + x);
+        const bool ext = W.r0 == 0;
+        vv = ld_in(W.inV + x, ext);
         if (W.src == GS_SQ2) {
             pv = wmul(eq_at(G.layers[W.layer].trp, x), vv);
         } else if (W.src == GS_TREE2) {
             const u64 w = (x & 1) ? 0 : eq_at(G.layers[W.layer].trp, x >> 1);
             pv = w;
-            bv = (x & 1) ? 0 : wmul(w, __ldcg(W.inV + x + 1));
+            bv = (x & 1) ? 0 : wmul(w, ld_in(W.inV + x + 1, ext));
         } else {
-            pv = __ldcg(W.inP + x);
-            bv = hasB ? __ldcg(W.inB + x) : 0;
+            pv = ld_in(W.inP + x, ext);
+            bv = hasB ? ld_in(W.inB + x, ext) : 0;
         }
     }
     gen_cross(pv, vv, bv, e, tid, na, nr, sm);
@@ -718,7 +786,7 @@ __device__ void line_chunk(const Globals &G, const LineWaveDev &W, u32 chunk, Li
                     u64 v[8];
 #pragma unroll
                     for (int t = 0; t < 4; t++) {
-                        const ulonglong2 w = __ldcg(src + 4 * run + t);
+                        const ulonglong2 w = __ldg(src + 4 * run + t);
                         v[2 * t] = w.x;
                         v[2 * t + 1] = w.y;
                     }
@@ -749,7 +817,7 @@ __device__ void line_chunk(const Globals &G, const LineWaveDev &W, u32 chunk, Li
 #pragma unroll
                 for (int c = 0; c < 7; c++) sm.bufA[tid * 7 + c] = p[c];
             } else {
-                sm.bufA[tid] = __ldcg(W.in + base + tid);
+                sm.bufA[tid] = __ldg(W.in + base + tid);
             }
         }
         m = na;
@@ -774,7 +842,35 @@ __device__ void line_chunk(const Globals &G, const LineWaveDev &W, u32 chunk, Li
     }
     __syncthreads();
     u64 *cur = sm.bufA, *nxt = sm.bufB;
-    for (u32 k = k0; k < W.nl; k++) {
+    u32 k = k0;
+    if (m == WV_NT && deg == LN_E && k + 5 <= W.nl) {
+        // One polynomial per thread: the first five levels stay inside each
+        // warp (its 32 polynomials -> 1) with no CTA barrier.  A warp works
+        // in its own parts of the buffers: its level-0 inputs in bufA, then
+        // alternately 256 entries of bufB and its bufA part; its result goes
+        // past every warp's inputs, to bufA[1024 + warp (LN_E + 6)].
+        const u32 warp = tid >> 5, lane = tid & 31;
+        u64 *ownA = sm.bufA + warp * 32 * (LN_E + 1), *ownB = sm.bufB + warp * 256;
+        const u64 *in = ownA;
+        u32 cnt = 32, d = deg;
+        for (u32 lv = 0; lv < 5; lv++, k++) {
+            u64 *out = (lv == 4) ? sm.bufA + 1024 + warp * (LN_E + 6) : ((lv & 1) ? ownA : ownB);
+            const u32 half = cnt >> 1, C = d + 2;
+            for (u32 idx = lane; idx < half * C; idx += 32) {
+                const u32 j = idx / C, c = idx - j * C;
+                out[j * C + c] = line_coef(in + (2 * j) * (d + 1), in + (2 * j + 1) * (d + 1), d, c, sm.la[k], sm.lb[k]);
+            }
+            __syncwarp();
+            in = out;
+            cnt = half;
+            d += 1;
+        }
+        __syncthreads();
+        cur = sm.bufA + 1024;
+        m = WV_NT / 32;
+        deg = d;
+    }
+    for (; k < W.nl; k++) {
         const u32 half = m >> 1, C = deg + 2;
         for (u32 idx = tid; idx < half * C; idx += WV_NT) {
             const u32 j = idx / C, c = idx - j * C;
@@ -922,6 +1018,7 @@ __global__ void __launch_bounds__(256) k_final(const Globals *Gs, const SciDev *
         u64 ez = 0, v1 = 0, ch = 0, es = 0, kap = 0, c0 = 0, c1 = 0;
         if (lane == 0) {
             ez = *R.ez;
+            if (R.defer) ch = *R.ch;
             if (!gen) {
                 v1 = *R.v1;
                 ch = *R.ch;
@@ -941,10 +1038,12 @@ __global__ void __launch_bounds__(256) k_final(const Globals *Gs, const SciDev *
         if (lane == 0) {
             u64 g0, g1, g2;
             if (gen) {
-                const u64 sg = (R.kind == PK_GEN_TAB) ? 1 : ez;
+                u64 sg = (R.kind == PK_GEN_TAB) ? 1 : ez;
+                if (R.defer) sg = f_mul(sg, f_sub(1, ch));  // TREE phase 2: 1 - r_0 left out of P, B
                 g0 = f_mul(sg, h[0]);
                 g1 = f_mul(sg, h[1]);
-                g2 = f_mul(sg, h[2]);
+                // h[2] is the leading coefficient: value at 2 = 2 h1 - h0 + 2 h2
+                g2 = f_mul(sg, f_add(f_sub(f_add(h[1], h[1]), h[0]), f_add(h[2], h[2])));
             } else {
                 u64 sigma = 1, c2u = 0;
                 if (R.kind == PK_TREE3) {

@@ -172,10 +172,11 @@ struct RoundRef {
     u32 circ;
     u32 sci;
     u32 j;            // round index within the SCI
-    u32 pad;
+    u32 defer;        // TREE phase 2, j >= 1: the message carries the factor 1 - (first challenge of the
+                      // phase), left out of P and B by the first wave's round 0
     const u64 *ez;    // eq(z_i, r_P) of the layer
     const u64 *v1;    // V~_{i+1}(r1) of the layer
-    const u64 *ch;    // TREE phase 3: the first challenge of phase 2
+    const u64 *ch;    // TREE phases 2 and 3: the first challenge of phase 2
     const u64 *lc;    // PROD: c0, c1 of round j
     const u64 *kap;   // PROD: kappa_j
     const u64 *esum;  // PROD: esum_j

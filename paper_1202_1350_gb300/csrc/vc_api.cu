@@ -371,6 +371,9 @@ static size_t layout(vc_circuit *c, uintptr_t base)
             const u64 *inP = tab ? (ph == 2 ? L.P2 : L.P3) : nullptr;
             const u64 *inB = tabB ? (ph == 2 ? L.B2 : L.B3) : nullptr;
             const u64 *inV = (ph == 1) ? L.V : L.Vn;
+            // TREE phase 2 with a first wave in registers: its round 0 leaves
+            // the factor 1 - r_0 out of P and B (applied per round by k_final)
+            const bool defer = Sc.kind == PK_GEN_TREE2 && std::min(C, n) > WV_LOG;
             u32 r0 = 0, g = 0;
             bool tail = false;
             for (u32 w = 0;; w++) {
@@ -391,6 +394,7 @@ static size_t layout(vc_circuit *c, uintptr_t base)
                     R.circ = 0;
                     R.sci = sci;
                     R.j = r0 + k;
+                    R.defer = (defer && R.j >= 1) ? 1u : 0u;
                     R.ez = G.scal + SCAL_EQZRP(i);
                     R.v1 = G.scal + SCAL_V1(i);
                     R.ch = G.chal + c->chal_off[i] + c->s[i];
