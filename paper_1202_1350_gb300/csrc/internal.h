@@ -22,7 +22,7 @@ struct PlanConfig {
     u32 pr_chunk = PR_CHUNK_LOG;
     u32 gn_chunk = GN_CHUNK_LOG;
     u32 ln_chunk0 = LN_CHUNK0_LOG;
-    u32 ev_chunk = 10;
+    u32 ev_chunk = 11;  // evaluation chunk: 2^11 inputs per CTA, eight per thread in registers
 };
 
 // Which layers' phase-2/3 tables are built by k_build23 (the rest are formed

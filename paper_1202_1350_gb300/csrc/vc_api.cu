@@ -834,13 +834,9 @@ void enqueue_plan(Plan &P, cudaStream_t st)
     };
     mark(VC_STAGE_PROOF, 0, st);
     // helper stream: coins, points, eq tables and product weights (they do not
-    // depend on the circuit's values), concurrently with the evaluation
+    // depend on the circuit's values), concurrently with the evaluation; the
+    // evaluation, the longer of the two, is put into the graph first
     cudaEventRecord(P.ev_fork, st);
-    cudaStreamWaitEvent(sa, P.ev_fork, 0);
-    mark(VC_STAGE_TABLES, 0, sa);
-    launch_coins(Gs, P.ncirc, P.d_eqjobs, (int)P.eqjobs.size(), P.d_scis, P.d_pw, (int)P.pw.size(), sa);
-    mark(VC_STAGE_TABLES, 1, sa);
-    cudaEventRecord(P.ev_tables, sa);
     mark(VC_STAGE_EVAL, 0, st);
     launch_check_inputs(Gs, P.d_checks, (int)P.checks.size(), st);
     for (size_t k = 0; k < P.seg_items.size(); k++) {
@@ -848,6 +844,11 @@ void enqueue_plan(Plan &P, cudaStream_t st)
         launch_eval_layers(Gs, P.d_levs, P.d_lev_items[k], (int)P.lev_items[k].size(), st);
     }
     mark(VC_STAGE_EVAL, 1, st);
+    cudaStreamWaitEvent(sa, P.ev_fork, 0);
+    mark(VC_STAGE_TABLES, 0, sa);
+    launch_coins(Gs, P.ncirc, P.d_eqjobs, (int)P.eqjobs.size(), P.d_scis, P.d_pw, (int)P.pw.size(), sa);
+    mark(VC_STAGE_TABLES, 1, sa);
+    cudaEventRecord(P.ev_tables, sa);
     cudaStreamWaitEvent(st, P.ev_tables, 0);
     // line reductions, product-weighted and on-the-fly general waves
     mark(VC_STAGE_WAVES, 0, st);
