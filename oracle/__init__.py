@@ -8,8 +8,9 @@ The arithmetic lives in ``vc_oracle.c`` (plain C, 128-bit products and ``%``),
 compiled with gcc into ``oracle/_build/liboracle.so`` and called through ctypes.
 The circuit descriptions below are this package's own restatement of the
 paper's benchmark circuits (Sec. 6.2.1): F2 (a squaring layer then a binary
-addition tree), F0 (Fermat power x^(p-1) then a tree) and MatMult (one layer of
-n^3 products then a tree over the summation index).
+addition tree), F0 (Fermat power x^(p-1) then a tree), MatMult (one layer of
+n^3 products then a tree over the summation index), pattern matching and the
+single-output MatMult check (both with the F0 subcircuit).
 """
 from __future__ import annotations
 
@@ -184,6 +185,79 @@ def matmult_layers(logn: int):
     log_width = [2 * L + j for j in range(0, L + 1)] + [2 * L + 1]
     kinds = [TREE] * L + [MATMULT]
     return log_width, kinds
+
+
+def pm_layers(log_n: int, log_q: int):
+    """Pattern matching (Sec. 6.2.1): for every location i of a text of n = 2^log_n
+    symbols, v_i = sum_j (t_{i+j} - p_j)^2 over a pattern of q = 2^log_q symbols
+    (zero exactly at an occurrence, for symbols far below p), then the F0
+    subcircuit 4 [v_i != 0] and a sum: the output is 4 (n - occurrences).
+
+    Input layout (2n entries): text, pattern, the constant p - 1 at n + q, the
+    constant 1 at n + q + 1, zeros.  The two lowest layers are explicit:
+      A: entry k <- text (times 1), -pattern (times p - 1), or 1 (1 times 1);
+      B: gate i q + j <- t_{i+j} + (-p_j) for locations with i + q <= n, and
+         1 = 1 * 1 at the q - 1 locations past the end (never an occurrence).
+    Then a squaring layer, log_q addition layers over j, the F0 layers and
+    log_n addition layers.  Returns (log_width, kinds, explicit)."""
+    a, b = log_n, log_q
+    assert a >= 2 and 0 <= b <= a - 1
+    n, q = 1 << a, 1 << b
+    m1, one = n + q, n + q + 1
+    W = 2 * n
+    ty_a = np.ones(W, np.uint8)
+    a1 = np.full(W, one, np.uint32)
+    a2 = np.full(W, one, np.uint32)
+    for k in range(n):
+        a1[k] = k
+    for k in range(n, n + q):
+        a1[k], a2[k] = k, m1
+    Sb = n * q
+    ty_b = np.zeros(Sb, np.uint8)
+    b1 = np.zeros(Sb, np.uint32)
+    b2 = np.zeros(Sb, np.uint32)
+    for i in range(n):
+        for j in range(q):
+            g = i * q + j
+            if i + q <= n:
+                b1[g], b2[g] = i + j, n + j
+            else:
+                ty_b[g], b1[g], b2[g] = 1, m1, m1  # A[n + q] = 1
+    log_width = list(range(0, a + 1)) + [a + 1] * 60 + list(range(a, a + b)) + [a + b, a + b, a + 1, a + 1]
+    kinds = [TREE] * a + [F0_FINAL] + [F0_PAIR] * 59 + [F0_FIRST] + [TREE] * b + [SQUARE, EXPLICIT, EXPLICIT]
+    explicit = [None] * (len(kinds) - 2) + [(ty_b, b1, b2), (ty_a, a1, a2)]
+    return log_width, kinds, explicit
+
+
+def mm1_layers(logm: int):
+    """Single-output MatMult (Sec. 6.2.1): for m x m matrices A, B and the
+    prover-supplied C, the output is 4 #{(i, j) : (A B)_ij != C_ij} (zero
+    exactly when C = A B).  One explicit layer holds, for each (i, j), the m
+    products A_ik B_kj, the entry C_ij (p - 1) and m - 1 zeros (0 0); log m + 1
+    addition layers give (A B - C)_ij; then the F0 layers and 2 log m addition
+    layers.  Input layout (4 m^2 entries): A row-major, B row-major, C
+    row-major, p - 1 at 3 m^2, zeros.  Returns (log_width, kinds, explicit)."""
+    L = logm
+    m = 1 << L
+    assert L >= 1
+    m2 = m * m
+    m1, zero = 3 * m2, 3 * m2 + 1
+    S = m2 * 2 * m
+    ty = np.ones(S, np.uint8)
+    i1 = np.full(S, zero, np.uint32)
+    i2 = np.full(S, zero, np.uint32)
+    for i in range(m):
+        for j in range(m):
+            base = (i * m + j) * 2 * m
+            for k in range(m):
+                i1[base + k] = i * m + k
+                i2[base + k] = m2 + k * m + j
+            i1[base + m] = 2 * m2 + i * m + j
+            i2[base + m] = m1
+    log_width = list(range(0, 2 * L + 1)) + [2 * L + 1] * 60 + list(range(2 * L, 3 * L + 1)) + [3 * L + 1, 2 * L + 2]
+    kinds = [TREE] * (2 * L) + [F0_FINAL] + [F0_PAIR] * 59 + [F0_FIRST] + [TREE] * (L + 1) + [EXPLICIT]
+    explicit = [None] * (len(kinds) - 1) + [(ty, i1, i2)]
+    return log_width, kinds, explicit
 
 
 class Circuit:

@@ -13,6 +13,8 @@ Recipes (input seed = 0xC0FFEE + workload index):
   MatMult, n = 128      A, B uniform in [0, 2^10]
   batch                 512 F2 with log2 n uniform in {8..18} + 64 MatMult, n in {16, 32, 64}
   serving               70 % F2 with log2 n uniform in {10..22}, 30 % MatMult, n in {32, 64, 128}
+  pattern matching      text and pattern uniform over 4 symbols, 3 planted occurrences
+  MatMult check         A, B uniform in [0, 2^10], C = A B with seeded off-by-one entries
 """
 from __future__ import annotations
 
@@ -66,6 +68,47 @@ def matmult_inputs(logn: int, hi: int, seed: int) -> np.ndarray:
     """Inputs of the MatMult circuit: A row-major, then B row-major (2 n^2 values)."""
     n = 1 << logn
     return uniform_ints(seed, 2 * n * n, hi)
+
+
+P61 = (1 << 61) - 1
+
+
+def pm_inputs(log_n: int, log_q: int, seed: int, alphabet: int = 4, planted: int = 3) -> np.ndarray:
+    """Inputs of the pattern-matching circuit: a text of n symbols and a
+    pattern of q symbols, both uniform over `alphabet` symbols, with the
+    pattern copied into the text at `planted` seeded locations; then the
+    constants p - 1 and 1 and zeros (2n entries)."""
+    n, q = 1 << log_n, 1 << log_q
+    text = uniform_ints(seed, n, alphabet - 1)
+    pat = uniform_ints(seed + 1, q, alphabet - 1)
+    locs = splitmix64_stream(seed + 2, planted) % np.uint64(n - q + 1)
+    for i in locs:
+        text[int(i):int(i) + q] = pat
+    x = np.zeros(2 * n, np.uint64)
+    x[:n] = text
+    x[n:n + q] = pat
+    x[n + q] = P61 - 1
+    x[n + q + 1] = 1
+    return x
+
+
+def mm1_inputs(logm: int, seed: int, hi: int = 1 << 10, errors: int = 0) -> np.ndarray:
+    """Inputs of the single-output MatMult check: A, B uniform in [0, hi], the
+    claimed product C = A B (exact integers, far below p) with `errors` seeded
+    entries off by one, the constant p - 1 and zeros (4 m^2 entries)."""
+    m = 1 << logm
+    ab = uniform_ints(seed, 2 * m * m, hi).astype(np.int64)
+    A, B = ab[:m * m].reshape(m, m), ab[m * m:].reshape(m, m)
+    C = (A @ B).astype(np.uint64).ravel()
+    if errors:
+        pos = splitmix64_stream(seed + 1, errors) % np.uint64(m * m)
+        for k in pos:
+            C[int(k)] += np.uint64(1)
+    x = np.zeros(4 * m * m, np.uint64)
+    x[:2 * m * m] = ab.astype(np.uint64)
+    x[2 * m * m:3 * m * m] = C
+    x[3 * m * m] = P61 - 1
+    return x
 
 
 # Workload table: name -> (circuit family, log size, input recipe)

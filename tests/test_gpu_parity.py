@@ -116,3 +116,18 @@ def test_workload_f0_2e16():
 def test_workload_matmult_128():
     fam, logn, gen, seed = I.WORKLOADS["matmult_128"]
     check(*circuits.matmult(logn), gen(seed), seeds=(1,))
+
+
+# the paper's pattern-matching circuit and its single-output MatMult check: two
+# explicit layers (one) under a squaring layer / addition trees and the F0 layers
+
+@pytest.mark.parametrize("a,b", [(2, 0), (3, 1), (5, 2), (7, 3), (9, 2)])
+def test_pattern_match(a, b):
+    w, k, ex = circuits.pattern_match(a, b)
+    check(w, k, I.pm_inputs(a, b, 40 + a), seeds=(3, 0xFEED), explicit=ex)
+
+
+@pytest.mark.parametrize("logm,errors", [(1, 0), (2, 0), (2, 2), (3, 0), (3, 4), (4, 1)])
+def test_matmult_check(logm, errors):
+    w, k, ex = circuits.matmult_check(logm)
+    check(w, k, I.mm1_inputs(logm, 50 + logm, errors=errors), seeds=(5,), explicit=ex)

@@ -150,3 +150,25 @@ def test_host_pointers():
         assert vc.vc_verify(h, dev(x), 6, tr)
     finally:
         vc.vc_circuit_destroy(h)
+
+
+@pytest.mark.parametrize("which", ["pm", "mm1"])
+def test_pm_and_mm1_verified(which):
+    """Explicit-wiring circuits: the CUDA verifier (wiring predicates summed
+    over the gates) accepts the honest proof and rejects a changed message."""
+    if which == "pm":
+        widths, kinds, ex = circuits.pattern_match(6, 2)
+        x = I.pm_inputs(6, 2, 21)
+    else:
+        widths, kinds, ex = circuits.matmult_check(3)
+        x = I.mm1_inputs(3, 22, errors=2)
+    h = vc.vc_circuit_create(widths, kinds, ex)
+    try:
+        tr = gpu_prove(widths, kinds, x, 41, ex)
+        assert vc.vc_verify(h, dev(x), 41, dev(tr))
+        for pos in (0, len(tr) // 3, len(tr) - 1):
+            bad = tr.copy()
+            bad[pos] = (int(bad[pos]) + 1) % P
+            assert not vc.vc_verify(h, dev(x), 41, dev(bad))
+    finally:
+        vc.vc_circuit_destroy(h)

@@ -439,3 +439,76 @@ def test_f2_circuit_size_matches_the_paper_table():
     widths, kinds = oracle.f2_layers(23)
     assert round((1 << widths[-1]) / 1e5) == round(inputs / 1e5)
     assert round(sum(1 << s for s in widths) / 1e5) == round(gates / 1e5)
+
+
+# --- pattern matching and the single-output MatMult check (Sec. 6.2.1) -----------
+
+def _occurrences(text, pat):
+    n, q = len(text), len(pat)
+    return sum(all(int(text[i + j]) == int(pat[j]) for j in range(q)) for i in range(n - q + 1))
+
+
+@pytest.mark.parametrize("a,b,seed", [(2, 0, 1), (2, 1, 2), (3, 1, 3), (5, 2, 4), (6, 3, 5), (7, 1, 6)])
+def test_pattern_match_output_counts_occurrences(a, b, seed):
+    """The circuit's output is 4 (n - occurrences), occurrences counted by
+    brute force over every location of the text."""
+    from paper_1202_1350_gb300 import inputs as I
+    w, k, ex = oracle.pm_layers(a, b)
+    c = oracle.Circuit(w, k, explicit=ex)
+    n, q = 1 << a, 1 << b
+    x = I.pm_inputs(a, b, seed)
+    occ = _occurrences(x[:n], x[n:n + q])
+    assert occ >= 1  # the planted copies
+    assert int(c.evaluate(x)[0][0]) == 4 * (n - occ)
+    # a text without the pattern anywhere: no occurrence
+    y = x.copy()
+    y[n:n + q] = 7  # a symbol outside the text's alphabet
+    assert int(c.evaluate(y)[0][0]) == 4 * n
+
+
+@pytest.mark.parametrize("logm,errors", [(1, 0), (2, 0), (2, 1), (2, 3), (3, 0), (3, 5)])
+def test_matmult_check_output_counts_wrong_entries(logm, errors):
+    """Output 4 #{(i, j) : (A B)_ij != C_ij}: zero exactly when C = A B."""
+    from paper_1202_1350_gb300 import inputs as I
+    w, k, ex = oracle.mm1_layers(logm)
+    c = oracle.Circuit(w, k, explicit=ex)
+    m = 1 << logm
+    x = I.mm1_inputs(logm, 70 + logm, errors=errors)
+    A = x[:m * m].astype(object).reshape(m, m)
+    B = x[m * m:2 * m * m].astype(object).reshape(m, m)
+    C = x[2 * m * m:3 * m * m].astype(object).reshape(m, m)
+    wrong = int(((A.dot(B) - C) % P != 0).sum())
+    assert wrong <= errors and (wrong > 0) == (errors > 0)
+    assert int(c.evaluate(x)[0][0]) == 4 * wrong
+
+
+@pytest.mark.parametrize("which", ["pm", "mm1"])
+def test_pm_and_mm1_proofs_accepted_and_tampering_rejected(which):
+    from paper_1202_1350_gb300 import inputs as I
+    if which == "pm":
+        w, k, ex = oracle.pm_layers(4, 2)
+        x = I.pm_inputs(4, 2, 11)
+    else:
+        w, k, ex = oracle.mm1_layers(2)
+        x = I.mm1_inputs(2, 12, errors=1)
+    c = oracle.Circuit(w, k, explicit=ex)
+    t = c.prove(x, 99)
+    assert c.verify(x, 99, t)[0]
+    bad = t.copy()
+    bad[len(bad) // 2] = (int(bad[len(bad) // 2]) + 1) % P
+    assert not c.verify(x, 99, bad)[0]
+
+
+def test_pm_and_mm1_wiring_equals_the_packages_description():
+    """The package describes these circuits with its own code; both
+    descriptions must be the same circuit."""
+    from paper_1202_1350_gb300 import circuits as C
+    pairs = [(oracle.pm_layers(a, b), C.pattern_match(a, b)) for a, b in [(2, 0), (3, 2), (6, 3)]]
+    pairs += [(oracle.mm1_layers(L), C.matmult_check(L)) for L in (1, 2, 3)]
+    for (w1, k1, e1), (w2, k2, e2) in pairs:
+        assert list(w1) == list(w2) and list(k1) == list(k2)
+        for x, y in zip(e1, e2):
+            assert (x is None) == (y is None)
+            if x is not None:
+                for u, v in zip(x, y):
+                    assert np.array_equal(np.asarray(u, np.int64), np.asarray(v, np.int64))
