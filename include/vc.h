@@ -121,6 +121,16 @@ vc_status vc_evaluate(vc_circuit *c, const uint64_t *inputs, uint64_t *outputs, 
 vc_status vc_prove(vc_circuit *c, const uint64_t *inputs, uint64_t seed,
                    uint64_t *transcript, void *stream);
 
+/* The same proof computed the way the paper's GPU prover computes it
+ * (Sec. 4.1.1; Sec. 4.2, "Memory access"): in every round one thread per gate
+ * adds that gate's independent contribution to the message, O(S log S) work
+ * per layer, instead of folding tables.  The transcript is identical to
+ * vc_prove's; arguments, asynchrony and errors are vc_prove's.  The first call
+ * allocates the per-gate tables (about 2 S_i + 3 S_{i+1} u64 per layer;
+ * VC_ENOMEM if they do not fit); they are freed with the circuit. */
+vc_status vc_prove_pergate(vc_circuit *c, const uint64_t *inputs, uint64_t seed,
+                           uint64_t *transcript, void *stream);
+
 /* Wait for the circuit's queued work on `stream` and return (and clear) any
  * error latched by asynchronous calls. */
 vc_status vc_circuit_sync(vc_circuit *c, void *stream);

@@ -159,6 +159,12 @@ struct vc_circuit {
     std::vector<u32> seg_maxblock;  // per segment: largest block of its run and tail
     Plan P;                       // this circuit alone (circ = 0)
     u64 *h_pinned = nullptr;      // small pinned buffer for status/result readback
+    // per-gate prover (allocated on its first use)
+    char *pg_arena = nullptr;
+    PgLayer *d_pg = nullptr;
+    u32 *d_pg_blk = nullptr, *d_pg_lblk = nullptr;
+    u32 pg_nblk = 0, pg_nlblk = 0, pg_rounds = 0;
+    cudaGraphExec_t pg_exec = nullptr;
 };
 
 struct vc_batch {

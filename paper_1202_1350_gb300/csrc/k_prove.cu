@@ -41,31 +41,6 @@ void launch_params_batch(Globals *Gs, const CallParams *cp, int n, cudaStream_t 
 }
 
 
-// --------------------------------------------------------------------------------
-// Wiring: in-neighbours and gate type of gate g (Sec. 5.1.4, Sec. 6.2.1).
-// --------------------------------------------------------------------------------
-
-__device__ __forceinline__ void gate_wiring(const LayerDev &L, u64 g, u64 &a, u64 &b, u32 &mul)
-{
-    switch (L.kind) {
-    case W_SQUARE: a = g; b = g; mul = 1; break;
-    case W_TREE: a = 2 * g; b = 2 * g + 1; mul = 0; break;
-    case W_MATMULT: {
-        const u32 Lb = L.s / 3;
-        const u64 n = 1ull << Lb, m = n - 1;
-        const u64 k = g & m, j = (g >> Lb) & m, ii = g >> (2 * Lb);
-        a = (ii << Lb) | k;
-        b = (1ull << (2 * Lb)) | (k << Lb) | j;
-        mul = 1;
-        break;
-    }
-    case W_F0_FIRST: a = g >> 1; b = g >> 1; mul = (g & 1) ? 0 : 1; break;
-    case W_F0_PAIR: a = g; b = g & ~1ull; mul = 1; break;
-    case W_F0_FINAL: a = 2 * g + 1; b = 2 * g + 1; mul = 1; break;
-    default: a = L.in1[g]; b = L.in2[g]; mul = L.type[g]; break;
-    }
-}
-
 // Layer evaluation: V_i[g] = V_{i+1}[in1] op V_{i+1}[in2] (Sec. 6.2.4); an
 // item covers 256 gates of one layer of one circuit.
 __global__ void __launch_bounds__(256) k_eval_layer(const Globals *Gs, const LayerEval *le, const Item *items)

@@ -51,6 +51,30 @@ struct LayerDev {
     const u32 *by2_off, *by2_g;  // gates grouped by in2
 };
 
+// In-neighbours and operation of gate g of layer i (Sec. 6.2.1 circuits):
+// computed from the index for the structured kinds (a tree gate reads 2g and
+// 2g+1, as in Sec. 4.2 "Memory access"), read for EXPLICIT layers.
+__device__ __forceinline__ void gate_wiring(const LayerDev &L, u64 g, u64 &a, u64 &b, u32 &mul)
+{
+    switch (L.kind) {
+    case W_SQUARE: a = g; b = g; mul = 1; break;
+    case W_TREE: a = 2 * g; b = 2 * g + 1; mul = 0; break;
+    case W_MATMULT: {
+        const u32 Lb = L.s / 3;
+        const u64 n = 1ull << Lb, m = n - 1;
+        const u64 k = g & m, j = (g >> Lb) & m, ii = g >> (2 * Lb);
+        a = (ii << Lb) | k;
+        b = (1ull << (2 * Lb)) | (k << Lb) | j;
+        mul = 1;
+        break;
+    }
+    case W_F0_FIRST: a = g >> 1; b = g >> 1; mul = (g & 1) ? 0 : 1; break;
+    case W_F0_PAIR: a = g; b = g & ~1ull; mul = 1; break;
+    case W_F0_FINAL: a = 2 * g + 1; b = 2 * g + 1; mul = 1; break;
+    default: a = L.in1[g]; b = L.in2[g]; mul = L.type[g]; break;
+    }
+}
+
 // Per-layer scalars written during a proof: scal[2 i] = eq(z_i, r_P),
 // scal[2 i + 1] = V~_{i+1}(r1) (= q_i(0)).
 #define SCAL_EQZRP(i) (2 * (i))
@@ -308,6 +332,26 @@ void launch_vparams(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *tr, const u
                     cudaStream_t st);
 void launch_verify(const Globals &G, const VerifyDev &V, const EqTab &tzd, const EqTab &tz0,
                    const u32 *explicit_layers, int n_explicit, cudaStream_t st);
+
+// Per-gate prover (k_pergate.cu): one descriptor per layer.
+struct PgLayer {
+    u32 layer;         // i
+    u32 s, sn, n;      // s_i, s_{i+1}, rounds s_i + 2 s_{i+1}
+    u32 blk0, nblk;    // CTAs of the gate launches covering this layer's gates
+    u32 lblk0, lnblk;  // CTAs of the line launch covering V_{i+1}
+    u64 *preP;         // eq over the bound p coordinates (S_i entries; eq(r_P, .) after phase 1)
+    u64 *preA, *preB;  // the same over the bound w1 / w2 coordinates (S_{i+1} each)
+    u64 *suf;          // phase-1 suffix tables of z_i (S_i - 1 entries)
+    u64 *fa, *fb;      // V_{i+1} folded with the bound coordinates (S_{i+1}/2, S_{i+1}/4)
+    u64 *v1;           // V~_{i+1}(r1)
+    u64 *part;         // per-CTA partial sums of the current round, 3 per CTA
+    u64 *ltab;         // line: split eq tables of l(t), t = 0..s_{i+1}
+    u64 *lpart;        // line: per-CTA partial sums, s_{i+1} + 1 per CTA
+};
+// Every launch of a per-gate proof after the evaluation and the coins.
+void launch_pergate(const Globals *G, const PgLayer *pl, int nl, const u32 *blk_layer, u32 nblk,
+                    const u32 *lblk_layer, u32 nlblk, u32 nrounds, cudaStream_t st);
+u32 pergate_gpt();  // gates (and line entries) per CTA
 
 void launch_field_mul(const u64 *a, const u64 *b, u64 *out, u64 n, cudaStream_t st);
 float run_field_mul_rate(int variant, u64 iters, int blocks, int threads, u64 *sink);

@@ -1042,6 +1042,8 @@ void circuit_free(vc_circuit *c)
 {
     if (!c) return;
     if (c->vexec) cudaGraphExecDestroy(c->vexec);
+    if (c->pg_exec) cudaGraphExecDestroy(c->pg_exec);
+    if (c->pg_arena) cudaFree(c->pg_arena);
     plan_release(c->P);
     if (c->arena) cudaFree(c->arena);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -1189,6 +1191,134 @@ extern "C" vc_status vc_prove(vc_circuit *c, const uint64_t *inputs, uint64_t se
     if (e != cudaSuccess) return VC_ECUDA;
     launch_params(c->d_G, seed, kt ? transcript : c->d_tr, st);
     e = plan_launch(c->P, st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return VC_ECUDA;
+    if (!kt) {
+        e = cudaMemcpyAsync(transcript, c->d_tr, c->tr_len * sizeof(u64), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return VC_ECUDA;
+    }
+    if (ki && kt) return VC_OK;
+    return read_status_and_clear(c, st);
+}
+
+// ---- the per-gate prover: device state and its launch sequence ---------------------
+
+static vc_status pergate_prepare(vc_circuit *c)
+{
+    if (c->pg_arena) return VC_OK;
+    const u32 d = c->d, gpc = pergate_gpt();
+    std::vector<PgLayer> pl(d);
+    std::vector<u32> blk, lblk;
+    u32 rounds = 0;
+    auto blocks = [&](u64 n) { return u32((n + gpc - 1) / gpc); };
+    for (u32 i = 0; i < d; i++) {
+        PgLayer &Q = pl[i];
+        Q = PgLayer{};
+        Q.layer = i;
+        Q.s = c->s[i];
+        Q.sn = c->s[i + 1];
+        Q.n = Q.s + 2 * Q.sn;
+        rounds = std::max(rounds, Q.n);
+        Q.blk0 = (u32)blk.size();
+        Q.nblk = blocks(u64(1) << Q.s);
+        blk.insert(blk.end(), Q.nblk, i);
+        Q.lblk0 = (u32)lblk.size();
+        Q.lnblk = blocks(u64(1) << Q.sn);
+        lblk.insert(lblk.end(), Q.lnblk, i);
+    }
+    // one allocation: sizing pass (base 0), then the real one
+    auto carve = [&](Arena &A) {
+        for (u32 i = 0; i < d; i++) {
+            PgLayer &Q = pl[i];
+            const u64 S = u64(1) << Q.s, Sn = u64(1) << Q.sn;
+            const u32 h = (Q.sn + 1) / 2;
+            Q.preP = A.take<u64>(S);
+            Q.preA = A.take<u64>(Sn);
+            Q.preB = A.take<u64>(Sn);
+            Q.suf = A.take<u64>(S);
+            Q.fa = A.take<u64>(std::max<u64>(1, Sn / 2));
+            Q.fb = A.take<u64>(std::max<u64>(1, Sn / 4));
+            Q.v1 = A.take<u64>(1);
+            Q.part = A.take<u64>(3ull * Q.nblk);
+            Q.ltab = A.take<u64>(u64(Q.sn + 1) * ((u64(1) << h) + (u64(1) << (Q.sn - h))));
+            Q.lpart = A.take<u64>(u64(Q.sn + 1) * Q.lnblk);
+        }
+        c->d_pg = A.take<PgLayer>(d);
+        c->d_pg_blk = A.take<u32>(blk.size());
+        c->d_pg_lblk = A.take<u32>(lblk.size());
+    };
+    Arena A0;
+    carve(A0);
+    char *mem = nullptr;
+    if (cudaMalloc(&mem, A0.off) != cudaSuccess) {
+        cudaGetLastError();
+        return VC_ENOMEM;
+    }
+    Arena A;
+    A.base = reinterpret_cast<uintptr_t>(mem);
+    carve(A);
+    cudaError_t e = upload(c->d_pg, pl);
+    if (e == cudaSuccess) e = upload(c->d_pg_blk, blk);
+    if (e == cudaSuccess) e = upload(c->d_pg_lblk, lblk);
+    if (e != cudaSuccess) {
+        cudaFree(mem);
+        return VC_ECUDA;
+    }
+    c->pg_arena = mem;
+    c->pg_nblk = (u32)blk.size();
+    c->pg_nlblk = (u32)lblk.size();
+    c->pg_rounds = rounds;
+    return VC_OK;
+}
+
+// Evaluation, the coins (challenges, points, eq(z_i, r_P)) and the per-gate
+// rounds, captured once per circuit.
+static cudaError_t pergate_launch(vc_circuit *c, cudaStream_t st)
+{
+    Plan &P = c->P;
+    if (!c->pg_exec) {
+        cudaError_t e = cudaStreamBeginCapture(P.cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        launch_check_inputs(P.d_G, P.d_checks, (int)P.checks.size(), P.cap);
+        for (size_t k = 0; k < P.seg_items.size(); k++) {
+            launch_eval_segs(P.d_G, P.d_segs, P.d_seg_items[k], (int)P.seg_items[k].size(), P.seg_maxblock[k], P.cap);
+            launch_eval_layers(P.d_G, P.d_levs, P.d_lev_items[k], (int)P.lev_items[k].size(), P.cap);
+        }
+        launch_coins(P.d_G, 1, nullptr, 0, nullptr, nullptr, 0, P.cap);
+        launch_pergate(P.d_G, c->d_pg, (int)c->d, c->d_pg_blk, c->pg_nblk, c->d_pg_lblk, c->pg_nlblk, c->pg_rounds,
+                       P.cap);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(P.cap, &g);
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return e;
+        }
+        e = cudaGraphInstantiate(&c->pg_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->pg_exec = nullptr;
+            return e;
+        }
+    }
+    return cudaGraphLaunch(c->pg_exec, st);
+}
+
+extern "C" vc_status vc_prove_pergate(vc_circuit *c, const uint64_t *inputs, uint64_t seed, uint64_t *transcript,
+                                      void *stream)
+{
+    if (!c || !inputs || !transcript) return VC_EINVAL;
+    DevGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ki = ptr_kind(inputs, c->device), kt = ptr_kind(transcript, c->device);
+    if (ki < 0 || kt < 0) return VC_EINVAL;
+    vc_status s = pergate_prepare(c);
+    if (s != VC_OK) return s;
+    const u64 nin = u64(1) << c->s[c->d];
+    cudaError_t e = cudaMemcpyAsync(c->V[c->d], inputs, nin * sizeof(u64),
+                                    ki ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return VC_ECUDA;
+    launch_params(c->d_G, seed, kt ? transcript : c->d_tr, st);
+    e = pergate_launch(c, st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return VC_ECUDA;
     if (!kt) {

@@ -110,6 +110,7 @@ def lib():
             L.vc_circuit_bytes.argtypes = [vp, _u64p]
             L.vc_evaluate.argtypes = [vp, vp, vp, vp]
             L.vc_prove.argtypes = [vp, vp, ctypes.c_uint64, vp, vp]
+            L.vc_prove_pergate.argtypes = [vp, vp, ctypes.c_uint64, vp, vp]
             L.vc_circuit_sync.argtypes = [vp, vp]
             L.vc_verify.argtypes = [vp, vp, ctypes.c_uint64, vp, ctypes.POINTER(ctypes.c_int), vp]
             L.vc_prove_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), _u64p, ctypes.POINTER(vp),
@@ -146,7 +147,7 @@ def lib():
                          "vc_circuit_get_info", "vc_batch_create", "vc_batch_destroy", "vc_batch_prove",
                          "vc_batch_sync", "vc_batch_get_info", "vc_server_create", "vc_server_destroy",
                          "vc_server_submit", "vc_server_poll", "vc_server_wait", "vc_server_get_stats",
-                         "vc_autotune", "vc_circuit_create_tiles", "vc_circuit_get_tiles"):
+                         "vc_autotune", "vc_circuit_create_tiles", "vc_circuit_get_tiles", "vc_prove_pergate"):
                 getattr(L, name).restype = st
             _lib = L
     return _lib
@@ -270,6 +271,17 @@ def vc_prove(h, inputs, seed: int, transcript, stream=None, device: int = 0):
     _need(transcript, ntr, "transcript")
     _check(lib().vc_prove(h, _ptr(inputs), seed & 0xFFFFFFFFFFFFFFFF, _ptr(transcript),
                           _stream(stream, device)), "vc_prove")
+    return transcript
+
+
+def vc_prove_pergate(h, inputs, seed: int, transcript, stream=None, device: int = 0):
+    """The same proof by the paper's per-gate method (one thread per gate per
+    round); the transcript equals vc_prove's."""
+    nin, _, ntr = _shapes[h]
+    _need(inputs, nin, "inputs")
+    _need(transcript, ntr, "transcript")
+    _check(lib().vc_prove_pergate(h, _ptr(inputs), seed & 0xFFFFFFFFFFFFFFFF, _ptr(transcript),
+                                  _stream(stream, device)), "vc_prove_pergate")
     return transcript
 
 
