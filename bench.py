@@ -150,7 +150,34 @@ def executed_work(widths, kinds, first_wave_log=12):
 # DRAM bytes (read + write) of one k_waves launch on this workload, from an ncu
 # capture of the current kernel; the V tables are mostly served from L2, so
 # this is below the algorithmic bytes
-K_WAVES_DRAM_BYTES = 25_562_368
+K_WAVES_DRAM_BYTES = 25_568_768
+
+
+def run_ablation(h, xd, tr, flush, reps=5):
+    """The same proof by the paper's per-gate method (one thread per gate per
+    round, vc_prove_pergate) against the folding prover, device time of one
+    proof each (L2 flushed before every call; transcripts compared)."""
+    import torch
+    from paper_1202_1350_gb300 import vc
+    out = {}
+    ref = torch.empty_like(tr)
+    for name, fn, dst in (("folding", vc.vc_prove, ref), ("pergate", vc.vc_prove_pergate, tr)):
+        ts = []
+        for k in range(reps + 2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn(h, xd, 4242, dst)
+            e1.record()
+            e1.synchronize()
+            if k >= 2:
+                ts.append(e0.elapsed_time(e1))
+        out[name + "_prove_ms"] = statistics.median(ts)
+    vc.vc_circuit_sync(h)
+    assert bool((ref == tr).all().item()), "per-gate and folding transcripts differ"
+    out["speedup_of_folding"] = out["pergate_prove_ms"] / out["folding_prove_ms"]
+    out["note"] = "prove only (no verification), median of 5, same transcript"
+    return out
 
 
 def measured_peaks():
@@ -318,6 +345,9 @@ def run_ours(args):
                 except RuntimeError:  # a stage with no work records nothing
                     pass
     vc.vc_circuit_set_stage_events(h, None)
+    ablation = None
+    if not args.no_ablation:
+        ablation = run_ablation(h, xd, tr, flush)
     vc.vc_prove(h, xh, 999, trh)
     e2e_ms = []
     for k in range(max(3, args.steps // 2)):
@@ -370,6 +400,7 @@ def run_ours(args):
                      "algorithmic_bytes": byts, "kernel_ms": sc0_ms,
                      "bytes_frac_of_hbm": (byts / (sc0_ms / 1000)) / (measured_peaks().get("hbm_gbs", 6787.9) * 1e9)},
         "stage_ms": stages,
+        "ablation": ablation,
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -536,6 +567,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the per-gate prover comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
