@@ -180,6 +180,37 @@ def run_ablation(h, xd, tr, flush, reps=5):
     return out
 
 
+def run_residency(widths, kinds, xd, flush, reps=5):
+    """Proof time with the layer values in mapped host memory (read and
+    written over the host link) against device-resident values; transcripts
+    compared."""
+    import torch
+    from paper_1202_1350_gb300 import vc
+    out = {}
+    trs = {}
+    for name, host in (("device", False), ("host_values", True)):
+        h = vc.vc_circuit_create(widths, kinds, host_values=host)
+        tr = torch.empty(vc.vc_transcript_len(h), dtype=torch.int64, device="cuda")
+        ts = []
+        for k in range(reps + 2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            vc.vc_prove(h, xd, 4343, tr)
+            e1.record()
+            e1.synchronize()
+            if k >= 2:
+                ts.append(e0.elapsed_time(e1))
+        vc.vc_circuit_sync(h)
+        out[name + "_prove_ms"] = statistics.median(ts)
+        out[name + "_device_bytes"] = vc.vc_circuit_bytes(h)
+        trs[name] = tr
+        vc.vc_circuit_destroy(h)
+    assert bool((trs["device"] == trs["host_values"]).all().item()), "residency changed the transcript"
+    out["slowdown"] = out["host_values_prove_ms"] / out["device_prove_ms"]
+    return out
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -345,9 +376,10 @@ def run_ours(args):
                 except RuntimeError:  # a stage with no work records nothing
                     pass
     vc.vc_circuit_set_stage_events(h, None)
-    ablation = None
+    ablation = residency = None
     if not args.no_ablation:
         ablation = run_ablation(h, xd, tr, flush)
+        residency = run_residency(widths, kinds, xd, flush)
     vc.vc_prove(h, xh, 999, trh)
     e2e_ms = []
     for k in range(max(3, args.steps // 2)):
@@ -401,6 +433,7 @@ def run_ours(args):
                      "bytes_frac_of_hbm": (byts / (sc0_ms / 1000)) / (measured_peaks().get("hbm_gbs", 6787.9) * 1e9)},
         "stage_ms": stages,
         "ablation": ablation,
+        "residency": residency,
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -567,7 +600,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--no-ablation", action="store_true", help="skip the per-gate prover comparison")
+    ap.add_argument("--no-ablation", action="store_true",
+                    help="skip the per-gate prover and host-residency comparisons")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")

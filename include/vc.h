@@ -95,6 +95,19 @@ typedef struct vc_circuit vc_circuit;
  * On success *out owns the circuit until vc_circuit_destroy. */
 vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, vc_circuit **out);
 
+/* Residency of a circuit's layer values (Sec. 5.1: a circuit whose gates do
+ * not fit in device memory).  With VC_VALUES_IN_HOST_MEMORY the values of
+ * every layer (S_0 + ... + S_d u64, the bulk of a proof's memory) live in
+ * pinned host memory mapped into the device's address space; evaluation
+ * writes them and the sum-check reads them over the host link at every use
+ * (the paper's copy-every-message strategy, with the link instead of copies).
+ * Everything else stays in device memory and the transcript is unchanged. */
+#define VC_VALUES_IN_HOST_MEMORY 1u
+
+/* vc_circuit_create with residency flags (0 or VC_VALUES_IN_HOST_MEMORY;
+ * VC_EINVAL for any other bit; VC_ENOMEM if the pinned host allocation fails). */
+vc_status vc_circuit_create_ex(const vc_circuit_desc *desc, int device, uint32_t flags, vc_circuit **out);
+
 /* Free the circuit and its device scratch (synchronises its device).  NULL is
  * accepted. */
 vc_status vc_circuit_destroy(vc_circuit *c);
@@ -102,7 +115,8 @@ vc_status vc_circuit_destroy(vc_circuit *c);
 /* Transcript length in u64 for this circuit (fixed by its shape). */
 vc_status vc_transcript_len(const vc_circuit *c, uint64_t *n_u64);
 
-/* Device bytes the circuit holds (scratch + plan). */
+/* Device bytes the circuit holds (scratch + plan; layer values in host memory
+ * are not counted). */
 vc_status vc_circuit_bytes(const vc_circuit *c, uint64_t *bytes);
 
 /* Layer-by-layer evaluation (Sec. 6.2.4: the prover's first step).

@@ -123,6 +123,7 @@ struct Plan {
 
 struct vc_circuit {
     int device = 0;
+    u32 flags = 0;                // VC_VALUES_IN_HOST_MEMORY
     PlanConfig cfg;
     u32 d = 0;
     std::vector<u32> s, kind, has_add;
@@ -137,6 +138,8 @@ struct vc_circuit {
 
     char *arena = nullptr;
     size_t arena_bytes = 0;
+    char *host_vals = nullptr;  // mapped host memory of the layer values (VC_VALUES_IN_HOST_MEMORY)
+    size_t host_bytes = 0;
     Globals G{};             // host copy of the circuit's globals
     Globals *d_G = nullptr;  // device copy (seed and tr written per call)
     std::vector<u64 *> V;
@@ -184,7 +187,7 @@ void init_device_once(int device);
 // plan, sized but not allocated (c->arena_bytes set).  circuit_allocate then
 // takes the device memory and uploads everything.
 vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **out,
-                          const PlanConfig *cfg = nullptr);
+                          const PlanConfig *cfg = nullptr, u32 flags = 0);
 vc_status circuit_allocate(vc_circuit *c);
 void circuit_free(vc_circuit *c);
 

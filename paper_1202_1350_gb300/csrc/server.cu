@@ -209,8 +209,8 @@ vc_status launch(vc_server *s, Slot &sl)
     for (int k = 0; k < n; k++) {
         Job *j = sl.jobs[k];
         vc_circuit *c = j->c;
-        if (cudaMemcpyAsync(c->V[c->d], j->inputs, j->shape->n_in * sizeof(u64),
-                            j->in_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, sl.st) != cudaSuccess)
+        if (cudaMemcpyAsync(c->V[c->d], j->inputs, j->shape->n_in * sizeof(u64), cudaMemcpyDefault, sl.st) !=
+            cudaSuccess)
             return VC_ECUDA;
         sl.h_cp[k].seed = j->seed;
         sl.h_cp[k].tr = j->tr_dev ? j->transcript : c->d_tr;

@@ -195,7 +195,7 @@ static void plan_eval(vc_circuit *c)
 
 // Lay out every buffer and descriptor relative to `base` (0 for sizing) and
 // fill the circuit's single-circuit plan (circ = 0).
-static size_t layout(vc_circuit *c, uintptr_t base)
+static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
 {
     Arena A;
     A.base = base;
@@ -203,8 +203,14 @@ static size_t layout(vc_circuit *c, uintptr_t base)
     auto S = [&](u32 i) { return u64(1) << c->s[i]; };
     Plan &P = c->P;
 
+    // layer values: device memory, or host memory mapped into the device's
+    // address space (read and written by the kernels over the host link)
+    Arena H;
+    H.base = hbase;
+    const bool host = (c->flags & VC_VALUES_IN_HOST_MEMORY) != 0;
     c->V.assign(d + 1, nullptr);
-    for (u32 i = 0; i <= d; i++) c->V[i] = A.take<u64>(S(i));
+    for (u32 i = 0; i <= d; i++) c->V[i] = host ? H.take<u64>(S(i)) : A.take<u64>(S(i));
+    c->host_bytes = host ? H.off + 256 : 0;
     Globals &G = c->G;
     G = Globals{};
     G.d = d;
@@ -938,8 +944,10 @@ static bool config_ok(const PlanConfig &f)
            f.ln_chunk0 >= 1 && f.ln_chunk0 <= LN_CHUNK0_LOG && f.ev_chunk >= 1 && f.ev_chunk <= 11;
 }
 
-vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **out, const PlanConfig *cfg)
+vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **out, const PlanConfig *cfg,
+                          u32 flags)
 {
+    if (flags & ~u32(VC_VALUES_IN_HOST_MEMORY)) return VC_EINVAL;
     if (!desc || !out || desc->n_layers < 1 || desc->n_layers > 4096 || !desc->log_width || !desc->wiring)
         return VC_EINVAL;
     *out = nullptr;
@@ -954,6 +962,7 @@ vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **
         if (it != g_tuned.end()) c->cfg = it->second;
     }
     c->device = device;
+    c->flags = flags;
     c->d = desc->n_layers;
     const u32 d = c->d;
     c->s.assign(desc->log_width, desc->log_width + d + 1);
@@ -1031,7 +1040,7 @@ vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **
     plan_eval(c);
     c->P.ncirc = 1;
     Arena A;
-    A.off = layout(c, 0);
+    A.off = layout(c, 0, 0);
     plan_take(c->P, A, false);
     c->arena_bytes = A.off + 256;
     *out = c;
@@ -1046,6 +1055,7 @@ void circuit_free(vc_circuit *c)
     if (c->pg_arena) cudaFree(c->pg_arena);
     plan_release(c->P);
     if (c->arena) cudaFree(c->arena);
+    if (c->host_vals) cudaFreeHost(c->host_vals);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     delete c;
 }
@@ -1062,10 +1072,22 @@ vc_status circuit_allocate(vc_circuit *c)
         c->arena = nullptr;
         return e == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA;
     }
+    uintptr_t hbase = 0;
+    if (c->host_bytes) {
+        void *dp = nullptr;
+        e = cudaHostAlloc(&c->host_vals, c->host_bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(&dp, c->host_vals, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA;
+        }
+        memset(c->host_vals, 0, c->host_bytes);
+        hbase = reinterpret_cast<uintptr_t>(dp);
+    }
     {
         Arena A;
         A.base = reinterpret_cast<uintptr_t>(c->arena);
-        A.off = layout(c, A.base);
+        A.off = layout(c, A.base, hbase);
         plan_take(c->P, A, false);
     }
     e = cudaMemset(c->arena, 0, bytes);
@@ -1103,10 +1125,15 @@ vc_status circuit_allocate(vc_circuit *c)
 
 extern "C" vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, vc_circuit **out)
 {
+    return vc_circuit_create_ex(desc, device, 0, out);
+}
+
+extern "C" vc_status vc_circuit_create_ex(const vc_circuit_desc *desc, int device, uint32_t flags, vc_circuit **out)
+{
     if (!out) return VC_EINVAL;
     *out = nullptr;
     vc_circuit *c = nullptr;
-    vc_status st = circuit_prepare(desc, device, &c);
+    vc_status st = circuit_prepare(desc, device, &c, nullptr, flags);
     if (st != VC_OK) return st;
     st = circuit_allocate(c);
     if (st != VC_OK) {
@@ -1187,7 +1214,7 @@ extern "C" vc_status vc_prove(vc_circuit *c, const uint64_t *inputs, uint64_t se
     if (ki < 0 || kt < 0) return VC_EINVAL;
     const u64 nin = u64(1) << c->s[c->d];
     cudaError_t e = cudaMemcpyAsync(c->V[c->d], inputs, nin * sizeof(u64),
-                                    ki ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+                                    cudaMemcpyDefault, st);
     if (e != cudaSuccess) return VC_ECUDA;
     launch_params(c->d_G, seed, kt ? transcript : c->d_tr, st);
     e = plan_launch(c->P, st);
@@ -1315,7 +1342,7 @@ extern "C" vc_status vc_prove_pergate(vc_circuit *c, const uint64_t *inputs, uin
     if (s != VC_OK) return s;
     const u64 nin = u64(1) << c->s[c->d];
     cudaError_t e = cudaMemcpyAsync(c->V[c->d], inputs, nin * sizeof(u64),
-                                    ki ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+                                    cudaMemcpyDefault, st);
     if (e != cudaSuccess) return VC_ECUDA;
     launch_params(c->d_G, seed, kt ? transcript : c->d_tr, st);
     e = pergate_launch(c, st);
@@ -1345,7 +1372,7 @@ extern "C" vc_status vc_evaluate(vc_circuit *c, const uint64_t *inputs, uint64_t
     if (ki < 0 || ko < 0) return VC_EINVAL;
     const u64 nin = u64(1) << c->s[c->d];
     cudaError_t e = cudaMemcpyAsync(c->V[c->d], inputs, nin * sizeof(u64),
-                                    ki ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+                                    cudaMemcpyDefault, st);
     if (e != cudaSuccess) return VC_ECUDA;
     launch_check_canonical(c->V[c->d], nin, c->G.status, st);
     const Plan &P = c->P;
@@ -1354,7 +1381,7 @@ extern "C" vc_status vc_evaluate(vc_circuit *c, const uint64_t *inputs, uint64_t
         launch_eval_layers(P.d_G, P.d_levs, P.d_lev_items[k], (int)P.lev_items[k].size(), st);
     }
     e = cudaMemcpyAsync(outputs, c->V[0], (u64(1) << c->s[0]) * sizeof(u64),
-                        ko ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+                        cudaMemcpyDefault, st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return VC_ECUDA;
     return read_status_and_clear(c, st);
@@ -1374,7 +1401,7 @@ extern "C" vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t s
     cudaError_t e = cudaSuccess;
     const u64 *din = inputs;
     if (!ki) {
-        e = cudaMemcpyAsync(c->V[c->d], inputs, nin * sizeof(u64), cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(c->V[c->d], inputs, nin * sizeof(u64), cudaMemcpyDefault, st);
         din = c->V[c->d];
     }
     const u64 *dtr = transcript;
@@ -1655,9 +1682,7 @@ extern "C" vc_status vc_batch_prove(vc_batch *b, const uint64_t *const *inputs, 
     for (int j = 0; j < n; j++) {
         vc_circuit *c = b->members[j];
         const u64 nin = u64(1) << c->s[c->d];
-        if (cudaMemcpyAsync(c->V[c->d], inputs[j], nin * sizeof(u64),
-                            ptr_kind(inputs[j], c->device) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                            st) != cudaSuccess)
+        if (cudaMemcpyAsync(c->V[c->d], inputs[j], nin * sizeof(u64), cudaMemcpyDefault, st) != cudaSuccess)
             return VC_ECUDA;
         b->h_cp[j].seed = seeds[j];
         b->h_cp[j].tr = kt[j] ? transcripts[j] : c->d_tr;

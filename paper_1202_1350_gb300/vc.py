@@ -105,6 +105,7 @@ def lib():
             vp = ctypes.c_void_p
             st = ctypes.c_int
             L.vc_circuit_create.argtypes = [ctypes.POINTER(_Desc), ctypes.c_int, ctypes.POINTER(vp)]
+            L.vc_circuit_create_ex.argtypes = [ctypes.POINTER(_Desc), ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(vp)]
             L.vc_circuit_destroy.argtypes = [vp]
             L.vc_transcript_len.argtypes = [vp, _u64p]
             L.vc_circuit_bytes.argtypes = [vp, _u64p]
@@ -147,7 +148,8 @@ def lib():
                          "vc_circuit_get_info", "vc_batch_create", "vc_batch_destroy", "vc_batch_prove",
                          "vc_batch_sync", "vc_batch_get_info", "vc_server_create", "vc_server_destroy",
                          "vc_server_submit", "vc_server_poll", "vc_server_wait", "vc_server_get_stats",
-                         "vc_autotune", "vc_circuit_create_tiles", "vc_circuit_get_tiles", "vc_prove_pergate"):
+                         "vc_autotune", "vc_circuit_create_tiles", "vc_circuit_get_tiles", "vc_prove_pergate",
+                         "vc_circuit_create_ex"):
                 getattr(L, name).restype = st
             _lib = L
     return _lib
@@ -198,8 +200,12 @@ def _stream(stream, device: int):
 
 # --- C ABI ----------------------------------------------------------------------------
 
-def vc_circuit_create(log_width, wiring, explicit=None, device: int = 0):
-    """Returns an opaque handle (int).  explicit: per-layer (type, in1, in2) or None."""
+VC_VALUES_IN_HOST_MEMORY = 1
+
+
+def vc_circuit_create(log_width, wiring, explicit=None, device: int = 0, host_values: bool = False):
+    """Returns an opaque handle (int).  explicit: per-layer (type, in1, in2) or
+    None.  host_values: keep the layer values in mapped host memory."""
     lw = [int(x) for x in log_width]
     kinds = [int(k) for k in wiring]
     d = len(kinds)
@@ -227,7 +233,11 @@ def vc_circuit_create(log_width, wiring, explicit=None, device: int = 0):
         desc.in1 = i1s
         desc.in2 = i2s
     h = ctypes.c_void_p()
-    _check(lib().vc_circuit_create(ctypes.byref(desc), device, ctypes.byref(h)), "vc_circuit_create")
+    if host_values:
+        _check(lib().vc_circuit_create_ex(ctypes.byref(desc), device, VC_VALUES_IN_HOST_MEMORY, ctypes.byref(h)),
+               "vc_circuit_create_ex")
+    else:
+        _check(lib().vc_circuit_create(ctypes.byref(desc), device, ctypes.byref(h)), "vc_circuit_create")
     del keep
     n = ctypes.c_uint64()
     _check(lib().vc_transcript_len(h, ctypes.byref(n)), "vc_transcript_len")

@@ -1,0 +1,107 @@
+"""Layer values in mapped host memory (VC_VALUES_IN_HOST_MEMORY): the same
+transcripts, accept bits and outputs as with device-resident values, and less
+device memory."""
+import numpy as np
+import pytest
+
+from gpu_util import ensure_built, oracle_prove, to_np
+from paper_1202_1350_gb300 import circuits, vc
+from paper_1202_1350_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(x, np.uint64)).view(np.int64).copy()).cuda()
+
+
+def prove(h, x, seed, host_tr=False):
+    n = vc.vc_transcript_len(h)
+    if host_tr:
+        tr = np.zeros(n, np.uint64)
+        vc.vc_prove(h, np.ascontiguousarray(x), seed, tr)
+        return tr
+    tr = torch.empty(n, dtype=torch.int64, device="cuda")
+    vc.vc_prove(h, dev(x), seed, tr)
+    vc.vc_circuit_sync(h)
+    return to_np(tr)
+
+
+CASES = [("f2", 0), ("f2", 5), ("f2", 12), ("f0", 3), ("matmult", 3)]
+
+
+@pytest.mark.parametrize("family,logn", CASES)
+def test_host_values_equal_oracle(family, logn):
+    w, k = circuits.by_name(family, logn)
+    x = I.job_inputs(family, logn, 80 + logn)
+    h = vc.vc_circuit_create(w, k, host_values=True)
+    try:
+        want = oracle_prove(w, k, x, 13)
+        assert (prove(h, x, 13) == want).all()
+        assert (prove(h, x, 13, host_tr=True) == want).all()
+        assert vc.vc_verify(h, dev(x), 13, dev(want))
+    finally:
+        vc.vc_circuit_destroy(h)
+
+
+def test_host_values_explicit_and_pergate():
+    w, k, ex = circuits.pattern_match(5, 2)
+    x = I.pm_inputs(5, 2, 9)
+    h = vc.vc_circuit_create(w, k, ex, host_values=True)
+    try:
+        want = oracle_prove(w, k, x, 5, explicit=ex)
+        assert (prove(h, x, 5) == want).all()
+        tr = torch.empty(len(want), dtype=torch.int64, device="cuda")
+        vc.vc_prove_pergate(h, dev(x), 5, tr)
+        vc.vc_circuit_sync(h)
+        assert (to_np(tr) == want).all()
+    finally:
+        vc.vc_circuit_destroy(h)
+
+
+def test_host_values_large_equal_device_and_smaller_footprint():
+    w, k = circuits.f2(18)
+    x = I.f2_inputs(18, 1 << 16, 4)
+    hd = vc.vc_circuit_create(w, k)
+    hh = vc.vc_circuit_create(w, k, host_values=True)
+    try:
+        assert (prove(hh, x, 77) == prove(hd, x, 77)).all()
+        assert vc.vc_circuit_bytes(hh) < vc.vc_circuit_bytes(hd) - 8 * (1 << 19)
+    finally:
+        vc.vc_circuit_destroy(hd)
+        vc.vc_circuit_destroy(hh)
+
+
+def test_host_values_in_a_batch():
+    specs = [("f2", 9), ("matmult", 2), ("f2", 4)]
+    hs, xs = [], []
+    for j, (fam, n) in enumerate(specs):
+        w, k = circuits.by_name(fam, n)
+        hs.append(vc.vc_circuit_create(w, k, host_values=(j != 1)))
+        xs.append(I.job_inputs(fam, n, 90 + j))
+    b = vc.vc_batch_create(hs)
+    try:
+        trs = [torch.empty(vc.vc_transcript_len(h), dtype=torch.int64, device="cuda") for h in hs]
+        vc.vc_batch_prove(b, [dev(x) for x in xs], [3, 4, 5], trs)
+        vc.vc_batch_sync(b)
+        for j, (fam, n) in enumerate(specs):
+            w, k = circuits.by_name(fam, n)
+            assert (to_np(trs[j]) == oracle_prove(w, k, xs[j], 3 + j)).all()
+    finally:
+        vc.vc_batch_destroy(b)
+        for h in hs:
+            vc.vc_circuit_destroy(h)
+
+
+def test_bad_flags_rejected():
+    import ctypes
+    w, k = circuits.f2(3)
+    desc, keep = vc._desc_struct(w, k)
+    h = ctypes.c_void_p()
+    assert vc.lib().vc_circuit_create_ex(ctypes.byref(desc), 0, 6, ctypes.byref(h)) == vc.VC_EINVAL
