@@ -10,7 +10,9 @@ The circuit descriptions below are this package's own restatement of the
 paper's benchmark circuits (Sec. 6.2.1): F2 (a squaring layer then a binary
 addition tree), F0 (Fermat power x^(p-1) then a tree), MatMult (one layer of
 n^3 products then a tree over the summation index), pattern matching and the
-single-output MatMult check (both with the F0 subcircuit).
+single-output MatMult check (both with the F0 subcircuit); and the
+special-purpose non-interactive F2 protocol (a v x h grid, rows extended as
+polynomials, the proof s(Y) = sum of squared row extensions).
 """
 from __future__ import annotations
 
@@ -95,6 +97,10 @@ def lib():
             L.or_verify.restype = ctypes.c_int
             L.or_verify.argtypes = [ctypes.c_void_p, _u64p, fe, _u64p,
                                     ctypes.POINTER(ctypes.c_int)]
+            L.or_f2sp_prove.restype = ctypes.c_int
+            L.or_f2sp_prove.argtypes = [_u64p, fe, fe, _u64p]
+            L.or_f2sp_verify.restype = ctypes.c_int
+            L.or_f2sp_verify.argtypes = [_u64p, fe, fe, fe, _u64p, _u64p]
             L.or_wiring_eval.restype = None
             L.or_wiring_eval.argtypes = [ctypes.c_void_p, ctypes.c_int, _u64p, _u64p, _u64p,
                                          _u64p, _u64p]
@@ -185,6 +191,32 @@ def matmult_layers(logn: int):
     log_width = [2 * L + j for j in range(0, L + 1)] + [2 * L + 1]
     kinds = [TREE] * L + [MATMULT]
     return log_width, kinds
+
+
+# --- special-purpose non-interactive F2 protocol (Sec. 2.3, 4.2, 6.3) ------------
+
+def f2sp_prove(a, v: int, h: int) -> np.ndarray:
+    """The proof of the special-purpose F2 protocol for the v x h grid a (row
+    x at a[x h : x h + h]): s(Y) = sum_x f_x(Y)^2 at Y = 0..2h-2, f_x the
+    degree < h extension of row x."""
+    x = _arr(a)
+    assert len(x) == v * h
+    out = np.zeros(2 * h - 1, np.uint64)
+    if lib().or_f2sp_prove(_p64(x), v, h, _p64(out)) != 0:
+        raise ValueError("non-canonical input")
+    return out
+
+
+def f2sp_verify(a, v: int, h: int, seed: int, proof):
+    """(accept, F2 answer) of the verifier with the secret point r drawn from seed."""
+    x = _arr(a)
+    pr = _arr(proof)
+    assert len(x) == v * h and len(pr) == 2 * h - 1
+    f2 = np.zeros(1, np.uint64)
+    rc = lib().or_f2sp_verify(_p64(x), v, h, seed, _p64(pr), _p64(f2))
+    if rc < 0:
+        raise ValueError("non-canonical input")
+    return bool(rc), int(f2[0])
 
 
 def pm_layers(log_n: int, log_q: int):

@@ -757,3 +757,91 @@ int or_verify(const or_circuit *c, const fe *inputs, uint64_t seed, const fe *tr
     if (fail_layer) *fail_layer = ok ? -1 : where;
     return ok;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Special-purpose non-interactive F2 protocol (Sec. 2.3 outline, Sec. 4.2,   */
+/* Sec. 6.3; the protocol of Chakrabarti et al. as implemented by CMT).       */
+/*                                                                           */
+/* The frequency vector a (n = v h entries) is a v x h grid, a(x, y) at      */
+/* x h + y.  Row x is extended in y by the polynomial f_x of degree < h with */
+/* f_x(y) = a(x, y) for y = 0..h-1.  The proof is the polynomial             */
+/* s(Y) = sum_x f_x(Y)^2 (degree <= 2h - 2) given by its values at           */
+/* Y = 0..2h-2.  The verifier keeps f_x(r) for a secret random r (one value  */
+/* per row, v words), accepts iff s(r) = sum_x f_x(r)^2, and then reads      */
+/* F2 = sum_x sum_y a(x,y)^2 = sum_{y<h} s(y).  Readings: nodes 0..h-1 for   */
+/* the data and 0..2h-2 for the proof; r is challenge 0 of the seed's        */
+/* stream (the coins of the GKR part).                                       */
+/*                                                                           */
+/* Everything below is the definition: Lagrange basis values as products,   */
+/* no FFT, no barycentric shortcut.                                          */
+/* ------------------------------------------------------------------------- */
+
+/* L_y(m) over the nodes 0..k-1: prod_{j != y} (m - j) / (y - j). */
+static fe lagrange_basis(uint64_t k, uint64_t y, fe m)
+{
+    fe num = 1, den = 1;
+    for (uint64_t j = 0; j < k; j++) {
+        if (j == y) continue;
+        num = or_mul(num, or_sub(m, j));
+        den = or_mul(den, or_sub(y, j));
+    }
+    return or_mul(num, or_inv(den));
+}
+
+/* Value at m of the polynomial through (j, vals[j]), j = 0..k-1. */
+static fe lagrange_eval(const fe *vals, uint64_t k, fe m)
+{
+    fe s = 0;
+    for (uint64_t y = 0; y < k; y++) s = or_add(s, or_mul(vals[y], lagrange_basis(k, y, m)));
+    return s;
+}
+
+/* Prover: proof[Y] = s(Y) for Y = 0..2h-2.  Returns -1 for a non-canonical
+ * entry of a (or h = 0). */
+int or_f2sp_prove(const fe *a, uint64_t v, uint64_t h, fe *proof)
+{
+    if (h == 0) return -1;
+    for (uint64_t i = 0; i < v * h; i++)
+        if (a[i] >= OR_P) return -1;
+    const uint64_t np = 2 * h - 1;
+    fe *L = (fe *)malloc(sizeof(fe) * h * np); /* L[m h + y] = L_y(m) */
+    for (uint64_t m = 0; m < np; m++)
+        for (uint64_t y = 0; y < h; y++) L[m * h + y] = lagrange_basis(h, y, m);
+    for (uint64_t m = 0; m < np; m++) proof[m] = 0;
+    for (uint64_t x = 0; x < v; x++) {
+        const fe *row = a + x * h;
+        for (uint64_t m = 0; m < np; m++) {
+            fe f = 0;
+            for (uint64_t y = 0; y < h; y++) f = or_add(f, or_mul(row[y], L[m * h + y]));
+            proof[m] = or_add(proof[m], or_mul(f, f));
+        }
+    }
+    free(L);
+    return 0;
+}
+
+/* Verifier: r from the seed; f_x(r) for every row; s(r) from the proof by
+ * Lagrange interpolation over 0..2h-2.  Returns 1 (accept) or 0, and the
+ * answer sum_{y<h} s(y) in *f2; -1 for a non-canonical entry of a or h = 0.
+ * A proof entry >= p is a rejection. */
+int or_f2sp_verify(const fe *a, uint64_t v, uint64_t h, uint64_t seed, const fe *proof, fe *f2)
+{
+    if (h == 0) return -1;
+    for (uint64_t i = 0; i < v * h; i++)
+        if (a[i] >= OR_P) return -1;
+    const uint64_t np = 2 * h - 1;
+    for (uint64_t m = 0; m < np; m++)
+        if (proof[m] >= OR_P) return 0;
+    fe r;
+    or_draw_challenges(seed, 1, &r);
+    fe lhs = 0;
+    for (uint64_t x = 0; x < v; x++) {
+        const fe fr = lagrange_eval(a + x * h, h, r);
+        lhs = or_add(lhs, or_mul(fr, fr));
+    }
+    const fe rhs = lagrange_eval(proof, np, r);
+    fe ans = 0;
+    for (uint64_t y = 0; y < h; y++) ans = or_add(ans, proof[y]);
+    *f2 = ans;
+    return lhs == rhs ? 1 : 0;
+}

@@ -512,3 +512,53 @@ def test_pm_and_mm1_wiring_equals_the_packages_description():
             if x is not None:
                 for u, v in zip(x, y):
                     assert np.array_equal(np.asarray(u, np.int64), np.asarray(v, np.int64))
+
+
+# --- the special-purpose non-interactive F2 protocol (Sec. 2.3, 4.2, 6.3) ----------
+
+def _sympy_extension(row, m):
+    """Value at m of the degree < h polynomial through (y, row[y]), by exact
+    rational interpolation (sympy), reduced mod p: an independent method."""
+    sympy = pytest.importorskip("sympy")
+    X = sympy.Symbol("X")
+    poly = sympy.interpolate([(y, int(row[y])) for y in range(len(row))], X)
+    val = sympy.Rational(poly.subs(X, m))
+    return int(val.p) * pow(int(val.q), -1, P) % P
+
+
+@pytest.mark.parametrize("v,h,seed", [(1, 1, 1), (1, 2, 2), (2, 3, 3), (4, 4, 4), (3, 7, 5), (8, 8, 6)])
+def test_f2sp_proof_against_sympy_interpolation(v, h, seed):
+    """s(Y) = sum_x f_x(Y)^2 with f_x the interpolant of row x, f_x computed by
+    sympy's exact rational interpolation; s(y) for y < h is the column's sum
+    of squares and sum_{y<h} s(y) = F2."""
+    rng = np.random.default_rng(seed)
+    a = rng.integers(0, 1000, v * h).astype(np.uint64)
+    proof = oracle.f2sp_prove(a, v, h)
+    for m in range(2 * h - 1):
+        want = sum(_sympy_extension(a[x * h:(x + 1) * h], m) ** 2 for x in range(v)) % P
+        assert int(proof[m]) == want
+    grid = a.astype(object).reshape(v, h)
+    for y in range(h):
+        assert int(proof[y]) == int((grid[:, y] ** 2).sum()) % P
+    assert sum(int(t) for t in proof[:h]) % P == int((grid ** 2).sum()) % P
+
+
+@pytest.mark.parametrize("v,h", [(1, 1), (5, 3), (16, 16), (10, 33)])
+def test_f2sp_complete_and_sound(v, h):
+    rng = np.random.default_rng(v * 100 + h)
+    a = rng.integers(0, 1 << 16, v * h).astype(np.uint64)
+    proof = oracle.f2sp_prove(a, v, h)
+    f2 = int((a.astype(object) ** 2).sum()) % P
+    for seed in range(1, 9):
+        assert oracle.f2sp_verify(a, v, h, seed, proof) == (True, f2)
+    for m in range(len(proof)):  # every single-entry change
+        bad = proof.copy()
+        bad[m] = (int(bad[m]) + 1 + m) % P
+        assert not oracle.f2sp_verify(a, v, h, 3, bad)[0]
+    bad = proof.copy()
+    bad[0] = P  # a non-canonical entry is a rejection
+    assert not oracle.f2sp_verify(a, v, h, 3, bad)[0]
+    # a different input is caught by the verifier's secret point
+    b = a.copy()
+    b[len(b) // 2] += np.uint64(1)
+    assert not oracle.f2sp_verify(b, v, h, 3, proof)[0]
