@@ -211,6 +211,49 @@ def run_residency(widths, kinds, xd, flush, reps=5):
     return out
 
 
+def run_special_purpose(flush, shapes=((1024, 1024), (5000, 5000)), reps=3):
+    """The special-purpose non-interactive F2 protocol: prover and streaming
+    verifier times for a v x h grid of frequencies uniform in [0, 2^16]
+    (n = 2^20, and the paper's n = 25 million with v = h = 5000, Sec. 6.3);
+    the answer is checked against sum a_i^2."""
+    import torch
+    from paper_1202_1350_gb300 import vc
+    from paper_1202_1350_gb300 import inputs as I
+    P = (1 << 61) - 1
+    out = []
+    for v, h in shapes:
+        a = I.uniform_ints(SEED_SP + v, v * h, 1 << 16)
+        ad = torch.from_numpy(a.view(np.int64)).cuda()
+        proof = torch.empty(2 * h - 1, dtype=torch.int64, device="cuda")
+        s = vc.vc_f2sp_create(v, h)
+        pt, vt = [], []
+        ok = True
+        for k in range(reps + 1):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            vc.vc_f2sp_prove(s, ad, proof)
+            t1 = time.perf_counter()
+            vc.vc_f2sp_verify_begin(s, 77 + k)
+            vc.vc_f2sp_verify_absorb(s, ad, 0, v)
+            acc, f2 = vc.vc_f2sp_verify_end(s, proof)
+            t2 = time.perf_counter()
+            ok &= acc
+            if k >= 1:
+                pt.append(1000 * (t1 - t0))
+                vt.append(1000 * (t2 - t1))
+        vc.vc_f2sp_destroy(s)
+        want = int((a.astype(object) ** 2).sum()) % P
+        out.append({"n": v * h, "v": v, "h": h, "prove_ms": statistics.median(pt),
+                    "verify_ms": statistics.median(vt), "accepted": bool(ok), "answer_ok": f2 == want,
+                    "proof_words": 2 * h - 1, "verifier_words": v})
+        del ad
+    return out
+
+
+SEED_SP = 0xC0FFEE + 7
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -376,10 +419,11 @@ def run_ours(args):
                 except RuntimeError:  # a stage with no work records nothing
                     pass
     vc.vc_circuit_set_stage_events(h, None)
-    ablation = residency = None
+    ablation = residency = special = None
     if not args.no_ablation:
         ablation = run_ablation(h, xd, tr, flush)
         residency = run_residency(widths, kinds, xd, flush)
+        special = run_special_purpose(flush)
     vc.vc_prove(h, xh, 999, trh)
     e2e_ms = []
     for k in range(max(3, args.steps // 2)):
@@ -434,6 +478,7 @@ def run_ours(args):
         "stage_ms": stages,
         "ablation": ablation,
         "residency": residency,
+        "special_purpose_f2": special,
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -601,7 +646,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-ablation", action="store_true",
-                    help="skip the per-gate prover and host-residency comparisons")
+                    help="skip the per-gate prover, host-residency and special-purpose protocol measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")

@@ -340,6 +340,40 @@ vc_status vc_server_wait(vc_server *s, uint64_t job_id, vc_job_info *info);
 
 vc_status vc_server_get_stats(vc_server *s, vc_server_stats *stats);
 
+/* ---- Special-purpose non-interactive F2 protocol (Sec. 2.3; Sec. 4.2;
+ * Sec. 6.3).  The frequency vector a of n = v h entries is a v x h grid,
+ * a(x, y) at x h + y (row-major).  Row x is the polynomial f_x of degree < h
+ * with f_x(y) = a(x, y) at y = 0..h-1.  The proof is s(Y) = sum_x f_x(Y)^2 at
+ * Y = 0..2h-2 (2h - 1 u64): proof length about 2h words, verifier space v
+ * words.  The verifier keeps f_x(r) for a secret random r (drawn from its
+ * seed like the GKR coins: the first accepted splitmix64 draw), accepts iff
+ * s(r) = sum_x f_x(r)^2, and answers F2 = sum_{y<h} s(y).  No interaction.
+ * Inputs must be canonical (< p). */
+typedef struct vc_f2sp vc_f2sp;
+#define VC_F2SP_MAX_H 8192u
+
+/* Node tables for h and scratch for v rows on `device`.  VC_EINVAL: v = 0,
+ * h = 0 or h > VC_F2SP_MAX_H. */
+vc_status vc_f2sp_create(uint64_t v, uint64_t h, int device, vc_f2sp **out);
+vc_status vc_f2sp_destroy(vc_f2sp *s);
+
+/* Prover: proof[Y] = s(Y), Y = 0..2h-2, for the v h entries at `a` (host or
+ * device).  Synchronous; VC_EINVAL for an entry >= p (the proof is then
+ * undefined). */
+vc_status vc_f2sp_prove(vc_f2sp *s, const uint64_t *a, uint64_t *proof, void *stream);
+
+/* Streaming verifier: begin draws r from `seed` and clears the row values;
+ * absorb adds the contribution of whole rows [first_row, first_row + nrows)
+ * given contiguously at `rows` (host or device; a row may be absorbed in
+ * several parts as additive updates of its counts); end checks `proof`
+ * (2h - 1 u64, host or device), sets *accept (1 or 0; an entry >= p is a
+ * rejection) and *f2 = sum_{y<h} proof[y], synchronously.  VC_EINVAL from end
+ * if an absorbed entry was >= p. */
+vc_status vc_f2sp_verify_begin(vc_f2sp *s, uint64_t seed, void *stream);
+vc_status vc_f2sp_verify_absorb(vc_f2sp *s, const uint64_t *rows, uint64_t first_row, uint64_t nrows,
+                                void *stream);
+vc_status vc_f2sp_verify_end(vc_f2sp *s, const uint64_t *proof, uint64_t *f2, int *accept, void *stream);
+
 /* Elementwise field product out[k] = a[k] b[k] mod p on the device (device
  * pointers, n elements, canonical inputs).  Used to check the device field
  * arithmetic.  Asynchronous. */

@@ -35,11 +35,13 @@ void init_device_once(int device)
     if (device < 0 || device >= 64) {
         prove_kernels_init();
         waves_init();
+        sp_init();
         return;
     }
     if (!done[device]) {
         prove_kernels_init();
         waves_init();
+        sp_init();
         done[device] = true;
     }
 }

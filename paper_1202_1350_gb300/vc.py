@@ -112,6 +112,13 @@ def lib():
             L.vc_evaluate.argtypes = [vp, vp, vp, vp]
             L.vc_prove.argtypes = [vp, vp, ctypes.c_uint64, vp, vp]
             L.vc_prove_pergate.argtypes = [vp, vp, ctypes.c_uint64, vp, vp]
+            L.vc_f2sp_create.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(vp)]
+            L.vc_f2sp_destroy.argtypes = [vp]
+            L.vc_f2sp_prove.argtypes = [vp, vp, vp, vp]
+            L.vc_f2sp_verify_begin.argtypes = [vp, ctypes.c_uint64, vp]
+            L.vc_f2sp_verify_absorb.argtypes = [vp, vp, ctypes.c_uint64, ctypes.c_uint64, vp]
+            L.vc_f2sp_verify_end.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int),
+                                             vp]
             L.vc_circuit_sync.argtypes = [vp, vp]
             L.vc_verify.argtypes = [vp, vp, ctypes.c_uint64, vp, ctypes.POINTER(ctypes.c_int), vp]
             L.vc_prove_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), _u64p, ctypes.POINTER(vp),
@@ -149,7 +156,8 @@ def lib():
                          "vc_batch_sync", "vc_batch_get_info", "vc_server_create", "vc_server_destroy",
                          "vc_server_submit", "vc_server_poll", "vc_server_wait", "vc_server_get_stats",
                          "vc_autotune", "vc_circuit_create_tiles", "vc_circuit_get_tiles", "vc_prove_pergate",
-                         "vc_circuit_create_ex"):
+                         "vc_circuit_create_ex", "vc_f2sp_create", "vc_f2sp_destroy", "vc_f2sp_prove",
+                         "vc_f2sp_verify_begin", "vc_f2sp_verify_absorb", "vc_f2sp_verify_end"):
                 getattr(L, name).restype = st
             _lib = L
     return _lib
@@ -293,6 +301,51 @@ def vc_prove_pergate(h, inputs, seed: int, transcript, stream=None, device: int 
     _check(lib().vc_prove_pergate(h, _ptr(inputs), seed & 0xFFFFFFFFFFFFFFFF, _ptr(transcript),
                                   _stream(stream, device)), "vc_prove_pergate")
     return transcript
+
+
+# ---- special-purpose non-interactive F2 protocol ---------------------------------------
+
+def vc_f2sp_create(v: int, h: int, device: int = 0):
+    s = ctypes.c_void_p()
+    _check(lib().vc_f2sp_create(v, h, device, ctypes.byref(s)), "vc_f2sp_create")
+    _shapes[("f2sp", s.value)] = (v, h)
+    return s.value
+
+
+def vc_f2sp_destroy(s):
+    _shapes.pop(("f2sp", s), None)
+    _check(lib().vc_f2sp_destroy(s), "vc_f2sp_destroy")
+
+
+def vc_f2sp_prove(s, a, proof, stream=None, device: int = 0):
+    """proof: 2h - 1 entries (host or device), written synchronously."""
+    v, h = _shapes[("f2sp", s)]
+    _need(a, v * h, "a")
+    _need(proof, 2 * h - 1, "proof")
+    _check(lib().vc_f2sp_prove(s, _ptr(a), _ptr(proof), _stream(stream, device)), "vc_f2sp_prove")
+    return proof
+
+
+def vc_f2sp_verify_begin(s, seed: int, stream=None, device: int = 0):
+    _check(lib().vc_f2sp_verify_begin(s, seed & 0xFFFFFFFFFFFFFFFF, _stream(stream, device)), "vc_f2sp_verify_begin")
+
+
+def vc_f2sp_verify_absorb(s, rows, first_row: int, nrows: int, stream=None, device: int = 0):
+    v, h = _shapes[("f2sp", s)]
+    _need(rows, nrows * h, "rows")
+    _check(lib().vc_f2sp_verify_absorb(s, _ptr(rows), first_row, nrows, _stream(stream, device)),
+           "vc_f2sp_verify_absorb")
+
+
+def vc_f2sp_verify_end(s, proof, stream=None, device: int = 0):
+    """Returns (accept, F2 answer)."""
+    v, h = _shapes[("f2sp", s)]
+    _need(proof, 2 * h - 1, "proof")
+    f2 = ctypes.c_uint64()
+    acc = ctypes.c_int()
+    _check(lib().vc_f2sp_verify_end(s, _ptr(proof), ctypes.byref(f2), ctypes.byref(acc), _stream(stream, device)),
+           "vc_f2sp_verify_end")
+    return bool(acc.value), f2.value
 
 
 def vc_circuit_sync(h, stream=None, device: int = 0):
