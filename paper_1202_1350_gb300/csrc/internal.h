@@ -153,7 +153,6 @@ struct vc_circuit {
     VerifyDev Vd{};
     VerifyPtrs *d_vp = nullptr;        // per-call verifier pointers (device)
     cudaGraphExec_t vexec = nullptr;   // the verifier's captured launches
-    EqTab tzd{};
     std::vector<u32> explicit_layers;
     u32 *d_explicit_layers = nullptr;
     std::vector<u32> round_layer, zmap;

@@ -8,36 +8,73 @@
 // layers are checked concurrently, one thread per layer.  The accept bit is the
 // conjunction of exactly the checks the sequential verifier makes.
 #include <cuda_runtime.h>
-#include "plan.h"
+#include "coins.cuh"
 
 #define VM_NT 256
+#define VM_MID 4  // at most 2^4 iterations per thread: a CTA covers at most 2^12 entries
 
 // Partial sums of the two multilinear extensions the verifier needs: the
 // input's at z_d (blocks [0, nin_blocks)) and the claimed outputs' at z_0 (the
 // remaining blocks).  Every value contributes independently (Sec. 4.1.2);
-// products accumulate exactly in 128 bits.  A non-canonical input latches
-// ST_BAD_INPUT; a non-canonical output entry marks the transcript bad.
-__global__ void __launch_bounds__(VM_NT) k_vmle(const EqTab tzd, const VerifyPtrs *vp, u64 n, const EqTab tz0,
-                                                u64 nout, u32 nin_blocks, u64 *part, u32 *status, u64 *result)
+// products accumulate exactly in 128 bits.  A CTA takes an aligned range of
+// 2^lr entries and derives the point's coordinates from the seed itself, so
+// the launch needs no eq table and does not wait for the coin launch:
+// eq(z, i) = (coordinates above the range: per CTA) x (the low min(8, lr):
+// per thread, from two 16-entry tables) x (the rest: per iteration, from a
+// small table).  A non-canonical input latches ST_BAD_INPUT; a non-canonical
+// output entry marks the transcript bad.
+__global__ void __launch_bounds__(VM_NT) k_vmle(const Globals *Gd, const VerifyPtrs *vp, u32 nd, u32 lin, u32 n0,
+                                                u32 lout, u32 nin_blocks, u64 *part, u32 *status, u64 *result)
 {
+    const Globals &G = *Gd;
     const bool inp = blockIdx.x < nin_blocks;
-    const EqTab &tz = inp ? tzd : tz0;
-    const u64 *src = inp ? vp->inputs : vp->tr;  // the claimed outputs open the transcript
-    const u64 cnt = inp ? n : nout;
+    const u32 nz = inp ? nd : n0, lr = inp ? lin : lout;
     const u32 b = inp ? blockIdx.x : blockIdx.x - nin_blocks;
-    const u32 nb = inp ? nin_blocks : gridDim.x - nin_blocks;
+    const u64 *src = inp ? vp->inputs : vp->tr;  // the claimed outputs open the transcript
+    __shared__ u64 z[32], zm[32], mid[1u << VM_MID], t1[16], t2[16], bfac;
+    const bool rej = draws_rejected(G);
+    if (threadIdx.x < nz) {
+        const u64 v = zcoord(G, rej, inp ? G.d : 0, threadIdx.x);
+        z[threadIdx.x] = v;
+        zm[threadIdx.x] = f_sub(1, v);
+    }
+    __syncthreads();
+    // small factor tables, each entry a product of at most four factors:
+    // t1 over coordinates [0, l1), t2 over [l1, lo), mid over [lo, lr); and
+    // the CTA's factor over [lr, nz) as a warp product
+    const u32 lo = lr < 8 ? lr : 8, nit = 1u << (lr - lo), l1 = lo < 4 ? lo : 4, l2 = lo - l1;
+    const u32 tid = threadIdx.x;
+    if (tid < 16) {
+        u64 f = 1;
+        for (u32 k = 0; k < l1; k++) f = f_mul(f, ((tid >> k) & 1) ? z[k] : zm[k]);
+        t1[tid] = f;
+    } else if (tid < 32) {
+        const u32 q = tid - 16;
+        u64 f = 1;
+        for (u32 k = 0; k < l2; k++) f = f_mul(f, ((q >> k) & 1) ? z[l1 + k] : zm[l1 + k]);
+        t2[q] = f;
+    } else if (tid < 32 + nit) {
+        const u32 q = tid - 32;
+        u64 f = 1;
+        for (u32 k = lo; k < lr; k++) f = f_mul(f, ((q >> (k - lo)) & 1) ? z[k] : zm[k]);
+        mid[q] = f;
+    } else if (tid >= 64 && tid < 96) {
+        const u32 k = lr + (tid - 64);
+        const u64 f = (k < nz) ? (((b >> (k - lr)) & 1) ? z[k] : zm[k]) : 1;
+        const u64 pr = warp_prod(f);
+        if (tid == 64) bfac = pr;
+    }
+    __syncthreads();
     acc128 acc;
     acc_zero(acc);
     bool bad = false;
-    u32 k = 0;
-    for (u64 i = b * (u64)VM_NT + threadIdx.x; i < cnt; i += (u64)nb * VM_NT, k++) {
-        const u64 v = src[i];
-        bad |= (v >= FP_P);
-        mac(acc, eq_at(tz, i), v >= FP_P ? 0 : v);
-        if ((k & 31) == 31) {  // keep the accumulator well below 2^128
-            const u64 r = acc_red(acc);
-            acc.lo = r;
-            acc.hi = 0;
+    if (tid < (1u << lo)) {
+        const u64 w = f_mul(f_mul(t1[tid & 15], t2[tid >> 4]), bfac);
+        const u64 base = ((u64)b << lr) + tid;
+        for (u32 it = 0; it < nit; it++) {
+            const u64 v = src[base + ((u64)it << lo)];
+            bad |= (v >= FP_P);
+            mac(acc, f_mul(w, mid[it]), v >= FP_P ? 0 : v);
         }
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) {
@@ -359,12 +396,18 @@ void launch_vparams(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *tr, const u
     k_vparams<<<1, 1, 0, st>>>(G, vp, seed, tr, inputs, accept);
 }
 
-void launch_verify(const Globals &G, const VerifyDev &V, const EqTab &tzd, const EqTab &tz0,
-                   const u32 *explicit_layers, int n_explicit, cudaStream_t st)
+// Entries per CTA (log2) of the MLE partial sums for a point of n coordinates.
+u32 vmle_log(u32 n) { return n < 11 ? n : 11; }
+
+void launch_verify(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0, const u32 *explicit_layers,
+                   int n_explicit, cudaStream_t st_mle, cudaEvent_t ev_join, cudaStream_t st)
 {
-    const u64 nin = 1ull << tzd.n, nout = 1ull << tz0.n;
-    k_vmle<<<V.mle_blocks + V.mle_out_blocks, VM_NT, 0, st>>>(tzd, V.vp, nin, tz0, nout, V.mle_blocks, V.mle_part,
-                                                              G.status, V.result);
+    // the MLE partial sums need only the seed: they run beside the coin launch
+    // (st_mle forked from st before it); the checks wait for both
+    k_vmle<<<V.mle_blocks + V.mle_out_blocks, VM_NT, 0, st_mle>>>(Gd, V.vp, nd, vmle_log(nd), n0, vmle_log(n0),
+                                                                   V.mle_blocks, V.mle_part, G.status, V.result);
+    cudaEventRecord(ev_join, st_mle);
+    cudaStreamWaitEvent(st, ev_join, 0);
     if (n_explicit > 0) k_vwire<<<n_explicit, VM_NT, 0, st>>>(G, explicit_layers, V.wire);
     const u64 threads = 32ull * G.d + V.nrounds;
     u64 blocks = (threads + VC_NT - 1) / VC_NT;

@@ -330,8 +330,12 @@ struct VerifyDev {
 void launch_init_invfact(u64 *invfact, cudaStream_t st);
 void launch_vparams(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *tr, const u64 *inputs, int *accept,
                     cudaStream_t st);
-void launch_verify(const Globals &G, const VerifyDev &V, const EqTab &tzd, const EqTab &tz0,
-                   const u32 *explicit_layers, int n_explicit, cudaStream_t st);
+// The verifier's launches after its coin launch was issued on st: the MLE
+// partial sums on st_mle (forked from st before the coins, so both run
+// together), joined back into st through ev_join, then the checks.
+u32 vmle_log(u32 n);
+void launch_verify(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0, const u32 *explicit_layers,
+                   int n_explicit, cudaStream_t st_mle, cudaEvent_t ev_join, cudaStream_t st);
 
 // Per-gate prover (k_pergate.cu): one descriptor per layer.
 struct PgLayer {

@@ -278,9 +278,6 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
             c->eq_verify.push_back({L.tr2, 0u, EQ_SRC_CHAL, L.chal_off + L.s + L.sn, 0u});
         }
     }
-    c->tzd = take_eq(A, G.pts + c->zd_off, c->s[d]);
-    c->eq_verify.push_back({c->tzd, 0u, EQ_SRC_Z, 0u, d});
-    c->eq_verify.push_back({c->L[0].tz, 0u, EQ_SRC_Z, 0u, 0u});
 
     // Waves.  A wave is one launch's share of an instance: chunks of 2^nr
     // entries (2^nl coordinates for the line reduction).  A wave followed by a
@@ -482,13 +479,10 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     sort_tasks(P);
 
     // verifier scratch
-    const u64 Sd = S(d);
-    u64 mb = (Sd + 255) / 256;
-    if (mb > 152 * 4) mb = 152 * 4;
-    if (mb == 0) mb = 1;
+    // MLE partial sums: one CTA per 2^vmle_log(s) entries
+    const u64 mb = u64(1) << (c->s[d] - vmle_log(c->s[d]));
+    const u64 mbo = u64(1) << (c->s[0] - vmle_log(c->s[0]));
     c->Vd.mle_blocks = (u32)mb;
-    u64 mbo = (S(0) + 255) / 256;
-    if (mbo > 64) mbo = 64;
     c->Vd.mle_out_blocks = (u32)mbo;
     c->Vd.mle_part = A.take<u64>(mb + mbo);
     c->Vd.counter = A.take<unsigned int>(4);
@@ -1420,8 +1414,11 @@ extern "C" vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t s
         if (e != cudaSuccess) return VC_ECUDA;
         cudaStream_t cs = c->P.cap;
         cudaMemsetAsync(c->d_result, 0, 8 * sizeof(u64), cs);
+        cudaEventRecord(c->P.ev_fork, cs);
+        cudaStreamWaitEvent(c->P.aux, c->P.ev_fork, 0);
         launch_coins(c->d_G, 1, c->d_eq_verify, (int)c->eq_verify.size(), nullptr, nullptr, 0, cs);
-        launch_verify(c->G, c->Vd, c->tzd, c->L[0].tz, c->d_explicit_layers, (int)c->explicit_layers.size(), cs);
+        launch_verify(c->d_G, c->G, c->Vd, c->s[c->d], c->s[0], c->d_explicit_layers,
+                      (int)c->explicit_layers.size(), c->P.aux, c->P.ev_tables, cs);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = cudaGraphInstantiate(&c->vexec, g, 0);
