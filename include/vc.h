@@ -136,7 +136,7 @@ vc_status vc_prove(vc_circuit *c, const uint64_t *inputs, uint64_t seed,
                    uint64_t *transcript, void *stream);
 
 /* The same proof computed the way the paper's GPU prover computes it
- * (Sec. 4.1.1; Sec. 4.2, "Memory access"): in every round one thread per gate
+ * (Sec. 4.1.1; memory access in Sec. 5.1.4): in every round one thread per gate
  * adds that gate's independent contribution to the message, O(S log S) work
  * per layer, instead of folding tables.  The transcript is identical to
  * vc_prove's; arguments, asynchrony and errors are vc_prove's.  The first call
@@ -340,7 +340,7 @@ vc_status vc_server_wait(vc_server *s, uint64_t job_id, vc_job_info *info);
 
 vc_status vc_server_get_stats(vc_server *s, vc_server_stats *stats);
 
-/* ---- Special-purpose non-interactive F2 protocol (Sec. 2.3; Sec. 4.2;
+/* ---- Special-purpose non-interactive F2 protocol (Sec. 3.2; Sec. 4.2;
  * Sec. 6.3).  The frequency vector a of n = v h entries is a v x h grid,
  * a(x, y) at x h + y (row-major).  Row x is the polynomial f_x of degree < h
  * with f_x(y) = a(x, y) at y = 0..h-1.  The proof is s(Y) = sum_x f_x(Y)^2 at

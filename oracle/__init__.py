@@ -193,7 +193,7 @@ def matmult_layers(logn: int):
     return log_width, kinds
 
 
-# --- special-purpose non-interactive F2 protocol (Sec. 2.3, 4.2, 6.3) ------------
+# --- special-purpose non-interactive F2 protocol (Sec. 3.2, 4.2, 6.3) ------------
 
 def f2sp_prove(a, v: int, h: int) -> np.ndarray:
     """The proof of the special-purpose F2 protocol for the v x h grid a (row

@@ -759,7 +759,7 @@ int or_verify(const or_circuit *c, const fe *inputs, uint64_t seed, const fe *tr
 }
 
 /* ------------------------------------------------------------------------- */
-/* Special-purpose non-interactive F2 protocol (Sec. 2.3 outline, Sec. 4.2,   */
+/* Special-purpose non-interactive F2 protocol (Sec. 3.2 outline, Sec. 4.2,   */
 /* Sec. 6.3; the protocol of Chakrabarti et al. as implemented by CMT).       */
 /*                                                                           */
 /* The frequency vector a (n = v h entries) is a v x h grid, a(x, y) at      */

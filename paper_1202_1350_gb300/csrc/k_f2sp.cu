@@ -1,6 +1,6 @@
 // k_f2sp.cu -- the special-purpose non-interactive F2 protocol (outlined in
-// Sec. 2.3; prover and verifier parallelisation in Sec. 4.2; GPU results in
-// Sec. 6.3).
+// Sec. 3.2; prover and verifier parallelisation in Sec. 4.2; memory access in
+// Sec. 5.2; GPU results in Sec. 6.3).
 //
 // The frequency vector a (n = v h entries) is a v x h grid, a(x, y) at
 // x h + y.  Row x is the polynomial f_x of degree < h with f_x(y) = a(x, y) at
@@ -16,7 +16,7 @@
 // inverses 1/d, d = 1..2h-2: h (h - 1) multiply-adds per row, O(n h) in all,
 // done directly (no FFT).  A CTA takes SP_RB rows: their b values and the whole
 // inverse table sit in shared memory (the tiles are read in shared-memory
-// order, so the grid's layout in HBM never costs coalescing: Sec. 4.2's
+// order, so the grid's layout in HBM never costs coalescing: Sec. 5.2's
 // column-major transpose is not needed); each thread owns four extension
 // points of all its CTA's rows, accumulating 128-bit products, then squares
 // and sums them over the rows.  A second launch sums the CTAs' column partials.

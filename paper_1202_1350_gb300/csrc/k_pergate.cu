@@ -1,5 +1,5 @@
-// k_pergate.cu -- the paper's per-gate prover (Sec. 4.1.1; Sec. 4.2, "Memory
-// access"), kept as a second prover path: same transcript as the folding
+// k_pergate.cu -- the paper's per-gate prover (Sec. 4.1.1; memory access in
+// Sec. 5.1.4), kept as a second prover path: same transcript as the folding
 // prover, computed the way the paper's GPU prover computes it.
 //
 // Every message of layer i is a sum of independent per-gate contributions: in

@@ -2,11 +2,13 @@
 //
 // The bulk of the verifier's work is its "secret": the input's multilinear
 // extension at the final random point, a sum in which every input contributes
-// independently (Sec. 4.1.2), computed here as a grid-wide reduction.  The
-// round checks of one layer form a short sequential chain; since each layer's
-// starting claim can be read off the transcript (q_{i-1}(tau_{i-1})), all
-// layers are checked concurrently, one thread per layer.  The accept bit is the
-// conjunction of exactly the checks the sequential verifier makes.
+// independently (Sec. 4.1.2), computed here as a grid-wide reduction whose
+// CTAs derive the point from the seed themselves (so it runs beside the coin
+// launch).  The round checks of one layer form a short sequential chain;
+// since each layer's starting claim can be read off the transcript
+// (q_{i-1}(tau_{i-1})), all layers are checked concurrently, a warp per layer,
+// and every round by its own thread.  The accept bit is the conjunction of
+// exactly the checks the sequential verifier makes.
 #include <cuda_runtime.h>
 #include "coins.cuh"
 

@@ -53,7 +53,7 @@ struct LayerDev {
 
 // In-neighbours and operation of gate g of layer i (Sec. 6.2.1 circuits):
 // computed from the index for the structured kinds (a tree gate reads 2g and
-// 2g+1, as in Sec. 4.2 "Memory access"), read for EXPLICIT layers.
+// 2g+1, as in Sec. 5.1.4), read for EXPLICIT layers.
 __device__ __forceinline__ void gate_wiring(const LayerDev &L, u64 g, u64 &a, u64 &b, u32 &mul)
 {
     switch (L.kind) {
@@ -109,7 +109,7 @@ struct SciDev {
     u32 layer;
     u32 chal_off;  // challenge of round k: chal[chal_off + k]
     u64 tr_off;    // transcript offset of round 0's three values
-    u64 *Lc;       // PROD: factors c0_m, c1_m (2n), written by k_prep_prod
+    u64 *Lc;       // PROD: factors c0_m, c1_m (2n), written by the coin launch
     u64 *kap;      // PROD: prod_{m<j} L_m(r_m)
     u64 *esum;     // PROD: prod_{m>j} (c0_m + c1_m)
 };

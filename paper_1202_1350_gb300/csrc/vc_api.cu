@@ -809,11 +809,13 @@ void plan_merge(Plan &B, const std::vector<vc_circuit *> &cs)
 // ---------------------------------------------------------------------------------------
 
 // The launches of one proof of every circuit of the plan, after the globals
-// hold the call's seeds.  Setup (coins, layer points) runs on `st`; then
-// helper stream A builds eq tables and product weights and, after the
-// evaluation, runs the product-weighted waves; `st` evaluates the circuit,
-// reduces the lines and builds the wiring tables; helper stream B runs the
-// general waves once the tables they read exist; the final reduction joins all.
+// hold the call's seeds.  `st` checks and evaluates the circuit; the helper
+// stream, forked from `st` at the start, runs the coin launch (challenges,
+// points, eq tables, product weights: none depends on the circuit's values);
+// `st` then waits for it and runs the persistent wave launches (line
+// reductions, product-weighted and general sum-checks), the wiring tables and
+// the general waves over them where the circuit has such layers, and the
+// final reduction.
 void enqueue_plan(Plan &P, cudaStream_t st)
 {
     cudaStream_t sa = P.aux;

@@ -514,7 +514,7 @@ def test_pm_and_mm1_wiring_equals_the_packages_description():
                     assert np.array_equal(np.asarray(u, np.int64), np.asarray(v, np.int64))
 
 
-# --- the special-purpose non-interactive F2 protocol (Sec. 2.3, 4.2, 6.3) ----------
+# --- the special-purpose non-interactive F2 protocol (Sec. 3.2, 4.2, 6.3) ----------
 
 def _sympy_extension(row, m):
     """Value at m of the degree < h polynomial through (y, row[y]), by exact
