@@ -922,7 +922,7 @@ __device__ __forceinline__ bool wave_done(u32 *counter, u32 nchunks, u32 &s_flag
 extern __shared__ __align__(16) unsigned char wv_dyn[];
 
 #ifndef WV_MINB
-#define WV_MINB 3  // resident CTAs per SM the register allocation is sized for (3: 168 registers, no spills)
+#define WV_MINB 4  // resident CTAs per SM the register allocation is sized for (4: 128 registers)
 #endif
 
 __global__ void __launch_bounds__(WV_NT, WV_MINB) k_waves(const Globals *Gs, const LineWaveDev *lw, const ProdWave *pw,
