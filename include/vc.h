@@ -211,14 +211,20 @@ vc_status vc_circuit_get_info(const vc_circuit *c, vc_circuit_info *info);
 
 /* Tile shapes of a circuit's launch plan: rounds folded by a first
  * product-weighted / general sum-check chunk (<= 13 / <= 12), coordinates
- * folded by a first line-reduction chunk (<= 13), and the smallest
- * evaluation chunk (log2 entries, <= 11).  Any choice gives the same
- * transcript; they only change speed. */
+ * folded by a first line-reduction chunk (<= 13), the smallest evaluation
+ * chunk (log2 entries, <= 11), and pr_split_log: product-weighted instances
+ * of fewer than 2^pr_split_log entries use chunks half as large (they are
+ * dispatched after the larger ones, so finer chunks even out the end of the
+ * persistent launch; 0 = never, VC_SPLIT_WIDEST = the circuit's widest
+ * layer, else <= 40).  Any choice gives the same transcript; they only
+ * change speed. */
+#define VC_SPLIT_WIDEST 0xFFFFFFFFu
 typedef struct {
     uint32_t pr_chunk_log;
     uint32_t gn_chunk_log;
     uint32_t line_chunk_log;
     uint32_t eval_chunk_log;
+    uint32_t pr_split_log;
 } vc_tile_config;
 
 /* Autotuner: times `reps` proofs of a circuit of shape `desc` (structured

@@ -17,12 +17,14 @@ constexpr u32 LN_CHUNKW_LOG = WV_LOG;        // coordinates of a later line-wave
 
 // Tile shapes of a circuit's plan (the autotuner's knobs): rounds folded
 // by a first PROD / GEN chunk, coordinates folded by a first line-wave chunk,
-// and the smallest evaluation chunk (log2 entries).
+// the smallest evaluation chunk (log2 entries), and the size below which PROD
+// instances use half-size chunks.
 struct PlanConfig {
     u32 pr_chunk = PR_CHUNK_LOG;
     u32 gn_chunk = GN_CHUNK_LOG;
     u32 ln_chunk0 = LN_CHUNK0_LOG;
-    u32 ev_chunk = 11;  // evaluation chunk: 2^11 inputs per CTA, eight per thread in registers
+    u32 ev_chunk = 11;  // evaluation chunk: 2^11 inputs per CTA
+    u32 pr_split = VC_SPLIT_WIDEST;  // PROD instances below 2^pr_split entries: chunks of 2^(pr_chunk - 1)
 };
 
 // Which layers' phase-2/3 tables are built by k_build23 (the rest are formed

@@ -24,8 +24,6 @@
 #define PG_NT 256
 #define PG_GPT 4  // gates (line: entries) per thread
 
-// eq(t, b) for t = 0, 1, 2 and a bit b: 1 - b, b, 3b - 1.
-
 // Sum of three W values over the CTA; thread 0 gets the totals.
 __device__ __forceinline__ void cta_sum3(u64 &c0, u64 &c1, u64 &c2)
 {
@@ -51,8 +49,9 @@ __device__ __forceinline__ void cta_sum3(u64 &c0, u64 &c1, u64 &c2)
     __syncthreads();
 }
 
-// Adds x e_t(bit) to c_t: bit 0 -> (x, 0, -x), bit 1 -> (0, x, 2x) at t = 0, 1, 2;
-// x1 is the term at t = bit, x2 the term at t = 2 (before e_t).
+// Adds a gate's term times e_t(bit) = eq(t, bit) = (1 - bit, bit, 3 bit - 1) at
+// t = 0, 1, 2 to c_t: bit 0 -> (x1, 0, -x2), bit 1 -> (0, x1, 2 x2), where x1
+// is the rest of the term at t = bit and x2 at t = 2.
 __device__ __forceinline__ void add_terms(u32 bit, u64 x1, u64 x2, u64 &c0, u64 &c1, u64 &c2)
 {
     if (bit) {

@@ -343,6 +343,8 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     P.rounds.clear();
     std::vector<u64> pw_off, gw_off, round_off;
     u64 part_total = 0;
+    u32 smax = 0;
+    for (u32 i = 0; i <= d; i++) smax = std::max(smax, c->s[i]);
     for (u32 i = 0; i < d; i++) {
         const LayerDev &L = c->L[i];
         for (u32 ph = 1; ph <= 3; ph++) {
@@ -368,7 +370,11 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
             }
             P.scis.push_back(Sc);
             const u32 nv = prod ? 2 : 3;
-            const u32 C = prod ? c->cfg.pr_chunk : c->cfg.gn_chunk;
+            // smaller PROD instances (dispatched after the larger ones) use
+            // half-size chunks, which evens out the end of the launch
+            const u32 split = (c->cfg.pr_split == VC_SPLIT_WIDEST) ? smax : c->cfg.pr_split;
+            const u32 C = prod ? ((n < split && c->cfg.pr_chunk > 1) ? c->cfg.pr_chunk - 1 : c->cfg.pr_chunk)
+                               : c->cfg.gn_chunk;
             const u32 M = prod ? (u32)PR_M : (u32)GN_M;
             const bool tab = Sc.kind == PK_GEN_TAB;
             const bool tabB = tab && L.has_add;
@@ -623,16 +629,17 @@ bool plan_valid(const Plan &P)
 void sort_tasks(Plan &P)
 {
     auto rank = [&](const Task &t) { return t.type == TK_LINE ? 0 : (t.type == TK_GEN ? 1 : 2); };
-    auto chunks = [&](const Task &t) {
-        return t.type == TK_LINE ? P.lw[t.wave].nchunks : (t.type == TK_PROD ? P.pw[t.wave].nchunks
-                                                                              : P.gw[t.wave].nchunks);
+    auto entries = [&](const Task &t) {  // the wave's whole size: larger waves first
+        return t.type == TK_LINE ? (u64(P.lw[t.wave].nchunks) << P.lw[t.wave].nl)
+                                 : (t.type == TK_PROD ? (u64(P.pw[t.wave].nchunks) << P.pw[t.wave].nr)
+                                                      : (u64(P.gw[t.wave].nchunks) << P.gw[t.wave].nr));
     };
     for (auto *grp : {&P.groupsA, &P.groupsB})
         for (auto &v : *grp)
             std::stable_sort(v.begin(), v.end(), [&](const Task &a, const Task &b) {
                 const int ra = rank(a), rb = rank(b);
                 if (ra != rb) return ra < rb;
-                return chunks(a) > chunks(b);
+                return entries(a) > entries(b);
             });
 }
 
@@ -939,7 +946,8 @@ static std::map<std::vector<u32>, PlanConfig> g_tuned;  // size class -> fastest
 static bool config_ok(const PlanConfig &f)
 {
     return f.pr_chunk >= 1 && f.pr_chunk <= PR_CHUNK_LOG && f.gn_chunk >= 1 && f.gn_chunk <= GN_CHUNK_LOG &&
-           f.ln_chunk0 >= 1 && f.ln_chunk0 <= LN_CHUNK0_LOG && f.ev_chunk >= 1 && f.ev_chunk <= 11;
+           f.ln_chunk0 >= 1 && f.ln_chunk0 <= LN_CHUNK0_LOG && f.ev_chunk >= 1 && f.ev_chunk <= 11 &&
+           (f.pr_split <= 40 || f.pr_split == VC_SPLIT_WIDEST);
 }
 
 vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **out, const PlanConfig *cfg,
@@ -1535,12 +1543,18 @@ extern "C" vc_status vc_autotune(const vc_circuit_desc *desc, int device, int re
     cudaMemsetAsync(din, 0, nin * sizeof(u64), st);
     double cur_ms = 0;
     s = time_config(desc, device, cur, reps, din, dtr, st, &cur_ms);
-    // coordinate descent over the four knobs
-    const u32 cand[4][4] = {{11, 12, 13, 0}, {10, 11, 12, 0}, {11, 12, 13, 0}, {8, 9, 10, 11}};
-    for (int knob = 0; knob < 4 && s == VC_OK; knob++)
-        for (int j = 0; j < 4 && cand[knob][j]; j++) {
+    // coordinate descent over the five knobs (split: below the widest layer,
+    // below half of its size, never)
+    u32 smax = 0;
+    for (u32 i = 0; i <= desc->n_layers; i++) smax = std::max(smax, desc->log_width[i]);
+    const u32 cand[5][4] = {{11, 12, 13, 0}, {10, 11, 12, 0}, {11, 12, 13, 0}, {8, 9, 10, 11},
+                            {VC_SPLIT_WIDEST, smax ? smax - 1 : 0, 0, VC_SPLIT_WIDEST}};
+    const int ncand[5] = {3, 3, 3, 4, 3};
+    for (int knob = 0; knob < 5 && s == VC_OK; knob++)
+        for (int j = 0; j < ncand[knob]; j++) {
             PlanConfig f = cur;
-            u32 *field = knob == 0 ? &f.pr_chunk : knob == 1 ? &f.gn_chunk : knob == 2 ? &f.ln_chunk0 : &f.ev_chunk;
+            u32 *field = knob == 0 ? &f.pr_chunk : knob == 1 ? &f.gn_chunk : knob == 2 ? &f.ln_chunk0
+                       : knob == 3 ? &f.ev_chunk : &f.pr_split;
             if (*field == cand[knob][j]) continue;
             *field = cand[knob][j];
             double ms = 0;
@@ -1558,7 +1572,7 @@ extern "C" vc_status vc_autotune(const vc_circuit_desc *desc, int device, int re
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_tuned[size_class(desc)] = cur;
     }
-    if (best) *best = {cur.pr_chunk, cur.gn_chunk, cur.ln_chunk0, cur.ev_chunk};
+    if (best) *best = {cur.pr_chunk, cur.gn_chunk, cur.ln_chunk0, cur.ev_chunk, cur.pr_split};
     if (best_ms) *best_ms = cur_ms;
     return VC_OK;
 }
@@ -1573,6 +1587,7 @@ extern "C" vc_status vc_circuit_create_tiles(const vc_circuit_desc *desc, int de
     f.gn_chunk = tiles->gn_chunk_log;
     f.ln_chunk0 = tiles->line_chunk_log;
     f.ev_chunk = tiles->eval_chunk_log;
+    f.pr_split = tiles->pr_split_log;
     vc_circuit *c = nullptr;
     vc_status st = circuit_prepare(desc, device, &c, &f);
     if (st != VC_OK) return st;
@@ -1589,7 +1604,7 @@ extern "C" vc_status vc_circuit_create_tiles(const vc_circuit_desc *desc, int de
 extern "C" vc_status vc_circuit_get_tiles(const vc_circuit *c, vc_tile_config *tiles)
 {
     if (!c || !tiles) return VC_EINVAL;
-    *tiles = {c->cfg.pr_chunk, c->cfg.gn_chunk, c->cfg.ln_chunk0, c->cfg.ev_chunk};
+    *tiles = {c->cfg.pr_chunk, c->cfg.gn_chunk, c->cfg.ln_chunk0, c->cfg.ev_chunk, c->cfg.pr_split};
     return VC_OK;
 }
 

@@ -78,9 +78,13 @@ class ServerStats(ctypes.Structure):
                 ("pending", ctypes.c_uint64), ("max_jobs_in_flight", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
+VC_SPLIT_WIDEST = 0xFFFFFFFF
+
+
 class TileConfig(ctypes.Structure):
     _fields_ = [("pr_chunk_log", ctypes.c_uint32), ("gn_chunk_log", ctypes.c_uint32),
-                ("line_chunk_log", ctypes.c_uint32), ("eval_chunk_log", ctypes.c_uint32)]
+                ("line_chunk_log", ctypes.c_uint32), ("eval_chunk_log", ctypes.c_uint32),
+                ("pr_split_log", ctypes.c_uint32)]
 
 
 _lock = threading.Lock()
@@ -524,7 +528,8 @@ def vc_autotune(log_width, wiring, device: int = 0, reps: int = 5):
 
 def vc_circuit_create_tiles(log_width, wiring, tiles: dict, device: int = 0):
     desc, keep = _desc_struct(log_width, wiring)
-    t = TileConfig(tiles["pr_chunk_log"], tiles["gn_chunk_log"], tiles["line_chunk_log"], tiles["eval_chunk_log"])
+    t = TileConfig(tiles["pr_chunk_log"], tiles["gn_chunk_log"], tiles["line_chunk_log"], tiles["eval_chunk_log"],
+                   tiles.get("pr_split_log", VC_SPLIT_WIDEST))
     h = ctypes.c_void_p()
     _check(lib().vc_circuit_create_tiles(ctypes.byref(desc), device, ctypes.byref(t), ctypes.byref(h)),
            "vc_circuit_create_tiles")

@@ -89,7 +89,9 @@ def test_tile_arguments_rejected_without_device(libvc):
                 {"pr_chunk_log": 13, "gn_chunk_log": 13, "line_chunk_log": 13, "eval_chunk_log": 10},
                 {"pr_chunk_log": 13, "gn_chunk_log": 12, "line_chunk_log": 14, "eval_chunk_log": 10},
                 {"pr_chunk_log": 13, "gn_chunk_log": 12, "line_chunk_log": 13, "eval_chunk_log": 12},
-                {"pr_chunk_log": 0, "gn_chunk_log": 12, "line_chunk_log": 13, "eval_chunk_log": 10}):
+                {"pr_chunk_log": 0, "gn_chunk_log": 12, "line_chunk_log": 13, "eval_chunk_log": 10},
+                {"pr_chunk_log": 13, "gn_chunk_log": 12, "line_chunk_log": 13, "eval_chunk_log": 10,
+                 "pr_split_log": 41}):
         with pytest.raises(vc.VcError) as e:
             vc.vc_circuit_create_tiles(w, k, bad)
         assert e.value.status == vc.VC_EINVAL

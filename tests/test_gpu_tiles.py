@@ -33,8 +33,9 @@ def prove_with(widths, kinds, x, seed, tiles):
         vc.vc_circuit_destroy(h)
 
 
-TILES = [(13, 12, 13, 10), (12, 11, 12, 9), (9, 8, 10, 8), (5, 4, 3, 11), (7, 7, 7, 8), (1, 1, 1, 1),
-         (13, 12, 6, 11), (8, 12, 13, 9)]
+W = vc.VC_SPLIT_WIDEST
+TILES = [(13, 12, 13, 10, W), (12, 11, 12, 9, 0), (9, 8, 10, 8, W), (5, 4, 3, 11, 12), (7, 7, 7, 8, 0),
+         (1, 1, 1, 1, W), (13, 12, 6, 11, 13), (8, 12, 13, 9, 5), (2, 12, 13, 11, W)]
 
 
 @pytest.mark.parametrize("family,logn", [("f2", 14), ("matmult", 4), ("f0", 3)])
@@ -42,8 +43,9 @@ def test_every_tile_shape_gives_the_oracle_transcript(family, logn):
     w, k = circuits.by_name(family, logn)
     x = I.job_inputs(family, logn, 21)
     want = oracle_prove(w, k, x, 33)
-    for pr, gn, ln, ev in TILES:
-        tiles = {"pr_chunk_log": pr, "gn_chunk_log": gn, "line_chunk_log": ln, "eval_chunk_log": ev}
+    for pr, gn, ln, ev, sp in TILES:
+        tiles = {"pr_chunk_log": pr, "gn_chunk_log": gn, "line_chunk_log": ln, "eval_chunk_log": ev,
+                 "pr_split_log": sp}
         got = prove_with(w, k, x, 33, tiles)
         assert (got == want).all(), tiles
 
