@@ -303,8 +303,8 @@ typedef struct vc_server vc_server;
 
 typedef struct {
     uint64_t mem_cap_bytes;  /* device bytes for resident circuits (0 = 150 GiB) */
-    uint32_t max_batch;      /* jobs per launch set (0 = 64)                     */
-    uint32_t max_inflight;   /* launch sets on the device at once (0 = 2, max 8) */
+    uint32_t max_batch;      /* jobs per launch set (0 = 16)                     */
+    uint32_t max_inflight;   /* launch sets on the device at once (0 = 4, max 8) */
 } vc_server_config;
 
 typedef struct {

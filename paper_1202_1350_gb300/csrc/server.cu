@@ -88,7 +88,7 @@ struct Slot {
 struct vc_server {
     int device = 0;
     u64 cap = 0;
-    u32 max_batch = 64, max_inflight = 2;
+    u32 max_batch = 16, max_inflight = 4;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Job *> pending;
@@ -332,8 +332,8 @@ extern "C" vc_status vc_server_create(int device, const vc_server_config *cfg, v
     if (!s) return VC_ENOMEM;
     s->device = device;
     s->cap = (cfg && cfg->mem_cap_bytes) ? cfg->mem_cap_bytes : (u64)150 << 30;
-    s->max_batch = (cfg && cfg->max_batch) ? cfg->max_batch : 64;
-    s->max_inflight = (cfg && cfg->max_inflight) ? cfg->max_inflight : 2;
+    s->max_batch = (cfg && cfg->max_batch) ? cfg->max_batch : 16;
+    s->max_inflight = (cfg && cfg->max_inflight) ? cfg->max_inflight : 4;
     if (s->max_inflight > 8) s->max_inflight = 8;
     DevGuard guard(device);
     init_device_once(device);
