@@ -179,6 +179,8 @@ struct vc_batch {
     size_t arena_bytes = 0;
     CallParams *d_cp = nullptr;
     CallParams *h_cp = nullptr;  // pinned parameter table
+    GatherChunk *d_gather = nullptr;  // the members' input copies, in chunks
+    int ngather = 0;
 };
 
 vc_status cuda_status(cudaError_t e);

@@ -33,6 +33,30 @@ __global__ void k_params_batch(Globals *Gs, const CallParams *cp, int n)
     }
 }
 
+// One CTA per chunk of a member's input copy (coalesced 16-byte moves; the
+// chunks start at multiples of GATHER_CHUNK, so a chunk is 16-byte aligned
+// at both ends whenever the member's buffers are).
+__global__ void __launch_bounds__(256) k_gather_inputs(const CallParams *cp, const GatherChunk *chunks)
+{
+    const GatherChunk C = chunks[blockIdx.x];
+    const u64 *src = cp[C.member].in + C.start;
+    u64 *dst = C.dst;
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
+    if (vec) {
+        const u32 np = C.count / 2;
+        for (u32 k = threadIdx.x; k < np; k += blockDim.x)
+            reinterpret_cast<ulonglong2 *>(dst)[k] = reinterpret_cast<const ulonglong2 *>(src)[k];
+        if ((C.count & 1) && threadIdx.x == 0) dst[C.count - 1] = src[C.count - 1];
+    } else {
+        for (u32 k = threadIdx.x; k < C.count; k += blockDim.x) dst[k] = src[k];
+    }
+}
+
+void launch_gather_inputs(const CallParams *cp, const GatherChunk *chunks, int nchunks, cudaStream_t st)
+{
+    if (nchunks > 0) k_gather_inputs<<<nchunks, 256, 0, st>>>(cp, chunks);
+}
+
 void launch_params(Globals *G, u64 seed, u64 *tr, cudaStream_t st) { k_params<<<1, 1, 0, st>>>(G, seed, tr); }
 
 void launch_params_batch(Globals *Gs, const CallParams *cp, int n, cudaStream_t st)

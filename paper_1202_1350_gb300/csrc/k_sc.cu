@@ -1063,14 +1063,14 @@ __global__ void __launch_bounds__(256) k_final(const Globals *Gs, const SciDev *
             tr[R.tr_pos + 2] = g2;
         }
     }
-    // the outputs open each transcript
-    const u64 gid = blockIdx.x * (u64)blockDim.x + threadIdx.x, gstride = (u64)gridDim.x * blockDim.x;
-    for (int j = 0; j < nouts; j++) {
+    // the outputs open each transcript: a CTA per circuit (grid-stride over
+    // the circuits), its threads over the outputs
+    for (int j = blockIdx.x; j < nouts; j += gridDim.x) {
         const Globals &G = Gs[outs[j]];
         const u64 n = G.S0;
         const u64 *__restrict__ src = G.layers[0].V;
         u64 *__restrict__ dst = G.tr;
-        for (u64 x = gid; x < n; x += gstride) dst[x] = src[x];
+        for (u64 x = threadIdx.x; x < n; x += blockDim.x) dst[x] = src[x];
     }
 }
 

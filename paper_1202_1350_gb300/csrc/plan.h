@@ -264,7 +264,19 @@ struct BuildItem {
 struct CallParams {
     u64 seed;
     u64 *tr;
+    const u64 *in;  // the member's inputs (device memory) for the gather launch
+    u64 pad;
 };
+
+// A piece of one batch member's input copy: count entries from the member's
+// inputs (CallParams::in) at `start` to dst (its input layer, at `start`).
+struct GatherChunk {
+    u64 *dst;
+    u64 start;
+    u32 member;
+    u32 count;
+};
+#define GATHER_CHUNK 2048
 
 #define ST_BAD_INPUT 1u
 #define ST_TIMEOUT 2u
@@ -283,6 +295,8 @@ struct EqJob {
 
 void launch_params(Globals *G, u64 seed, u64 *tr, cudaStream_t st);
 void launch_params_batch(Globals *Gs, const CallParams *cp, int n, cudaStream_t st);
+// Every member's inputs into its input layer, one launch (all inputs device memory).
+void launch_gather_inputs(const CallParams *cp, const GatherChunk *chunks, int nchunks, cudaStream_t st);
 // One launch: setup of every circuit (challenges, points, eq(z_i, r_P)),
 // the eq tables and the product weights of the PROD waves.
 void launch_coins(const Globals *Gs, int ncirc, const EqJob *eqjobs, int neq, const SciDev *scis,

@@ -849,11 +849,13 @@ void enqueue_plan(Plan &P, cudaStream_t st)
     // evaluation, the longer of the two, is put into the graph first
     cudaEventRecord(P.ev_fork, st);
     mark(VC_STAGE_EVAL, 0, st);
-    launch_check_inputs(Gs, P.d_checks, (int)P.checks.size(), st);
     for (size_t k = 0; k < P.seg_items.size(); k++) {
         launch_eval_segs(Gs, P.d_segs, P.d_seg_items[k], (int)P.seg_items[k].size(), P.seg_maxblock[k], st);
         launch_eval_layers(Gs, P.d_levs, P.d_lev_items[k], (int)P.lev_items[k].size(), st);
     }
+    // inputs not checked by an evaluation segment: the check only latches a
+    // status read after the proof, so it need not delay the evaluation
+    launch_check_inputs(Gs, P.d_checks, (int)P.checks.size(), st);
     mark(VC_STAGE_EVAL, 1, st);
     cudaStreamWaitEvent(sa, P.ev_fork, 0);
     mark(VC_STAGE_TABLES, 0, sa);
@@ -1628,11 +1630,21 @@ extern "C" vc_status vc_batch_create(vc_circuit *const *circuits, int n, vc_batc
     b->members.assign(circuits, circuits + n);
     DevGuard guard(b->device);
     plan_merge(b->P, b->members);
+    // the members' input copies as chunks of one gather launch
+    std::vector<GatherChunk> gather;
+    for (int j = 0; j < n; j++) {
+        vc_circuit *c = b->members[j];
+        const u64 nin = u64(1) << c->s[c->d];
+        for (u64 s0 = 0; s0 < nin; s0 += GATHER_CHUNK)
+            gather.push_back({c->V[c->d] + s0, s0, (u32)j, (u32)std::min<u64>(GATHER_CHUNK, nin - s0)});
+    }
+    b->ngather = (int)gather.size();
     size_t bytes = 0;
     {
         Arena A;
         plan_take(b->P, A, true);
         A.take<CallParams>(n);
+        A.take<GatherChunk>(gather.size());
         bytes = A.off + 256;
     }
     cudaError_t e = cudaMalloc(&b->arena, bytes);
@@ -1647,8 +1659,10 @@ extern "C" vc_status vc_batch_create(vc_circuit *const *circuits, int n, vc_batc
         A.base = reinterpret_cast<uintptr_t>(b->arena);
         plan_take(b->P, A, true);
         b->d_cp = A.take<CallParams>(n);
+        b->d_gather = A.take<GatherChunk>(gather.size());
     }
     e = upload(b->P.d_G, b->P.h_G);
+    if (e == cudaSuccess) e = upload(b->d_gather, gather);
     if (e == cudaSuccess) e = plan_upload(b->P);
     if (e == cudaSuccess) e = cudaHostAlloc(&b->h_cp, n * sizeof(CallParams), cudaHostAllocDefault);
     if (e == cudaSuccess) e = plan_resources(b->P);
@@ -1684,7 +1698,7 @@ extern "C" vc_status vc_batch_prove(vc_batch *b, const uint64_t *const *inputs, 
     cudaStream_t st = (cudaStream_t)stream;
     const int n = (int)b->members.size();
     std::vector<int> kt(n);
-    bool all_dev = true;
+    bool all_dev = true, all_in_dev = true;
     for (int j = 0; j < n; j++) {
         vc_circuit *c = b->members[j];
         if (!inputs[j] || !transcripts[j]) return VC_EINVAL;
@@ -1692,20 +1706,26 @@ extern "C" vc_status vc_batch_prove(vc_batch *b, const uint64_t *const *inputs, 
         kt[j] = ptr_kind(transcripts[j], c->device);
         if (ki < 0 || kt[j] < 0) return VC_EINVAL;
         all_dev = all_dev && ki && kt[j];
+        all_in_dev = all_in_dev && ki;
     }
     // the pinned parameter table is rewritten only after the previous call's copy of it finished
     if (cudaEventSynchronize(b->P.ev_params) != cudaSuccess) return VC_ECUDA;
     for (int j = 0; j < n; j++) {
         vc_circuit *c = b->members[j];
-        const u64 nin = u64(1) << c->s[c->d];
-        if (cudaMemcpyAsync(c->V[c->d], inputs[j], nin * sizeof(u64), cudaMemcpyDefault, st) != cudaSuccess)
-            return VC_ECUDA;
+        if (!all_in_dev) {  // host inputs: one copy per member
+            const u64 nin = u64(1) << c->s[c->d];
+            if (cudaMemcpyAsync(c->V[c->d], inputs[j], nin * sizeof(u64), cudaMemcpyDefault, st) != cudaSuccess)
+                return VC_ECUDA;
+        }
         b->h_cp[j].seed = seeds[j];
         b->h_cp[j].tr = kt[j] ? transcripts[j] : c->d_tr;
+        b->h_cp[j].in = inputs[j];
     }
     cudaError_t e = cudaMemcpyAsync(b->d_cp, b->h_cp, n * sizeof(CallParams), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(b->P.ev_params, st);
     if (e != cudaSuccess) return VC_ECUDA;
+    // device inputs: every member's copy in one launch
+    if (all_in_dev) launch_gather_inputs(b->d_cp, b->d_gather, b->ngather, st);
     launch_params_batch(b->P.d_G, b->d_cp, n, st);
     e = plan_launch(b->P, st);
     if (e == cudaSuccess) e = cudaGetLastError();
