@@ -183,7 +183,11 @@ __device__ __forceinline__ void eval_warp_layers(LayerFn layer, int hi, int lo, 
     }
 }
 
-__global__ void __launch_bounds__(EV_NT) k_eval_seg(const Globals *Gs, const EvalSeg *segs, const Item *items,
+#ifndef EV_MINB
+#define EV_MINB 4  // resident evaluation CTAs per SM the register allocation is sized for
+#endif
+
+__global__ void __launch_bounds__(EV_NT, EV_MINB) k_eval_seg(const Globals *Gs, const EvalSeg *segs, const Item *items,
                                                     u32 bufsz)
 {
     u64 *bufA = ev_dyn, *bufB = ev_dyn + bufsz;  // bufsz >= every block of the launch's runs and tails
