@@ -239,3 +239,36 @@ __device__ __forceinline__ u64 warp_wsum(u64 x)
     x += __shfl_xor_sync(0xffffffffu, x, 1);
     return wred(x);
 }
+
+// Warp-wide sums of n records of NV values in W (record q at part[q NV ..]):
+// the lanes take every 32nd record, FN_U records' loads in flight per lane
+// before any is added (the reductions over hundreds of per-CTA partials are
+// load-latency bound).  h[t] (t < NV) = the canonical total of value t, in every lane.
+#define FN_U 8
+static_assert(FN_U == 8, "warp_record_sums adds its loads in two quarter-sums of four");
+template <int NV>
+__device__ __forceinline__ void warp_record_sums(const u64 *__restrict__ part, u32 n, u32 lane, u64 *h)
+{
+    u64 acc[NV];
+#pragma unroll
+    for (int t = 0; t < NV; t++) acc[t] = 0;
+    for (u32 q0 = lane; q0 < n; q0 += 32 * FN_U) {
+        u64 x[FN_U][NV];
+#pragma unroll
+        for (int u = 0; u < FN_U; u++) {
+            const u32 q = q0 + 32 * u;
+#pragma unroll
+            for (int t = 0; t < NV; t++) x[u][t] = q < n ? part[(u64)q * NV + t] : 0;
+        }
+#pragma unroll
+        for (int t = 0; t < NV; t++) {
+            // four W values sum below 2^64; wred brings each quarter-sum back to W
+            const u64 lo = wred(x[0][t] + x[1][t] + x[2][t] + x[3][t]);
+            const u64 hi = wred(x[4][t] + x[5][t] + x[6][t] + x[7][t]);
+            acc[t] = wred(acc[t] + lo + hi);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NV; t++) h[t] = wcanon(warp_wsum(acc[t]));
+}
+

@@ -119,6 +119,13 @@ struct Plan {
     cudaEvent_t ev_fork = nullptr, ev_tables = nullptr;
     cudaEvent_t ev_params = nullptr;  // a batch's parameter table was copied
     cudaGraphExec_t exec = nullptr;
+    // own_params: the graph's first node is the per-proof parameter write
+    // (k_params), whose arguments are set on the instantiated graph before
+    // each launch; the graph is kept because that update names its node
+    bool own_params = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphNode_t pnode = nullptr;
+    cudaKernelNodeParams pkp{};
     cudaEvent_t stage_ev[2 * VC_NUM_STAGES] = {};
     bool stage_on = false;
 };
@@ -154,7 +161,10 @@ struct vc_circuit {
     u64 *partials = nullptr;
     VerifyDev Vd{};
     VerifyPtrs *d_vp = nullptr;        // per-call verifier pointers (device)
-    cudaGraphExec_t vexec = nullptr;   // the verifier's captured launches
+    cudaGraphExec_t vexec = nullptr;   // the verifier's captured launches, parameter write first
+    cudaGraph_t vgraph = nullptr;
+    cudaGraphNode_t vpnode = nullptr;
+    cudaKernelNodeParams vpkp{};
     std::vector<u32> explicit_layers;
     u32 *d_explicit_layers = nullptr;
     std::vector<u32> round_layer, zmap;
@@ -202,6 +212,9 @@ cudaError_t plan_resources(Plan &P);
 void plan_release(Plan &P);
 void plan_merge(Plan &B, const std::vector<vc_circuit *> &cs);
 void enqueue_plan(Plan &P, cudaStream_t st);
+void plan_drop_graph(Plan &P);
+// The kernel node of `fn` in a captured graph (cudaErrorInvalidValue if none).
+cudaError_t find_kernel_node(cudaGraph_t g, const void *fn, cudaGraphNode_t *node, cudaKernelNodeParams *kp);
 void sort_tasks(Plan &P);
 int count_launches(const Plan &P);
 size_t plan_bytes(Plan &P, bool own_G);  // device bytes of the plan's descriptors

@@ -58,6 +58,7 @@ void launch_gather_inputs(const CallParams *cp, const GatherChunk *chunks, int n
 }
 
 void launch_params(Globals *G, u64 seed, u64 *tr, cudaStream_t st) { k_params<<<1, 1, 0, st>>>(G, seed, tr); }
+const void *params_kernel() { return reinterpret_cast<const void *>(k_params); }
 
 void launch_params_batch(Globals *Gs, const CallParams *cp, int n, cudaStream_t st)
 {

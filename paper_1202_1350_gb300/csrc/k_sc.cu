@@ -1013,7 +1013,6 @@ __global__ void __launch_bounds__(256) k_final(const Globals *Gs, const SciDev *
     for (u64 gw = (blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5; gw < (u64)nrounds; gw += nwarps) {
         const RoundRef R = rounds[gw];
         const bool gen = R.kind >= PK_GEN_FIRST;
-        const u32 nv = gen ? 3 : 2;
         // the round's scalars, loaded while the partials are summed
         u64 ez = 0, v1 = 0, ch = 0, es = 0, kap = 0, c0 = 0, c1 = 0;
         if (lane == 0) {
@@ -1030,11 +1029,10 @@ __global__ void __launch_bounds__(256) k_final(const Globals *Gs, const SciDev *
         }
         u64 *tr = Gs[R.circ].tr;
         u64 h[3];
-        for (u32 t = 0; t < nv; t++) {
-            u64 s = 0;
-            for (u32 q = lane; q < R.nchunks; q += 32) s = wred(s + R.part_pos[(u64)q * nv + t]);
-            h[t] = wcanon(warp_wsum(s));
-        }
+        if (gen)
+            warp_record_sums<3>(R.part_pos, R.nchunks, lane, h);
+        else
+            warp_record_sums<2>(R.part_pos, R.nchunks, lane, h);
         if (lane == 0) {
             u64 g0, g1, g2;
             if (gen) {

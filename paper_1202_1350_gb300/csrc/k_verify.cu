@@ -304,9 +304,7 @@ __global__ void __launch_bounds__(VC_NT) k_vcheck(Globals G, VerifyDev V, const 
         const u64 *r = G.chal + L.chal_off;
         u64 start;
         if (i == 0) {
-            u64 acc = 0;
-            for (u32 k = lane; k < V.mle_out_blocks; k += 32) acc = wred(acc + V.mle_part[V.mle_blocks + k]);
-            start = wcanon(warp_wsum(acc));
+            warp_record_sums<1>(V.mle_part + V.mle_blocks, V.mle_out_blocks, lane, &start);
         } else {
             const LayerDev &Lp = G.layers[i - 1];
             start = lagrange_warp(tr + Lp.tr_q, Lp.sn, G.chal[Lp.chal_off + Lp.s + 2 * Lp.sn], G.invfact);
@@ -333,9 +331,8 @@ __global__ void __launch_bounds__(VC_NT) k_vcheck(Globals G, VerifyDev V, const 
         }
         if (i + 1 == G.d) {
             const u64 fin = lagrange_warp(q, sn, G.chal[L.chal_off + n], G.invfact);
-            u64 acc = 0;
-            for (u32 k = lane; k < V.mle_blocks; k += 32) acc = wred(acc + V.mle_part[k]);
-            const u64 in_mle = wcanon(warp_wsum(acc));
+            u64 in_mle;
+            warp_record_sums<1>(V.mle_part, V.mle_blocks, lane, &in_mle);
             if (lane == 0 && fin != in_mle) fail = 1;
         }
     } else {
@@ -384,19 +381,24 @@ __global__ void k_init_invfact(u64 *invfact)
 
 void launch_init_invfact(u64 *invfact, cudaStream_t st) { k_init_invfact<<<1, 64, 0, st>>>(invfact); }
 
-__global__ void k_vparams(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *tr, const u64 *inputs, int *accept)
+// Per-call verifier parameters; also clears the result words (flags, accept bit).
+__global__ void k_vparams(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *tr, const u64 *inputs, int *accept,
+                          u64 *result)
 {
     G->seed = seed;
     vp->tr = tr;
     vp->inputs = inputs;
     vp->accept_out = accept;
+    for (int k = 0; k < VC_RESULT_WORDS; k++) result[k] = 0;
 }
 
 void launch_vparams(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *tr, const u64 *inputs, int *accept,
-                    cudaStream_t st)
+                    u64 *result, cudaStream_t st)
 {
-    k_vparams<<<1, 1, 0, st>>>(G, vp, seed, tr, inputs, accept);
+    k_vparams<<<1, 1, 0, st>>>(G, vp, seed, tr, inputs, accept, result);
 }
+
+const void *vparams_kernel() { return reinterpret_cast<const void *>(k_vparams); }
 
 // Entries per CTA (log2) of the MLE partial sums for a point of n coordinates.
 u32 vmle_log(u32 n) { return n < 11 ? n : 11; }

@@ -280,6 +280,7 @@ struct GatherChunk {
 
 #define ST_BAD_INPUT 1u
 #define ST_TIMEOUT 2u
+#define VC_RESULT_WORDS 8  // verifier result words (device)
 
 // ---- launch entry points (implemented in the .cu files) -------------------------
 // An eq table to build and where its point comes from: challenges
@@ -294,6 +295,8 @@ struct EqJob {
 };
 
 void launch_params(Globals *G, u64 seed, u64 *tr, cudaStream_t st);
+const void *params_kernel();   // k_params, to find its node in a captured graph
+const void *vparams_kernel();  // k_vparams, likewise
 void launch_params_batch(Globals *Gs, const CallParams *cp, int n, cudaStream_t st);
 // Every member's inputs into its input layer, one launch (all inputs device memory).
 void launch_gather_inputs(const CallParams *cp, const GatherChunk *chunks, int nchunks, cudaStream_t st);
@@ -342,8 +345,9 @@ struct VerifyDev {
     u32 nrounds;
 };
 void launch_init_invfact(u64 *invfact, cudaStream_t st);
+// result: VC_RESULT_WORDS words, cleared by the launch
 void launch_vparams(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *tr, const u64 *inputs, int *accept,
-                    cudaStream_t st);
+                    u64 *result, cudaStream_t st);
 // The verifier's launches after its coin launch was issued on st: the MLE
 // partial sums on st_mle (forked from st before the coins, so both run
 // together), joined back into st through ev_join, then the checks.

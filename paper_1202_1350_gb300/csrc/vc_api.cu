@@ -228,7 +228,7 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     G.S0 = S(0);
     c->d_G = A.take<Globals>(1);
     P.d_G = c->d_G;
-    c->d_result = A.take<u64>(8);
+    c->d_result = A.take<u64>(VC_RESULT_WORDS);
     c->d_tr = A.take<u64>(c->tr_len);
     G.tr = c->d_tr;
 
@@ -713,10 +713,18 @@ cudaError_t plan_resources(Plan &P)
     return e;
 }
 
-void plan_release(Plan &P)
+void plan_drop_graph(Plan &P)
 {
     if (P.exec) cudaGraphExecDestroy(P.exec);
+    if (P.graph) cudaGraphDestroy(P.graph);
     P.exec = nullptr;
+    P.graph = nullptr;
+    P.pnode = nullptr;
+}
+
+void plan_release(Plan &P)
+{
+    plan_drop_graph(P);
     for (cudaEvent_t *ev : {&P.ev_fork, &P.ev_tables, &P.ev_params}) {
         if (*ev) cudaEventDestroy(*ev);
         *ev = nullptr;
@@ -844,6 +852,7 @@ void enqueue_plan(Plan &P, cudaStream_t st)
         launch_waves(Gs, P.d_lw, P.d_pw, P.d_gw, d_tasks, (int)tasks.size(), P.d_ctr + 2 * g, st);
     };
     mark(VC_STAGE_PROOF, 0, st);
+    if (P.own_params) launch_params(P.d_G, 0, nullptr, st);  // arguments set per launch
     // helper stream: coins, points, eq tables and product weights (they do not
     // depend on the circuit's values), concurrently with the evaluation; the
     // evaluation, the longer of the two, is put into the graph first
@@ -889,26 +898,79 @@ void enqueue_plan(Plan &P, cudaStream_t st)
     mark(VC_STAGE_PROOF, 1, st);
 }
 
-// Run the plan on `st`: replay its CUDA graph (captured on first use, and
-// again after the stage events change).
-static cudaError_t plan_launch(Plan &P, cudaStream_t st)
+cudaError_t find_kernel_node(cudaGraph_t g, const void *fn, cudaGraphNode_t *node, cudaKernelNodeParams *kp)
 {
-    if (!P.exec) {
-        cudaError_t e = cudaStreamBeginCapture(P.cap, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return e;
-        enqueue_plan(P, P.cap);
-        cudaGraph_t g = nullptr;
-        e = cudaStreamEndCapture(P.cap, &g);
-        if (e != cudaSuccess) {
-            if (g) cudaGraphDestroy(g);
-            return e;
+    size_t n = 0;
+    cudaError_t e = cudaGraphGetNodes(g, nullptr, &n);
+    if (e != cudaSuccess) return e;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n) e = cudaGraphGetNodes(g, nodes.data(), &n);
+    for (size_t k = 0; e == cudaSuccess && k < n; k++) {
+        cudaGraphNodeType t;
+        e = cudaGraphNodeGetType(nodes[k], &t);
+        if (e != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams p{};
+        e = cudaGraphKernelNodeGetParams(nodes[k], &p);
+        if (e == cudaSuccess && p.func == fn) {
+            *node = nodes[k];
+            *kp = p;
+            kp->kernelParams = nullptr;  // owned by the node; each update passes its own
+            kp->extra = nullptr;
+            return cudaSuccess;
         }
-        e = cudaGraphInstantiate(&P.exec, g, 0);
+    }
+    return e == cudaSuccess ? cudaErrorInvalidValue : e;
+}
+
+// Capture what `enqueue` puts on a stream into an instantiated graph; with
+// `fn`, also find that kernel's node (the graph is then kept in *keep).
+template <class F>
+static cudaError_t capture_graph(cudaStream_t cap, F enqueue, cudaGraphExec_t *exec, const void *fn,
+                                 cudaGraph_t *keep, cudaGraphNode_t *node, cudaKernelNodeParams *kp)
+{
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    enqueue(cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cap, &g);
+    if (e == cudaSuccess && fn) e = find_kernel_node(g, fn, node, kp);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+    if (e != cudaSuccess) *exec = nullptr;
+    if (e == cudaSuccess && fn)
+        *keep = g;
+    else if (g)
         cudaGraphDestroy(g);
+    return e;
+}
+
+// Set the arguments of a graph's parameter node for its next launch (launches
+// already queued keep theirs).
+static cudaError_t set_node_args(cudaGraphExec_t exec, cudaGraphNode_t node, cudaKernelNodeParams kp, void **args)
+{
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    return cudaGraphExecKernelNodeSetParams(exec, node, &kp);
+}
+
+// Run the plan on `st`: replay its CUDA graph (captured on first use, and
+// again after the stage events change).  A plan with its own parameter node
+// gets (seed, tr) through it.
+static cudaError_t plan_launch(Plan &P, cudaStream_t st, u64 seed = 0, u64 *tr = nullptr)
+{
+    cudaError_t e = cudaSuccess;
+    if (!P.exec) {
+        e = capture_graph(P.cap, [&](cudaStream_t cs) { enqueue_plan(P, cs); }, &P.exec,
+                          P.own_params ? params_kernel() : nullptr, &P.graph, &P.pnode, &P.pkp);
         if (e != cudaSuccess) {
-            P.exec = nullptr;
+            plan_drop_graph(P);
             return e;
         }
+    }
+    if (P.own_params) {
+        Globals *G = P.d_G;
+        void *args[3] = {&G, &seed, &tr};
+        e = set_node_args(P.exec, P.pnode, P.pkp, args);
+        if (e != cudaSuccess) return e;
     }
     return cudaGraphLaunch(P.exec, st);
 }
@@ -1047,6 +1109,7 @@ vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **
     c->tr_len = tp;
     plan_eval(c);
     c->P.ncirc = 1;
+    c->P.own_params = true;
     Arena A;
     A.off = layout(c, 0, 0);
     plan_take(c->P, A, false);
@@ -1059,6 +1122,7 @@ void circuit_free(vc_circuit *c)
 {
     if (!c) return;
     if (c->vexec) cudaGraphExecDestroy(c->vexec);
+    if (c->vgraph) cudaGraphDestroy(c->vgraph);
     if (c->pg_exec) cudaGraphExecDestroy(c->pg_exec);
     if (c->pg_arena) cudaFree(c->pg_arena);
     plan_release(c->P);
@@ -1224,8 +1288,7 @@ extern "C" vc_status vc_prove(vc_circuit *c, const uint64_t *inputs, uint64_t se
     cudaError_t e = cudaMemcpyAsync(c->V[c->d], inputs, nin * sizeof(u64),
                                     cudaMemcpyDefault, st);
     if (e != cudaSuccess) return VC_ECUDA;
-    launch_params(c->d_G, seed, kt ? transcript : c->d_tr, st);
-    e = plan_launch(c->P, st);
+    e = plan_launch(c->P, st, seed, kt ? transcript : c->d_tr);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return VC_ECUDA;
     if (!kt) {
@@ -1418,29 +1481,33 @@ extern "C" vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t s
         dtr = c->d_tr;
     }
     if (e != cudaSuccess) return VC_ECUDA;
-    // the verifier's launches are one captured graph; the per-call pointers
-    // and seed are written on the stream ahead of it
-    launch_vparams(c->d_G, c->d_vp, seed, dtr, din, ka ? accept : nullptr, st);
+    // the verifier's launches are one captured graph; its first node writes
+    // the per-call pointers and seed, with arguments set before each launch
     if (!c->vexec) {
-        e = cudaStreamBeginCapture(c->P.cap, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return VC_ECUDA;
-        cudaStream_t cs = c->P.cap;
-        cudaMemsetAsync(c->d_result, 0, 8 * sizeof(u64), cs);
-        cudaEventRecord(c->P.ev_fork, cs);
-        cudaStreamWaitEvent(c->P.aux, c->P.ev_fork, 0);
-        launch_coins(c->d_G, 1, c->d_eq_verify, (int)c->eq_verify.size(), nullptr, nullptr, 0, cs);
-        launch_verify(c->d_G, c->G, c->Vd, c->s[c->d], c->s[0], c->d_explicit_layers,
-                      (int)c->explicit_layers.size(), c->P.aux, c->P.ev_tables, cs);
-        cudaGraph_t g = nullptr;
-        e = cudaStreamEndCapture(cs, &g);
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->vexec, g, 0);
-        if (g) cudaGraphDestroy(g);
+        auto enqueue = [&](cudaStream_t cs) {
+            launch_vparams(c->d_G, c->d_vp, 0, nullptr, nullptr, nullptr, c->d_result, cs);
+            cudaEventRecord(c->P.ev_fork, cs);
+            cudaStreamWaitEvent(c->P.aux, c->P.ev_fork, 0);
+            launch_coins(c->d_G, 1, c->d_eq_verify, (int)c->eq_verify.size(), nullptr, nullptr, 0, cs);
+            launch_verify(c->d_G, c->G, c->Vd, c->s[c->d], c->s[0], c->d_explicit_layers,
+                          (int)c->explicit_layers.size(), c->P.aux, c->P.ev_tables, cs);
+        };
+        e = capture_graph(c->P.cap, enqueue, &c->vexec, vparams_kernel(), &c->vgraph, &c->vpnode, &c->vpkp);
         if (e != cudaSuccess) {
+            if (c->vexec) cudaGraphExecDestroy(c->vexec);
             c->vexec = nullptr;
             return VC_ECUDA;
         }
     }
-    e = cudaGraphLaunch(c->vexec, st);
+    {
+        Globals *G = c->d_G;
+        VerifyPtrs *vp = c->d_vp;
+        int *acc_out = ka ? accept : nullptr;
+        u64 *res = c->d_result;
+        void *args[7] = {&G, &vp, &seed, &dtr, &din, &acc_out, &res};
+        e = set_node_args(c->vexec, c->vpnode, c->vpkp, args);
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(c->vexec, st);
     if (e != cudaSuccess) return VC_ECUDA;
     if (ka && ki && kt) return cudaGetLastError() == cudaSuccess ? VC_OK : VC_ECUDA;
     e = cudaMemcpyAsync(c->h_pinned + 8, c->d_result, 4 * sizeof(u64), cudaMemcpyDeviceToHost, st);
@@ -1457,8 +1524,7 @@ extern "C" vc_status vc_circuit_set_stage_events(vc_circuit *c, void *const *eve
     if (!c) return VC_EINVAL;
     DevGuard guard(c->device);
     if (c->P.exec) {  // the events are part of the captured graph: capture again
-        cudaGraphExecDestroy(c->P.exec);
-        c->P.exec = nullptr;
+        plan_drop_graph(c->P);
     }
     c->P.stage_on = events != nullptr;
     if (events)
