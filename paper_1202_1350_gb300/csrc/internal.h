@@ -133,6 +133,7 @@ struct Plan {
 struct vc_circuit {
     int device = 0;
     u32 flags = 0;                // VC_VALUES_IN_HOST_MEMORY
+    bool eval_reads_inputs = false;  // the first evaluation launch can read the inputs in place
     PlanConfig cfg;
     u32 d = 0;
     std::vector<u32> s, kind, has_add;
@@ -219,6 +220,6 @@ void sort_tasks(Plan &P);
 int count_launches(const Plan &P);
 size_t plan_bytes(Plan &P, bool own_G);  // device bytes of the plan's descriptors
 
-int ptr_kind(const void *p, int device);
+int ptr_kind(const void *p, int device, const void **mapped = nullptr);
 cudaError_t queue_status(vc_circuit *c, cudaStream_t st);
 vc_status decode_status(const vc_circuit *c);

@@ -18,11 +18,13 @@
 // Setup: verifier coins (splitmix64 stream), the layer points z_i, eq(z_i, r_P).
 // --------------------------------------------------------------------------------
 
-// Per-proof parameters of one circuit (seed, transcript pointer).
-__global__ void k_params(Globals *G, u64 seed, u64 *tr)
+// Per-proof parameters of one circuit (seed, transcript pointer, and the
+// inputs when the evaluation reads them in place).
+__global__ void k_params(Globals *G, u64 seed, u64 *tr, const u64 *in)
 {
     G->seed = seed;
     G->tr = tr;
+    G->in = in;
 }
 
 __global__ void k_params_batch(Globals *Gs, const CallParams *cp, int n)
@@ -57,7 +59,10 @@ void launch_gather_inputs(const CallParams *cp, const GatherChunk *chunks, int n
     if (nchunks > 0) k_gather_inputs<<<nchunks, 256, 0, st>>>(cp, chunks);
 }
 
-void launch_params(Globals *G, u64 seed, u64 *tr, cudaStream_t st) { k_params<<<1, 1, 0, st>>>(G, seed, tr); }
+void launch_params(Globals *G, u64 seed, u64 *tr, const u64 *in, cudaStream_t st)
+{
+    k_params<<<1, 1, 0, st>>>(G, seed, tr, in);
+}
 const void *params_kernel() { return reinterpret_cast<const void *>(k_params); }
 
 void launch_params_batch(Globals *Gs, const CallParams *cp, int n, cudaStream_t st)
@@ -211,7 +216,14 @@ __global__ void __launch_bounds__(EV_NT, EV_MINB) k_eval_seg(const Globals *Gs, 
         s_sn[j] = L.sn;
         s_V[j] = L.V;
     }
-    if (threadIdx.x == 0) s_in = Ls[S.i_hi].Vn;
+    __shared__ u64 *s_copy;
+    if (threadIdx.x == 0) {
+        // a run over the input layer reads this proof's inputs in place, if
+        // given, and writes them to the layer's values
+        const bool inplace = G.in != nullptr && S.i_hi + 1 == G.d;
+        s_in = inplace ? G.in : Ls[S.i_hi].Vn;
+        s_copy = inplace ? Ls[S.i_hi].Vn : nullptr;
+    }
     __syncthreads();
     auto layer = [&](u32 i) {
         const u32 j = S.i_hi - i;
@@ -242,12 +254,14 @@ __global__ void __launch_bounds__(EV_NT, EV_MINB) k_eval_seg(const Globals *Gs, 
             r[j] = (k < B) ? src[k] : 0;
         }
         bool bad = false;
+        u64 *const copy = s_copy ? s_copy + ((u64)chunk << S.c) : nullptr;
 #pragma unroll
         for (int j = 0; j < R; j++) {
             const u32 k = threadIdx.x + j * EV_NT;
             if (k < B) {
                 bad |= (r[j] >= FP_P);
                 bufA[k] = r[j];
+                if (copy) copy[k] = r[j];
             }
         }
         if (S.check_input && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_BAD_INPUT);

@@ -1004,7 +1004,7 @@ void launch_waves(const Globals *Gs, const LineWaveDev *lw, const ProdWave *pw, 
 // partials; the round's scalars turn the sums into g(0), g(1), g(2).
 // --------------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_final(const Globals *Gs, const SciDev *scis, const RoundRef *rounds,
+__global__ void __launch_bounds__(256) k_final(Globals *Gs, const SciDev *scis, const RoundRef *rounds,
                                                int nrounds, const u32 *outs, int nouts)
 {
     (void)scis;
@@ -1062,9 +1062,11 @@ __global__ void __launch_bounds__(256) k_final(const Globals *Gs, const SciDev *
         }
     }
     // the outputs open each transcript: a CTA per circuit (grid-stride over
-    // the circuits), its threads over the outputs
+    // the circuits), its threads over the outputs; the proof's in-place input
+    // pointer is cleared (later evaluations read the input layer)
     for (int j = blockIdx.x; j < nouts; j += gridDim.x) {
-        const Globals &G = Gs[outs[j]];
+        Globals &G = Gs[outs[j]];
+        if (threadIdx.x == 0) G.in = nullptr;
         const u64 n = G.S0;
         const u64 *__restrict__ src = G.layers[0].V;
         u64 *__restrict__ dst = G.tr;
@@ -1072,7 +1074,7 @@ __global__ void __launch_bounds__(256) k_final(const Globals *Gs, const SciDev *
     }
 }
 
-void launch_final(const Globals *Gs, const SciDev *scis, const RoundRef *rounds, int nrounds, const u32 *outs,
+void launch_final(Globals *Gs, const SciDev *scis, const RoundRef *rounds, int nrounds, const u32 *outs,
                   int nouts, cudaStream_t st)
 {
     u64 blocks = ((u64)nrounds * 32 + 255) / 256;

@@ -226,6 +226,9 @@ struct Globals {
     u32 nz;
     u32 zd_off;       // z_d in pts[]
     u64 S0;           // outputs
+    const u64 *in;    // this proof's inputs when the first evaluation launch reads them
+                      // in place (it also writes the input layer's values); set by
+                      // k_params, cleared by k_final; NULL: the inputs are in layer d
 };
 
 // A run of block-local layers evaluated by one launch (k_eval_seg): layers
@@ -294,7 +297,7 @@ struct EqJob {
     u32 layer;
 };
 
-void launch_params(Globals *G, u64 seed, u64 *tr, cudaStream_t st);
+void launch_params(Globals *G, u64 seed, u64 *tr, const u64 *in, cudaStream_t st);
 const void *params_kernel();   // k_params, to find its node in a captured graph
 const void *vparams_kernel();  // k_vparams, likewise
 void launch_params_batch(Globals *Gs, const CallParams *cp, int n, cudaStream_t st);
@@ -315,7 +318,7 @@ void launch_build23(const Globals *Gs, const BuildItem *items, int nitems, cudaS
 // One persistent launch over `tasks` (ctr: two zeroed counters, left zeroed).
 void launch_waves(const Globals *Gs, const LineWaveDev *lw, const ProdWave *pw, const GenWave *gw, const Task *tasks,
                   int ntasks, u32 *ctr, cudaStream_t st);
-void launch_final(const Globals *Gs, const SciDev *scis, const RoundRef *rounds, int nrounds, const u32 *outs,
+void launch_final(Globals *Gs, const SciDev *scis, const RoundRef *rounds, int nrounds, const u32 *outs,
                   int nouts, cudaStream_t st);
 void prove_kernels_init();
 void waves_init();

@@ -84,6 +84,16 @@ static EqTab take_eq(Arena &A, const u64 *pt, u32 n)
 // run's input layer (about 256 CTAs for wide layers) and keeps going while its
 // block stays >= 32 entries (or while one CTA covers the whole layer) and
 // <= 4096 entries.  Layers outside any run are evaluated alone (k_eval_layer).
+// Whether the first evaluation launch of a single-circuit plan is a run of
+// block-local layers over the input layer (it can then read the inputs in place).
+static bool first_eval_is_input_run(const Plan &P, u32 d)
+{
+    if (P.seg_items.empty() || P.seg_items[0].empty() || !P.lev_items[0].empty()) return false;
+    for (const Item &it : P.seg_items[0])
+        if (P.segs[it.wave].i_hi + 1 != d) return false;
+    return true;
+}
+
 static void plan_eval(vc_circuit *c)
 {
     Plan &P = c->P;
@@ -852,7 +862,7 @@ void enqueue_plan(Plan &P, cudaStream_t st)
         launch_waves(Gs, P.d_lw, P.d_pw, P.d_gw, d_tasks, (int)tasks.size(), P.d_ctr + 2 * g, st);
     };
     mark(VC_STAGE_PROOF, 0, st);
-    if (P.own_params) launch_params(P.d_G, 0, nullptr, st);  // arguments set per launch
+    if (P.own_params) launch_params(P.d_G, 0, nullptr, nullptr, st);  // arguments set per launch
     // helper stream: coins, points, eq tables and product weights (they do not
     // depend on the circuit's values), concurrently with the evaluation; the
     // evaluation, the longer of the two, is put into the graph first
@@ -893,7 +903,7 @@ void enqueue_plan(Plan &P, cudaStream_t st)
         mark(VC_STAGE_TABWAVES, 1, st);
     }
     mark(VC_STAGE_FINAL, 0, st);
-    launch_final(Gs, P.d_scis, P.d_rounds, (int)P.rounds.size(), P.d_outs, (int)P.outs.size(), st);
+    launch_final(P.d_G, P.d_scis, P.d_rounds, (int)P.rounds.size(), P.d_outs, (int)P.outs.size(), st);
     mark(VC_STAGE_FINAL, 1, st);
     mark(VC_STAGE_PROOF, 1, st);
 }
@@ -954,8 +964,9 @@ static cudaError_t set_node_args(cudaGraphExec_t exec, cudaGraphNode_t node, cud
 
 // Run the plan on `st`: replay its CUDA graph (captured on first use, and
 // again after the stage events change).  A plan with its own parameter node
-// gets (seed, tr) through it.
-static cudaError_t plan_launch(Plan &P, cudaStream_t st, u64 seed = 0, u64 *tr = nullptr)
+// gets (seed, tr, in) through it.
+static cudaError_t plan_launch(Plan &P, cudaStream_t st, u64 seed = 0, u64 *tr = nullptr,
+                               const u64 *in = nullptr)
 {
     cudaError_t e = cudaSuccess;
     if (!P.exec) {
@@ -968,7 +979,7 @@ static cudaError_t plan_launch(Plan &P, cudaStream_t st, u64 seed = 0, u64 *tr =
     }
     if (P.own_params) {
         Globals *G = P.d_G;
-        void *args[3] = {&G, &seed, &tr};
+        void *args[4] = {&G, &seed, &tr, &in};
         e = set_node_args(P.exec, P.pnode, P.pkp, args);
         if (e != cudaSuccess) return e;
     }
@@ -1110,6 +1121,7 @@ vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **
     plan_eval(c);
     c->P.ncirc = 1;
     c->P.own_params = true;
+    c->eval_reads_inputs = first_eval_is_input_run(c->P, c->d);
     Arena A;
     A.off = layout(c, 0, 0);
     plan_take(c->P, A, false);
@@ -1240,15 +1252,20 @@ extern "C" vc_status vc_circuit_bytes(const vc_circuit *c, uint64_t *bytes)
     return VC_OK;
 }
 
-// Pointer kind: 1 = device memory of `device`, 0 = host, -1 = device memory of another device.
-int ptr_kind(const void *p, int device)
+// Pointer kind: 1 = device memory of `device`, 0 = host, -1 = device memory of
+// another device.  With `mapped`: for page-locked host memory that the current
+// device can address, its device address (else NULL).
+int ptr_kind(const void *p, int device, const void **mapped)
 {
+    if (mapped) *mapped = nullptr;
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return a.device == device ? 1 : -1;
+    // (only where the device address is the host address, as under unified addressing)
+    if (mapped && a.type == cudaMemoryTypeHost && a.devicePointer == p) *mapped = p;
     return 0;
 }
 
@@ -1282,13 +1299,20 @@ extern "C" vc_status vc_prove(vc_circuit *c, const uint64_t *inputs, uint64_t se
     if (!c || !inputs || !transcript) return VC_EINVAL;
     DevGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
-    const int ki = ptr_kind(inputs, c->device), kt = ptr_kind(transcript, c->device);
+    const void *mapped = nullptr;
+    const int ki = ptr_kind(inputs, c->device, &mapped), kt = ptr_kind(transcript, c->device);
     if (ki < 0 || kt < 0) return VC_EINVAL;
-    const u64 nin = u64(1) << c->s[c->d];
-    cudaError_t e = cudaMemcpyAsync(c->V[c->d], inputs, nin * sizeof(u64),
-                                    cudaMemcpyDefault, st);
-    if (e != cudaSuccess) return VC_ECUDA;
-    e = plan_launch(c->P, st, seed, kt ? transcript : c->d_tr);
+    // inputs the device can address are read in place by the first evaluation
+    // launch (which writes the input layer); otherwise they are copied first
+    const u64 *in = nullptr;
+    if (c->eval_reads_inputs) in = ki ? inputs : static_cast<const u64 *>(mapped);
+    cudaError_t e = cudaSuccess;
+    if (!in) {
+        const u64 nin = u64(1) << c->s[c->d];
+        e = cudaMemcpyAsync(c->V[c->d], inputs, nin * sizeof(u64), cudaMemcpyDefault, st);
+        if (e != cudaSuccess) return VC_ECUDA;
+    }
+    e = plan_launch(c->P, st, seed, kt ? transcript : c->d_tr, in);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return VC_ECUDA;
     if (!kt) {
@@ -1415,7 +1439,7 @@ extern "C" vc_status vc_prove_pergate(vc_circuit *c, const uint64_t *inputs, uin
     cudaError_t e = cudaMemcpyAsync(c->V[c->d], inputs, nin * sizeof(u64),
                                     cudaMemcpyDefault, st);
     if (e != cudaSuccess) return VC_ECUDA;
-    launch_params(c->d_G, seed, kt ? transcript : c->d_tr, st);
+    launch_params(c->d_G, seed, kt ? transcript : c->d_tr, nullptr, st);
     e = pergate_launch(c, st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return VC_ECUDA;
@@ -1464,14 +1488,17 @@ extern "C" vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t s
     if (!c || !inputs || !transcript || !accept) return VC_EINVAL;
     DevGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
-    const int ki = ptr_kind(inputs, c->device), kt = ptr_kind(transcript, c->device);
+    const void *mapped = nullptr;
+    const int ki = ptr_kind(inputs, c->device, &mapped), kt = ptr_kind(transcript, c->device);
     const int ka = ptr_kind(accept, c->device);
     if (ki < 0 || kt < 0 || ka < 0) return VC_EINVAL;
     if (!ka) *accept = 0;
     const u64 nin = u64(1) << c->s[c->d];
     cudaError_t e = cudaSuccess;
-    const u64 *din = inputs;
-    if (!ki) {
+    // the input MLE reads the inputs once: in place when the device can address
+    // them, else from a copy
+    const u64 *din = ki ? inputs : static_cast<const u64 *>(mapped);
+    if (!din) {
         e = cudaMemcpyAsync(c->V[c->d], inputs, nin * sizeof(u64), cudaMemcpyDefault, st);
         din = c->V[c->d];
     }

@@ -89,6 +89,43 @@ def test_noncanonical_input_reported():
         vc.vc_circuit_destroy(h)
 
 
+@pytest.mark.parametrize("family,logn", [("f2", 11), ("matmult", 3), ("f0", 3)])
+def test_input_memory_kinds_agree(family, logn):
+    """Device inputs and page-locked host inputs are read in place by the first
+    evaluation launch where it runs over the input layer; pageable host inputs
+    are copied.  All give the oracle's transcript, and a later evaluation on
+    the handle reads its own inputs, not the earlier proof's buffer."""
+    widths, kinds = circuits.by_name(family, logn)
+    x = I.job_inputs(family, logn, 21)
+    want = oracle_prove(widths, kinds, x, 77)
+    h = vc.vc_circuit_create(widths, kinds)
+    try:
+        n = vc.vc_transcript_len(h)
+        xd = dev(x)
+        xp = torch.from_numpy(np.ascontiguousarray(x).view(np.int64).copy()).pin_memory()
+        for src in (xd, xp, np.ascontiguousarray(x)):
+            tr = torch.empty(n, dtype=torch.int64, device="cuda")
+            vc.vc_prove(h, src, 77, tr)
+            vc.vc_circuit_sync(h)
+            assert (to_np(tr) == want).all()
+        # the last proof read xd in place: overwrite it, then evaluate other inputs
+        vc.vc_prove(h, xd, 78, tr)
+        vc.vc_circuit_sync(h)
+        xd.fill_(1)
+        y = I.job_inputs(family, logn, 22)
+        out = torch.empty(1 << widths[0], dtype=torch.int64, device="cuda")
+        vc.vc_evaluate(h, dev(y), out)
+        assert (to_np(out) == oracle.Circuit(widths, kinds).evaluate(y)[0]).all()
+        # a non-canonical page-locked input is reported
+        bad = xp.clone().pin_memory()
+        bad[3] = P
+        with pytest.raises(vc.VcError) as e:
+            vc.vc_prove(h, bad, 1, tr)  # host inputs: the status is read before returning
+        assert e.value.status == vc.VC_EINVAL
+    finally:
+        vc.vc_circuit_destroy(h)
+
+
 def test_deterministic_and_seed_dependent():
     widths, kinds = circuits.f2(9)
     x = I.f2_inputs(9, 1 << 16, 2)
