@@ -161,6 +161,34 @@ vc_status vc_circuit_sync(vc_circuit *c, void *stream);
 vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t seed,
                     const uint64_t *transcript, int *accept, void *stream);
 
+/* The same verification in two passes (Sec. 2.2, Sec. 4.1.2).  The coins
+ * are fixed by the seed, so the final point z_d is known before any message
+ * arrives, and the verifier's one pass over the input (the input's
+ * multilinear extension at z_d, the bulk of its work, in which every input
+ * contributes independently) can run before or beside the proof.
+ *
+ * vc_verify_input queues that pass and the coins for `seed`.  `inputs` (S_d
+ * canonical u64) must be device memory of the circuit's device or
+ * page-locked host memory the device can address (VC_EINVAL otherwise); it
+ * is read in place, so it must stay unchanged until the pass has run.  The
+ * pass writes only the verifier's own scratch: its device work may run on
+ * another stream concurrently with a vc_prove on the same handle (the host
+ * calls themselves must not overlap, and no other call on the handle may run
+ * between it and its vc_verify_transcript).  It is always asynchronous.
+ *
+ * vc_verify_transcript queues the rest for the same seed: the claimed
+ * outputs' multilinear extension, every round and layer check, the final
+ * comparison with the input pass's value.  It must be ordered after the
+ * input pass on the device (same stream, or an event).  VC_EINVAL: no input
+ * pass was queued since the last transcript pass or vc_verify, or it was for
+ * another seed.  It is asynchronous when `transcript` and `accept` are
+ * device memory and the input pass read device memory; otherwise it returns
+ * after *accept is set and reports VC_EINVAL for an input >= p.  The accept
+ * bit equals vc_verify's for the same arguments. */
+vc_status vc_verify_input(vc_circuit *c, const uint64_t *inputs, uint64_t seed, void *stream);
+vc_status vc_verify_transcript(vc_circuit *c, uint64_t seed, const uint64_t *transcript, int *accept,
+                               void *stream);
+
 /* Stages of a proof, for timing them.  A proof runs on the caller's stream;
  * the coins, eq tables and product weights run on a helper stream owned by
  * the circuit (forked from and joined back to the caller's stream),
@@ -204,7 +232,8 @@ typedef struct {
     uint32_t prove_launches;     /* kernel launches per vc_prove                  */
     uint32_t verify_launches;    /* kernel launches per vc_verify                 */
     uint32_t wave_tasks;         /* chunks in the first persistent wave launch    */
-    uint32_t pad;
+    uint32_t verify2_launches;   /* kernel launches per vc_verify_input +
+                                    vc_verify_transcript                          */
 } vc_circuit_info;
 
 vc_status vc_circuit_get_info(const vc_circuit *c, vc_circuit_info *info);

@@ -162,10 +162,24 @@ struct vc_circuit {
     u64 *partials = nullptr;
     VerifyDev Vd{};
     VerifyPtrs *d_vp = nullptr;        // per-call verifier pointers (device)
+    // the verifier's own globals: coins, points and eq(z_i, r_P) in arrays of
+    // its own, its status in word 1 of the status words; a verification never
+    // writes what a proof on the handle reads
+    Globals Gv{};
+    Globals *d_Gv = nullptr;
     cudaGraphExec_t vexec = nullptr;   // the verifier's captured launches, parameter write first
     cudaGraph_t vgraph = nullptr;
     cudaGraphNode_t vpnode = nullptr;
     cudaKernelNodeParams vpkp{};
+    // the verifier in two passes: input (coins and the input's MLE) and
+    // transcript (everything else), each a captured graph
+    cudaGraphExec_t vin_exec = nullptr, vtr_exec = nullptr;
+    cudaGraph_t vin_graph = nullptr, vtr_graph = nullptr;
+    cudaGraphNode_t vin_node = nullptr, vtr_node = nullptr;
+    cudaKernelNodeParams vin_kp{}, vtr_kp{};
+    bool vin_pending = false;  // an input pass is queued and not yet consumed
+    u64 vin_seed = 0;
+    bool vin_sync = false;     // its inputs were host memory: the transcript pass reads the status
     std::vector<u32> explicit_layers;
     u32 *d_explicit_layers = nullptr;
     std::vector<u32> round_layer, zmap;
@@ -221,5 +235,7 @@ int count_launches(const Plan &P);
 size_t plan_bytes(Plan &P, bool own_G);  // device bytes of the plan's descriptors
 
 int ptr_kind(const void *p, int device, const void **mapped = nullptr);
-cudaError_t queue_status(vc_circuit *c, cudaStream_t st);
-vc_status decode_status(const vc_circuit *c);
+// Status words: 0 = the prover's, 1 = the verifier's.  Queue the readback
+// (and reset) of words [w0, w0 + n) on `st`; decode what was read back.
+cudaError_t queue_status(vc_circuit *c, cudaStream_t st, int w0 = 0, int n = 1);
+vc_status decode_status(const vc_circuit *c, int w0 = 0, int n = 1);

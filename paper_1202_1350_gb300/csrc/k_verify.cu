@@ -25,13 +25,15 @@
 // per thread, from two 16-entry tables) x (the rest: per iteration, from a
 // small table).  A non-canonical input latches ST_BAD_INPUT; a non-canonical
 // output entry marks the transcript bad.
+// A launch covers blocks [b0, b0 + gridDim.x) of the two ranges.
 __global__ void __launch_bounds__(VM_NT) k_vmle(const Globals *Gd, const VerifyPtrs *vp, u32 nd, u32 lin, u32 n0,
-                                                u32 lout, u32 nin_blocks, u64 *part, u32 *status, u64 *result)
+                                                u32 lout, u32 nin_blocks, u32 b0, u64 *part, u32 *status, u64 *result)
 {
     const Globals &G = *Gd;
-    const bool inp = blockIdx.x < nin_blocks;
+    const u32 blk = blockIdx.x + b0;
+    const bool inp = blk < nin_blocks;
     const u32 nz = inp ? nd : n0, lr = inp ? lin : lout;
-    const u32 b = inp ? blockIdx.x : blockIdx.x - nin_blocks;
+    const u32 b = inp ? blk : blk - nin_blocks;
     const u64 *src = inp ? vp->inputs : vp->tr;  // the claimed outputs open the transcript
     __shared__ u64 z[32], zm[32], mid[1u << VM_MID], t1[16], t2[16], bfac;
     const bool rej = draws_rejected(G);
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(VM_NT) k_vmle(const Globals *Gd, const VerifyP
     if (threadIdx.x < 32) {
         const u64 v = threadIdx.x < VM_NT / 32 ? s[threadIdx.x] : 0;
         const u64 t = warp_wsum(v);
-        if (threadIdx.x == 0) part[blockIdx.x] = wcanon(t);
+        if (threadIdx.x == 0) part[blk] = wcanon(t);
     }
 }
 
@@ -400,6 +402,34 @@ void launch_vparams(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *tr, const u
 
 const void *vparams_kernel() { return reinterpret_cast<const void *>(k_vparams); }
 
+// Parameters of the verifier's input pass (seed, inputs) and of its
+// transcript pass (transcript, accept pointer; clears the result words).
+__global__ void k_vparams_in(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *inputs)
+{
+    G->seed = seed;
+    vp->inputs = inputs;
+}
+
+__global__ void k_vparams_tr(VerifyPtrs *vp, const u64 *tr, int *accept, u64 *result)
+{
+    vp->tr = tr;
+    vp->accept_out = accept;
+    for (int k = 0; k < VC_RESULT_WORDS; k++) result[k] = 0;
+}
+
+void launch_vparams_in(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *inputs, cudaStream_t st)
+{
+    k_vparams_in<<<1, 1, 0, st>>>(G, vp, seed, inputs);
+}
+
+void launch_vparams_tr(VerifyPtrs *vp, const u64 *tr, int *accept, u64 *result, cudaStream_t st)
+{
+    k_vparams_tr<<<1, 1, 0, st>>>(vp, tr, accept, result);
+}
+
+const void *vparams_in_kernel() { return reinterpret_cast<const void *>(k_vparams_in); }
+const void *vparams_tr_kernel() { return reinterpret_cast<const void *>(k_vparams_tr); }
+
 // Entries per CTA (log2) of the MLE partial sums for a point of n coordinates.
 u32 vmle_log(u32 n) { return n < 11 ? n : 11; }
 
@@ -409,9 +439,28 @@ void launch_verify(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 
     // the MLE partial sums need only the seed: they run beside the coin launch
     // (st_mle forked from st before it); the checks wait for both
     k_vmle<<<V.mle_blocks + V.mle_out_blocks, VM_NT, 0, st_mle>>>(Gd, V.vp, nd, vmle_log(nd), n0, vmle_log(n0),
-                                                                   V.mle_blocks, V.mle_part, G.status, V.result);
+                                                                   V.mle_blocks, 0, V.mle_part, G.status, V.result);
     cudaEventRecord(ev_join, st_mle);
     cudaStreamWaitEvent(st, ev_join, 0);
+    if (n_explicit > 0) k_vwire<<<n_explicit, VM_NT, 0, st>>>(G, explicit_layers, V.wire);
+    const u64 threads = 32ull * G.d + V.nrounds;
+    u64 blocks = (threads + VC_NT - 1) / VC_NT;
+    if (blocks < 1) blocks = 1;
+    k_vcheck<<<(unsigned)blocks, VC_NT, 0, st>>>(G, V, V.round_layer, V.nrounds);
+}
+
+void launch_verify_input(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0, cudaStream_t st)
+{
+    k_vmle<<<V.mle_blocks, VM_NT, 0, st>>>(Gd, V.vp, nd, vmle_log(nd), n0, vmle_log(n0), V.mle_blocks, 0,
+                                           V.mle_part, G.status, V.result);
+}
+
+void launch_verify_transcript(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0,
+                              const u32 *explicit_layers, int n_explicit, cudaStream_t st)
+{
+    if (V.mle_out_blocks > 0)
+        k_vmle<<<V.mle_out_blocks, VM_NT, 0, st>>>(Gd, V.vp, nd, vmle_log(nd), n0, vmle_log(n0), V.mle_blocks,
+                                                   V.mle_blocks, V.mle_part, G.status, V.result);
     if (n_explicit > 0) k_vwire<<<n_explicit, VM_NT, 0, st>>>(G, explicit_layers, V.wire);
     const u64 threads = 32ull * G.d + V.nrounds;
     u64 blocks = (threads + VC_NT - 1) / VC_NT;

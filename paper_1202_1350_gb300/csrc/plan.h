@@ -357,6 +357,17 @@ void launch_vparams(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *tr, const u
 u32 vmle_log(u32 n);
 void launch_verify(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0, const u32 *explicit_layers,
                    int n_explicit, cudaStream_t st_mle, cudaEvent_t ev_join, cudaStream_t st);
+// The verifier in two passes.  Input pass: the input's MLE partial sums (the
+// coins are launched beside it by the caller).  Transcript pass: the claimed
+// outputs' MLE partial sums, add~/mult~ of explicit layers, the checks (the
+// eq tables of explicit layers are launched before it by the caller).
+void launch_verify_input(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0, cudaStream_t st);
+void launch_verify_transcript(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0,
+                              const u32 *explicit_layers, int n_explicit, cudaStream_t st);
+void launch_vparams_in(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *inputs, cudaStream_t st);
+void launch_vparams_tr(VerifyPtrs *vp, const u64 *tr, int *accept, u64 *result, cudaStream_t st);
+const void *vparams_in_kernel();
+const void *vparams_tr_kernel();
 
 // Per-gate prover (k_pergate.cu): one descriptor per layer.
 struct PgLayer {

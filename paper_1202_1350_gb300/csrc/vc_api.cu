@@ -526,6 +526,16 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     G.layers = c->d_layers;
     c->d_eq_verify = A.take<EqJob>(c->eq_verify.size());
     c->d_explicit_layers = A.take<u32>(c->explicit_layers.size() + 1);
+
+    // the verifier's globals (everything else shared, read-only for it)
+    Globals &Gv = c->Gv;
+    Gv = G;
+    Gv.chal = A.take<u64>(c->nchal + 1);
+    Gv.pts = A.take<u64>(npts + 1);
+    Gv.scal = A.take<u64>(2 * d + 2);
+    Gv.status = G.status + 1;
+    Gv.tr = nullptr;
+    c->d_Gv = A.take<Globals>(1);
     return A.off;
 }
 
@@ -1133,8 +1143,10 @@ vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **
 void circuit_free(vc_circuit *c)
 {
     if (!c) return;
-    if (c->vexec) cudaGraphExecDestroy(c->vexec);
-    if (c->vgraph) cudaGraphDestroy(c->vgraph);
+    for (cudaGraphExec_t x : {c->vexec, c->vin_exec, c->vtr_exec})
+        if (x) cudaGraphExecDestroy(x);
+    for (cudaGraph_t g : {c->vgraph, c->vin_graph, c->vtr_graph})
+        if (g) cudaGraphDestroy(g);
     if (c->pg_exec) cudaGraphExecDestroy(c->pg_exec);
     if (c->pg_arena) cudaFree(c->pg_arena);
     plan_release(c->P);
@@ -1181,6 +1193,7 @@ vc_status circuit_allocate(vc_circuit *c)
     if (e == cudaSuccess) e = upload(c->d_round_layer, c->round_layer);
     if (e == cudaSuccess) e = upload(c->d_zmap, c->zmap);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_G, &c->G, sizeof(Globals), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_Gv, &c->Gv, sizeof(Globals), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = plan_upload(c->P);
     for (u32 i = 0; e == cudaSuccess && i < d; i++) {
         if (c->kind[i] != W_EXPLICIT) continue;
@@ -1269,28 +1282,29 @@ int ptr_kind(const void *p, int device, const void **mapped)
     return 0;
 }
 
-// Queue the readback of the circuit's error flags (and their reset) on `st`.
-cudaError_t queue_status(vc_circuit *c, cudaStream_t st)
+cudaError_t queue_status(vc_circuit *c, cudaStream_t st, int w0, int n)
 {
-    cudaError_t e = cudaMemcpyAsync(c->h_pinned, c->G.status, sizeof(u32), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->G.status, 0, sizeof(u32), st);
+    u32 *h = reinterpret_cast<u32 *>(c->h_pinned) + w0;
+    cudaError_t e = cudaMemcpyAsync(h, c->G.status + w0, n * sizeof(u32), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->G.status + w0, 0, n * sizeof(u32), st);
     return e;
 }
 
-vc_status decode_status(const vc_circuit *c)
+vc_status decode_status(const vc_circuit *c, int w0, int n)
 {
-    const u32 s = *reinterpret_cast<const u32 *>(c->h_pinned);
+    u32 s = 0;
+    for (int k = 0; k < n; k++) s |= reinterpret_cast<const u32 *>(c->h_pinned)[w0 + k];
     if (s & ST_BAD_INPUT) return VC_EINVAL;
     if (s & ST_TIMEOUT) return VC_ETIMEOUT;
     return VC_OK;
 }
 
-static vc_status read_status_and_clear(vc_circuit *c, cudaStream_t st)
+static vc_status read_status_and_clear(vc_circuit *c, cudaStream_t st, int w0 = 0, int n = 1)
 {
-    cudaError_t e = queue_status(c, st);
+    cudaError_t e = queue_status(c, st, w0, n);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return VC_ECUDA;
-    return decode_status(c);
+    return decode_status(c, w0, n);
 }
 
 extern "C" vc_status vc_prove(vc_circuit *c, const uint64_t *inputs, uint64_t seed, uint64_t *transcript,
@@ -1455,7 +1469,7 @@ extern "C" vc_status vc_circuit_sync(vc_circuit *c, void *stream)
 {
     if (!c) return VC_EINVAL;
     DevGuard guard(c->device);
-    return read_status_and_clear(c, (cudaStream_t)stream);
+    return read_status_and_clear(c, (cudaStream_t)stream, 0, 2);  // the prover's and the verifier's words
 }
 
 extern "C" vc_status vc_evaluate(vc_circuit *c, const uint64_t *inputs, uint64_t *outputs, void *stream)
@@ -1482,6 +1496,31 @@ extern "C" vc_status vc_evaluate(vc_circuit *c, const uint64_t *inputs, uint64_t
     return read_status_and_clear(c, st);
 }
 
+// The transcript on the device for the verifier: in place, or copied into
+// the handle's transcript buffer.
+static cudaError_t verifier_transcript(vc_circuit *c, const uint64_t *transcript, int kt, cudaStream_t st,
+                                       const u64 **dtr)
+{
+    *dtr = transcript;
+    if (kt) return cudaSuccess;
+    *dtr = c->d_tr;
+    return cudaMemcpyAsync(c->d_tr, transcript, c->tr_len * sizeof(u64), cudaMemcpyHostToDevice, st);
+}
+
+// After a verifier launch: asynchronous return, or wait for the accept bit
+// and the verifier's status word.
+static vc_status verifier_finish(vc_circuit *c, bool async, int ka, int *accept, cudaStream_t st)
+{
+    if (async) return cudaGetLastError() == cudaSuccess ? VC_OK : VC_ECUDA;
+    cudaError_t e = cudaMemcpyAsync(c->h_pinned + 8, c->d_result, 4 * sizeof(u64), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return VC_ECUDA;
+    vc_status s = read_status_and_clear(c, st, 1, 1);
+    if (s != VC_OK) return s;
+    if (!ka) *accept = c->h_pinned[8 + 2] ? 1 : 0;
+    return VC_OK;
+}
+
 extern "C" vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t seed, const uint64_t *transcript,
                                int *accept, void *stream)
 {
@@ -1493,6 +1532,7 @@ extern "C" vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t s
     const int ka = ptr_kind(accept, c->device);
     if (ki < 0 || kt < 0 || ka < 0) return VC_EINVAL;
     if (!ka) *accept = 0;
+    c->vin_pending = false;  // this call reuses the input pass's scratch
     const u64 nin = u64(1) << c->s[c->d];
     cudaError_t e = cudaSuccess;
     // the input MLE reads the inputs once: in place when the device can address
@@ -1502,32 +1542,25 @@ extern "C" vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t s
         e = cudaMemcpyAsync(c->V[c->d], inputs, nin * sizeof(u64), cudaMemcpyDefault, st);
         din = c->V[c->d];
     }
-    const u64 *dtr = transcript;
-    if (e == cudaSuccess && !kt) {
-        e = cudaMemcpyAsync(c->d_tr, transcript, c->tr_len * sizeof(u64), cudaMemcpyHostToDevice, st);
-        dtr = c->d_tr;
-    }
+    const u64 *dtr = nullptr;
+    if (e == cudaSuccess) e = verifier_transcript(c, transcript, kt, st, &dtr);
     if (e != cudaSuccess) return VC_ECUDA;
     // the verifier's launches are one captured graph; its first node writes
     // the per-call pointers and seed, with arguments set before each launch
     if (!c->vexec) {
         auto enqueue = [&](cudaStream_t cs) {
-            launch_vparams(c->d_G, c->d_vp, 0, nullptr, nullptr, nullptr, c->d_result, cs);
+            launch_vparams(c->d_Gv, c->d_vp, 0, nullptr, nullptr, nullptr, c->d_result, cs);
             cudaEventRecord(c->P.ev_fork, cs);
             cudaStreamWaitEvent(c->P.aux, c->P.ev_fork, 0);
-            launch_coins(c->d_G, 1, c->d_eq_verify, (int)c->eq_verify.size(), nullptr, nullptr, 0, cs);
-            launch_verify(c->d_G, c->G, c->Vd, c->s[c->d], c->s[0], c->d_explicit_layers,
+            launch_coins(c->d_Gv, 1, c->d_eq_verify, (int)c->eq_verify.size(), nullptr, nullptr, 0, cs);
+            launch_verify(c->d_Gv, c->Gv, c->Vd, c->s[c->d], c->s[0], c->d_explicit_layers,
                           (int)c->explicit_layers.size(), c->P.aux, c->P.ev_tables, cs);
         };
         e = capture_graph(c->P.cap, enqueue, &c->vexec, vparams_kernel(), &c->vgraph, &c->vpnode, &c->vpkp);
-        if (e != cudaSuccess) {
-            if (c->vexec) cudaGraphExecDestroy(c->vexec);
-            c->vexec = nullptr;
-            return VC_ECUDA;
-        }
+        if (e != cudaSuccess) return VC_ECUDA;
     }
     {
-        Globals *G = c->d_G;
+        Globals *G = c->d_Gv;
         VerifyPtrs *vp = c->d_vp;
         int *acc_out = ka ? accept : nullptr;
         u64 *res = c->d_result;
@@ -1536,14 +1569,80 @@ extern "C" vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t s
     }
     if (e == cudaSuccess) e = cudaGraphLaunch(c->vexec, st);
     if (e != cudaSuccess) return VC_ECUDA;
-    if (ka && ki && kt) return cudaGetLastError() == cudaSuccess ? VC_OK : VC_ECUDA;
-    e = cudaMemcpyAsync(c->h_pinned + 8, c->d_result, 4 * sizeof(u64), cudaMemcpyDeviceToHost, st);
+    return verifier_finish(c, ka && ki && kt, ka, accept, st);
+}
+
+extern "C" vc_status vc_verify_input(vc_circuit *c, const uint64_t *inputs, uint64_t seed, void *stream)
+{
+    if (!c || !inputs) return VC_EINVAL;
+    DevGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const void *mapped = nullptr;
+    const int ki = ptr_kind(inputs, c->device, &mapped);
+    const u64 *din = ki > 0 ? inputs : static_cast<const u64 *>(mapped);
+    if (ki < 0 || !din) return VC_EINVAL;  // the pass reads its inputs in place
+    cudaError_t e = cudaSuccess;
+    if (!c->vin_exec) {
+        auto enqueue = [&](cudaStream_t cs) {
+            launch_vparams_in(c->d_Gv, c->d_vp, 0, nullptr, cs);
+            cudaEventRecord(c->P.ev_fork, cs);
+            cudaStreamWaitEvent(c->P.aux, c->P.ev_fork, 0);
+            launch_verify_input(c->d_Gv, c->Gv, c->Vd, c->s[c->d], c->s[0], c->P.aux);
+            cudaEventRecord(c->P.ev_tables, c->P.aux);
+            launch_coins(c->d_Gv, 1, nullptr, 0, nullptr, nullptr, 0, cs);
+            cudaStreamWaitEvent(cs, c->P.ev_tables, 0);
+        };
+        e = capture_graph(c->P.cap, enqueue, &c->vin_exec, vparams_in_kernel(), &c->vin_graph, &c->vin_node,
+                          &c->vin_kp);
+        if (e != cudaSuccess) return VC_ECUDA;
+    }
+    Globals *G = c->d_Gv;
+    VerifyPtrs *vp = c->d_vp;
+    void *args[4] = {&G, &vp, &seed, &din};
+    e = set_node_args(c->vin_exec, c->vin_node, c->vin_kp, args);
+    if (e == cudaSuccess) e = cudaGraphLaunch(c->vin_exec, st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return VC_ECUDA;
-    vc_status s = read_status_and_clear(c, st);
-    if (s != VC_OK) return s;
-    if (!ka) *accept = c->h_pinned[8 + 2] ? 1 : 0;
+    c->vin_pending = true;
+    c->vin_seed = seed;
+    c->vin_sync = ki == 0;
     return VC_OK;
+}
+
+extern "C" vc_status vc_verify_transcript(vc_circuit *c, uint64_t seed, const uint64_t *transcript, int *accept,
+                                          void *stream)
+{
+    if (!c || !transcript || !accept) return VC_EINVAL;
+    if (!c->vin_pending || c->vin_seed != seed) return VC_EINVAL;
+    DevGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int kt = ptr_kind(transcript, c->device), ka = ptr_kind(accept, c->device);
+    if (kt < 0 || ka < 0) return VC_EINVAL;
+    c->vin_pending = false;
+    if (!ka) *accept = 0;
+    const u64 *dtr = nullptr;
+    cudaError_t e = verifier_transcript(c, transcript, kt, st, &dtr);
+    if (e != cudaSuccess) return VC_ECUDA;
+    if (!c->vtr_exec) {
+        auto enqueue = [&](cudaStream_t cs) {
+            launch_vparams_tr(c->d_vp, nullptr, nullptr, c->d_result, cs);
+            // eq tables of explicit layers (their add~/mult~ need them)
+            launch_coins(c->d_Gv, 0, c->d_eq_verify, (int)c->eq_verify.size(), nullptr, nullptr, 0, cs);
+            launch_verify_transcript(c->d_Gv, c->Gv, c->Vd, c->s[c->d], c->s[0], c->d_explicit_layers,
+                                     (int)c->explicit_layers.size(), cs);
+        };
+        e = capture_graph(c->P.cap, enqueue, &c->vtr_exec, vparams_tr_kernel(), &c->vtr_graph, &c->vtr_node,
+                          &c->vtr_kp);
+        if (e != cudaSuccess) return VC_ECUDA;
+    }
+    VerifyPtrs *vp = c->d_vp;
+    int *acc_out = ka ? accept : nullptr;
+    u64 *res = c->d_result;
+    void *args[4] = {&vp, &dtr, &acc_out, &res};
+    e = set_node_args(c->vtr_exec, c->vtr_node, c->vtr_kp, args);
+    if (e == cudaSuccess) e = cudaGraphLaunch(c->vtr_exec, st);
+    if (e != cudaSuccess) return VC_ECUDA;
+    return verifier_finish(c, ka && kt && !c->vin_sync, ka, accept, st);
 }
 
 extern "C" vc_status vc_circuit_set_stage_events(vc_circuit *c, void *const *events)
@@ -1576,6 +1675,9 @@ extern "C" vc_status vc_circuit_get_info(const vc_circuit *c, vc_circuit_info *i
     I.prove_launches = (uint32_t)count_launches(c->P);
     // parameters, coins and eq tables, input/output MLE, wiring (EXPLICIT only), checks
     I.verify_launches = (uint32_t)(4 + (c->explicit_layers.empty() ? 0 : 1));
+    // input pass: parameters, coins, input MLE; transcript pass: parameters,
+    // eq tables and wiring (EXPLICIT only), output MLE, checks
+    I.verify2_launches = (uint32_t)(6 + (c->explicit_layers.empty() ? 0 : 2));
     I.wave_tasks = (uint32_t)(c->P.groupsA.empty() ? 0 : c->P.groupsA[0].size());
     *info = I;
     return VC_OK;

@@ -53,7 +53,7 @@ class CircuitInfo(ctypes.Structure):
                 ("transcript_len", ctypes.c_uint64), ("gates", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64), ("prove_launches", ctypes.c_uint32),
                 ("verify_launches", ctypes.c_uint32), ("wave_tasks", ctypes.c_uint32),
-                ("pad", ctypes.c_uint32)]
+                ("verify2_launches", ctypes.c_uint32)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -125,6 +125,8 @@ def lib():
                                              vp]
             L.vc_circuit_sync.argtypes = [vp, vp]
             L.vc_verify.argtypes = [vp, vp, ctypes.c_uint64, vp, ctypes.POINTER(ctypes.c_int), vp]
+            L.vc_verify_input.argtypes = [vp, vp, ctypes.c_uint64, vp]
+            L.vc_verify_transcript.argtypes = [vp, ctypes.c_uint64, vp, ctypes.POINTER(ctypes.c_int), vp]
             L.vc_prove_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), _u64p, ctypes.POINTER(vp),
                                          ctypes.c_int, vp]
             L.vc_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
@@ -161,7 +163,8 @@ def lib():
                          "vc_server_submit", "vc_server_poll", "vc_server_wait", "vc_server_get_stats",
                          "vc_autotune", "vc_circuit_create_tiles", "vc_circuit_get_tiles", "vc_prove_pergate",
                          "vc_circuit_create_ex", "vc_f2sp_create", "vc_f2sp_destroy", "vc_f2sp_prove",
-                         "vc_f2sp_verify_begin", "vc_f2sp_verify_absorb", "vc_f2sp_verify_end"):
+                         "vc_f2sp_verify_begin", "vc_f2sp_verify_absorb", "vc_f2sp_verify_end",
+                         "vc_verify_input", "vc_verify_transcript"):
                 getattr(L, name).restype = st
             _lib = L
     return _lib
@@ -354,6 +357,35 @@ def vc_f2sp_verify_end(s, proof, stream=None, device: int = 0):
 
 def vc_circuit_sync(h, stream=None, device: int = 0):
     _check(lib().vc_circuit_sync(h, _stream(stream, device)), "vc_circuit_sync")
+
+
+def vc_verify_input(h, inputs, seed: int, stream=None, device: int = 0):
+    """The verifier's input pass for `seed` (coins and the input's MLE at the
+    final point): inputs on the device or in page-locked host memory, read in
+    place; asynchronous.  May run on another stream beside a proof."""
+    nin, _, _ = _shapes[h]
+    _need(inputs, nin, "inputs")
+    _check(lib().vc_verify_input(h, _ptr(inputs), seed & 0xFFFFFFFFFFFFFFFF, _stream(stream, device)),
+           "vc_verify_input")
+
+
+def vc_verify_transcript(h, seed: int, transcript, stream=None, device: int = 0, accept=None) -> bool:
+    """The rest of the verification, after vc_verify_input for the same seed.
+    Returns the accept bit; with `accept` (a CUDA int32 tensor) the call is
+    asynchronous where vc_verify's would be and the bit is written there."""
+    _, _, ntr = _shapes[h]
+    _need(transcript, ntr, "transcript")
+    if accept is not None:
+        if accept.element_size() != 4 or accept.numel() < 1:
+            raise ValueError("accept must be an int32 tensor")
+        _check(lib().vc_verify_transcript(h, seed & 0xFFFFFFFFFFFFFFFF, _ptr(transcript),
+                                          ctypes.cast(ctypes.c_void_p(accept.data_ptr()), ctypes.POINTER(ctypes.c_int)),
+                                          _stream(stream, device)), "vc_verify_transcript")
+        return None
+    acc = ctypes.c_int(0)
+    _check(lib().vc_verify_transcript(h, seed & 0xFFFFFFFFFFFFFFFF, _ptr(transcript), ctypes.byref(acc),
+                                      _stream(stream, device)), "vc_verify_transcript")
+    return bool(acc.value)
 
 
 def vc_verify(h, inputs, seed: int, transcript, stream=None, device: int = 0, accept=None) -> bool:

@@ -93,8 +93,10 @@ def test_noncanonical_input_reported():
 def test_input_memory_kinds_agree(family, logn):
     """Device inputs and page-locked host inputs are read in place by the first
     evaluation launch where it runs over the input layer; pageable host inputs
-    are copied.  All give the oracle's transcript, and a later evaluation on
-    the handle reads its own inputs, not the earlier proof's buffer."""
+    are copied.  All give the oracle's transcript, which the verifier accepts
+    from each kind of input memory (and a forged last entry it rejects); a
+    later evaluation on the handle reads its own inputs, not the earlier
+    proof's buffer."""
     widths, kinds = circuits.by_name(family, logn)
     x = I.job_inputs(family, logn, 21)
     want = oracle_prove(widths, kinds, x, 77)
@@ -108,6 +110,12 @@ def test_input_memory_kinds_agree(family, logn):
             vc.vc_prove(h, src, 77, tr)
             vc.vc_circuit_sync(h)
             assert (to_np(tr) == want).all()
+            # the verifier's input MLE reads the same three kinds of input memory
+            assert vc.vc_verify(h, src, 77, tr)
+            assert vc.vc_verify(h, src, 77, to_np(tr))
+            forged = tr.clone()
+            forged[-1] = (int(forged[-1]) + 1) % P
+            assert not vc.vc_verify(h, src, 77, forged)
         # the last proof read xd in place: overwrite it, then evaluate other inputs
         vc.vc_prove(h, xd, 78, tr)
         vc.vc_circuit_sync(h)

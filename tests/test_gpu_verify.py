@@ -172,3 +172,114 @@ def test_pm_and_mm1_verified(which):
             assert not vc.vc_verify(h, dev(x), 41, dev(bad))
     finally:
         vc.vc_circuit_destroy(h)
+
+
+# ---- the verifier in two passes: input pass (beside the proof), transcript pass
+
+def two_pass(h, x, seed, tr, stream=None):
+    vc.vc_verify_input(h, x, seed, stream=stream)
+    return vc.vc_verify_transcript(h, seed, tr, stream=stream)
+
+
+@pytest.mark.parametrize("family,logn", CASES + [("pm", 0), ("mm1", 0)])
+def test_two_pass_agrees_with_one_pass(family, logn):
+    """Honest transcripts accepted, changed ones rejected, exactly as vc_verify
+    decides, for structured and explicitly wired circuits."""
+    ex = None
+    if family == "pm":
+        widths, kinds, ex = circuits.pattern_match(5, 2)
+        x = I.pm_inputs(5, 2, 23)
+    elif family == "mm1":
+        widths, kinds, ex = circuits.matmult_check(2)
+        x = I.mm1_inputs(2, 24, errors=1)
+    else:
+        widths, kinds = circuits.by_name(family, logn)
+        x = I.job_inputs(family, logn, 19)
+    h = vc.vc_circuit_create(widths, kinds, ex)
+    rng = random.Random(7)
+    try:
+        xd = dev(x)
+        for seed in (3, 1 << 62):
+            tr = gpu_prove(widths, kinds, x, seed, ex)
+            assert two_pass(h, xd, seed, dev(tr))
+            assert two_pass(h, xd, seed, tr)  # host transcript: returns after the bit is read
+            for _ in range(4):
+                bad = tr.copy()
+                k = rng.randrange(len(tr))
+                bad[k] = (int(bad[k]) + 1 + rng.randrange(P - 1)) % P
+                assert not two_pass(h, xd, seed, dev(bad))
+                assert not vc.vc_verify(h, xd, seed, dev(bad))
+    finally:
+        vc.vc_circuit_destroy(h)
+
+
+def test_input_pass_beside_the_proof():
+    """The input pass runs on a second stream while the proof runs on the
+    first, on one handle; the transcript pass then accepts the proof."""
+    widths, kinds = circuits.f2(16)
+    h = vc.vc_circuit_create(widths, kinds)
+    side = torch.cuda.Stream()
+    main = torch.cuda.current_stream()
+    try:
+        n = vc.vc_transcript_len(h)
+        acc = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for seed in (5, 6, 7):
+            x = I.f2_inputs(16, 1 << 16, seed)
+            xd, tr = dev(x), torch.empty(n, dtype=torch.int64, device="cuda")
+            start, done = torch.cuda.Event(), torch.cuda.Event()
+            start.record(main)
+            side.wait_event(start)
+            vc.vc_verify_input(h, xd, seed, stream=side)
+            done.record(side)
+            vc.vc_prove(h, xd, seed, tr)
+            main.wait_event(done)
+            acc.zero_()
+            vc.vc_verify_transcript(h, seed, tr, accept=acc)
+            vc.vc_circuit_sync(h)
+            assert int(acc.item()) == 1
+            if seed == 5:
+                assert (to_np(tr) == oracle.Circuit(widths, kinds).prove(x, seed)).all()
+    finally:
+        torch.cuda.synchronize()
+        vc.vc_circuit_destroy(h)
+
+
+def test_two_pass_misuse_and_bad_inputs():
+    widths, kinds = circuits.f2(6)
+    x = I.f2_inputs(6, 1 << 16, 4)
+    tr = gpu_prove(widths, kinds, x, 8)
+    h = vc.vc_circuit_create(widths, kinds)
+    try:
+        def einval(f, *a, **k):
+            with pytest.raises(vc.VcError) as e:
+                f(*a, **k)
+            assert e.value.status == vc.VC_EINVAL
+
+        einval(vc.vc_verify_transcript, h, 8, tr)           # no input pass
+        vc.vc_verify_input(h, dev(x), 8)
+        einval(vc.vc_verify_transcript, h, 9, tr)           # another seed
+        assert vc.vc_verify_transcript(h, 8, tr)
+        einval(vc.vc_verify_transcript, h, 8, tr)           # the pass was consumed
+        vc.vc_verify_input(h, dev(x), 8)
+        assert vc.vc_verify(h, dev(x), 8, dev(tr))          # a one-pass call in between
+        einval(vc.vc_verify_transcript, h, 8, tr)
+        einval(vc.vc_verify_input, h, np.ascontiguousarray(x), 8)  # pageable host inputs
+        # page-locked host inputs are read in place
+        xp = torch.from_numpy(np.ascontiguousarray(x).view(np.int64).copy()).pin_memory()
+        vc.vc_verify_input(h, xp, 8)
+        assert vc.vc_verify_transcript(h, 8, dev(tr))
+        # a non-canonical input: reported by the synchronous transcript pass,
+        # or latched for vc_circuit_sync by the asynchronous one
+        bad = xp.clone().pin_memory()
+        bad[2] = P
+        vc.vc_verify_input(h, bad, 8)
+        einval(vc.vc_verify_transcript, h, 8, dev(tr))
+        yd = dev(x)
+        yd[2] = P
+        acc = torch.zeros(1, dtype=torch.int32, device="cuda")
+        vc.vc_verify_input(h, yd, 8)
+        vc.vc_verify_transcript(h, 8, dev(tr), accept=acc)
+        einval(vc.vc_circuit_sync, h)
+        vc.vc_circuit_sync(h)
+    finally:
+        vc.vc_circuit_destroy(h)
