@@ -367,16 +367,17 @@ def run_ours(args):
     side = torch.cuda.Stream()
     ev_start, ev_input = torch.cuda.Event(), torch.cuda.Event()
 
-    def step(seed, x=xd, t=tr, a=acc, input_first=False):
+    def step(seed, start, x=xd, t=tr, a=acc, input_first=False):
         # the proof on the main stream; the verifier's input pass (its coins and
         # the inputs' MLE at the final point, fixed by the seed alone) beside it
-        # on a second stream; then the transcript pass
-        ev_start.record(main)
-        side.wait_event(ev_start)
+        # on a second stream, from the step's start event `start` on; then the
+        # transcript pass
         if input_first:  # a proof into a host transcript returns when it is done
+            side.wait_event(start)
             vc.vc_verify_input(h, x, seed, stream=side)
         vc.vc_prove(h, x, seed, t)
         if not input_first:
+            side.wait_event(start)
             vc.vc_verify_input(h, x, seed, stream=side)
         ev_input.record(side)
         main.wait_event(ev_input)
@@ -384,7 +385,8 @@ def run_ours(args):
 
     for w in range(args.warmup):
         flush.zero_()
-        step(100 + w)
+        ev_start.record(main)
+        step(100 + w, ev_start)
     torch.cuda.synchronize()
     vc.vc_circuit_sync(h)
     assert int(acc.item()) == 1, "warm-up proof rejected"
@@ -400,7 +402,7 @@ def run_ours(args):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        step(1 + k)
+        step(1 + k, e0)
         e1.record()
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -439,12 +441,14 @@ def run_ours(args):
         ablation = run_ablation(h, xd, tr, flush)
         residency = run_residency(widths, kinds, xd, flush)
         special = run_special_purpose(flush)
-    step(999, xh, trh, None, True)
+    ev_start.record(main)
+    step(999, ev_start, xh, trh, None, True)
     e2e_ms = []
     for k in range(max(3, args.steps // 2)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ok = step(500 + k, xh, trh, None, True)  # host transcript, accept bit read back
+        ev_start.record(main)
+        ok = step(500 + k, ev_start, xh, trh, None, True)  # host transcript, accept bit read back
         e2e_ms.append(1000 * (time.perf_counter() - t0))
         assert ok
     e2e_ms_mean = replicas.max_over_ranks(statistics.mean(e2e_ms), dist, "cuda")

@@ -171,12 +171,12 @@ struct vc_circuit {
     cudaGraph_t vgraph = nullptr;
     cudaGraphNode_t vpnode = nullptr;
     cudaKernelNodeParams vpkp{};
-    // the verifier in two passes: input (coins and the input's MLE) and
-    // transcript (everything else), each a captured graph
-    cudaGraphExec_t vin_exec = nullptr, vtr_exec = nullptr;
-    cudaGraph_t vin_graph = nullptr, vtr_graph = nullptr;
-    cudaGraphNode_t vin_node = nullptr, vtr_node = nullptr;
-    cudaKernelNodeParams vin_kp{}, vtr_kp{};
+    // the verifier in two passes: input (coins and the input's MLE; a captured
+    // graph) and transcript (everything else; plain launches)
+    cudaGraphExec_t vin_exec = nullptr;
+    cudaGraph_t vin_graph = nullptr;
+    cudaGraphNode_t vin_node = nullptr;
+    cudaKernelNodeParams vin_kp{};
     bool vin_pending = false;  // an input pass is queued and not yet consumed
     u64 vin_seed = 0;
     bool vin_sync = false;     // its inputs were host memory: the transcript pass reads the status

@@ -9,7 +9,9 @@
 // (q_{i-1}(tau_{i-1})), all layers are checked concurrently, a warp per layer,
 // and every round by its own thread.  The accept bit is the conjunction of
 // exactly the checks the sequential verifier makes.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
+
 #include "coins.cuh"
 
 #define VM_NT 256
@@ -25,16 +27,19 @@
 // per thread, from two 16-entry tables) x (the rest: per iteration, from a
 // small table).  A non-canonical input latches ST_BAD_INPUT; a non-canonical
 // output entry marks the transcript bad.
-// A launch covers blocks [b0, b0 + gridDim.x) of the two ranges.
+// A launch covers blocks [b0, b0 + gridDim.x) of the two ranges; src_arg,
+// if given, is the source of a launch within one range (else vp's inputs and
+// transcript).
 __global__ void __launch_bounds__(VM_NT) k_vmle(const Globals *Gd, const VerifyPtrs *vp, u32 nd, u32 lin, u32 n0,
-                                                u32 lout, u32 nin_blocks, u32 b0, u64 *part, u32 *status, u64 *result)
+                                                u32 lout, u32 nin_blocks, u32 b0, const u64 *src_arg, u64 *part,
+                                                u32 *status, u64 *result)
 {
     const Globals &G = *Gd;
     const u32 blk = blockIdx.x + b0;
     const bool inp = blk < nin_blocks;
     const u32 nz = inp ? nd : n0, lr = inp ? lin : lout;
     const u32 b = inp ? blk : blk - nin_blocks;
-    const u64 *src = inp ? vp->inputs : vp->tr;  // the claimed outputs open the transcript
+    const u64 *src = src_arg ? src_arg : (inp ? vp->inputs : vp->tr);  // the claimed outputs open the transcript
     __shared__ u64 z[32], zm[32], mid[1u << VM_MID], t1[16], t2[16], bfac;
     const bool rej = draws_rejected(G);
     if (threadIdx.x < nz) {
@@ -280,33 +285,50 @@ __device__ void wiring_warp(u32 kind, u32 si, u32 sn, const u64 *p, const u64 *w
 }
 
 #define VC_NT 256
+#define VC_CL 8  // CTAs of the check launch: one thread-block cluster
 
-// All checks of the verifier, concurrently.  Warp i < d checks layer i: its
-// starting claim (the claimed outputs' MLE at z_0 for i = 0, else
-// q_{i-1}(tau_{i-1})), round 0 (g_0(0) + g_0(1) = starting claim), the end of
-// the layer (g_{n-1}(r_{n-1}) = eq(z_i, r_P)[add~ (v1 + v2) + mult~ v1 v2], or the
+// All checks of the verifier in one cluster of VC_CL CTAs; the accept bit is
+// combined through the cluster's distributed shared memory (no grid-wide
+// atomics).  Warp w of the cluster checks layers w, w + 32 VC_CL, ...: the
+// layer's starting claim (for layer 0 the claimed outputs' MLE at z_0: formed
+// by the warp itself when there are at most VC_OUT_INLINE outputs, else
+// summed from k_vmle's partials; for layer i > 0, q_{i-1}(tau_{i-1})), round
+// 0 (g_0(0) + g_0(1) = starting claim), the end of the layer
+// (g_{n-1}(r_{n-1}) = eq(z_i, r_P)[add~ (v1 + v2) + mult~ v1 v2], or the
 // starting claim itself when the layer has no rounds) and, for the last
-// layer, q(tau) = the input's MLE at z_d.  The remaining threads check rounds
-// j >= 1 (g_j(0) + g_j(1) = g_{j-1}(r_{j-1})) and that every transcript entry is
-// canonical.  The last CTA to finish turns the failure flags into the accept
-// bit.  The accept bit is the conjunction of exactly the sequential
-// verifier's checks.
-__global__ void __launch_bounds__(VC_NT) k_vcheck(Globals G, VerifyDev V, const u32 *round_layer, u32 nrounds)
+// layer, q(tau) = the input's MLE at z_d.  Every thread checks rounds j >= 1
+// (g_j(0) + g_j(1) = g_{j-1}(r_{j-1})) of a grid-stride share of the global
+// rounds, and its share of the transcript entries for canonical form.  The
+// accept bit is the conjunction of exactly the sequential verifier's checks.
+// tr_arg: the transcript and accept pointer given directly (NULL: from V.vp).
+__global__ void __cluster_dims__(VC_CL, 1, 1) __launch_bounds__(VC_NT)
+    k_vcheck(Globals G, VerifyDev V, const u64 *tr_arg, int *accept_arg)
 {
-    const u64 *const tr = V.vp->tr;
+    namespace cg = cooperative_groups;
+    const u64 *const tr = tr_arg ? tr_arg : V.vp->tr;
     const u32 lane = threadIdx.x & 31;
-    const u64 g = blockIdx.x * (u64)VC_NT + threadIdx.x;
-    const u64 gw = g >> 5;
-    const u64 nthreads = (u64)gridDim.x * VC_NT;
+    const u32 g = blockIdx.x * VC_NT + threadIdx.x, nthreads = VC_CL * VC_NT;
     u32 fail = 0;
-    if (gw < G.d) {
-        const u32 i = (u32)gw;
+    for (u32 i = g >> 5; i < G.d; i += nthreads >> 5) {
         const LayerDev &L = G.layers[i];
         const u32 si = L.s, sn = L.sn, n = si + 2 * sn;
         const u64 *r = G.chal + L.chal_off;
         u64 start;
         if (i == 0) {
-            warp_record_sums<1>(V.mle_part + V.mle_blocks, V.mle_out_blocks, lane, &start);
+            if (V.mle_out_blocks == 0) {
+                // every output's eq weight a direct product over the s_0
+                // coordinates of z_0 (the first s_0 challenges)
+                u64 sum = 0;
+                for (u64 b = lane; b < G.S0; b += 32) {
+                    const u64 v = tr[b];
+                    u64 w = 1;
+                    for (u32 k = 0; k < si; k++) w = f_mul(w, ((b >> k) & 1) ? G.chal[k] : f_sub(1, G.chal[k]));
+                    sum = f_add(sum, f_mul(w, v >= FP_P ? 0 : v));  // a non-canonical entry fails the scan
+                }
+                start = warp_sum(sum);
+            } else {
+                warp_record_sums<1>(V.mle_part + V.mle_blocks, V.mle_out_blocks, lane, &start);
+            }
         } else {
             const LayerDev &Lp = G.layers[i - 1];
             start = lagrange_warp(tr + Lp.tr_q, Lp.sn, G.chal[Lp.chal_off + Lp.s + 2 * Lp.sn], G.invfact);
@@ -337,37 +359,32 @@ __global__ void __launch_bounds__(VC_NT) k_vcheck(Globals G, VerifyDev V, const 
             warp_record_sums<1>(V.mle_part, V.mle_blocks, lane, &in_mle);
             if (lane == 0 && fin != in_mle) fail = 1;
         }
-    } else {
-        const u64 rho = g - 32ull * G.d;
-        if (rho < nrounds) {
-            const u32 i = round_layer[rho] >> 8, j = round_layer[rho] & 0xFF;
-            if (j > 0) {
-                const LayerDev &L = G.layers[i];
-                const u64 *m = tr + L.tr_msg + 3ull * j;
-                const u64 prev = interp3(m[-3], m[-2], m[-1], G.chal[L.chal_off + j - 1]);
-                if (f_add(m[0], m[1]) != prev) fail = 1;
-            }
+    }
+    for (u32 rho = g; rho < V.nrounds; rho += nthreads) {
+        const u32 i = V.round_layer[rho] >> 8, j = V.round_layer[rho] & 0xFF;
+        if (j > 0) {
+            const LayerDev &L = G.layers[i];
+            const u64 *m = tr + L.tr_msg + 3ull * j;
+            const u64 prev = interp3(m[-3], m[-2], m[-1], G.chal[L.chal_off + j - 1]);
+            if (f_add(m[0], m[1]) != prev) fail = 1;
         }
     }
     for (u64 k = g; k < V.tr_len; k += nthreads)
         if (tr[k] >= FP_P) fail = 1;
-    if (__any_sync(0xffffffffu, fail != 0) && lane == 0) atomicOr(reinterpret_cast<unsigned long long *>(&V.result[3]), 1ull);
-    // last CTA: publish the accept bit and reset the counter for the next call
-    __shared__ bool s_last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned int done = atomicAdd(V.counter, 1u);
-        s_last = (done == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        __threadfence();
-        const u64 bad = atomicOr(reinterpret_cast<unsigned long long *>(&V.result[3]), 0ull);
+    // each CTA's verdict into CTA 0's shared memory, then CTA 0 decides
+    __shared__ u32 s_fail[VC_CL];
+    fail = __syncthreads_or(fail);
+    cg::cluster_group cluster = cg::this_cluster();
+    if (threadIdx.x == 0) *cluster.map_shared_rank(&s_fail[cluster.block_rank()], 0) = fail ? 1u : 0u;
+    cluster.sync();
+    if (cluster.block_rank() == 0 && threadIdx.x == 0) {
+        u32 bad = 0;
+        for (int k = 0; k < VC_CL; k++) bad |= s_fail[k];
         const int acc = bad ? 0 : 1;
         V.result[2] = (u64)acc;
-        if (V.vp->accept_out) *V.vp->accept_out = acc;
-        *V.counter = 0;
+        V.result[3] = bad;
+        int *const accept_out = tr_arg ? accept_arg : V.vp->accept_out;
+        if (accept_out) *accept_out = acc;
     }
 }
 
@@ -402,33 +419,22 @@ void launch_vparams(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *tr, const u
 
 const void *vparams_kernel() { return reinterpret_cast<const void *>(k_vparams); }
 
-// Parameters of the verifier's input pass (seed, inputs) and of its
-// transcript pass (transcript, accept pointer; clears the result words).
+// Parameters of the verifier's input pass (seed, inputs).
 __global__ void k_vparams_in(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *inputs)
 {
     G->seed = seed;
     vp->inputs = inputs;
 }
 
-__global__ void k_vparams_tr(VerifyPtrs *vp, const u64 *tr, int *accept, u64 *result)
-{
-    vp->tr = tr;
-    vp->accept_out = accept;
-    for (int k = 0; k < VC_RESULT_WORDS; k++) result[k] = 0;
-}
 
 void launch_vparams_in(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *inputs, cudaStream_t st)
 {
     k_vparams_in<<<1, 1, 0, st>>>(G, vp, seed, inputs);
 }
 
-void launch_vparams_tr(VerifyPtrs *vp, const u64 *tr, int *accept, u64 *result, cudaStream_t st)
-{
-    k_vparams_tr<<<1, 1, 0, st>>>(vp, tr, accept, result);
-}
 
 const void *vparams_in_kernel() { return reinterpret_cast<const void *>(k_vparams_in); }
-const void *vparams_tr_kernel() { return reinterpret_cast<const void *>(k_vparams_tr); }
+
 
 // Entries per CTA (log2) of the MLE partial sums for a point of n coordinates.
 u32 vmle_log(u32 n) { return n < 11 ? n : 11; }
@@ -439,31 +445,27 @@ void launch_verify(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 
     // the MLE partial sums need only the seed: they run beside the coin launch
     // (st_mle forked from st before it); the checks wait for both
     k_vmle<<<V.mle_blocks + V.mle_out_blocks, VM_NT, 0, st_mle>>>(Gd, V.vp, nd, vmle_log(nd), n0, vmle_log(n0),
-                                                                   V.mle_blocks, 0, V.mle_part, G.status, V.result);
+                                                                   V.mle_blocks, 0, nullptr, V.mle_part, G.status,
+                                                                   V.result);
     cudaEventRecord(ev_join, st_mle);
     cudaStreamWaitEvent(st, ev_join, 0);
     if (n_explicit > 0) k_vwire<<<n_explicit, VM_NT, 0, st>>>(G, explicit_layers, V.wire);
-    const u64 threads = 32ull * G.d + V.nrounds;
-    u64 blocks = (threads + VC_NT - 1) / VC_NT;
-    if (blocks < 1) blocks = 1;
-    k_vcheck<<<(unsigned)blocks, VC_NT, 0, st>>>(G, V, V.round_layer, V.nrounds);
+    k_vcheck<<<VC_CL, VC_NT, 0, st>>>(G, V, nullptr, nullptr);
 }
 
 void launch_verify_input(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0, cudaStream_t st)
 {
-    k_vmle<<<V.mle_blocks, VM_NT, 0, st>>>(Gd, V.vp, nd, vmle_log(nd), n0, vmle_log(n0), V.mle_blocks, 0,
+    k_vmle<<<V.mle_blocks, VM_NT, 0, st>>>(Gd, V.vp, nd, vmle_log(nd), n0, vmle_log(n0), V.mle_blocks, 0, nullptr,
                                            V.mle_part, G.status, V.result);
 }
 
 void launch_verify_transcript(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0,
-                              const u32 *explicit_layers, int n_explicit, cudaStream_t st)
+                              const u32 *explicit_layers, int n_explicit, const u64 *tr, int *accept,
+                              cudaStream_t st)
 {
     if (V.mle_out_blocks > 0)
         k_vmle<<<V.mle_out_blocks, VM_NT, 0, st>>>(Gd, V.vp, nd, vmle_log(nd), n0, vmle_log(n0), V.mle_blocks,
-                                                   V.mle_blocks, V.mle_part, G.status, V.result);
+                                                   V.mle_blocks, tr, V.mle_part, G.status, V.result);
     if (n_explicit > 0) k_vwire<<<n_explicit, VM_NT, 0, st>>>(G, explicit_layers, V.wire);
-    const u64 threads = 32ull * G.d + V.nrounds;
-    u64 blocks = (threads + VC_NT - 1) / VC_NT;
-    if (blocks < 1) blocks = 1;
-    k_vcheck<<<(unsigned)blocks, VC_NT, 0, st>>>(G, V, V.round_layer, V.nrounds);
+    k_vcheck<<<VC_CL, VC_NT, 0, st>>>(G, V, tr, accept);
 }

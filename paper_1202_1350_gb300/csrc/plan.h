@@ -342,8 +342,7 @@ struct VerifyDev {
     u64 *result;        // [0] input MLE, [1] output MLE, [2] accept flag, [3] bad-value flag
     u64 *wire;          // generic add~/mult~ per layer (EXPLICIT layers)
     u64 *claims;        // starting claim of every layer (d entries)
-    u32 mle_out_blocks; // blocks of the output-MLE partials (after the input's)
-    unsigned int *counter;  // CTAs of k_vcheck that finished (reset by the last)
+    u32 mle_out_blocks; // blocks of the output-MLE partials (after the input's; 0: formed by k_vcheck)
     const u32 *round_layer;  // per global round: layer << 8 | round within layer
     u32 nrounds;
 };
@@ -358,16 +357,19 @@ u32 vmle_log(u32 n);
 void launch_verify(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0, const u32 *explicit_layers,
                    int n_explicit, cudaStream_t st_mle, cudaEvent_t ev_join, cudaStream_t st);
 // The verifier in two passes.  Input pass: the input's MLE partial sums (the
-// coins are launched beside it by the caller).  Transcript pass: the claimed
-// outputs' MLE partial sums, add~/mult~ of explicit layers, the checks (the
-// eq tables of explicit layers are launched before it by the caller).
+// coins are launched beside it by the caller).  Transcript pass, with the
+// transcript and accept pointer as arguments: the claimed outputs' MLE
+// partial sums (many outputs only), add~/mult~ of explicit layers, the checks
+// (the eq tables of explicit layers are launched before it by the caller).
 void launch_verify_input(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0, cudaStream_t st);
 void launch_verify_transcript(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0,
-                              const u32 *explicit_layers, int n_explicit, cudaStream_t st);
+                              const u32 *explicit_layers, int n_explicit, const u64 *tr, int *accept,
+                              cudaStream_t st);
 void launch_vparams_in(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *inputs, cudaStream_t st);
-void launch_vparams_tr(VerifyPtrs *vp, const u64 *tr, int *accept, u64 *result, cudaStream_t st);
 const void *vparams_in_kernel();
-const void *vparams_tr_kernel();
+// Circuits with at most this many outputs have their claimed outputs' MLE
+// formed inside the check launch, by one warp (more: k_vmle partial sums).
+#define VC_OUT_INLINE 256u
 
 // Per-gate prover (k_pergate.cu): one descriptor per layer.
 struct PgLayer {

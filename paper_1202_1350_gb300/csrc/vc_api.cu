@@ -499,9 +499,8 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     const u64 mb = u64(1) << (c->s[d] - vmle_log(c->s[d]));
     const u64 mbo = u64(1) << (c->s[0] - vmle_log(c->s[0]));
     c->Vd.mle_blocks = (u32)mb;
-    c->Vd.mle_out_blocks = (u32)mbo;
+    c->Vd.mle_out_blocks = S(0) <= VC_OUT_INLINE ? 0u : (u32)mbo;  // few outputs: formed in the check launch
     c->Vd.mle_part = A.take<u64>(mb + mbo);
-    c->Vd.counter = A.take<unsigned int>(4);
     c->Vd.wire = A.take<u64>(2 * d + 2);
     c->Vd.claims = A.take<u64>(d + 1);
     c->round_layer.clear();
@@ -1143,9 +1142,9 @@ vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **
 void circuit_free(vc_circuit *c)
 {
     if (!c) return;
-    for (cudaGraphExec_t x : {c->vexec, c->vin_exec, c->vtr_exec})
+    for (cudaGraphExec_t x : {c->vexec, c->vin_exec})
         if (x) cudaGraphExecDestroy(x);
-    for (cudaGraph_t g : {c->vgraph, c->vin_graph, c->vtr_graph})
+    for (cudaGraph_t g : {c->vgraph, c->vin_graph})
         if (g) cudaGraphDestroy(g);
     if (c->pg_exec) cudaGraphExecDestroy(c->pg_exec);
     if (c->pg_arena) cudaFree(c->pg_arena);
@@ -1623,25 +1622,11 @@ extern "C" vc_status vc_verify_transcript(vc_circuit *c, uint64_t seed, const ui
     const u64 *dtr = nullptr;
     cudaError_t e = verifier_transcript(c, transcript, kt, st, &dtr);
     if (e != cudaSuccess) return VC_ECUDA;
-    if (!c->vtr_exec) {
-        auto enqueue = [&](cudaStream_t cs) {
-            launch_vparams_tr(c->d_vp, nullptr, nullptr, c->d_result, cs);
-            // eq tables of explicit layers (their add~/mult~ need them)
-            launch_coins(c->d_Gv, 0, c->d_eq_verify, (int)c->eq_verify.size(), nullptr, nullptr, 0, cs);
-            launch_verify_transcript(c->d_Gv, c->Gv, c->Vd, c->s[c->d], c->s[0], c->d_explicit_layers,
-                                     (int)c->explicit_layers.size(), cs);
-        };
-        e = capture_graph(c->P.cap, enqueue, &c->vtr_exec, vparams_tr_kernel(), &c->vtr_graph, &c->vtr_node,
-                          &c->vtr_kp);
-        if (e != cudaSuccess) return VC_ECUDA;
-    }
-    VerifyPtrs *vp = c->d_vp;
-    int *acc_out = ka ? accept : nullptr;
-    u64 *res = c->d_result;
-    void *args[4] = {&vp, &dtr, &acc_out, &res};
-    e = set_node_args(c->vtr_exec, c->vtr_node, c->vtr_kp, args);
-    if (e == cudaSuccess) e = cudaGraphLaunch(c->vtr_exec, st);
-    if (e != cudaSuccess) return VC_ECUDA;
+    // plain launches with the per-call pointers as arguments (one launch for
+    // structured circuits): nothing to capture, nothing to write first
+    launch_coins(c->d_Gv, 0, c->d_eq_verify, (int)c->eq_verify.size(), nullptr, nullptr, 0, st);
+    launch_verify_transcript(c->d_Gv, c->Gv, c->Vd, c->s[c->d], c->s[0], c->d_explicit_layers,
+                             (int)c->explicit_layers.size(), dtr, ka ? accept : nullptr, st);
     return verifier_finish(c, ka && kt && !c->vin_sync, ka, accept, st);
 }
 
@@ -1675,9 +1660,9 @@ extern "C" vc_status vc_circuit_get_info(const vc_circuit *c, vc_circuit_info *i
     I.prove_launches = (uint32_t)count_launches(c->P);
     // parameters, coins and eq tables, input/output MLE, wiring (EXPLICIT only), checks
     I.verify_launches = (uint32_t)(4 + (c->explicit_layers.empty() ? 0 : 1));
-    // input pass: parameters, coins, input MLE; transcript pass: parameters,
-    // eq tables and wiring (EXPLICIT only), output MLE, checks
-    I.verify2_launches = (uint32_t)(6 + (c->explicit_layers.empty() ? 0 : 2));
+    // input pass: parameters, coins, input MLE; transcript pass: eq tables
+    // and wiring (EXPLICIT only), output MLE (many outputs only), checks
+    I.verify2_launches = (uint32_t)(4 + (c->explicit_layers.empty() ? 0 : 2) + (c->Vd.mle_out_blocks ? 1 : 0));
     I.wave_tasks = (uint32_t)(c->P.groupsA.empty() ? 0 : c->P.groupsA[0].size());
     *info = I;
     return VC_OK;

@@ -181,10 +181,12 @@ def two_pass(h, x, seed, tr, stream=None):
     return vc.vc_verify_transcript(h, seed, tr, stream=stream)
 
 
-@pytest.mark.parametrize("family,logn", CASES + [("pm", 0), ("mm1", 0)])
+@pytest.mark.parametrize("family,logn", CASES + [("matmult", 5), ("pm", 0), ("mm1", 0)])
 def test_two_pass_agrees_with_one_pass(family, logn):
     """Honest transcripts accepted, changed ones rejected, exactly as vc_verify
-    decides, for structured and explicitly wired circuits."""
+    decides, for structured and explicitly wired circuits (MatMult n = 32:
+    2^10 outputs, whose MLE comes from partial sums; fewer outputs: formed in
+    the check launch)."""
     ex = None
     if family == "pm":
         widths, kinds, ex = circuits.pattern_match(5, 2)
