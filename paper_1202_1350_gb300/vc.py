@@ -99,6 +99,8 @@ def library_path() -> str:
 def lib():
     """Load libvc.so (raises if it has not been built)."""
     global _lib
+    if _lib is not None:
+        return _lib
     with _lock:
         if _lib is None:
             path = _build.LIB
@@ -201,16 +203,25 @@ def _numel(x) -> int:
     return int(x.size if isinstance(x, np.ndarray) else x.numel())
 
 
+_current_stream = None  # device -> raw handle of torch's current stream (resolved once)
+
+
 def _stream(stream, device: int):
+    """Raw cudaStream_t of `stream` (a torch stream or an int), else torch's
+    current stream on `device` (None without CUDA: the legacy default stream)."""
     if stream is not None:
         return stream if isinstance(stream, int) else stream.cuda_stream
-    try:
-        import torch
-        if torch.cuda.is_available():
-            return torch.cuda.current_stream(device).cuda_stream
-    except Exception:
-        pass
-    return None
+    global _current_stream
+    if _current_stream is None:
+        _current_stream = lambda d: None
+        try:
+            import torch
+            if torch.cuda.is_available():
+                raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+                _current_stream = raw if raw is not None else (lambda d: torch.cuda.current_stream(d).cuda_stream)
+        except Exception:
+            pass
+    return _current_stream(device)
 
 
 # --- C ABI ----------------------------------------------------------------------------
