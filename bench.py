@@ -150,7 +150,7 @@ def executed_work(widths, kinds, first_wave_log=12):
 # DRAM bytes (read + write) of one k_waves launch on this workload, from an ncu
 # capture of the current kernel; the V tables are mostly served from L2, so
 # this is below the algorithmic bytes
-K_WAVES_DRAM_BYTES = 25_566_720
+K_WAVES_DRAM_BYTES = 25_572_096
 
 
 def run_ablation(h, xd, tr, flush, reps=5):
