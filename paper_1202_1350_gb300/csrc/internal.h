@@ -96,7 +96,8 @@ struct Plan {
     // persistent wave launches: groups A (before the wiring tables are built)
     // and B (general waves over built tables), each one launch
     std::vector<std::vector<Task>> groupsA, groupsB;
-    std::vector<RoundRef> rounds;
+    std::vector<RoundRef> rounds;  // those with more than FINAL_WARP_MIN partials first (nbig of them)
+    u32 nbig = 0;
     std::vector<u32> outs;
     // device copies
     Item *d_checks = nullptr;

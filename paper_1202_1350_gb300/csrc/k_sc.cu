@@ -1000,66 +1000,95 @@ void launch_waves(const Globals *Gs, const LineWaveDev *lw, const ProdWave *pw, 
 }
 
 // --------------------------------------------------------------------------------
-// Final reduction into the transcript: a warp per round sums the chunks'
-// partials; the round's scalars turn the sums into g(0), g(1), g(2).
+// Final reduction into the transcript.  Rounds with more than
+// FINAL_WARP_MIN chunk partials (they come first in the round list) are
+// summed by a warp each; the rest, the great majority in a batch of small
+// circuits, by a thread each.  The round's scalars then turn the sums into
+// g(0), g(1), g(2).
 // --------------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_final(Globals *Gs, const SciDev *scis, const RoundRef *rounds,
-                                               int nrounds, const u32 *outs, int nouts)
+// The scalars a round's message needs besides its partial sums (loaded
+// before the sums, so that both sets of loads are in flight together).
+struct RoundScalars {
+    u64 ez, ch, v1, es, kap, c0, c1;
+};
+
+__device__ __forceinline__ RoundScalars round_scalars(const RoundRef &R)
 {
-    (void)scis;
-    const u32 lane = threadIdx.x & 31;
-    const u64 nwarps = ((u64)gridDim.x * blockDim.x) >> 5;
-    for (u64 gw = (blockIdx.x * (u64)blockDim.x + threadIdx.x) >> 5; gw < (u64)nrounds; gw += nwarps) {
-        const RoundRef R = rounds[gw];
-        const bool gen = R.kind >= PK_GEN_FIRST;
-        // the round's scalars, loaded while the partials are summed
-        u64 ez = 0, v1 = 0, ch = 0, es = 0, kap = 0, c0 = 0, c1 = 0;
-        if (lane == 0) {
-            ez = *R.ez;
-            if (R.defer) ch = *R.ch;
-            if (!gen) {
-                v1 = *R.v1;
-                ch = *R.ch;
-                es = *R.esum;
-                kap = *R.kap;
-                c0 = R.lc[0];
-                c1 = R.lc[1];
-            }
+    RoundScalars S{};
+    S.ez = *R.ez;
+    if (R.defer || R.kind < PK_GEN_FIRST) S.ch = *R.ch;
+    if (R.kind < PK_GEN_FIRST) {
+        S.v1 = *R.v1;
+        S.es = *R.esum;
+        S.kap = *R.kap;
+        S.c0 = R.lc[0];
+        S.c1 = R.lc[1];
+    }
+    return S;
+}
+
+// g(0), g(1), g(2) of round R from its canonical partial sums h, written to
+// the circuit's transcript.
+__device__ __forceinline__ void final_round(const Globals *Gs, const RoundRef &R, const RoundScalars &S,
+                                            const u64 (&h)[3])
+{
+    const bool gen = R.kind >= PK_GEN_FIRST;
+    const u64 ez = S.ez;
+    u64 g0, g1, g2;
+    if (gen) {
+        u64 sg = (R.kind == PK_GEN_TAB) ? 1 : ez;
+        if (R.defer) sg = f_mul(sg, f_sub(1, S.ch));  // TREE phase 2: 1 - r_0 left out of P, B
+        g0 = f_mul(sg, h[0]);
+        g1 = f_mul(sg, h[1]);
+        // h[2] is the leading coefficient: value at 2 = 2 h1 - h0 + 2 h2
+        g2 = f_mul(sg, f_add(f_sub(f_add(h[1], h[1]), h[0]), f_add(h[2], h[2])));
+    } else {
+        const u64 v1 = S.v1, ch = S.ch, es = S.es, kap = S.kap, c0 = S.c0, c1 = S.c1;
+        u64 sigma = 1, c2u = 0;
+        if (R.kind == PK_TREE3) {
+            sigma = f_mul(ez, f_sub(1, ch));
+            c2u = v1;
+        } else if (R.kind == PK_SQ3) {
+            sigma = f_mul(ez, v1);
         }
-        u64 *tr = Gs[R.circ].tr;
-        u64 h[3];
-        if (gen)
+        const u64 h0 = f_add(h[0], f_mul(c2u, es)), h1 = f_add(h[1], f_mul(c2u, es));
+        const u64 kj = f_mul(sigma, kap);
+        g0 = f_mul(kj, f_mul(c0, h0));
+        g1 = f_mul(kj, f_mul(c1, h1));
+        g2 = f_mul(kj, f_mul(f_sub(f_add(c1, c1), c0), f_sub(f_add(h1, h1), h0)));
+    }
+    u64 *tr = Gs[R.circ].tr;
+    tr[R.tr_pos] = g0;
+    tr[R.tr_pos + 1] = g1;
+    tr[R.tr_pos + 2] = g2;
+}
+
+__global__ void __launch_bounds__(256) k_final(Globals *Gs, const RoundRef *rounds, int nrounds, int nbig,
+                                               const u32 *outs, int nouts)
+{
+    const u32 lane = threadIdx.x & 31;
+    const u64 gt = blockIdx.x * (u64)blockDim.x + threadIdx.x, nthreads = (u64)gridDim.x * blockDim.x;
+    for (u64 gw = gt >> 5; gw < (u64)nbig; gw += nthreads >> 5) {
+        const RoundRef R = rounds[gw];
+        RoundScalars S{};
+        if (lane == 0) S = round_scalars(R);
+        u64 h[3] = {0, 0, 0};
+        if (R.kind >= PK_GEN_FIRST)
             warp_record_sums<3>(R.part_pos, R.nchunks, lane, h);
         else
             warp_record_sums<2>(R.part_pos, R.nchunks, lane, h);
-        if (lane == 0) {
-            u64 g0, g1, g2;
-            if (gen) {
-                u64 sg = (R.kind == PK_GEN_TAB) ? 1 : ez;
-                if (R.defer) sg = f_mul(sg, f_sub(1, ch));  // TREE phase 2: 1 - r_0 left out of P, B
-                g0 = f_mul(sg, h[0]);
-                g1 = f_mul(sg, h[1]);
-                // h[2] is the leading coefficient: value at 2 = 2 h1 - h0 + 2 h2
-                g2 = f_mul(sg, f_add(f_sub(f_add(h[1], h[1]), h[0]), f_add(h[2], h[2])));
-            } else {
-                u64 sigma = 1, c2u = 0;
-                if (R.kind == PK_TREE3) {
-                    sigma = f_mul(ez, f_sub(1, ch));
-                    c2u = v1;
-                } else if (R.kind == PK_SQ3) {
-                    sigma = f_mul(ez, v1);
-                }
-                const u64 h0 = f_add(h[0], f_mul(c2u, es)), h1 = f_add(h[1], f_mul(c2u, es));
-                const u64 kj = f_mul(sigma, kap);
-                g0 = f_mul(kj, f_mul(c0, h0));
-                g1 = f_mul(kj, f_mul(c1, h1));
-                g2 = f_mul(kj, f_mul(f_sub(f_add(c1, c1), c0), f_sub(f_add(h1, h1), h0)));
-            }
-            tr[R.tr_pos] = g0;
-            tr[R.tr_pos + 1] = g1;
-            tr[R.tr_pos + 2] = g2;
-        }
+        if (lane == 0) final_round(Gs, R, S, h);
+    }
+    for (u64 t = gt; t < (u64)(nrounds - nbig); t += nthreads) {
+        const RoundRef R = rounds[nbig + t];
+        const RoundScalars S = round_scalars(R);
+        const u32 nv = R.kind >= PK_GEN_FIRST ? 3 : 2;
+        u64 h[3] = {0, 0, 0};
+        for (u32 q = 0; q < R.nchunks; q++)
+            for (u32 v = 0; v < nv; v++) h[v] = wred(h[v] + R.part_pos[(u64)q * nv + v]);
+        for (u32 v = 0; v < 3; v++) h[v] = wcanon(h[v]);
+        final_round(Gs, R, S, h);
     }
     // the outputs open each transcript: a CTA per circuit (grid-stride over
     // the circuits), its threads over the outputs; the proof's in-place input
@@ -1074,11 +1103,13 @@ __global__ void __launch_bounds__(256) k_final(Globals *Gs, const SciDev *scis, 
     }
 }
 
-void launch_final(Globals *Gs, const SciDev *scis, const RoundRef *rounds, int nrounds, const u32 *outs,
-                  int nouts, cudaStream_t st)
+void launch_final(Globals *Gs, const RoundRef *rounds, int nrounds, int nbig, const u32 *outs, int nouts,
+                  cudaStream_t st)
 {
-    u64 blocks = ((u64)nrounds * 32 + 255) / 256;
+    const u64 warp_blocks = ((u64)nbig * 32 + 255) / 256, thread_blocks = ((u64)(nrounds - nbig) + 255) / 256;
+    u64 blocks = warp_blocks > thread_blocks ? warp_blocks : thread_blocks;
+    if (blocks < (u64)nouts) blocks = (u64)nouts;
     if (blocks < 64) blocks = 64;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    k_final<<<(unsigned)blocks, 256, 0, st>>>(Gs, scis, rounds, nrounds, outs, nouts);
+    k_final<<<(unsigned)blocks, 256, 0, st>>>(Gs, rounds, nrounds, nbig, outs, nouts);
 }

@@ -318,8 +318,13 @@ void launch_build23(const Globals *Gs, const BuildItem *items, int nitems, cudaS
 // One persistent launch over `tasks` (ctr: two zeroed counters, left zeroed).
 void launch_waves(const Globals *Gs, const LineWaveDev *lw, const ProdWave *pw, const GenWave *gw, const Task *tasks,
                   int ntasks, u32 *ctr, cudaStream_t st);
-void launch_final(Globals *Gs, const SciDev *scis, const RoundRef *rounds, int nrounds, const u32 *outs,
-                  int nouts, cudaStream_t st);
+// Rounds [0, nbig) are reduced a warp each: all rounds when there are at most
+// FINAL_ALL_WARPS (the warps of one full launch), else those with more than
+// FINAL_WARP_MIN chunk partials; the rest a thread each.
+#define FINAL_WARP_MIN 8u
+#define FINAL_ALL_WARPS (152u * 8u * 8u)
+void launch_final(Globals *Gs, const RoundRef *rounds, int nrounds, int nbig, const u32 *outs, int nouts,
+                  cudaStream_t st);
 void prove_kernels_init();
 void waves_init();
 

@@ -647,6 +647,15 @@ bool plan_valid(const Plan &P)
 // chunks of larger waves first.
 void sort_tasks(Plan &P)
 {
+    // the final reduction takes every round a warp each while one launch has
+    // a warp for each; beyond that the rounds with many partials a warp each,
+    // the rest a thread each
+    if (P.rounds.size() <= FINAL_ALL_WARPS) {
+        P.nbig = (u32)P.rounds.size();
+    } else {
+        auto many = [](const RoundRef &R) { return R.nchunks > FINAL_WARP_MIN; };
+        P.nbig = (u32)(std::stable_partition(P.rounds.begin(), P.rounds.end(), many) - P.rounds.begin());
+    }
     auto rank = [&](const Task &t) { return t.type == TK_LINE ? 0 : (t.type == TK_GEN ? 1 : 2); };
     auto entries = [&](const Task &t) {  // the wave's whole size: larger waves first
         return t.type == TK_LINE ? (u64(P.lw[t.wave].nchunks) << P.lw[t.wave].nl)
@@ -912,7 +921,7 @@ void enqueue_plan(Plan &P, cudaStream_t st)
         mark(VC_STAGE_TABWAVES, 1, st);
     }
     mark(VC_STAGE_FINAL, 0, st);
-    launch_final(P.d_G, P.d_scis, P.d_rounds, (int)P.rounds.size(), P.d_outs, (int)P.outs.size(), st);
+    launch_final(P.d_G, P.d_rounds, (int)P.rounds.size(), (int)P.nbig, P.d_outs, (int)P.outs.size(), st);
     mark(VC_STAGE_FINAL, 1, st);
     mark(VC_STAGE_PROOF, 1, st);
 }

@@ -70,6 +70,35 @@ def test_batch_mixed_families_repeated():
             vc.vc_circuit_destroy(h)
 
 
+def test_large_batch_final_reduction_paths():
+    """A batch with more rounds than one final-reduction launch has warps
+    (80 F2 circuits of 2^8..2^12 inputs plus MatMult members, about 12 K
+    rounds): rounds with many chunk partials are summed a warp each, the rest
+    a thread each.  Every member equals its standalone proof; a sample equals
+    the oracle's transcript."""
+    shapes = [("f2", 8 + (j % 5)) for j in range(80)] + [("matmult", 3), ("matmult", 4)]
+    specs = [make_job(f, n, k) for k, (f, n) in enumerate(shapes)]
+    hs = [vc.vc_circuit_create(w, k, ex) for w, k, ex, _ in specs]
+    rounds = sum(vc.vc_circuit_get_info(h)["n_rounds"] for h in hs)
+    assert rounds > 152 * 8 * 8
+    b = vc.vc_batch_create(hs)
+    try:
+        trs = [torch.empty(vc.vc_transcript_len(h), dtype=torch.int64, device="cuda") for h in hs]
+        vc.vc_batch_prove(b, [dev(x) for *_, x in specs], [300 + j for j in range(len(hs))], trs)
+        vc.vc_batch_sync(b)
+        for j, (w, k, ex, x) in enumerate(specs):
+            one = torch.empty_like(trs[j])
+            vc.vc_prove(hs[j], dev(x), 300 + j, one)
+            vc.vc_circuit_sync(hs[j])
+            assert (to_np(trs[j]) == to_np(one)).all(), shapes[j]
+            if j % 20 == 0 or shapes[j][0] == "matmult":
+                assert (to_np(trs[j]) == oracle_prove(w, k, x, 300 + j, explicit=ex)).all(), shapes[j]
+    finally:
+        vc.vc_batch_destroy(b)
+        for h in hs:
+            vc.vc_circuit_destroy(h)
+
+
 def test_batch_host_pointers():
     """Host inputs and host transcripts: synchronous form."""
     specs = [make_job(f, n, k) for k, (f, n) in enumerate(JOBS[:4])]
