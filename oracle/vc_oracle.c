@@ -47,8 +47,8 @@
  *     round challenges in round order, then tau;
  *   - transcript = [S_0 outputs] ++ per layer [3 values per round] ++ [q(0..s_{i+1})].
  *
- * Parity unpinned: the splitmix64 stream (a convention; the paper fixes no
- * generator) is pinned only by restating its published definition.
+ * The splitmix64 stream (a convention; the paper fixes no generator) is
+ * pinned to the generator's published known-answer values.
  */
 #include <stdint.h>
 #include <stdlib.h>

@@ -112,6 +112,18 @@ def test_splitmix64_restatement_and_range():
     assert [int(v) for v in ch[:8]] == [v >> 3 for v in ref(9, 8)]
 
 
+def test_splitmix64_published_values():
+    """The oracle's stream against splitmix64's published known-answer values
+    (tests/golden/splitmix64_kat.txt), not against a restatement."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "splitmix64_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 2
+    for row in rows:
+        seed, want = int(row[0]), [int(v) for v in row[1:]]
+        assert [int(v) for v in oracle.splitmix64(seed, len(want))] == want
+
+
 # --- circuit expansions -------------------------------------------------------------
 
 def expand_kind(kind, si, sn):
