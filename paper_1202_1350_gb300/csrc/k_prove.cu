@@ -32,6 +32,7 @@ __global__ void k_params_batch(Globals *Gs, const CallParams *cp, int n)
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         Gs[j].seed = cp[j].seed;
         Gs[j].tr = cp[j].tr;
+        Gs[j].in = cp[j].in_eval;
     }
 }
 

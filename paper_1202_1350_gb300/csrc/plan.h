@@ -267,8 +267,9 @@ struct BuildItem {
 struct CallParams {
     u64 seed;
     u64 *tr;
-    const u64 *in;  // the member's inputs (device memory) for the gather launch
-    u64 pad;
+    const u64 *in;       // the member's inputs (device memory) for the gather launch
+    const u64 *in_eval;  // the same when the member's first evaluation launch reads them in
+                         // place (written to Globals::in), else NULL
 };
 
 // A piece of one batch member's input copy: count entries from the member's

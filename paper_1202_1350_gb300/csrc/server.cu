@@ -214,6 +214,8 @@ vc_status launch(vc_server *s, Slot &sl)
             return VC_ECUDA;
         sl.h_cp[k].seed = j->seed;
         sl.h_cp[k].tr = j->tr_dev ? j->transcript : c->d_tr;
+        sl.h_cp[k].in = nullptr;
+        sl.h_cp[k].in_eval = nullptr;  // the server copies every job's inputs into its input layer
     }
     if (cudaMemcpyAsync(d_cp, sl.h_cp, n * sizeof(CallParams), cudaMemcpyHostToDevice, sl.st) != cudaSuccess)
         return VC_ECUDA;

@@ -1819,10 +1819,12 @@ extern "C" vc_status vc_batch_create(vc_circuit *const *circuits, int n, vc_batc
     b->members.assign(circuits, circuits + n);
     DevGuard guard(b->device);
     plan_merge(b->P, b->members);
-    // the members' input copies as chunks of one gather launch
+    // the input copies of members whose first evaluation launch cannot read
+    // device inputs in place, as chunks of one gather launch
     std::vector<GatherChunk> gather;
     for (int j = 0; j < n; j++) {
         vc_circuit *c = b->members[j];
+        if (c->eval_reads_inputs) continue;
         const u64 nin = u64(1) << c->s[c->d];
         for (u64 s0 = 0; s0 < nin; s0 += GATHER_CHUNK)
             gather.push_back({c->V[c->d] + s0, s0, (u32)j, (u32)std::min<u64>(GATHER_CHUNK, nin - s0)});
@@ -1909,11 +1911,13 @@ extern "C" vc_status vc_batch_prove(vc_batch *b, const uint64_t *const *inputs, 
         b->h_cp[j].seed = seeds[j];
         b->h_cp[j].tr = kt[j] ? transcripts[j] : c->d_tr;
         b->h_cp[j].in = inputs[j];
+        b->h_cp[j].in_eval = (all_in_dev && c->eval_reads_inputs) ? inputs[j] : nullptr;
     }
     cudaError_t e = cudaMemcpyAsync(b->d_cp, b->h_cp, n * sizeof(CallParams), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(b->P.ev_params, st);
     if (e != cudaSuccess) return VC_ECUDA;
-    // device inputs: every member's copy in one launch
+    // device inputs: read in place by the first evaluation launch, or copied
+    // by one gather launch (members whose first evaluation step cannot)
     if (all_in_dev) launch_gather_inputs(b->d_cp, b->d_gather, b->ngather, st);
     launch_params_batch(b->P.d_G, b->d_cp, n, st);
     e = plan_launch(b->P, st);
