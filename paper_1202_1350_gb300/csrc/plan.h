@@ -345,9 +345,8 @@ struct VerifyDev {
     const VerifyPtrs *vp;  // device
     u64 *mle_part;      // partial sums of the input MLE
     u32 mle_blocks;
-    u64 *result;        // [0] input MLE, [1] output MLE, [2] accept flag, [3] bad-value flag
+    u64 *result;        // [2] accept bit, [3] a check failed (k_vcheck writes both); others unused
     u64 *wire;          // generic add~/mult~ per layer (EXPLICIT layers)
-    u64 *claims;        // starting claim of every layer (d entries)
     u32 mle_out_blocks; // blocks of the output-MLE partials (after the input's; 0: formed by k_vcheck)
     const u32 *round_layer;  // per global round: layer << 8 | round within layer
     u32 nrounds;

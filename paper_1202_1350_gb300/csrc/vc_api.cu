@@ -502,7 +502,6 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     c->Vd.mle_out_blocks = S(0) <= VC_OUT_INLINE ? 0u : (u32)mbo;  // few outputs: formed in the check launch
     c->Vd.mle_part = A.take<u64>(mb + mbo);
     c->Vd.wire = A.take<u64>(2 * d + 2);
-    c->Vd.claims = A.take<u64>(d + 1);
     c->round_layer.clear();
     for (u32 i = 0; i < d; i++)
         for (u32 j = 0; j < c->s[i] + 2 * c->s[i + 1]; j++) c->round_layer.push_back((i << 8) | j);
