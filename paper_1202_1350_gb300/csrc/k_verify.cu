@@ -289,14 +289,14 @@ __device__ void wiring_warp(u32 kind, u32 si, u32 sn, const u64 *p, const u64 *w
 
 // All checks of the verifier in one cluster of VC_CL CTAs; the accept bit is
 // combined through the cluster's distributed shared memory (no grid-wide
-// atomics).  Warp w of the cluster checks layers w, w + 32 VC_CL, ...: the
+// atomics).  Warp w of the cluster checks layers w, w + 32 VC_CL, ... (and
+// warp d the last claim, q(tau) of layer d-1 = the input's MLE at z_d): the
 // layer's starting claim (for layer 0 the claimed outputs' MLE at z_0: formed
 // by the warp itself when there are at most VC_OUT_INLINE outputs, else
 // summed from k_vmle's partials; for layer i > 0, q_{i-1}(tau_{i-1})), round
 // 0 (g_0(0) + g_0(1) = starting claim), the end of the layer
 // (g_{n-1}(r_{n-1}) = eq(z_i, r_P)[add~ (v1 + v2) + mult~ v1 v2], or the
-// starting claim itself when the layer has no rounds) and, for the last
-// layer, q(tau) = the input's MLE at z_d.  Every thread checks rounds j >= 1
+// starting claim itself when the layer has no rounds).  Every thread checks rounds j >= 1
 // (g_j(0) + g_j(1) = g_{j-1}(r_{j-1})) of a grid-stride share of the global
 // rounds, and its share of the transcript entries for canonical form.  The
 // accept bit is the conjunction of exactly the sequential verifier's checks.
@@ -309,7 +309,17 @@ __global__ void __cluster_dims__(VC_CL, 1, 1) __launch_bounds__(VC_NT)
     const u32 lane = threadIdx.x & 31;
     const u32 g = blockIdx.x * VC_NT + threadIdx.x, nthreads = VC_CL * VC_NT;
     u32 fail = 0;
-    for (u32 i = g >> 5; i < G.d; i += nthreads >> 5) {
+    for (u32 i = g >> 5; i <= G.d; i += nthreads >> 5) {
+        if (i == G.d) {
+            // the last claim against the input's MLE at z_d, beside layer d-1's checks
+            if (G.d == 0) continue;
+            const LayerDev &L = G.layers[G.d - 1];
+            const u64 fin = lagrange_warp(tr + L.tr_q, L.sn, G.chal[L.chal_off + L.s + 2 * L.sn], G.invfact);
+            u64 in_mle;
+            warp_record_sums<1>(V.mle_part, V.mle_blocks, lane, &in_mle);
+            if (lane == 0 && fin != in_mle) fail = 1;
+            continue;
+        }
         const LayerDev &L = G.layers[i];
         const u32 si = L.s, sn = L.sn, n = si + 2 * sn;
         const u64 *r = G.chal + L.chal_off;
@@ -352,12 +362,6 @@ __global__ void __cluster_dims__(VC_CL, 1, 1) __launch_bounds__(VC_NT)
             const u64 v1 = q[0], v2 = sn ? q[1] : q[0];
             const u64 expect = f_mul(G.scal[SCAL_EQZRP(i)], f_add(f_mul(add, f_add(v1, v2)), f_mul(mult, f_mul(v1, v2))));
             if (expect != claim) fail = 1;
-        }
-        if (i + 1 == G.d) {
-            const u64 fin = lagrange_warp(q, sn, G.chal[L.chal_off + n], G.invfact);
-            u64 in_mle;
-            warp_record_sums<1>(V.mle_part, V.mle_blocks, lane, &in_mle);
-            if (lane == 0 && fin != in_mle) fail = 1;
         }
     }
     for (u32 rho = g; rho < V.nrounds; rho += nthreads) {
