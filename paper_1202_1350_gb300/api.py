@@ -74,6 +74,36 @@ class Circuit:
         x = _as_tensor(inputs, f"cuda:{self.device}")
         return _vc.vc_verify(self.handle, x, seed, transcript, device=self.device)
 
+    def verify_input(self, inputs, seed: int, stream=None):
+        """The verifier's input pass for `seed` (its coins and the inputs'
+        multilinear extension at the final point), queued on `stream` (a torch
+        stream; default: the current one) after the work already queued on the
+        current stream; it may run beside a proof on this circuit.  The inputs
+        (or their device copy) are held until verify_transcript, which waits
+        for the pass."""
+        import torch
+        x = _as_tensor(inputs, f"cuda:{self.device}")
+        cur = torch.cuda.current_stream(self.device)
+        st = cur if stream is None else stream
+        if st != cur:
+            st.wait_stream(cur)
+        _vc.vc_verify_input(self.handle, x, seed, stream=st, device=self.device)
+        ev = torch.cuda.Event()
+        ev.record(st)
+        self._vin = (x, ev)
+
+    def verify_transcript(self, seed: int, transcript, stream=None) -> bool:
+        """The rest of the verification, after verify_input for the same seed,
+        queued on `stream` (default: the current one) behind the input pass."""
+        import torch
+        st = torch.cuda.current_stream(self.device) if stream is None else stream
+        vin = getattr(self, "_vin", None)
+        if vin is not None:
+            st.wait_event(vin[1])
+        ok = _vc.vc_verify_transcript(self.handle, seed, transcript, stream=st, device=self.device)
+        self._vin = None
+        return ok
+
     def close(self):
         if getattr(self, "handle", None):
             _vc.vc_circuit_destroy(self.handle)
