@@ -511,10 +511,12 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
-    if not args.no_batch:
-        line["batched"] = run_batch(local)
+    # serving first: the batch leg runs the autotuner, whose per-class tile
+    # shapes every later circuit of those classes in this process would use
     if not args.no_serve:
         line["serving"] = run_serving(local)
+    if not args.no_batch:
+        line["batched"] = run_batch(local)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
