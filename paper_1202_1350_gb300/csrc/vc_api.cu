@@ -79,11 +79,6 @@ static EqTab take_eq(Arena &A, const u64 *pt, u32 n)
     return t;
 }
 
-// Evaluation plan: runs of block-local layers (every kind but MATMULT and
-// EXPLICIT) go to one k_eval_seg launch each; a CTA takes 2^c entries of the
-// run's input layer (about 256 CTAs for wide layers) and keeps going while its
-// block stays >= 32 entries (or while one CTA covers the whole layer) and
-// <= 4096 entries.  Layers outside any run are evaluated alone (k_eval_layer).
 // Whether the first evaluation launch of a single-circuit plan is a run of
 // block-local layers over the input layer (it can then read the inputs in place).
 static bool first_eval_is_input_run(const Plan &P, u32 d)
@@ -94,6 +89,11 @@ static bool first_eval_is_input_run(const Plan &P, u32 d)
     return true;
 }
 
+// Evaluation plan: runs of block-local layers (every kind but MATMULT and
+// EXPLICIT) go to one k_eval_seg launch each; a CTA takes 2^c entries of the
+// run's input layer (about 256 CTAs for wide layers) and keeps going while its
+// block stays >= 32 entries (or while one CTA covers the whole layer) and
+// <= 4096 entries.  Layers outside any run are evaluated alone (k_eval_layer).
 static void plan_eval(vc_circuit *c)
 {
     Plan &P = c->P;
