@@ -181,12 +181,12 @@ def two_pass(h, x, seed, tr, stream=None):
     return vc.vc_verify_transcript(h, seed, tr, stream=stream)
 
 
-@pytest.mark.parametrize("family,logn", CASES + [("matmult", 5), ("pm", 0), ("mm1", 0)])
+@pytest.mark.parametrize("family,logn", CASES + [("matmult", 4), ("matmult", 5), ("pm", 0), ("mm1", 0)])
 def test_two_pass_agrees_with_one_pass(family, logn):
     """Honest transcripts accepted, changed ones rejected, exactly as vc_verify
     decides, for structured and explicitly wired circuits (MatMult n = 32:
-    2^10 outputs, whose MLE comes from partial sums; fewer outputs: formed in
-    the check launch)."""
+    2^10 outputs, whose MLE comes from partial sums; up to 256 outputs, as for
+    n = 16: formed in the check launch)."""
     ex = None
     if family == "pm":
         widths, kinds, ex = circuits.pattern_match(5, 2)
@@ -284,4 +284,33 @@ def test_two_pass_misuse_and_bad_inputs():
         einval(vc.vc_circuit_sync, h)
         vc.vc_circuit_sync(h)
     finally:
+        vc.vc_circuit_destroy(h)
+
+
+def test_two_pass_at_the_bench_size():
+    """F2 n = 2^20 (the bench workload): the input pass beside the proof, the
+    transcript pass accepts; changed round values, line values and the output
+    are rejected."""
+    widths, kinds = circuits.f2(20)
+    h = vc.vc_circuit_create(widths, kinds)
+    side = torch.cuda.Stream()
+    main = torch.cuda.current_stream()
+    try:
+        x = dev(I.f2_inputs(20, 1 << 16, 77))
+        tr = torch.empty(vc.vc_transcript_len(h), dtype=torch.int64, device="cuda")
+        start = torch.cuda.Event()
+        start.record(main)
+        vc.vc_prove(h, x, 123, tr)
+        side.wait_event(start)
+        vc.vc_verify_input(h, x, 123, stream=side)
+        main.wait_stream(side)
+        assert vc.vc_verify_transcript(h, 123, tr)
+        n = len(tr)
+        for pos in (0, 1, 2, n // 2, n - 1):
+            bad = tr.clone()
+            bad[pos] = (int(bad[pos]) + 1) % P
+            vc.vc_verify_input(h, x, 123)
+            assert not vc.vc_verify_transcript(h, 123, bad), pos
+    finally:
+        torch.cuda.synchronize()
         vc.vc_circuit_destroy(h)
