@@ -334,6 +334,10 @@ typedef struct {
     uint64_t mem_cap_bytes;  /* device bytes for resident circuits (0 = 150 GiB) */
     uint32_t max_batch;      /* jobs per launch set (0 = 16)                     */
     uint32_t max_inflight;   /* launch sets on the device at once (0 = 4, max 8) */
+    uint32_t pr_split_log;   /* the server's circuits: product-weighted instances
+                                below 2^pr_split_log entries use half-size chunks
+                                (vc_tile_config; 0 = each circuit's own shapes) */
+    uint32_t pad;
 } vc_server_config;
 
 typedef struct {

@@ -153,9 +153,10 @@ class Server:
     written into the caller's transcript buffers (continuous batching under a
     device-memory cap)."""
 
-    def __init__(self, device: int = 0, mem_cap_bytes: int = 0, max_batch: int = 0, max_inflight: int = 0):
+    def __init__(self, device: int = 0, mem_cap_bytes: int = 0, max_batch: int = 0, max_inflight: int = 0,
+                 pr_split_log: int = 0):
         self.device = device
-        self.handle = _vc.vc_server_create(device, mem_cap_bytes, max_batch, max_inflight)
+        self.handle = _vc.vc_server_create(device, mem_cap_bytes, max_batch, max_inflight, pr_split_log)
         self._keep = {}  # job id -> buffers that must outlive the job
 
     def submit(self, log_width, wiring, inputs, seed: int, transcript) -> int:

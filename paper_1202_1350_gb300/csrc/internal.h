@@ -217,6 +217,9 @@ void init_device_once(int device);
 // takes the device memory and uploads everything.
 vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **out,
                           const PlanConfig *cfg = nullptr, u32 flags = 0);
+// The tile shapes a circuit of this shape gets without explicit ones (the
+// autotuned shapes of its size class, else the defaults).
+PlanConfig shape_config(const vc_circuit_desc *desc);
 vc_status circuit_allocate(vc_circuit *c);
 void circuit_free(vc_circuit *c);
 

@@ -85,10 +85,14 @@ struct Slot {
 
 }  // namespace
 
+struct vc_server;
+static vc_status server_prepare(const vc_server *s, const vc_circuit_desc *desc, vc_circuit **out);
+
 struct vc_server {
     int device = 0;
     u64 cap = 0;
     u32 max_batch = 16, max_inflight = 4;
+    u32 pr_split = 0;  // 0: each circuit's own tile shapes
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Job *> pending;
@@ -138,7 +142,7 @@ Acq acquire(vc_server *s, Job *j, vc_circuit **out)
     d.log_width = j->key.widths.data();
     d.wiring = j->key.kinds.data();
     vc_circuit *c = nullptr;
-    if (circuit_prepare(&d, s->device, &c) != VC_OK) return ACQ_FAIL;
+    if (server_prepare(s, &d, &c) != VC_OK) return ACQ_FAIL;
     if (circuit_allocate(c) != VC_OK) {
         circuit_free(c);
         return ACQ_FAIL;
@@ -326,10 +330,21 @@ void worker_main(vc_server *s)
 
 }  // namespace
 
+// A circuit for the server: its shape's tile shapes, with the server's split
+// threshold if one was configured.
+static vc_status server_prepare(const vc_server *s, const vc_circuit_desc *desc, vc_circuit **out)
+{
+    if (!s->pr_split) return circuit_prepare(desc, s->device, out);
+    PlanConfig f = shape_config(desc);
+    f.pr_split = s->pr_split;
+    return circuit_prepare(desc, s->device, out, &f);
+}
+
 extern "C" vc_status vc_server_create(int device, const vc_server_config *cfg, vc_server **out)
 {
     if (!out) return VC_EINVAL;
     *out = nullptr;
+    if (cfg && cfg->pr_split_log > 40) return VC_EINVAL;
     vc_server *s = new (std::nothrow) vc_server();
     if (!s) return VC_ENOMEM;
     s->device = device;
@@ -337,6 +352,7 @@ extern "C" vc_status vc_server_create(int device, const vc_server_config *cfg, v
     s->max_batch = (cfg && cfg->max_batch) ? cfg->max_batch : 16;
     s->max_inflight = (cfg && cfg->max_inflight) ? cfg->max_inflight : 4;
     if (s->max_inflight > 8) s->max_inflight = 8;
+    s->pr_split = cfg ? cfg->pr_split_log : 0;
     DevGuard guard(device);
     init_device_once(device);
     s->slots.resize(s->max_inflight);
@@ -404,7 +420,7 @@ extern "C" vc_status vc_server_submit(vc_server *s, const vc_circuit_desc *desc,
     auto it = s->shapes.find(key);
     if (it == s->shapes.end()) {
         vc_circuit *c = nullptr;
-        const vc_status st = circuit_prepare(desc, s->device, &c);
+        const vc_status st = server_prepare(s, desc, &c);
         if (st != VC_OK) return st;
         Shape sh;
         sh.bytes = c->arena_bytes;

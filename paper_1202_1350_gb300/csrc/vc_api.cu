@@ -1042,6 +1042,15 @@ static bool config_ok(const PlanConfig &f)
            (f.pr_split <= 40 || f.pr_split == VC_SPLIT_WIDEST);
 }
 
+PlanConfig shape_config(const vc_circuit_desc *desc)
+{
+    PlanConfig f;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tuned.find(size_class(desc));
+    if (it != g_tuned.end()) f = it->second;
+    return f;
+}
+
 vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **out, const PlanConfig *cfg,
                           u32 flags)
 {
@@ -1052,13 +1061,7 @@ vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **
     if (cfg && !config_ok(*cfg)) return VC_EINVAL;
     vc_circuit *c = new (std::nothrow) vc_circuit();
     if (!c) return VC_ENOMEM;
-    if (cfg) {
-        c->cfg = *cfg;
-    } else {
-        std::lock_guard<std::mutex> g(g_tune_mu);
-        auto it = g_tuned.find(size_class(desc));
-        if (it != g_tuned.end()) c->cfg = it->second;
-    }
+    c->cfg = cfg ? *cfg : shape_config(desc);
     c->device = device;
     c->flags = flags;
     c->d = desc->n_layers;

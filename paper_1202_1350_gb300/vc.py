@@ -63,7 +63,7 @@ class BatchInfo(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("mem_cap_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_uint32),
-                ("max_inflight", ctypes.c_uint32)]
+                ("max_inflight", ctypes.c_uint32), ("pr_split_log", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 class JobInfo(ctypes.Structure):
@@ -508,8 +508,12 @@ def _desc_struct(log_width, wiring):
     return _Desc(d, ctypes.cast(lw_a, _u32p), ctypes.cast(k_a, _u32p), None, None, None), (lw_a, k_a)
 
 
-def vc_server_create(device: int = 0, mem_cap_bytes: int = 0, max_batch: int = 0, max_inflight: int = 0):
-    cfg = ServerConfig(mem_cap_bytes, max_batch, max_inflight)
+def vc_server_create(device: int = 0, mem_cap_bytes: int = 0, max_batch: int = 0, max_inflight: int = 0,
+                     pr_split_log: int = 0):
+    """pr_split_log: the server's circuits split product-weighted instances
+    below 2^pr_split_log entries into half-size chunks (0: each circuit's own
+    tile shapes)."""
+    cfg = ServerConfig(mem_cap_bytes, max_batch, max_inflight, pr_split_log, 0)
     h = ctypes.c_void_p()
     _check(lib().vc_server_create(device, ctypes.byref(cfg), ctypes.byref(h)), "vc_server_create")
     return h.value

@@ -38,8 +38,12 @@ MIX = [("f2", 5), ("f2", 10), ("matmult", 2), ("f2", 0), ("f0", 2), ("f2", 12), 
        ("f2", 10), ("f2", 5), ("matmult", 3), ("f2", 16)]
 
 
-def test_server_mix_equals_alone():
-    srv = Server(max_batch=4, max_inflight=3)
+@pytest.mark.parametrize("split", [0, 13])
+def test_server_mix_equals_alone(split):
+    """Every job of a mix equals the oracle (small) or a standalone proof;
+    split 13: the server's circuits use half-size chunks for product-weighted
+    instances below 2^13 entries."""
+    srv = Server(max_batch=4, max_inflight=3, pr_split_log=split)
     try:
         jobs = []
         for k, (fam, logn) in enumerate(MIX * 2):
@@ -119,6 +123,9 @@ def test_server_rejects_oversized_and_explicit():
         assert e.value.status == vc.VC_EINVAL
     finally:
         srv.close()
+    with pytest.raises(vc.VcError) as e:  # a split threshold beyond any layer width
+        Server(pr_split_log=41)
+    assert e.value.status == vc.VC_EINVAL
 
 
 def test_server_noncanonical_job_reported_alone():
