@@ -127,6 +127,10 @@ vc_status vc_evaluate(vc_circuit *c, const uint64_t *inputs, uint64_t *outputs, 
 /* Prover (Sec. 3.1, Sec. 4.1.1): evaluate the circuit on `inputs` (S_d
  * canonical elements) and write the whole transcript for the verifier coins
  * derived from `seed`.  transcript: vc_transcript_len() u64.
+ * Inputs the device can address (device memory, or page-locked host memory
+ * whose device address is its host address) are read in place by the first
+ * evaluation launch, which writes them into the input layer; others are
+ * copied first.  Either way they are read on `stream`, in stream order.
  * If `inputs` and `transcript` are both device memory the call is
  * asynchronous with respect to the host: a non-canonical input is then
  * latched in the circuit and reported by the next vc_circuit_sync.
