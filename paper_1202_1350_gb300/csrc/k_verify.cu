@@ -289,16 +289,18 @@ __device__ void wiring_warp(u32 kind, u32 si, u32 sn, const u64 *p, const u64 *w
 
 // All checks of the verifier in one cluster of VC_CL CTAs; the accept bit is
 // combined through the cluster's distributed shared memory (no grid-wide
-// atomics).  Warp w of the cluster checks layers w, w + 32 VC_CL, ... (and
-// warp d the last claim, q(tau) of layer d-1 = the input's MLE at z_d): the
+// atomics).  The warps of the cluster take three kinds of item: a layer's
+// starting claim with its round 0, a layer's end, and the last claim (q(tau)
+// of layer d-1 = the input's MLE at z_d), all independent.  The checks: the
 // layer's starting claim (for layer 0 the claimed outputs' MLE at z_0: formed
 // by the warp itself when there are at most VC_OUT_INLINE outputs, else
 // summed from k_vmle's partials; for layer i > 0, q_{i-1}(tau_{i-1})), round
 // 0 (g_0(0) + g_0(1) = starting claim), the end of the layer
 // (g_{n-1}(r_{n-1}) = eq(z_i, r_P)[add~ (v1 + v2) + mult~ v1 v2], or the
-// starting claim itself when the layer has no rounds).  Every thread checks rounds j >= 1
-// (g_j(0) + g_j(1) = g_{j-1}(r_{j-1})) of a grid-stride share of the global
-// rounds, and its share of the transcript entries for canonical form.  The
+// starting claim itself when the layer has no rounds).  Every thread checks
+// rounds j >= 1 (g_j(0) + g_j(1) = g_{j-1}(r_{j-1})) of a grid-stride share of
+// the global rounds, and its share of the transcript entries for canonical
+// form.  The
 // accept bit is the conjunction of exactly the sequential verifier's checks.
 // tr_arg: the transcript and accept pointer given directly (NULL: from V.vp).
 __global__ void __cluster_dims__(VC_CL, 1, 1) __launch_bounds__(VC_NT)
@@ -309,9 +311,11 @@ __global__ void __cluster_dims__(VC_CL, 1, 1) __launch_bounds__(VC_NT)
     const u32 lane = threadIdx.x & 31;
     const u32 g = blockIdx.x * VC_NT + threadIdx.x, nthreads = VC_CL * VC_NT;
     u32 fail = 0;
-    for (u32 i = g >> 5; i <= G.d; i += nthreads >> 5) {
-        if (i == G.d) {
-            // the last claim against the input's MLE at z_d, beside layer d-1's checks
+    // warp items: [0, d) a layer's starting claim and its round 0 (with the
+    // end of the layer when it has no rounds, whose claim is the start);
+    // [d, 2d) the end of layer i - d; 2d the last claim against the input's MLE
+    for (u32 item = g >> 5; item <= 2 * G.d; item += nthreads >> 5) {
+        if (item == 2 * G.d) {
             if (G.d == 0) continue;
             const LayerDev &L = G.layers[G.d - 1];
             const u64 fin = lagrange_warp(tr + L.tr_q, L.sn, G.chal[L.chal_off + L.s + 2 * L.sn], G.invfact);
@@ -320,28 +324,43 @@ __global__ void __cluster_dims__(VC_CL, 1, 1) __launch_bounds__(VC_NT)
             if (lane == 0 && fin != in_mle) fail = 1;
             continue;
         }
+        const bool end_item = item >= G.d;
+        const u32 i = end_item ? item - G.d : item;
         const LayerDev &L = G.layers[i];
         const u32 si = L.s, sn = L.sn, n = si + 2 * sn;
+        if (end_item && n == 0) continue;  // checked with the start
         const u64 *r = G.chal + L.chal_off;
-        u64 start;
-        if (i == 0) {
-            if (V.mle_out_blocks == 0) {
-                // every output's eq weight a direct product over the s_0
-                // coordinates of z_0 (the first s_0 challenges)
-                u64 sum = 0;
-                for (u64 b = lane; b < G.S0; b += 32) {
-                    const u64 v = tr[b];
-                    u64 w = 1;
-                    for (u32 k = 0; k < si; k++) w = f_mul(w, ((b >> k) & 1) ? G.chal[k] : f_sub(1, G.chal[k]));
-                    sum = f_add(sum, f_mul(w, v >= FP_P ? 0 : v));  // a non-canonical entry fails the scan
+        const u64 *m = tr + L.tr_msg;
+        u64 claim = 0;
+        if (!end_item) {
+            u64 start;
+            if (i == 0) {
+                if (V.mle_out_blocks == 0) {
+                    // every output's eq weight a direct product over the s_0
+                    // coordinates of z_0 (the first s_0 challenges)
+                    u64 sum = 0;
+                    for (u64 b = lane; b < G.S0; b += 32) {
+                        const u64 v = tr[b];
+                        u64 w = 1;
+                        for (u32 k = 0; k < si; k++) w = f_mul(w, ((b >> k) & 1) ? G.chal[k] : f_sub(1, G.chal[k]));
+                        sum = f_add(sum, f_mul(w, v >= FP_P ? 0 : v));  // a non-canonical entry fails the scan
+                    }
+                    start = warp_sum(sum);
+                } else {
+                    warp_record_sums<1>(V.mle_part + V.mle_blocks, V.mle_out_blocks, lane, &start);
                 }
-                start = warp_sum(sum);
             } else {
-                warp_record_sums<1>(V.mle_part + V.mle_blocks, V.mle_out_blocks, lane, &start);
+                const LayerDev &Lp = G.layers[i - 1];
+                start = lagrange_warp(tr + Lp.tr_q, Lp.sn, G.chal[Lp.chal_off + Lp.s + 2 * Lp.sn], G.invfact);
             }
-        } else {
-            const LayerDev &Lp = G.layers[i - 1];
-            start = lagrange_warp(tr + Lp.tr_q, Lp.sn, G.chal[Lp.chal_off + Lp.s + 2 * Lp.sn], G.invfact);
+            if (n > 0) {
+                if (lane == 0 && f_add(m[0], m[1]) != start) fail = 1;
+                continue;
+            }
+            claim = start;
+        } else if (lane == 0) {
+            const u64 *ml = m + 3ull * (n - 1);
+            claim = interp3(ml[0], ml[1], ml[2], r[n - 1]);
         }
         u64 add = 0, mult = 0;
         if (L.kind == W_EXPLICIT) {
@@ -350,15 +369,8 @@ __global__ void __cluster_dims__(VC_CL, 1, 1) __launch_bounds__(VC_NT)
         } else {
             wiring_warp(L.kind, si, sn, r, r + si, r + si + sn, add, mult);
         }
-        const u64 *q = tr + L.tr_q;
         if (lane == 0) {
-            const u64 *m = tr + L.tr_msg;
-            if (n > 0 && f_add(m[0], m[1]) != start) fail = 1;
-            u64 claim = start;
-            if (n > 0) {
-                const u64 *ml = m + 3ull * (n - 1);
-                claim = interp3(ml[0], ml[1], ml[2], r[n - 1]);
-            }
+            const u64 *q = tr + L.tr_q;
             const u64 v1 = q[0], v2 = sn ? q[1] : q[0];
             const u64 expect = f_mul(G.scal[SCAL_EQZRP(i)], f_add(f_mul(add, f_add(v1, v2)), f_mul(mult, f_mul(v1, v2))));
             if (expect != claim) fail = 1;
