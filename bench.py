@@ -293,6 +293,24 @@ def cpu_baseline(logn: int = 20):
                       f"({wall:.1f} s wall, {sum(t for t, _ in res):.1f} s CPU)"}
 
 
+REFERENCE_BUDGET_S = 100.0
+REFERENCE_MIN_LOGN = 10
+
+
+def reference_logn(steps: int, warmup: int, probe_s: float, probe_logn: int = 14,
+                   budget_s: float = REFERENCE_BUDGET_S, max_logn: int = 20) -> int:
+    """Size of the F2 instance the reference arm proves per step: the largest
+    log2 n <= max_logn whose estimated (steps + warmup) proofs fit in budget_s,
+    never below REFERENCE_MIN_LOGN.  The oracle's prove + verify time grows
+    linearly in n (folding prover, one MLE pass), so a step at log2 n is
+    estimated from one probe proof at probe_logn, with a 25 % margin."""
+    n_runs = max(1, steps + warmup)
+    logn = max_logn
+    while logn > REFERENCE_MIN_LOGN and n_runs * 1.25 * probe_s * 2.0 ** (logn - probe_logn) > budget_s:
+        logn -= 1
+    return logn
+
+
 def run_reference(args):
     rank, local, world = env_rank()
     if rank != 0:
@@ -300,11 +318,12 @@ def run_reference(args):
     import oracle
     from paper_1202_1350_gb300 import inputs as I
     oracle.build()
-    # size each step so the whole run stays within about two minutes
-    budget = 120.0 / max(1, args.steps + args.warmup)
-    logn = 20
-    while logn > 10 and 5.5 * (1 << (logn - 20)) > budget:
-        logn -= 1
+    # size each step so the whole run stays within about REFERENCE_BUDGET_S
+    probe = oracle.Circuit(*oracle.f2_layers(14))
+    xp = I.f2_inputs(14, 1 << 16, 6999)
+    t0 = time.perf_counter()
+    probe.verify(xp, 1, probe.prove(xp, 1))
+    logn = reference_logn(args.steps, args.warmup, time.perf_counter() - t0)
     c = oracle.Circuit(*oracle.f2_layers(logn))
     gates = 2 * (1 << logn) - 1
     times = []
