@@ -375,10 +375,13 @@ vc_status vc_server_submit(vc_server *s, const vc_circuit_desc *desc, const uint
                            uint64_t seed, uint64_t *transcript, uint64_t *job_id);
 
 /* Job state without blocking.  Once a call reports done = 1 the job is
- * forgotten (its id becomes invalid). */
+ * forgotten (its id becomes invalid).  One consumer per job: while a
+ * vc_server_wait on the job is blocked, poll and wait on it from other
+ * threads return VC_EINVAL. */
 vc_status vc_server_poll(vc_server *s, uint64_t job_id, vc_job_info *info);
 
-/* Block until the job is done, report it and forget it. */
+/* Block until the job is done, report it and forget it.  VC_EINVAL for an
+ * unknown id or one another thread is already waiting on. */
 vc_status vc_server_wait(vc_server *s, uint64_t job_id, vc_job_info *info);
 
 vc_status vc_server_get_stats(vc_server *s, vc_server_stats *stats);
@@ -423,13 +426,20 @@ vc_status vc_f2sp_verify_end(vc_f2sp *s, const uint64_t *proof, uint64_t *f2, in
 vc_status vc_field_mul(const uint64_t *a, const uint64_t *b, uint64_t *out, uint64_t n,
                        void *stream);
 
-/* Field-multiply issue-rate microbenchmark: runs `iters` dependent products on
- * `chains` independent chains per thread over a grid that fills the device,
- * and returns the measured products per second (CUDA events) in *rate.
- * variant 0: canonical 32-bit-limb Mersenne product + add; 1: canonical
- * 64x64->128 product then fold + add; 2: the product-weighted sum-check pair
- * step (two 128-bit multiply-adds and one lazily reduced fold, counted as three
- * products), the arithmetic mix of the dominant kernel. */
+/* Integer-arithmetic rate microbenchmarks (the denominators of the prover's
+ * roofline; the paper has no counterpart).  Each runs `iters` steps of
+ * independent dependency chains per thread over a grid of exactly one wave
+ * (every SM holding as many 256-thread CTAs as fit), times the launch with
+ * CUDA events after a warm-up launch, and returns units per second in *rate.
+ * variant 0: canonical 32-bit-limb Mersenne product + add (8 chains; units:
+ * field products); 1: canonical 64x64->128 product, fold, add (8 chains;
+ * field products); 2: the product-weighted sum-check pair step of the
+ * dominant kernel (two exact 128-bit multiply-adds and one lazily reduced
+ * fold, counted as three field products), the best of 2, 4 and 8 pairs per
+ * thread at several register budgets; 3: 32-bit integer multiply-adds (8
+ * chains; units: multiply-adds); 4: exact 64x64->128-bit multiply-accumulates
+ * (8 accumulators; units: multiply-accumulates).  Synchronous; VC_EINVAL for
+ * another variant or iters = 0, VC_ECUDA on a CUDA error. */
 vc_status vc_field_mul_rate(int device, int variant, uint64_t iters, double *rate);
 
 /* Circuit evaluation that allocates nothing: no cudaMalloc, no cudaFree, no
@@ -448,7 +458,11 @@ vc_status vc_field_mul_rate(int device, int variant, uint64_t iters, double *rat
  * which this function has run keeps that array until the process exits.
  *
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All calls
+ * device current); make that first call before any stream capture.  The
+ * address is kept for the life of the process: after a cudaDeviceReset of
+ * that device it is stale, so do not call this function after one.  A CUDA
+ * error already pending when it is called (left by other code) is not
+ * cleared: the call returns VC_ECUDA without queuing work.  All calls
  * share the one array and it keeps the last call's contents, so calls that
  * overlap on the GPU (other streams, other host threads) race: serialise them.
  * Synchronous: returns after `outputs` is written; VC_EINVAL if an input is

@@ -297,7 +297,7 @@ void sp_init()
 
 void launch_sp_tables(u64 h, u64 *w, u64 *C, u64 *iv, u64 *w2, cudaStream_t st)
 {
-    k_sp_tables<<<152, SP_NT, 0, st>>>(h, w, C, iv, w2);
+    k_sp_tables<<<device_sms(), SP_NT, 0, st>>>(h, w, C, iv, w2);
 }
 
 void launch_sp_prove(const u64 *a, u64 v, u64 h, const u64 *w, const u64 *C, const u64 *iv, u64 *part, u64 *proof,
@@ -311,16 +311,13 @@ void launch_sp_prove(const u64 *a, u64 v, u64 h, const u64 *w, const u64 *C, con
 void launch_sp_vbegin(u64 seed, u64 v, u64 h, const u64 *w, const u64 *w2, u64 *L, u64 *M, u64 *acc, u64 *res,
                       cudaStream_t st)
 {
-    k_sp_vbegin<<<1 + 152, SP_NT, 0, st>>>(seed, v, h, w, w2, L, M, acc, res);
+    k_sp_vbegin<<<1 + device_sms(), SP_NT, 0, st>>>(seed, v, h, w, w2, L, M, acc, res);
 }
 
 void launch_sp_vabsorb(const u64 *rows, u64 x0, u64 nrows, u64 h, const u64 *L, u64 *acc, u32 *status,
                        cudaStream_t st)
 {
-    u64 blocks = (nrows * 32 + SP_NT - 1) / SP_NT;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    if (blocks < 1) blocks = 1;
-    k_sp_vabsorb<<<(unsigned)blocks, SP_NT, 0, st>>>(rows, x0, nrows, h, L, acc, status);
+    k_sp_vabsorb<<<grid_for_items(nrows * 32, SP_NT, 8), SP_NT, 0, st>>>(rows, x0, nrows, h, L, acc, status);
 }
 
 void launch_sp_vend(const u64 *proof, u64 v, u64 h, const u64 *M, const u64 *acc, u64 *res, cudaStream_t st)

@@ -353,10 +353,7 @@ __global__ void k_check_canonical(const u64 *x, u64 n, u32 *status)
 
 void launch_check_canonical(const u64 *x, u64 n, u32 *status, cudaStream_t st)
 {
-    u64 blocks = (n + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    if (blocks == 0) blocks = 1;
-    k_check_canonical<<<(unsigned)blocks, 256, 0, st>>>(x, n, status);
+    k_check_canonical<<<grid_for_items(n, 256, 8), 256, 0, st>>>(x, n, status);
 }
 
 // Canonical-input check inside a proof plan: an item covers 2048 inputs of

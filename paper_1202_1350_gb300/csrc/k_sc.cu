@@ -971,15 +971,10 @@ __global__ void __launch_bounds__(WV_NT, WV_MINB) k_waves(const Globals *Gs, con
     }
 }
 
-static int g_sm_count[64];
-
-// SM count of the current device, cached (called outside stream capture).
+// Shared-memory size of the wave launch (called outside stream capture).
 void waves_init()
 {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (dev >= 0 && dev < 64 && sms > 0) g_sm_count[dev] = sms;
+    device_sms();
     cudaFuncSetAttribute(k_waves, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(WaveSmem));
 }
 
@@ -987,14 +982,7 @@ void launch_waves(const Globals *Gs, const LineWaveDev *lw, const ProdWave *pw, 
                   int ntasks, u32 *ctr, cudaStream_t st)
 {
     if (ntasks <= 0) return;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int sms = (dev >= 0 && dev < 64) ? g_sm_count[dev] : 0;
-    if (sms <= 0) {
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 152;
-        if (dev >= 0 && dev < 64) g_sm_count[dev] = sms;
-    }
+    const int sms = device_sms();
     const int grid = std::min(ntasks, sms * WV_MINB);
     k_waves<<<grid, WV_NT, sizeof(WaveSmem), st>>>(Gs, lw, pw, gw, tasks, ntasks, ctr);
 }
@@ -1110,6 +1098,6 @@ void launch_final(Globals *Gs, const RoundRef *rounds, int nrounds, int nbig, co
     u64 blocks = warp_blocks > thread_blocks ? warp_blocks : thread_blocks;
     if (blocks < (u64)nouts) blocks = (u64)nouts;
     if (blocks < 64) blocks = 64;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > (u64)device_sms() * 8) blocks = (u64)device_sms() * 8;
     k_final<<<(unsigned)blocks, 256, 0, st>>>(Gs, rounds, nrounds, nbig, outs, nouts);
 }

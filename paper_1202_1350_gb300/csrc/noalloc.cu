@@ -13,6 +13,8 @@
 #include "field.cuh"
 #include "vc.h"
 
+unsigned grid_for_items(u64 n, unsigned threads, unsigned per_sm);  // k_misc.cu
+
 // Intermediate-layer capacity in field elements (8 MiB), plus one status slot.
 #define NOALLOC_MAX_VALUES (1u << 20)
 
@@ -90,12 +92,7 @@ __global__ void k_noalloc_check(const u64 *x, u64 n, u64 *status)
     if (bad) atomicOr(reinterpret_cast<unsigned long long *>(status), 1ull);
 }
 
-static unsigned grid_for(u64 n)
-{
-    u64 b = (n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
-    return b ? (unsigned)b : 1u;
-}
+static unsigned grid_for(u64 n) { return grid_for_items(n, 256, 16); }
 
 extern "C" vc_status vc_evaluate_noalloc(const vc_circuit_desc *desc, const uint64_t *inputs, uint64_t *outputs,
                                          void *stream)
@@ -114,6 +111,9 @@ extern "C" vc_status vc_evaluate_noalloc(const vc_circuit_desc *desc, const uint
 
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices) return VC_ECUDA;
+    // an error left pending by other code stays for its owner to read; the
+    // error checks below then see only this call's own calls and launches
+    if (cudaPeekAtLastError() != cudaSuccess) return VC_ECUDA;
     for (const void *p : {static_cast<const void *>(inputs), static_cast<const void *>(outputs)}) {
         cudaPointerAttributes a{};
         if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {

@@ -323,7 +323,7 @@ void launch_waves(const Globals *Gs, const LineWaveDev *lw, const ProdWave *pw, 
 // FINAL_ALL_WARPS (the warps of one full launch), else those with more than
 // FINAL_WARP_MIN chunk partials; the rest a thread each.
 #define FINAL_WARP_MIN 8u
-#define FINAL_ALL_WARPS (152u * 8u * 8u)
+#define FINAL_ALL_WARPS ((u32)device_sms() * 8u * 8u)
 void launch_final(Globals *Gs, const RoundRef *rounds, int nrounds, int nbig, const u32 *outs, int nouts,
                   cudaStream_t st);
 void prove_kernels_init();
@@ -409,5 +409,10 @@ void launch_sp_vabsorb(const u64 *rows, u64 x0, u64 nrows, u64 h, const u64 *L, 
                        cudaStream_t st);
 void launch_sp_vend(const u64 *proof, u64 v, u64 h, const u64 *M, const u64 *acc, u64 *res, cudaStream_t st);
 
+// SM count of the current device (queried once per device; 1 if the query
+// fails), and the grid of a grid-stride loop over n items capped at per_sm
+// CTAs per SM.
+int device_sms();
+unsigned grid_for_items(u64 n, unsigned threads, unsigned per_sm);
 void launch_field_mul(const u64 *a, const u64 *b, u64 *out, u64 n, cudaStream_t st);
-float run_field_mul_rate(int variant, u64 iters, int blocks, int threads, u64 *sink);
+double run_field_mul_rate(int variant, u64 iters, int sms, u64 *sink);

@@ -65,6 +65,7 @@ struct Job {
     u64 t_submit = 0, t_start = 0, t_done = 0;
     vc_status status = VC_OK;
     bool done = false;
+    bool claimed = false;  // a vc_server_wait owns the job (one consumer per job)
     u64 stage_off = 0;  // offset of the job's transcript in the slot's pinned staging buffer
 };
 
@@ -463,7 +464,7 @@ extern "C" vc_status vc_server_poll(vc_server *s, uint64_t job_id, vc_job_info *
     if (!s || !info) return VC_EINVAL;
     std::lock_guard<std::mutex> g(s->mu);
     auto it = s->jobs.find(job_id);
-    if (it == s->jobs.end()) return VC_EINVAL;
+    if (it == s->jobs.end() || it->second->claimed) return VC_EINVAL;
     fill_info(it->second, info);
     if (it->second->done) {
         delete it->second;
@@ -477,8 +478,9 @@ extern "C" vc_status vc_server_wait(vc_server *s, uint64_t job_id, vc_job_info *
     if (!s || !info) return VC_EINVAL;
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->jobs.find(job_id);
-    if (it == s->jobs.end()) return VC_EINVAL;
+    if (it == s->jobs.end() || it->second->claimed) return VC_EINVAL;
     Job *j = it->second;
+    j->claimed = true;  // no other poll or wait can take (and free) the job meanwhile
     s->cv_done.wait(lk, [&] { return j->done; });
     fill_info(j, info);
     s->jobs.erase(job_id);

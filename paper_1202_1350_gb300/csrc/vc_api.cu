@@ -1994,20 +1994,17 @@ extern "C" vc_status vc_field_mul(const uint64_t *a, const uint64_t *b, uint64_t
 
 extern "C" vc_status vc_field_mul_rate(int device, int variant, uint64_t iters, double *rate)
 {
-    if (!rate || iters == 0 || variant < 0 || variant > 2) return VC_EINVAL;
+    if (!rate || iters == 0 || variant < 0 || variant > 4) return VC_EINVAL;
     DevGuard guard(device);
-    cudaDeviceProp prop{};
-    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return VC_ECUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0)
+        return VC_ECUDA;
     u64 *sink = nullptr;
     if (cudaMalloc(&sink, 64) != cudaSuccess) return VC_ENOMEM;
-    const int threads = 256, blocks = prop.multiProcessorCount * 8;
-    const float ms = run_field_mul_rate(variant, iters, blocks, threads, sink);
-    cudaError_t e = cudaGetLastError();
+    const double r = run_field_mul_rate(variant, iters, sms, sink);
     cudaFree(sink);
-    if (e != cudaSuccess || ms <= 0.f) return VC_ECUDA;
-    // variants 0, 1: 8 chains x one product per step; variant 2: 4 chains x 3 products per step
-    const double per_step = (variant == 2) ? 12.0 : 8.0;
-    *rate = double(blocks) * threads * per_step * double(iters) / (ms * 1e-3);
+    if (r <= 0) return VC_ECUDA;
+    *rate = r;
     return VC_OK;
 }
 

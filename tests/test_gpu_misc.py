@@ -38,9 +38,12 @@ def test_field_mul_matches_bigint():
 
 
 def test_field_mul_rate_runs():
-    for variant in (0, 1):
-        r = vc.vc_field_mul_rate(0, variant, 1 << 12)
-        assert r > 1e10
+    rates = [vc.vc_field_mul_rate(0, variant, 1 << 10) for variant in range(5)]
+    assert all(r > 1e10 for r in rates), rates
+    # a 32-bit multiply-add is cheaper than any field product
+    assert rates[3] > max(rates[0], rates[1], rates[2])
+    with pytest.raises(vc.VcError):
+        vc.vc_field_mul_rate(0, 5, 1 << 10)
 
 
 @pytest.mark.parametrize("family,logn", [("f2", 12), ("f0", 5), ("matmult", 4)])

@@ -2,12 +2,14 @@
 device memory (their memory belongs to another allocator, or the implicit
 synchronisation of cudaMalloc/cudaFree is unacceptable to them).
 
-Its outputs must equal vc_evaluate's (exact field elements, so bit for bit) on
-two calls in a row, since every call reuses one fixed device array that keeps
-the previous call's contents.  This file is collected last on purpose."""
+Its outputs must equal vc_evaluate's and the CPU oracle's evaluation (exact
+field elements, so bit for bit) on two calls in a row, since every call reuses
+one fixed device array that keeps the previous call's contents.  This file is
+collected last on purpose."""
 import numpy as np
 import pytest
 
+import oracle
 from gpu_util import ensure_built, to_np
 from paper_1202_1350_gb300 import circuits, vc
 from paper_1202_1350_gb300 import inputs as I
@@ -36,12 +38,19 @@ def reference_outputs(widths, kinds, xd):
         vc.vc_circuit_destroy(h)
 
 
+def oracle_outputs(widths, kinds, x):
+    """Layer 0 of the CPU oracle's evaluation (independent of the CUDA path)."""
+    return oracle.Circuit(widths, kinds).evaluate(np.asarray(x, np.uint64))[0]
+
+
 @pytest.mark.parametrize("family,logn", [("f2", 10), ("f2", 18), ("f0", 5), ("matmult", 4), ("matmult", 6)])
 def test_matches_vc_evaluate_on_two_calls(family, logn):
     widths, kinds = circuits.by_name(family, logn)
-    want = reference_outputs(widths, kinds, dev(I.job_inputs(family, logn, 71)))
+    x = I.job_inputs(family, logn, 71)
+    want = reference_outputs(widths, kinds, dev(x))
+    assert (want == oracle_outputs(widths, kinds, x)).all()
     for call in range(2):
-        xd = dev(I.job_inputs(family, logn, 71))
+        xd = dev(x)
         out = torch.full((1 << widths[0],), -1, dtype=torch.int64, device="cuda")
         vc.vc_evaluate_noalloc(widths, kinds, xd, out)
         assert (to_np(out) == want).all(), f"call {call}"
@@ -59,6 +68,8 @@ def test_different_circuits_back_to_back():
     vc.vc_evaluate_noalloc(small_w, small_k, xs, os_)
     assert (to_np(os_) == reference_outputs(small_w, small_k, xs)).all()
     assert (to_np(ob) == reference_outputs(big_w, big_k, xb)).all()
+    assert (to_np(os_) == oracle_outputs(small_w, small_k, to_np(xs))).all()
+    assert (to_np(ob) == oracle_outputs(big_w, big_k, to_np(xb))).all()
 
 
 def test_rejects_what_it_cannot_do():
