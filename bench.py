@@ -152,6 +152,13 @@ def executed_work(widths, kinds, first_wave_log=12):
 # capture of the current kernel; the V tables are mostly served from L2, so
 # this is below the algorithmic bytes
 K_WAVES_DRAM_BYTES = 25_572_096
+# The same launch's integer pipes (ncu, % of peak sustained while active):
+# the multiply pipe (fmaheavy) cycles, ALU instructions, issue slots
+K_WAVES_PIPES = {"fmaheavy_cycles_pct": 52.4, "alu_inst_pct": 49.9, "issue_active_pct": 48.7}
+# ncu: the pair-step microbenchmark keeps the multiply pipe (fmaheavy) busy
+# this fraction of its cycles (83-86 % over its configurations), so the pipe
+# saturated would give its rate / this fraction
+PAIR_STEP_FMAHEAVY_FRAC = 0.847
 
 
 def run_ablation(h, xd, tr, flush, reps=5):
@@ -546,7 +553,13 @@ def run_ours(args):
                      "frac": achieved / rate, "traffic": K_WAVES_DRAM_BYTES,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "peak_source": "measured on this GPU: vc_field_mul_rate variant 2, the kernel's own "
-                                    "pair step (2 multiply-adds + 1 lazy fold) over 1216x256 threads",
+                                    "pair step (2 exact multiply-adds + 1 lazy fold), best of 5 chain-count and "
+                                    "register-budget configurations on a one-wave grid; ncu shows that step keeps "
+                                    "the integer-multiply (fmaheavy) pipe 83-86 % of its cycles busy "
+                                    "(profiles/int_rate_microbench.md)",
+                     "peak_pipe_saturated": rate / PAIR_STEP_FMAHEAVY_FRAC / 1e12,
+                     "frac_of_pipe_saturated": achieved / (rate / PAIR_STEP_FMAHEAVY_FRAC),
+                     "kernel_pipes_ncu": K_WAVES_PIPES,
                      "algorithmic_mulmods": mul, "algorithmic_rule": "7 S_i + 24 S_{i+1} per layer (folding prover)",
                      "executed_mulmods": executed, "executed_frac": executed / (wave_launch_ms / 1000) / rate,
                      "algorithmic_bytes": byts, "kernel_ms": wave_launch_ms,
