@@ -271,33 +271,93 @@ def measured_peaks():
 
 # ---- the oracle on the host cores ---------------------------------------------------------
 
-def _oracle_job(args):
-    logn, seed = args
+def _oracle_warm(_):
+    """Pool warm-up: load the oracle library and run one tiny proof."""
+    sys.path.insert(0, ROOT)
+    import oracle
+    c = oracle.Circuit(*oracle.f2_layers(4))
+    c.prove(np.arange(16, dtype=np.uint64), 1)
+    return os.getpid()
+
+
+def _oracle_layers(fam, logn):
+    import oracle
+    return {"f2": oracle.f2_layers, "f0": oracle.f0_layers, "matmult": oracle.matmult_layers}[fam](logn)
+
+
+def _oracle_run(args):
+    """Prove (and optionally verify) a list of jobs with the C oracle; returns
+    the seconds spent in the proofs."""
+    jobs, verify = args
     sys.path.insert(0, ROOT)
     import oracle
     from paper_1202_1350_gb300 import inputs as I
-    c = oracle.Circuit(*oracle.f2_layers(logn))
-    x = I.f2_inputs(logn, 1 << 16, seed)
-    t0 = time.perf_counter()
-    tr = c.prove(x, 1)
-    ok, _ = c.verify(x, 1, tr)
-    return time.perf_counter() - t0, ok
+    t = 0.0
+    for fam, logn, seed in jobs:
+        c = oracle.Circuit(*_oracle_layers(fam, logn))
+        x = I.job_inputs(fam, logn, seed)
+        t0 = time.perf_counter()
+        tr = c.prove(x, seed & 0xFFFFFFFF)
+        if verify:
+            ok, _ = c.verify(x, seed & 0xFFFFFFFF, tr)
+            assert ok
+        t += time.perf_counter() - t0
+    return t
 
 
-def cpu_baseline(logn: int = 20):
+def _oracle_pool_run(job_lists, verify):
+    """Run job_lists[k] in worker k (one process per host core, spawned and
+    warmed up before the clock starts); returns (wall seconds, CPU seconds)."""
     import oracle
     oracle.build()
-    cores = max(1, min(8, os.cpu_count() or 1))
     ctx = mp.get_context("spawn")
-    t0 = time.perf_counter()
-    with ctx.Pool(cores) as pool:
-        res = pool.map(_oracle_job, [(logn, 5000 + j) for j in range(cores)])
-    wall = time.perf_counter() - t0
+    n = len(job_lists)
+    with ctx.Pool(n) as pool:
+        pool.map(_oracle_warm, range(n), chunksize=1)
+        t0 = time.perf_counter()
+        cpu = pool.map(_oracle_run, [(jl, verify) for jl in job_lists], chunksize=1)
+        wall = time.perf_counter() - t0
+    return wall, sum(cpu)
+
+
+def _deal(jobs, n, weight):
+    """Split jobs over n workers, heaviest first to the least loaded."""
+    lists, load = [[] for _ in range(n)], [0.0] * n
+    for j in sorted(jobs, key=weight, reverse=True):
+        k = min(range(n), key=load.__getitem__)
+        lists[k].append(j)
+        load[k] += weight(j)
+    return [jl for jl in lists if jl]
+
+
+def host_cores() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def cpu_baseline(logn: int = 20, per_core: int = 2):
+    """The C oracle on every host core: each process proves and verifies
+    `per_core` F2 n = 2^logn instances (after a warm-up proof); value = all
+    gates / the wall time of the timed phase."""
+    cores = host_cores()
+    jobs = [[("f2", logn, 5000 + cores * r + j) for r in range(per_core)] for j in range(cores)]
+    wall, cpu = _oracle_pool_run(jobs, True)
     gates = 2 * (1 << logn) - 1
-    assert all(ok for _, ok in res)
-    return {"value": cores * gates / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{cores} independent F2 n=2^{logn} prove+verify runs of the C oracle, one per process "
-                      f"({wall:.1f} s wall, {sum(t for t, _ in res):.1f} s CPU)"}
+    return {"value": cores * per_core * gates / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes (one per host core, os.cpu_count() = {cores}), each proving and verifying "
+                      f"{per_core} F2 n=2^{logn} instances with the C oracle after a warm-up proof "
+                      f"({wall:.1f} s wall, {cpu:.1f} s CPU)"}
+
+
+def cpu_baseline_jobs(jobs, what: str):
+    """Proofs per second of the C oracle over a job list, one process per host
+    core (jobs dealt heaviest first); prove only, as the GPU legs time."""
+    from paper_1202_1350_gb300 import circuits
+    cores = host_cores()
+    weight = lambda j: float(circuits.non_input_gates(circuits.by_name(j[0], j[1])[0]))  # noqa: E731
+    wall, cpu = _oracle_pool_run(_deal(jobs, cores, weight), False)
+    return {"proofs_per_s": len(jobs) / wall, "jobs": len(jobs), "cores": cores, "kind": "oracle",
+            "wall_s": wall, "cpu_s": cpu,
+            "sample": f"{what}: {len(jobs)} proofs by the C oracle on {cores} processes (one per host core)"}
 
 
 REFERENCE_BUDGET_S = 100.0
@@ -579,6 +639,11 @@ def run_ours(args):
         line["batched"] = run_batch(local)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        if "batched" in line:
+            line["batched"]["cpu_baseline"] = cpu_baseline_jobs(I.batch_mix(), "the batched workload (every job)")
+        if "serving" in line:
+            line["serving"]["cpu_baseline"] = cpu_baseline_jobs(
+                I.serving_mix(0xC0FFEE + 6, 64), "the first 64 jobs of the serving mix's closed-loop trace")
     print(json.dumps(line), flush=True)
     vc.vc_circuit_destroy(h)
     if dist:
@@ -592,11 +657,11 @@ def run_batch(local: int, reps: int = 5):
     (n in {16, 32, 64}) proved as one batch (merged launches, CUDA graph)
     against the same proofs one at a time (vc_prove per circuit, each its own
     graph) on one stream.  Inputs and transcripts resident in HBM.  The tile
-    shapes are chosen on the batch itself: it is timed with each circuit's
-    default shapes, with those but half-size chunks for product-weighted
-    instances below 2^13 entries, and with the shapes the autotuner picks per
-    size class (it times single circuits of the class, not the merged batch);
-    the fastest is reported, all are listed."""
+    shapes are the autotuner's: vc_autotune_batch searches one configuration
+    for the whole mix by timing the merged batch itself and records it for
+    every member's size class, so the circuits built afterwards use it.  The
+    same batch with each circuit's default shapes is timed first, for
+    comparison."""
     import torch
     from paper_1202_1350_gb300 import circuits, vc
     from paper_1202_1350_gb300 import inputs as I
@@ -631,38 +696,20 @@ def run_batch(local: int, reps: int = 5):
         vc.vc_batch_sync(b)
         return e0.elapsed_time(e1) / reps
 
-    def build_with(tiles):
-        hs = [vc.vc_circuit_create_tiles(*circuits.by_name(fam, logn), t, local)
-              for (fam, logn, _), t in zip(jobs, tiles)]
-        trs = [torch.empty(vc.vc_transcript_len(h), dtype=torch.int64, device="cuda") for h in hs]
-        return hs, trs, vc.vc_batch_create(hs)
-
     # each circuit's default tile shapes (no size class tuned yet in this process)
     hs, trs, b = build()
-    cand = {"default": [vc.vc_circuit_get_tiles(h) for h in hs]}
+    default_tiles = vc.vc_circuit_get_tiles(hs[0])
     times = {"default": time_batch(b, trs)}
     destroy(hs, b)
-    cand["default, product-weighted split below 2^13"] = [dict(t, pr_split_log=13) for t in cand["default"]]
-    hs, trs, b = build_with(cand["default, product-weighted split below 2^13"])
-    times["default, product-weighted split below 2^13"] = time_batch(b, trs)
-    destroy(hs, b)
-    # the autotuner's tile shapes per size class, picked before the circuits are built
-    tuned = {}
-    for fam, logn, _ in jobs:
-        if (fam, logn) not in tuned:
-            w, k = circuits.by_name(fam, logn)
-            tuned[(fam, logn)] = vc.vc_autotune(w, k, local, reps=3)
-    hs, trs, b = build()
-    cand["autotuned per size class"] = [vc.vc_circuit_get_tiles(h) for h in hs]
-    times["autotuned per size class"] = time_batch(b, trs)
-    best = min(times, key=times.get)
-    if best != "autotuned per size class":  # rebuild with the chosen shapes for the rest
-        destroy(hs, b)
-        hs, trs, b = build_with(cand[best])
-    batch_ms = times[best]
+    t0 = time.perf_counter()
+    tuned, tuned_ms = vc.vc_autotune_batch([circuits.by_name(fam, logn) for fam, logn, _ in jobs], local, reps=3)
+    tune_s = time.perf_counter() - t0
+    hs, trs, b = build()  # the circuits take the recorded configuration
+    assert vc.vc_circuit_get_tiles(hs[0]) == tuned
+    times["autotuned"] = time_batch(b, trs)
+    batch_ms = times["autotuned"]
     info = vc.vc_batch_get_info(b)
     try:
-        time_batch(b, trs)
         # spot-check: the batched transcript of job 0 equals its standalone proof
         ref = torch.empty_like(trs[0])
         vc.vc_prove(hs[0], xs[0], seeds[0] + 1000 * (reps - 1), ref)
@@ -691,20 +738,27 @@ def run_batch(local: int, reps: int = 5):
             "launches_per_batch": info["prove_launches"],
             "one_at_a_time_proofs_per_s": n / (single_ms / 1000), "one_at_a_time_ms": single_ms,
             "speedup_vs_one_at_a_time": single_ms / batch_ms, "batched_equals_standalone": same,
-            "reps": reps,
-            "tiles": best, "ms_per_batch_by_tiles": times,
-            "autotuned_tiles": {f"{f} 2^{n}": t[0] for (f, n), t in sorted(tuned.items())}}
+            "reps": reps, "tiles": "autotuned (vc_autotune_batch on this batch)",
+            "ms_per_batch_by_tiles": times, "default_tiles": default_tiles, "autotuned_tiles": tuned,
+            "autotune_s": tune_s, "autotune_ms_per_batch": tuned_ms}
 
 
 # ---- serving: Poisson arrivals into the proof server ---------------------------------------
 
-def run_serving(local: int, seconds_per_rate: float = 1.5):
+def run_serving(local: int, seconds_per_rate: float = 1.5, repeats: int = 3):
     """70% F2 (log2 n uniform in [10, 22]) and 30% MatMult (n in {32, 64, 128})
     jobs submitted to vc_server (admission cap 150 GB, continuous batching);
-    inputs resident in HBM, one input vector per shape.  First a saturating
-    burst gives the sustained throughput; then Poisson arrivals at 0.5x, 0.9x
-    and 1.2x of it give proofs/s and p50/p99 latency (submit to transcript
-    written, the server's own clock)."""
+    inputs resident in HBM, one input vector per shape.  Jobs are submitted
+    from this thread and collected (vc_server_wait, in submission order) by a
+    second one, so collection never delays a submission.  Saturation: a closed
+    loop keeps max_inflight x max_batch x 2 jobs outstanding; its rate over
+    windows of 1000 completions, after the first window, is the saturated
+    throughput.  Then Poisson arrivals at 0.5x, 0.9x and 1.2x of it, each rate
+    `repeats` times with other seeds: proofs/s and p50/p99 latency (submit to
+    transcript written, on the server's own clock)."""
+    import queue
+    import threading
+
     import torch
     from paper_1202_1350_gb300 import Server, circuits
     from paper_1202_1350_gb300 import inputs as I
@@ -717,51 +771,93 @@ def run_serving(local: int, seconds_per_rate: float = 1.5):
     xin = {k: torch.from_numpy(I.job_inputs(k[0], k[1], 11 + k[1]).view(np.int64).copy()).cuda() for k in shapes}
     trl = {k: circuits.transcript_len(w) for k, (w, _) in shapes.items()}
     gates = {k: circuits.non_input_gates(w) for k, (w, _) in shapes.items()}
-    srv = Server(local, mem_cap_bytes=150 << 30)
+    max_batch, max_inflight = 16, 4
+    srv = Server(local, mem_cap_bytes=150 << 30, max_batch=max_batch, max_inflight=max_inflight)
 
-    def run(jobs, arrivals):
+    def run(jobs, arrivals=None, outstanding=None):
         trbuf = torch.empty(sum(trl[(f, n)] for f, n, _ in jobs), dtype=torch.int64, device="cuda")
-        ids, off = [], 0
+        q = queue.Queue()
+        infos = []
+        slots = threading.Semaphore(outstanding) if outstanding else None
+
+        def collect():
+            while True:
+                jid = q.get()
+                if jid is None:
+                    return
+                infos.append(srv.wait(jid))
+                if slots:
+                    slots.release()
+
+        th = threading.Thread(target=collect)
+        th.start()
+        off = 0
         t0 = time.perf_counter()
         for k, (fam, logn, seed) in enumerate(jobs):
             if arrivals is not None:
+                wait = arrivals[k] - (time.perf_counter() - t0)
+                if wait > 2e-4:
+                    time.sleep(wait - 1e-4)
                 while time.perf_counter() - t0 < arrivals[k]:
                     pass
+            if slots:
+                slots.acquire()
             w, kinds = shapes[(fam, logn)]
             n = trl[(fam, logn)]
-            ids.append(srv.submit(w, kinds, xin[(fam, logn)], seed, trbuf[off:off + n]))
+            q.put(srv.submit(w, kinds, xin[(fam, logn)], seed, trbuf[off:off + n]))
             off += n
-        infos = [srv.wait(j) for j in ids]
+        q.put(None)
+        th.join()
         assert all(i["status"] == 0 for i in infos)
         lat = np.array([(i["done_ns"] - i["submit_ns"]) / 1e6 for i in infos])
         span = (max(i["done_ns"] for i in infos) - min(i["submit_ns"] for i in infos)) / 1e9
         g = sum(gates[(f, n)] for f, n, _ in jobs)
         return {"proofs_per_s": len(jobs) / span, "gates_per_s": g / span, "jobs": len(jobs),
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "mean_ms": float(lat.mean())}
+                "mean_ms": float(lat.mean())}, infos
+
+    def windows(infos, size=1000):
+        done = np.sort(np.array([i["done_ns"] for i in infos], dtype=np.float64))
+        rates = []
+        for a in range(0, len(done) - size, size):
+            rates.append(size / ((done[a + size] - done[a]) / 1e9))
+        return rates
 
     try:
-        burst = I.serving_mix(0xC0FFEE + 5, 1500)
-        run(burst, None)  # warm-up: fills the circuit pool
-        sat = run(burst, None)
+        warm = I.serving_mix(0xC0FFEE + 5, 1500)
+        run(warm, outstanding=2 * max_batch * max_inflight)  # fills the circuit pool
+        closed = I.serving_mix(0xC0FFEE + 6, 6000)
+        sat, infos = run(closed, outstanding=2 * max_batch * max_inflight)
+        win = windows(infos)
+        sat["window_proofs_per_s"] = win
+        sat["outstanding"] = 2 * max_batch * max_inflight
+        sat_rate = float(np.median(win[1:])) if len(win) > 1 else sat["proofs_per_s"]
+        sat["saturated_proofs_per_s"] = sat_rate
         rates = []
         for mult in (0.5, 0.9, 1.2):
-            rate = mult * sat["proofs_per_s"]
-            n = int(min(20000, max(200, rate * seconds_per_rate)))
-            jobs = I.serving_mix(0xC0FFEE + 5 + int(mult * 10), n)
-            arr = I.poisson_arrivals(0xC0FFEE + int(mult * 10), n, rate)
-            r = run(jobs, arr)
-            r["offered_per_s"] = rate
-            r["load"] = mult
-            rates.append(r)
+            rate = mult * sat_rate
+            n = int(min(30000, max(300, rate * seconds_per_rate)))
+            reps = []
+            for r in range(repeats):
+                jobs = I.serving_mix(0xC0FFEE + 5 + int(mult * 10) + 100 * r, n)
+                arr = I.poisson_arrivals(0xC0FFEE + int(mult * 10) + 100 * r, n, rate)
+                res, _ = run(jobs, arrivals=arr)
+                reps.append(res)
+            summ = {"load": mult, "offered_per_s": rate, "jobs_per_repeat": n, "repeats": reps}
+            for key in ("proofs_per_s", "p50_ms", "p99_ms"):
+                vals = [x[key] for x in reps]
+                summ[key] = float(np.median(vals))
+                summ[key + "_range"] = [float(min(vals)), float(max(vals))]
+            rates.append(summ)
         st = srv.stats()
     finally:
         srv.close()
     return {"workload": "Poisson arrivals; 70% F2 (log2 n uniform in [10,22], x uniform in [0,2^16]), "
                         "30% MatMult (n in {32,64,128}); admission cap 150 GB; inputs resident in HBM",
             "saturated": sat, "rates": rates,
-            "server": {"launch_sets": st["launch_sets"], "max_jobs_in_flight": st["max_jobs_in_flight"],
-                       "circuits": st["circuits_created"], "peak_held_gb": st["peak_held_bytes"] / 1e9}}
+            "server": {"max_batch": max_batch, "max_inflight": max_inflight, "launch_sets": st["launch_sets"],
+                       "max_jobs_in_flight": st["max_jobs_in_flight"], "circuits": st["circuits_created"],
+                       "peak_held_gb": st["peak_held_bytes"] / 1e9}}
 
 
 def main():

@@ -58,8 +58,10 @@ typedef enum {
     VC_EINVAL = 1,    /* bad argument, bad circuit shape, non-canonical input */
     VC_ENOMEM = 2,    /* device or host allocation failed */
     VC_ECUDA = 3,     /* a CUDA runtime call failed */
-    VC_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
-    VC_EBUSY = 5      /* no free capacity (serving admission) */
+    VC_ETIMEOUT = 4,  /* a bounded device-side wait gave up (reserved: no kernel of
+                         this library waits on another, so nothing returns it) */
+    VC_EBUSY = 5,     /* no free capacity (serving admission); a job already on the device */
+    VC_ECANCELED = 6  /* a served job was cancelled before it reached the device */
 } vc_status;
 
 /* How layer i is wired to layer i+1 (Sec. 5.1.4: in-neighbour indices computed
@@ -269,6 +271,18 @@ typedef struct {
  * Allocates and frees scratch; synchronous. */
 vc_status vc_autotune(const vc_circuit_desc *desc, int device, int reps, vc_tile_config *best, double *best_ms);
 
+/* Autotuner for a batch: the same search, but every candidate is one tile
+ * configuration for all n shapes (structured wirings only) and is timed as
+ * their merged batch (vc_batch_prove, `reps` timed proofs after two untimed
+ * ones, every member on zero inputs), starting from each circuit's default
+ * shapes; coordinate descent until a pass improves nothing (at most two
+ * passes).  The chosen configuration is recorded for the size class of every
+ * shape, so circuits of these shapes created later use it, and returned with
+ * the batch's mean proof time in ms.  Creates and frees the candidate
+ * circuits and batches; synchronous. */
+vc_status vc_autotune_batch(const vc_circuit_desc *descs, int n, int device, int reps, vc_tile_config *best,
+                            double *best_ms);
+
 /* vc_circuit_create with explicit tile shapes (VC_EINVAL outside the
  * bounds above). */
 vc_status vc_circuit_create_tiles(const vc_circuit_desc *desc, int device, const vc_tile_config *tiles,
@@ -357,7 +371,7 @@ typedef struct {
     uint64_t circuits_created, circuits_evicted;
     uint64_t held_bytes, peak_held_bytes, pending;
     uint32_t max_jobs_in_flight;
-    uint32_t pad;
+    uint32_t cancelled;      /* jobs cancelled before admission (counted in completed) */
 } vc_server_stats;
 
 /* Start a server on `device` (cfg may be NULL for the defaults). */
@@ -385,6 +399,28 @@ vc_status vc_server_poll(vc_server *s, uint64_t job_id, vc_job_info *info);
 vc_status vc_server_wait(vc_server *s, uint64_t job_id, vc_job_info *info);
 
 vc_status vc_server_get_stats(vc_server *s, vc_server_stats *stats);
+
+/* Cancel a job that is still queued (not yet admitted to a launch set): it is
+ * removed from the queue and completes at once with status VC_ECANCELED (a
+ * poll or wait still reports it, then forgets it); its inputs and transcript
+ * buffer are no longer used.  VC_EBUSY if the job is already on the device or
+ * done (it then completes normally); VC_EINVAL for an unknown id. */
+vc_status vc_server_cancel(vc_server *s, uint64_t job_id);
+
+/* Library-wide memory budget (the paper has no counterpart).  Caps the bytes
+ * of device memory and of page-locked host memory that this library holds at
+ * once, over all circuits, batches, servers and special-purpose states of the
+ * process (0 = no cap, the default).  An allocation past a cap fails before
+ * any CUDA call, as a refused cudaMalloc would: the call that needed it
+ * returns VC_ENOMEM and frees what it had taken, and a served job that
+ * needed a new circuit completes with status VC_ENOMEM while other jobs go
+ * on.  Lowering a cap below what is held frees nothing; later allocations
+ * fail until enough is released.  Never fails. */
+vc_status vc_set_memory_limit(uint64_t device_bytes, uint64_t pinned_bytes);
+
+/* Bytes of device and page-locked host memory the library holds now (either
+ * pointer may be NULL, not both: VC_EINVAL). */
+vc_status vc_get_memory_usage(uint64_t *device_bytes, uint64_t *pinned_bytes);
 
 /* ---- Special-purpose non-interactive F2 protocol (Sec. 3.2; Sec. 4.2;
  * Sec. 6.3).  The frequency vector a of n = v h entries is a v x h grid,

@@ -175,6 +175,10 @@ class Server:
             self._keep.pop(job_id, None)
         return info
 
+    def cancel(self, job_id: int) -> None:
+        """Cancel a queued job; it then reports status VC_ECANCELED."""
+        _vc.vc_server_cancel(self.handle, job_id)
+
     def stats(self) -> dict:
         return _vc.vc_server_get_stats(self.handle)
 

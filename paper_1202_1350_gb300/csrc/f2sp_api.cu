@@ -61,22 +61,22 @@ extern "C" vc_status vc_f2sp_create(uint64_t v, uint64_t h, int device, vc_f2sp 
     };
     Arena A0;
     carve(A0);
-    cudaError_t e = cudaMalloc(&s->mem, A0.off);
+    cudaError_t e = lib_malloc(&s->mem, A0.off);
     if (e == cudaSuccess) {
         Arena A;
         A.base = reinterpret_cast<uintptr_t>(s->mem);
         carve(A);
         e = cudaMemset(s->mem, 0, A0.off);
     }
-    if (e == cudaSuccess) e = cudaHostAlloc(&s->h_res, 8 * sizeof(u64), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = lib_host_alloc(&s->h_res, 8 * sizeof(u64), cudaHostAllocDefault);
     if (e == cudaSuccess) {
         launch_sp_tables(h, s->w, s->C, s->iv, s->w2, 0);
         e = cudaDeviceSynchronize();
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
-        if (s->mem) cudaFree(s->mem);
-        if (s->h_res) cudaFreeHost(s->h_res);
+        if (s->mem) lib_free(s->mem);
+        if (s->h_res) lib_free_host(s->h_res);
         delete s;
         return e == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA;
     }
@@ -89,9 +89,9 @@ extern "C" vc_status vc_f2sp_destroy(vc_f2sp *s)
     if (!s) return VC_OK;
     DevGuard guard(s->device);
     cudaDeviceSynchronize();
-    if (s->mem) cudaFree(s->mem);
-    if (s->a_stage) cudaFree(s->a_stage);
-    if (s->h_res) cudaFreeHost(s->h_res);
+    if (s->mem) lib_free(s->mem);
+    if (s->a_stage) lib_free(s->a_stage);
+    if (s->h_res) lib_free_host(s->h_res);
     delete s;
     return VC_OK;
 }
@@ -106,7 +106,7 @@ static const u64 *sp_device_input(vc_f2sp *s, const uint64_t *p, u64 n, cudaStre
         return nullptr;
     }
     if (k == 1) return p;
-    if (!s->a_stage && cudaMalloc(&s->a_stage, s->v * s->h * sizeof(u64)) != cudaSuccess) {
+    if (!s->a_stage && lib_malloc(&s->a_stage, s->v * s->h * sizeof(u64)) != cudaSuccess) {
         cudaGetLastError();
         s->a_stage = nullptr;
         *err = VC_ENOMEM;

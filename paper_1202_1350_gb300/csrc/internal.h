@@ -27,6 +27,24 @@ struct PlanConfig {
     u32 pr_split = VC_SPLIT_WIDEST;  // PROD instances below 2^pr_split entries: chunks of 2^(pr_chunk - 1)
 };
 
+// Every device and page-locked host allocation of the library goes through
+// these (mem.cu): they keep the process-wide budget of vc_set_memory_limit
+// and fail with cudaErrorMemoryAllocation, before any CUDA call, past it.
+cudaError_t lib_malloc(void **p, size_t n);
+cudaError_t lib_free(void *p);
+cudaError_t lib_host_alloc(void **p, size_t n, unsigned flags);
+cudaError_t lib_free_host(void *p);
+template <class T>
+cudaError_t lib_malloc(T **p, size_t n)
+{
+    return lib_malloc(reinterpret_cast<void **>(p), n);
+}
+template <class T>
+cudaError_t lib_host_alloc(T **p, size_t n, unsigned flags)
+{
+    return lib_host_alloc(reinterpret_cast<void **>(p), n, flags);
+}
+
 // Which layers' phase-2/3 tables are built by k_build23 (the rest are formed
 // on the fly or never stored).
 inline bool needs_tables(u32 kind) { return kind != W_SQUARE && kind != W_TREE; }

@@ -161,10 +161,10 @@ bool ensure_pinned(T *&p, size_t &cap, size_t n)
 {
     if (n <= cap) return true;
     const size_t want = std::max(n, cap * 2);
-    if (p) cudaFreeHost(p);
+    if (p) lib_free_host(p);
     p = nullptr;
     cap = 0;
-    if (cudaHostAlloc(&p, want * sizeof(T), cudaHostAllocDefault) != cudaSuccess) return false;
+    if (lib_host_alloc(&p, want * sizeof(T), cudaHostAllocDefault) != cudaSuccess) return false;
     cap = want;
     return true;
 }
@@ -187,12 +187,12 @@ vc_status launch(vc_server *s, Slot &sl)
     if (need > sl.dev_cap) {
         if (sl.dev) {
             cudaStreamSynchronize(sl.st);
-            cudaFree(sl.dev);
+            lib_free(sl.dev);
         }
         sl.dev = nullptr;
         sl.dev_cap = 0;
         const size_t want = std::max(need, (size_t)16 << 20);
-        if (cudaMalloc(&sl.dev, want) != cudaSuccess) {
+        if (lib_malloc(&sl.dev, want) != cudaSuccess) {
             cudaGetLastError();
             return VC_ENOMEM;
         }
@@ -391,9 +391,9 @@ extern "C" vc_status vc_server_destroy(vc_server *s)
     cudaDeviceSynchronize();
     for (Slot &sl : s->slots) {
         plan_release(sl.P);
-        if (sl.dev) cudaFree(sl.dev);
-        if (sl.h_cp) cudaFreeHost(sl.h_cp);
-        if (sl.h_stage) cudaFreeHost(sl.h_stage);
+        if (sl.dev) lib_free(sl.dev);
+        if (sl.h_cp) lib_free_host(sl.h_cp);
+        if (sl.h_stage) lib_free_host(sl.h_stage);
         cudaStreamDestroy(sl.st);
         cudaEventDestroy(sl.done);
     }
@@ -485,6 +485,25 @@ extern "C" vc_status vc_server_wait(vc_server *s, uint64_t job_id, vc_job_info *
     fill_info(j, info);
     s->jobs.erase(job_id);
     delete j;
+    return VC_OK;
+}
+
+extern "C" vc_status vc_server_cancel(vc_server *s, uint64_t job_id)
+{
+    if (!s) return VC_EINVAL;
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return VC_EINVAL;
+    Job *j = it->second;
+    auto q = std::find(s->pending.begin(), s->pending.end(), j);
+    if (q == s->pending.end()) return VC_EBUSY;  // admitted (on the device) or done
+    s->pending.erase(q);
+    j->status = VC_ECANCELED;
+    j->t_start = j->t_done = now_ns();
+    j->done = true;
+    s->stats.completed++;
+    s->stats.cancelled++;
+    s->cv_done.notify_all();
     return VC_OK;
 }
 

@@ -228,6 +228,7 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     G.d = d;
     G.nchal = c->nchal;
     G.chal = A.take<u64>(c->nchal + 1);
+    G.ichal = A.take<u64>(c->nchal + 1);
     u32 npts = 0;
     for (u32 i = 0; i <= d; i++) npts += c->s[i];
     G.pts = A.take<u64>(npts + 1);
@@ -288,6 +289,10 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
             c->eq_verify.push_back({L.tr2, 0u, EQ_SRC_CHAL, L.chal_off + L.s + L.sn, 0u});
         }
     }
+
+    // the inverse challenges (used by the sum-check waves)
+    for (u32 c0 = 0; c0 < c->nchal; c0 += INV_PER_JOB)
+        P.eqjobs.push_back({EqTab{}, 0u, EQ_SRC_INV, c0, std::min<u32>(INV_PER_JOB, c->nchal - c0)});
 
     // Waves.  A wave is one launch's share of an instance: chunks of 2^nr
     // entries (2^nl coordinates for the line reduction).  A wave followed by a
@@ -440,6 +445,7 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
                     W.no = n - r0 - nr;
                     W.ho = (W.no + 1) / 2;
                     W.chal_off = Sc.chal_off + r0;
+                    W.lc = Sc.Lc + 2 * r0;
                     W.in = inV;
                     W.out = last ? nullptr : A.take<u64>(nchunks);
                     const u32 kb = W.e ? W.e - 1 : 0;
@@ -529,6 +535,7 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     Globals &Gv = c->Gv;
     Gv = G;
     Gv.chal = A.take<u64>(c->nchal + 1);
+    Gv.ichal = nullptr;  // the verifier needs no inverse challenges
     Gv.pts = A.take<u64>(npts + 1);
     Gv.scal = A.take<u64>(2 * d + 2);
     Gv.status = G.status + 1;
@@ -577,7 +584,9 @@ bool plan_valid(const Plan &P)
     for (const Item &it : P.checks)
         if (it.wave >= nc) return false;
     for (const EqJob &J : P.eqjobs)
-        if (J.circ >= nc || J.t.n > 30 || (J.src != EQ_SRC_CHAL && J.src != EQ_SRC_Z)) return false;
+        if (J.circ >= nc || J.t.n > 30 || (J.src != EQ_SRC_CHAL && J.src != EQ_SRC_Z && J.src != EQ_SRC_INV) ||
+            (J.src == EQ_SRC_INV && J.layer > INV_PER_JOB))
+            return false;
     for (const EvalSeg &S : P.segs)
         if (S.circ >= nc) return false;
     for (const LayerEval &E : P.levs)
@@ -1158,11 +1167,11 @@ void circuit_free(vc_circuit *c)
     for (cudaGraph_t g : {c->vgraph, c->vin_graph})
         if (g) cudaGraphDestroy(g);
     if (c->pg_exec) cudaGraphExecDestroy(c->pg_exec);
-    if (c->pg_arena) cudaFree(c->pg_arena);
+    if (c->pg_arena) lib_free(c->pg_arena);
     plan_release(c->P);
-    if (c->arena) cudaFree(c->arena);
-    if (c->host_vals) cudaFreeHost(c->host_vals);
-    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    if (c->arena) lib_free(c->arena);
+    if (c->host_vals) lib_free_host(c->host_vals);
+    if (c->h_pinned) lib_free_host(c->h_pinned);
     delete c;
 }
 
@@ -1172,7 +1181,7 @@ vc_status circuit_allocate(vc_circuit *c)
     const size_t bytes = c->arena_bytes;
     DevGuard guard(c->device);
     init_device_once(c->device);
-    cudaError_t e = cudaMalloc(&c->arena, bytes);
+    cudaError_t e = lib_malloc(&c->arena, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         c->arena = nullptr;
@@ -1181,7 +1190,7 @@ vc_status circuit_allocate(vc_circuit *c)
     uintptr_t hbase = 0;
     if (c->host_bytes) {
         void *dp = nullptr;
-        e = cudaHostAlloc(&c->host_vals, c->host_bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+        e = lib_host_alloc(&c->host_vals, c->host_bytes, cudaHostAllocMapped | cudaHostAllocPortable);
         if (e == cudaSuccess) e = cudaHostGetDevicePointer(&dp, c->host_vals, 0);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -1222,7 +1231,7 @@ vc_status circuit_allocate(vc_circuit *c)
         launch_init_invfact(c->G.invfact, c->P.cap);
         e = cudaStreamSynchronize(c->P.cap);
     }
-    if (e == cudaSuccess) e = cudaHostAlloc(&c->h_pinned, 64 * sizeof(u64), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = lib_host_alloc(&c->h_pinned, 64 * sizeof(u64), cudaHostAllocDefault);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return cuda_status(e);
@@ -1396,7 +1405,7 @@ static vc_status pergate_prepare(vc_circuit *c)
     Arena A0;
     carve(A0);
     char *mem = nullptr;
-    if (cudaMalloc(&mem, A0.off) != cudaSuccess) {
+    if (lib_malloc(&mem, A0.off) != cudaSuccess) {
         cudaGetLastError();
         return VC_ENOMEM;
     }
@@ -1407,7 +1416,7 @@ static vc_status pergate_prepare(vc_circuit *c)
     if (e == cudaSuccess) e = upload(c->d_pg_blk, blk);
     if (e == cudaSuccess) e = upload(c->d_pg_lblk, lblk);
     if (e != cudaSuccess) {
-        cudaFree(mem);
+        lib_free(mem);
         return VC_ECUDA;
     }
     c->pg_arena = mem;
@@ -1726,11 +1735,11 @@ extern "C" vc_status vc_autotune(const vc_circuit_desc *desc, int device, int re
     circuit_free(probe);
     u64 *din = nullptr, *dtr = nullptr;
     cudaStream_t st = nullptr;
-    if (cudaMalloc(&din, nin * sizeof(u64)) != cudaSuccess || cudaMalloc(&dtr, trl * sizeof(u64)) != cudaSuccess ||
+    if (lib_malloc(&din, nin * sizeof(u64)) != cudaSuccess || lib_malloc(&dtr, trl * sizeof(u64)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
-        if (din) cudaFree(din);
-        if (dtr) cudaFree(dtr);
+        if (din) lib_free(din);
+        if (dtr) lib_free(dtr);
         return VC_ENOMEM;
     }
     cudaMemsetAsync(din, 0, nin * sizeof(u64), st);
@@ -1757,13 +1766,135 @@ extern "C" vc_status vc_autotune(const vc_circuit_desc *desc, int device, int re
                 cur_ms = ms;
             }
         }
-    cudaFree(din);
-    cudaFree(dtr);
+    lib_free(din);
+    lib_free(dtr);
     cudaStreamDestroy(st);
     if (s != VC_OK) return s;
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_tuned[size_class(desc)] = cur;
+    }
+    if (best) *best = {cur.pr_chunk, cur.gn_chunk, cur.ln_chunk0, cur.ev_chunk, cur.pr_split};
+    if (best_ms) *best_ms = cur_ms;
+    return VC_OK;
+}
+
+// Mean time of `reps` proofs of a merged batch of circuits of shapes
+// descs[0..n) built with tile shapes f (after two untimed proofs; the first
+// captures the batch's graph).  Every member reads the same zero inputs.
+static vc_status time_batch_config(const vc_circuit_desc *descs, int n, int device, const PlanConfig &f, int reps,
+                                   const u64 *din, cudaStream_t st, double *ms)
+{
+    std::vector<vc_circuit *> cs(n, nullptr);
+    vc_status s = VC_OK;
+    u64 trl = 0;
+    for (int j = 0; j < n && s == VC_OK; j++) {
+        s = circuit_prepare(&descs[j], device, &cs[j], &f);
+        if (s == VC_OK) s = circuit_allocate(cs[j]);
+        if (s == VC_OK) trl += cs[j]->tr_len;
+    }
+    vc_batch *b = nullptr;
+    u64 *dtr = nullptr;
+    if (s == VC_OK) s = vc_batch_create(cs.data(), n, &b);
+    if (s == VC_OK && lib_malloc(&dtr, trl * sizeof(u64)) != cudaSuccess) {
+        cudaGetLastError();
+        s = VC_ENOMEM;
+    }
+    if (s == VC_OK) {
+        std::vector<const uint64_t *> ins(n, din);
+        std::vector<uint64_t *> trs(n);
+        std::vector<uint64_t> seeds(n);
+        u64 off = 0;
+        for (int j = 0; j < n; j++) {
+            trs[j] = dtr + off;
+            off += cs[j]->tr_len;
+        }
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) s = VC_ECUDA;
+        for (int k = 0; k < 2 + reps && s == VC_OK; k++) {
+            if (k == 2) cudaEventRecord(e0, st);
+            for (int j = 0; j < n; j++) seeds[j] = 1000u * k + j + 1;
+            s = vc_batch_prove(b, ins.data(), seeds.data(), trs.data(), st);
+        }
+        if (s == VC_OK) {
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) s = VC_ECUDA;
+            float t = 0;
+            cudaEventElapsedTime(&t, e0, e1);
+            *ms = t / reps;
+        }
+        if (s == VC_OK) s = vc_batch_sync(b, st);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+    cudaStreamSynchronize(st);
+    if (b) vc_batch_destroy(b);
+    if (dtr) lib_free(dtr);
+    for (vc_circuit *c : cs)
+        if (c) circuit_free(c);
+    return s;
+}
+
+extern "C" vc_status vc_autotune_batch(const vc_circuit_desc *descs, int n, int device, int reps,
+                                       vc_tile_config *best, double *best_ms)
+{
+    if (!descs || n < 1 || reps < 1) return VC_EINVAL;
+    u64 nin = 0;
+    u32 smax = 0;
+    for (int j = 0; j < n; j++) {
+        const vc_circuit_desc &D = descs[j];
+        if (!D.log_width || !D.wiring || D.n_layers < 1 || D.n_layers > 4096) return VC_EINVAL;
+        for (u32 i = 0; i < D.n_layers; i++)
+            if (D.wiring[i] == W_EXPLICIT || D.log_width[i] > 30) return VC_EINVAL;
+        if (D.log_width[D.n_layers] > 30) return VC_EINVAL;
+        nin = std::max(nin, u64(1) << D.log_width[D.n_layers]);
+        for (u32 i = 0; i <= D.n_layers; i++) smax = std::max(smax, D.log_width[i]);
+    }
+    DevGuard guard(device);
+    init_device_once(device);
+    u64 *din = nullptr;
+    cudaStream_t st = nullptr;
+    if (lib_malloc(&din, nin * sizeof(u64)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        if (din) lib_free(din);
+        return VC_ENOMEM;
+    }
+    cudaMemsetAsync(din, 0, nin * sizeof(u64), st);
+    PlanConfig cur;  // every member's default tile shapes
+    double cur_ms = 0;
+    vc_status s = time_batch_config(descs, n, device, cur, reps, din, st, &cur_ms);
+    // coordinate descent over the knobs, one configuration for every member,
+    // timed on the merged batch itself (the split threshold below the widest
+    // layer of the batch, below 2^13 and 2^11, or never)
+    const u32 cand[5][4] = {{11, 12, 13, 0}, {10, 11, 12, 0}, {11, 12, 13, 0}, {8, 9, 10, 11},
+                            {VC_SPLIT_WIDEST, 13, 11, smax ? smax - 1 : 0}};
+    const int ncand[5] = {3, 3, 3, 4, 4};
+    for (int pass = 0; pass < 2 && s == VC_OK; pass++) {
+        bool moved = false;
+        for (int knob = 0; knob < 5 && s == VC_OK; knob++)
+            for (int j = 0; j < ncand[knob]; j++) {
+                PlanConfig f = cur;
+                u32 *field = knob == 0 ? &f.pr_chunk : knob == 1 ? &f.gn_chunk : knob == 2 ? &f.ln_chunk0
+                           : knob == 3 ? &f.ev_chunk : &f.pr_split;
+                if (*field == cand[knob][j]) continue;
+                *field = cand[knob][j];
+                double ms = 0;
+                s = time_batch_config(descs, n, device, f, reps, din, st, &ms);
+                if (s == VC_OK && ms < 0.98 * cur_ms) {
+                    cur = f;
+                    cur_ms = ms;
+                    moved = true;
+                }
+            }
+        if (!moved) break;
+    }
+    lib_free(din);
+    cudaStreamDestroy(st);
+    if (s != VC_OK) return s;
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        for (int j = 0; j < n; j++) g_tuned[size_class(&descs[j])] = cur;
     }
     if (best) *best = {cur.pr_chunk, cur.gn_chunk, cur.ln_chunk0, cur.ev_chunk, cur.pr_split};
     if (best_ms) *best_ms = cur_ms;
@@ -1840,7 +1971,7 @@ extern "C" vc_status vc_batch_create(vc_circuit *const *circuits, int n, vc_batc
         A.take<GatherChunk>(gather.size());
         bytes = A.off + 256;
     }
-    cudaError_t e = cudaMalloc(&b->arena, bytes);
+    cudaError_t e = lib_malloc(&b->arena, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete b;
@@ -1857,13 +1988,13 @@ extern "C" vc_status vc_batch_create(vc_circuit *const *circuits, int n, vc_batc
     e = upload(b->P.d_G, b->P.h_G);
     if (e == cudaSuccess) e = upload(b->d_gather, gather);
     if (e == cudaSuccess) e = plan_upload(b->P);
-    if (e == cudaSuccess) e = cudaHostAlloc(&b->h_cp, n * sizeof(CallParams), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = lib_host_alloc(&b->h_cp, n * sizeof(CallParams), cudaHostAllocDefault);
     if (e == cudaSuccess) e = plan_resources(b->P);
     if (e != cudaSuccess) {
         cudaGetLastError();
         plan_release(b->P);
-        if (b->h_cp) cudaFreeHost(b->h_cp);
-        cudaFree(b->arena);
+        if (b->h_cp) lib_free_host(b->h_cp);
+        lib_free(b->arena);
         delete b;
         return cuda_status(e);
     }
@@ -1877,8 +2008,8 @@ extern "C" vc_status vc_batch_destroy(vc_batch *b)
     DevGuard guard(b->device);
     cudaDeviceSynchronize();
     plan_release(b->P);
-    if (b->arena) cudaFree(b->arena);
-    if (b->h_cp) cudaFreeHost(b->h_cp);
+    if (b->arena) lib_free(b->arena);
+    if (b->h_cp) lib_free_host(b->h_cp);
     delete b;
     return VC_OK;
 }
@@ -2000,9 +2131,9 @@ extern "C" vc_status vc_field_mul_rate(int device, int variant, uint64_t iters, 
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0)
         return VC_ECUDA;
     u64 *sink = nullptr;
-    if (cudaMalloc(&sink, 64) != cudaSuccess) return VC_ENOMEM;
+    if (lib_malloc(&sink, 64) != cudaSuccess) return VC_ENOMEM;
     const double r = run_field_mul_rate(variant, iters, sms, sink);
-    cudaFree(sink);
+    lib_free(sink);
     if (r <= 0) return VC_ECUDA;
     *rate = r;
     return VC_OK;
@@ -2017,6 +2148,7 @@ extern "C" const char *vc_status_string(vc_status s)
     case VC_ECUDA: return "CUDA error";
     case VC_ETIMEOUT: return "device wait timed out";
     case VC_EBUSY: return "busy";
+    case VC_ECANCELED: return "cancelled";
     default: return "unknown status";
     }
 }

@@ -20,8 +20,9 @@ from . import build as _build
 P = (1 << 61) - 1
 SQUARE, TREE, MATMULT, F0_FIRST, F0_PAIR, F0_FINAL, EXPLICIT = range(7)
 
-VC_OK, VC_EINVAL, VC_ENOMEM, VC_ECUDA, VC_ETIMEOUT, VC_EBUSY = range(6)
-_STATUS = {0: "VC_OK", 1: "VC_EINVAL", 2: "VC_ENOMEM", 3: "VC_ECUDA", 4: "VC_ETIMEOUT", 5: "VC_EBUSY"}
+VC_OK, VC_EINVAL, VC_ENOMEM, VC_ECUDA, VC_ETIMEOUT, VC_EBUSY, VC_ECANCELED = range(7)
+_STATUS = {0: "VC_OK", 1: "VC_EINVAL", 2: "VC_ENOMEM", 3: "VC_ECUDA", 4: "VC_ETIMEOUT", 5: "VC_EBUSY",
+           6: "VC_ECANCELED"}
 
 
 class VcError(RuntimeError):
@@ -75,7 +76,7 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("launch_sets", ctypes.c_uint64),
                 ("circuits_created", ctypes.c_uint64), ("circuits_evicted", ctypes.c_uint64),
                 ("held_bytes", ctypes.c_uint64), ("peak_held_bytes", ctypes.c_uint64),
-                ("pending", ctypes.c_uint64), ("max_jobs_in_flight", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+                ("pending", ctypes.c_uint64), ("max_jobs_in_flight", ctypes.c_uint32), ("cancelled", ctypes.c_uint32)]
 
 
 VC_SPLIT_WIDEST = 0xFFFFFFFF
@@ -143,8 +144,13 @@ def lib():
             L.vc_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(JobInfo)]
             L.vc_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(JobInfo)]
             L.vc_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+            L.vc_server_cancel.argtypes = [vp, ctypes.c_uint64]
+            L.vc_set_memory_limit.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+            L.vc_get_memory_usage.argtypes = [_u64p, _u64p]
             L.vc_autotune.argtypes = [ctypes.POINTER(_Desc), ctypes.c_int, ctypes.c_int, ctypes.POINTER(TileConfig),
                                       ctypes.POINTER(ctypes.c_double)]
+            L.vc_autotune_batch.argtypes = [ctypes.POINTER(_Desc), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(TileConfig), ctypes.POINTER(ctypes.c_double)]
             L.vc_circuit_create_tiles.argtypes = [ctypes.POINTER(_Desc), ctypes.c_int, ctypes.POINTER(TileConfig),
                                                   ctypes.POINTER(vp)]
             L.vc_circuit_get_tiles.argtypes = [vp, ctypes.POINTER(TileConfig)]
@@ -163,7 +169,8 @@ def lib():
                          "vc_circuit_get_info", "vc_batch_create", "vc_batch_destroy", "vc_batch_prove",
                          "vc_batch_sync", "vc_batch_get_info", "vc_server_create", "vc_server_destroy",
                          "vc_server_submit", "vc_server_poll", "vc_server_wait", "vc_server_get_stats",
-                         "vc_autotune", "vc_circuit_create_tiles", "vc_circuit_get_tiles", "vc_prove_pergate",
+                         "vc_server_cancel", "vc_set_memory_limit", "vc_get_memory_usage", "vc_autotune",
+                         "vc_autotune_batch", "vc_circuit_create_tiles", "vc_circuit_get_tiles", "vc_prove_pergate",
                          "vc_circuit_create_ex", "vc_f2sp_create", "vc_f2sp_destroy", "vc_f2sp_prove",
                          "vc_f2sp_verify_begin", "vc_f2sp_verify_absorb", "vc_f2sp_verify_end",
                          "vc_verify_input", "vc_verify_transcript"):
@@ -554,7 +561,24 @@ def vc_server_wait(s, job_id: int) -> dict:
 def vc_server_get_stats(s) -> dict:
     st = ServerStats()
     _check(lib().vc_server_get_stats(s, ctypes.byref(st)), "vc_server_get_stats")
-    return {name: getattr(st, name) for name, _ in ServerStats._fields_ if name != "pad"}
+    return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+
+def vc_server_cancel(s, job_id: int) -> None:
+    """Cancel a queued job (raises VcError VC_EBUSY once it is on the device or done)."""
+    _check(lib().vc_server_cancel(s, job_id), "vc_server_cancel")
+
+
+def vc_set_memory_limit(device_bytes: int = 0, pinned_bytes: int = 0) -> None:
+    """Cap the device / page-locked host bytes the library holds (0: no cap)."""
+    _check(lib().vc_set_memory_limit(int(device_bytes), int(pinned_bytes)), "vc_set_memory_limit")
+
+
+def vc_get_memory_usage() -> tuple:
+    """(device bytes, page-locked host bytes) the library holds now."""
+    d, h = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().vc_get_memory_usage(ctypes.byref(d), ctypes.byref(h)), "vc_get_memory_usage")
+    return d.value, h.value
 
 
 def _tiles(t: TileConfig) -> dict:
@@ -569,6 +593,24 @@ def vc_autotune(log_width, wiring, device: int = 0, reps: int = 5):
     best = TileConfig()
     ms = ctypes.c_double(0)
     _check(lib().vc_autotune(ctypes.byref(desc), device, reps, ctypes.byref(best), ctypes.byref(ms)), "vc_autotune")
+    del keep
+    return _tiles(best), ms.value
+
+
+def vc_autotune_batch(shapes, device: int = 0, reps: int = 3):
+    """Tune one tile configuration for the merged batch of `shapes` (a list of
+    (log_width, wiring)); it is recorded for every shape's size class.
+    Returns (tiles dict, mean batch ms)."""
+    descs = (_Desc * len(shapes))()
+    keep = []
+    for j, (lw, wr) in enumerate(shapes):
+        d, k = _desc_struct(lw, wr)
+        descs[j] = d
+        keep.append(k)
+    best = TileConfig()
+    ms = ctypes.c_double(0)
+    _check(lib().vc_autotune_batch(descs, len(shapes), device, reps, ctypes.byref(best), ctypes.byref(ms)),
+           "vc_autotune_batch")
     del keep
     return _tiles(best), ms.value
 

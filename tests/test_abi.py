@@ -27,6 +27,17 @@ def test_exports_every_declared_function(libvc):
 def test_status_strings(libvc):
     assert vc.vc_status_string(0) == "ok"
     assert vc.vc_status_string(1) == "invalid argument"
+    assert vc.vc_status_string(vc.VC_ECANCELED) == "cancelled"
+
+
+def test_memory_budget_host_side(libvc):
+    """The library-wide memory budget is host state: it can be set and read
+    without a device, and a refused allocation (exercised on the GPU) leaves
+    the accounting unchanged."""
+    assert vc.vc_get_memory_usage() == (0, 0)
+    vc.vc_set_memory_limit(1 << 20, 1 << 10)
+    vc.vc_set_memory_limit(0, 0)
+    assert libvc.vc_get_memory_usage(None, None) == vc.VC_EINVAL
 
 
 @pytest.mark.parametrize("widths,kinds", [

@@ -64,3 +64,31 @@ def test_autotune_records_tiles_for_the_size_class():
         assert (to_np(tr) == oracle_prove(w, k, x, 8)).all()
     finally:
         vc.vc_circuit_destroy(h)
+
+
+def test_batch_autotune_tunes_the_merged_batch():
+    """vc_autotune_batch times candidate configurations on the merged batch
+    and records its choice for every member's size class; a batch of
+    circuits built afterwards uses it and still gives the oracle's
+    transcripts."""
+    mix = [("f2", 9), ("f2", 11), ("matmult", 3), ("f0", 3), ("f2", 10), ("matmult", 4)]
+    shapes = [circuits.by_name(f, n) for f, n in mix]
+    best, ms = vc.vc_autotune_batch(shapes, reps=1)
+    assert ms > 0
+    hs = [vc.vc_circuit_create(w, k) for w, k in shapes]
+    b = vc.vc_batch_create(hs)
+    try:
+        assert all(vc.vc_circuit_get_tiles(h) == best for h in hs)
+        xs = [I.job_inputs(f, n, 60 + j) for j, (f, n) in enumerate(mix)]
+        trs = [torch.empty(vc.vc_transcript_len(h), dtype=torch.int64, device="cuda") for h in hs]
+        seeds = [90 + j for j in range(len(mix))]
+        vc.vc_batch_prove(b, [dev(x) for x in xs], seeds, trs)
+        vc.vc_batch_sync(b)
+        for (w, k), x, s, tr in zip(shapes, xs, seeds, trs):
+            assert (to_np(tr) == oracle_prove(w, k, x, s)).all()
+    finally:
+        vc.vc_batch_destroy(b)
+        for h in hs:
+            vc.vc_circuit_destroy(h)
+    with pytest.raises(vc.VcError):
+        vc.vc_autotune_batch([circuits.by_name("f2", 4)], reps=0)
