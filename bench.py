@@ -190,14 +190,17 @@ def run_ablation(h, xd, tr, flush, reps=5):
 
 def run_residency(widths, kinds, xd, flush, reps=5):
     """Proof time with the layer values in mapped host memory (read and
-    written over the host link) against device-resident values; transcripts
-    compared."""
+    written over the host link at every use) and staged through host memory
+    a layer at a time (copy-once-per-layer: three device slots), against
+    device-resident values; transcripts compared.  link_bytes: what the
+    staged mode moves over the host link per proof (every layer written once,
+    layers 3..d read back once)."""
     import torch
     from paper_1202_1350_gb300 import vc
     out = {}
     trs = {}
-    for name, host in (("device", False), ("host_values", True)):
-        h = vc.vc_circuit_create(widths, kinds, host_values=host)
+    for name, kw in (("device", {}), ("host_values", {"host_values": True}), ("staged", {"staged": True})):
+        h = vc.vc_circuit_create(widths, kinds, **kw)
         tr = torch.empty(vc.vc_transcript_len(h), dtype=torch.int64, device="cuda")
         ts = []
         for k in range(reps + 2):
@@ -214,8 +217,11 @@ def run_residency(widths, kinds, xd, flush, reps=5):
         out[name + "_device_bytes"] = vc.vc_circuit_bytes(h)
         trs[name] = tr
         vc.vc_circuit_destroy(h)
-    assert bool((trs["device"] == trs["host_values"]).all().item()), "residency changed the transcript"
+    for name in ("host_values", "staged"):
+        assert bool((trs["device"] == trs[name]).all().item()), f"residency {name} changed the transcript"
     out["slowdown"] = out["host_values_prove_ms"] / out["device_prove_ms"]
+    out["staged_slowdown"] = out["staged_prove_ms"] / out["device_prove_ms"]
+    out["staged_link_bytes"] = 8 * (sum(1 << s for s in widths) + sum(1 << s for s in widths[3:]))
     return out
 
 

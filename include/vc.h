@@ -106,8 +106,23 @@ vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, vc_circuit 
  * Everything else stays in device memory and the transcript is unchanged. */
 #define VC_VALUES_IN_HOST_MEMORY 1u
 
-/* vc_circuit_create with residency flags (0 or VC_VALUES_IN_HOST_MEMORY;
- * VC_EINVAL for any other bit; VC_ENOMEM if the pinned host allocation fails). */
+/* With VC_VALUES_STAGED the values of every layer live in page-locked host
+ * memory and the device holds three slots of the widest layer's size that
+ * the layers rotate through (Sec. 5.1.2, copy-once-per-layer: a layer
+ * iteration needs only layers i and i+1 on the device).  A proof evaluates
+ * the circuit layer by layer from the input up, writing each layer to host
+ * memory once as soon as it is computed, then runs the layer iterations in
+ * order 0..d-1, each on its two layers; the next layer is copied in while the
+ * current one is proved (layers 0, 1 and 2 are still on the device after
+ * the evaluation).  Device memory for values: 3 S_max u64 instead of
+ * S_0 + ... + S_d.  Structured wirings only (EXPLICIT: VC_EINVAL); such a
+ * circuit cannot join a batch (vc_batch_create: VC_EINVAL) or use
+ * vc_prove_pergate (VC_EINVAL).  The transcript is unchanged. */
+#define VC_VALUES_STAGED 2u
+
+/* vc_circuit_create with residency flags (0, VC_VALUES_IN_HOST_MEMORY or
+ * VC_VALUES_STAGED; VC_EINVAL for any other value; VC_ENOMEM if the pinned
+ * host allocation fails). */
 vc_status vc_circuit_create_ex(const vc_circuit_desc *desc, int device, uint32_t flags, vc_circuit **out);
 
 /* Free the circuit and its device scratch (synchronises its device).  NULL is

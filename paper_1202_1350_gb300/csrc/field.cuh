@@ -82,28 +82,6 @@ __device__ __forceinline__ u64 f_inv(u64 a)
     return r;
 }
 
-// The same inverse a^(p-2) = a^(2^61 - 3) by an addition chain over the
-// exponents 2^k - 1 (71 squarings and 10 products instead of about 120):
-// x_k = a^(2^k - 1), x_{j+k} = x_j^(2^k) x_k; then a^(2^61 - 3) = x_59^4 a.
-__device__ __forceinline__ u64 f_sqn(u64 x, int n)
-{
-    for (int i = 0; i < n; i++) x = f_mul(x, x);
-    return x;
-}
-__device__ __forceinline__ u64 f_inv_chain(u64 a)
-{
-    const u64 x2 = f_mul(f_mul(a, a), a);
-    const u64 x4 = f_mul(f_sqn(x2, 2), x2);
-    const u64 x8 = f_mul(f_sqn(x4, 4), x4);
-    const u64 x16 = f_mul(f_sqn(x8, 8), x8);
-    const u64 x24 = f_mul(f_sqn(x16, 8), x8);
-    const u64 x26 = f_mul(f_sqn(x24, 2), x2);
-    const u64 x27 = f_mul(f_sqn(x26, 1), a);
-    const u64 x32 = f_mul(f_sqn(x16, 16), x16);
-    const u64 x59 = f_mul(f_sqn(x32, 27), x27);
-    return f_mul(f_sqn(x59, 2), a);
-}
-
 // 1/2 = 2^60 mod p, since 2 * 2^60 = 2^61 = 1.
 #define FP_INV2 0x1000000000000000ull
 

@@ -137,6 +137,7 @@ struct Plan {
     cudaStream_t cap = nullptr;  // private stream: graph capture, creation work
     cudaEvent_t ev_fork = nullptr, ev_tables = nullptr;
     cudaEvent_t ev_params = nullptr;  // a batch's parameter table was copied
+    struct vc_circuit *staged = nullptr;  // a single staged circuit: its own launch sequence
     cudaGraphExec_t exec = nullptr;
     // own_params: the graph's first node is the per-proof parameter write
     // (k_params), whose arguments are set on the instantiated graph before
@@ -203,6 +204,22 @@ struct vc_circuit {
     u32 *d_explicit_layers = nullptr;
     std::vector<u32> round_layer, zmap;
     u32 *d_round_layer = nullptr, *d_zmap = nullptr;
+    // VC_VALUES_STAGED: every layer in page-locked host memory (hV), V[i] =
+    // device slot i mod 3; per-layer task lists of the wave launches (groups
+    // A and B), table builds and launch counters; a copy stream and events
+    std::vector<u64 *> hV;
+    u64 *d_out = nullptr;  // copy of the outputs for the final reduction
+    std::vector<std::vector<std::vector<Task>>> stA, stB;  // [layer][group]
+    std::vector<std::vector<Task *>> d_stA, d_stB;
+    std::vector<std::vector<BuildItem>> stBuild;  // [layer]
+    std::vector<BuildItem *> d_stBuild;
+    std::vector<std::vector<Item>> stEval;  // [layer]: 256-gate blocks of k_eval_layer
+    std::vector<Item *> d_stEval;
+    LayerEval *d_stLev = nullptr;  // one descriptor per layer
+    u32 *d_stctr = nullptr;        // two launch counters per (layer, group)
+    std::vector<u32> stctr_off;    // per layer: its first counter
+    cudaStream_t st_copy = nullptr;
+    std::vector<cudaEvent_t> st_ev;  // per layer: evaluated, written to host, copied in, proved
     std::vector<int> eval_steps;  // >= 0: a segment; < 0: layer -step - 1 alone
     std::vector<u32> seg_maxblock;  // per segment: largest block of its run and tail
     Plan P;                       // this circuit alone (circ = 0)
@@ -229,6 +246,11 @@ struct vc_batch {
 
 vc_status cuda_status(cudaError_t e);
 void init_device_once(int device);
+
+// One proof of circuit c on stream st: its inputs (any memory the runtime can
+// copy from) into the input layer, then its plan (resident or staged) with
+// the transcript written to tr (device memory).  Asynchronous.
+cudaError_t circuit_enqueue_proof(vc_circuit *c, const u64 *inputs, u64 seed, u64 *tr, cudaStream_t st);
 
 // Host-side circuit construction: validation, offsets and the single-circuit
 // plan, sized but not allocated (c->arena_bytes set).  circuit_allocate then

@@ -195,17 +195,6 @@ __global__ void __launch_bounds__(CN_NT) k_coins(const Globals *Gs, int ncirc, c
     if (b < neq) {
         const EqJob J = eqjobs[b];
         const Globals &G = Gs[J.circ];
-        if (J.src == EQ_SRC_INV) {
-            // inverse challenges: each chunk of a sum-check wave recovers its
-            // rounds' values at 1 from those at 0, dividing by the challenge
-            const bool rej = draws_rejected(G);
-            if (G.ichal && threadIdx.x < J.layer) {
-                const u32 c = J.off + threadIdx.x;
-                const u64 r = chal_of(G, rej, c);
-                G.ichal[c] = r ? f_inv_chain(r) : 0;
-            }
-            return;
-        }
         coins_eq(G, draws_rejected(G), J);
         return;
     }

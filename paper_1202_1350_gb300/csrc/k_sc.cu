@@ -24,19 +24,6 @@
 // Arithmetic is lazy: table values stay in W = [0, 2^61 + 8), products
 // accumulate exactly in 128 bits and are reduced once per round per thread;
 // only transcript entries are made canonical.
-//
-// Values at t = 1 are not summed pair by pair.  A chunk's rounds are chained
-// by the sum-check identity (Sec. 3.1: the round polynomial at the challenge
-// equals the next round's values at 0 and 1 summed), which holds for the
-// chunk's own sub-sums: with H_k the chunk's sum for local round k,
-//   PROD: (1 - r_k) H_k(0) + r_k H_k(1) = c0_{k+1} H_{k+1}(0) + c1_{k+1} H_{k+1}(1)
-//         (c0, c1: the next round's linear factor, which weights the two halves),
-//   GEN:  (1 - r_k) H_k(0) + r_k H_k(1) - r_k (1 - r_k) H_k(2) = H_{k+1}(0) + H_{k+1}(1)
-//         (H_k(2): the leading coefficient).
-// So each chunk sums every round's value at 0 (and the leading coefficient),
-// sums both values only for its last round and for a round whose challenge is
-// zero, and recovers the other values at 1 from the last round backwards,
-// dividing by r_k (inverse challenges come with the coins).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -106,9 +93,6 @@ __device__ __forceinline__ u64 warp_sum32(u64 (&v)[32])
 
 struct ProdSmem {
     u32 r[32][2];
-    u32 dmask;  // local rounds whose values at 1 are summed directly
-    u64 hs[64];  // canonical per-round sums H_k(0), H_k(1) of the chunk
-    u64 rc[32][4];  // per local round: r_k, 1/r_k, and the next round's factors c0, c1
     u64 Q[64];
     u64 E[256];
     u64 lvl[WV_NT / 32];
@@ -118,9 +102,6 @@ struct ProdSmem {
 
 struct GenSmem {
     u32 r[32][2];
-    u32 dmask;  // local rounds whose values at 1 are summed directly
-    u64 cs[96];  // canonical per-round sums H_k(0), H_k(1), H_k(2) of the chunk
-    u64 rc[32][2];  // per local round: r_k, 1/r_k
     u64 lvl[3][WV_NT / 32];
     u64 w[WV_NT / 32][40];
     u64 hs[9][WV_NT];  // per-thread sums of in-register rounds 2..4 (kept out of registers)
@@ -183,7 +164,7 @@ __device__ __forceinline__ void prod_round_sum(u64 c0, u64 c1, u32 kk, u64 *out)
 // warp 0 after one exchange through shared memory.  The active thread of a
 // pair contributes E_k(y) u0 and E_k(y) u1; the per-warp sums of round k go
 // to sm.w[warp][2k..2k+1] (CTA-level rounds: warp 0's row, zeros elsewhere).
-__device__ __forceinline__ void prod_cross(u64 uv, u32 off, u32 tid, u32 na, u32 nr, ProdSmem &sm, u32 eoff0, u32 dm)
+__device__ __forceinline__ void prod_cross(u64 uv, u32 off, u32 tid, u32 na, u32 nr, ProdSmem &sm, u32 eoff0)
 {
     const u32 lane = tid & 31, warp = tid >> 5;
     // rolled: one copy of the round body keeps the kernel small
@@ -197,7 +178,7 @@ __device__ __forceinline__ void prod_cross(u64 uv, u32 off, u32 tid, u32 na, u32
                 const u32 y = tid >> (kk + 1);
                 const u64 w = sm.E[eoff0 - (1u << (nr - k)) + y];
                 c0 = wmul(w, uv);
-                if ((dm >> k) & 1) c1 = wmul(w, u1);
+                c1 = wmul(w, u1);
                 uv = wfold(uv, u1, sm.r[k][0], sm.r[k][1]);
             }
             prod_round_sum(c0, c1, kk, &sm.w[warp][2 * k]);
@@ -221,7 +202,7 @@ __device__ __forceinline__ void prod_cross(u64 uv, u32 off, u32 tid, u32 na, u32
                     const u32 y = t >> (kk + 1);
                     const u64 w = sm.E[eoff0 - (1u << (nr - k)) + y];
                     c0 = wmul(w, uv);
-                    if ((dm >> k) & 1) c1 = wmul(w, u1);
+                    c1 = wmul(w, u1);
                     uv = wfold(uv, u1, sm.r[k][0], sm.r[k][1]);
                 }
                 prod_round_sum(c0, c1, kk - 5, &sm.w[0][2 * k]);
@@ -233,7 +214,6 @@ __device__ __forceinline__ void prod_cross(u64 uv, u32 off, u32 tid, u32 na, u32
 
 // Rounds 0..3 of one run of 16 entries (run `sub` of the thread's 2^e):
 // pair weights Q_k(q), q = pair index + (sub << (3 - k)).
-template <bool H1>
 __device__ __forceinline__ u64 prod_run16(u64 (&u)[16], u32 sub, u32 e, const ProdSmem &sm, u64 (&h)[12])
 {
 #pragma unroll
@@ -251,10 +231,10 @@ __device__ __forceinline__ u64 prod_run16(u64 (&u)[16], u32 sub, u32 e, const Pr
             const u64 u0 = u[2 * q], u1 = u[2 * q + 1];
             if (q & 1) {
                 mac(b0, w, u0);
-                if (H1) mac(b1, w, u1);
+                mac(b1, w, u1);
             } else {
                 mac(a0, w, u0);
-                if (H1) mac(a1, w, u1);
+                mac(a1, w, u1);
             }
             u[q] = wfold(u0, u1, rr0, rr1);
         }
@@ -266,7 +246,6 @@ __device__ __forceinline__ u64 prod_run16(u64 (&u)[16], u32 sub, u32 e, const Pr
 
 // In-register rounds for e in 4..6: runs of 16, then rounds 4 and 5 on the
 // runs' folded values.
-template <bool H1>
 __device__ __forceinline__ u64 prod_regs_runs(const u64 *src, u32 e, bool ext, const ProdSmem &sm, u64 (&h)[12])
 {
     const u32 nruns = 1u << (e - 4);
@@ -284,13 +263,13 @@ __device__ __forceinline__ u64 prod_regs_runs(const u64 *src, u32 e, bool ext, c
             u[2 * q] = t.x;
             u[2 * q + 1] = t.y;
         }
-        const u64 fs = prod_run16<H1>(u, sub, e, sm, h);
+        const u64 fs = prod_run16(u, sub, e, sm, h);
         if (nruns == 1) {
             uv = fs;
         } else if (sub & 1) {
             const u64 w = sm.Q[q4 + (sub >> 1)];
             h[8] = wred(h[8] + wmul(w, f0));
-            if (H1) h[9] = wred(h[9] + wmul(w, fs));
+            h[9] = wred(h[9] + wmul(w, fs));
             const u64 g = wfold(f0, fs, sm.r[4][0], sm.r[4][1]);
             if (nruns == 2) {
                 uv = g;
@@ -299,7 +278,7 @@ __device__ __forceinline__ u64 prod_regs_runs(const u64 *src, u32 e, bool ext, c
             } else {
                 const u64 w5 = sm.Q[q5];
                 h[10] = wmul(w5, g0);
-                if (H1) h[11] = wmul(w5, g);
+                h[11] = wmul(w5, g);
                 uv = wfold(g0, g, sm.r[5][0], sm.r[5][1]);
             }
         } else {
@@ -316,21 +295,7 @@ __device__ void prod_chunk(const Globals &G, const ProdWave &W, u32 chunk, ProdS
     const u32 nr = W.nr, e = W.e;
     const u32 na = 1u << (nr - e);
     const u64 base = (u64)chunk << nr;
-    if (tid < nr) {
-        const u64 r = G.chal[W.chal_off + tid];
-        limbs31(r, sm.r[tid][0], sm.r[tid][1]);
-        sm.rc[tid][0] = r;
-        sm.rc[tid][1] = G.ichal[W.chal_off + tid];
-        if (tid + 1 < nr) {
-            sm.rc[tid][2] = W.lc[2 * (tid + 1)];
-            sm.rc[tid][3] = W.lc[2 * (tid + 1) + 1];
-        }
-    }
-    if (tid < 32) {  // the last local round and zero challenges: values at 1 summed directly
-        const bool direct = tid < nr && (tid == nr - 1 || G.chal[W.chal_off + tid] == 0);
-        const u32 m = __ballot_sync(0xffffffffu, direct);
-        if (tid == 0) sm.dmask = m;
-    }
+    if (tid < nr) limbs31(G.chal[W.chal_off + tid], sm.r[tid][0], sm.r[tid][1]);
     const u64 *blk = W.wblk;
     const u32 qsize = (1u << e) - 1;
     const u32 kb = e ? e - 1 : 0;
@@ -343,12 +308,6 @@ __device__ void prod_chunk(const Globals &G, const ProdWave &W, u32 chunk, ProdS
         sm.echunk = f_mul(olo[chunk & ((1u << W.ho) - 1)], ohi[chunk >> W.ho]);
     }
     __syncthreads();
-    // in-register rounds: values at 1 summed either in none (the usual case:
-    // the last local round is a cross round) or, if one of their challenges
-    // is zero, in all of them
-    const u32 rmask = e ? (1u << e) - 1 : 0u;
-    const bool regs_h1 = (sm.dmask & rmask) != 0;
-    const u32 dm = sm.dmask | (regs_h1 ? rmask : 0u);
     const u32 eoff0 = 1u << (nr - kb);
     u64 uv = 0;
     if (e > 0) {
@@ -357,8 +316,7 @@ __device__ void prod_chunk(const Globals &G, const ProdWave &W, u32 chunk, ProdS
         for (int i = 0; i < 12; i++) h[i] = 0;
         if (tid < na) {
             const u64 *src = W.in + base + ((u64)tid << e);
-            uv = regs_h1 ? prod_regs_runs<true>(src, e, W.r0 == 0, sm, h)
-                         : prod_regs_runs<false>(src, e, W.r0 == 0, sm, h);
+            uv = prod_regs_runs(src, e, W.r0 == 0, sm, h);
             const u64 T = sm.E[tid];  // E_{e-1}(tid): weight of the chunk bits above the thread's run
 #pragma unroll
             for (int i = 0; i < 12; i++) h[i] = wmul(T, h[i]);
@@ -371,28 +329,12 @@ __device__ void prod_chunk(const Globals &G, const ProdWave &W, u32 chunk, ProdS
     } else if (tid < na) {
         uv = ld_in(W.in + base + tid, W.r0 == 0);
     }
-    prod_cross(uv, e, tid, na, nr, sm, eoff0, dm);
-    __syncthreads();
-    if (tid < 2 * nr) sm.hs[tid] = wcanon(wred(sm.w[0][tid] + sm.w[1][tid] + sm.w[2][tid] + sm.w[3][tid]));
-    __syncthreads();
-    // H_k(1) = (c0_{k+1} H_{k+1}(0) + c1_{k+1} H_{k+1}(1) - (1 - r_k) H_k(0)) / r_k
-    //        = alpha_k H_{k+1}(1) + beta_k: the coefficients a round a thread
-    // (in place of c0, c1), then the chain from the last round down
-    if (tid + 1 < nr && !((dm >> tid) & 1)) {
-        const u32 k = tid;
-        const u64 ir = sm.rc[k][1];
-        const u64 beta = f_mul(f_sub(f_mul(sm.rc[k][2], sm.hs[2 * k + 2]), f_mul(f_sub(1, sm.rc[k][0]), sm.hs[2 * k])), ir);
-        sm.rc[k][2] = f_mul(sm.rc[k][3], ir);
-        sm.rc[k][3] = beta;
-    }
-    __syncthreads();
-    if (tid == 0)
-        for (int k = (int)nr - 2; k >= 0; k--)
-            if (!((dm >> k) & 1)) sm.hs[2 * k + 1] = f_add(f_mul(sm.rc[k][2], sm.hs[2 * k + 3]), sm.rc[k][3]);
+    prod_cross(uv, e, tid, na, nr, sm, eoff0);
     __syncthreads();
     if (tid < 2 * nr) {
+        const u64 sum = wred(sm.w[0][tid] + sm.w[1][tid] + sm.w[2][tid] + sm.w[3][tid]);
         const u32 k = tid >> 1, t = tid & 1;
-        W.part[((u64)k * W.nchunks + chunk) * 2 + t] = wmul(sm.hs[tid], sm.echunk);
+        W.part[((u64)k * W.nchunks + chunk) * 2 + t] = wmul(sum, sm.echunk);
     }
     if (!(W.flags & WF_LAST) && tid == 0) W.out[chunk] = sm.lvl[0];
 }
@@ -439,11 +381,11 @@ __device__ __forceinline__ void gen_load(const GenWave &W, u64 x0, bool hasB, u6
 // 2 c1 - c0 + 2 c2 (B is linear in t); then the folds, which share the
 // differences P1 - P0, V1 - V0, B1 - B0 (lazy, below 2^62.6).
 __device__ __forceinline__ void gen_pair(u64 p0, u64 p1, u64 v0, u64 v1, u64 b0, u64 b1, u32 rr0, u32 rr1,
-                                         bool need1, u64 &c0, u64 &c1, u64 &c2, u64 &pn, u64 &vn, u64 &bn)
+                                         u64 &c0, u64 &c1, u64 &c2, u64 &pn, u64 &vn, u64 &bn)
 {
     const u64 dp = p1 + (2 * FP_P) - p0, dv = v1 + (2 * FP_P) - v0, db = b1 + (2 * FP_P) - b0;
     c0 = wred(wmul(p0, v0) + b0);
-    c1 = need1 ? wred(wmul(p1, v1) + b1) : 0;
+    c1 = wred(wmul(p1, v1) + b1);
     c2 = wmul(wred(dp), wred(dv));
     pn = wlin1(p0, dp, rr0, rr1);
     vn = wlin1(v0, dv, rr0, rr1);
@@ -453,19 +395,19 @@ __device__ __forceinline__ void gen_pair(u64 p0, u64 p1, u64 v0, u64 v1, u64 b0,
 // Round k on two folded triples held by one thread, summed into the
 // thread's shared-memory slots hs[3j..3j+2].
 __device__ __forceinline__ void gen_pair_acc(u64 p0, u64 p1, u64 v0, u64 v1, u64 b0, u64 b1, u32 rr0, u32 rr1,
-                                             bool need1, GenSmem &sm, u32 j, u64 &pn, u64 &vn, u64 &bn)
+                                             GenSmem &sm, u32 j, u64 &pn, u64 &vn, u64 &bn)
 {
     u64 c0, c1, c2;
-    gen_pair(p0, p1, v0, v1, b0, b1, rr0, rr1, need1, c0, c1, c2, pn, vn, bn);
+    gen_pair(p0, p1, v0, v1, b0, b1, rr0, rr1, c0, c1, c2, pn, vn, bn);
     const u32 t = threadIdx.x;
     sm.hs[3 * j][t] = wred(sm.hs[3 * j][t] + c0);
-    if (need1) sm.hs[3 * j + 1][t] = wred(sm.hs[3 * j + 1][t] + c1);
+    sm.hs[3 * j + 1][t] = wred(sm.hs[3 * j + 1][t] + c1);
     sm.hs[3 * j + 2][t] = wred(sm.hs[3 * j + 2][t] + c2);
 }
 
 // Rounds 0..R-1 of N = 2^R entries held by one thread; adds to h[0..3R) and
 // leaves the folded values in p[0], v[0], b[0].
-template <int R, bool H1>
+template <int R>
 __device__ __forceinline__ void gen_regs(u64 (&p)[1 << R], u64 (&v)[1 << R], u64 (&b)[1 << R], const GenSmem &sm,
                                          u64 (&h)[15])
 {
@@ -482,12 +424,10 @@ __device__ __forceinline__ void gen_regs(u64 (&p)[1 << R], u64 (&v)[1 << R], u64
             const u64 b0 = b[2 * q], b1 = b[2 * q + 1];
             const u64 dp = p1 + (2 * FP_P) - p0, dv = v1 + (2 * FP_P) - v0, db = b1 + (2 * FP_P) - b0;
             mac(a0, p0, v0);
-            if (H1) {
-                mac(a1, p1, v1);
-                acc_add(a1, b1);
-            }
+            mac(a1, p1, v1);
             mac(a2, wred(dp), wred(dv));  // leading coefficient (see gen_pair)
             acc_add(a0, b0);
+            acc_add(a1, b1);
             p[q] = wlin1(p0, dp, rr0, rr1);
             v[q] = wlin1(v0, dv, rr0, rr1);
             b[q] = wlin1(b0, db, rr0, rr1);
@@ -507,7 +447,6 @@ __device__ __forceinline__ void gen_regs(u64 (&p)[1 << R], u64 (&v)[1 << R], u64
 // is left out here: it multiplies the message of every later round of the
 // instance and is applied in the final reduction.  h[2] collects the c2 sum
 // with its sign flipped (restored by the caller).
-template <bool H1>
 __device__ __forceinline__ void tree2_run(const Globals &G, const GenWave &W, u64 x0, const GenSmem &sm,
                                           u64 (&h)[15], u64 &pn, u64 &vn, u64 &bn)
 {
@@ -529,7 +468,7 @@ __device__ __forceinline__ void tree2_run(const Globals &G, const GenWave &W, u6
     const u64 v0 = wlin1(va.x, da, a0, a1), v1 = wlin1(vb.x, db, a0, a1);
     const u64 b0 = wmul(wa, va.y), b1 = wmul(wb, vb.y);
     u64 c0, c1, c2;
-    gen_pair(wa, wb, v0, v1, b0, b1, sm.r[1][0], sm.r[1][1], H1, c0, c1, c2, pn, vn, bn);
+    gen_pair(wa, wb, v0, v1, b0, b1, sm.r[1][0], sm.r[1][1], c0, c1, c2, pn, vn, bn);
     h[3] = wred(h[3] + c0);
     h[4] = wred(h[4] + c1);
     h[5] = wred(h[5] + c2);
@@ -537,7 +476,6 @@ __device__ __forceinline__ void tree2_run(const Globals &G, const GenWave &W, u6
 
 // Rounds 0 and 1 of the first wave of a SQUARE phase-2 instance on the 4
 // entries at x0: P[x] = eq(r_P, x) V[x] and B = 0, so the B terms drop out.
-template <bool H1>
 __device__ __forceinline__ void sq2_run(const Globals &G, const GenWave &W, u64 x0, const GenSmem &sm, u64 (&h)[15],
                                         u64 &pn, u64 &vn)
 {
@@ -559,7 +497,7 @@ __device__ __forceinline__ void sq2_run(const Globals &G, const GenWave &W, u64 
             const u64 p0 = p[2 * q], p1 = p[2 * q + 1], v0 = v[2 * q], v1 = v[2 * q + 1];
             const u64 dp = p1 + (2 * FP_P) - p0, dv = v1 + (2 * FP_P) - v0;
             mac(a0, p0, v0);
-            if (H1) mac(a1, p1, v1);
+            mac(a1, p1, v1);
             mac(a2, wred(dp), wred(dv));
             p[q] = wlin1(p0, dp, rr0, rr1);
             v[q] = wlin1(v0, dv, rr0, rr1);
@@ -574,7 +512,6 @@ __device__ __forceinline__ void sq2_run(const Globals &G, const GenWave &W, u64 
 
 // In-register rounds for e in 3..5: runs of 4 entries (rounds 0, 1), then
 // rounds 2.. on the runs' folded triples, combined like a binary counter.
-template <bool H1>
 __device__ __forceinline__ void gen_regs_runs(const Globals &G, const GenWave &W, u64 x0, u32 e, bool hasB,
                                               GenSmem &sm, u64 (&h)[15], u64 &pv, u64 &vv, u64 &bv)
 {
@@ -596,14 +533,14 @@ __device__ __forceinline__ void gen_regs_runs(const Globals &G, const GenWave &W
             }
         }
         if (tree2) {
-            tree2_run<H1>(G, W, x0 + 4 * sub, sm, h, tp, tv, tb);
+            tree2_run(G, W, x0 + 4 * sub, sm, h, tp, tv, tb);
         } else if (W.src == GS_SQ2) {
-            sq2_run<H1>(G, W, x0 + 4 * sub, sm, h, tp, tv);
+            sq2_run(G, W, x0 + 4 * sub, sm, h, tp, tv);
             tb = 0;
         } else {
             u64 p[4], v[4], b[4];
             gen_load<4>(W, x0 + 4 * sub, hasB, p, v, b);
-            gen_regs<2, H1>(p, v, b, sm, h);
+            gen_regs<2>(p, v, b, sm, h);
             tp = p[0];
             tv = v[0];
             tb = b[0];
@@ -612,19 +549,19 @@ __device__ __forceinline__ void gen_regs_runs(const Globals &G, const GenWave &W
             p0 = tp, v0 = tv, b0 = tb;
             continue;
         }
-        gen_pair_acc(p0, tp, v0, tv, b0, tb, sm.r[2][0], sm.r[2][1], H1, sm, 0, tp, tv, tb);
+        gen_pair_acc(p0, tp, v0, tv, b0, tb, sm.r[2][0], sm.r[2][1], sm, 0, tp, tv, tb);
         if (nruns == 2) continue;
         if (!(sub & 2)) {
             p1 = tp, v1 = tv, b1 = tb;
             continue;
         }
-        gen_pair_acc(p1, tp, v1, tv, b1, tb, sm.r[3][0], sm.r[3][1], H1, sm, 1, tp, tv, tb);
+        gen_pair_acc(p1, tp, v1, tv, b1, tb, sm.r[3][0], sm.r[3][1], sm, 1, tp, tv, tb);
         if (nruns == 4) continue;
         if (!(sub & 4)) {
             p2 = tp, v2 = tv, b2 = tb;
             continue;
         }
-        gen_pair_acc(p2, tp, v2, tv, b2, tb, sm.r[4][0], sm.r[4][1], H1, sm, 2, tp, tv, tb);
+        gen_pair_acc(p2, tp, v2, tv, b2, tb, sm.r[4][0], sm.r[4][1], sm, 2, tp, tv, tb);
     }
     pv = tp;
     vv = tv;
@@ -657,8 +594,7 @@ __device__ __forceinline__ void gen_round_sum(u64 c0, u64 c1, u64 c2, u32 kk, u6
 // prod_cross: the first thread of each pair keeps the folded values).  The
 // per-warp sums of round k go to sm.w[warp][3k..3k+2] (CTA-level rounds: warp
 // 0's row, zeros in the other rows).
-__device__ __forceinline__ void gen_cross(u64 &p, u64 &v, u64 &b, u32 off, u32 tid, u32 na, u32 nr, GenSmem &sm,
-                                          u32 dm)
+__device__ __forceinline__ void gen_cross(u64 &p, u64 &v, u64 &b, u32 off, u32 tid, u32 na, u32 nr, GenSmem &sm)
 {
     const u32 lane = tid & 31, warp = tid >> 5;
     // rolled: one copy of the round body keeps the kernel small
@@ -672,7 +608,7 @@ __device__ __forceinline__ void gen_cross(u64 &p, u64 &v, u64 &b, u32 off, u32 t
             const u64 b1 = __shfl_down_sync(0xffffffffu, b, d);
             u64 c0 = 0, c1 = 0, c2 = 0;
             if ((tid & ((2u << kk) - 1)) == 0 && tid < na)
-                gen_pair(p, p1, v, v1, b, b1, sm.r[k][0], sm.r[k][1], (dm >> k) & 1, c0, c1, c2, p, v, b);
+                gen_pair(p, p1, v, v1, b, b1, sm.r[k][0], sm.r[k][1], c0, c1, c2, p, v, b);
             gen_round_sum(c0, c1, c2, kk, &sm.w[warp][3 * k]);
         }
     }
@@ -700,7 +636,7 @@ __device__ __forceinline__ void gen_cross(u64 &p, u64 &v, u64 &b, u32 off, u32 t
                 const u32 t = lane << 5;
                 u64 c0 = 0, c1 = 0, c2 = 0;
                 if ((t & ((2u << kk) - 1)) == 0 && t < na)
-                    gen_pair(p, p1, v, v1, b, b1, sm.r[k][0], sm.r[k][1], (dm >> k) & 1, c0, c1, c2, p, v, b);
+                    gen_pair(p, p1, v, v1, b, b1, sm.r[k][0], sm.r[k][1], c0, c1, c2, p, v, b);
                 gen_round_sum(c0, c1, c2, kk - 5, &sm.w[0][3 * k]);
             }
         }
@@ -720,28 +656,8 @@ __device__ void gen_chunk(const Globals &G, const GenWave &W, u32 chunk, GenSmem
     const u32 na = 1u << (nr - e);
     const u64 base = (u64)chunk << nr;
     const bool hasB = (W.flags & WF_HASB) != 0;
-    if (tid < nr) {
-        const u64 r = G.chal[W.chal_off + tid];
-        limbs31(r, sm.r[tid][0], sm.r[tid][1]);
-        sm.rc[tid][0] = r;
-        sm.rc[tid][1] = G.ichal[W.chal_off + tid];
-    }
-    if (tid < 32) {
-        // values at 1 summed directly: the last local round, zero challenges,
-        // and round 0 of a TREE phase-2 first wave (P and B vanish at odd
-        // entries: its value at 1 is 0, and its folded tables leave out 1 - r_0)
-        const bool direct = tid < nr && (tid == nr - 1 || G.chal[W.chal_off + tid] == 0 ||
-                                         (tid == 0 && W.src == GS_TREE2));
-        const u32 m = __ballot_sync(0xffffffffu, direct);
-        if (tid == 0) sm.dmask = m;
-    }
+    if (tid < nr) limbs31(G.chal[W.chal_off + tid], sm.r[tid][0], sm.r[tid][1]);
     __syncthreads();
-    // in-register rounds: values at 1 summed in none of them, or in all if
-    // one of their challenges is zero (round 0 of a TREE phase-2 first wave
-    // has value 0 at 1 by construction either way)
-    const u32 rmask = e ? (((1u << e) - 1) & ~(W.src == GS_TREE2 ? 1u : 0u)) : 0u;
-    const bool regs_h1 = (sm.dmask & rmask) != 0;
-    const u32 dm = sm.dmask | (regs_h1 ? rmask : 0u);
     u64 pv = 0, vv = 0, bv = 0;
     if (e > 0) {
         u64 h[15];
@@ -749,10 +665,7 @@ __device__ void gen_chunk(const Globals &G, const GenWave &W, u32 chunk, GenSmem
         for (int i = 0; i < 15; i++) h[i] = 0;
         if (tid < na) {
             const u64 x0 = base + ((u64)tid << e);
-            if (regs_h1)
-                gen_regs_runs<true>(G, W, x0, e, hasB, sm, h, pv, vv, bv);
-            else
-                gen_regs_runs<false>(G, W, x0, e, hasB, sm, h, pv, vv, bv);
+            gen_regs_runs(G, W, x0, e, hasB, sm, h, pv, vv, bv);
         }
         u64 h16[16];
 #pragma unroll
@@ -774,27 +687,12 @@ __device__ void gen_chunk(const Globals &G, const GenWave &W, u32 chunk, GenSmem
             bv = hasB ? ld_in(W.inB + x, ext) : 0;
         }
     }
-    gen_cross(pv, vv, bv, e, tid, na, nr, sm, dm);
-    __syncthreads();
-    if (tid < 3 * nr) sm.cs[tid] = wcanon(wred(sm.w[0][tid] + sm.w[1][tid] + sm.w[2][tid] + sm.w[3][tid]));
-    __syncthreads();
-    // H_k(1) = (H_{k+1}(0) + H_{k+1}(1) - (1 - r_k) H_k(0) + r_k (1 - r_k) H_k(2)) / r_k
-    //        = H_{k+1}(1) / r_k + beta_k: beta a round a thread (in place of
-    // r_k), then the chain from the last round down
-    if (tid + 1 < nr && !((dm >> tid) & 1)) {
-        const u32 k = tid;
-        const u64 r = sm.rc[k][0], omr = f_sub(1, r);
-        const u64 t = f_add(f_sub(sm.cs[3 * k + 3], f_mul(omr, sm.cs[3 * k])), f_mul(f_mul(r, omr), sm.cs[3 * k + 2]));
-        sm.rc[k][0] = f_mul(t, sm.rc[k][1]);
-    }
-    __syncthreads();
-    if (tid == 0)
-        for (int k = (int)nr - 2; k >= 0; k--)
-            if (!((dm >> k) & 1)) sm.cs[3 * k + 1] = f_add(f_mul(sm.rc[k][1], sm.cs[3 * k + 4]), sm.rc[k][0]);
+    gen_cross(pv, vv, bv, e, tid, na, nr, sm);
     __syncthreads();
     if (tid < 3 * nr) {
+        const u64 sum = wred(sm.w[0][tid] + sm.w[1][tid] + sm.w[2][tid] + sm.w[3][tid]);
         const u32 k = tid / 3, t = tid % 3;
-        W.part[((u64)k * W.nchunks + chunk) * 3 + t] = sm.cs[tid];
+        W.part[((u64)k * W.nchunks + chunk) * 3 + t] = sum;
     }
     if (!(W.flags & WF_LAST) && tid == 0) {
         W.outP[chunk] = sm.lvl[0][0];
@@ -1187,7 +1085,7 @@ __global__ void __launch_bounds__(256) k_final(Globals *Gs, const RoundRef *roun
         Globals &G = Gs[outs[j]];
         if (threadIdx.x == 0) G.in = nullptr;
         const u64 n = G.S0;
-        const u64 *__restrict__ src = G.layers[0].V;
+        const u64 *__restrict__ src = G.out_src;
         u64 *__restrict__ dst = G.tr;
         for (u64 x = threadIdx.x; x < n; x += blockDim.x) dst[x] = src[x];
     }

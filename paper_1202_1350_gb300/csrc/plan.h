@@ -125,7 +125,6 @@ struct ProdWave {
     u32 no, ho;        // coordinates beyond the chunk (r0+nr..n-1) and their split
     u32 chal_off;      // challenge of local round k: chal[chal_off + k]
     u32 pad;
-    const u64 *lc;     // factors c0, c1 of the instance's round r0 (SciDev::Lc + 2 r0)
     const u64 *in;     // entries of this wave's table
     u64 *out;          // one folded value per chunk (unused on the last wave)
     u64 *wblk;         // weight block: Q, E, outer lo, outer hi
@@ -217,7 +216,6 @@ struct Globals {
     u32 d;
     u32 nchal;
     u64 *chal;        // nchal challenges
-    u64 *ichal;       // their inverses (0 for a zero challenge); NULL: not formed (verifier)
     u64 *pts;         // z_0 .. z_d
     u64 *scal;        // per-layer scalars (SCAL_*)
     u64 *tr;          // transcript (device)
@@ -228,6 +226,8 @@ struct Globals {
     u32 nz;
     u32 zd_off;       // z_d in pts[]
     u64 S0;           // outputs
+    const u64 *out_src;  // where the final reduction reads the outputs (layer 0, or a
+                         // copy of it when the layer values rotate through device slots)
     const u64 *in;    // this proof's inputs when the first evaluation launch reads them
                       // in place (it also writes the input layer's values); set by
                       // k_params, cleared by k_final; NULL: the inputs are in layer d
@@ -291,10 +291,7 @@ struct GatherChunk {
 // ---- launch entry points (implemented in the .cu files) -------------------------
 // An eq table to build and where its point comes from: challenges
 // chal[off ..] (EQ_SRC_CHAL) or the point z_layer (EQ_SRC_Z).
-// EQ_SRC_INV: no table; the job inverts challenges chal[off .. off + layer)
-// into ichal (at most INV_PER_JOB of them, a thread each).
-enum : u32 { EQ_SRC_CHAL = 0, EQ_SRC_Z = 1, EQ_SRC_INV = 2 };
-#define INV_PER_JOB 256u
+enum : u32 { EQ_SRC_CHAL = 0, EQ_SRC_Z = 1 };
 struct EqJob {
     EqTab t;
     u32 circ;

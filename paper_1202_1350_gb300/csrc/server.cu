@@ -47,6 +47,8 @@ struct ShapeKey {
 
 struct Shape {
     u64 bytes = 0;                     // device bytes of one circuit of this shape
+    bool staged = false;               // resident values exceed the cap: values staged through
+                                       // host memory (copy-once-per-layer), jobs run alone
     u64 tr_len = 0, n_in = 0;
     std::vector<vc_circuit *> idle;    // allocated, not in use
     u32 live = 0;                      // allocated (idle or in use)
@@ -87,7 +89,8 @@ struct Slot {
 }  // namespace
 
 struct vc_server;
-static vc_status server_prepare(const vc_server *s, const vc_circuit_desc *desc, vc_circuit **out);
+static vc_status server_prepare(const vc_server *s, const vc_circuit_desc *desc, vc_circuit **out,
+                                u32 flags = 0);
 
 struct vc_server {
     int device = 0;
@@ -143,7 +146,7 @@ Acq acquire(vc_server *s, Job *j, vc_circuit **out)
     d.log_width = j->key.widths.data();
     d.wiring = j->key.kinds.data();
     vc_circuit *c = nullptr;
-    if (server_prepare(s, &d, &c) != VC_OK) return ACQ_FAIL;
+    if (server_prepare(s, &d, &c, sh.staged ? VC_VALUES_STAGED : 0u) != VC_OK) return ACQ_FAIL;
     if (circuit_allocate(c) != VC_OK) {
         circuit_free(c);
         return ACQ_FAIL;
@@ -169,9 +172,30 @@ bool ensure_pinned(T *&p, size_t &cap, size_t n)
     return true;
 }
 
+// A job whose values are staged through host memory: its circuit's own
+// launch sequence on the slot's stream (it cannot be merged with others).
+vc_status launch_staged(Slot &sl)
+{
+    Job *j = sl.jobs[0];
+    vc_circuit *c = j->c;
+    if (!j->tr_dev) {
+        j->stage_off = 0;
+        if (!ensure_pinned(sl.h_stage, sl.stage_cap, (size_t)j->shape->tr_len)) return VC_ENOMEM;
+    }
+    if (circuit_enqueue_proof(c, j->inputs, j->seed, j->tr_dev ? j->transcript : c->d_tr, sl.st) != cudaSuccess)
+        return VC_ECUDA;
+    if (!j->tr_dev && cudaMemcpyAsync(sl.h_stage, c->d_tr, j->shape->tr_len * sizeof(u64), cudaMemcpyDeviceToHost,
+                                      sl.st) != cudaSuccess)
+        return VC_ECUDA;
+    if (queue_status(c, sl.st) != cudaSuccess) return VC_ECUDA;
+    if (cudaEventRecord(sl.done, sl.st) != cudaSuccess) return VC_ECUDA;
+    return cudaGetLastError() == cudaSuccess ? VC_OK : VC_ECUDA;
+}
+
 // Issue one launch set for the slot's jobs (circuits assigned).
 vc_status launch(vc_server *s, Slot &sl)
 {
+    if (sl.jobs.size() == 1 && sl.jobs[0]->shape->staged) return launch_staged(sl);
     std::vector<vc_circuit *> cs;
     for (Job *j : sl.jobs) cs.push_back(j->c);
     // merged plan; the slot's streams and events are kept across sets
@@ -289,6 +313,8 @@ void worker_main(vc_server *s)
             const u64 t = now_ns();
             while (!s->pending.empty() && free_slot->jobs.size() < s->max_batch) {
                 Job *j = s->pending.front();
+                // a job with staged values runs alone in its slot
+                if (!free_slot->jobs.empty() && (j->shape->staged || free_slot->jobs[0]->shape->staged)) break;
                 vc_circuit *c = nullptr;
                 const Acq a = acquire(s, j, &c);
                 if (a == ACQ_WAIT && (any_busy || !free_slot->jobs.empty())) break;  // memory frees up later
@@ -304,6 +330,7 @@ void worker_main(vc_server *s)
                 j->c = c;
                 j->t_start = t;
                 free_slot->jobs.push_back(j);
+                if (j->shape->staged) break;
             }
             if (!free_slot->jobs.empty()) {
                 s->in_flight += (u32)free_slot->jobs.size();
@@ -333,12 +360,12 @@ void worker_main(vc_server *s)
 
 // A circuit for the server: its shape's tile shapes, with the server's split
 // threshold if one was configured.
-static vc_status server_prepare(const vc_server *s, const vc_circuit_desc *desc, vc_circuit **out)
+static vc_status server_prepare(const vc_server *s, const vc_circuit_desc *desc, vc_circuit **out, u32 flags)
 {
-    if (!s->pr_split) return circuit_prepare(desc, s->device, out);
+    if (!s->pr_split) return circuit_prepare(desc, s->device, out, nullptr, flags);
     PlanConfig f = shape_config(desc);
     f.pr_split = s->pr_split;
-    return circuit_prepare(desc, s->device, out, &f);
+    return circuit_prepare(desc, s->device, out, &f, flags);
 }
 
 extern "C" vc_status vc_server_create(int device, const vc_server_config *cfg, vc_server **out)
@@ -428,6 +455,16 @@ extern "C" vc_status vc_server_submit(vc_server *s, const vc_circuit_desc *desc,
         sh.tr_len = c->tr_len;
         sh.n_in = u64(1) << c->s[c->d];
         circuit_free(c);  // host-only object
+        if (sh.bytes > s->cap) {
+            // too large to keep its values on the device: stage them through
+            // host memory a layer at a time (Sec. 5.1.2) if that fits
+            vc_circuit *cs = nullptr;
+            if (server_prepare(s, desc, &cs, VC_VALUES_STAGED) == VC_OK) {
+                sh.bytes = cs->arena_bytes;
+                sh.staged = true;
+                circuit_free(cs);
+            }
+        }
         it = s->shapes.emplace(key, sh).first;
     }
     if (it->second.bytes > s->cap) return VC_EBUSY;

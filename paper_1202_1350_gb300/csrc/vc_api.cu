@@ -103,7 +103,9 @@ static void plan_eval(vc_circuit *c)
     c->eval_steps.clear();
     c->seg_maxblock.clear();
     int i = (int)c->d - 1;
-    auto local = [&](int j) { return c->kind[j] != W_MATMULT && c->kind[j] != W_EXPLICIT; };
+    // staged values: every layer alone (its slot is reused three layers on)
+    const bool staged = (c->flags & VC_VALUES_STAGED) != 0;
+    auto local = [&](int j) { return !staged && c->kind[j] != W_MATMULT && c->kind[j] != W_EXPLICIT; };
     while (i >= 0) {
         if (!local(i)) {
             c->eval_steps.push_back(-i - 1);
@@ -205,6 +207,81 @@ static void plan_eval(vc_circuit *c)
     }
 }
 
+// Staged values: the plan's wave tasks, table builds and evaluation blocks
+// split by layer iteration (each layer's launches run while only its two
+// layers are on the device), with their device arrays and launch counters.
+static void staged_partition(vc_circuit *c, Arena &A)
+{
+    Plan &P = c->P;
+    const u32 d = c->d;
+    auto layer_of = [&](const Task &t) {
+        return t.type == TK_LINE ? P.lw[t.wave].layer
+                                 : (t.type == TK_PROD ? P.scis[P.pw[t.wave].sci].layer : P.gw[t.wave].layer);
+    };
+    auto split = [&](const std::vector<std::vector<Task>> &grp, std::vector<std::vector<std::vector<Task>>> &dst) {
+        dst.assign(d, {});
+        for (size_t g = 0; g < grp.size(); g++)
+            for (const Task &t : grp[g]) {
+                auto &v = dst[layer_of(t)];
+                if (v.size() <= g) v.resize(g + 1);
+                v[g].push_back(t);
+            }
+    };
+    split(P.groupsA, c->stA);
+    split(P.groupsB, c->stB);
+    c->stBuild.assign(d, {});
+    for (const BuildItem &b : P.builds) c->stBuild[b.layer].push_back(b);
+    c->stEval.assign(d, {});
+    for (u32 i = 0; i < d; i++) {
+        const u64 blocks = ((u64(1) << c->s[i]) + 255) / 256;
+        for (u64 b = 0; b < blocks; b++) c->stEval[i].push_back({i, (u32)b});
+    }
+    c->d_stLev = A.take<LayerEval>(d);
+    auto take_lists = [&](auto &lists, auto &dv) {
+        dv.assign(lists.size(), {});
+        for (size_t i = 0; i < lists.size(); i++)
+            for (auto &v : lists[i]) dv[i].push_back(A.take<Task>(v.size() + 1));
+    };
+    take_lists(c->stA, c->d_stA);
+    take_lists(c->stB, c->d_stB);
+    c->d_stBuild.assign(d, nullptr);
+    c->d_stEval.assign(d, nullptr);
+    for (u32 i = 0; i < d; i++) {
+        c->d_stBuild[i] = A.take<BuildItem>(c->stBuild[i].size() + 1);
+        c->d_stEval[i] = A.take<Item>(c->stEval[i].size() + 1);
+    }
+    c->stctr_off.assign(d, 0);
+    u32 nctr = 0;
+    for (u32 i = 0; i < d; i++) {
+        c->stctr_off[i] = nctr;
+        nctr += 2 * (u32)(c->stA[i].size() + c->stB[i].size());
+    }
+    c->d_stctr = A.take<u32>(nctr + 2);  // layer i's launch g: counters stctr_off[i] + 2 g, + 1
+}
+
+static cudaError_t staged_upload(vc_circuit *c)
+{
+    std::vector<LayerEval> lev(c->d);
+    for (u32 i = 0; i < c->d; i++) lev[i] = {0u, i};
+    cudaError_t e = upload(c->d_stLev, lev);
+    for (size_t i = 0; e == cudaSuccess && i < c->stA.size(); i++)
+        for (size_t g = 0; e == cudaSuccess && g < c->stA[i].size(); g++) e = upload(c->d_stA[i][g], c->stA[i][g]);
+    for (size_t i = 0; e == cudaSuccess && i < c->stB.size(); i++)
+        for (size_t g = 0; e == cudaSuccess && g < c->stB[i].size(); g++) e = upload(c->d_stB[i][g], c->stB[i][g]);
+    for (u32 i = 0; e == cudaSuccess && i < c->d; i++) {
+        e = upload(c->d_stBuild[i], c->stBuild[i]);
+        if (e == cudaSuccess) e = upload(c->d_stEval[i], c->stEval[i]);
+    }
+    u32 nctr = 0;
+    for (u32 i = 0; i < c->d; i++) nctr += 2 * (u32)(c->stA[i].size() + c->stB[i].size());
+    if (e == cudaSuccess) e = cudaMemset(c->d_stctr, 0, sizeof(u32) * (nctr + 2));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->st_copy, cudaStreamNonBlocking);
+    c->st_ev.assign(4 * (c->d + 1), nullptr);
+    for (cudaEvent_t &ev : c->st_ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    return e;
+}
+
 // Lay out every buffer and descriptor relative to `base` (0 for sizing) and
 // fill the circuit's single-circuit plan (circ = 0).
 static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
@@ -220,15 +297,30 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     Arena H;
     H.base = hbase;
     const bool host = (c->flags & VC_VALUES_IN_HOST_MEMORY) != 0;
+    const bool staged = (c->flags & VC_VALUES_STAGED) != 0;
     c->V.assign(d + 1, nullptr);
-    for (u32 i = 0; i <= d; i++) c->V[i] = host ? H.take<u64>(S(i)) : A.take<u64>(S(i));
-    c->host_bytes = host ? H.off + 256 : 0;
+    c->hV.assign(staged ? d + 1 : 0, nullptr);
+    if (staged) {
+        // every layer in page-locked host memory; three device slots of the
+        // widest layer's size, layer i in slot i mod 3
+        u64 smax = 1;
+        for (u32 i = 0; i <= d; i++) smax = std::max(smax, S(i));
+        u64 *slot[3];
+        for (int k = 0; k < 3; k++) slot[k] = A.take<u64>(smax);
+        for (u32 i = 0; i <= d; i++) {
+            c->V[i] = slot[i % 3];
+            c->hV[i] = H.take<u64>(S(i));
+        }
+        c->d_out = A.take<u64>(S(0));
+    } else {
+        for (u32 i = 0; i <= d; i++) c->V[i] = host ? H.take<u64>(S(i)) : A.take<u64>(S(i));
+    }
+    c->host_bytes = (host || staged) ? H.off + 256 : 0;
     Globals &G = c->G;
     G = Globals{};
     G.d = d;
     G.nchal = c->nchal;
     G.chal = A.take<u64>(c->nchal + 1);
-    G.ichal = A.take<u64>(c->nchal + 1);
     u32 npts = 0;
     for (u32 i = 0; i <= d; i++) npts += c->s[i];
     G.pts = A.take<u64>(npts + 1);
@@ -237,6 +329,7 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     G.invfact = A.take<u64>(64);
     G.zd_off = c->zd_off;
     G.S0 = S(0);
+    G.out_src = staged ? c->d_out : c->V[0];
     c->d_G = A.take<Globals>(1);
     P.d_G = c->d_G;
     c->d_result = A.take<u64>(VC_RESULT_WORDS);
@@ -289,10 +382,6 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
             c->eq_verify.push_back({L.tr2, 0u, EQ_SRC_CHAL, L.chal_off + L.s + L.sn, 0u});
         }
     }
-
-    // the inverse challenges (used by the sum-check waves)
-    for (u32 c0 = 0; c0 < c->nchal; c0 += INV_PER_JOB)
-        P.eqjobs.push_back({EqTab{}, 0u, EQ_SRC_INV, c0, std::min<u32>(INV_PER_JOB, c->nchal - c0)});
 
     // Waves.  A wave is one launch's share of an instance: chunks of 2^nr
     // entries (2^nl coordinates for the line reduction).  A wave followed by a
@@ -445,7 +534,6 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
                     W.no = n - r0 - nr;
                     W.ho = (W.no + 1) / 2;
                     W.chal_off = Sc.chal_off + r0;
-                    W.lc = Sc.Lc + 2 * r0;
                     W.in = inV;
                     W.out = last ? nullptr : A.take<u64>(nchunks);
                     const u32 kb = W.e ? W.e - 1 : 0;
@@ -535,12 +623,12 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     Globals &Gv = c->Gv;
     Gv = G;
     Gv.chal = A.take<u64>(c->nchal + 1);
-    Gv.ichal = nullptr;  // the verifier needs no inverse challenges
     Gv.pts = A.take<u64>(npts + 1);
     Gv.scal = A.take<u64>(2 * d + 2);
     Gv.status = G.status + 1;
     Gv.tr = nullptr;
     c->d_Gv = A.take<Globals>(1);
+    if (staged) staged_partition(c, A);
     return A.off;
 }
 
@@ -584,9 +672,7 @@ bool plan_valid(const Plan &P)
     for (const Item &it : P.checks)
         if (it.wave >= nc) return false;
     for (const EqJob &J : P.eqjobs)
-        if (J.circ >= nc || J.t.n > 30 || (J.src != EQ_SRC_CHAL && J.src != EQ_SRC_Z && J.src != EQ_SRC_INV) ||
-            (J.src == EQ_SRC_INV && J.layer > INV_PER_JOB))
-            return false;
+        if (J.circ >= nc || J.t.n > 30 || (J.src != EQ_SRC_CHAL && J.src != EQ_SRC_Z)) return false;
     for (const EvalSeg &S : P.segs)
         if (S.circ >= nc) return false;
     for (const LayerEval &E : P.levs)
@@ -991,12 +1077,75 @@ static cudaError_t set_node_args(cudaGraphExec_t exec, cudaGraphNode_t node, cud
 // Run the plan on `st`: replay its CUDA graph (captured on first use, and
 // again after the stage events change).  A plan with its own parameter node
 // gets (seed, tr, in) through it.
+// The launches and copies of one proof of a circuit with staged values
+// (Sec. 5.1.2, copy-once-per-layer).  Evaluation runs layer by layer from
+// the input up, layer i in slot i mod 3; each layer is written to host memory
+// on the copy stream as soon as it is computed, and a layer reuses a slot
+// only after the host copy of the layer three above it is done.  Then the
+// layer iterations run in order 0..d-1, iteration i on slots i mod 3 and
+// (i+1) mod 3 (layers 0..2 are still in their slots); while iteration i runs,
+// layer i+2 is copied from host memory into the slot iteration i-1 has
+// released.  Coins and the final reduction are those of the resident plan.
+static void enqueue_staged(vc_circuit &c, cudaStream_t st)
+{
+    Plan &P = c.P;
+    const Globals *Gs = P.d_G;
+    const u32 d = c.d;
+    cudaStream_t sa = P.aux, cp = c.st_copy;
+    enum { EVALUATED = 0, ON_HOST = 1, COPIED_IN = 2, PROVED = 3 };
+    auto ev = [&](u32 i, int k) { return c.st_ev[4 * i + k]; };
+    auto bytes = [&](u32 i) { return (u64(1) << c.s[i]) * sizeof(u64); };
+    launch_params(P.d_G, 0, nullptr, nullptr, st);  // arguments set per launch
+    cudaEventRecord(P.ev_fork, st);
+    cudaStreamWaitEvent(sa, P.ev_fork, 0);
+    launch_coins(Gs, P.ncirc, P.d_eqjobs, (int)P.eqjobs.size(), P.d_scis, P.d_pw, (int)P.pw.size(), sa);
+    cudaEventRecord(P.ev_tables, sa);
+    // the inputs (copied into slot d mod 3 by the caller): checked, then to host memory
+    launch_check_inputs(Gs, P.d_checks, (int)P.checks.size(), st);
+    cudaEventRecord(ev(d, EVALUATED), st);
+    cudaStreamWaitEvent(cp, ev(d, EVALUATED), 0);
+    cudaMemcpyAsync(c.hV[d], c.V[d], bytes(d), cudaMemcpyDeviceToHost, cp);
+    cudaEventRecord(ev(d, ON_HOST), cp);
+    for (int i = (int)d - 1; i >= 0; i--) {
+        if ((u32)i + 3 <= d) cudaStreamWaitEvent(st, ev(i + 3, ON_HOST), 0);
+        launch_eval_layers(Gs, c.d_stLev, c.d_stEval[i], (int)c.stEval[i].size(), st);
+        cudaEventRecord(ev(i, EVALUATED), st);
+        cudaStreamWaitEvent(cp, ev(i, EVALUATED), 0);
+        cudaMemcpyAsync(c.hV[i], c.V[i], bytes(i), cudaMemcpyDeviceToHost, cp);
+        cudaEventRecord(ev(i, ON_HOST), cp);
+    }
+    // the outputs for the final reduction (slot 0 is reused by layer 3)
+    cudaMemcpyAsync(c.d_out, c.V[0], bytes(0), cudaMemcpyDeviceToDevice, st);
+    cudaStreamWaitEvent(st, P.ev_tables, 0);
+    for (u32 i = 0; i < d; i++) {
+        const u32 nx = i + 2;
+        if (nx <= d && nx >= 3) {  // slot nx mod 3 held layer i - 1, released by iteration i - 1
+            cudaStreamWaitEvent(cp, ev(i - 1, PROVED), 0);
+            cudaMemcpyAsync(c.V[nx], c.hV[nx], bytes(nx), cudaMemcpyHostToDevice, cp);
+            cudaEventRecord(ev(nx, COPIED_IN), cp);
+        }
+        if (i + 1 >= 3) cudaStreamWaitEvent(st, ev(i + 1, COPIED_IN), 0);
+        for (size_t g = 0; g < c.stA[i].size(); g++)
+            launch_waves(Gs, P.d_lw, P.d_pw, P.d_gw, c.d_stA[i][g], (int)c.stA[i][g].size(),
+                         c.d_stctr + c.stctr_off[i] + 2 * g, st);
+        if (!c.stBuild[i].empty()) launch_build23(Gs, c.d_stBuild[i], (int)c.stBuild[i].size(), st);
+        for (size_t g = 0; g < c.stB[i].size(); g++)
+            launch_waves(Gs, P.d_lw, P.d_pw, P.d_gw, c.d_stB[i][g], (int)c.stB[i][g].size(),
+                         c.d_stctr + c.stctr_off[i] + 2 * (c.stA[i].size() + g), st);
+        cudaEventRecord(ev(i, PROVED), st);
+    }
+    cudaEventRecord(ev(d, PROVED), cp);  // join the copy stream
+    cudaStreamWaitEvent(st, ev(d, PROVED), 0);
+    launch_final(P.d_G, P.d_rounds, (int)P.rounds.size(), (int)P.nbig, P.d_outs, (int)P.outs.size(), st);
+}
+
 static cudaError_t plan_launch(Plan &P, cudaStream_t st, u64 seed = 0, u64 *tr = nullptr,
                                const u64 *in = nullptr)
 {
     cudaError_t e = cudaSuccess;
     if (!P.exec) {
-        e = capture_graph(P.cap, [&](cudaStream_t cs) { enqueue_plan(P, cs); }, &P.exec,
+        e = capture_graph(P.cap, [&](cudaStream_t cs) { P.staged ? enqueue_staged(*P.staged, cs) : enqueue_plan(P, cs); },
+                          &P.exec,
                           P.own_params ? params_kernel() : nullptr, &P.graph, &P.pnode, &P.pkp);
         if (e != cudaSuccess) {
             plan_drop_graph(P);
@@ -1022,6 +1171,14 @@ int count_launches(const Plan &P)
     n += !P.builds.empty();
     for (const auto &v : P.groupsB) n += !v.empty();
     return n + 1;  // final
+}
+
+cudaError_t circuit_enqueue_proof(vc_circuit *c, const u64 *inputs, u64 seed, u64 *tr, cudaStream_t st)
+{
+    const u64 nin = u64(1) << c->s[c->d];
+    cudaError_t e = cudaMemcpyAsync(c->V[c->d], inputs, nin * sizeof(u64), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = plan_launch(c->P, st, seed, tr, nullptr);
+    return e;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1063,7 +1220,7 @@ PlanConfig shape_config(const vc_circuit_desc *desc)
 vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **out, const PlanConfig *cfg,
                           u32 flags)
 {
-    if (flags & ~u32(VC_VALUES_IN_HOST_MEMORY)) return VC_EINVAL;
+    if (flags != 0 && flags != VC_VALUES_IN_HOST_MEMORY && flags != VC_VALUES_STAGED) return VC_EINVAL;
     if (!desc || !out || desc->n_layers < 1 || desc->n_layers > 4096 || !desc->log_width || !desc->wiring)
         return VC_EINVAL;
     *out = nullptr;
@@ -1092,7 +1249,7 @@ vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **
     c->by2_g.resize(d);
     for (u32 i = 0; i < d; i++) {
         const u32 si = c->s[i], sn = c->s[i + 1];
-        if (!shape_ok(c->kind[i], si, sn)) {
+        if (!shape_ok(c->kind[i], si, sn) || ((flags & VC_VALUES_STAGED) && c->kind[i] == W_EXPLICIT)) {
             delete c;
             return VC_EINVAL;
         }
@@ -1150,6 +1307,7 @@ vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **
     plan_eval(c);
     c->P.ncirc = 1;
     c->P.own_params = true;
+    c->P.staged = (flags & VC_VALUES_STAGED) ? c : nullptr;
     c->eval_reads_inputs = first_eval_is_input_run(c->P, c->d);
     Arena A;
     A.off = layout(c, 0, 0);
@@ -1168,6 +1326,9 @@ void circuit_free(vc_circuit *c)
         if (g) cudaGraphDestroy(g);
     if (c->pg_exec) cudaGraphExecDestroy(c->pg_exec);
     if (c->pg_arena) lib_free(c->pg_arena);
+    for (cudaEvent_t ev : c->st_ev)
+        if (ev) cudaEventDestroy(ev);
+    if (c->st_copy) cudaStreamDestroy(c->st_copy);
     plan_release(c->P);
     if (c->arena) lib_free(c->arena);
     if (c->host_vals) lib_free_host(c->host_vals);
@@ -1188,16 +1349,20 @@ vc_status circuit_allocate(vc_circuit *c)
         return e == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA;
     }
     uintptr_t hbase = 0;
+    const bool staged = (c->flags & VC_VALUES_STAGED) != 0;
     if (c->host_bytes) {
+        // mapped for kernels reading the values in place; staged values are
+        // only copied, by address on the host
         void *dp = nullptr;
-        e = lib_host_alloc(&c->host_vals, c->host_bytes, cudaHostAllocMapped | cudaHostAllocPortable);
-        if (e == cudaSuccess) e = cudaHostGetDevicePointer(&dp, c->host_vals, 0);
+        e = lib_host_alloc(&c->host_vals, c->host_bytes,
+                           staged ? cudaHostAllocDefault : (cudaHostAllocMapped | cudaHostAllocPortable));
+        if (e == cudaSuccess && !staged) e = cudaHostGetDevicePointer(&dp, c->host_vals, 0);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return e == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA;
         }
         memset(c->host_vals, 0, c->host_bytes);
-        hbase = reinterpret_cast<uintptr_t>(dp);
+        hbase = reinterpret_cast<uintptr_t>(staged ? static_cast<void *>(c->host_vals) : dp);
     }
     {
         Arena A;
@@ -1214,6 +1379,7 @@ vc_status circuit_allocate(vc_circuit *c)
     if (e == cudaSuccess) e = cudaMemcpy(c->d_G, &c->G, sizeof(Globals), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_Gv, &c->Gv, sizeof(Globals), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = plan_upload(c->P);
+    if (e == cudaSuccess && staged) e = staged_upload(c);
     for (u32 i = 0; e == cudaSuccess && i < d; i++) {
         if (c->kind[i] != W_EXPLICIT) continue;
         const LayerDev &L = c->L[i];
@@ -1462,6 +1628,7 @@ extern "C" vc_status vc_prove_pergate(vc_circuit *c, const uint64_t *inputs, uin
                                       void *stream)
 {
     if (!c || !inputs || !transcript) return VC_EINVAL;
+    if (c->flags & VC_VALUES_STAGED) return VC_EINVAL;  // reads every layer in place
     DevGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int ki = ptr_kind(inputs, c->device), kt = ptr_kind(transcript, c->device);
@@ -1942,7 +2109,8 @@ extern "C" vc_status vc_batch_create(vc_circuit *const *circuits, int n, vc_batc
     *out = nullptr;
     if (n <= 0 || !circuits) return VC_EINVAL;
     for (int j = 0; j < n; j++) {
-        if (!circuits[j] || circuits[j]->device != circuits[0]->device) return VC_EINVAL;
+        if (!circuits[j] || circuits[j]->device != circuits[0]->device || (circuits[j]->flags & VC_VALUES_STAGED))
+            return VC_EINVAL;
         for (int k = 0; k < j; k++)
             if (circuits[k] == circuits[j]) return VC_EINVAL;
     }

@@ -234,11 +234,15 @@ def _stream(stream, device: int):
 # --- C ABI ----------------------------------------------------------------------------
 
 VC_VALUES_IN_HOST_MEMORY = 1
+VC_VALUES_STAGED = 2
 
 
-def vc_circuit_create(log_width, wiring, explicit=None, device: int = 0, host_values: bool = False):
+def vc_circuit_create(log_width, wiring, explicit=None, device: int = 0, host_values: bool = False,
+                      staged: bool = False):
     """Returns an opaque handle (int).  explicit: per-layer (type, in1, in2) or
-    None.  host_values: keep the layer values in mapped host memory."""
+    None.  host_values: keep the layer values in mapped host memory; staged:
+    keep them in host memory and copy each layer through three device slots
+    (copy-once-per-layer)."""
     lw = [int(x) for x in log_width]
     kinds = [int(k) for k in wiring]
     d = len(kinds)
@@ -266,8 +270,9 @@ def vc_circuit_create(log_width, wiring, explicit=None, device: int = 0, host_va
         desc.in1 = i1s
         desc.in2 = i2s
     h = ctypes.c_void_p()
-    if host_values:
-        _check(lib().vc_circuit_create_ex(ctypes.byref(desc), device, VC_VALUES_IN_HOST_MEMORY, ctypes.byref(h)),
+    if host_values or staged:
+        flags = VC_VALUES_STAGED if staged else VC_VALUES_IN_HOST_MEMORY
+        _check(lib().vc_circuit_create_ex(ctypes.byref(desc), device, flags, ctypes.byref(h)),
                "vc_circuit_create_ex")
     else:
         _check(lib().vc_circuit_create(ctypes.byref(desc), device, ctypes.byref(h)), "vc_circuit_create")

@@ -1,6 +1,7 @@
-"""Layer values in mapped host memory (VC_VALUES_IN_HOST_MEMORY): the same
-transcripts, accept bits and outputs as with device-resident values, and less
-device memory."""
+"""Layer values in mapped host memory (VC_VALUES_IN_HOST_MEMORY) or in host
+memory copied once per layer through three device slots (VC_VALUES_STAGED):
+the same transcripts, accept bits and outputs as with device-resident values,
+and less device memory."""
 import numpy as np
 import pytest
 
@@ -104,4 +105,67 @@ def test_bad_flags_rejected():
     w, k = circuits.f2(3)
     desc, keep = vc._desc_struct(w, k)
     h = ctypes.c_void_p()
-    assert vc.lib().vc_circuit_create_ex(ctypes.byref(desc), 0, 6, ctypes.byref(h)) == vc.VC_EINVAL
+    for flags in (6, 3, 4):
+        assert vc.lib().vc_circuit_create_ex(ctypes.byref(desc), 0, flags, ctypes.byref(h)) == vc.VC_EINVAL
+
+
+STAGED = [("f2", 0), ("f2", 1), ("f2", 2), ("f2", 5), ("f2", 13), ("f0", 3), ("f0", 6), ("matmult", 2),
+          ("matmult", 4)]
+
+
+@pytest.mark.parametrize("family,logn", STAGED)
+def test_staged_values_equal_oracle(family, logn):
+    """Copy-once-per-layer: every transcript entry equals the oracle's (device
+    and host transcripts, two proofs in a row on one handle), the verifier
+    accepts it and vc_evaluate gives the outputs."""
+    w, k = circuits.by_name(family, logn)
+    x = I.job_inputs(family, logn, 70 + logn)
+    h = vc.vc_circuit_create(w, k, staged=True)
+    try:
+        for seed in (13, 14):
+            want = oracle_prove(w, k, x, seed)
+            assert (prove(h, x, seed) == want).all(), seed
+            assert (prove(h, x, seed, host_tr=True) == want).all(), seed
+        assert vc.vc_verify(h, dev(x), 14, dev(want))
+        out = torch.empty(1 << w[0], dtype=torch.int64, device="cuda")
+        vc.vc_evaluate(h, dev(x), out)
+        assert (to_np(out) == want[:1 << w[0]]).all()
+    finally:
+        vc.vc_circuit_destroy(h)
+
+
+def test_staged_values_large_equal_device_and_device_bytes():
+    """F2 2^18 and F0 2^12 with staged values equal the device-resident
+    proofs; the deep F0 circuit needs far less device memory (three slots
+    instead of 62 layers of values)."""
+    for fam, n, seed in (("f2", 18, 5), ("f0", 12, 6)):
+        w, k = circuits.by_name(fam, n)
+        x = I.job_inputs(fam, n, 40 + n)
+        hd = vc.vc_circuit_create(w, k)
+        hs = vc.vc_circuit_create(w, k, staged=True)
+        try:
+            assert (prove(hs, x, seed) == prove(hd, x, seed)).all(), fam
+            if fam == "f0":
+                values = 8 * sum(1 << s for s in w)
+                assert vc.vc_circuit_bytes(hs) < vc.vc_circuit_bytes(hd) - values // 2
+        finally:
+            vc.vc_circuit_destroy(hd)
+            vc.vc_circuit_destroy(hs)
+
+
+def test_staged_rejected_where_layers_are_read_in_place():
+    w, k = circuits.f2(6)
+    h = vc.vc_circuit_create(w, k, staged=True)
+    h2 = vc.vc_circuit_create(w, k)
+    try:
+        with pytest.raises(vc.VcError):
+            vc.vc_batch_create([h, h2])
+        tr = torch.empty(vc.vc_transcript_len(h), dtype=torch.int64, device="cuda")
+        with pytest.raises(vc.VcError):
+            vc.vc_prove_pergate(h, dev(I.f2_inputs(6, 1 << 16, 1)), 3, tr)
+    finally:
+        vc.vc_circuit_destroy(h)
+        vc.vc_circuit_destroy(h2)
+    wp, kp, ex = circuits.pattern_match(5, 2)
+    with pytest.raises(vc.VcError):
+        vc.vc_circuit_create(wp, kp, ex, staged=True)

@@ -160,3 +160,42 @@ def test_server_overlaps_launch_sets():
         assert (to_np(trs[23]) == want).all()
     finally:
         srv.close()
+
+
+def test_over_cap_job_proved_with_staged_values():
+    """A job whose circuit does not fit the memory cap with its values on the
+    device is proved with the values staged through host memory (copy once
+    per layer) instead of being refused; it equals the oracle, and jobs of
+    other shapes around it are unaffected.  Below even the staged footprint
+    the submission is refused (VC_EBUSY)."""
+    w, k = circuits.f0(8)
+    hd = vc.vc_circuit_create(w, k)
+    hs = vc.vc_circuit_create(w, k, staged=True)
+    resident, staged = vc.vc_circuit_bytes(hd), vc.vc_circuit_bytes(hs)
+    vc.vc_circuit_destroy(hd)
+    vc.vc_circuit_destroy(hs)
+    assert staged < resident
+    srv = Server(mem_cap_bytes=(staged + resident) // 2, max_batch=4, max_inflight=2)
+    try:
+        jobs = []
+        for j, (fam, logn) in enumerate([("f2", 6), ("f0", 8), ("f2", 7), ("f0", 8), ("matmult", 2)]):
+            wj, kj = circuits.by_name(fam, logn)
+            x = I.job_inputs(fam, logn, 700 + j)
+            host = j == 3  # one staged job with a host transcript
+            tr = np.zeros(circuits.transcript_len(wj), np.uint64) if host else \
+                torch.empty(circuits.transcript_len(wj), dtype=torch.int64, device="cuda")
+            jobs.append((srv.submit(wj, kj, dev(x), 40 + j, tr), wj, kj, x, 40 + j, tr))
+        for jid, wj, kj, x, seed, tr in jobs:
+            assert srv.wait(jid)["status"] == 0
+            got = tr if isinstance(tr, np.ndarray) else to_np(tr)
+            assert (got == oracle_prove(wj, kj, x, seed)).all()
+    finally:
+        srv.close()
+    srv = Server(mem_cap_bytes=staged // 2)
+    try:
+        tr = torch.empty(circuits.transcript_len(w), dtype=torch.int64, device="cuda")
+        with pytest.raises(vc.VcError) as e:
+            srv.submit(w, k, dev(I.job_inputs("f0", 8, 1)), 1, tr)
+        assert e.value.status == vc.VC_EBUSY
+    finally:
+        srv.close()
