@@ -195,15 +195,26 @@ def matmult_layers(logn: int):
 
 # --- special-purpose non-interactive F2 protocol (Sec. 3.2, 4.2, 6.3) ------------
 
+F2SP_GENERATOR = 37  # the least primitive root of p
+
+
+def f2sp_root(h: int) -> int:
+    """u = 37^((p-1)/(2h)): a generator of the subgroup of order 2h (h must
+    divide (p - 1) / 2); the nodes are u^(2y), the proof points u^k."""
+    if h <= 0 or (P - 1) % (2 * h):
+        raise ValueError("h must divide (p - 1) / 2")
+    return pow(F2SP_GENERATOR, (P - 1) // (2 * h), P)
+
+
 def f2sp_prove(a, v: int, h: int) -> np.ndarray:
     """The proof of the special-purpose F2 protocol for the v x h grid a (row
-    x at a[x h : x h + h]): s(Y) = sum_x f_x(Y)^2 at Y = 0..2h-2, f_x the
-    degree < h extension of row x."""
+    x at a[x h : x h + h]): s(u^k) = sum_x f_x(u^k)^2 for k = 0..2h-1, f_x the
+    degree < h polynomial with f_x(u^(2y)) = a(x, y)."""
     x = _arr(a)
     assert len(x) == v * h
-    out = np.zeros(2 * h - 1, np.uint64)
+    out = np.zeros(2 * h, np.uint64)
     if lib().or_f2sp_prove(_p64(x), v, h, _p64(out)) != 0:
-        raise ValueError("non-canonical input")
+        raise ValueError("non-canonical input or h not dividing (p - 1) / 2")
     return out
 
 
@@ -211,7 +222,7 @@ def f2sp_verify(a, v: int, h: int, seed: int, proof):
     """(accept, F2 answer) of the verifier with the secret point r drawn from seed."""
     x = _arr(a)
     pr = _arr(proof)
-    assert len(x) == v * h and len(pr) == 2 * h - 1
+    assert len(x) == v * h and len(pr) == 2 * h
     f2 = np.zeros(1, np.uint64)
     rc = lib().or_f2sp_verify(_p64(x), v, h, seed, _p64(pr), _p64(f2))
     if rc < 0:

@@ -763,85 +763,121 @@ int or_verify(const or_circuit *c, const fe *inputs, uint64_t seed, const fe *tr
 /* Sec. 6.3; the protocol of Chakrabarti et al. as implemented by CMT).       */
 /*                                                                           */
 /* The frequency vector a (n = v h entries) is a v x h grid, a(x, y) at      */
-/* x h + y.  Row x is extended in y by the polynomial f_x of degree < h with */
-/* f_x(y) = a(x, y) for y = 0..h-1.  The proof is the polynomial             */
-/* s(Y) = sum_x f_x(Y)^2 (degree <= 2h - 2) given by its values at           */
-/* Y = 0..2h-2.  The verifier keeps f_x(r) for a secret random r (one value  */
-/* per row, v words), accepts iff s(r) = sum_x f_x(r)^2, and then reads      */
-/* F2 = sum_x sum_y a(x,y)^2 = sum_{y<h} s(y).  Readings: nodes 0..h-1 for   */
-/* the data and 0..2h-2 for the proof; r is challenge 0 of the seed's        */
-/* stream (the coins of the GKR part).                                       */
+/* x h + y.  Row x is extended by the polynomial f_x of degree < h that      */
+/* takes the value a(x, y) at the node w^y, y = 0..h-1, where w generates    */
+/* the subgroup of order h of F_p^*.  The proof is the polynomial            */
+/* s(Y) = sum_x f_x(Y)^2 (degree <= 2h - 2) given by its values at the 2h    */
+/* points u^k, k = 0..2h-1, where u generates the subgroup of order 2h and   */
+/* u^2 = w (so the even points are the nodes).  The verifier keeps f_x(r)    */
+/* for a secret random r (one value per row, v words), accepts iff           */
+/* s(r) = sum_x f_x(r)^2, and reads F2 = sum_x sum_y a(x,y)^2 =              */
+/* sum_{k even} s(u^k).  Readings: the nodes form a multiplicative subgroup  */
+/* (the paper's prover runs the Prime Factor FFT on each row, which needs    */
+/* points of smooth multiplicative order, Sec. 4.2 and 5.2), so h must       */
+/* divide (p - 1) / 2; u = 37^((p-1)/(2h)) with 37 the least primitive root  */
+/* of p; r is challenge 0 of the seed's stream (the coins of the GKR part).  */
 /*                                                                           */
-/* Everything below is the definition: Lagrange basis values as products,   */
-/* no FFT, no barycentric shortcut.                                          */
+/* Everything below is the definition: Lagrange basis values as products    */
+/* over the node sets, no FFT, no barycentric shortcut.                      */
 /* ------------------------------------------------------------------------- */
 
-/* L_y(m) over the nodes 0..k-1: prod_{j != y} (m - j) / (y - j). */
-static fe lagrange_basis(uint64_t k, uint64_t y, fe m)
+#define OR_F2SP_GEN 37u
+
+/* u = 37^((p-1)/(2h)), a generator of the subgroup of order 2h; 0 if 2h does
+ * not divide p - 1. */
+static fe f2sp_root(uint64_t h)
+{
+    if (h == 0 || (OR_P - 1) % (2 * h) != 0) return 0;
+    return or_pow(OR_F2SP_GEN, (OR_P - 1) / (2 * h));
+}
+
+/* L_y(m) over the nodes pts[0..k-1]: prod_{j != y} (m - pts[j]) / (pts[y] - pts[j]). */
+static fe lagrange_basis(const fe *pts, uint64_t k, uint64_t y, fe m)
 {
     fe num = 1, den = 1;
     for (uint64_t j = 0; j < k; j++) {
         if (j == y) continue;
-        num = or_mul(num, or_sub(m, j));
-        den = or_mul(den, or_sub(y, j));
+        num = or_mul(num, or_sub(m, pts[j]));
+        den = or_mul(den, or_sub(pts[y], pts[j]));
     }
     return or_mul(num, or_inv(den));
 }
 
-/* Value at m of the polynomial through (j, vals[j]), j = 0..k-1. */
-static fe lagrange_eval(const fe *vals, uint64_t k, fe m)
+/* Value at m of the polynomial through (pts[j], vals[j]), j = 0..k-1. */
+static fe lagrange_eval(const fe *pts, const fe *vals, uint64_t k, fe m)
 {
     fe s = 0;
-    for (uint64_t y = 0; y < k; y++) s = or_add(s, or_mul(vals[y], lagrange_basis(k, y, m)));
+    for (uint64_t y = 0; y < k; y++) s = or_add(s, or_mul(vals[y], lagrange_basis(pts, k, y, m)));
     return s;
 }
 
-/* Prover: proof[Y] = s(Y) for Y = 0..2h-2.  Returns -1 for a non-canonical
- * entry of a (or h = 0). */
+/* nodes[y] = u^(2y), y < h; points[k] = u^k, k < 2h. */
+static void f2sp_points(fe u, uint64_t h, fe *nodes, fe *points)
+{
+    fe t = 1;
+    for (uint64_t k = 0; k < 2 * h; k++) {
+        points[k] = t;
+        if (k % 2 == 0) nodes[k / 2] = t;
+        t = or_mul(t, u);
+    }
+}
+
+/* Prover: proof[k] = s(u^k) for k = 0..2h-1.  Returns -1 for a non-canonical
+ * entry of a, or for h = 0 or h not dividing (p - 1) / 2. */
 int or_f2sp_prove(const fe *a, uint64_t v, uint64_t h, fe *proof)
 {
-    if (h == 0) return -1;
+    const fe u = f2sp_root(h);
+    if (!u) return -1;
     for (uint64_t i = 0; i < v * h; i++)
         if (a[i] >= OR_P) return -1;
-    const uint64_t np = 2 * h - 1;
-    fe *L = (fe *)malloc(sizeof(fe) * h * np); /* L[m h + y] = L_y(m) */
-    for (uint64_t m = 0; m < np; m++)
-        for (uint64_t y = 0; y < h; y++) L[m * h + y] = lagrange_basis(h, y, m);
-    for (uint64_t m = 0; m < np; m++) proof[m] = 0;
+    const uint64_t np = 2 * h;
+    fe *nodes = (fe *)malloc(sizeof(fe) * h), *points = (fe *)malloc(sizeof(fe) * np);
+    f2sp_points(u, h, nodes, points);
+    fe *L = (fe *)malloc(sizeof(fe) * h * np); /* L[k h + y] = L_y(u^k) */
+    for (uint64_t k = 0; k < np; k++)
+        for (uint64_t y = 0; y < h; y++) L[k * h + y] = lagrange_basis(nodes, h, y, points[k]);
+    for (uint64_t k = 0; k < np; k++) proof[k] = 0;
     for (uint64_t x = 0; x < v; x++) {
         const fe *row = a + x * h;
-        for (uint64_t m = 0; m < np; m++) {
+        for (uint64_t k = 0; k < np; k++) {
             fe f = 0;
-            for (uint64_t y = 0; y < h; y++) f = or_add(f, or_mul(row[y], L[m * h + y]));
-            proof[m] = or_add(proof[m], or_mul(f, f));
+            for (uint64_t y = 0; y < h; y++) f = or_add(f, or_mul(row[y], L[k * h + y]));
+            proof[k] = or_add(proof[k], or_mul(f, f));
         }
     }
     free(L);
+    free(nodes);
+    free(points);
     return 0;
 }
 
 /* Verifier: r from the seed; f_x(r) for every row; s(r) from the proof by
- * Lagrange interpolation over 0..2h-2.  Returns 1 (accept) or 0, and the
- * answer sum_{y<h} s(y) in *f2; -1 for a non-canonical entry of a or h = 0.
- * A proof entry >= p is a rejection. */
+ * Lagrange interpolation over the 2h points.  Returns 1 (accept) or 0, and the
+ * answer sum_{k even} proof[k] in *f2; -1 for a non-canonical entry of a, or
+ * an h the prover rejects.  A proof entry >= p is a rejection. */
 int or_f2sp_verify(const fe *a, uint64_t v, uint64_t h, uint64_t seed, const fe *proof, fe *f2)
 {
-    if (h == 0) return -1;
+    const fe u = f2sp_root(h);
+    if (!u) return -1;
     for (uint64_t i = 0; i < v * h; i++)
         if (a[i] >= OR_P) return -1;
-    const uint64_t np = 2 * h - 1;
-    for (uint64_t m = 0; m < np; m++)
-        if (proof[m] >= OR_P) return 0;
+    const uint64_t np = 2 * h;
+    for (uint64_t k = 0; k < np; k++)
+        if (proof[k] >= OR_P) return 0;
+    fe *nodes = (fe *)malloc(sizeof(fe) * h), *points = (fe *)malloc(sizeof(fe) * np);
+    f2sp_points(u, h, nodes, points);
     fe r;
     or_draw_challenges(seed, 1, &r);
     fe lhs = 0;
     for (uint64_t x = 0; x < v; x++) {
-        const fe fr = lagrange_eval(a + x * h, h, r);
+        const fe fr = lagrange_eval(nodes, a + x * h, h, r);
         lhs = or_add(lhs, or_mul(fr, fr));
     }
-    const fe rhs = lagrange_eval(proof, np, r);
+    const fe rhs = lagrange_eval(points, proof, np, r);
     fe ans = 0;
-    for (uint64_t y = 0; y < h; y++) ans = or_add(ans, proof[y]);
+    for (uint64_t k = 0; k < np; k += 2) ans = or_add(ans, proof[k]);
     *f2 = ans;
+    free(nodes);
+    free(points);
     return lhs == rhs ? 1 : 0;
 }

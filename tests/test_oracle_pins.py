@@ -528,34 +528,56 @@ def test_pm_and_mm1_wiring_equals_the_packages_description():
 
 # --- the special-purpose non-interactive F2 protocol (Sec. 3.2, 4.2, 6.3) ----------
 
-def _sympy_extension(row, m):
-    """Value at m of the degree < h polynomial through (y, row[y]), by exact
-    rational interpolation (sympy), reduced mod p: an independent method."""
+def _sympy_coefficients(row, nodes):
+    """Coefficients of the degree < h polynomial through (nodes[y], row[y]) by
+    solving the Vandermonde system mod p with sympy's modular matrix inverse:
+    an independent method (no Lagrange products)."""
     sympy = pytest.importorskip("sympy")
-    X = sympy.Symbol("X")
-    poly = sympy.interpolate([(y, int(row[y])) for y in range(len(row))], X)
-    val = sympy.Rational(poly.subs(X, m))
-    return int(val.p) * pow(int(val.q), -1, P) % P
+    h = len(row)
+    V = sympy.Matrix(h, h, lambda y, j: pow(int(nodes[int(y)]), int(j), P))
+    c = V.inv_mod(P) * sympy.Matrix([int(t) for t in row])
+    return [int(t) % P for t in c]
 
 
-@pytest.mark.parametrize("v,h,seed", [(1, 1, 1), (1, 2, 2), (2, 3, 3), (4, 4, 4), (3, 7, 5), (8, 8, 6)])
+def test_f2sp_nodes_form_subgroups():
+    """37 generates F_p^* (sympy); u = 37^((p-1)/(2h)) has order exactly 2h,
+    so the nodes u^(2y) are the h distinct elements of the subgroup of order h
+    and the proof points u^k those of the subgroup of order 2h; an h that does
+    not divide (p - 1) / 2 is refused."""
+    sympy = pytest.importorskip("sympy")
+    assert sympy.is_primitive_root(oracle.F2SP_GENERATOR, P)
+    for h in (1, 3, 5, 7, 9, 15, 21, 45, 1001, 5005):
+        u = oracle.f2sp_root(h)
+        assert pow(u, 2 * h, P) == 1 and pow(u, h, P) == P - 1
+        assert sympy.n_order(u, P) == 2 * h
+    for h in (2, 4, 8, 1024, 17):
+        with pytest.raises(ValueError):
+            oracle.f2sp_prove(np.zeros(h, np.uint64), 1, h)
+
+
+@pytest.mark.parametrize("v,h,seed", [(1, 1, 1), (1, 3, 2), (2, 3, 3), (4, 5, 4), (3, 7, 5), (2, 9, 6), (2, 15, 7)])
 def test_f2sp_proof_against_sympy_interpolation(v, h, seed):
-    """s(Y) = sum_x f_x(Y)^2 with f_x the interpolant of row x, f_x computed by
-    sympy's exact rational interpolation; s(y) for y < h is the column's sum
-    of squares and sum_{y<h} s(y) = F2."""
+    """s(u^k) = sum_x f_x(u^k)^2 with f_x's coefficients from a modular
+    Vandermonde solve (sympy); at the nodes (k even) s is the column's sum of
+    squares, and the even points sum to F2."""
     rng = np.random.default_rng(seed)
     a = rng.integers(0, 1000, v * h).astype(np.uint64)
     proof = oracle.f2sp_prove(a, v, h)
-    for m in range(2 * h - 1):
-        want = sum(_sympy_extension(a[x * h:(x + 1) * h], m) ** 2 for x in range(v)) % P
-        assert int(proof[m]) == want
+    assert len(proof) == 2 * h
+    u = oracle.f2sp_root(h)
+    nodes = [pow(u, 2 * y, P) for y in range(h)]
+    coeffs = [_sympy_coefficients(a[x * h:(x + 1) * h], nodes) for x in range(v)]
+    for k in range(2 * h):
+        pt = pow(u, k, P)
+        want = sum(sum(c * pow(pt, j, P) for j, c in enumerate(cs)) ** 2 for cs in coeffs) % P
+        assert int(proof[k]) == want
     grid = a.astype(object).reshape(v, h)
     for y in range(h):
-        assert int(proof[y]) == int((grid[:, y] ** 2).sum()) % P
-    assert sum(int(t) for t in proof[:h]) % P == int((grid ** 2).sum()) % P
+        assert int(proof[2 * y]) == int((grid[:, y] ** 2).sum()) % P
+    assert sum(int(t) for t in proof[0::2]) % P == int((grid ** 2).sum()) % P
 
 
-@pytest.mark.parametrize("v,h", [(1, 1), (5, 3), (16, 16), (10, 33)])
+@pytest.mark.parametrize("v,h", [(1, 1), (5, 3), (16, 15), (10, 33)])
 def test_f2sp_complete_and_sound(v, h):
     rng = np.random.default_rng(v * 100 + h)
     a = rng.integers(0, 1 << 16, v * h).astype(np.uint64)
