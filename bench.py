@@ -222,14 +222,52 @@ def run_residency(widths, kinds, xd, flush, reps=5):
     out["slowdown"] = out["host_values_prove_ms"] / out["device_prove_ms"]
     out["staged_slowdown"] = out["staged_prove_ms"] / out["device_prove_ms"]
     out["staged_link_bytes"] = 8 * (sum(1 << s for s in widths) + sum(1 << s for s in widths[3:]))
+    out["note"] = ("F2's three widest layers are 3/4 of its values, so three slots save little there; "
+                   "the deep F0 circuit (62 layers of values) shows the saving: see `deep`")
     return out
 
 
-def run_special_purpose(flush, shapes=((1024, 1024), (5000, 5000)), reps=3):
+def run_residency_deep(flush, reps=3):
+    """The same comparison on the F0 circuit with 2^16 inputs (61 power
+    layers of 2^17 values each): staged values need three slots of device
+    memory instead of every layer."""
+    import torch
+    from paper_1202_1350_gb300 import circuits, vc
+    from paper_1202_1350_gb300 import inputs as I
+    widths, kinds = circuits.f0(16)
+    x = torch.from_numpy(I.f0_inputs(16, 0xC0FFEE + 1).view(np.int64).copy()).cuda()
+    out = {"workload": "F0, 2^16 inputs (Poisson(1) capped at 2^10)"}
+    trs = {}
+    for name, kw in (("device", {}), ("staged", {"staged": True})):
+        h = vc.vc_circuit_create(widths, kinds, **kw)
+        tr = torch.empty(vc.vc_transcript_len(h), dtype=torch.int64, device="cuda")
+        ts = []
+        for k in range(reps + 1):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            vc.vc_prove(h, x, 4444, tr)
+            e1.record()
+            e1.synchronize()
+            if k >= 1:
+                ts.append(e0.elapsed_time(e1))
+        vc.vc_circuit_sync(h)
+        out[name + "_prove_ms"] = statistics.median(ts)
+        out[name + "_device_bytes"] = vc.vc_circuit_bytes(h)
+        trs[name] = tr
+        vc.vc_circuit_destroy(h)
+    assert bool((trs["device"] == trs["staged"]).all().item()), "staged values changed the F0 transcript"
+    out["values_bytes"] = 8 * sum(1 << s for s in widths)
+    out["staged_link_bytes"] = 8 * (sum(1 << s for s in widths) + sum(1 << s for s in widths[3:]))
+    return out
+
+
+def run_special_purpose(flush, shapes=((1048, 1001), (4995, 5005)), reps=3):
     """The special-purpose non-interactive F2 protocol: prover and streaming
     verifier times for a v x h grid of frequencies uniform in [0, 2^16]
-    (n = 2^20, and the paper's n = 25 million with v = h = 5000, Sec. 6.3);
-    the answer is checked against sum a_i^2."""
+    (n ~ 2^20 with h = 1001 = 7 11 13, and the paper's n ~ 25 million with
+    h = 5005 = 5 7 11 13, v = 4995: Sec. 6.3's table row of 39.1 KB of verifier
+    space and 78.1 KB of proof); the answer is checked against sum a_i^2."""
     import torch
     from paper_1202_1350_gb300 import vc
     from paper_1202_1350_gb300 import inputs as I
@@ -238,7 +276,7 @@ def run_special_purpose(flush, shapes=((1024, 1024), (5000, 5000)), reps=3):
     for v, h in shapes:
         a = I.uniform_ints(SEED_SP + v, v * h, 1 << 16)
         ad = torch.from_numpy(a.view(np.int64)).cuda()
-        proof = torch.empty(2 * h - 1, dtype=torch.int64, device="cuda")
+        proof = torch.empty(2 * h, dtype=torch.int64, device="cuda")
         s = vc.vc_f2sp_create(v, h)
         pt, vt = [], []
         ok = True
@@ -260,9 +298,22 @@ def run_special_purpose(flush, shapes=((1024, 1024), (5000, 5000)), reps=3):
         want = int((a.astype(object) ** 2).sum()) % P
         out.append({"n": v * h, "v": v, "h": h, "prove_ms": statistics.median(pt),
                     "verify_ms": statistics.median(vt), "accepted": bool(ok), "answer_ok": f2 == want,
-                    "proof_words": 2 * h - 1, "verifier_words": v})
+                    "proof_words": 2 * h, "verifier_words": v,
+                    "transform_products": 2 * v * h * sum(_f2sp_factors(h))})
         del ad
     return out
+
+
+def _f2sp_factors(h):
+    q = []
+    for pr in (3, 5, 7, 11, 13, 31, 41, 61):
+        pp = 1
+        while h % pr == 0:
+            h //= pr
+            pp *= pr
+        if pp > 1:
+            q.append(pp)
+    return q
 
 
 SEED_SP = 0xC0FFEE + 7
@@ -557,6 +608,7 @@ def run_ours(args):
     if not args.no_ablation:
         ablation = run_ablation(h, xd, tr, flush)
         residency = run_residency(widths, kinds, xd, flush)
+        residency["deep"] = run_residency_deep(flush)
         special = run_special_purpose(flush)
     # end to end: each step uploads its inputs from page-locked host memory
     # once (the prover and the verifier's input pass both read that copy),

@@ -439,22 +439,28 @@ vc_status vc_get_memory_usage(uint64_t *device_bytes, uint64_t *pinned_bytes);
 
 /* ---- Special-purpose non-interactive F2 protocol (Sec. 3.2; Sec. 4.2;
  * Sec. 6.3).  The frequency vector a of n = v h entries is a v x h grid,
- * a(x, y) at x h + y (row-major).  Row x is the polynomial f_x of degree < h
- * with f_x(y) = a(x, y) at y = 0..h-1.  The proof is s(Y) = sum_x f_x(Y)^2 at
- * Y = 0..2h-2 (2h - 1 u64): proof length about 2h words, verifier space v
- * words.  The verifier keeps f_x(r) for a secret random r (drawn from its
- * seed like the GKR coins: the first accepted splitmix64 draw), accepts iff
- * s(r) = sum_x f_x(r)^2, and answers F2 = sum_{y<h} s(y).  No interaction.
- * Inputs must be canonical (< p). */
+ * a(x, y) at x h + y (row-major).  Let u = 37^((p-1)/(2h)) (37 generates
+ * F_p^*), so u has order 2h and w = u^2 order h.  Row x is the polynomial f_x
+ * of degree < h with f_x(w^y) = a(x, y), y = 0..h-1.  The proof is
+ * s(Y) = sum_x f_x(Y)^2 at the points u^k, k = 0..2h-1 (2h u64; the even
+ * points are the nodes): proof length 2h words, verifier space v words.
+ * The verifier keeps f_x(r) for a secret random r (drawn from its seed like
+ * the GKR coins: the first accepted splitmix64 draw), accepts iff
+ * s(r) = sum_x f_x(r)^2, and answers F2 = sum_{k even} s(u^k).  No
+ * interaction.  Nodes of a multiplicative subgroup let the prover extend each
+ * row with the Prime Factor FFT (Sec. 4.2, 5.2): h must divide (p - 1) / 2
+ * with every prime-power factor at most 61, i.e. h is a product of distinct
+ * members of {3 or 9, 5 or 25, 7, 11, 13, 31, 41, 61}.  Inputs must be
+ * canonical (< p). */
 typedef struct vc_f2sp vc_f2sp;
-#define VC_F2SP_MAX_H 8192u
+#define VC_F2SP_MAX_H 7000u
 
-/* Node tables for h and scratch for v rows on `device`.  VC_EINVAL: v = 0,
- * h = 0 or h > VC_F2SP_MAX_H. */
+/* Transform tables for h and scratch for v rows on `device`.  VC_EINVAL:
+ * v = 0, h > VC_F2SP_MAX_H, or h not of the form above. */
 vc_status vc_f2sp_create(uint64_t v, uint64_t h, int device, vc_f2sp **out);
 vc_status vc_f2sp_destroy(vc_f2sp *s);
 
-/* Prover: proof[Y] = s(Y), Y = 0..2h-2, for the v h entries at `a` (host or
+/* Prover: proof[k] = s(u^k), k = 0..2h-1, for the v h entries at `a` (host or
  * device).  Synchronous; VC_EINVAL for an entry >= p (the proof is then
  * undefined). */
 vc_status vc_f2sp_prove(vc_f2sp *s, const uint64_t *a, uint64_t *proof, void *stream);
@@ -463,9 +469,9 @@ vc_status vc_f2sp_prove(vc_f2sp *s, const uint64_t *a, uint64_t *proof, void *st
  * absorb adds the contribution of whole rows [first_row, first_row + nrows)
  * given contiguously at `rows` (host or device; a row may be absorbed in
  * several parts as additive updates of its counts); end checks `proof`
- * (2h - 1 u64, host or device), sets *accept (1 or 0; an entry >= p is a
- * rejection) and *f2 = sum_{y<h} proof[y], synchronously.  VC_EINVAL from end
- * if an absorbed entry was >= p. */
+ * (2h u64, host or device), sets *accept (1 or 0; an entry >= p is a
+ * rejection) and *f2 = sum of the proof's even entries, synchronously.
+ * VC_EINVAL from end if an absorbed entry was >= p. */
 vc_status vc_f2sp_verify_begin(vc_f2sp *s, uint64_t seed, void *stream);
 vc_status vc_f2sp_verify_absorb(vc_f2sp *s, const uint64_t *rows, uint64_t first_row, uint64_t nrows,
                                 void *stream);

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <new>
+#include <vector>
 
 #include "internal.h"
 
@@ -10,13 +11,54 @@ struct vc_f2sp {
     int device = 0;
     u64 v = 0, h = 0;
     char *mem = nullptr;
-    u64 *w = nullptr, *C = nullptr, *iv = nullptr, *w2 = nullptr;  // node tables
-    u64 *L = nullptr, *M = nullptr, *acc = nullptr;                 // verifier state
-    u64 *part = nullptr, *proof = nullptr, *res = nullptr;          // prover partials, staging, results
+    SpFftHost F{};                                            // prover's transform (device tables)
+    u64 *pw = nullptr;                                        // u^k, k < 2h (the proof points)
+    u64 inv_h = 0;
+    u64 *L = nullptr, *M = nullptr, *acc = nullptr;           // verifier state
+    u64 *part = nullptr, *proof = nullptr, *res = nullptr;    // prover partials, staging, results
+    u32 nparts = 0;
     u32 *status = nullptr;
     u64 *a_stage = nullptr;  // host inputs are staged here (allocated on first use)
     u64 *h_res = nullptr;    // pinned: results and status readback
 };
+
+namespace {
+
+u64 h_pow(u64 b, u64 e)
+{
+    u64 r = 1;
+    while (e) {
+        if (e & 1) r = h_mul(r, b);
+        b = h_mul(b, b);
+        e >>= 1;
+    }
+    return r;
+}
+
+u64 h_inv(u64 a) { return h_pow(a, FP_P - 2); }
+
+// The factors of h for the prime-factor transform: pairwise coprime prime
+// powers, each a divisor of p - 1 and at most 61 (so that a length-q DFT sums
+// at most 61 exact products in 128 bits).  False if h has another factor.
+bool sp_factor(u64 h, std::vector<u32> &q)
+{
+    static const u32 primes[] = {3, 5, 7, 11, 13, 31, 41, 61};
+    q.clear();
+    for (u32 pr : primes) {
+        u32 pp = 1;
+        while (h % pr == 0) {
+            h /= pr;
+            pp *= pr;
+        }
+        if (pp > 1) {
+            if (pp > 61 || (FP_P - 1) % pp != 0) return false;
+            q.push_back(pp);
+        }
+    }
+    return h == 1 && q.size() <= 8;
+}
+
+}  // namespace
 
 static vc_status sp_status(vc_f2sp *s, cudaStream_t st)
 {
@@ -37,7 +79,10 @@ extern "C" vc_status vc_f2sp_create(uint64_t v, uint64_t h, int device, vc_f2sp 
 {
     if (!out) return VC_EINVAL;
     *out = nullptr;
-    if (v < 1 || h < 1 || h > VC_F2SP_MAX_H || v > (uint64_t(1) << 40) / h) return VC_EINVAL;
+    std::vector<u32> q;
+    if (v < 1 || h < 1 || h > VC_F2SP_MAX_H || v > (uint64_t(1) << 40) / h || (FP_P - 1) % (2 * h) != 0 ||
+        !sp_factor(h, q))
+        return VC_EINVAL;
     DevGuard guard(device);
     init_device_once(device);
     vc_f2sp *s = new (std::nothrow) vc_f2sp();
@@ -45,16 +90,41 @@ extern "C" vc_status vc_f2sp_create(uint64_t v, uint64_t h, int device, vc_f2sp 
     s->device = device;
     s->v = v;
     s->h = h;
-    const u64 n2 = 2 * h - 1, nc = sp_prove_ctas(v);
+    // the transform's geometry: dimension d has size q[d]; slot = sum of
+    // digit_d stride_d, the last dimension innermost
+    const u32 m = (u32)q.size();
+    std::vector<u32> stride(m), N(m), t(m);
+    u32 nroots = 0;
+    for (int d = (int)m - 1; d >= 0; d--) stride[d] = (d == (int)m - 1) ? 1 : stride[d + 1] * q[d + 1];
+    SpFftHost &F = s->F;
+    F.h = (u32)h;
+    F.m = m;
+    for (u32 d = 0; d < m; d++) {
+        N[d] = (u32)(h / q[d]);
+        t[d] = 0;
+        while ((u64)N[d] * t[d] % q[d] != 1 % q[d]) t[d]++;  // (h / q_d)^{-1} mod q_d
+        F.q[d] = q[d];
+        F.magic[d] = ((1u << 20) + q[d] - 1) / q[d];
+        F.twoff[d] = nroots;
+        nroots += q[d];
+    }
+    F.nroots = nroots;
+    s->nparts = sp_prove_ctas(v);
+    const u64 n2 = 2 * h;
+    u32 *d_pin = nullptr, *d_perm = nullptr, *d_idx = nullptr;
+    u64 *d_fw = nullptr, *d_bw = nullptr, *d_twist = nullptr;
     auto carve = [&](Arena &A) {
-        s->w = A.take<u64>(h);
-        s->C = A.take<u64>(h);
-        s->iv = A.take<u64>(n2);
-        s->w2 = A.take<u64>(n2);
+        d_pin = A.take<u32>(h);
+        d_perm = A.take<u32>(h);
+        d_idx = A.take<u32>(h);
+        d_twist = A.take<u64>(h);
+        d_fw = A.take<u64>(nroots + 1);
+        d_bw = A.take<u64>(nroots + 1);
+        s->pw = A.take<u64>(n2);
         s->L = A.take<u64>(h);
         s->M = A.take<u64>(n2);
         s->acc = A.take<u64>(v);
-        s->part = A.take<u64>(nc * n2);
+        s->part = A.take<u64>((u64)s->nparts * n2);
         s->proof = A.take<u64>(n2);
         s->res = A.take<u64>(4);
         s->status = A.take<u32>(1);
@@ -68,11 +138,54 @@ extern "C" vc_status vc_f2sp_create(uint64_t v, uint64_t h, int device, vc_f2sp 
         carve(A);
         e = cudaMemset(s->mem, 0, A0.off);
     }
-    if (e == cudaSuccess) e = lib_host_alloc(&s->h_res, 8 * sizeof(u64), cudaHostAllocDefault);
     if (e == cudaSuccess) {
-        launch_sp_tables(h, s->w, s->C, s->iv, s->w2, 0);
-        e = cudaDeviceSynchronize();
+        // tables (exact host arithmetic): u generates the subgroup of order
+        // 2h, w = u^2 the one of order h; root of dimension d = w^{h / q_d}
+        const u64 u = h_pow(37, (FP_P - 1) / n2), w = h_mul(u, u);
+        s->inv_h = h_inv(h);
+        std::vector<u64> pw(n2), fw(nroots + 1, 0), bw(nroots + 1, 0), twist(h);
+        std::vector<u32> pin(h), perm(h), idx(h);
+        u64 tpow = 1;
+        for (u64 k = 0; k < n2; k++, tpow = h_mul(tpow, u)) pw[k] = tpow;
+        for (u32 d = 0; d < m; d++) {
+            const u64 root = h_pow(w, N[d]), iroot = h_inv(root);
+            u64 f = 1, b = 1;
+            for (u32 e2 = 0; e2 < q[d]; e2++, f = h_mul(f, root), b = h_mul(b, iroot)) {
+                fw[F.twoff[d] + e2] = f;
+                bw[F.twoff[d] + e2] = b;
+            }
+        }
+        auto slot_of_input = [&](u64 y) {  // digits y t_d mod q_d
+            u64 p = 0;
+            for (u32 d = 0; d < m; d++) p += ((y * t[d]) % q[d]) * stride[d];
+            return (u32)p;
+        };
+        for (u64 y = 0; y < h; y++) pin[y] = slot_of_input(y);
+        for (u64 P = 0; P < h; P++) {  // output slot: digits k_d = j mod q_d; j by CRT
+            u64 j = 0;
+            for (u32 d = 0; d < m; d++) {
+                const u64 kd = (P / stride[d]) % q[d];
+                j = (j + kd * N[d] % h * t[d]) % h;
+            }
+            idx[P] = (u32)j;
+            perm[P] = slot_of_input(j);
+            twist[P] = h_mul(pw[j], s->inv_h);
+        }
+        e = upload(d_pin, pin);
+        if (e == cudaSuccess) e = upload(d_perm, perm);
+        if (e == cudaSuccess) e = upload(d_idx, idx);
+        if (e == cudaSuccess) e = upload(d_twist, twist);
+        if (e == cudaSuccess) e = upload(d_fw, fw);
+        if (e == cudaSuccess) e = upload(d_bw, bw);
+        if (e == cudaSuccess) e = upload(s->pw, pw);
+        F.fw = d_fw;
+        F.bw = d_bw;
+        F.pin = d_pin;
+        F.perm = d_perm;
+        F.idx = d_idx;
+        F.twist = d_twist;
     }
+    if (e == cudaSuccess) e = lib_host_alloc(&s->h_res, 8 * sizeof(u64), cudaHostAllocDefault);
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (s->mem) lib_free(s->mem);
@@ -128,10 +241,9 @@ extern "C" vc_status vc_f2sp_prove(vc_f2sp *s, const uint64_t *a, uint64_t *proo
     vc_status err;
     const u64 *da = sp_device_input(s, a, s->v * s->h, st, &err);
     if (!da) return err;
-    launch_sp_prove(da, s->v, s->h, s->w, s->C, s->iv, s->part, s->proof, s->status, st);
+    launch_sp_prove(da, s->v, s->F, s->part, s->nparts, s->proof, s->status, st);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(proof, s->proof, (2 * s->h - 1) * sizeof(u64), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(proof, s->proof, 2 * s->h * sizeof(u64), cudaMemcpyDefault, st);
     if (e != cudaSuccess) return cuda_status(e);
     return sp_status(s, st);
 }
@@ -141,7 +253,7 @@ extern "C" vc_status vc_f2sp_verify_begin(vc_f2sp *s, uint64_t seed, void *strea
     if (!s) return VC_EINVAL;
     DevGuard guard(s->device);
     cudaStream_t st = (cudaStream_t)stream;
-    launch_sp_vbegin(seed, s->v, s->h, s->w, s->w2, s->L, s->M, s->acc, s->res, st);
+    launch_sp_vbegin(seed, s->v, s->h, s->inv_h, s->pw, s->L, s->M, s->acc, s->res, st);
     return cuda_status(cudaGetLastError());
 }
 
@@ -166,7 +278,7 @@ extern "C" vc_status vc_f2sp_verify_end(vc_f2sp *s, const uint64_t *proof, uint6
     if (!s || !proof || !f2 || !accept) return VC_EINVAL;
     DevGuard guard(s->device);
     cudaStream_t st = (cudaStream_t)stream;
-    const u64 n2 = 2 * s->h - 1;
+    const u64 n2 = 2 * s->h;
     const int kp = ptr_kind(proof, s->device);
     if (kp < 0) return VC_EINVAL;
     cudaError_t e = cudaSuccess;

@@ -3,155 +3,132 @@
 // Sec. 5.2; GPU results in Sec. 6.3).
 //
 // The frequency vector a (n = v h entries) is a v x h grid, a(x, y) at
-// x h + y.  Row x is the polynomial f_x of degree < h with f_x(y) = a(x, y) at
-// the nodes y = 0..h-1; the proof is s(Y) = sum_x f_x(Y)^2 at Y = 0..2h-2.
-// The verifier keeps f_x(r) for a secret random r, accepts iff
-// s(r) = sum_x f_x(r)^2 and answers F2 = sum_{y<h} s(y).
+// x h + y.  Row x is the polynomial f_x of degree < h with f_x(w^y) = a(x, y),
+// w a generator of the subgroup of order h of F_p^*; the proof is
+// s(Y) = sum_x f_x(Y)^2 at the 2h points u^k (u of order 2h, u^2 = w).  The
+// verifier keeps f_x(r) for a secret random r, accepts iff
+// s(r) = sum_x f_x(r)^2 and answers F2 = sum_{k even} s(u^k).
 //
-// Prover.  Every row is extended to h - 1 more points independently (the
-// paper's per-row transform).  With the barycentric weights of the nodes,
-//   f_x(h + j) = C_j sum_y b_y / (h + j - y),  b_y = a(x, y) w_y,
-//   w_y = 1 / prod_{k != y} (y - k),  C_j = prod_{k<h} (h + j - k),
-// so a row's extension is a Toeplitz product of b with the table of
-// inverses 1/d, d = 1..2h-2: h (h - 1) multiply-adds per row, O(n h) in all,
-// done directly (no FFT).  A CTA takes SP_RB rows: their b values and the whole
-// inverse table sit in shared memory (the tiles are read in shared-memory
-// order, so the grid's layout in HBM never costs coalescing: Sec. 5.2's
-// column-major transpose is not needed); each thread owns four extension
-// points of all its CTA's rows, accumulating 128-bit products, then squares
-// and sums them over the rows.  A second launch sums the CTAs' column partials.
+// Prover (the paper's per-row transform by the Prime Factor FFT, Sec. 4.2).
+// The even points u^{2y} = w^y are the nodes: s there is the column's sum of
+// squares.  For the odd points u w^y: the row's coefficients are the inverse
+// DFT of its values over the subgroup of order h, c_j = (1/h) sum_y a_y w^{-jy},
+// and f(u w^y) = sum_j (c_j u^j) w^{jy} is a forward DFT of the twisted
+// coefficients.  h = q_1 ... q_m with pairwise coprime prime powers q_i <= 61,
+// so each DFT is an m-dimensional DFT with no twiddles between dimensions
+// (Good-Thomas): the input index n sits at digits (n t_i mod q_i), the output
+// index k at digits (k mod q_i), t_i = (h/q_i)^{-1} mod q_i, and the root of
+// dimension i is w^{h/q_i}.  A CTA holds one row at a time in shared memory and
+// runs each dimension as small DFTs along the innermost (contiguous) digit,
+// writing that digit outermost, so after m passes the digits are back in
+// order.  The host-built tables give every digit position's input slot, the
+// twist factor u^j / h with the slot of the forward transform, and the index
+// of every output; the CTA accumulates the squares of its rows per point and a
+// second launch sums the CTAs' partials.  Work per row: 2 h (q_1 + ... + q_m)
+// multiply-adds instead of the O(h^2) of a direct extension.
 //
-// Verifier.  A streaming pass per chunk of whole rows: f_x(r) = sum_y a(x, y)
-// L_y(r) with the Lagrange basis at r computed once; at the end s(r) by the
-// barycentric form over the 2h - 1 proof nodes.
+// Verifier.  f_x(r) = sum_y a(x, y) L_y(r) with the subgroup's Lagrange basis
+// L_y(r) = w^y (r^h - 1) / (h (r - w^y)), streamed over whole rows; at the end
+// s(r) = sum_k s_k u^k (r^{2h} - 1) / (2h (r - u^k)) over the 2h proof points
+// (an indicator basis when r lies in the subgroup).
 #include <cuda_runtime.h>
 
 #include "plan.h"
 
 #define SP_NT 256
-#define SP_RB 4   // rows per prover CTA
-#define SP_PT 4   // extension points per thread per pass
-#define SP_YT 1024  // y-tile of the rows' b values in shared memory
+#define SP_PNT 512  // prover CTA
 
-// prod_{k < cnt, k != skip} (m - k) for a canonical m (skip = cnt: no skip).
-__device__ u64 node_prod(u64 m, u64 cnt, u64 skip)
-{
-    u64 v = 1;
-    for (u64 k = 0; k < cnt; k++)
-        if (k != skip) v = f_mul(v, f_sub(m, k % FP_P));
-    return v;
-}
+// Geometry and tables of the prover's transform (device pointers; built on
+// the host by vc_f2sp_create).
+struct SpFft {
+    u32 h, m;             // h = q_0 ... q_{m-1}
+    u32 nroots;           // q_0 + ... + q_{m-1}
+    u32 q[8];             // dimension sizes, innermost last
+    u32 magic[8];         // ceil(2^20 / q): floor(i / q) = (i magic) >> 20 for i < 2^13
+    u32 twoff[8];         // offset of dimension i's roots in fw / bw
+    const u64 *fw, *bw;   // roots w_i^e and w_i^{-e}, e < q_i, per dimension
+    const u32 *pin;       // input slot of index y (digits y t_i mod q_i)
+    const u32 *perm;      // output slot P of the inverse DFT -> its input slot in the forward one
+    const u64 *twist;     // output slot P -> u^j / h (j the index at P)
+    const u32 *idx;       // output slot P -> its index j (k mod q_i digits)
+};
 
-// Tables of a node count h (every entry by a direct product):
-//   w[y]  = 1 / prod_{k<h, k != y} (y - k),             y < h
-//   C[j]  = prod_{k<h} (h + j - k),                      j < h - 1
-//   iv[d] = 1 / d,                                       d < 2h - 1 (iv[0] unused)
-//   w2[y] = 1 / prod_{k<2h-1, k != y} (y - k),           y < 2h - 1
-__global__ void __launch_bounds__(SP_NT) k_sp_tables(u64 h, u64 *w, u64 *C, u64 *iv, u64 *w2)
+// One pass of the multi-dimensional DFT: small DFTs of size q along the
+// innermost digit (lines of q consecutive slots), output digit written
+// outermost: out[k (h/q) + L] = sum_j in[L q + j] root^{jk}.
+__device__ __forceinline__ void sp_pass(const u64 *in, u64 *out, u32 h, u32 q, u32 magic, const u64 *roots)
 {
-    const u64 n2 = 2 * h - 1;
-    const u64 total = h + (h - 1) + n2 + n2;
-    for (u64 e = blockIdx.x * (u64)SP_NT + threadIdx.x; e < total; e += (u64)gridDim.x * SP_NT) {
-        if (e < h) {
-            w[e] = f_inv(node_prod(e, h, e));
-        } else if (e < 2 * h - 1) {
-            const u64 j = e - h;
-            C[j] = node_prod(h + j, h, h);
-        } else if (e < 2 * h - 1 + n2) {
-            const u64 d = e - (2 * h - 1);
-            iv[d] = d ? f_inv(d) : 0;
-        } else {
-            const u64 y = e - (2 * h - 1 + n2);
-            w2[y] = f_inv(node_prod(y, n2, y));
+    const u32 lines = h / q;
+    for (u32 i = threadIdx.x; i < h; i += SP_PNT) {
+        const u32 L = (u32)(((u64)i * magic) >> 20), k = i - L * q;
+        const u64 *src = in + L * q;
+        acc128 a;
+        acc_zero(a);
+        u32 e = 0;
+        for (u32 j = 0; j < q; j++) {  // q <= 61 products of a W value and a canonical root
+            mac(a, src[j], roots[e]);
+            e += k;
+            if (e >= q) e -= q;
         }
+        out[k * lines + L] = acc_red(a);
     }
 }
 
-// Column partials of the proof for the CTA's rows: part[cta][m], m < 2h - 1
-// (m < h: sum of a(x, m)^2; m = h + j: sum of f_x(h + j)^2).
-__global__ void __launch_bounds__(SP_NT, 2) k_sp_prove(const u64 *a, u64 v, u64 h, const u64 *w, const u64 *C,
-                                                    const u64 *iv, u64 *part, u32 *status)
+// Column partials of the proof for the CTA's rows x = blockIdx.x, +gridDim.x,
+// ...: part[cta][2y] = sum a(x, y)^2, part[cta][2y + 1] = sum f_x(u w^y)^2.
+__global__ void __launch_bounds__(SP_PNT, 1) k_sp_prove(const u64 *a, u64 v, SpFft F, u64 *part, u32 *status)
 {
     extern __shared__ u64 sp_dyn[];
-    const u64 n2 = 2 * h - 1;
-    u64 *s_iv = sp_dyn;        // 2h - 1 entries
-    u64 *s_b = sp_dyn + n2;    // SP_RB x SP_YT
-    const u64 x0 = (u64)blockIdx.x * SP_RB;
-    const u32 nrows = (u32)((v - x0) < SP_RB ? (v - x0) : SP_RB);
-    u64 *out = part + (u64)blockIdx.x * n2;
-    for (u64 d = threadIdx.x; d < n2; d += SP_NT) s_iv[d] = iv[d];
-    // original columns, and the canonical check of the CTA's entries
+    const u32 h = F.h, nt = F.nroots;
+    u64 *bufA = sp_dyn, *bufB = bufA + h, *acc_e = bufB + h, *acc_o = acc_e + h, *s_fw = acc_o + h, *s_bw = s_fw + nt;
+    for (u32 i = threadIdx.x; i < h; i += SP_PNT) acc_e[i] = acc_o[i] = 0;
+    for (u32 i = threadIdx.x; i < nt; i += SP_PNT) {
+        s_fw[i] = F.fw[i];
+        s_bw[i] = F.bw[i];
+    }
     bool bad = false;
-    for (u64 y = threadIdx.x; y < h; y += SP_NT) {
-        u64 s = 0;
-        for (u32 r = 0; r < nrows; r++) {
-            const u64 val = a[(x0 + r) * h + y];
+    for (u64 x = blockIdx.x; x < v; x += gridDim.x) {
+        __syncthreads();  // the previous row is done with the buffers
+        const u64 *row = a + x * h;
+        for (u32 y = threadIdx.x; y < h; y += SP_PNT) {
+            u64 val = row[y];
             bad |= val >= FP_P;
-            s = wred(s + wmul(val, val));
+            val = val >= FP_P ? 0 : val;
+            bufA[__ldg(F.pin + y)] = val;
+            acc_e[y] = wred(acc_e[y] + wmul(val, val));
         }
-        out[y] = wcanon(s);
-    }
-    if (__syncthreads_or(bad)) {
-        if (threadIdx.x == 0) atomicOr(status, ST_BAD_INPUT);
-        return;
-    }
-    // extension points h + j, j < h - 1, four per thread per pass
-    for (u64 j0 = 0; j0 < h - 1; j0 += (u64)SP_PT * SP_NT) {
-        acc128 acc[SP_RB][SP_PT];
-#pragma unroll
-        for (int r = 0; r < SP_RB; r++)
-#pragma unroll
-            for (int q = 0; q < SP_PT; q++) acc_zero(acc[r][q]);
-        for (u64 y0 = 0; y0 < h; y0 += SP_YT) {
-            const u64 yt = (h - y0) < SP_YT ? (h - y0) : SP_YT;
-            __syncthreads();  // the previous tile is consumed
-            for (u64 e = threadIdx.x; e < (u64)SP_RB * yt; e += SP_NT) {
-                const u32 r = (u32)(e / yt);
-                const u64 y = e - (u64)r * yt;
-                s_b[r * SP_YT + y] = (r < nrows) ? f_mul(a[(x0 + r) * h + y0 + y], w[y0 + y]) : 0;
-            }
+        __syncthreads();
+        u64 *cur = bufA, *nxt = bufB;
+        // inverse DFT: c_j (times h) at the digits of j
+        for (int d = (int)F.m - 1; d >= 0; d--) {
+            sp_pass(cur, nxt, h, F.q[d], F.magic[d], s_bw + F.twoff[d]);
             __syncthreads();
-            for (u64 y = 0; y < yt; y++) {
-                u64 ivq[SP_PT];
-#pragma unroll
-                for (int q = 0; q < SP_PT; q++) {
-                    const u64 j = j0 + threadIdx.x + (u64)q * SP_NT;
-                    ivq[q] = (j < h - 1) ? s_iv[h + j - (y0 + y)] : 0;  // h + j - y >= 1
-                }
-#pragma unroll
-                for (int r = 0; r < SP_RB; r++) {
-                    const u64 b = s_b[r * SP_YT + y];
-#pragma unroll
-                    for (int q = 0; q < SP_PT; q++) mac(acc[r][q], b, ivq[q]);
-                }
-                if ((y & 31) == 31) {  // 32 products of canonical values on a W value stay below 2^128
-#pragma unroll
-                    for (int r = 0; r < SP_RB; r++)
-#pragma unroll
-                        for (int q = 0; q < SP_PT; q++) {
-                            acc[r][q].lo = acc_red(acc[r][q]);
-                            acc[r][q].hi = 0;
-                        }
-                }
-            }
+            u64 *t = cur; cur = nxt; nxt = t;
         }
-#pragma unroll
-        for (int q = 0; q < SP_PT; q++) {
-            const u64 j = j0 + threadIdx.x + (u64)q * SP_NT;
-            if (j >= h - 1) continue;
-            const u64 cj = C[j];
-            u64 s = 0;
-#pragma unroll
-            for (int r = 0; r < SP_RB; r++) {
-                const u64 f = wmul(cj, acc_red(acc[r][q]));
-                s = wred(s + wmul(f, f));
-            }
-            out[h + j] = wcanon(s);
+        // twist by u^j / h, into the forward transform's input slots
+        for (u32 i = threadIdx.x; i < h; i += SP_PNT) nxt[__ldg(F.perm + i)] = wmul(cur[i], __ldg(F.twist + i));
+        __syncthreads();
+        { u64 *t = cur; cur = nxt; nxt = t; }
+        for (int d = (int)F.m - 1; d >= 0; d--) {
+            sp_pass(cur, nxt, h, F.q[d], F.magic[d], s_fw + F.twoff[d]);
+            __syncthreads();
+            u64 *t = cur; cur = nxt; nxt = t;
         }
+        // f(u w^j) at slot i, j = idx[i]: squares accumulated by slot
+        for (u32 i = threadIdx.x; i < h; i += SP_PNT) {
+            const u64 f = cur[i];
+            acc_o[i] = wred(acc_o[i] + wmul(f, f));
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_BAD_INPUT);
+    u64 *out = part + (u64)blockIdx.x * 2 * h;
+    for (u32 i = threadIdx.x; i < h; i += SP_PNT) {
+        out[2 * i] = wcanon(acc_e[i]);
+        out[2 * __ldg(F.idx + i) + 1] = wcanon(acc_o[i]);
     }
 }
 
-// proof[m] = sum over CTAs of part[cta][m].
+// proof[k] = sum over CTAs of part[cta][k].
 __global__ void __launch_bounds__(SP_NT) k_sp_reduce(const u64 *part, u32 nparts, u64 n2, u64 *proof)
 {
     for (u64 m = blockIdx.x * (u64)SP_NT + threadIdx.x; m < n2; m += (u64)gridDim.x * SP_NT) {
@@ -161,59 +138,53 @@ __global__ void __launch_bounds__(SP_NT) k_sp_reduce(const u64 *part, u32 nparts
     }
 }
 
-// Product of one canonical value per thread over the CTA (thread 0 returns it).
-__device__ u64 cta_prod(u64 x)
+__device__ u64 f_pow(u64 b, u64 e)
 {
-    __shared__ u64 s[SP_NT / 32];
-    x = warp_prod(x);
-    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = x;
-    __syncthreads();
     u64 r = 1;
-    if (threadIdx.x < 32) {
-        r = threadIdx.x < SP_NT / 32 ? s[threadIdx.x] : 1;
-        r = warp_prod(r);
+    while (e) {
+        if (e & 1) r = f_mul(r, b);
+        b = f_mul(b, b);
+        e >>= 1;
     }
-    __syncthreads();
     return r;
 }
 
-// Verifier setup (one CTA): r = the seed's first accepted draw; L[y] = L_y(r)
-// over the nodes 0..h-1 and M[y] = the basis at r over 0..2h-2; rows zeroed
-// by the other CTAs.  st[0] = r.
-__global__ void __launch_bounds__(SP_NT) k_sp_vbegin(u64 seed, u64 v, u64 h, const u64 *w, const u64 *w2, u64 *L,
-                                                     u64 *M, u64 *acc, u64 *st)
+// The verifier's secret point: the seed's first accepted draw.
+__device__ u64 sp_secret(u64 seed)
 {
-    if (blockIdx.x > 0) {
-        for (u64 x = (blockIdx.x - 1) * (u64)SP_NT + threadIdx.x; x < v; x += (u64)(gridDim.x - 1) * SP_NT) acc[x] = 0;
-        return;
-    }
-    u64 r = 0;
     for (u64 k = 1;; k++) {
-        r = splitmix64_at(seed, k) >> 3;
-        if (r != FP_P) break;
+        const u64 r = splitmix64_at(seed, k) >> 3;
+        if (r != FP_P) return r;
     }
-    const u64 n2 = 2 * h - 1;
-    // C(r) = prod_{k<h} (r - k), C2(r) = prod_{k<2h-1} (r - k)
-    u64 p1 = 1, p2 = 1;
-    for (u64 k = threadIdx.x; k < n2; k += SP_NT) {
-        const u64 f = f_sub(r, k);
-        p2 = f_mul(p2, f);
-        if (k < h) p1 = f_mul(p1, f);
-    }
-    const u64 c1 = cta_prod(p1), c2 = cta_prod(p2);
-    __shared__ u64 s_c[2];
-    if (threadIdx.x == 0) {
-        s_c[0] = c1;
-        s_c[1] = c2;
-        st[0] = r;
-    }
-    __syncthreads();
-    for (u64 y = threadIdx.x; y < n2; y += SP_NT) {
-        // r equal to a node: the basis is the indicator of that node
-        const bool at = (r == y);
-        const u64 inv = at ? 0 : f_inv(f_sub(r, y));
-        if (y < h) L[y] = (r < h) ? (at ? 1 : 0) : f_mul(f_mul(s_c[0], w[y]), inv);
-        M[y] = (r < n2) ? (at ? 1 : 0) : f_mul(f_mul(s_c[1], w2[y]), inv);
+}
+
+// Verifier setup, every CTA: r from the seed (res[0] = r, written by CTA 0);
+// L[y] = L_y(r) over the nodes pw[2y] (y < h) and M[k] = the basis at r over
+// the proof points pw[k] (k < 2h), grid-stride; row values zeroed.
+__global__ void __launch_bounds__(SP_NT) k_sp_vbegin(u64 seed, u64 v, u64 h, u64 inv_h, const u64 *pw, u64 *L,
+                                                     u64 *M, u64 *acc, u64 *res)
+{
+    const u64 r = sp_secret(seed);
+    const u64 gt = blockIdx.x * (u64)SP_NT + threadIdx.x, nth = (u64)gridDim.x * SP_NT;
+    if (gt == 0) res[0] = r;
+    for (u64 x = gt; x < v; x += nth) acc[x] = 0;
+    const u64 rh = f_pow(r, h), r2h = f_mul(rh, rh);
+    const u64 ch = f_mul(f_sub(rh, 1), inv_h);                        // (r^h - 1) / h
+    const u64 c2h = f_mul(f_mul(f_sub(r2h, 1), inv_h), FP_INV2);      // (r^2h - 1) / (2h)
+    for (u64 e = gt; e < 3 * h; e += nth) {
+        // e < h: node y = e (point pw[2y]); else proof point k = e - h
+        const bool node = e < h;
+        const u64 k = node ? 2 * e : e - h;
+        const u64 pt = pw[k];
+        const bool in_group = node ? (rh == 1) : (r2h == 1);
+        u64 val;
+        if (in_group) {
+            val = (r == pt) ? 1 : 0;  // r is a point of the set: indicator basis
+        } else {
+            val = f_mul(f_mul(pt, node ? ch : c2h), f_inv(f_sub(r, pt)));
+        }
+        if (node) L[e] = val;
+        else M[k] = val;
     }
 }
 
@@ -246,20 +217,20 @@ __global__ void __launch_bounds__(SP_NT) k_sp_vabsorb(const u64 *rows, u64 x0, u
     }
 }
 
-// Verifier end (one CTA): res[0] = accept, res[1] = F2 answer, res[2] = s(r),
-// res[3] = sum_x f_x(r)^2.
+// Verifier end (one CTA): res[0] = accept, res[1] = F2 answer (the even
+// points), res[2] = s(r), res[3] = sum_x f_x(r)^2.
 __global__ void __launch_bounds__(SP_NT) k_sp_vend(const u64 *proof, u64 v, u64 h, const u64 *M, const u64 *acc,
                                                    u64 *res)
 {
-    const u64 n2 = 2 * h - 1;
+    const u64 n2 = 2 * h;
     u64 lhs = 0, rhs = 0, ans = 0;
     bool bad = false;
     for (u64 x = threadIdx.x; x < v; x += SP_NT) lhs = wred(lhs + wmul(acc[x], acc[x]));
-    for (u64 y = threadIdx.x; y < n2; y += SP_NT) {
-        const u64 s = proof[y];
+    for (u64 k = threadIdx.x; k < n2; k += SP_NT) {
+        const u64 s = proof[k];
         bad |= s >= FP_P;
-        rhs = wred(rhs + wmul(s >= FP_P ? 0 : s, M[y]));
-        if (y < h) ans = wred(ans + (s >= FP_P ? 0 : s));
+        rhs = wred(rhs + wmul(s >= FP_P ? 0 : s, M[k]));
+        if ((k & 1) == 0) ans = wred(ans + (s >= FP_P ? 0 : s));
     }
     __shared__ u64 sh[3][SP_NT / 32];
     lhs = warp_wsum(lhs);
@@ -287,31 +258,42 @@ __global__ void __launch_bounds__(SP_NT) k_sp_vend(const u64 *proof, u64 v, u64 
     }
 }
 
-size_t sp_prove_smem(u64 h) { return (size_t)(2 * h - 1 + (u64)SP_RB * SP_YT) * sizeof(u64); }
-u32 sp_prove_ctas(u64 v) { return (u32)((v + SP_RB - 1) / SP_RB); }
+size_t sp_prove_smem(u64 h, u32 nroots) { return (size_t)(4 * h + 2 * nroots) * sizeof(u64); }
+
+u32 sp_prove_ctas(u64 v) { return (u32)(v < (u64)device_sms() ? v : (u64)device_sms()); }
 
 void sp_init()
 {
     cudaFuncSetAttribute(k_sp_prove, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
-void launch_sp_tables(u64 h, u64 *w, u64 *C, u64 *iv, u64 *w2, cudaStream_t st)
+void launch_sp_prove(const u64 *a, u64 v, const SpFftHost &H, u64 *part, u32 nparts, u64 *proof, u32 *status,
+                     cudaStream_t st)
 {
-    k_sp_tables<<<device_sms(), SP_NT, 0, st>>>(h, w, C, iv, w2);
+    SpFft F{};
+    F.h = H.h;
+    F.m = H.m;
+    F.nroots = H.nroots;
+    for (u32 i = 0; i < 8; i++) {
+        F.q[i] = H.q[i];
+        F.magic[i] = H.magic[i];
+        F.twoff[i] = H.twoff[i];
+    }
+    F.fw = H.fw;
+    F.bw = H.bw;
+    F.pin = H.pin;
+    F.perm = H.perm;
+    F.twist = H.twist;
+    F.idx = H.idx;
+    k_sp_prove<<<nparts, SP_PNT, sp_prove_smem(H.h, H.nroots), st>>>(a, v, F, part, status);
+    k_sp_reduce<<<(unsigned)((2 * H.h + SP_NT - 1) / SP_NT), SP_NT, 0, st>>>(part, nparts, 2 * H.h, proof);
 }
 
-void launch_sp_prove(const u64 *a, u64 v, u64 h, const u64 *w, const u64 *C, const u64 *iv, u64 *part, u64 *proof,
-                     u32 *status, cudaStream_t st)
-{
-    const u32 nc = sp_prove_ctas(v);
-    k_sp_prove<<<nc, SP_NT, sp_prove_smem(h), st>>>(a, v, h, w, C, iv, part, status);
-    k_sp_reduce<<<(unsigned)((2 * h - 1 + SP_NT - 1) / SP_NT), SP_NT, 0, st>>>(part, nc, 2 * h - 1, proof);
-}
-
-void launch_sp_vbegin(u64 seed, u64 v, u64 h, const u64 *w, const u64 *w2, u64 *L, u64 *M, u64 *acc, u64 *res,
+void launch_sp_vbegin(u64 seed, u64 v, u64 h, u64 inv_h, const u64 *pw, u64 *L, u64 *M, u64 *acc, u64 *res,
                       cudaStream_t st)
 {
-    k_sp_vbegin<<<1 + device_sms(), SP_NT, 0, st>>>(seed, v, h, w, w2, L, M, acc, res);
+    k_sp_vbegin<<<grid_for_items(3 * h > v ? 3 * h : v, SP_NT, 4), SP_NT, 0, st>>>(seed, v, h, inv_h, pw, L, M, acc,
+                                                                                  res);
 }
 
 void launch_sp_vabsorb(const u64 *rows, u64 x0, u64 nrows, u64 h, const u64 *L, u64 *acc, u32 *status,

@@ -398,14 +398,22 @@ void launch_pergate(const Globals *G, const PgLayer *pl, int nl, const u32 *blk_
                     const u32 *lblk_layer, u32 nlblk, u32 nrounds, cudaStream_t st);
 u32 pergate_gpt();  // gates (and line entries) per CTA
 
-// Special-purpose non-interactive F2 protocol (k_f2sp.cu).
+// Special-purpose non-interactive F2 protocol (k_f2sp.cu).  The prover's
+// transform (built by vc_f2sp_create): h = q_0 ... q_{m-1}, pairwise coprime
+// prime powers <= 61; device tables.
+struct SpFftHost {
+    u32 h, m, nroots;
+    u32 q[8], magic[8], twoff[8];
+    const u64 *fw, *bw;      // per dimension: its root's powers and inverse powers
+    const u32 *pin, *perm, *idx;
+    const u64 *twist;
+};
 void sp_init();
-size_t sp_prove_smem(u64 h);
+size_t sp_prove_smem(u64 h, u32 nroots);
 u32 sp_prove_ctas(u64 v);
-void launch_sp_tables(u64 h, u64 *w, u64 *C, u64 *iv, u64 *w2, cudaStream_t st);
-void launch_sp_prove(const u64 *a, u64 v, u64 h, const u64 *w, const u64 *C, const u64 *iv, u64 *part, u64 *proof,
-                     u32 *status, cudaStream_t st);
-void launch_sp_vbegin(u64 seed, u64 v, u64 h, const u64 *w, const u64 *w2, u64 *L, u64 *M, u64 *acc, u64 *res,
+void launch_sp_prove(const u64 *a, u64 v, const SpFftHost &H, u64 *part, u32 nparts, u64 *proof, u32 *status,
+                     cudaStream_t st);
+void launch_sp_vbegin(u64 seed, u64 v, u64 h, u64 inv_h, const u64 *pw, u64 *L, u64 *M, u64 *acc, u64 *res,
                       cudaStream_t st);
 void launch_sp_vabsorb(const u64 *rows, u64 x0, u64 nrows, u64 h, const u64 *L, u64 *acc, u32 *status,
                        cudaStream_t st);

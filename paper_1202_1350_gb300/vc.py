@@ -347,11 +347,29 @@ def vc_f2sp_destroy(s):
     _check(lib().vc_f2sp_destroy(s), "vc_f2sp_destroy")
 
 
+F2SP_FACTORS = (9, 3, 25, 5, 7, 11, 13, 31, 41, 61)
+
+
+def f2sp_valid_h(h: int) -> bool:
+    """h of the special-purpose protocol: a product of distinct members of
+    {3 or 9, 5 or 25, 7, 11, 13, 31, 41, 61}, at most VC_F2SP_MAX_H (7000)."""
+    if h < 1 or h > 7000 or (P - 1) % (2 * h):
+        return False
+    for pr in (3, 5, 7, 11, 13, 31, 41, 61):
+        pp = 1
+        while h % pr == 0:
+            h //= pr
+            pp *= pr
+        if pp > 61:
+            return False
+    return h == 1
+
+
 def vc_f2sp_prove(s, a, proof, stream=None, device: int = 0):
-    """proof: 2h - 1 entries (host or device), written synchronously."""
+    """proof: 2h entries (host or device), written synchronously."""
     v, h = _shapes[("f2sp", s)]
     _need(a, v * h, "a")
-    _need(proof, 2 * h - 1, "proof")
+    _need(proof, 2 * h, "proof")
     _check(lib().vc_f2sp_prove(s, _ptr(a), _ptr(proof), _stream(stream, device)), "vc_f2sp_prove")
     return proof
 
@@ -370,7 +388,7 @@ def vc_f2sp_verify_absorb(s, rows, first_row: int, nrows: int, stream=None, devi
 def vc_f2sp_verify_end(s, proof, stream=None, device: int = 0):
     """Returns (accept, F2 answer)."""
     v, h = _shapes[("f2sp", s)]
-    _need(proof, 2 * h - 1, "proof")
+    _need(proof, 2 * h, "proof")
     f2 = ctypes.c_uint64()
     acc = ctypes.c_int()
     _check(lib().vc_f2sp_verify_end(s, _ptr(proof), ctypes.byref(f2), ctypes.byref(acc), _stream(stream, device)),

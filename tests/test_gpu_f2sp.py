@@ -26,10 +26,10 @@ def dev(x):
 
 def gpu_proof(s, a, h, host=False):
     if host:
-        out = np.zeros(2 * h - 1, np.uint64)
+        out = np.zeros(2 * h, np.uint64)
         vc.vc_f2sp_prove(s, np.ascontiguousarray(a), out)
         return out
-    out = torch.empty(2 * h - 1, dtype=torch.int64, device="cuda")
+    out = torch.empty(2 * h, dtype=torch.int64, device="cuda")
     vc.vc_f2sp_prove(s, dev(a), out)
     return to_np(out)
 
@@ -43,7 +43,9 @@ def gpu_verify(s, a, v, h, seed, proof, chunk=None):
     return vc.vc_f2sp_verify_end(s, dev(proof))
 
 
-SHAPES = [(1, 1), (1, 2), (3, 4), (8, 8), (5, 31), (64, 64), (17, 130), (2, 300), (300, 3)]
+# h: one and several transform dimensions, every allowed prime power
+SHAPES = [(1, 1), (1, 3), (3, 5), (8, 9), (5, 31), (64, 63), (17, 143), (2, 315), (300, 3), (7, 25), (3, 41 * 3),
+          (2, 61 * 5), (4, 1001)]
 
 
 @pytest.mark.parametrize("v,h", SHAPES)
@@ -58,7 +60,7 @@ def test_proof_equals_oracle(v, h):
         vc.vc_f2sp_destroy(s)
 
 
-@pytest.mark.parametrize("v,h", [(1, 1), (3, 4), (8, 8), (64, 64), (17, 130)])
+@pytest.mark.parametrize("v,h", [(1, 1), (3, 5), (8, 9), (64, 63), (17, 143)])
 def test_verifier_equals_oracle(v, h):
     a = I.uniform_ints(2000 + v + h, v * h, 1 << 16)
     s = vc.vc_f2sp_create(v, h)
@@ -68,7 +70,7 @@ def test_verifier_equals_oracle(v, h):
             got = gpu_verify(s, a, v, h, seed, proof, chunk=max(1, v // 3))
             assert got == oracle.f2sp_verify(a, v, h, seed, proof)
             assert got[0]
-        for m in (0, h - 1, 2 * h - 2):
+        for m in (0, 1, h - 1, 2 * h - 1):
             bad = proof.copy()
             bad[m] = (int(bad[m]) + 5) % P
             got = gpu_verify(s, a, v, h, 7, bad)
@@ -78,21 +80,40 @@ def test_verifier_equals_oracle(v, h):
         vc.vc_f2sp_destroy(s)
 
 
+def _odd_point_direct(a, v, h, y):
+    """s(u w^y) from f_x(u w^y) = sum_j a(x, j) L_j(u w^y) with the subgroup's
+    Lagrange basis L_j(X) = w^j (X^h - 1) / (h (X - w^j)) (big integers): a
+    check independent of the prover's transform."""
+    u = oracle.f2sp_root(h)
+    w = u * u % P
+    X = u * pow(w, y, P) % P
+    c = (pow(X, h, P) - 1) * pow(h, -1, P) % P
+    basis = [pow(w, j, P) * c * pow((X - pow(w, j, P)) % P, -1, P) % P for j in range(h)]
+    total = 0
+    for x in range(v):
+        f = sum(int(a[x * h + j]) * basis[j] for j in range(h)) % P
+        total += f * f
+    return total % P
+
+
 def test_bench_size_closed_form():
-    """n = 2^20 as a 1024 x 1024 grid: the answer is sum a_i^2 (big integers)
-    and the honest proof is accepted at several secret points; a changed
-    entry anywhere is rejected."""
-    v = h = 1024
-    a = I.f2_inputs(20, 1 << 16, 5)
+    """n ~ 2^20 as a 1048 x 1001 grid (1001 = 7 11 13): the answer is sum a_i^2
+    (big integers), the even points are the columns' sums of squares, sampled
+    odd points equal a direct evaluation, the honest proof is accepted at
+    several secret points and a changed entry anywhere is rejected."""
+    v, h = 1048, 1001
+    a = I.uniform_ints(5, v * h, 1 << 16)
     s = vc.vc_f2sp_create(v, h)
     try:
         proof = gpu_proof(s, a, h)
         f2 = int((a.astype(object) ** 2).sum()) % P
         grid = a.astype(object).reshape(v, h)
-        assert [int(t) for t in proof[:h]] == [int(c) % P for c in (grid ** 2).sum(axis=0)]
+        assert [int(t) for t in proof[0::2]] == [int(c) % P for c in (grid ** 2).sum(axis=0)]
+        for y in (0, 500, h - 1):
+            assert int(proof[2 * y + 1]) == _odd_point_direct(a, v, h, y)
         for seed in (3, 4, 5):
             assert gpu_verify(s, a, v, h, seed, proof, chunk=300) == (True, f2)
-        for m in (5, h + 7, 2 * h - 2):
+        for m in (5, h + 8, 2 * h - 1):
             bad = proof.copy()
             bad[m] = (int(bad[m]) + 1) % P
             assert not gpu_verify(s, a, v, h, 3, bad)[0]
@@ -100,44 +121,48 @@ def test_bench_size_closed_form():
         vc.vc_f2sp_destroy(s)
 
 
-def test_rows_longer_than_one_tile():
-    """h above the prover's 1024-entry shared-memory tile (the oracle is too
-    slow here): the first h proof entries are the columns' sums of squares and
-    the verifier, equal to the oracle's at small sizes, accepts the proof at
-    several secret points and rejects a changed extension value."""
-    v, h = 3, 2100
+def test_paper_row_length():
+    """h = 5005 = 5 7 11 13 (the paper's 25-million-entry rows of about 5000
+    entries; the oracle is too slow here): even points are the columns' sums
+    of squares, sampled odd points equal a direct evaluation, the verifier
+    (equal to the oracle's at small sizes) accepts at several secret points
+    and rejects a changed extension value."""
+    v, h = 3, 5005
     a = I.uniform_ints(31, v * h, 1 << 16)
     s = vc.vc_f2sp_create(v, h)
     try:
         proof = gpu_proof(s, a, h)
         grid = a.astype(object).reshape(v, h)
-        assert [int(t) for t in proof[:h]] == [int(c) % P for c in (grid ** 2).sum(axis=0)]
+        assert [int(t) for t in proof[0::2]] == [int(c) % P for c in (grid ** 2).sum(axis=0)]
+        for y in (0, 1, 1234, h - 1):
+            assert int(proof[2 * y + 1]) == _odd_point_direct(a, v, h, y)
         for seed in (1, 2, 3):
             assert gpu_verify(s, a, v, h, seed, proof)[0]
         bad = proof.copy()
-        bad[h + 1500] = (int(bad[h + 1500]) + 1) % P
+        bad[2 * 1500 + 1] = (int(bad[2 * 1500 + 1]) + 1) % P
         assert not gpu_verify(s, a, v, h, 1, bad)[0]
     finally:
         vc.vc_f2sp_destroy(s)
 
 
 def test_bad_inputs():
-    s = vc.vc_f2sp_create(4, 4)
+    s = vc.vc_f2sp_create(4, 5)
     try:
-        a = I.uniform_ints(9, 16, 100)
+        a = I.uniform_ints(9, 20, 100)
         a[3] = P
         with pytest.raises(vc.VcError) as e:
-            gpu_proof(s, a, 4)
+            gpu_proof(s, a, 5)
         assert e.value.status == vc.VC_EINVAL
         with pytest.raises(vc.VcError) as e:
-            gpu_verify(s, a, 4, 4, 1, oracle.f2sp_prove(I.uniform_ints(9, 16, 100), 4, 4))
+            gpu_verify(s, a, 4, 5, 1, oracle.f2sp_prove(I.uniform_ints(9, 20, 100), 4, 5))
         assert e.value.status == vc.VC_EINVAL
-        good = I.uniform_ints(10, 16, 100)
-        proof = gpu_proof(s, good, 4)  # the context is usable again
-        assert (proof == oracle.f2sp_prove(good, 4, 4)).all()
+        good = I.uniform_ints(10, 20, 100)
+        proof = gpu_proof(s, good, 5)  # the context is usable again
+        assert (proof == oracle.f2sp_prove(good, 4, 5)).all()
     finally:
         vc.vc_f2sp_destroy(s)
-    with pytest.raises(vc.VcError):
-        vc.vc_f2sp_create(4, 0)
-    with pytest.raises(vc.VcError):
-        vc.vc_f2sp_create(4, 9000)
+    # h must be a product of distinct members of {3|9, 5|25, 7, 11, 13, 31, 41, 61}, at most 7000
+    for h in (0, 2, 4, 27, 125, 151, 9009, 7007 * 3):
+        assert not vc.f2sp_valid_h(h)
+        with pytest.raises(vc.VcError):
+            vc.vc_f2sp_create(4, h)
