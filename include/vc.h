@@ -106,18 +106,21 @@ vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, vc_circuit 
  * Everything else stays in device memory and the transcript is unchanged. */
 #define VC_VALUES_IN_HOST_MEMORY 1u
 
-/* With VC_VALUES_STAGED the values of every layer live in page-locked host
- * memory and the device holds three slots of the widest layer's size that
- * the layers rotate through (Sec. 5.1.2, copy-once-per-layer: a layer
+/* With VC_VALUES_STAGED the values of the wide layers (more than a quarter
+ * of the widest) live in page-locked host memory and pass through
+ * W = min(8, number of wide layers) device slots of the widest layer's size;
+ * narrow layers stay on the device (Sec. 5.1.2, copy-once-per-layer: a layer
  * iteration needs only layers i and i+1 on the device).  A proof evaluates
- * the circuit layer by layer from the input up, writing each layer to host
- * memory once as soon as it is computed, then runs the layer iterations in
- * order 0..d-1, each on its two layers; the next layer is copied in while the
- * current one is proved (layers 0, 1 and 2 are still on the device after
- * the evaluation).  Device memory for values: 3 S_max u64 instead of
- * S_0 + ... + S_d.  Structured wirings only (EXPLICIT: VC_EINVAL); such a
- * circuit cannot join a batch (vc_batch_create: VC_EINVAL) or use
- * vc_prove_pergate (VC_EINVAL).  The transcript is unchanged. */
+ * the circuit layer by layer from the input up, writing each wide layer to
+ * host memory once as soon as it is computed; then it runs every iteration
+ * between narrow layers together, and the iterations that touch a wide layer
+ * in order, in groups whose wide layers fit the slots, copying each group's
+ * missing layers in from host memory once the slots' previous layers are no
+ * longer needed.  Device memory for values: W S_max u64 plus the narrow
+ * layers, instead of S_0 + ... + S_d.  Structured wirings only (EXPLICIT:
+ * VC_EINVAL); such a circuit cannot join a batch (vc_batch_create:
+ * VC_EINVAL) or use vc_prove_pergate (VC_EINVAL).  The transcript is
+ * unchanged. */
 #define VC_VALUES_STAGED 2u
 
 /* vc_circuit_create with residency flags (0, VC_VALUES_IN_HOST_MEMORY or
@@ -255,6 +258,10 @@ typedef struct {
     uint32_t wave_tasks;         /* chunks in the first persistent wave launch    */
     uint32_t verify2_launches;   /* kernel launches per vc_verify_input +
                                     vc_verify_transcript                          */
+    uint64_t link_bytes;         /* VC_VALUES_STAGED: layer-value bytes one
+                                    vc_prove moves over the host link (each wide
+                                    layer written once, plus the layers copied
+                                    back in); 0 otherwise                         */
 } vc_circuit_info;
 
 vc_status vc_circuit_get_info(const vc_circuit *c, vc_circuit_info *info);

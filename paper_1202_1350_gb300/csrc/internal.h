@@ -45,6 +45,9 @@ cudaError_t lib_host_alloc(T **p, size_t n, unsigned flags)
     return lib_host_alloc(reinterpret_cast<void **>(p), n, flags);
 }
 
+// Device slots of the wide layers of a circuit with staged values.
+constexpr u32 STAGED_SLOTS = 8;
+
 // Which layers' phase-2/3 tables are built by k_build23 (the rest are formed
 // on the fly or never stored).
 inline bool needs_tables(u32 kind) { return kind != W_SQUARE && kind != W_TREE; }
@@ -207,11 +210,18 @@ struct vc_circuit {
     // VC_VALUES_STAGED: every layer in page-locked host memory (hV), V[i] =
     // device slot i mod 3; per-layer task lists of the wave launches (groups
     // A and B), table builds and launch counters; a copy stream and events
-    std::vector<u64 *> hV;
+    std::vector<u64 *> hV;        // wide layers only
+    std::vector<int> st_slot;     // per layer: its slot (wide layers) or -1 (kept on the device)
+    u32 st_nslots = 0;            // W
+    u64 st_link_bytes = 0;        // host-link bytes of one proof
+    std::vector<int> st_group;    // per iteration: its group, or -1 (between narrow layers)
+    std::vector<std::pair<u32, u32>> st_groups;  // first and last iteration of each group
     u64 *d_out = nullptr;  // copy of the outputs for the final reduction
-    std::vector<std::vector<std::vector<Task>>> stA, stB;  // [layer][group]
+    std::vector<std::vector<std::vector<Task>>> stA, stB;  // [list][wave group]: list g < ng = iteration
+                                                          // group g, list ng = every iteration between
+                                                          // narrow layers
     std::vector<std::vector<Task *>> d_stA, d_stB;
-    std::vector<std::vector<BuildItem>> stBuild;  // [layer]
+    std::vector<std::vector<BuildItem>> stBuild;  // [list]
     std::vector<BuildItem *> d_stBuild;
     std::vector<std::vector<Item>> stEval;  // [layer]: 256-gate blocks of k_eval_layer
     std::vector<Item *> d_stEval;

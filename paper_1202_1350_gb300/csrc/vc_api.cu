@@ -210,6 +210,33 @@ static void plan_eval(vc_circuit *c)
 // Staged values: the plan's wave tasks, table builds and evaluation blocks
 // split by layer iteration (each layer's launches run while only its two
 // layers are on the device), with their device arrays and launch counters.
+// The copies into the slots that a staged proof makes after the evaluation,
+// in order: group g needs layer L, which replaces layer prev (-1: none) in
+// its slot.  After the evaluation each slot holds the last wide layer
+// evaluated into it; a group's wide layers missing from their slots are
+// copied in before it runs.
+struct StagedCopy {
+    u32 group, layer;
+    int prev;
+};
+
+static std::vector<StagedCopy> staged_copies(const vc_circuit &c)
+{
+    const u32 d = c.d;
+    auto wide = [&](u32 i) { return c.st_slot[i] >= 0; };
+    std::vector<int> holder(c.st_nslots, -1);
+    for (int i = (int)d; i >= 0; i--)
+        if (wide(i)) holder[c.st_slot[i]] = i;
+    std::vector<StagedCopy> out;
+    for (u32 g = 0; g < c.st_groups.size(); g++)
+        for (u32 L = c.st_groups[g].first; L <= c.st_groups[g].second + 1; L++) {
+            if (!wide(L) || holder[c.st_slot[L]] == (int)L) continue;
+            out.push_back({g, L, holder[c.st_slot[L]]});
+            holder[c.st_slot[L]] = (int)L;
+        }
+    return out;
+}
+
 static void staged_partition(vc_circuit *c, Arena &A)
 {
     Plan &P = c->P;
@@ -218,19 +245,49 @@ static void staged_partition(vc_circuit *c, Arena &A)
         return t.type == TK_LINE ? P.lw[t.wave].layer
                                  : (t.type == TK_PROD ? P.scis[P.pw[t.wave].sci].layer : P.gw[t.wave].layer);
     };
+    // Iterations touching a wide layer form groups, in order, each as long as
+    // its wide layers (consecutive in wide order, so in distinct slots) number
+    // at most W; group g is launch list g.  Every iteration between narrow
+    // layers goes to the last list (ng), run first.
+    const auto wide = [&](u32 i) { return c->st_slot[i] >= 0; };
+    c->st_group.assign(d, -1);
+    c->st_groups.clear();
+    {
+        int lo_ord = -1, hi_ord = -1;  // the current group's wide layers, by ordinal
+        std::vector<int> ordinal(d + 1, -1);
+        int o = 0;
+        for (u32 i = 0; i <= d; i++)
+            if (wide(i)) ordinal[i] = o++;
+        for (u32 i = 0; i < d; i++) {
+            if (!wide(i) && !wide(i + 1)) continue;
+            const int a = wide(i) ? ordinal[i] : ordinal[i + 1], b = wide(i + 1) ? ordinal[i + 1] : ordinal[i];
+            if (c->st_groups.empty() || std::max(hi_ord, b) - std::min(lo_ord, a) + 1 > (int)c->st_nslots) {
+                c->st_groups.push_back({i, i});
+                lo_ord = a;
+                hi_ord = b;
+            } else {
+                c->st_groups.back().second = i;
+                lo_ord = std::min(lo_ord, a);
+                hi_ord = std::max(hi_ord, b);
+            }
+            c->st_group[i] = (int)c->st_groups.size() - 1;
+        }
+    }
+    const u32 ng = (u32)c->st_groups.size();
+    auto list_of = [&](u32 i) { return c->st_group[i] < 0 ? ng : (u32)c->st_group[i]; };
     auto split = [&](const std::vector<std::vector<Task>> &grp, std::vector<std::vector<std::vector<Task>>> &dst) {
-        dst.assign(d, {});
+        dst.assign(ng + 1, {});
         for (size_t g = 0; g < grp.size(); g++)
             for (const Task &t : grp[g]) {
-                auto &v = dst[layer_of(t)];
+                auto &v = dst[list_of(layer_of(t))];
                 if (v.size() <= g) v.resize(g + 1);
                 v[g].push_back(t);
             }
     };
     split(P.groupsA, c->stA);
     split(P.groupsB, c->stB);
-    c->stBuild.assign(d, {});
-    for (const BuildItem &b : P.builds) c->stBuild[b.layer].push_back(b);
+    c->stBuild.assign(ng + 1, {});
+    for (const BuildItem &b : P.builds) c->stBuild[list_of(b.layer)].push_back(b);
     c->stEval.assign(d, {});
     for (u32 i = 0; i < d; i++) {
         const u64 blocks = ((u64(1) << c->s[i]) + 255) / 256;
@@ -244,19 +301,23 @@ static void staged_partition(vc_circuit *c, Arena &A)
     };
     take_lists(c->stA, c->d_stA);
     take_lists(c->stB, c->d_stB);
-    c->d_stBuild.assign(d, nullptr);
+    c->d_stBuild.assign(ng + 1, nullptr);
     c->d_stEval.assign(d, nullptr);
-    for (u32 i = 0; i < d; i++) {
-        c->d_stBuild[i] = A.take<BuildItem>(c->stBuild[i].size() + 1);
-        c->d_stEval[i] = A.take<Item>(c->stEval[i].size() + 1);
-    }
-    c->stctr_off.assign(d, 0);
+    for (u32 l = 0; l <= ng; l++) c->d_stBuild[l] = A.take<BuildItem>(c->stBuild[l].size() + 1);
+    for (u32 i = 0; i < d; i++) c->d_stEval[i] = A.take<Item>(c->stEval[i].size() + 1);
+    c->stctr_off.assign(ng + 1, 0);
     u32 nctr = 0;
-    for (u32 i = 0; i < d; i++) {
+    for (u32 i = 0; i <= ng; i++) {
         c->stctr_off[i] = nctr;
         nctr += 2 * (u32)(c->stA[i].size() + c->stB[i].size());
     }
-    c->d_stctr = A.take<u32>(nctr + 2);  // layer i's launch g: counters stctr_off[i] + 2 g, + 1
+    c->d_stctr = A.take<u32>(nctr + 2);  // list l's launch g: counters stctr_off[l] + 2 g, + 1
+    // host-link traffic of one proof: every wide layer written once, plus
+    // the copies back in
+    c->st_link_bytes = 0;
+    for (u32 i = 0; i <= d; i++)
+        if (wide(i)) c->st_link_bytes += (u64(1) << c->s[i]) * sizeof(u64);
+    for (const StagedCopy &k : staged_copies(*c)) c->st_link_bytes += (u64(1) << c->s[k.layer]) * sizeof(u64);
 }
 
 static cudaError_t staged_upload(vc_circuit *c)
@@ -268,12 +329,10 @@ static cudaError_t staged_upload(vc_circuit *c)
         for (size_t g = 0; e == cudaSuccess && g < c->stA[i].size(); g++) e = upload(c->d_stA[i][g], c->stA[i][g]);
     for (size_t i = 0; e == cudaSuccess && i < c->stB.size(); i++)
         for (size_t g = 0; e == cudaSuccess && g < c->stB[i].size(); g++) e = upload(c->d_stB[i][g], c->stB[i][g]);
-    for (u32 i = 0; e == cudaSuccess && i < c->d; i++) {
-        e = upload(c->d_stBuild[i], c->stBuild[i]);
-        if (e == cudaSuccess) e = upload(c->d_stEval[i], c->stEval[i]);
-    }
+    for (size_t l = 0; e == cudaSuccess && l < c->stBuild.size(); l++) e = upload(c->d_stBuild[l], c->stBuild[l]);
+    for (u32 i = 0; e == cudaSuccess && i < c->d; i++) e = upload(c->d_stEval[i], c->stEval[i]);
     u32 nctr = 0;
-    for (u32 i = 0; i < c->d; i++) nctr += 2 * (u32)(c->stA[i].size() + c->stB[i].size());
+    for (size_t l = 0; l < c->stA.size(); l++) nctr += 2 * (u32)(c->stA[l].size() + c->stB[l].size());
     if (e == cudaSuccess) e = cudaMemset(c->d_stctr, 0, sizeof(u32) * (nctr + 2));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->st_copy, cudaStreamNonBlocking);
     c->st_ev.assign(4 * (c->d + 1), nullptr);
@@ -301,15 +360,28 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     c->V.assign(d + 1, nullptr);
     c->hV.assign(staged ? d + 1 : 0, nullptr);
     if (staged) {
-        // every layer in page-locked host memory; three device slots of the
-        // widest layer's size, layer i in slot i mod 3
+        // wide layers (more than a quarter of the widest) in page-locked host
+        // memory, passing through W = min(VC_STAGED_SLOTS, wide layers)
+        // device slots of the widest layer's size (the k-th wide layer in
+        // slot k mod W); narrow layers stay on the device
         u64 smax = 1;
+        u32 nwide = 0;
         for (u32 i = 0; i <= d; i++) smax = std::max(smax, S(i));
-        u64 *slot[3];
-        for (int k = 0; k < 3; k++) slot[k] = A.take<u64>(smax);
+        for (u32 i = 0; i <= d; i++) nwide += (4 * S(i) > smax) ? 1 : 0;
+        const u32 W = std::min<u32>(STAGED_SLOTS, nwide);
+        c->st_nslots = W;
+        std::vector<u64 *> slot(W);
+        for (u32 k = 0; k < W; k++) slot[k] = A.take<u64>(smax);
+        c->st_slot.assign(d + 1, -1);
+        int ord = 0;
         for (u32 i = 0; i <= d; i++) {
-            c->V[i] = slot[i % 3];
-            c->hV[i] = H.take<u64>(S(i));
+            if (4 * S(i) > smax) {
+                c->st_slot[i] = ord % (int)W;
+                c->V[i] = slot[ord++ % W];
+                c->hV[i] = H.take<u64>(S(i));
+            } else {
+                c->V[i] = A.take<u64>(S(i));
+            }
         }
         c->d_out = A.take<u64>(S(0));
     } else {
@@ -1078,14 +1150,17 @@ static cudaError_t set_node_args(cudaGraphExec_t exec, cudaGraphNode_t node, cud
 // again after the stage events change).  A plan with its own parameter node
 // gets (seed, tr, in) through it.
 // The launches and copies of one proof of a circuit with staged values
-// (Sec. 5.1.2, copy-once-per-layer).  Evaluation runs layer by layer from
-// the input up, layer i in slot i mod 3; each layer is written to host memory
-// on the copy stream as soon as it is computed, and a layer reuses a slot
-// only after the host copy of the layer three above it is done.  Then the
-// layer iterations run in order 0..d-1, iteration i on slots i mod 3 and
-// (i+1) mod 3 (layers 0..2 are still in their slots); while iteration i runs,
-// layer i+2 is copied from host memory into the slot iteration i-1 has
-// released.  Coins and the final reduction are those of the resident plan.
+// (Sec. 5.1.2, copy-once-per-layer).  Narrow layers stay on the device; wide
+// layers pass through three slots.  Evaluation runs layer by layer from the
+// input up; each wide layer is written to host memory on the copy stream as
+// soon as it is computed, and a wide layer reuses a slot only after the host
+// copy of the slot's previous layer is done.  Then every iteration between
+// narrow layers runs in one merged set of launches, and the iterations that
+// touch a wide layer run one after the other in order, each on its two
+// layers: a wide layer missing from its slot is copied in from host memory,
+// ahead of time (while the previous iteration runs) when the slot's previous
+// layer is no longer needed by then.  Coins and the final reduction are
+// those of the resident plan.
 static void enqueue_staged(vc_circuit &c, cudaStream_t st)
 {
     Plan &P = c.P;
@@ -1095,44 +1170,67 @@ static void enqueue_staged(vc_circuit &c, cudaStream_t st)
     enum { EVALUATED = 0, ON_HOST = 1, COPIED_IN = 2, PROVED = 3 };
     auto ev = [&](u32 i, int k) { return c.st_ev[4 * i + k]; };
     auto bytes = [&](u32 i) { return (u64(1) << c.s[i]) * sizeof(u64); };
+    auto wide = [&](u32 i) { return c.st_slot[i] >= 0; };
+    auto run_list = [&](u32 l) {  // the launches of list l (a group of iterations, or the narrow ones)
+        for (size_t g = 0; g < c.stA[l].size(); g++)
+            launch_waves(Gs, P.d_lw, P.d_pw, P.d_gw, c.d_stA[l][g], (int)c.stA[l][g].size(),
+                         c.d_stctr + c.stctr_off[l] + 2 * g, st);
+        if (!c.stBuild[l].empty()) launch_build23(Gs, c.d_stBuild[l], (int)c.stBuild[l].size(), st);
+        for (size_t g = 0; g < c.stB[l].size(); g++)
+            launch_waves(Gs, P.d_lw, P.d_pw, P.d_gw, c.d_stB[l][g], (int)c.stB[l][g].size(),
+                         c.d_stctr + c.stctr_off[l] + 2 * (c.stA[l].size() + g), st);
+    };
     launch_params(P.d_G, 0, nullptr, nullptr, st);  // arguments set per launch
     cudaEventRecord(P.ev_fork, st);
     cudaStreamWaitEvent(sa, P.ev_fork, 0);
     launch_coins(Gs, P.ncirc, P.d_eqjobs, (int)P.eqjobs.size(), P.d_scis, P.d_pw, (int)P.pw.size(), sa);
     cudaEventRecord(P.ev_tables, sa);
-    // the inputs (copied into slot d mod 3 by the caller): checked, then to host memory
-    launch_check_inputs(Gs, P.d_checks, (int)P.checks.size(), st);
-    cudaEventRecord(ev(d, EVALUATED), st);
-    cudaStreamWaitEvent(cp, ev(d, EVALUATED), 0);
-    cudaMemcpyAsync(c.hV[d], c.V[d], bytes(d), cudaMemcpyDeviceToHost, cp);
-    cudaEventRecord(ev(d, ON_HOST), cp);
-    for (int i = (int)d - 1; i >= 0; i--) {
-        if ((u32)i + 3 <= d) cudaStreamWaitEvent(st, ev(i + 3, ON_HOST), 0);
-        launch_eval_layers(Gs, c.d_stLev, c.d_stEval[i], (int)c.stEval[i].size(), st);
+    // evaluation; holder[s] = the wide layer in slot s (-1: none yet)
+    std::vector<int> holder(c.st_nslots, -1);
+    auto to_host = [&](u32 i) {
         cudaEventRecord(ev(i, EVALUATED), st);
         cudaStreamWaitEvent(cp, ev(i, EVALUATED), 0);
         cudaMemcpyAsync(c.hV[i], c.V[i], bytes(i), cudaMemcpyDeviceToHost, cp);
         cudaEventRecord(ev(i, ON_HOST), cp);
+    };
+    launch_check_inputs(Gs, P.d_checks, (int)P.checks.size(), st);  // the inputs are in layer d
+    if (wide(d)) {
+        holder[c.st_slot[d]] = (int)d;
+        to_host(d);
     }
-    // the outputs for the final reduction (slot 0 is reused by layer 3)
+    for (int i = (int)d - 1; i >= 0; i--) {
+        if (wide(i)) {
+            const int sl = c.st_slot[i];
+            if (holder[sl] >= 0) cudaStreamWaitEvent(st, ev(holder[sl], ON_HOST), 0);
+            holder[sl] = i;
+        }
+        launch_eval_layers(Gs, c.d_stLev, c.d_stEval[i], (int)c.stEval[i].size(), st);
+        if (wide(i)) to_host(i);
+    }
+    // the outputs for the final reduction (layer 0's slot may be reused)
     cudaMemcpyAsync(c.d_out, c.V[0], bytes(0), cudaMemcpyDeviceToDevice, st);
     cudaStreamWaitEvent(st, P.ev_tables, 0);
-    for (u32 i = 0; i < d; i++) {
-        const u32 nx = i + 2;
-        if (nx <= d && nx >= 3) {  // slot nx mod 3 held layer i - 1, released by iteration i - 1
-            cudaStreamWaitEvent(cp, ev(i - 1, PROVED), 0);
-            cudaMemcpyAsync(c.V[nx], c.hV[nx], bytes(nx), cudaMemcpyHostToDevice, cp);
-            cudaEventRecord(ev(nx, COPIED_IN), cp);
+    run_list((u32)c.st_groups.size());  // every iteration between narrow layers
+    // the groups of iterations touching a wide layer, in order: the group's
+    // wide layers missing from their slots are copied in once the group that
+    // last used the slot's layer is done (its PROVED event, recorded at its
+    // first iteration)
+    auto last_use = [&](int L) { return L < (int)d ? L : (int)d - 1; };
+    const std::vector<StagedCopy> copies = staged_copies(c);
+    size_t k = 0;
+    for (u32 g = 0; g < c.st_groups.size(); g++) {
+        for (; k < copies.size() && copies[k].group == g; k++) {
+            const u32 L = copies[k].layer;
+            if (copies[k].prev >= 0) {
+                const int pg = c.st_group[last_use(copies[k].prev)];
+                cudaStreamWaitEvent(cp, ev(c.st_groups[pg].first, PROVED), 0);
+            }
+            cudaMemcpyAsync(c.V[L], c.hV[L], bytes(L), cudaMemcpyHostToDevice, cp);
+            cudaEventRecord(ev(L, COPIED_IN), cp);
+            cudaStreamWaitEvent(st, ev(L, COPIED_IN), 0);
         }
-        if (i + 1 >= 3) cudaStreamWaitEvent(st, ev(i + 1, COPIED_IN), 0);
-        for (size_t g = 0; g < c.stA[i].size(); g++)
-            launch_waves(Gs, P.d_lw, P.d_pw, P.d_gw, c.d_stA[i][g], (int)c.stA[i][g].size(),
-                         c.d_stctr + c.stctr_off[i] + 2 * g, st);
-        if (!c.stBuild[i].empty()) launch_build23(Gs, c.d_stBuild[i], (int)c.stBuild[i].size(), st);
-        for (size_t g = 0; g < c.stB[i].size(); g++)
-            launch_waves(Gs, P.d_lw, P.d_pw, P.d_gw, c.d_stB[i][g], (int)c.stB[i][g].size(),
-                         c.d_stctr + c.stctr_off[i] + 2 * (c.stA[i].size() + g), st);
-        cudaEventRecord(ev(i, PROVED), st);
+        run_list(g);
+        cudaEventRecord(ev(c.st_groups[g].first, PROVED), st);
     }
     cudaEventRecord(ev(d, PROVED), cp);  // join the copy stream
     cudaStreamWaitEvent(st, ev(d, PROVED), 0);
@@ -1851,6 +1949,7 @@ extern "C" vc_status vc_circuit_get_info(const vc_circuit *c, vc_circuit_info *i
     // and wiring (EXPLICIT only), output MLE (many outputs only), checks
     I.verify2_launches = (uint32_t)(4 + (c->explicit_layers.empty() ? 0 : 2) + (c->Vd.mle_out_blocks ? 1 : 0));
     I.wave_tasks = (uint32_t)(c->P.groupsA.empty() ? 0 : c->P.groupsA[0].size());
+    I.link_bytes = c->P.staged ? c->st_link_bytes : 0;
     *info = I;
     return VC_OK;
 }

@@ -54,7 +54,7 @@ class CircuitInfo(ctypes.Structure):
                 ("transcript_len", ctypes.c_uint64), ("gates", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64), ("prove_launches", ctypes.c_uint32),
                 ("verify_launches", ctypes.c_uint32), ("wave_tasks", ctypes.c_uint32),
-                ("verify2_launches", ctypes.c_uint32)]
+                ("verify2_launches", ctypes.c_uint32), ("link_bytes", ctypes.c_uint64)]
 
 
 class BatchInfo(ctypes.Structure):

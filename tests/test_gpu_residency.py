@@ -136,8 +136,10 @@ def test_staged_values_equal_oracle(family, logn):
 
 def test_staged_values_large_equal_device_and_device_bytes():
     """F2 2^18 and F0 2^12 with staged values equal the device-resident
-    proofs; the deep F0 circuit needs far less device memory (three slots
-    instead of 62 layers of values)."""
+    proofs; the deep F0 circuit needs far less device memory (eight slots
+    instead of 62 layers of values).  Host-link bytes: F2's three wide
+    layers fit its three slots, so each crosses once; F0's wide layers cross
+    once on the way out and at most once back in."""
     for fam, n, seed in (("f2", 18, 5), ("f0", 12, 6)):
         w, k = circuits.by_name(fam, n)
         x = I.job_inputs(fam, n, 40 + n)
@@ -145,9 +147,16 @@ def test_staged_values_large_equal_device_and_device_bytes():
         hs = vc.vc_circuit_create(w, k, staged=True)
         try:
             assert (prove(hs, x, seed) == prove(hd, x, seed)).all(), fam
-            if fam == "f0":
+            assert vc.vc_circuit_get_info(hd)["link_bytes"] == 0
+            link = vc.vc_circuit_get_info(hs)["link_bytes"]
+            wide = 8 * sum(1 << s for s in w if 4 * (1 << s) > (1 << max(w)))
+            if fam == "f2":
+                assert wide == 8 * (2 * (1 << 18) + (1 << 17))
+                assert link == wide
+            else:
                 values = 8 * sum(1 << s for s in w)
                 assert vc.vc_circuit_bytes(hs) < vc.vc_circuit_bytes(hd) - values // 2
+                assert wide < link < 2 * wide
         finally:
             vc.vc_circuit_destroy(hd)
             vc.vc_circuit_destroy(hs)
