@@ -151,9 +151,11 @@ vc_status vc_evaluate(vc_circuit *c, const uint64_t *inputs, uint64_t *outputs, 
  * whose device address is its host address) are read in place by the first
  * evaluation launch, which writes them into the input layer; others are
  * copied first.  Either way they are read on `stream`, in stream order.
- * If `inputs` and `transcript` are both device memory the call is
+ * If `transcript` is device memory and `inputs` are read in place (device
+ * memory, or page-locked host memory the device addresses) the call is
  * asynchronous with respect to the host: a non-canonical input is then
- * latched in the circuit and reported by the next vc_circuit_sync.
+ * latched in the circuit and reported by the next vc_circuit_sync, and
+ * page-locked inputs must stay unchanged until the proof is done.
  * Otherwise the call returns after the transcript is written and reports
  * VC_EINVAL itself. */
 vc_status vc_prove(vc_circuit *c, const uint64_t *inputs, uint64_t seed,
@@ -478,7 +480,15 @@ vc_status vc_f2sp_prove(vc_f2sp *s, const uint64_t *a, uint64_t *proof, void *st
  * several parts as additive updates of its counts); end checks `proof`
  * (2h u64, host or device), sets *accept (1 or 0; an entry >= p is a
  * rejection) and *f2 = sum of the proof's even entries, synchronously.
- * VC_EINVAL from end if an absorbed entry was >= p. */
+ * VC_EINVAL from end if an absorbed entry was >= p.  begin and absorb are
+ * asynchronous.  Device rows are read in place (keep them until end).  Host
+ * rows stream through two device buffers of about 8 MB of whole rows
+ * (Sec. 4.2's double buffering): each chunk is copied on the verifier's own
+ * copy stream into one buffer while the previous chunk is absorbed from the
+ * other, and the alternation carries over from one absorb call to the next;
+ * absorb returns once the last of its rows has been copied, so the caller
+ * may refill its host buffer while the absorbs run.  The buffers are
+ * allocated by the first absorb of host rows (VC_ENOMEM if they cannot be). */
 vc_status vc_f2sp_verify_begin(vc_f2sp *s, uint64_t seed, void *stream);
 vc_status vc_f2sp_verify_absorb(vc_f2sp *s, const uint64_t *rows, uint64_t first_row, uint64_t nrows,
                                 void *stream);

@@ -2,6 +2,7 @@
 // (declarations and contracts in include/vc.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -18,8 +19,17 @@ struct vc_f2sp {
     u64 *part = nullptr, *proof = nullptr, *res = nullptr;    // prover partials, staging, results
     u32 nparts = 0;
     u32 *status = nullptr;
-    u64 *a_stage = nullptr;  // host inputs are staged here (allocated on first use)
+    u64 *a_stage = nullptr;  // the prover's host inputs are staged here (allocated on first use)
     u64 *h_res = nullptr;    // pinned: results and status readback
+    // the verifier's host rows stream through two device buffers of
+    // `chunk_rows` rows on their own copy stream: chunk j is copied into
+    // buffer j % 2 while chunk j - 1 is absorbed from the other (allocated on
+    // first use; the alternation carries over between absorb calls)
+    u64 *rbuf[2] = {};
+    u64 chunk_rows = 0;
+    int next_buf = 0;
+    cudaStream_t rcopy = nullptr;
+    cudaEvent_t copied[2] = {}, absorbed[2] = {};
 };
 
 namespace {
@@ -205,7 +215,47 @@ extern "C" vc_status vc_f2sp_destroy(vc_f2sp *s)
     if (s->mem) lib_free(s->mem);
     if (s->a_stage) lib_free(s->a_stage);
     if (s->h_res) lib_free_host(s->h_res);
+    for (int b = 0; b < 2; b++) {
+        if (s->rbuf[b]) lib_free(s->rbuf[b]);
+        if (s->copied[b]) cudaEventDestroy(s->copied[b]);
+        if (s->absorbed[b]) cudaEventDestroy(s->absorbed[b]);
+    }
+    if (s->rcopy) cudaStreamDestroy(s->rcopy);
     delete s;
+    return VC_OK;
+}
+
+// Rows per streaming chunk: about 8 MB, whole rows, at most v.
+static u64 sp_chunk_rows(u64 v, u64 h)
+{
+    const u64 rows = std::max<u64>(1, (u64(1) << 20) / h);
+    return std::min(rows, v);
+}
+
+static vc_status sp_stream_prepare(vc_f2sp *s)
+{
+    if (s->rcopy) return VC_OK;
+    const u64 rows = sp_chunk_rows(s->v, s->h);
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && e == cudaSuccess; b++) e = lib_malloc((void **)&s->rbuf[b], rows * s->h * sizeof(u64));
+    for (int b = 0; b < 2 && e == cudaSuccess; b++) {
+        e = cudaEventCreateWithFlags(&s->copied[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->absorbed[b], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->rcopy, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        for (int b = 0; b < 2; b++) {
+            if (s->rbuf[b]) lib_free(s->rbuf[b]);
+            if (s->copied[b]) cudaEventDestroy(s->copied[b]);
+            if (s->absorbed[b]) cudaEventDestroy(s->absorbed[b]);
+            s->rbuf[b] = nullptr;
+            s->copied[b] = s->absorbed[b] = nullptr;
+        }
+        s->rcopy = nullptr;
+        return e == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA;
+    }
+    s->chunk_rows = rows;
     return VC_OK;
 }
 
@@ -264,12 +314,39 @@ extern "C" vc_status vc_f2sp_verify_absorb(vc_f2sp *s, const uint64_t *rows, uin
     if (nrows == 0) return VC_OK;
     DevGuard guard(s->device);
     cudaStream_t st = (cudaStream_t)stream;
-    vc_status err;
-    const u64 *dr = sp_device_input(s, rows, nrows * s->h, st, &err);
-    if (!dr) return err;
-    launch_sp_vabsorb(dr, first_row, nrows, s->h, s->L, s->acc, s->status, st);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && dr == s->a_stage) e = cudaStreamSynchronize(st);  // the stage is reused
+    const int k = ptr_kind(rows, s->device);
+    if (k < 0) return VC_EINVAL;
+    if (k == 1) {
+        launch_sp_vabsorb(rows, first_row, nrows, s->h, s->L, s->acc, s->status, st);
+        return cuda_status(cudaGetLastError());
+    }
+    // host rows: double-buffered (Sec. 4.2): the copy of each chunk waits
+    // only for the absorb that last read its buffer, so it overlaps the
+    // absorb of the chunk before it
+    const vc_status ps = sp_stream_prepare(s);
+    if (ps != VC_OK) return ps;
+    const u64 h = s->h;
+    cudaError_t e = cudaSuccess;
+    int last = -1;
+    for (u64 r = 0; r < nrows && e == cudaSuccess; r += s->chunk_rows) {
+        const u64 m = std::min(s->chunk_rows, nrows - r);
+        const int b = s->next_buf;
+        s->next_buf ^= 1;
+        e = cudaStreamWaitEvent(s->rcopy, s->absorbed[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->rbuf[b], rows + r * h, m * h * sizeof(u64), cudaMemcpyHostToDevice, s->rcopy);
+        if (e == cudaSuccess) e = cudaEventRecord(s->copied[b], s->rcopy);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->copied[b], 0);
+        if (e == cudaSuccess) {
+            launch_sp_vabsorb(s->rbuf[b], first_row + r, m, h, s->L, s->acc, s->status, st);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(s->absorbed[b], st);
+        last = b;
+    }
+    // the rows have been read when the last copy is done: the caller may
+    // refill its buffer on return while the absorbs run on
+    if (e == cudaSuccess && last >= 0) e = cudaEventSynchronize(s->copied[last]);
     return cuda_status(e);
 }
 

@@ -1616,7 +1616,7 @@ extern "C" vc_status vc_prove(vc_circuit *c, const uint64_t *inputs, uint64_t se
         e = cudaMemcpyAsync(transcript, c->d_tr, c->tr_len * sizeof(u64), cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return VC_ECUDA;
     }
-    if (ki && kt) return VC_OK;
+    if (kt && (ki || in)) return VC_OK;  // everything read in place: asynchronous, status latched
     return read_status_and_clear(c, st);
 }
 

@@ -145,6 +145,49 @@ def test_paper_row_length():
         vc.vc_f2sp_destroy(s)
 
 
+def _absorb_split(s, rows, h, splits):
+    """Absorb rows [0, v) in calls of the given row counts (host memory)."""
+    x0 = 0
+    for n in splits:
+        vc.vc_f2sp_verify_absorb(s, rows[x0 * h:(x0 + n) * h], x0, n)
+        x0 += n
+
+
+@pytest.mark.parametrize("v,h", [(800_000, 3), (150_000, 15)])
+def test_streaming_host_rows_double_buffered(v, h):
+    """Host rows stream through the verifier's two device buffers of about
+    8 MB (2^20 / h rows each), so these grids span three chunks: one absorb
+    call over all rows, calls that split chunks unevenly (1 row, a chunk less
+    one, a chunk plus one, the rest), page-locked and pageable rows, and host
+    calls mixed with device rows all give the oracle verifier's accept bit and
+    answer, for the honest proof and a changed one."""
+    chunk = (1 << 20) // h
+    a = I.uniform_ints(4000 + h, v * h, 1 << 16)
+    proof = oracle.f2sp_prove(a, v, h)
+    bad = proof.copy()
+    bad[2 * (h // 2) + 1] = (int(bad[2 * (h // 2) + 1]) + 3) % P
+    pinned = torch.from_numpy(a.view(np.int64).copy()).pin_memory()
+    pageable = np.ascontiguousarray(a)
+    uneven = [1, chunk - 1, chunk + 1, v - 2 * chunk - 1]
+    s = vc.vc_f2sp_create(v, h)
+    try:
+        for pr, seed in ((proof, 11), (bad, 12)):
+            want = oracle.f2sp_verify(a, v, h, seed, pr)
+            assert want[0] == (pr is proof)
+            for rows, splits in ((pinned, [v]), (pinned, uneven), (pageable, [v]), (pageable, uneven)):
+                vc.vc_f2sp_verify_begin(s, seed)
+                _absorb_split(s, rows, h, splits)
+                assert vc.vc_f2sp_verify_end(s, dev(pr)) == want, (len(splits), type(rows))
+            # host chunks, then the rest from the device
+            vc.vc_f2sp_verify_begin(s, seed)
+            _absorb_split(s, pinned, h, [chunk + 5])
+            x0 = chunk + 5
+            vc.vc_f2sp_verify_absorb(s, dev(a[x0 * h:]), x0, v - x0)
+            assert vc.vc_f2sp_verify_end(s, pr) == want
+    finally:
+        vc.vc_f2sp_destroy(s)
+
+
 def test_bad_inputs():
     s = vc.vc_f2sp_create(4, 5)
     try:

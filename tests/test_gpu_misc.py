@@ -127,12 +127,20 @@ def test_input_memory_kinds_agree(family, logn):
         out = torch.empty(1 << widths[0], dtype=torch.int64, device="cuda")
         vc.vc_evaluate(h, dev(y), out)
         assert (to_np(out) == oracle.Circuit(widths, kinds).evaluate(y)[0]).all()
-        # a non-canonical page-locked input is reported
+        # a non-canonical page-locked input is reported: by the call itself
+        # with a host transcript; with a device transcript by the call where
+        # the inputs are copied, else (read in place: asynchronous) latched
+        # for vc_circuit_sync
         bad = xp.clone().pin_memory()
         bad[3] = P
         with pytest.raises(vc.VcError) as e:
-            vc.vc_prove(h, bad, 1, tr)  # host inputs: the status is read before returning
+            vc.vc_prove(h, bad, 1, np.zeros(n, np.uint64))
         assert e.value.status == vc.VC_EINVAL
+        with pytest.raises(vc.VcError) as e:
+            vc.vc_prove(h, bad, 1, tr)
+            vc.vc_circuit_sync(h)
+        assert e.value.status == vc.VC_EINVAL
+        vc.vc_circuit_sync(h)  # the latch is cleared
     finally:
         vc.vc_circuit_destroy(h)
 
