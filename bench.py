@@ -856,9 +856,10 @@ def run_serving(local: int, seconds_per_rate: float = 1.5, repeats: int = 3):
     inputs resident in HBM, one input vector per shape.  Jobs are submitted
     from this thread and collected (vc_server_wait, in submission order) by a
     second one, so collection never delays a submission.  Saturation: a closed
-    loop keeps max_inflight x max_batch x 2 jobs outstanding; its rate over
-    windows of 1000 completions, after the first window, is the saturated
-    throughput.  Then Poisson arrivals at 0.5x, 0.9x and 1.2x of it, each rate
+    loop keeps max_inflight x max_batch x 16 jobs outstanding (a queue deep
+    enough that every launch set is formed from a full choice of jobs, as
+    under overload); its rate over windows of 1000 completions, after the
+    first window, is the saturated throughput.  Then Poisson arrivals at 0.5x, 0.9x and 1.2x of it, each rate
     `repeats` times with other seeds: proofs/s and p50/p99 latency (submit to
     transcript written, on the server's own clock)."""
     import queue
@@ -931,11 +932,11 @@ def run_serving(local: int, seconds_per_rate: float = 1.5, repeats: int = 3):
     try:
         warm = I.serving_mix(0xC0FFEE + 5, 1500)
         run(warm, outstanding=2 * max_batch * max_inflight)  # fills the circuit pool
-        closed = I.serving_mix(0xC0FFEE + 6, 6000)
-        sat, infos = run(closed, outstanding=2 * max_batch * max_inflight)
+        closed = I.serving_mix(0xC0FFEE + 6, 10000)
+        sat, infos = run(closed, outstanding=16 * max_batch * max_inflight)
         win = windows(infos)
         sat["window_proofs_per_s"] = win
-        sat["outstanding"] = 2 * max_batch * max_inflight
+        sat["outstanding"] = 16 * max_batch * max_inflight
         sat_rate = float(np.median(win[1:])) if len(win) > 1 else sat["proofs_per_s"]
         sat["saturated_proofs_per_s"] = sat_rate
         rates = []
