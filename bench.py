@@ -216,9 +216,11 @@ def run_residency(widths, kinds, xd, flush, reps=5):
         vc.vc_circuit_sync(h)
         out[name + "_prove_ms"] = statistics.median(ts)
         out[name + "_device_bytes"] = vc.vc_circuit_bytes(h)
+        trs[name] = tr.clone()
         if name == "staged":
             out["staged_link_bytes"] = vc.vc_circuit_get_info(h)["link_bytes"]
-        trs[name] = tr
+        else:
+            out[name + "_stage_ms"] = _stage_split(h, xd, tr, flush)
         vc.vc_circuit_destroy(h)
     for name in ("host_values", "staged"):
         assert bool((trs["device"] == trs[name]).all().item()), f"residency {name} changed the transcript"
@@ -228,6 +230,33 @@ def run_residency(widths, kinds, xd, flush, reps=5):
                    "size, so staging saves F2 no device memory; the deep F0 circuit (62 layers of values) "
                    "shows the saving: see `deep`")
     return out
+
+
+def _stage_split(h, xd, tr, flush, reps=3):
+    """Device time of the evaluation, wave and final-reduction stages of a
+    proof (CUDA events the library records around them), medians of `reps`
+    proofs after one warm-up."""
+    import torch
+    from paper_1202_1350_gb300 import vc
+    names = ("eval", "waves", "final")
+    ev = [None] * (2 * vc.NUM_STAGES)
+    for nm in names:
+        i = vc.STAGES.index(nm)
+        ev[2 * i] = torch.cuda.Event(enable_timing=True)
+        ev[2 * i + 1] = torch.cuda.Event(enable_timing=True)
+    vc.vc_circuit_set_stage_events(h, ev)
+    got = {nm: [] for nm in names}
+    for k in range(reps + 1):
+        flush.zero_()
+        vc.vc_prove(h, xd, 4545 + k, tr)
+        torch.cuda.synchronize()
+        if k:
+            for nm in names:
+                i = vc.STAGES.index(nm)
+                got[nm].append(ev[2 * i].elapsed_time(ev[2 * i + 1]))
+    vc.vc_circuit_sync(h)
+    vc.vc_circuit_set_stage_events(h, None)
+    return {nm: statistics.median(v) for nm, v in got.items()}
 
 
 def run_residency_deep(flush, reps=3):
@@ -939,6 +968,8 @@ def run_serving(local: int, seconds_per_rate: float = 1.5, repeats: int = 3):
         sat["outstanding"] = 16 * max_batch * max_inflight
         sat_rate = float(np.median(win[1:])) if len(win) > 1 else sat["proofs_per_s"]
         sat["saturated_proofs_per_s"] = sat_rate
+        if len(win) > 1:
+            sat["saturated_proofs_per_s_range"] = [float(min(win[1:])), float(max(win[1:]))]
         rates = []
         for mult in (0.5, 0.9, 1.2):
             rate = mult * sat_rate
@@ -977,13 +1008,30 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--residency-only", action="store_true",
+                    help="print only the residency comparison on the F2 n=2^20 workload (for profiling it)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.residency_only:
+        run_residency_only()
     else:
         run_ours(args)
+
+
+def run_residency_only():
+    import torch
+    from paper_1202_1350_gb300 import build as vcbuild
+    from paper_1202_1350_gb300 import circuits
+    from paper_1202_1350_gb300 import inputs as I
+    vcbuild.build()
+    fam, logn, gen, seed0 = I.WORKLOADS[WORKLOAD]
+    widths, kinds = circuits.by_name(fam, logn)
+    xd = torch.from_numpy(gen(seed0).view(np.int64).copy()).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.int64, device="cuda")
+    print(json.dumps(run_residency(widths, kinds, xd, flush)), flush=True)
 
 
 if __name__ == "__main__":
