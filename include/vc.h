@@ -407,8 +407,10 @@ vc_status vc_server_destroy(vc_server *s);
 /* Queue one proof: circuit shape `desc` (host memory, read during the call),
  * S_d canonical inputs and a transcript buffer of the shape's length, each
  * host or device memory; both must stay valid until the job is done.  Returns
- * at once with *job_id.  VC_EINVAL: bad shape or pointer; VC_EBUSY: one
- * circuit of this shape alone exceeds the memory cap. */
+ * at once with *job_id.  A shape whose circuit with device-resident values
+ * exceeds the memory cap is proved with staged values (VC_VALUES_STAGED),
+ * alone in its launch set.  VC_EINVAL: bad shape or pointer; VC_EBUSY: even
+ * with staged values one circuit of this shape exceeds the memory cap. */
 vc_status vc_server_submit(vc_server *s, const vc_circuit_desc *desc, const uint64_t *inputs,
                            uint64_t seed, uint64_t *transcript, uint64_t *job_id);
 
