@@ -123,9 +123,16 @@ vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, vc_circuit 
  * unchanged. */
 #define VC_VALUES_STAGED 2u
 
-/* vc_circuit_create with residency flags (0, VC_VALUES_IN_HOST_MEMORY or
- * VC_VALUES_STAGED; VC_EINVAL for any other value; VC_ENOMEM if the pinned
- * host allocation fails). */
+/* With VC_VALUES_AUTO the circuit gets device-resident values if their
+ * memory can be had (from the device and within vc_set_memory_limit's cap),
+ * else staged values (VC_VALUES_STAGED; circuits with explicit wirings skip
+ * this step), else values in mapped host memory; vc_circuit_get_info's
+ * `residency` reports the choice.  VC_ENOMEM only when none fits. */
+#define VC_VALUES_AUTO 4u
+
+/* vc_circuit_create with residency flags (0, VC_VALUES_IN_HOST_MEMORY,
+ * VC_VALUES_STAGED or VC_VALUES_AUTO; VC_EINVAL for any other value;
+ * VC_ENOMEM if the device or pinned host allocation fails). */
 vc_status vc_circuit_create_ex(const vc_circuit_desc *desc, int device, uint32_t flags, vc_circuit **out);
 
 /* Free the circuit and its device scratch (synchronises its device).  NULL is
@@ -264,6 +271,9 @@ typedef struct {
                                     vc_prove moves over the host link (each wide
                                     layer written once, plus the layers copied
                                     back in); 0 otherwise                         */
+    uint32_t residency;          /* 0, VC_VALUES_IN_HOST_MEMORY or
+                                    VC_VALUES_STAGED: where the layer values live */
+    uint32_t pad;
 } vc_circuit_info;
 
 vc_status vc_circuit_get_info(const vc_circuit *c, vc_circuit_info *info);

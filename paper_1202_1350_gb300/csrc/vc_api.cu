@@ -1512,6 +1512,15 @@ extern "C" vc_status vc_circuit_create_ex(const vc_circuit_desc *desc, int devic
 {
     if (!out) return VC_EINVAL;
     *out = nullptr;
+    if (flags == VC_VALUES_AUTO) {
+        // device-resident values, else copy-once-per-layer, else mapped host
+        // memory: the first whose memory can be had
+        vc_status st = vc_circuit_create_ex(desc, device, 0, out);
+        if (st != VC_ENOMEM) return st;
+        st = vc_circuit_create_ex(desc, device, VC_VALUES_STAGED, out);
+        if (st != VC_ENOMEM && st != VC_EINVAL) return st;  // VC_EINVAL: explicit wirings are not staged
+        return vc_circuit_create_ex(desc, device, VC_VALUES_IN_HOST_MEMORY, out);
+    }
     vc_circuit *c = nullptr;
     vc_status st = circuit_prepare(desc, device, &c, nullptr, flags);
     if (st != VC_OK) return st;
@@ -1949,6 +1958,7 @@ extern "C" vc_status vc_circuit_get_info(const vc_circuit *c, vc_circuit_info *i
     // and wiring (EXPLICIT only), output MLE (many outputs only), checks
     I.verify2_launches = (uint32_t)(4 + (c->explicit_layers.empty() ? 0 : 2) + (c->Vd.mle_out_blocks ? 1 : 0));
     I.wave_tasks = (uint32_t)(c->P.groupsA.empty() ? 0 : c->P.groupsA[0].size());
+    I.residency = c->flags;
     I.link_bytes = c->P.staged ? c->st_link_bytes : 0;
     *info = I;
     return VC_OK;

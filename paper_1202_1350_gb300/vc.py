@@ -54,7 +54,8 @@ class CircuitInfo(ctypes.Structure):
                 ("transcript_len", ctypes.c_uint64), ("gates", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64), ("prove_launches", ctypes.c_uint32),
                 ("verify_launches", ctypes.c_uint32), ("wave_tasks", ctypes.c_uint32),
-                ("verify2_launches", ctypes.c_uint32), ("link_bytes", ctypes.c_uint64)]
+                ("verify2_launches", ctypes.c_uint32), ("link_bytes", ctypes.c_uint64),
+                ("residency", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -235,14 +236,17 @@ def _stream(stream, device: int):
 
 VC_VALUES_IN_HOST_MEMORY = 1
 VC_VALUES_STAGED = 2
+VC_VALUES_AUTO = 4
 
 
 def vc_circuit_create(log_width, wiring, explicit=None, device: int = 0, host_values: bool = False,
-                      staged: bool = False):
+                      staged: bool = False, auto: bool = False):
     """Returns an opaque handle (int).  explicit: per-layer (type, in1, in2) or
     None.  host_values: keep the layer values in mapped host memory; staged:
-    keep them in host memory and copy each layer through three device slots
-    (copy-once-per-layer)."""
+    keep the wide layers in host memory and pass them through device slots
+    (copy-once-per-layer); auto: the first of device memory, staged and
+    mapped host memory whose memory can be had (vc_circuit_get_info's
+    "residency" says which)."""
     lw = [int(x) for x in log_width]
     kinds = [int(k) for k in wiring]
     d = len(kinds)
@@ -270,8 +274,8 @@ def vc_circuit_create(log_width, wiring, explicit=None, device: int = 0, host_va
         desc.in1 = i1s
         desc.in2 = i2s
     h = ctypes.c_void_p()
-    if host_values or staged:
-        flags = VC_VALUES_STAGED if staged else VC_VALUES_IN_HOST_MEMORY
+    if host_values or staged or auto:
+        flags = VC_VALUES_AUTO if auto else (VC_VALUES_STAGED if staged else VC_VALUES_IN_HOST_MEMORY)
         _check(lib().vc_circuit_create_ex(ctypes.byref(desc), device, flags, ctypes.byref(h)),
                "vc_circuit_create_ex")
     else:

@@ -24,6 +24,41 @@ def test_exports_every_declared_function(libvc):
         assert isinstance(getattr(libvc, name), ctypes._CFuncPtr)
 
 
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the header's size and field
+    offsets: a C program compiled with gcc against include/vc.h prints them."""
+    import os
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    mirrors = {"vc_circuit_desc": vc._Desc, "vc_circuit_info": vc.CircuitInfo, "vc_batch_info": vc.BatchInfo,
+               "vc_server_config": vc.ServerConfig, "vc_job_info": vc.JobInfo, "vc_server_stats": vc.ServerStats,
+               "vc_tile_config": vc.TileConfig}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "vc.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([gcc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            cname, what, val = line.split()
+            got[(cname, what)] = int(val)
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
 def test_status_strings(libvc):
     assert vc.vc_status_string(0) == "ok"
     assert vc.vc_status_string(1) == "invalid argument"

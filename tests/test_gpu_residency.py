@@ -105,7 +105,7 @@ def test_bad_flags_rejected():
     w, k = circuits.f2(3)
     desc, keep = vc._desc_struct(w, k)
     h = ctypes.c_void_p()
-    for flags in (6, 3, 4):
+    for flags in (6, 3, 5, 8):
         assert vc.lib().vc_circuit_create_ex(ctypes.byref(desc), 0, flags, ctypes.byref(h)) == vc.VC_EINVAL
 
 
@@ -178,3 +178,54 @@ def test_staged_rejected_where_layers_are_read_in_place():
     wp, kp, ex = circuits.pattern_match(5, 2)
     with pytest.raises(vc.VcError):
         vc.vc_circuit_create(wp, kp, ex, staged=True)
+
+
+def test_auto_residency_follows_the_memory_cap():
+    """VC_VALUES_AUTO under the library's device-memory cap: device-resident
+    values when the whole circuit fits, staged values when only they fit,
+    mapped host memory when neither does, and VC_ENOMEM below that; every
+    choice gives the oracle's transcript.  F0 with 2^10 inputs (62 layers of
+    2^11 values), where the staged mode needs far less device memory."""
+    w, k = circuits.f0(10)
+    x = I.job_inputs("f0", 10, 5)
+    want = oracle_prove(w, k, x, 3)
+    sizes = {}
+    for mode, kw in ((0, {}), (vc.VC_VALUES_STAGED, {"staged": True}), (vc.VC_VALUES_IN_HOST_MEMORY,
+                                                                          {"host_values": True})):
+        h = vc.vc_circuit_create(w, k, **kw)
+        sizes[mode] = vc.vc_circuit_bytes(h)
+        vc.vc_circuit_destroy(h)
+    dev, stg, hst = sizes[0], sizes[vc.VC_VALUES_STAGED], sizes[vc.VC_VALUES_IN_HOST_MEMORY]
+    assert hst < stg < dev
+    used = vc.vc_get_memory_usage()[0]
+    try:
+        for cap, mode in ((dev, 0), ((stg + dev) // 2, vc.VC_VALUES_STAGED),
+                          ((hst + stg) // 2, vc.VC_VALUES_IN_HOST_MEMORY)):
+            vc.vc_set_memory_limit(used + cap, 0)
+            h = vc.vc_circuit_create(w, k, auto=True)
+            try:
+                assert vc.vc_circuit_get_info(h)["residency"] == mode
+                assert (prove(h, x, 3) == want).all(), mode
+            finally:
+                vc.vc_circuit_destroy(h)
+        vc.vc_set_memory_limit(used + hst // 2, 0)
+        with pytest.raises(vc.VcError) as e:
+            vc.vc_circuit_create(w, k, auto=True)
+        assert e.value.status == vc.VC_ENOMEM
+    finally:
+        vc.vc_set_memory_limit(0, 0)
+    # explicit wirings skip the staged step
+    wp, kp, ex = circuits.pattern_match(5, 2)
+    h = vc.vc_circuit_create(wp, kp, ex)
+    dev_p = vc.vc_circuit_bytes(h)
+    vc.vc_circuit_destroy(h)
+    used = vc.vc_get_memory_usage()[0]
+    try:
+        vc.vc_set_memory_limit(used + dev_p - 1, 0)
+        h = vc.vc_circuit_create(wp, kp, ex, auto=True)
+        try:
+            assert vc.vc_circuit_get_info(h)["residency"] == vc.VC_VALUES_IN_HOST_MEMORY
+        finally:
+            vc.vc_circuit_destroy(h)
+    finally:
+        vc.vc_set_memory_limit(0, 0)

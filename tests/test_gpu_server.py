@@ -45,13 +45,19 @@ def test_server_mix_equals_alone(split):
     instances below 2^13 entries."""
     srv = Server(max_batch=4, max_inflight=3, pr_split_log=split)
     try:
-        jobs = []
+        # inputs and transcript buffers first, then the submissions back to
+        # back, so that jobs queue up behind the ones in flight
+        prepared = []
         for k, (fam, logn) in enumerate(MIX * 2):
             w, kinds = circuits.by_name(fam, logn)
             x = I.job_inputs(fam, logn, 300 + k)
             tr = torch.empty(circuits.transcript_len(w), dtype=torch.int64, device="cuda")
-            jid = srv.submit(w, kinds, dev(x), 500 + k, tr)
-            jobs.append((jid, fam, logn, w, kinds, x, 500 + k, tr))
+            prepared.append((fam, logn, w, kinds, x, dev(x), 500 + k, tr))
+        torch.cuda.synchronize()
+        jobs = []
+        for fam, logn, w, kinds, x, xd, seed, tr in prepared:
+            jid = srv.submit(w, kinds, xd, seed, tr)
+            jobs.append((jid, fam, logn, w, kinds, x, seed, tr))
         for jid, fam, logn, w, kinds, x, seed, tr in jobs:
             info = srv.wait(jid)
             assert info["done"] and info["status"] == 0
