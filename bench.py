@@ -226,9 +226,9 @@ def run_residency(widths, kinds, xd, flush, reps=5):
         assert bool((trs["device"] == trs[name]).all().item()), f"residency {name} changed the transcript"
     out["slowdown"] = out["host_values_prove_ms"] / out["device_prove_ms"]
     out["staged_slowdown"] = out["staged_prove_ms"] / out["device_prove_ms"]
-    out["note"] = ("F2's wide layers (2^20, 2^20 and 2^19 values) each take a slot of the widest layer's "
-                   "size, so staging saves F2 no device memory; the deep F0 circuit (62 layers of values) "
-                   "shows the saving: see `deep`")
+    out["note"] = ("F2's wide layers (2^20, 2^20 and 2^19 values) pass through two slots of 2^20 values, "
+                   "so staging saves F2 half a slot and copies the input layer back in once; the deep F0 "
+                   "circuit (62 layers of values, eight slots) shows the saving: see `deep`")
     return out
 
 

@@ -107,9 +107,11 @@ vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, vc_circuit 
 #define VC_VALUES_IN_HOST_MEMORY 1u
 
 /* With VC_VALUES_STAGED the values of the wide layers (more than a quarter
- * of the widest) live in page-locked host memory and pass through
- * W = min(8, number of wide layers) device slots of the widest layer's size;
- * narrow layers stay on the device (Sec. 5.1.2, copy-once-per-layer: a layer
+ * of the widest) live in page-locked host memory and pass through W device
+ * slots of the widest layer's size, W = floor(wide layers' values / widest
+ * layer's values) clamped to [2, 8] (and to the number of wide layers), so
+ * the slots never hold more than the wide layers would; narrow layers stay
+ * on the device (Sec. 5.1.2, copy-once-per-layer: a layer
  * iteration needs only layers i and i+1 on the device).  A proof evaluates
  * the circuit layer by layer from the input up, writing each wide layer to
  * host memory once as soon as it is computed; then it runs every iteration

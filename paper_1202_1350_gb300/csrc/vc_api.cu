@@ -361,14 +361,20 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     c->hV.assign(staged ? d + 1 : 0, nullptr);
     if (staged) {
         // wide layers (more than a quarter of the widest) in page-locked host
-        // memory, passing through W = min(VC_STAGED_SLOTS, wide layers)
-        // device slots of the widest layer's size (the k-th wide layer in
-        // slot k mod W); narrow layers stay on the device
-        u64 smax = 1;
+        // memory, passing through W device slots of the widest layer's size
+        // (the k-th wide layer in slot k mod W); narrow layers stay on the
+        // device.  W: as many slots as the wide layers' values fill, so the
+        // slots never take more device memory than the layers would, at
+        // least 2 (an iteration's two layers) and at most STAGED_SLOTS
+        u64 smax = 1, wide_sum = 0;
         u32 nwide = 0;
         for (u32 i = 0; i <= d; i++) smax = std::max(smax, S(i));
-        for (u32 i = 0; i <= d; i++) nwide += (4 * S(i) > smax) ? 1 : 0;
-        const u32 W = std::min<u32>(STAGED_SLOTS, nwide);
+        for (u32 i = 0; i <= d; i++)
+            if (4 * S(i) > smax) {
+                nwide++;
+                wide_sum += S(i);
+            }
+        const u32 W = std::min<u32>(nwide, (u32)std::min<u64>(STAGED_SLOTS, std::max<u64>(2, wide_sum / smax)));
         c->st_nslots = W;
         std::vector<u64 *> slot(W);
         for (u32 k = 0; k < W; k++) slot[k] = A.take<u64>(smax);

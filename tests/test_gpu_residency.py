@@ -1,5 +1,5 @@
 """Layer values in mapped host memory (VC_VALUES_IN_HOST_MEMORY) or in host
-memory copied once per layer through three device slots (VC_VALUES_STAGED):
+memory passing through device slots (VC_VALUES_STAGED, copy-once-per-layer):
 the same transcripts, accept bits and outputs as with device-resident values,
 and less device memory."""
 import numpy as np
@@ -137,9 +137,10 @@ def test_staged_values_equal_oracle(family, logn):
 def test_staged_values_large_equal_device_and_device_bytes():
     """F2 2^18 and F0 2^12 with staged values equal the device-resident
     proofs; the deep F0 circuit needs far less device memory (eight slots
-    instead of 62 layers of values).  Host-link bytes: F2's three wide
-    layers fit its three slots, so each crosses once; F0's wide layers cross
-    once on the way out and at most once back in."""
+    instead of 62 layers of values) and F2 less too (two slots for its wide
+    layers of 2^18, 2^18 and 2^17 values).  Host-link bytes: every wide layer
+    crosses once on the way out; F2's input layer comes back in once (its
+    slot held layer 17 meanwhile); F0's wide layers come back at most once."""
     for fam, n, seed in (("f2", 18, 5), ("f0", 12, 6)):
         w, k = circuits.by_name(fam, n)
         x = I.job_inputs(fam, n, 40 + n)
@@ -152,7 +153,8 @@ def test_staged_values_large_equal_device_and_device_bytes():
             wide = 8 * sum(1 << s for s in w if 4 * (1 << s) > (1 << max(w)))
             if fam == "f2":
                 assert wide == 8 * (2 * (1 << 18) + (1 << 17))
-                assert link == wide
+                assert link == wide + 8 * (1 << 18)
+                assert vc.vc_circuit_bytes(hs) < vc.vc_circuit_bytes(hd)
             else:
                 values = 8 * sum(1 << s for s in w)
                 assert vc.vc_circuit_bytes(hs) < vc.vc_circuit_bytes(hd) - values // 2
