@@ -548,6 +548,54 @@ def event_recorder():
     return rec
 
 
+def e2e_pipelined(h, step, xh, n_in, tr_len, side, main, ev_start, nsteps, dist):
+    """A stream of proofs from page-locked host inputs: step k's upload runs
+    on a copy stream into one of two device input buffers while step k - 1
+    proves and verifies from the other, and each step's transcript and accept
+    bit are read back into page-locked host memory on the step's stream.
+    Every step's copies are inside the timed region (host wall clock from the
+    first upload to the last read-back); the per-step figure is throughput,
+    not the latency of one step."""
+    import torch
+    from paper_1202_1350_gb300 import replicas
+    copy = torch.cuda.Stream()
+    xe = [torch.empty(n_in, dtype=torch.int64, device="cuda") for _ in range(2)]
+    tr = [torch.empty(tr_len, dtype=torch.int64, device="cuda") for _ in range(2)]
+    acc = [torch.zeros(1, dtype=torch.int32, device="cuda") for _ in range(2)]
+    trh = torch.empty((nsteps, tr_len), dtype=torch.int64).pin_memory()
+    acch = torch.zeros(nsteps, dtype=torch.int32).pin_memory()
+    up = [torch.cuda.Event() for _ in range(2)]
+    free = [torch.cuda.Event() for _ in range(2)]
+
+    def run(seed0):
+        for k in range(nsteps):
+            b = k & 1
+            if k >= 2:
+                copy.wait_event(free[b])  # step k - 2 is done with buffer b
+            with torch.cuda.stream(copy):
+                xe[b].copy_(xh, non_blocking=True)
+            up[b].record(copy)
+            main.wait_event(up[b])
+            ev_start.record(main)
+            step(seed0 + k, ev_start, xe[b], tr[b], acc[b])
+            free[b].record(main)
+            trh[k].copy_(tr[b], non_blocking=True)
+            acch[k:k + 1].copy_(acc[b], non_blocking=True)
+        main.synchronize()
+        return int(acch.sum()) == nsteps
+
+    assert run(7000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ok = run(8000)
+    ms = 1000 * (time.perf_counter() - t0) / nsteps
+    assert ok, "a pipelined proof was rejected"
+    ms = replicas.max_over_ranks(ms, dist, "cuda")
+    return {"ms_per_step": ms, "steps": nsteps, "h2d_bytes_per_step": n_in * 8, "d2h_bytes_per_step": tr_len * 8 + 4,
+            "note": "throughput of a stream of proofs with each step's upload overlapping the previous step's "
+                    "proof; not the latency of one step (the `modes` above)"}
+
+
 def run_ours(args):
     import torch
     from paper_1202_1350_gb300 import build as vcbuild
@@ -715,7 +763,9 @@ def run_ours(args):
     best = min(modes, key=lambda m: modes[m]["ms_per_step"])
     e2e = {"value": world * gates / (modes[best]["ms_per_step"] / 1000), "unit": UNIT,
            "h2d_bytes_per_step": modes[best]["h2d_bytes_per_step"], "d2h_bytes_per_step": tr_bytes,
-           "ms_per_step": modes[best]["ms_per_step"], "mode": best, "modes": modes}
+           "ms_per_step": modes[best]["ms_per_step"], "mode": best, "modes": modes,
+           "pipelined": e2e_pipelined(h, step, xh, x.size, info["transcript_len"], side, main, ev_start,
+                                      max(8, args.steps), dist)}
 
     if rank != 0:
         vc.vc_circuit_destroy(h)
