@@ -98,7 +98,9 @@ void launch_eval_layers(const Globals *Gs, const LayerEval *le, const Item *item
 // MATMULT): a CTA loads an aligned chunk of the run's input layer and
 // evaluates it upward through the run in shared memory, writing each layer.
 // Block size of layer i = chunk size * 2^(s_i - s_in); all stay <= EV_MAXB.
-#define EV_NT 256
+#ifndef EV_NT
+#define EV_NT 256  // threads of an evaluation CTA
+#endif
 #define EV_MAXB 2048
 
 extern __shared__ u64 ev_dyn[];
