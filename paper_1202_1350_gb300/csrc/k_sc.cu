@@ -931,6 +931,9 @@ __global__ void __launch_bounds__(WV_NT, WV_MINB) k_waves(const Globals *Gs, con
     WaveSmem &sm = *reinterpret_cast<WaveSmem *>(wv_dyn);
     __shared__ int s_task;
     __shared__ u32 s_flag;
+    // the final reduction may begin its launch on SMs this launch frees as it
+    // drains (it waits for the whole launch before it reads what it wrote)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     for (;;) {
         __syncthreads();  // the previous task is done with shared memory
         if (threadIdx.x == 0) s_task = (int)atomicAdd(&ctr[0], 1u);
@@ -1001,13 +1004,13 @@ struct RoundScalars {
     u64 ez, ch, v1, es, kap, c0, c1;
 };
 
-__device__ __forceinline__ RoundScalars round_scalars(const RoundRef &R)
+// Everything but v1 (the coin launch wrote it all before the wave launch).
+__device__ __forceinline__ RoundScalars round_scalars_pre(const RoundRef &R)
 {
     RoundScalars S{};
     S.ez = *R.ez;
     if (R.defer || R.kind < PK_GEN_FIRST) S.ch = *R.ch;
     if (R.kind < PK_GEN_FIRST) {
-        S.v1 = *R.v1;
         S.es = *R.esum;
         S.kap = *R.kap;
         S.c0 = R.lc[0];
@@ -1057,10 +1060,24 @@ __global__ void __launch_bounds__(256) k_final(Globals *Gs, const RoundRef *roun
 {
     const u32 lane = threadIdx.x & 31;
     const u64 gt = blockIdx.x * (u64)blockDim.x + threadIdx.x, nthreads = (u64)gridDim.x * blockDim.x;
-    for (u64 gw = gt >> 5; gw < (u64)nbig; gw += nthreads >> 5) {
-        const RoundRef R = rounds[gw];
+    // launched early (programmatic dependence on the wave launch): the first
+    // round's descriptor and coin-launch scalars are loaded before waiting
+    // for the waves; v1 and the partials only after
+    const u64 gw0 = gt >> 5;
+    RoundRef R0{};
+    RoundScalars S0{};
+    if (gw0 < (u64)nbig) {
+        R0 = rounds[gw0];
+        if (lane == 0) S0 = round_scalars_pre(R0);
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    for (u64 gw = gw0; gw < (u64)nbig; gw += nthreads >> 5) {
+        const RoundRef R = (gw == gw0) ? R0 : rounds[gw];
         RoundScalars S{};
-        if (lane == 0) S = round_scalars(R);
+        if (lane == 0) {
+            S = (gw == gw0) ? S0 : round_scalars_pre(R);
+            if (R.kind < PK_GEN_FIRST) S.v1 = *R.v1;  // written by the layer's line reduction
+        }
         u64 h[3] = {0, 0, 0};
         if (R.kind >= PK_GEN_FIRST)
             warp_record_sums<3>(R.part_pos, R.nchunks, lane, h);
@@ -1070,7 +1087,8 @@ __global__ void __launch_bounds__(256) k_final(Globals *Gs, const RoundRef *roun
     }
     for (u64 t = gt; t < (u64)(nrounds - nbig); t += nthreads) {
         const RoundRef R = rounds[nbig + t];
-        const RoundScalars S = round_scalars(R);
+        RoundScalars S = round_scalars_pre(R);
+        if (R.kind < PK_GEN_FIRST) S.v1 = *R.v1;
         const u32 nv = R.kind >= PK_GEN_FIRST ? 3 : 2;
         u64 h[3] = {0, 0, 0};
         for (u32 q = 0; q < R.nchunks; q++)
@@ -1099,5 +1117,17 @@ void launch_final(Globals *Gs, const RoundRef *rounds, int nrounds, int nbig, co
     if (blocks < (u64)nouts) blocks = (u64)nouts;
     if (blocks < 64) blocks = 64;
     if (blocks > (u64)device_sms() * 8) blocks = (u64)device_sms() * 8;
-    k_final<<<(unsigned)blocks, 256, 0, st>>>(Gs, rounds, nrounds, nbig, outs, nouts);
+    // programmatic dependence: the launch may begin while the wave launch
+    // drains (k_final waits for it with griddepcontrol.wait)
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_final, Gs, rounds, nrounds, nbig, outs, nouts);
 }
