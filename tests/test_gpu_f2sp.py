@@ -188,6 +188,28 @@ def test_streaming_host_rows_double_buffered(v, h):
         vc.vc_f2sp_destroy(s)
 
 
+def test_streaming_reuses_one_host_buffer():
+    """The caller streams every row through one page-locked buffer, refilling
+    it as soon as each absorb call returns (the rows have been copied by
+    then, while the absorbs still run): the verdict equals the oracle's."""
+    v, h = 600_000, 5
+    part = 50_000
+    a = I.uniform_ints(4100, v * h, 1 << 16)
+    proof = oracle.f2sp_prove(a, v, h)
+    want = oracle.f2sp_verify(a, v, h, 21, proof)
+    assert want[0]
+    buf = torch.empty(part * h, dtype=torch.int64).pin_memory()
+    s = vc.vc_f2sp_create(v, h)
+    try:
+        vc.vc_f2sp_verify_begin(s, 21)
+        for x0 in range(0, v, part):
+            buf.copy_(torch.from_numpy(a[x0 * h:(x0 + part) * h].view(np.int64)))
+            vc.vc_f2sp_verify_absorb(s, buf, x0, part)
+        assert vc.vc_f2sp_verify_end(s, proof) == want
+    finally:
+        vc.vc_f2sp_destroy(s)
+
+
 def test_bad_inputs():
     s = vc.vc_f2sp_create(4, 5)
     try:
