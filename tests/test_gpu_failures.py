@@ -79,12 +79,13 @@ def test_cancel_queued_job():
     srv = Server(max_batch=1, max_inflight=1)
     try:
         w, k = circuits.f2(18)
-        xs = [dev(I.f2_inputs(18, 1 << 16, 100 + j)) for j in range(60)]
-        trs = [torch.full((circuits.transcript_len(w),), -1, dtype=torch.int64, device="cuda") for _ in range(60)]
+        n = 120
+        xs = [dev(I.f2_inputs(18, 1 << 16, 100 + j)) for j in range(n)]
+        trs = [torch.full((circuits.transcript_len(w),), -1, dtype=torch.int64, device="cuda") for _ in range(n)]
         torch.cuda.synchronize()
         # one job at a time on the device: submitted back to back, the last
-        # one waits behind 59 proofs when it is cancelled
-        jobs = [(srv.submit(w, k, xs[j], 200 + j, trs[j]), xs[j], trs[j]) for j in range(60)]
+        # one waits behind n - 1 proofs when it is cancelled
+        jobs = [(srv.submit(w, k, xs[j], 200 + j, trs[j]), xs[j], trs[j]) for j in range(n)]
         last, _, last_tr = jobs[-1]
         srv.cancel(last)
         with pytest.raises(vc.VcError) as e:
@@ -94,7 +95,7 @@ def test_cancel_queued_job():
         assert infos[-1]["status"] == vc.VC_ECANCELED and infos[-1]["done"]
         assert all(i["status"] == vc.VC_OK for i in infos[:-1])
         assert bool((last_tr == -1).all().item())  # never written
-        for j in (0, 58):
+        for j in (0, n - 2):
             jid, x, tr = jobs[j]
             assert (to_np(tr) == oracle_prove(w, k, to_np(x), 200 + j)).all()
         assert srv.stats()["cancelled"] == 1
