@@ -190,17 +190,19 @@ def run_ablation(h, xd, tr, flush, reps=5):
 
 def run_residency(widths, kinds, xd, flush, reps=5):
     """Proof time with the layer values in mapped host memory (read and
-    written over the host link at every use) and staged through host memory
+    written over the host link at every use), staged through host memory
     (copy-once-per-layer: the wide layers pass through device slots of the
-    widest layer's size), against device-resident values; transcripts
-    compared.  link_bytes: what the staged mode moves over the host link per
-    proof (each wide layer written once, plus the layers copied back in), as
-    the library reports it."""
+    widest layer's size) and windowed (the same slots, each iteration run
+    while its layers are there, nothing copied to the host), against
+    device-resident values; transcripts compared.  link_bytes: what a mode
+    moves over the host link per proof (staged: each wide layer written once,
+    plus the layers copied back in), as the library reports it."""
     import torch
     from paper_1202_1350_gb300 import vc
     out = {}
     trs = {}
-    for name, kw in (("device", {}), ("host_values", {"host_values": True}), ("staged", {"staged": True})):
+    for name, kw in (("device", {}), ("host_values", {"host_values": True}), ("staged", {"staged": True}),
+                     ("windowed", {"windowed": True})):
         h = vc.vc_circuit_create(widths, kinds, **kw)
         tr = torch.empty(vc.vc_transcript_len(h), dtype=torch.int64, device="cuda")
         ts = []
@@ -217,18 +219,20 @@ def run_residency(widths, kinds, xd, flush, reps=5):
         out[name + "_prove_ms"] = statistics.median(ts)
         out[name + "_device_bytes"] = vc.vc_circuit_bytes(h)
         trs[name] = tr.clone()
-        if name == "staged":
-            out["staged_link_bytes"] = vc.vc_circuit_get_info(h)["link_bytes"]
+        if name in ("staged", "windowed"):
+            out[name + "_link_bytes"] = vc.vc_circuit_get_info(h)["link_bytes"]
         else:
             out[name + "_stage_ms"] = _stage_split(h, xd, tr, flush)
         vc.vc_circuit_destroy(h)
-    for name in ("host_values", "staged"):
+    for name in ("host_values", "staged", "windowed"):
         assert bool((trs["device"] == trs[name]).all().item()), f"residency {name} changed the transcript"
     out["slowdown"] = out["host_values_prove_ms"] / out["device_prove_ms"]
     out["staged_slowdown"] = out["staged_prove_ms"] / out["device_prove_ms"]
+    out["windowed_slowdown"] = out["windowed_prove_ms"] / out["device_prove_ms"]
     out["note"] = ("F2's wide layers (2^20, 2^20 and 2^19 values) pass through two slots of 2^20 values, "
-                   "so staging saves F2 half a slot and copies the input layer back in once; the deep F0 "
-                   "circuit (62 layers of values, eight slots) shows the saving: see `deep`")
+                   "so staging saves F2 half a slot and copies the input layer back in once; windowed values "
+                   "use the same slots with no host copies (each iteration runs while its two layers are "
+                   "there); the deep F0 circuit (62 layers of values, eight slots) shows the saving: see `deep`")
     return out
 
 
@@ -261,8 +265,8 @@ def _stage_split(h, xd, tr, flush, reps=3):
 
 def run_residency_deep(flush, reps=3):
     """The same comparison on the F0 circuit with 2^16 inputs (61 power
-    layers of 2^17 values each): staged values need eight slots of device
-    memory instead of every layer."""
+    layers of 2^17 values each): staged and windowed values need eight slots
+    of device memory instead of every layer."""
     import torch
     from paper_1202_1350_gb300 import circuits, vc
     from paper_1202_1350_gb300 import inputs as I
@@ -270,7 +274,7 @@ def run_residency_deep(flush, reps=3):
     x = torch.from_numpy(I.f0_inputs(16, 0xC0FFEE + 1).view(np.int64).copy()).cuda()
     out = {"workload": "F0, 2^16 inputs (Poisson(1) capped at 2^10)"}
     trs = {}
-    for name, kw in (("device", {}), ("staged", {"staged": True})):
+    for name, kw in (("device", {}), ("staged", {"staged": True}), ("windowed", {"windowed": True})):
         h = vc.vc_circuit_create(widths, kinds, **kw)
         tr = torch.empty(vc.vc_transcript_len(h), dtype=torch.int64, device="cuda")
         ts = []
@@ -290,7 +294,8 @@ def run_residency_deep(flush, reps=3):
             out["staged_link_bytes"] = vc.vc_circuit_get_info(h)["link_bytes"]
         trs[name] = tr
         vc.vc_circuit_destroy(h)
-    assert bool((trs["device"] == trs["staged"]).all().item()), "staged values changed the F0 transcript"
+    for name in ("staged", "windowed"):
+        assert bool((trs["device"] == trs[name]).all().item()), f"{name} values changed the F0 transcript"
     out["values_bytes"] = 8 * sum(1 << s for s in widths)
     return out
 

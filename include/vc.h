@@ -125,16 +125,27 @@ vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, vc_circuit 
  * unchanged. */
 #define VC_VALUES_STAGED 2u
 
+/* With VC_VALUES_WINDOWED the wide layers pass through the same W device
+ * slots as with VC_VALUES_STAGED, but never leave the device: since every
+ * coin is known from the seed, a layer iteration can run as soon as its two
+ * layers are evaluated, so a proof evaluates from the input up and, before a
+ * layer overwrites a slot, runs every evaluated iteration not yet run (in one
+ * merged set of launches, the narrow layers' iterations with the last set).
+ * Device memory for values as with VC_VALUES_STAGED, no host memory and no
+ * host-link traffic; the same restrictions (structured wirings only, no
+ * batch, no vc_prove_pergate).  The transcript is unchanged. */
+#define VC_VALUES_WINDOWED 8u
+
 /* With VC_VALUES_AUTO the circuit gets device-resident values if their
  * memory can be had (from the device and within vc_set_memory_limit's cap),
- * else staged values (VC_VALUES_STAGED; circuits with explicit wirings skip
- * this step), else values in mapped host memory; vc_circuit_get_info's
+ * else windowed values (VC_VALUES_WINDOWED; circuits with explicit wirings
+ * skip this step), else values in mapped host memory; vc_circuit_get_info's
  * `residency` reports the choice.  VC_ENOMEM only when none fits. */
 #define VC_VALUES_AUTO 4u
 
 /* vc_circuit_create with residency flags (0, VC_VALUES_IN_HOST_MEMORY,
- * VC_VALUES_STAGED or VC_VALUES_AUTO; VC_EINVAL for any other value;
- * VC_ENOMEM if the device or pinned host allocation fails). */
+ * VC_VALUES_STAGED, VC_VALUES_WINDOWED or VC_VALUES_AUTO; VC_EINVAL for any
+ * other value; VC_ENOMEM if the device or pinned host allocation fails). */
 vc_status vc_circuit_create_ex(const vc_circuit_desc *desc, int device, uint32_t flags, vc_circuit **out);
 
 /* Free the circuit and its device scratch (synchronises its device).  NULL is
@@ -273,8 +284,9 @@ typedef struct {
                                     vc_prove moves over the host link (each wide
                                     layer written once, plus the layers copied
                                     back in); 0 otherwise                         */
-    uint32_t residency;          /* 0, VC_VALUES_IN_HOST_MEMORY or
-                                    VC_VALUES_STAGED: where the layer values live */
+    uint32_t residency;          /* 0, VC_VALUES_IN_HOST_MEMORY, VC_VALUES_STAGED
+                                    or VC_VALUES_WINDOWED: where the layer values
+                                    live                                          */
     uint32_t pad;
 } vc_circuit_info;
 
@@ -420,9 +432,10 @@ vc_status vc_server_destroy(vc_server *s);
  * S_d canonical inputs and a transcript buffer of the shape's length, each
  * host or device memory; both must stay valid until the job is done.  Returns
  * at once with *job_id.  A shape whose circuit with device-resident values
- * exceeds the memory cap is proved with staged values (VC_VALUES_STAGED),
- * alone in its launch set.  VC_EINVAL: bad shape or pointer; VC_EBUSY: even
- * with staged values one circuit of this shape exceeds the memory cap. */
+ * exceeds the memory cap is proved with windowed values
+ * (VC_VALUES_WINDOWED), alone in its launch set.  VC_EINVAL: bad shape or
+ * pointer; VC_EBUSY: even with windowed values one circuit of this shape
+ * exceeds the memory cap. */
 vc_status vc_server_submit(vc_server *s, const vc_circuit_desc *desc, const uint64_t *inputs,
                            uint64_t seed, uint64_t *transcript, uint64_t *job_id);
 

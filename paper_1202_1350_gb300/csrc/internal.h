@@ -47,6 +47,8 @@ cudaError_t lib_host_alloc(T **p, size_t n, unsigned flags)
 
 // Device slots of the wide layers of a circuit with staged values.
 constexpr u32 STAGED_SLOTS = 8;
+// residencies whose wide layers pass through device slots
+constexpr u32 VC_VALUES_SLOTTED = VC_VALUES_STAGED | VC_VALUES_WINDOWED;
 
 // Which layers' phase-2/3 tables are built by k_build23 (the rest are formed
 // on the fly or never stored).
@@ -207,10 +209,15 @@ struct vc_circuit {
     u32 *d_explicit_layers = nullptr;
     std::vector<u32> round_layer, zmap;
     u32 *d_round_layer = nullptr, *d_zmap = nullptr;
-    // VC_VALUES_STAGED: every layer in page-locked host memory (hV), V[i] =
-    // device slot i mod 3; per-layer task lists of the wave launches (groups
-    // A and B), table builds and launch counters; a copy stream and events
-    std::vector<u64 *> hV;        // wide layers only
+    // VC_VALUES_STAGED / VC_VALUES_WINDOWED: wide layers through W device
+    // slots (V[i] = slot k mod W for the k-th wide layer), staged ones also in
+    // page-locked host memory (hV); per-group task lists of the wave launches
+    // (groups A and B), table builds and launch counters; a copy stream and
+    // events (staged)
+    std::vector<u64 *> hV;        // wide layers only (staged)
+    // windowed: the proof's order of evaluations (a layer index >= 0) and
+    // iteration groups run (-(g + 1))
+    std::vector<int> wn_steps;
     std::vector<int> st_slot;     // per layer: its slot (wide layers) or -1 (kept on the device)
     u32 st_nslots = 0;            // W
     u64 st_link_bytes = 0;        // host-link bytes of one proof

@@ -47,8 +47,8 @@ struct ShapeKey {
 
 struct Shape {
     u64 bytes = 0;                     // device bytes of one circuit of this shape
-    bool staged = false;               // resident values exceed the cap: values staged through
-                                       // host memory (copy-once-per-layer), jobs run alone
+    bool staged = false;               // resident values exceed the cap: values through device
+                                       // slots (windowed), jobs run alone
     u64 tr_len = 0, n_in = 0;
     std::vector<vc_circuit *> idle;    // allocated, not in use
     u32 live = 0;                      // allocated (idle or in use)
@@ -146,7 +146,7 @@ Acq acquire(vc_server *s, Job *j, vc_circuit **out)
     d.log_width = j->key.widths.data();
     d.wiring = j->key.kinds.data();
     vc_circuit *c = nullptr;
-    if (server_prepare(s, &d, &c, sh.staged ? VC_VALUES_STAGED : 0u) != VC_OK) return ACQ_FAIL;
+    if (server_prepare(s, &d, &c, sh.staged ? VC_VALUES_WINDOWED : 0u) != VC_OK) return ACQ_FAIL;
     if (circuit_allocate(c) != VC_OK) {
         circuit_free(c);
         return ACQ_FAIL;
@@ -172,8 +172,8 @@ bool ensure_pinned(T *&p, size_t &cap, size_t n)
     return true;
 }
 
-// A job whose values are staged through host memory: its circuit's own
-// launch sequence on the slot's stream (it cannot be merged with others).
+// A job whose values pass through device slots: its circuit's own launch
+// sequence on the slot's stream (it cannot be merged with others).
 vc_status launch_staged(Slot &sl)
 {
     Job *j = sl.jobs[0];
@@ -456,10 +456,11 @@ extern "C" vc_status vc_server_submit(vc_server *s, const vc_circuit_desc *desc,
         sh.n_in = u64(1) << c->s[c->d];
         circuit_free(c);  // host-only object
         if (sh.bytes > s->cap) {
-            // too large to keep its values on the device: stage them through
-            // host memory a layer at a time (Sec. 5.1.2) if that fits
+            // too large to keep every layer on the device: pass the wide
+            // layers through device slots, each iteration run while its two
+            // layers are there (windowed values), if that fits
             vc_circuit *cs = nullptr;
-            if (server_prepare(s, desc, &cs, VC_VALUES_STAGED) == VC_OK) {
+            if (server_prepare(s, desc, &cs, VC_VALUES_WINDOWED) == VC_OK) {
                 sh.bytes = cs->arena_bytes;
                 sh.staged = true;
                 circuit_free(cs);

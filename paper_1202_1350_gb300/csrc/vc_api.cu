@@ -103,8 +103,8 @@ static void plan_eval(vc_circuit *c)
     c->eval_steps.clear();
     c->seg_maxblock.clear();
     int i = (int)c->d - 1;
-    // staged values: every layer alone (its slot is reused three layers on)
-    const bool staged = (c->flags & VC_VALUES_STAGED) != 0;
+    // values through slots: every layer alone (its slot is reused W layers on)
+    const bool staged = (c->flags & VC_VALUES_SLOTTED) != 0;
     auto local = [&](int j) { return !staged && c->kind[j] != W_MATMULT && c->kind[j] != W_EXPLICIT; };
     while (i >= 0) {
         if (!local(i)) {
@@ -252,7 +252,43 @@ static void staged_partition(vc_circuit *c, Arena &A)
     const auto wide = [&](u32 i) { return c->st_slot[i] >= 0; };
     c->st_group.assign(d, -1);
     c->st_groups.clear();
-    {
+    c->wn_steps.clear();
+    if (c->flags & VC_VALUES_WINDOWED) {
+        // Windowed: evaluate from the input up; iteration i is ready once
+        // layer i is evaluated (layer i + 1 already is).  Before a wide layer
+        // overwrites its slot, every ready iteration not yet run joins one
+        // group (run there) if any of them reads the slot's layer.  The
+        // iterations between narrow layers join the last group.
+        std::vector<int> holder(c->st_nslots, -1);
+        if (wide(d)) holder[c->st_slot[d]] = (int)d;
+        std::vector<u32> ready;
+        auto flush = [&]() {
+            if (ready.empty()) return;
+            const u32 g = (u32)c->st_groups.size();
+            c->st_groups.push_back({ready.back(), ready.front()});  // ready runs downward
+            for (u32 j : ready) c->st_group[j] = (int)g;
+            c->wn_steps.push_back(-(int)g - 1);
+            ready.clear();
+        };
+        for (int i = (int)d - 1; i >= 0; i--) {
+            if (wide((u32)i)) {
+                const int L = holder[c->st_slot[i]];  // the layer it replaces
+                if (L >= 0)
+                    for (u32 j : ready)
+                        if ((int)j == L || (int)j + 1 == L) {
+                            flush();
+                            break;
+                        }
+                holder[c->st_slot[i]] = i;
+            }
+            c->wn_steps.push_back(i);
+            if (wide((u32)i) || wide((u32)i + 1)) ready.push_back((u32)i);
+        }
+        flush();
+        if (!c->st_groups.empty())
+            for (u32 i = 0; i < d; i++)
+                if (c->st_group[i] < 0) c->st_group[i] = (int)c->st_groups.size() - 1;
+    } else {
         int lo_ord = -1, hi_ord = -1;  // the current group's wide layers, by ordinal
         std::vector<int> ordinal(d + 1, -1);
         int o = 0;
@@ -312,9 +348,10 @@ static void staged_partition(vc_circuit *c, Arena &A)
         nctr += 2 * (u32)(c->stA[i].size() + c->stB[i].size());
     }
     c->d_stctr = A.take<u32>(nctr + 2);  // list l's launch g: counters stctr_off[l] + 2 g, + 1
-    // host-link traffic of one proof: every wide layer written once, plus
-    // the copies back in
+    // host-link traffic of one proof (staged): every wide layer written once,
+    // plus the copies back in
     c->st_link_bytes = 0;
+    if (c->flags & VC_VALUES_WINDOWED) return;
     for (u32 i = 0; i <= d; i++)
         if (wide(i)) c->st_link_bytes += (u64(1) << c->s[i]) * sizeof(u64);
     for (const StagedCopy &k : staged_copies(*c)) c->st_link_bytes += (u64(1) << c->s[k.layer]) * sizeof(u64);
@@ -356,7 +393,8 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     Arena H;
     H.base = hbase;
     const bool host = (c->flags & VC_VALUES_IN_HOST_MEMORY) != 0;
-    const bool staged = (c->flags & VC_VALUES_STAGED) != 0;
+    const bool staged = (c->flags & VC_VALUES_SLOTTED) != 0;
+    const bool windowed = (c->flags & VC_VALUES_WINDOWED) != 0;  // no host copies
     c->V.assign(d + 1, nullptr);
     c->hV.assign(staged ? d + 1 : 0, nullptr);
     if (staged) {
@@ -384,7 +422,7 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
             if (4 * S(i) > smax) {
                 c->st_slot[i] = ord % (int)W;
                 c->V[i] = slot[ord++ % W];
-                c->hV[i] = H.take<u64>(S(i));
+                if (!windowed) c->hV[i] = H.take<u64>(S(i));
             } else {
                 c->V[i] = A.take<u64>(S(i));
             }
@@ -393,7 +431,7 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     } else {
         for (u32 i = 0; i <= d; i++) c->V[i] = host ? H.take<u64>(S(i)) : A.take<u64>(S(i));
     }
-    c->host_bytes = (host || staged) ? H.off + 256 : 0;
+    c->host_bytes = (host || (staged && !windowed)) ? H.off + 256 : 0;
     Globals &G = c->G;
     G = Globals{};
     G.d = d;
@@ -1243,12 +1281,64 @@ static void enqueue_staged(vc_circuit &c, cudaStream_t st)
     launch_final(P.d_G, P.d_rounds, (int)P.rounds.size(), (int)P.nbig, P.d_outs, (int)P.outs.size(), st);
 }
 
+// Windowed values: one stream evaluates from the input up and runs each
+// group of iterations where the plan placed it (before the layer that
+// overwrites a slot one of them reads), so stream order alone keeps every
+// slot's layer until its last reader is done; the coins run beside the
+// evaluation, and the first group waits for them.
+static void enqueue_windowed(vc_circuit &c, cudaStream_t st)
+{
+    Plan &P = c.P;
+    const Globals *Gs = P.d_G;
+    cudaStream_t sa = P.aux;
+    auto run_list = [&](u32 l) {
+        for (size_t g = 0; g < c.stA[l].size(); g++)
+            launch_waves(Gs, P.d_lw, P.d_pw, P.d_gw, c.d_stA[l][g], (int)c.stA[l][g].size(),
+                         c.d_stctr + c.stctr_off[l] + 2 * g, st);
+        if (!c.stBuild[l].empty()) launch_build23(Gs, c.d_stBuild[l], (int)c.stBuild[l].size(), st);
+        for (size_t g = 0; g < c.stB[l].size(); g++)
+            launch_waves(Gs, P.d_lw, P.d_pw, P.d_gw, c.d_stB[l][g], (int)c.stB[l][g].size(),
+                         c.d_stctr + c.stctr_off[l] + 2 * (c.stA[l].size() + g), st);
+    };
+    launch_params(P.d_G, 0, nullptr, nullptr, st);  // arguments set per launch
+    cudaEventRecord(P.ev_fork, st);
+    cudaStreamWaitEvent(sa, P.ev_fork, 0);
+    launch_coins(Gs, P.ncirc, P.d_eqjobs, (int)P.eqjobs.size(), P.d_scis, P.d_pw, (int)P.pw.size(), sa);
+    cudaEventRecord(P.ev_tables, sa);
+    launch_check_inputs(Gs, P.d_checks, (int)P.checks.size(), st);  // the inputs are in layer d
+    bool coins = false;
+    for (int step : c.wn_steps) {
+        if (step >= 0) {
+            launch_eval_layers(Gs, c.d_stLev, c.d_stEval[step], (int)c.stEval[step].size(), st);
+            // the outputs for the transcript, while layer 0 is in its slot
+            if (step == 0) cudaMemcpyAsync(c.d_out, c.V[0], (u64(1) << c.s[0]) * sizeof(u64), cudaMemcpyDeviceToDevice, st);
+            continue;
+        }
+        if (!coins) {
+            cudaStreamWaitEvent(st, P.ev_tables, 0);
+            coins = true;
+        }
+        run_list((u32)(-step - 1));
+    }
+    if (!coins) cudaStreamWaitEvent(st, P.ev_tables, 0);
+    run_list((u32)c.st_groups.size());  // iterations between narrow layers not placed in a group
+    launch_final(P.d_G, P.d_rounds, (int)P.rounds.size(), (int)P.nbig, P.d_outs, (int)P.outs.size(), st);
+}
+
 static cudaError_t plan_launch(Plan &P, cudaStream_t st, u64 seed = 0, u64 *tr = nullptr,
                                const u64 *in = nullptr)
 {
     cudaError_t e = cudaSuccess;
     if (!P.exec) {
-        e = capture_graph(P.cap, [&](cudaStream_t cs) { P.staged ? enqueue_staged(*P.staged, cs) : enqueue_plan(P, cs); },
+        e = capture_graph(P.cap,
+                          [&](cudaStream_t cs) {
+                              if (!P.staged)
+                                  enqueue_plan(P, cs);
+                              else if (P.staged->flags & VC_VALUES_WINDOWED)
+                                  enqueue_windowed(*P.staged, cs);
+                              else
+                                  enqueue_staged(*P.staged, cs);
+                          },
                           &P.exec,
                           P.own_params ? params_kernel() : nullptr, &P.graph, &P.pnode, &P.pkp);
         if (e != cudaSuccess) {
@@ -1324,7 +1414,8 @@ PlanConfig shape_config(const vc_circuit_desc *desc)
 vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **out, const PlanConfig *cfg,
                           u32 flags)
 {
-    if (flags != 0 && flags != VC_VALUES_IN_HOST_MEMORY && flags != VC_VALUES_STAGED) return VC_EINVAL;
+    if (flags != 0 && flags != VC_VALUES_IN_HOST_MEMORY && flags != VC_VALUES_STAGED && flags != VC_VALUES_WINDOWED)
+        return VC_EINVAL;
     if (!desc || !out || desc->n_layers < 1 || desc->n_layers > 4096 || !desc->log_width || !desc->wiring)
         return VC_EINVAL;
     *out = nullptr;
@@ -1353,7 +1444,7 @@ vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **
     c->by2_g.resize(d);
     for (u32 i = 0; i < d; i++) {
         const u32 si = c->s[i], sn = c->s[i + 1];
-        if (!shape_ok(c->kind[i], si, sn) || ((flags & VC_VALUES_STAGED) && c->kind[i] == W_EXPLICIT)) {
+        if (!shape_ok(c->kind[i], si, sn) || ((flags & VC_VALUES_SLOTTED) && c->kind[i] == W_EXPLICIT)) {
             delete c;
             return VC_EINVAL;
         }
@@ -1411,7 +1502,7 @@ vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **
     plan_eval(c);
     c->P.ncirc = 1;
     c->P.own_params = true;
-    c->P.staged = (flags & VC_VALUES_STAGED) ? c : nullptr;
+    c->P.staged = (flags & VC_VALUES_SLOTTED) ? c : nullptr;
     c->eval_reads_inputs = first_eval_is_input_run(c->P, c->d);
     Arena A;
     A.off = layout(c, 0, 0);
@@ -1453,7 +1544,7 @@ vc_status circuit_allocate(vc_circuit *c)
         return e == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA;
     }
     uintptr_t hbase = 0;
-    const bool staged = (c->flags & VC_VALUES_STAGED) != 0;
+    const bool staged = (c->flags & VC_VALUES_SLOTTED) != 0;
     if (c->host_bytes) {
         // mapped for kernels reading the values in place; staged values are
         // only copied, by address on the host
@@ -1519,12 +1610,12 @@ extern "C" vc_status vc_circuit_create_ex(const vc_circuit_desc *desc, int devic
     if (!out) return VC_EINVAL;
     *out = nullptr;
     if (flags == VC_VALUES_AUTO) {
-        // device-resident values, else copy-once-per-layer, else mapped host
+        // device-resident values, else windowed ones, else mapped host
         // memory: the first whose memory can be had
         vc_status st = vc_circuit_create_ex(desc, device, 0, out);
         if (st != VC_ENOMEM) return st;
-        st = vc_circuit_create_ex(desc, device, VC_VALUES_STAGED, out);
-        if (st != VC_ENOMEM && st != VC_EINVAL) return st;  // VC_EINVAL: explicit wirings are not staged
+        st = vc_circuit_create_ex(desc, device, VC_VALUES_WINDOWED, out);
+        if (st != VC_ENOMEM && st != VC_EINVAL) return st;  // VC_EINVAL: explicit wirings are not windowed
         return vc_circuit_create_ex(desc, device, VC_VALUES_IN_HOST_MEMORY, out);
     }
     vc_circuit *c = nullptr;
@@ -1741,7 +1832,7 @@ extern "C" vc_status vc_prove_pergate(vc_circuit *c, const uint64_t *inputs, uin
                                       void *stream)
 {
     if (!c || !inputs || !transcript) return VC_EINVAL;
-    if (c->flags & VC_VALUES_STAGED) return VC_EINVAL;  // reads every layer in place
+    if (c->flags & VC_VALUES_SLOTTED) return VC_EINVAL;  // reads every layer in place
     DevGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int ki = ptr_kind(inputs, c->device), kt = ptr_kind(transcript, c->device);
@@ -2224,7 +2315,7 @@ extern "C" vc_status vc_batch_create(vc_circuit *const *circuits, int n, vc_batc
     *out = nullptr;
     if (n <= 0 || !circuits) return VC_EINVAL;
     for (int j = 0; j < n; j++) {
-        if (!circuits[j] || circuits[j]->device != circuits[0]->device || (circuits[j]->flags & VC_VALUES_STAGED))
+        if (!circuits[j] || circuits[j]->device != circuits[0]->device || (circuits[j]->flags & VC_VALUES_SLOTTED))
             return VC_EINVAL;
         for (int k = 0; k < j; k++)
             if (circuits[k] == circuits[j]) return VC_EINVAL;

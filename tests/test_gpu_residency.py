@@ -105,7 +105,7 @@ def test_bad_flags_rejected():
     w, k = circuits.f2(3)
     desc, keep = vc._desc_struct(w, k)
     h = ctypes.c_void_p()
-    for flags in (6, 3, 5, 8):
+    for flags in (6, 3, 5, 16, 10):
         assert vc.lib().vc_circuit_create_ex(ctypes.byref(desc), 0, flags, ctypes.byref(h)) == vc.VC_EINVAL
 
 
@@ -113,14 +113,16 @@ STAGED = [("f2", 0), ("f2", 1), ("f2", 2), ("f2", 5), ("f2", 13), ("f0", 3), ("f
           ("matmult", 4)]
 
 
+@pytest.mark.parametrize("mode", ["staged", "windowed"])
 @pytest.mark.parametrize("family,logn", STAGED)
-def test_staged_values_equal_oracle(family, logn):
-    """Copy-once-per-layer: every transcript entry equals the oracle's (device
-    and host transcripts, two proofs in a row on one handle), the verifier
-    accepts it and vc_evaluate gives the outputs."""
+def test_staged_values_equal_oracle(family, logn, mode):
+    """Copy-once-per-layer (staged) and windowed values: every transcript
+    entry equals the oracle's (device and host transcripts, two proofs in a
+    row on one handle), the verifier accepts it and vc_evaluate gives the
+    outputs."""
     w, k = circuits.by_name(family, logn)
     x = I.job_inputs(family, logn, 70 + logn)
-    h = vc.vc_circuit_create(w, k, staged=True)
+    h = vc.vc_circuit_create(w, k, **{mode: True})
     try:
         for seed in (13, 14):
             want = oracle_prove(w, k, x, seed)
@@ -140,14 +142,22 @@ def test_staged_values_large_equal_device_and_device_bytes():
     instead of 62 layers of values) and F2 less too (two slots for its wide
     layers of 2^18, 2^18 and 2^17 values).  Host-link bytes: every wide layer
     crosses once on the way out; F2's input layer comes back in once (its
-    slot held layer 17 meanwhile); F0's wide layers come back at most once."""
+    slot held layer 17 meanwhile); F0's wide layers come back at most once.
+    Windowed values: the same device bytes (up to launch lists), the same
+    proofs, no host link."""
     for fam, n, seed in (("f2", 18, 5), ("f0", 12, 6)):
         w, k = circuits.by_name(fam, n)
         x = I.job_inputs(fam, n, 40 + n)
         hd = vc.vc_circuit_create(w, k)
         hs = vc.vc_circuit_create(w, k, staged=True)
+        hw = vc.vc_circuit_create(w, k, windowed=True)
         try:
             assert (prove(hs, x, seed) == prove(hd, x, seed)).all(), fam
+            assert (prove(hw, x, seed) == prove(hd, x, seed)).all(), fam
+            # the same slots and narrow layers (the launch lists differ slightly)
+            assert abs(vc.vc_circuit_bytes(hw) - vc.vc_circuit_bytes(hs)) <= 4096
+            info = vc.vc_circuit_get_info(hw)
+            assert info["link_bytes"] == 0 and info["residency"] == vc.VC_VALUES_WINDOWED
             assert vc.vc_circuit_get_info(hd)["link_bytes"] == 0
             link = vc.vc_circuit_get_info(hs)["link_bytes"]
             wide = 8 * sum(1 << s for s in w if 4 * (1 << s) > (1 << max(w)))
@@ -162,11 +172,13 @@ def test_staged_values_large_equal_device_and_device_bytes():
         finally:
             vc.vc_circuit_destroy(hd)
             vc.vc_circuit_destroy(hs)
+            vc.vc_circuit_destroy(hw)
 
 
-def test_staged_rejected_where_layers_are_read_in_place():
+@pytest.mark.parametrize("mode", ["staged", "windowed"])
+def test_staged_rejected_where_layers_are_read_in_place(mode):
     w, k = circuits.f2(6)
-    h = vc.vc_circuit_create(w, k, staged=True)
+    h = vc.vc_circuit_create(w, k, **{mode: True})
     h2 = vc.vc_circuit_create(w, k)
     try:
         with pytest.raises(vc.VcError):
@@ -179,29 +191,29 @@ def test_staged_rejected_where_layers_are_read_in_place():
         vc.vc_circuit_destroy(h2)
     wp, kp, ex = circuits.pattern_match(5, 2)
     with pytest.raises(vc.VcError):
-        vc.vc_circuit_create(wp, kp, ex, staged=True)
+        vc.vc_circuit_create(wp, kp, ex, **{mode: True})
 
 
 def test_auto_residency_follows_the_memory_cap():
     """VC_VALUES_AUTO under the library's device-memory cap: device-resident
-    values when the whole circuit fits, staged values when only they fit,
+    values when the whole circuit fits, windowed values when only they fit,
     mapped host memory when neither does, and VC_ENOMEM below that; every
     choice gives the oracle's transcript.  F0 with 2^10 inputs (62 layers of
-    2^11 values), where the staged mode needs far less device memory."""
+    2^11 values), where windowed values need far less device memory."""
     w, k = circuits.f0(10)
     x = I.job_inputs("f0", 10, 5)
     want = oracle_prove(w, k, x, 3)
     sizes = {}
-    for mode, kw in ((0, {}), (vc.VC_VALUES_STAGED, {"staged": True}), (vc.VC_VALUES_IN_HOST_MEMORY,
-                                                                          {"host_values": True})):
+    for mode, kw in ((0, {}), (vc.VC_VALUES_WINDOWED, {"windowed": True}), (vc.VC_VALUES_IN_HOST_MEMORY,
+                                                                              {"host_values": True})):
         h = vc.vc_circuit_create(w, k, **kw)
         sizes[mode] = vc.vc_circuit_bytes(h)
         vc.vc_circuit_destroy(h)
-    dev, stg, hst = sizes[0], sizes[vc.VC_VALUES_STAGED], sizes[vc.VC_VALUES_IN_HOST_MEMORY]
+    dev, stg, hst = sizes[0], sizes[vc.VC_VALUES_WINDOWED], sizes[vc.VC_VALUES_IN_HOST_MEMORY]
     assert hst < stg < dev
     used = vc.vc_get_memory_usage()[0]
     try:
-        for cap, mode in ((dev, 0), ((stg + dev) // 2, vc.VC_VALUES_STAGED),
+        for cap, mode in ((dev, 0), ((stg + dev) // 2, vc.VC_VALUES_WINDOWED),
                           ((hst + stg) // 2, vc.VC_VALUES_IN_HOST_MEMORY)):
             vc.vc_set_memory_limit(used + cap, 0)
             h = vc.vc_circuit_create(w, k, auto=True)
@@ -216,7 +228,7 @@ def test_auto_residency_follows_the_memory_cap():
         assert e.value.status == vc.VC_ENOMEM
     finally:
         vc.vc_set_memory_limit(0, 0)
-    # explicit wirings skip the staged step
+    # explicit wirings skip the windowed step
     wp, kp, ex = circuits.pattern_match(5, 2)
     h = vc.vc_circuit_create(wp, kp, ex)
     dev_p = vc.vc_circuit_bytes(h)

@@ -168,15 +168,15 @@ def test_server_overlaps_launch_sets():
         srv.close()
 
 
-def test_over_cap_job_proved_with_staged_values():
-    """A job whose circuit does not fit the memory cap with its values on the
-    device is proved with the values staged through host memory (copy once
-    per layer) instead of being refused; it equals the oracle, and jobs of
-    other shapes around it are unaffected.  Below even the staged footprint
-    the submission is refused (VC_EBUSY)."""
+def test_over_cap_job_proved_with_windowed_values():
+    """A job whose circuit does not fit the memory cap with every layer on the
+    device is proved with windowed values (the wide layers through device
+    slots) instead of being refused; it equals the oracle, and jobs of other
+    shapes around it are unaffected.  Below even the windowed footprint the
+    submission is refused (VC_EBUSY)."""
     w, k = circuits.f0(8)
     hd = vc.vc_circuit_create(w, k)
-    hs = vc.vc_circuit_create(w, k, staged=True)
+    hs = vc.vc_circuit_create(w, k, windowed=True)
     resident, staged = vc.vc_circuit_bytes(hd), vc.vc_circuit_bytes(hs)
     vc.vc_circuit_destroy(hd)
     vc.vc_circuit_destroy(hs)
@@ -187,7 +187,7 @@ def test_over_cap_job_proved_with_staged_values():
         for j, (fam, logn) in enumerate([("f2", 6), ("f0", 8), ("f2", 7), ("f0", 8), ("matmult", 2)]):
             wj, kj = circuits.by_name(fam, logn)
             x = I.job_inputs(fam, logn, 700 + j)
-            host = j == 3  # one staged job with a host transcript
+            host = j == 3  # one windowed job with a host transcript
             tr = np.zeros(circuits.transcript_len(wj), np.uint64) if host else \
                 torch.empty(circuits.transcript_len(wj), dtype=torch.int64, device="cuda")
             jobs.append((srv.submit(wj, kj, dev(x), 40 + j, tr), wj, kj, x, 40 + j, tr))
