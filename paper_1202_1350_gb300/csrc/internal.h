@@ -218,6 +218,9 @@ struct vc_circuit {
     // windowed: the proof's order of evaluations (a layer index >= 0) and
     // iteration groups run (-(g + 1))
     std::vector<int> wn_steps;
+    // per layer: the evaluation step that launches it (a run of narrow layers,
+    // at its first layer), -2 (inside such a run) or -1 (alone, per layer)
+    std::vector<int> st_evalstep;
     std::vector<int> st_slot;     // per layer: its slot (wide layers) or -1 (kept on the device)
     u32 st_nslots = 0;            // W
     u64 st_link_bytes = 0;        // host-link bytes of one proof

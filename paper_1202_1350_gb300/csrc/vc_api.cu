@@ -103,9 +103,15 @@ static void plan_eval(vc_circuit *c)
     c->eval_steps.clear();
     c->seg_maxblock.clear();
     int i = (int)c->d - 1;
-    // values through slots: every layer alone (its slot is reused W layers on)
+    // values through slots: every wide layer alone (it goes into a slot, which
+    // the proof may have to free first); narrow layers in runs as usual
     const bool staged = (c->flags & VC_VALUES_SLOTTED) != 0;
-    auto local = [&](int j) { return !staged && c->kind[j] != W_MATMULT && c->kind[j] != W_EXPLICIT; };
+    u64 smax = 1;
+    for (u32 j = 0; j <= c->d; j++) smax = std::max(smax, u64(1) << c->s[j]);
+    auto wide = [&](int j) { return 4 * (u64(1) << c->s[j]) > smax; };
+    auto local = [&](int j) {
+        return !(staged && wide(j)) && c->kind[j] != W_MATMULT && c->kind[j] != W_EXPLICIT;
+    };
     while (i >= 0) {
         if (!local(i)) {
             c->eval_steps.push_back(-i - 1);
@@ -328,6 +334,14 @@ static void staged_partition(vc_circuit *c, Arena &A)
     for (u32 i = 0; i < d; i++) {
         const u64 blocks = ((u64(1) << c->s[i]) + 255) / 256;
         for (u64 b = 0; b < blocks; b++) c->stEval[i].push_back({i, (u32)b});
+    }
+    c->st_evalstep.assign(d, -1);
+    for (size_t k = 0; k < c->eval_steps.size(); k++) {
+        const int step = c->eval_steps[k];
+        if (step < 0) continue;
+        const EvalSeg &S = P.segs[step];
+        for (u32 j = S.tail_lo; j <= S.i_hi; j++) c->st_evalstep[j] = -2;
+        c->st_evalstep[S.i_hi] = (int)k;
     }
     c->d_stLev = A.take<LayerEval>(d);
     auto take_lists = [&](auto &lists, auto &dv) {
@@ -1205,6 +1219,18 @@ static cudaError_t set_node_args(cudaGraphExec_t exec, cudaGraphNode_t node, cud
 // ahead of time (while the previous iteration runs) when the slot's previous
 // layer is no longer needed by then.  Coins and the final reduction are
 // those of the resident plan.
+// Evaluation of layer i in a proof with values through slots: a wide layer
+// alone; a run of narrow layers in one launch, at its first layer.
+static void eval_layer(vc_circuit &c, u32 i, cudaStream_t st)
+{
+    Plan &P = c.P;
+    const int k = c.st_evalstep[i];
+    if (k >= 0)
+        launch_eval_segs(P.d_G, P.d_segs, P.d_seg_items[k], (int)P.seg_items[k].size(), P.seg_maxblock[k], st);
+    else if (k == -1)
+        launch_eval_layers(P.d_G, c.d_stLev, c.d_stEval[i], (int)c.stEval[i].size(), st);
+}
+
 static void enqueue_staged(vc_circuit &c, cudaStream_t st)
 {
     Plan &P = c.P;
@@ -1248,7 +1274,7 @@ static void enqueue_staged(vc_circuit &c, cudaStream_t st)
             if (holder[sl] >= 0) cudaStreamWaitEvent(st, ev(holder[sl], ON_HOST), 0);
             holder[sl] = i;
         }
-        launch_eval_layers(Gs, c.d_stLev, c.d_stEval[i], (int)c.stEval[i].size(), st);
+        eval_layer(c, (u32)i, st);
         if (wide(i)) to_host(i);
     }
     // the outputs for the final reduction (layer 0's slot may be reused)
@@ -1309,7 +1335,7 @@ static void enqueue_windowed(vc_circuit &c, cudaStream_t st)
     bool coins = false;
     for (int step : c.wn_steps) {
         if (step >= 0) {
-            launch_eval_layers(Gs, c.d_stLev, c.d_stEval[step], (int)c.stEval[step].size(), st);
+            eval_layer(c, (u32)step, st);
             // the outputs for the transcript, while layer 0 is in its slot
             if (step == 0) cudaMemcpyAsync(c.d_out, c.V[0], (u64(1) << c.s[0]) * sizeof(u64), cudaMemcpyDeviceToDevice, st);
             continue;
@@ -1503,7 +1529,8 @@ vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **
     c->P.ncirc = 1;
     c->P.own_params = true;
     c->P.staged = (flags & VC_VALUES_SLOTTED) ? c : nullptr;
-    c->eval_reads_inputs = first_eval_is_input_run(c->P, c->d);
+    // values through slots: the proof copies the inputs into their layer first
+    c->eval_reads_inputs = !(flags & VC_VALUES_SLOTTED) && first_eval_is_input_run(c->P, c->d);
     Arena A;
     A.off = layout(c, 0, 0);
     plan_take(c->P, A, false);
