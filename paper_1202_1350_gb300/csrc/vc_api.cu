@@ -94,6 +94,73 @@ static bool first_eval_is_input_run(const Plan &P, u32 d)
 // run's input layer (about 256 CTAs for wide layers) and keeps going while its
 // block stays >= 32 entries (or while one CTA covers the whole layer) and
 // <= 4096 entries.  Layers outside any run are evaluated alone (k_eval_layer).
+// Slots of the wide layers (more than a quarter of the widest) when the
+// values pass through device slots: W slots of the widest layer's size, as
+// many as the wide layers' values fill (so the slots never take more device
+// memory than the layers would), at least 2 (an iteration's two layers) and
+// at most STAGED_SLOTS; the k-th wide layer in slot k mod W.
+static void slot_plan(vc_circuit *c)
+{
+    const u32 d = c->d;
+    u64 smax = 1, wide_sum = 0;
+    u32 nwide = 0;
+    for (u32 i = 0; i <= d; i++) smax = std::max(smax, u64(1) << c->s[i]);
+    for (u32 i = 0; i <= d; i++)
+        if (4 * (u64(1) << c->s[i]) > smax) {
+            nwide++;
+            wide_sum += u64(1) << c->s[i];
+        }
+    const u32 W = std::min<u32>(nwide, (u32)std::min<u64>(STAGED_SLOTS, std::max<u64>(2, wide_sum / smax)));
+    c->st_nslots = W;
+    c->st_slot.assign(d + 1, -1);
+    int ord = 0;
+    for (u32 i = 0; i <= d; i++)
+        if (4 * (u64(1) << c->s[i]) > smax) c->st_slot[i] = ord++ % (int)W;
+}
+
+// Windowed values: evaluate from the input up; iteration i is ready once
+// layer i is evaluated (layer i + 1 already is).  Before a wide layer
+// overwrites its slot, every ready iteration not yet run joins one group
+// (run there) if any of them reads the slot's layer.  The iterations between
+// narrow layers join the last group.  Sets st_group, st_groups and wn_steps.
+static void windowed_groups(vc_circuit *c)
+{
+    const u32 d = c->d;
+    const auto wide = [&](u32 i) { return c->st_slot[i] >= 0; };
+    c->st_group.assign(d, -1);
+    c->st_groups.clear();
+    c->wn_steps.clear();
+    std::vector<int> holder(c->st_nslots, -1);
+    if (wide(d)) holder[c->st_slot[d]] = (int)d;
+    std::vector<u32> ready;
+    auto flush = [&]() {
+        if (ready.empty()) return;
+        const u32 g = (u32)c->st_groups.size();
+        c->st_groups.push_back({ready.back(), ready.front()});  // ready runs downward
+        for (u32 j : ready) c->st_group[j] = (int)g;
+        c->wn_steps.push_back(-(int)g - 1);
+        ready.clear();
+    };
+    for (int i = (int)d - 1; i >= 0; i--) {
+        if (wide((u32)i)) {
+            const int L = holder[c->st_slot[i]];  // the layer it replaces
+            if (L >= 0)
+                for (u32 j : ready)
+                    if ((int)j == L || (int)j + 1 == L) {
+                        flush();
+                        break;
+                    }
+            holder[c->st_slot[i]] = i;
+        }
+        c->wn_steps.push_back(i);
+        if (wide((u32)i) || wide((u32)i + 1)) ready.push_back((u32)i);
+    }
+    flush();
+    if (!c->st_groups.empty())
+        for (u32 i = 0; i < d; i++)
+            if (c->st_group[i] < 0) c->st_group[i] = (int)c->st_groups.size() - 1;
+}
+
 static void plan_eval(vc_circuit *c)
 {
     Plan &P = c->P;
@@ -103,12 +170,19 @@ static void plan_eval(vc_circuit *c)
     c->eval_steps.clear();
     c->seg_maxblock.clear();
     int i = (int)c->d - 1;
-    // values through slots: every wide layer alone (it goes into a slot, which
-    // the proof may have to free first); narrow layers in runs as usual
-    const bool staged = (c->flags & VC_VALUES_SLOTTED) != 0;
-    u64 smax = 1;
-    for (u32 j = 0; j <= c->d; j++) smax = std::max(smax, u64(1) << c->s[j]);
-    auto wide = [&](int j) { return 4 * (u64(1) << c->s[j]) > smax; };
+    // values through slots: with staged values every wide layer alone (its
+    // slot may have to be freed and it goes to host memory right after);
+    // with windowed values runs stop where a group of iterations must run
+    // first (flush[j]: before layer j is evaluated); narrow layers in runs
+    const bool staged = (c->flags & VC_VALUES_STAGED) != 0;
+    std::vector<char> flush(c->d + 1, 0);
+    if (c->flags & VC_VALUES_SLOTTED) slot_plan(c);
+    if (c->flags & VC_VALUES_WINDOWED) {
+        windowed_groups(c);
+        for (size_t k = 1; k < c->wn_steps.size(); k++)
+            if (c->wn_steps[k] >= 0 && c->wn_steps[k - 1] < 0) flush[c->wn_steps[k]] = 1;
+    }
+    auto wide = [&](int j) { return (c->flags & VC_VALUES_SLOTTED) && c->st_slot[j] >= 0; };
     auto local = [&](int j) {
         return !(staged && wide(j)) && c->kind[j] != W_MATMULT && c->kind[j] != W_EXPLICIT;
     };
@@ -129,7 +203,7 @@ static void plan_eval(vc_circuit *c)
             int e = cl, j = i;
             i_lo = i + 1;
             maxblock = 1u << cl;
-            while (j >= 0 && local(j)) {
+            while (j >= 0 && local(j) && !(j < i && flush[j])) {
                 const int ne = e + (int)c->s[j] - (int)c->s[j + 1];
                 if (ne < 0 || ne > 11) break;
                 if (c->kind[j] == W_F0_PAIR && ne < 1) break;
@@ -157,7 +231,7 @@ static void plan_eval(vc_circuit *c)
         // input <= 2^16) go to the CTA that finishes last
         S.tail_lo = S.i_lo;
         if (S.nchunks > 1 && c->s[i_lo] <= 16)
-            for (int j = i_lo - 1; j >= 0 && local(j) && c->s[j] <= 11; j--) {
+            for (int j = i_lo - 1; j >= 0 && local(j) && !flush[j] && c->s[j] <= 11; j--) {
                 S.tail_lo = (u32)j;
                 maxblock = std::max(maxblock, 1u << c->s[j]);
             }
@@ -256,45 +330,11 @@ static void staged_partition(vc_circuit *c, Arena &A)
     // at most W; group g is launch list g.  Every iteration between narrow
     // layers goes to the last list (ng), run first.
     const auto wide = [&](u32 i) { return c->st_slot[i] >= 0; };
-    c->st_group.assign(d, -1);
-    c->st_groups.clear();
-    c->wn_steps.clear();
     if (c->flags & VC_VALUES_WINDOWED) {
-        // Windowed: evaluate from the input up; iteration i is ready once
-        // layer i is evaluated (layer i + 1 already is).  Before a wide layer
-        // overwrites its slot, every ready iteration not yet run joins one
-        // group (run there) if any of them reads the slot's layer.  The
-        // iterations between narrow layers join the last group.
-        std::vector<int> holder(c->st_nslots, -1);
-        if (wide(d)) holder[c->st_slot[d]] = (int)d;
-        std::vector<u32> ready;
-        auto flush = [&]() {
-            if (ready.empty()) return;
-            const u32 g = (u32)c->st_groups.size();
-            c->st_groups.push_back({ready.back(), ready.front()});  // ready runs downward
-            for (u32 j : ready) c->st_group[j] = (int)g;
-            c->wn_steps.push_back(-(int)g - 1);
-            ready.clear();
-        };
-        for (int i = (int)d - 1; i >= 0; i--) {
-            if (wide((u32)i)) {
-                const int L = holder[c->st_slot[i]];  // the layer it replaces
-                if (L >= 0)
-                    for (u32 j : ready)
-                        if ((int)j == L || (int)j + 1 == L) {
-                            flush();
-                            break;
-                        }
-                holder[c->st_slot[i]] = i;
-            }
-            c->wn_steps.push_back(i);
-            if (wide((u32)i) || wide((u32)i + 1)) ready.push_back((u32)i);
-        }
-        flush();
-        if (!c->st_groups.empty())
-            for (u32 i = 0; i < d; i++)
-                if (c->st_group[i] < 0) c->st_group[i] = (int)c->st_groups.size() - 1;
+        // groups and steps from windowed_groups (plan_eval)
     } else {
+        c->st_group.assign(d, -1);
+        c->st_groups.clear();
         int lo_ord = -1, hi_ord = -1;  // the current group's wide layers, by ordinal
         std::vector<int> ordinal(d + 1, -1);
         int o = 0;
@@ -418,24 +458,15 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
         // device.  W: as many slots as the wide layers' values fill, so the
         // slots never take more device memory than the layers would, at
         // least 2 (an iteration's two layers) and at most STAGED_SLOTS
-        u64 smax = 1, wide_sum = 0;
-        u32 nwide = 0;
+        // (slot_plan, called by plan_eval, chose W and each wide layer's slot)
+        u64 smax = 1;
         for (u32 i = 0; i <= d; i++) smax = std::max(smax, S(i));
-        for (u32 i = 0; i <= d; i++)
-            if (4 * S(i) > smax) {
-                nwide++;
-                wide_sum += S(i);
-            }
-        const u32 W = std::min<u32>(nwide, (u32)std::min<u64>(STAGED_SLOTS, std::max<u64>(2, wide_sum / smax)));
-        c->st_nslots = W;
+        const u32 W = c->st_nslots;
         std::vector<u64 *> slot(W);
         for (u32 k = 0; k < W; k++) slot[k] = A.take<u64>(smax);
-        c->st_slot.assign(d + 1, -1);
-        int ord = 0;
         for (u32 i = 0; i <= d; i++) {
-            if (4 * S(i) > smax) {
-                c->st_slot[i] = ord % (int)W;
-                c->V[i] = slot[ord++ % W];
+            if (c->st_slot[i] >= 0) {
+                c->V[i] = slot[c->st_slot[i]];
                 if (!windowed) c->hV[i] = H.take<u64>(S(i));
             } else {
                 c->V[i] = A.take<u64>(S(i));
