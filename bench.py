@@ -307,9 +307,9 @@ def run_special_purpose(flush, shapes=((1048, 1001), (4995, 5005)), reps=3):
     h = 5005 = 5 7 11 13, v = 4995: Sec. 6.3's table row of 39.1 KB of verifier
     space and 78.1 KB of proof); the answer is checked against sum a_i^2.
     verify_stream_ms: the verifier fed from page-locked host memory in 16
-    absorb calls of whole rows (as rows would arrive), double-buffered through
-    the device, from begin to the end's answer; stream_gbs: the rows' bytes
-    over that time."""
+    asynchronous absorb calls of whole rows (as rows would arrive),
+    double-buffered through the device, from begin to the end's answer;
+    stream_gbs: the rows' bytes over that time."""
     import torch
     from paper_1202_1350_gb300 import vc
     from paper_1202_1350_gb300 import inputs as I
@@ -339,8 +339,8 @@ def run_special_purpose(flush, shapes=((1048, 1001), (4995, 5005)), reps=3):
             torch.cuda.synchronize()
             t3 = time.perf_counter()
             vc.vc_f2sp_verify_begin(s, 177 + k)
-            for x0, x1 in zip(parts[:-1], parts[1:]):
-                vc.vc_f2sp_verify_absorb(s, ah[x0 * h:x1 * h], int(x0), int(x1 - x0))
+            for x0, x1 in zip(parts[:-1], parts[1:]):  # each part its own rows: no buffer is refilled
+                vc.vc_f2sp_verify_absorb_async(s, ah[x0 * h:x1 * h], int(x0), int(x1 - x0))
             acc2, f2s = vc.vc_f2sp_verify_end(s, proof)
             t4 = time.perf_counter()
             ok &= acc2 and f2s == f2

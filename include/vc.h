@@ -509,7 +509,7 @@ vc_status vc_f2sp_prove(vc_f2sp *s, const uint64_t *a, uint64_t *proof, void *st
  * rejection) and *f2 = sum of the proof's even entries, synchronously.
  * VC_EINVAL from end if an absorbed entry was >= p.  begin and absorb are
  * asynchronous.  Device rows are read in place (keep them until end).  Host
- * rows stream through two device buffers of about 8 MB of whole rows
+ * rows stream through two device buffers of about 16 MB of whole rows
  * (Sec. 4.2's double buffering): each chunk is copied on the verifier's own
  * copy stream into one buffer while the previous chunk is absorbed from the
  * other, and the alternation carries over from one absorb call to the next;
@@ -519,6 +519,15 @@ vc_status vc_f2sp_prove(vc_f2sp *s, const uint64_t *a, uint64_t *proof, void *st
 vc_status vc_f2sp_verify_begin(vc_f2sp *s, uint64_t seed, void *stream);
 vc_status vc_f2sp_verify_absorb(vc_f2sp *s, const uint64_t *rows, uint64_t first_row, uint64_t nrows,
                                 void *stream);
+
+/* As vc_f2sp_verify_absorb, but for host rows it returns once the rows of
+ * the previous absorb call have been copied (at once for the first call), so
+ * the copy engine never waits for the host: a caller alternating two (or
+ * more) host buffers refills the one it passed two calls ago.  The rows of
+ * the last call are in use until vc_f2sp_verify_end returns.  Device rows
+ * behave as with vc_f2sp_verify_absorb. */
+vc_status vc_f2sp_verify_absorb_async(vc_f2sp *s, const uint64_t *rows, uint64_t first_row, uint64_t nrows,
+                                      void *stream);
 vc_status vc_f2sp_verify_end(vc_f2sp *s, const uint64_t *proof, uint64_t *f2, int *accept, void *stream);
 
 /* Elementwise field product out[k] = a[k] b[k] mod p on the device (device

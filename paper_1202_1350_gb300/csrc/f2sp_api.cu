@@ -30,6 +30,8 @@ struct vc_f2sp {
     int next_buf = 0;
     cudaStream_t rcopy = nullptr;
     cudaEvent_t copied[2] = {}, absorbed[2] = {};
+    cudaEvent_t call_copied[2] = {};  // absorb call k's last copy: call_copied[k % 2]
+    u64 ncalls = 0;
 };
 
 namespace {
@@ -219,6 +221,7 @@ extern "C" vc_status vc_f2sp_destroy(vc_f2sp *s)
         if (s->rbuf[b]) lib_free(s->rbuf[b]);
         if (s->copied[b]) cudaEventDestroy(s->copied[b]);
         if (s->absorbed[b]) cudaEventDestroy(s->absorbed[b]);
+        if (s->call_copied[b]) cudaEventDestroy(s->call_copied[b]);
     }
     if (s->rcopy) cudaStreamDestroy(s->rcopy);
     delete s;
@@ -226,9 +229,12 @@ extern "C" vc_status vc_f2sp_destroy(vc_f2sp *s)
 }
 
 // Rows per streaming chunk: about 8 MB, whole rows, at most v.
+#ifndef SP_CHUNK_LOG
+#define SP_CHUNK_LOG 21  // streaming chunks of about 2^SP_CHUNK_LOG entries (16 MB)
+#endif
 static u64 sp_chunk_rows(u64 v, u64 h)
 {
-    const u64 rows = std::max<u64>(1, (u64(1) << 20) / h);
+    const u64 rows = std::max<u64>(1, (u64(1) << SP_CHUNK_LOG) / h);
     return std::min(rows, v);
 }
 
@@ -241,6 +247,7 @@ static vc_status sp_stream_prepare(vc_f2sp *s)
     for (int b = 0; b < 2 && e == cudaSuccess; b++) {
         e = cudaEventCreateWithFlags(&s->copied[b], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->absorbed[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->call_copied[b], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->rcopy, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -249,8 +256,9 @@ static vc_status sp_stream_prepare(vc_f2sp *s)
             if (s->rbuf[b]) lib_free(s->rbuf[b]);
             if (s->copied[b]) cudaEventDestroy(s->copied[b]);
             if (s->absorbed[b]) cudaEventDestroy(s->absorbed[b]);
+            if (s->call_copied[b]) cudaEventDestroy(s->call_copied[b]);
             s->rbuf[b] = nullptr;
-            s->copied[b] = s->absorbed[b] = nullptr;
+            s->copied[b] = s->absorbed[b] = s->call_copied[b] = nullptr;
         }
         s->rcopy = nullptr;
         return e == cudaErrorMemoryAllocation ? VC_ENOMEM : VC_ECUDA;
@@ -307,8 +315,10 @@ extern "C" vc_status vc_f2sp_verify_begin(vc_f2sp *s, uint64_t seed, void *strea
     return cuda_status(cudaGetLastError());
 }
 
-extern "C" vc_status vc_f2sp_verify_absorb(vc_f2sp *s, const uint64_t *rows, uint64_t first_row, uint64_t nrows,
-                                           void *stream)
+// One absorb call.  Host rows: returns once the rows of this call (wait_own)
+// or of the previous call (otherwise) have been copied to the device.
+static vc_status sp_absorb(vc_f2sp *s, const uint64_t *rows, uint64_t first_row, uint64_t nrows, void *stream,
+                           bool wait_own)
 {
     if (!s || !rows || first_row > s->v || nrows > s->v - first_row) return VC_EINVAL;
     if (nrows == 0) return VC_OK;
@@ -327,7 +337,6 @@ extern "C" vc_status vc_f2sp_verify_absorb(vc_f2sp *s, const uint64_t *rows, uin
     if (ps != VC_OK) return ps;
     const u64 h = s->h;
     cudaError_t e = cudaSuccess;
-    int last = -1;
     for (u64 r = 0; r < nrows && e == cudaSuccess; r += s->chunk_rows) {
         const u64 m = std::min(s->chunk_rows, nrows - r);
         const int b = s->next_buf;
@@ -342,12 +351,26 @@ extern "C" vc_status vc_f2sp_verify_absorb(vc_f2sp *s, const uint64_t *rows, uin
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaEventRecord(s->absorbed[b], st);
-        last = b;
     }
-    // the rows have been read when the last copy is done: the caller may
-    // refill its buffer on return while the absorbs run on
-    if (e == cudaSuccess && last >= 0) e = cudaEventSynchronize(s->copied[last]);
+    // the rows have been read when the call's last copy is done: the caller
+    // may refill that buffer then while the absorbs run on
+    const u64 call = s->ncalls++;
+    if (e == cudaSuccess) e = cudaEventRecord(s->call_copied[call & 1], s->rcopy);
+    if (e == cudaSuccess && wait_own) e = cudaEventSynchronize(s->call_copied[call & 1]);
+    if (e == cudaSuccess && !wait_own && call > 0) e = cudaEventSynchronize(s->call_copied[(call - 1) & 1]);
     return cuda_status(e);
+}
+
+extern "C" vc_status vc_f2sp_verify_absorb(vc_f2sp *s, const uint64_t *rows, uint64_t first_row, uint64_t nrows,
+                                           void *stream)
+{
+    return sp_absorb(s, rows, first_row, nrows, stream, true);
+}
+
+extern "C" vc_status vc_f2sp_verify_absorb_async(vc_f2sp *s, const uint64_t *rows, uint64_t first_row,
+                                                 uint64_t nrows, void *stream)
+{
+    return sp_absorb(s, rows, first_row, nrows, stream, false);
 }
 
 extern "C" vc_status vc_f2sp_verify_end(vc_f2sp *s, const uint64_t *proof, uint64_t *f2, int *accept, void *stream)

@@ -125,6 +125,7 @@ def lib():
             L.vc_f2sp_prove.argtypes = [vp, vp, vp, vp]
             L.vc_f2sp_verify_begin.argtypes = [vp, ctypes.c_uint64, vp]
             L.vc_f2sp_verify_absorb.argtypes = [vp, vp, ctypes.c_uint64, ctypes.c_uint64, vp]
+            L.vc_f2sp_verify_absorb_async.argtypes = [vp, vp, ctypes.c_uint64, ctypes.c_uint64, vp]
             L.vc_f2sp_verify_end.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int),
                                              vp]
             L.vc_circuit_sync.argtypes = [vp, vp]
@@ -173,8 +174,8 @@ def lib():
                          "vc_server_cancel", "vc_set_memory_limit", "vc_get_memory_usage", "vc_autotune",
                          "vc_autotune_batch", "vc_circuit_create_tiles", "vc_circuit_get_tiles", "vc_prove_pergate",
                          "vc_circuit_create_ex", "vc_f2sp_create", "vc_f2sp_destroy", "vc_f2sp_prove",
-                         "vc_f2sp_verify_begin", "vc_f2sp_verify_absorb", "vc_f2sp_verify_end",
-                         "vc_verify_input", "vc_verify_transcript"):
+                         "vc_f2sp_verify_begin", "vc_f2sp_verify_absorb", "vc_f2sp_verify_absorb_async",
+                         "vc_f2sp_verify_end", "vc_verify_input", "vc_verify_transcript"):
                 getattr(L, name).restype = st
             _lib = L
     return _lib
@@ -390,6 +391,15 @@ def vc_f2sp_verify_absorb(s, rows, first_row: int, nrows: int, stream=None, devi
     _need(rows, nrows * h, "rows")
     _check(lib().vc_f2sp_verify_absorb(s, _ptr(rows), first_row, nrows, _stream(stream, device)),
            "vc_f2sp_verify_absorb")
+
+
+def vc_f2sp_verify_absorb_async(s, rows, first_row: int, nrows: int, stream=None, device: int = 0):
+    """Host rows: returns once the previous call's rows are copied (alternate
+    at least two host buffers)."""
+    v, h = _shapes[("f2sp", s)]
+    _need(rows, nrows * h, "rows")
+    _check(lib().vc_f2sp_verify_absorb_async(s, _ptr(rows), first_row, nrows, _stream(stream, device)),
+           "vc_f2sp_verify_absorb_async")
 
 
 def vc_f2sp_verify_end(s, proof, stream=None, device: int = 0):

@@ -153,22 +153,25 @@ def _absorb_split(s, rows, h, splits):
         x0 += n
 
 
-@pytest.mark.parametrize("v,h", [(800_000, 3), (150_000, 15)])
-def test_streaming_host_rows_double_buffered(v, h):
-    """Host rows stream through the verifier's two device buffers of about
-    8 MB (2^20 / h rows each), so these grids span three chunks: one absorb
-    call over all rows, calls that split chunks unevenly (1 row, a chunk less
-    one, a chunk plus one, the rest), page-locked and pageable rows, and host
-    calls mixed with device rows all give the oracle verifier's accept bit and
-    answer, for the honest proof and a changed one."""
-    chunk = (1 << 20) // h
+# the library streams host rows in chunks of about 2^21 entries (16 MB):
+# these grids span at least three
+@pytest.mark.parametrize("v,h,uneven", [(2_200_000, 3, [1, 300_001, 1_000_000]),
+                                        (450_000, 15, [1, 60_001, 200_000])])
+def test_streaming_host_rows_double_buffered(v, h, uneven):
+    """Host rows stream through the verifier's two device buffers, so these
+    grids span several chunks: one absorb call over all rows, calls that
+    split chunks unevenly (1 row, then sizes that are no multiple of a
+    chunk, the rest), page-locked and pageable rows, and host calls mixed
+    with device rows all give the oracle verifier's accept bit and answer,
+    for the honest proof and a changed one."""
+    chunk = (1 << 21) // h
     a = I.uniform_ints(4000 + h, v * h, 1 << 16)
     proof = oracle.f2sp_prove(a, v, h)
     bad = proof.copy()
     bad[2 * (h // 2) + 1] = (int(bad[2 * (h // 2) + 1]) + 3) % P
     pinned = torch.from_numpy(a.view(np.int64).copy()).pin_memory()
     pageable = np.ascontiguousarray(a)
-    uneven = [1, chunk - 1, chunk + 1, v - 2 * chunk - 1]
+    uneven = uneven + [v - sum(uneven)]
     s = vc.vc_f2sp_create(v, h)
     try:
         for pr, seed in ((proof, 11), (bad, 12)):
@@ -206,6 +209,31 @@ def test_streaming_reuses_one_host_buffer():
             buf.copy_(torch.from_numpy(a[x0 * h:(x0 + part) * h].view(np.int64)))
             vc.vc_f2sp_verify_absorb(s, buf, x0, part)
         assert vc.vc_f2sp_verify_end(s, proof) == want
+    finally:
+        vc.vc_f2sp_destroy(s)
+
+
+def test_async_streaming_two_buffers():
+    """The asynchronous absorb returns before its own rows are copied (once
+    the previous call's are), so the caller alternates two page-locked
+    buffers, refilling the one it passed two calls ago: the verdict equals the
+    oracle's, for chunks smaller and larger than the device buffers."""
+    v, h = 600_000, 5
+    a = I.uniform_ints(4200, v * h, 1 << 16)
+    proof = oracle.f2sp_prove(a, v, h)
+    want = oracle.f2sp_verify(a, v, h, 22, proof)
+    assert want[0]
+    s = vc.vc_f2sp_create(v, h)
+    try:
+        for part in (30_000, 250_000):
+            bufs = [torch.empty(part * h, dtype=torch.int64).pin_memory() for _ in range(2)]
+            vc.vc_f2sp_verify_begin(s, 22)
+            for k, x0 in enumerate(range(0, v, part)):
+                n = min(part, v - x0)
+                b = bufs[k & 1]
+                b[:n * h].copy_(torch.from_numpy(a[x0 * h:(x0 + n) * h].view(np.int64)))
+                vc.vc_f2sp_verify_absorb_async(s, b[:n * h], x0, n)
+            assert vc.vc_f2sp_verify_end(s, proof) == want, part
     finally:
         vc.vc_f2sp_destroy(s)
 
