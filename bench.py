@@ -46,9 +46,11 @@ def env_rank():
 # ---- clocks during the timed region --------------------------------------------------
 
 class ClockSampler:
+    """nvidia-smi every 100 ms from start() to stop(); the SM clock is the
+    median over the samples that saw the GPU busy (all samples if none did)."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
@@ -68,7 +70,7 @@ class ClockSampler:
     def stop(self):
         if self.proc is None:
             return None
-        time.sleep(0.25)
+        time.sleep(0.12)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -85,12 +87,13 @@ class ClockSampler:
             return None
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        busy = [r for r in rows if len(r) >= 10 and r[9].isdigit() and int(r[9]) >= 50]
+        sm = [float(r[1]) for r in (busy or rows) if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "busy_samples": len(busy)}
 
 
 # ---- work of the dominant launch ---------------------------------------------------------
@@ -662,6 +665,20 @@ def run_ours(args):
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
+    # the timed steps take a few ms, less than the sampler's period: the same
+    # step runs untimed for 0.5 s first, so that the samples see the clocks
+    # under this load right up to the timed region
+    t_soak = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t_soak < 0.5:
+        flush.zero_()
+        ev_start.record(main)
+        step(5000 + k, ev_start)
+        k += 1
+        if k % 64 == 0:
+            main.synchronize()
+    torch.cuda.synchronize()
+    vc.vc_circuit_sync(h)
     step_ms, wave_ms = [], []
     oks = 0
     rec = event_recorder()
@@ -794,6 +811,8 @@ def run_ours(args):
         "config": {"workload": "F2 n=2^20, x uniform in [0, 2^16], prove + verify per step",
                    "gates": gates, "transcript_u64": info["transcript_len"], "rounds": info["n_rounds"],
                    "l2": "flushed between steps (256 MiB write outside the step events)",
+                   "clock_sampling": "nvidia-smi every 100 ms over 0.5 s of the same step run untimed right before "
+                                     "the timed steps, and over them; SM clock median over the busy samples",
                    "parallelism": f"replicas x{world}"},
         "e2e": e2e,
         "roofline": {"bound": "alu", "kernel": "k_waves (persistent launch: every sum-check round and line "
