@@ -363,6 +363,51 @@ def run_special_purpose(flush, shapes=((1048, 1001), (4995, 5005)), reps=3):
     return out
 
 
+def run_size_sweep(flush, reps=5):
+    """Prover and verifier time against input size for each of the paper's
+    benchmark problems (its scaling experiment, on synthetic inputs): F2, F0,
+    MatMult (n^2 outputs), pattern matching (pattern of 2^4 symbols) and the
+    single-output MatMult check.  Device inputs and transcripts, L2 flushed
+    before each proof, median of `reps`; the proof's transcript is checked
+    by the device verifier (one pass) each time."""
+    import torch
+    from paper_1202_1350_gb300 import circuits, vc
+    from paper_1202_1350_gb300 import inputs as I
+    cases = [("f2", n, circuits.f2(n), None, lambda n=n: I.f2_inputs(n, 1 << 16, 11 + n)) for n in (10, 14, 18, 22)]
+    cases += [("f0", n, circuits.f0(n), None, lambda n=n: I.f0_inputs(n, 11 + n)) for n in (8, 12, 16)]
+    cases += [("matmult", 1 << n, circuits.matmult(n), None, lambda n=n: I.matmult_inputs(n, 1 << 10, 11 + n))
+              for n in (4, 6, 7)]
+    cases += [("pattern_match", n, circuits.pattern_match(n, 4)[:2], circuits.pattern_match(n, 4)[2],
+               lambda n=n: I.pm_inputs(n, 4, 11 + n)) for n in (10, 14, 18)]
+    cases += [("matmult_check", 1 << m, circuits.matmult_check(m)[:2], circuits.matmult_check(m)[2],
+               lambda m=m: I.mm1_inputs(m, 11 + m)) for m in (4, 6)]
+    out = []
+    for fam, size, (w, k), ex, gen in cases:
+        h = vc.vc_circuit_create(w, k, ex)
+        x = torch.from_numpy(np.ascontiguousarray(gen()).view(np.int64).copy()).cuda()
+        tr = torch.empty(vc.vc_transcript_len(h), dtype=torch.int64, device="cuda")
+        pt, vt, ok = [], [], True
+        for r in range(reps + 2):
+            flush.zero_()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            vc.vc_prove(h, x, 300 + r, tr)
+            e1.record()
+            ok &= vc.vc_verify(h, x, 300 + r, tr)
+            e2.record()
+            e2.synchronize()
+            if r >= 2:
+                pt.append(e0.elapsed_time(e1))
+                vt.append(e1.elapsed_time(e2))
+        vc.vc_circuit_sync(h)
+        gates = circuits.non_input_gates(w)
+        out.append({"problem": fam, "size": size, "inputs": 1 << w[-1], "gates": gates,
+                    "prove_ms": statistics.median(pt), "verify_ms": statistics.median(vt),
+                    "prove_gates_per_s": gates / (statistics.median(pt) / 1000), "accepted": bool(ok)})
+        vc.vc_circuit_destroy(h)
+    return out
+
+
 def _f2sp_factors(h):
     q = []
     for pr in (3, 5, 7, 11, 13, 31, 41, 61):
@@ -725,12 +770,13 @@ def run_ours(args):
                 except RuntimeError:  # a stage with no work records nothing
                     pass
     vc.vc_circuit_set_stage_events(h, None)
-    ablation = residency = special = None
+    ablation = residency = special = size_sweep = None
     if not args.no_ablation:
         ablation = run_ablation(h, xd, tr, flush)
         residency = run_residency(widths, kinds, xd, flush)
         residency["deep"] = run_residency_deep(flush)
         special = run_special_purpose(flush)
+        size_sweep = run_size_sweep(flush)
     # end to end through the C ABI from page-locked host memory, two ways;
     # each step ends with the transcript and the accept bit read back into
     # page-locked host memory.  "copy": the inputs are uploaded once and the
@@ -836,6 +882,7 @@ def run_ours(args):
         "ablation": ablation,
         "residency": residency,
         "special_purpose_f2": special,
+        "size_sweep": size_sweep,
         "gpu_launches": launches,
         "clocks": clocks,
     }

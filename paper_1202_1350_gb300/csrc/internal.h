@@ -113,6 +113,7 @@ struct Plan {
     std::vector<u32> seg_maxblock;                         // per step: largest block of its runs
     std::vector<LineWaveDev> lw;
     std::vector<BuildItem> builds;
+    std::vector<BuildItem> heavy;  // explicit layers' entries with long gate lists (k_build_heavy)
     std::vector<SciDev> scis;
     std::vector<ProdWave> pw;
     std::vector<GenWave> gw;
@@ -132,6 +133,7 @@ struct Plan {
     u32 *d_ctr = nullptr;  // two task counters per wave launch (A groups, then B groups)
     LineWaveDev *d_lw = nullptr;
     BuildItem *d_builds = nullptr;
+    BuildItem *d_heavy = nullptr;
     SciDev *d_scis = nullptr;
     ProdWave *d_pw = nullptr;
     GenWave *d_gw = nullptr;
@@ -207,6 +209,8 @@ struct vc_circuit {
     bool vin_sync = false;     // its inputs were host memory: the transcript pass reads the status
     std::vector<u32> explicit_layers;
     u32 *d_explicit_layers = nullptr;
+    std::vector<VwireItem> vwire;  // the verifier's wiring-sum CTAs over the explicit layers
+    VwireItem *d_vwire = nullptr;
     std::vector<u32> round_layer, zmap;
     u32 *d_round_layer = nullptr, *d_zmap = nullptr;
     // VC_VALUES_STAGED / VC_VALUES_WINDOWED: wide layers through W device

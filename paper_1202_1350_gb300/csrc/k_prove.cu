@@ -477,7 +477,10 @@ __global__ void __launch_bounds__(256) k_build23(const Globals *Gs, const BuildI
         break;
     }
     default: {  // explicit wiring, gates grouped by in1 and by in2
-        for (u32 q = L.by1_off[w]; q < L.by1_off[w + 1]; q++) {
+        // an entry read by more than BUILD_HEAVY gates is summed by a whole
+        // CTA afterwards (k_build_heavy), which adds to what is written here
+        const u32 a0 = L.by1_off[w], a1 = L.by1_off[w + 1];
+        for (u32 q = a0; q < a1 && a1 - a0 <= BUILD_HEAVY; q++) {
             const u32 g = L.by1_g[q];
             const u64 wg = f_mul(ez, eq_at(L.trp, g));
             if (L.type[g]) {
@@ -487,7 +490,8 @@ __global__ void __launch_bounds__(256) k_build23(const Globals *Gs, const BuildI
                 B2 = f_add(B2, f_mul(wg, V[L.in2[g]]));
             }
         }
-        for (u32 q = L.by2_off[w]; q < L.by2_off[w + 1]; q++) {
+        const u32 b0 = L.by2_off[w], b1 = L.by2_off[w + 1];
+        for (u32 q = b0; q < b1 && b1 - b0 <= BUILD_HEAVY; q++) {
             const u32 g = L.by2_g[q];
             const u64 ug = f_mul(f_mul(ez, eq_at(L.trp, g)), eq_at(L.tr1, L.in1[g]));
             if (L.type[g]) M2 = f_add(M2, ug);
@@ -507,5 +511,70 @@ __global__ void __launch_bounds__(256) k_build23(const Globals *Gs, const BuildI
 void launch_build23(const Globals *Gs, const BuildItem *items, int nitems, cudaStream_t st)
 {
     if (nitems > 0) k_build23<<<nitems, 256, 0, st>>>(Gs, items);
+}
+
+// An explicit layer's entry w of layer i+1 read by more than BUILD_HEAVY
+// gates (a constant such as 1 or p - 1 feeding a whole layer): one CTA sums
+// its gate list (item.block = w; item.pad = 1: the gates with in1 = w, adding
+// to P2 and B2; 2: those with in2 = w, adding to P3 and B3), after k_build23
+// wrote the entry's other sums.
+__global__ void __launch_bounds__(256) k_build_heavy(const Globals *Gs, const BuildItem *items)
+{
+    const BuildItem bi = items[blockIdx.x];
+    const Globals &G = Gs[bi.circ];
+    const u32 i = bi.layer;
+    const LayerDev &L = G.layers[i];
+    const u64 w = bi.block;
+    const u64 ez = G.scal[SCAL_EQZRP(i)];
+    const u64 *V = L.Vn;
+    u64 x = 0, y = 0;  // in1 lists: P2, B2 parts; in2 lists: A2, M2 parts
+    if (bi.pad == 1) {
+        for (u32 q = L.by1_off[w] + threadIdx.x; q < L.by1_off[w + 1]; q += blockDim.x) {
+            const u32 g = L.by1_g[q];
+            const u64 wg = f_mul(ez, eq_at(L.trp, g));
+            if (L.type[g]) {
+                x = f_add(x, f_mul(wg, V[L.in2[g]]));
+            } else {
+                x = f_add(x, wg);
+                y = f_add(y, f_mul(wg, V[L.in2[g]]));
+            }
+        }
+    } else {
+        for (u32 q = L.by2_off[w] + threadIdx.x; q < L.by2_off[w + 1]; q += blockDim.x) {
+            const u32 g = L.by2_g[q];
+            const u64 ug = f_mul(f_mul(ez, eq_at(L.trp, g)), eq_at(L.tr1, L.in1[g]));
+            if (L.type[g])
+                y = f_add(y, ug);
+            else
+                x = f_add(x, ug);
+        }
+    }
+    __shared__ u64 sx[256], sy[256];
+    sx[threadIdx.x] = x;
+    sy[threadIdx.x] = y;
+    __syncthreads();
+    for (u32 h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            sx[threadIdx.x] = f_add(sx[threadIdx.x], sx[threadIdx.x + h]);
+            sy[threadIdx.x] = f_add(sy[threadIdx.x], sy[threadIdx.x + h]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x) return;
+    x = sx[0];
+    y = sy[0];
+    if (bi.pad == 1) {
+        L.P2[w] = f_add(L.P2[w], x);
+        if (L.has_add) L.B2[w] = f_add(L.B2[w], y);
+    } else {
+        const u64 v1 = G.scal[SCAL_V1(i)];
+        L.P3[w] = f_add(L.P3[w], f_add(x, f_mul(v1, y)));
+        if (L.has_add) L.B3[w] = f_add(L.B3[w], f_mul(v1, x));
+    }
+}
+
+void launch_build_heavy(const Globals *Gs, const BuildItem *items, int nitems, cudaStream_t st)
+{
+    if (nitems > 0) k_build_heavy<<<nitems, 256, 0, st>>>(Gs, items);
 }
 

@@ -101,22 +101,13 @@ __global__ void __launch_bounds__(VM_NT) k_vmle(const Globals *Gd, const VerifyP
     }
 }
 
-// Generic add~/mult~ of an explicitly wired layer at (r_P, r1, r2):
-// sum over gates of eq(r_P, g) eq(r1, in1) eq(r2, in2), split by gate type.
-__global__ void __launch_bounds__(VM_NT) k_vwire(Globals G, const u32 *layers_idx, u64 *wire)
+// Sums of a CTA's (add, mult) pair, in thread 0.
+__device__ __forceinline__ void block_sum2(u64 &add, u64 &mult)
 {
-    const u32 i = layers_idx[blockIdx.x];
-    const LayerDev &L = G.layers[i];
-    const u64 S = 1ull << L.s;
-    u64 add = 0, mult = 0;
-    for (u64 g = threadIdx.x; g < S; g += VM_NT) {
-        const u64 w = f_mul(eq_at(L.trp, g), f_mul(eq_at(L.tr1, L.in1[g]), eq_at(L.tr2, L.in2[g])));
-        if (L.type[g]) mult = f_add(mult, w);
-        else add = f_add(add, w);
-    }
     __shared__ u64 s[2][VM_NT / 32];
     add = warp_sum(add);
     mult = warp_sum(mult);
+    __syncthreads();  // s may still be read by an earlier call
     if ((threadIdx.x & 31) == 0) {
         s[0][threadIdx.x >> 5] = add;
         s[1][threadIdx.x >> 5] = mult;
@@ -125,12 +116,56 @@ __global__ void __launch_bounds__(VM_NT) k_vwire(Globals G, const u32 *layers_id
     if (threadIdx.x < 32) {
         u64 a = threadIdx.x < VM_NT / 32 ? s[0][threadIdx.x] : 0;
         u64 m = threadIdx.x < VM_NT / 32 ? s[1][threadIdx.x] : 0;
-        a = warp_sum(a);
-        m = warp_sum(m);
+        add = warp_sum(a);
+        mult = warp_sum(m);
+    }
+}
+
+// Generic add~/mult~ of an explicitly wired layer at (r_P, r1, r2):
+// sum over gates of eq(r_P, g) eq(r1, in1) eq(r2, in2), split by gate type.
+// Each CTA sums a range of the layer's gates; the CTA that finishes a layer
+// last (a counter, no waiting) adds the layer's partial sums.
+__global__ void __launch_bounds__(VM_NT) k_vwire(Globals G, const VwireItem *items, VerifyDev V)
+{
+    const VwireItem it = items[blockIdx.x];
+    const u32 i = it.layer;
+    const LayerDev &L = G.layers[i];
+    const u64 S = 1ull << L.s, chunk = (S + it.nblocks - 1) / it.nblocks;
+    const u64 g0 = (u64)it.block * chunk, g1 = g0 + chunk < S ? g0 + chunk : S;
+    u64 add = 0, mult = 0;
+    for (u64 g = g0 + threadIdx.x; g < g1; g += VM_NT) {
+        const u64 w = f_mul(eq_at(L.trp, g), f_mul(eq_at(L.tr1, L.in1[g]), eq_at(L.tr2, L.in2[g])));
+        if (L.type[g]) mult = f_add(mult, w);
+        else add = f_add(add, w);
+    }
+    block_sum2(add, mult);
+    if (it.nblocks == 1) {
         if (threadIdx.x == 0) {
-            wire[2 * i] = a;
-            wire[2 * i + 1] = m;
+            V.wire[2 * i] = add;
+            V.wire[2 * i + 1] = mult;
         }
+        return;
+    }
+    __shared__ u32 s_last;
+    if (threadIdx.x == 0) {
+        V.wire_part[2 * (it.part_off + it.block)] = add;
+        V.wire_part[2 * (it.part_off + it.block) + 1] = mult;
+        __threadfence();
+        s_last = (atomicAdd(&V.wire_ctr[i], 1u) == it.nblocks - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    add = mult = 0;
+    for (u32 b = threadIdx.x; b < it.nblocks; b += VM_NT) {
+        add = f_add(add, __ldcg(V.wire_part + 2 * (it.part_off + b)));
+        mult = f_add(mult, __ldcg(V.wire_part + 2 * (it.part_off + b) + 1));
+    }
+    block_sum2(add, mult);
+    if (threadIdx.x == 0) {
+        V.wire[2 * i] = add;
+        V.wire[2 * i + 1] = mult;
+        V.wire_ctr[i] = 0;
     }
 }
 
@@ -455,8 +490,8 @@ const void *vparams_in_kernel() { return reinterpret_cast<const void *>(k_vparam
 // Entries per CTA (log2) of the MLE partial sums for a point of n coordinates.
 u32 vmle_log(u32 n) { return n < 11 ? n : 11; }
 
-void launch_verify(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0, const u32 *explicit_layers,
-                   int n_explicit, cudaStream_t st_mle, cudaEvent_t ev_join, cudaStream_t st)
+void launch_verify(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0, const VwireItem *wire_items,
+                   int n_wire, cudaStream_t st_mle, cudaEvent_t ev_join, cudaStream_t st)
 {
     // the MLE partial sums need only the seed: they run beside the coin launch
     // (st_mle forked from st before it); the checks wait for both
@@ -465,7 +500,7 @@ void launch_verify(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 
                                                                    V.result);
     cudaEventRecord(ev_join, st_mle);
     cudaStreamWaitEvent(st, ev_join, 0);
-    if (n_explicit > 0) k_vwire<<<n_explicit, VM_NT, 0, st>>>(G, explicit_layers, V.wire);
+    if (n_wire > 0) k_vwire<<<n_wire, VM_NT, 0, st>>>(G, wire_items, V);
     k_vcheck<<<VC_CL, VC_NT, 0, st>>>(G, V, nullptr, nullptr);
 }
 
@@ -476,12 +511,12 @@ void launch_verify_input(const Globals *Gd, const Globals &G, const VerifyDev &V
 }
 
 void launch_verify_transcript(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0,
-                              const u32 *explicit_layers, int n_explicit, const u64 *tr, int *accept,
+                              const VwireItem *wire_items, int n_wire, const u64 *tr, int *accept,
                               cudaStream_t st)
 {
     if (V.mle_out_blocks > 0)
         k_vmle<<<V.mle_out_blocks, VM_NT, 0, st>>>(Gd, V.vp, nd, vmle_log(nd), n0, vmle_log(n0), V.mle_blocks,
                                                    V.mle_blocks, tr, V.mle_part, G.status, V.result);
-    if (n_explicit > 0) k_vwire<<<n_explicit, VM_NT, 0, st>>>(G, explicit_layers, V.wire);
+    if (n_wire > 0) k_vwire<<<n_wire, VM_NT, 0, st>>>(G, wire_items, V);
     k_vcheck<<<VC_CL, VC_NT, 0, st>>>(G, V, tr, accept);
 }

@@ -318,6 +318,11 @@ void launch_eval_segs(const Globals *Gs, const EvalSeg *segs, const Item *items,
 void launch_check_canonical(const u64 *x, u64 n, u32 *status, cudaStream_t st);
 void launch_check_inputs(const Globals *Gs, const Item *items, int nitems, cudaStream_t st);
 void launch_build23(const Globals *Gs, const BuildItem *items, int nitems, cudaStream_t st);
+// Explicit layers: entries of layer i+1 read by more than BUILD_HEAVY gates
+// are summed by a CTA each after launch_build23 (item.block = the entry,
+// item.pad = 1: its in1 list, 2: its in2 list).
+#define BUILD_HEAVY 256u
+void launch_build_heavy(const Globals *Gs, const BuildItem *items, int nitems, cudaStream_t st);
 // One persistent launch over `tasks` (ctr: two zeroed counters, left zeroed).
 void launch_waves(const Globals *Gs, const LineWaveDev *lw, const ProdWave *pw, const GenWave *gw, const Task *tasks,
                   int ntasks, u32 *ctr, cudaStream_t st);
@@ -349,9 +354,16 @@ struct VerifyDev {
     u32 mle_blocks;
     u64 *result;        // [2] accept bit, [3] a check failed (k_vcheck writes both); others unused
     u64 *wire;          // generic add~/mult~ per layer (EXPLICIT layers)
+    u64 *wire_part;     // their per-CTA partial sums (two per CTA, VwireItem::part_off)
+    u32 *wire_ctr;      // per layer: CTAs done (reset by the last)
     u32 mle_out_blocks; // blocks of the output-MLE partials (after the input's; 0: formed by k_vcheck)
     const u32 *round_layer;  // per global round: layer << 8 | round within layer
     u32 nrounds;
+};
+// One CTA's share of an explicit layer's generic wiring sum: gates
+// [block, block + 1) * ceil(S_i / nblocks); partial sums at part_off + block.
+struct VwireItem {
+    u32 layer, block, nblocks, part_off;
 };
 void launch_init_invfact(u64 *invfact, cudaStream_t st);
 // result: VC_RESULT_WORDS words, cleared by the launch
@@ -361,8 +373,8 @@ void launch_vparams(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *tr, const u
 // partial sums on st_mle (forked from st before the coins, so both run
 // together), joined back into st through ev_join, then the checks.
 u32 vmle_log(u32 n);
-void launch_verify(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0, const u32 *explicit_layers,
-                   int n_explicit, cudaStream_t st_mle, cudaEvent_t ev_join, cudaStream_t st);
+void launch_verify(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0, const VwireItem *wire_items,
+                   int n_wire, cudaStream_t st_mle, cudaEvent_t ev_join, cudaStream_t st);
 // The verifier in two passes.  Input pass: the input's MLE partial sums (the
 // coins are launched beside it by the caller).  Transcript pass, with the
 // transcript and accept pointer as arguments: the claimed outputs' MLE
@@ -370,7 +382,7 @@ void launch_verify(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 
 // (the eq tables of explicit layers are launched before it by the caller).
 void launch_verify_input(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0, cudaStream_t st);
 void launch_verify_transcript(const Globals *Gd, const Globals &G, const VerifyDev &V, u32 nd, u32 n0,
-                              const u32 *explicit_layers, int n_explicit, const u64 *tr, int *accept,
+                              const VwireItem *wire_items, int n_wire, const u64 *tr, int *accept,
                               cudaStream_t st);
 void launch_vparams_in(Globals *G, VerifyPtrs *vp, u64 seed, const u64 *inputs, cudaStream_t st);
 const void *vparams_in_kernel();

@@ -593,12 +593,19 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
         }
     }
 
-    // phase-2/3 table builds: one thread per entry of layer i+1
+    // phase-2/3 table builds: one thread per entry of layer i+1, and a CTA
+    // per entry of an explicit layer that more than BUILD_HEAVY gates read
     P.builds.clear();
+    P.heavy.clear();
     for (u32 i = 0; i < d; i++) {
         if (!needs_tables(c->kind[i])) continue;
         const u64 blocks = (S(i + 1) + 255) / 256;
         for (u64 b = 0; b < blocks; b++) P.builds.push_back({0u, i, (u32)b, 0u});
+        if (c->kind[i] != W_EXPLICIT) continue;
+        for (u64 w = 0; w < S(i + 1); w++) {
+            if (c->by1_off[i][w + 1] - c->by1_off[i][w] > BUILD_HEAVY) P.heavy.push_back({0u, i, (u32)w, 1u});
+            if (c->by2_off[i][w + 1] - c->by2_off[i][w] > BUILD_HEAVY) P.heavy.push_back({0u, i, (u32)w, 2u});
+        }
     }
 
     // sum-check instances and their waves; all partial sums go to one buffer
@@ -757,6 +764,17 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     c->Vd.mle_out_blocks = S(0) <= VC_OUT_INLINE ? 0u : (u32)mbo;  // few outputs: formed in the check launch
     c->Vd.mle_part = A.take<u64>(mb + mbo);
     c->Vd.wire = A.take<u64>(2 * d + 2);
+    // the verifier's wiring sums: about 4096 gates per CTA, at most 1024 CTAs a layer
+    c->vwire.clear();
+    u32 nparts = 0;
+    for (u32 i : c->explicit_layers) {
+        const u32 nb = (u32)std::min<u64>(1024, std::max<u64>(1, S(i) / 4096));
+        for (u32 b = 0; b < nb; b++) c->vwire.push_back({i, b, nb, nparts});
+        nparts += nb;
+    }
+    c->Vd.wire_part = A.take<u64>(2 * (u64)nparts + 2);
+    c->Vd.wire_ctr = A.take<u32>(d + 1);
+    c->d_vwire = A.take<VwireItem>(c->vwire.size() + 1);
     c->round_layer.clear();
     for (u32 i = 0; i < d; i++)
         for (u32 j = 0; j < c->s[i] + 2 * c->s[i + 1]; j++) c->round_layer.push_back((i << 8) | j);
@@ -817,6 +835,7 @@ void plan_take(Plan &P, Arena &A, bool own_G)
     P.d_ctr = A.take<u32>(2 * (P.groupsA.size() + P.groupsB.size()) + 2);
     P.d_lw = A.take<LineWaveDev>(P.lw.size() + 1);
     P.d_builds = A.take<BuildItem>(P.builds.size() + 1);
+    P.d_heavy = A.take<BuildItem>(P.heavy.size() + 1);
     P.d_scis = A.take<SciDev>(P.scis.size() + 1);
     P.d_pw = A.take<ProdWave>(P.pw.size() + 1);
     P.d_gw = A.take<GenWave>(P.gw.size() + 1);
@@ -847,6 +866,8 @@ bool plan_valid(const Plan &P)
     }
     for (const BuildItem &b : P.builds)
         if (b.circ >= nc) return false;
+    for (const BuildItem &b : P.heavy)
+        if (b.circ >= nc || (b.pad != 1 && b.pad != 2)) return false;
     for (const SciDev &S : P.scis)
         if (S.circ >= nc) return false;
     for (size_t k = 0; k < P.pw.size(); k++) {
@@ -943,6 +964,7 @@ cudaError_t plan_upload(Plan &P)
     if (e == cudaSuccess) e = cudaMemset(P.d_ctr, 0, sizeof(u32) * (2 * (P.groupsA.size() + P.groupsB.size()) + 2));
     if (e == cudaSuccess) e = upload(P.d_lw, P.lw);
     if (e == cudaSuccess) e = upload(P.d_builds, P.builds);
+    if (e == cudaSuccess) e = upload(P.d_heavy, P.heavy);
     if (e == cudaSuccess) e = upload(P.d_scis, P.scis);
     if (e == cudaSuccess) e = upload(P.d_pw, P.pw);
     if (e == cudaSuccess) e = upload(P.d_gw, P.gw);
@@ -972,6 +994,7 @@ cudaError_t plan_upload_async(Plan &P, cudaStream_t st)
         e = cudaMemsetAsync(P.d_ctr, 0, sizeof(u32) * (2 * (P.groupsA.size() + P.groupsB.size()) + 2), st);
     if (e == cudaSuccess) e = upload_async(P.d_lw, P.lw, st);
     if (e == cudaSuccess) e = upload_async(P.d_builds, P.builds, st);
+    if (e == cudaSuccess) e = upload_async(P.d_heavy, P.heavy, st);
     if (e == cudaSuccess) e = upload_async(P.d_scis, P.scis, st);
     if (e == cudaSuccess) e = upload_async(P.d_pw, P.pw, st);
     if (e == cudaSuccess) e = upload_async(P.d_gw, P.gw, st);
@@ -1077,6 +1100,10 @@ void plan_merge(Plan &B, const std::vector<vc_circuit *> &cs)
             b.circ = cj;
             B.builds.push_back(b);
         }
+        for (BuildItem b : P.heavy) {
+            b.circ = cj;
+            B.heavy.push_back(b);
+        }
         for (SciDev Sc : P.scis) {
             Sc.circ = cj;
             B.scis.push_back(Sc);
@@ -1168,6 +1195,7 @@ void enqueue_plan(Plan &P, cudaStream_t st)
     if (has_build) {
         mark(VC_STAGE_BUILD, 0, st);
         launch_build23(Gs, P.d_builds, (int)P.builds.size(), st);
+        launch_build_heavy(Gs, P.d_heavy, (int)P.heavy.size(), st);
         mark(VC_STAGE_BUILD, 1, st);
     }
     if (has_tabwaves) {
@@ -1420,6 +1448,7 @@ int count_launches(const Plan &P)
     for (size_t k = 0; k < P.seg_items.size(); k++) n += (!P.seg_items[k].empty()) + (!P.lev_items[k].empty());
     for (const auto &v : P.groupsA) n += !v.empty();
     n += !P.builds.empty();
+    n += !P.heavy.empty();
     for (const auto &v : P.groupsB) n += !v.empty();
     return n + 1;  // final
 }
@@ -1627,6 +1656,7 @@ vc_status circuit_allocate(vc_circuit *c)
     if (e == cudaSuccess) e = upload(c->d_layers, c->L);
     if (e == cudaSuccess) e = upload(c->d_eq_verify, c->eq_verify);
     if (e == cudaSuccess) e = upload(c->d_explicit_layers, c->explicit_layers);
+    if (e == cudaSuccess) e = upload(c->d_vwire, c->vwire);
     if (e == cudaSuccess) e = upload(c->d_round_layer, c->round_layer);
     if (e == cudaSuccess) e = upload(c->d_zmap, c->zmap);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_G, &c->G, sizeof(Globals), cudaMemcpyHostToDevice);
@@ -2001,8 +2031,8 @@ extern "C" vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t s
             cudaEventRecord(c->P.ev_fork, cs);
             cudaStreamWaitEvent(c->P.aux, c->P.ev_fork, 0);
             launch_coins(c->d_Gv, 1, c->d_eq_verify, (int)c->eq_verify.size(), nullptr, nullptr, 0, cs);
-            launch_verify(c->d_Gv, c->Gv, c->Vd, c->s[c->d], c->s[0], c->d_explicit_layers,
-                          (int)c->explicit_layers.size(), c->P.aux, c->P.ev_tables, cs);
+            launch_verify(c->d_Gv, c->Gv, c->Vd, c->s[c->d], c->s[0], c->d_vwire, (int)c->vwire.size(),
+                          c->P.aux, c->P.ev_tables, cs);
         };
         e = capture_graph(c->P.cap, enqueue, &c->vexec, vparams_kernel(), &c->vgraph, &c->vpnode, &c->vpkp);
         if (e != cudaSuccess) return VC_ECUDA;
@@ -2074,8 +2104,8 @@ extern "C" vc_status vc_verify_transcript(vc_circuit *c, uint64_t seed, const ui
     // plain launches with the per-call pointers as arguments (one launch for
     // structured circuits): nothing to capture, nothing to write first
     launch_coins(c->d_Gv, 0, c->d_eq_verify, (int)c->eq_verify.size(), nullptr, nullptr, 0, st);
-    launch_verify_transcript(c->d_Gv, c->Gv, c->Vd, c->s[c->d], c->s[0], c->d_explicit_layers,
-                             (int)c->explicit_layers.size(), dtr, ka ? accept : nullptr, st);
+    launch_verify_transcript(c->d_Gv, c->Gv, c->Vd, c->s[c->d], c->s[0], c->d_vwire, (int)c->vwire.size(), dtr,
+                             ka ? accept : nullptr, st);
     return verifier_finish(c, ka && kt && !c->vin_sync, ka, accept, st);
 }
 
