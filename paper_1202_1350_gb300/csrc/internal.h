@@ -113,7 +113,7 @@ struct Plan {
     std::vector<u32> seg_maxblock;                         // per step: largest block of its runs
     std::vector<LineWaveDev> lw;
     std::vector<BuildItem> builds;
-    std::vector<BuildItem> heavy;  // explicit layers' entries with long gate lists (k_build_heavy)
+    std::vector<HeavyItem> heavy;  // explicit layers' entries with long gate lists (k_build_heavy)
     std::vector<SciDev> scis;
     std::vector<ProdWave> pw;
     std::vector<GenWave> gw;
@@ -133,7 +133,7 @@ struct Plan {
     u32 *d_ctr = nullptr;  // two task counters per wave launch (A groups, then B groups)
     LineWaveDev *d_lw = nullptr;
     BuildItem *d_builds = nullptr;
-    BuildItem *d_heavy = nullptr;
+    HeavyItem *d_heavy = nullptr;
     SciDev *d_scis = nullptr;
     ProdWave *d_pw = nullptr;
     GenWave *d_gw = nullptr;

@@ -513,43 +513,11 @@ void launch_build23(const Globals *Gs, const BuildItem *items, int nitems, cudaS
     if (nitems > 0) k_build23<<<nitems, 256, 0, st>>>(Gs, items);
 }
 
-// An explicit layer's entry w of layer i+1 read by more than BUILD_HEAVY
-// gates (a constant such as 1 or p - 1 feeding a whole layer): one CTA sums
-// its gate list (item.block = w; item.pad = 1: the gates with in1 = w, adding
-// to P2 and B2; 2: those with in2 = w, adding to P3 and B3), after k_build23
-// wrote the entry's other sums.
-__global__ void __launch_bounds__(256) k_build_heavy(const Globals *Gs, const BuildItem *items)
+// Sums of a CTA's (x, y) pair, in thread 0.
+__device__ __forceinline__ void block_sum_pair(u64 &x, u64 &y)
 {
-    const BuildItem bi = items[blockIdx.x];
-    const Globals &G = Gs[bi.circ];
-    const u32 i = bi.layer;
-    const LayerDev &L = G.layers[i];
-    const u64 w = bi.block;
-    const u64 ez = G.scal[SCAL_EQZRP(i)];
-    const u64 *V = L.Vn;
-    u64 x = 0, y = 0;  // in1 lists: P2, B2 parts; in2 lists: A2, M2 parts
-    if (bi.pad == 1) {
-        for (u32 q = L.by1_off[w] + threadIdx.x; q < L.by1_off[w + 1]; q += blockDim.x) {
-            const u32 g = L.by1_g[q];
-            const u64 wg = f_mul(ez, eq_at(L.trp, g));
-            if (L.type[g]) {
-                x = f_add(x, f_mul(wg, V[L.in2[g]]));
-            } else {
-                x = f_add(x, wg);
-                y = f_add(y, f_mul(wg, V[L.in2[g]]));
-            }
-        }
-    } else {
-        for (u32 q = L.by2_off[w] + threadIdx.x; q < L.by2_off[w + 1]; q += blockDim.x) {
-            const u32 g = L.by2_g[q];
-            const u64 ug = f_mul(f_mul(ez, eq_at(L.trp, g)), eq_at(L.tr1, L.in1[g]));
-            if (L.type[g])
-                y = f_add(y, ug);
-            else
-                x = f_add(x, ug);
-        }
-    }
     __shared__ u64 sx[256], sy[256];
+    __syncthreads();  // the arrays may still be read by an earlier call
     sx[threadIdx.x] = x;
     sy[threadIdx.x] = y;
     __syncthreads();
@@ -560,10 +528,70 @@ __global__ void __launch_bounds__(256) k_build_heavy(const Globals *Gs, const Bu
         }
         __syncthreads();
     }
-    if (threadIdx.x) return;
     x = sx[0];
     y = sy[0];
-    if (bi.pad == 1) {
+}
+
+// One piece of the gate list of an explicit layer's entry w that more than
+// BUILD_HEAVY gates read (a constant such as 1 or p - 1 feeding a whole
+// layer): kind 1, the gates with in1 = w (sums for P2 and B2); kind 2, those
+// with in2 = w (for A2 and M2, which enter P3 and B3).  The last piece to
+// finish adds every piece's sums to what k_build23 wrote for the entry.
+__global__ void __launch_bounds__(256) k_build_heavy(const Globals *Gs, const HeavyItem *items)
+{
+    const HeavyItem it = items[blockIdx.x];
+    const Globals &G = Gs[it.circ];
+    const u32 i = it.layer;
+    const LayerDev &L = G.layers[i];
+    const u64 w = it.w;
+    const u64 ez = G.scal[SCAL_EQZRP(i)];
+    const u64 *V = L.Vn;
+    const u32 *off = (it.kind == 1) ? L.by1_off : L.by2_off;
+    const u32 q0 = off[w] + it.piece * BUILD_PIECE, q1 = min(off[w + 1], q0 + BUILD_PIECE);
+    u64 x = 0, y = 0;  // in1 lists: P2, B2 parts; in2 lists: A2, M2 parts
+    if (it.kind == 1) {
+        for (u32 q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+            const u32 g = L.by1_g[q];
+            const u64 wg = f_mul(ez, eq_at(L.trp, g));
+            if (L.type[g]) {
+                x = f_add(x, f_mul(wg, V[L.in2[g]]));
+            } else {
+                x = f_add(x, wg);
+                y = f_add(y, f_mul(wg, V[L.in2[g]]));
+            }
+        }
+    } else {
+        for (u32 q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+            const u32 g = L.by2_g[q];
+            const u64 ug = f_mul(f_mul(ez, eq_at(L.trp, g)), eq_at(L.tr1, L.in1[g]));
+            if (L.type[g])
+                y = f_add(y, ug);
+            else
+                x = f_add(x, ug);
+        }
+    }
+    block_sum_pair(x, y);
+    if (it.npieces > 1) {
+        __shared__ u32 s_last;
+        if (threadIdx.x == 0) {
+            it.part[2 * it.piece] = x;
+            it.part[2 * it.piece + 1] = y;
+            __threadfence();
+            s_last = (atomicAdd(it.ctr, 1u) == it.npieces - 1) ? 1u : 0u;
+        }
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        x = y = 0;
+        for (u32 q = threadIdx.x; q < it.npieces; q += blockDim.x) {
+            x = f_add(x, __ldcg(it.part + 2 * q));
+            y = f_add(y, __ldcg(it.part + 2 * q + 1));
+        }
+        block_sum_pair(x, y);
+        if (threadIdx.x == 0) *it.ctr = 0;
+    }
+    if (threadIdx.x) return;
+    if (it.kind == 1) {
         L.P2[w] = f_add(L.P2[w], x);
         if (L.has_add) L.B2[w] = f_add(L.B2[w], y);
     } else {
@@ -573,7 +601,7 @@ __global__ void __launch_bounds__(256) k_build_heavy(const Globals *Gs, const Bu
     }
 }
 
-void launch_build_heavy(const Globals *Gs, const BuildItem *items, int nitems, cudaStream_t st)
+void launch_build_heavy(const Globals *Gs, const HeavyItem *items, int nitems, cudaStream_t st)
 {
     if (nitems > 0) k_build_heavy<<<nitems, 256, 0, st>>>(Gs, items);
 }

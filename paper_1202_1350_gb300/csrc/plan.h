@@ -318,11 +318,20 @@ void launch_eval_segs(const Globals *Gs, const EvalSeg *segs, const Item *items,
 void launch_check_canonical(const u64 *x, u64 n, u32 *status, cudaStream_t st);
 void launch_check_inputs(const Globals *Gs, const Item *items, int nitems, cudaStream_t st);
 void launch_build23(const Globals *Gs, const BuildItem *items, int nitems, cudaStream_t st);
-// Explicit layers: entries of layer i+1 read by more than BUILD_HEAVY gates
-// are summed by a CTA each after launch_build23 (item.block = the entry,
-// item.pad = 1: its in1 list, 2: its in2 list).
-#define BUILD_HEAVY 256u
-void launch_build_heavy(const Globals *Gs, const BuildItem *items, int nitems, cudaStream_t st);
+// Explicit layers: an entry w of layer i+1 read by more than BUILD_HEAVY
+// gates is summed after launch_build23 by npieces CTAs of up to
+// BUILD_PIECE gates each (kind 1: its in1 list, 2: its in2 list); each writes
+// its sums to part[2 piece ..], and the last to finish (ctr) adds them all to
+// the entry's tables.
+#define BUILD_HEAVY 32u
+#define BUILD_PIECE 4096u
+struct HeavyItem {
+    u32 circ, layer, w, kind;
+    u32 piece, npieces, pad0, pad1;
+    u64 *part;  // 2 npieces u64
+    u32 *ctr;   // zero between proofs (reset by the last piece)
+};
+void launch_build_heavy(const Globals *Gs, const HeavyItem *items, int nitems, cudaStream_t st);
 // One persistent launch over `tasks` (ctr: two zeroed counters, left zeroed).
 void launch_waves(const Globals *Gs, const LineWaveDev *lw, const ProdWave *pw, const GenWave *gw, const Task *tasks,
                   int ntasks, u32 *ctr, cudaStream_t st);

@@ -602,10 +602,16 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
         const u64 blocks = (S(i + 1) + 255) / 256;
         for (u64 b = 0; b < blocks; b++) P.builds.push_back({0u, i, (u32)b, 0u});
         if (c->kind[i] != W_EXPLICIT) continue;
-        for (u64 w = 0; w < S(i + 1); w++) {
-            if (c->by1_off[i][w + 1] - c->by1_off[i][w] > BUILD_HEAVY) P.heavy.push_back({0u, i, (u32)w, 1u});
-            if (c->by2_off[i][w + 1] - c->by2_off[i][w] > BUILD_HEAVY) P.heavy.push_back({0u, i, (u32)w, 2u});
-        }
+        for (u64 w = 0; w < S(i + 1); w++)
+            for (u32 kind = 1; kind <= 2; kind++) {
+                const auto &off = (kind == 1) ? c->by1_off[i] : c->by2_off[i];
+                const u32 n = off[w + 1] - off[w];
+                if (n <= BUILD_HEAVY) continue;
+                const u32 np = (n + BUILD_PIECE - 1) / BUILD_PIECE;
+                u64 *part = A.take<u64>(2 * (u64)np);
+                u32 *ctr = A.take<u32>(1);
+                for (u32 q = 0; q < np; q++) P.heavy.push_back({0u, i, (u32)w, kind, q, np, 0u, 0u, part, ctr});
+            }
     }
 
     // sum-check instances and their waves; all partial sums go to one buffer
@@ -835,7 +841,7 @@ void plan_take(Plan &P, Arena &A, bool own_G)
     P.d_ctr = A.take<u32>(2 * (P.groupsA.size() + P.groupsB.size()) + 2);
     P.d_lw = A.take<LineWaveDev>(P.lw.size() + 1);
     P.d_builds = A.take<BuildItem>(P.builds.size() + 1);
-    P.d_heavy = A.take<BuildItem>(P.heavy.size() + 1);
+    P.d_heavy = A.take<HeavyItem>(P.heavy.size() + 1);
     P.d_scis = A.take<SciDev>(P.scis.size() + 1);
     P.d_pw = A.take<ProdWave>(P.pw.size() + 1);
     P.d_gw = A.take<GenWave>(P.gw.size() + 1);
@@ -866,8 +872,8 @@ bool plan_valid(const Plan &P)
     }
     for (const BuildItem &b : P.builds)
         if (b.circ >= nc) return false;
-    for (const BuildItem &b : P.heavy)
-        if (b.circ >= nc || (b.pad != 1 && b.pad != 2)) return false;
+    for (const HeavyItem &b : P.heavy)
+        if (b.circ >= nc || (b.kind != 1 && b.kind != 2) || b.piece >= b.npieces || !b.part || !b.ctr) return false;
     for (const SciDev &S : P.scis)
         if (S.circ >= nc) return false;
     for (size_t k = 0; k < P.pw.size(); k++) {
@@ -1100,7 +1106,7 @@ void plan_merge(Plan &B, const std::vector<vc_circuit *> &cs)
             b.circ = cj;
             B.builds.push_back(b);
         }
-        for (BuildItem b : P.heavy) {
+        for (HeavyItem b : P.heavy) {
             b.circ = cj;
             B.heavy.push_back(b);
         }
