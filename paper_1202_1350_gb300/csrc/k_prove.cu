@@ -192,6 +192,46 @@ __device__ __forceinline__ void eval_warp_layers(LayerFn layer, int hi, int lo, 
     }
 }
 
+// A chain of F0_PAIR layers (gate 2j = v_2j^2, gate 2j+1 = v_2j+1 v_2j): every
+// pair of entries evolves on its own, so a thread keeps its pairs in registers
+// through the whole chain, writes each layer with 16-byte stores and needs no
+// barrier between the layers.  `cur` holds the block below layer hi (B
+// entries); the pairs after layer lo go to `nxt`.
+template <class LayerFn>
+__device__ __forceinline__ void eval_pair_chain(LayerFn layer, int hi, int lo, const u64 *cur, u64 *nxt, u32 B,
+                                                u32 chunk)
+{
+    constexpr int PP = EV_MAXB / 2 / EV_NT;  // pairs a thread holds
+    const u32 np = B >> 1;
+    u64 x0[PP], x1[PP];
+#pragma unroll
+    for (int h = 0; h < PP; h++) {
+        const u32 q = threadIdx.x + h * EV_NT;
+        x0[h] = (q < np) ? cur[2 * q] : 0;
+        x1[h] = (q < np) ? cur[2 * q + 1] : 0;
+    }
+    for (int i = hi; i >= lo; i--) {
+        ulonglong2 *__restrict__ out = reinterpret_cast<ulonglong2 *>(layer((u32)i).V + (u64)chunk * B);
+#pragma unroll
+        for (int h = 0; h < PP; h++) {
+            const u32 q = threadIdx.x + h * EV_NT;
+            if (q < np) {
+                x1[h] = f_mul(x1[h], x0[h]);
+                x0[h] = f_mul(x0[h], x0[h]);
+                out[q] = make_ulonglong2(x0[h], x1[h]);
+            }
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < PP; h++) {
+        const u32 q = threadIdx.x + h * EV_NT;
+        if (q < np) {
+            nxt[2 * q] = x0[h];
+            nxt[2 * q + 1] = x1[h];
+        }
+    }
+}
+
 #ifndef EV_MINB
 #define EV_MINB 4  // resident evaluation CTAs per SM the register allocation is sized for
 #endif
@@ -275,6 +315,15 @@ __global__ void __launch_bounds__(EV_NT, EV_MINB) k_eval_seg(const Globals *Gs, 
     for (; i >= (int)S.i_lo; i--) {
         if (i == (int)S.warp_from) break;
         const EvLayer L = layer((u32)i);
+        if (L.kind == W_F0_PAIR) {  // the chain of pair layers from here, in registers
+            int lo = i;
+            while (lo - 1 >= (int)S.i_lo && lo - 1 != (int)S.warp_from && layer((u32)(lo - 1)).kind == W_F0_PAIR) lo--;
+            eval_pair_chain(layer, i, lo, cur, nxt, B, chunk);
+            __syncthreads();
+            u64 *t = cur; cur = nxt; nxt = t;
+            i = lo;
+            continue;
+        }
         const u32 Bo = (L.s >= L.sn) ? (B << (L.s - L.sn)) : (B >> (L.sn - L.s));
         eval_block_smem(L.kind, cur, nxt, L.V + (u64)chunk * Bo, Bo);
         __syncthreads();

@@ -101,6 +101,9 @@ enum : u32 { GS_NONE = 0, GS_SQ2 = 1, GS_TREE2 = 2 };
 
 #define PR_M 6  // PROD: at most 2^6 entries per thread, folded in registers (128 threads per CTA)
 #define GN_M 5  // GEN: at most 2^5 entries per thread (128 threads per CTA)
+// Evaluation runs holding F0_PAIR layers take chunks of at most 2^8 input
+// entries: one pair per thread of a 256-thread evaluation CTA.
+#define EV_PAIR_CHUNK 8
 
 struct SciDev {
     u32 circ;

@@ -199,21 +199,33 @@ static void plan_eval(vc_circuit *c)
         cl = std::min(cl, 11);
         int i_lo = i + 1;
         u32 maxblock = 1;
-        while (true) {
-            int e = cl, j = i;
+        bool pairs = false;  // the run holds F0_PAIR layers
+        auto grow = [&](int cl_) {
+            int e = cl_, j = i;
             i_lo = i + 1;
-            maxblock = 1u << cl;
+            maxblock = 1u << cl_;
+            pairs = false;
             while (j >= 0 && local(j) && !(j < i && flush[j])) {
                 const int ne = e + (int)c->s[j] - (int)c->s[j + 1];
                 if (ne < 0 || ne > 11) break;
                 if (c->kind[j] == W_F0_PAIR && ne < 1) break;
+                pairs |= c->kind[j] == W_F0_PAIR;
                 e = ne;
                 i_lo = j;
                 maxblock = std::max(maxblock, 1u << ne);
                 j--;
             }
+        };
+        while (true) {
+            grow(cl);
             if (i_lo <= i || cl == 0) break;
             cl--;  // the first layer did not fit: smaller chunks
+        }
+        // pair layers run in registers, one pair per thread at most: chunks
+        // of up to 2^8 entries (more CTAs, shorter chains)
+        if (pairs && cl > EV_PAIR_CHUNK) {
+            cl = EV_PAIR_CHUNK;
+            grow(cl);
         }
         if (i_lo > i) {  // no run possible: evaluate this layer alone
             c->eval_steps.push_back(-i - 1);

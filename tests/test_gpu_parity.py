@@ -45,7 +45,7 @@ def test_f2_edge_values():
     check(*circuits.f2(5), x, seeds=(3,))
 
 
-@pytest.mark.parametrize("logn", [1, 2, 3, 4, 6, 10])
+@pytest.mark.parametrize("logn", [1, 2, 3, 4, 6, 8, 9, 10, 12])
 def test_f0_sizes(logn):
     x = I.f0_inputs(logn, 2000 + logn)
     check(*circuits.f0(logn), x, seeds=(7,))
