@@ -448,10 +448,39 @@ __global__ void __launch_bounds__(256) k_build23(const Globals *Gs, const BuildI
     const LayerDev &L = G.layers[i];
     const u64 w = (u64)bi.block * blockDim.x + threadIdx.x;
     const u64 Sn = 1ull << L.sn;
-    if (w >= Sn) return;
     const u64 ez = G.scal[SCAL_EQZRP(i)];
     const u64 v1 = G.scal[SCAL_V1(i)];
     const u64 *V = L.Vn;
+    if (L.kind == W_F0_PAIR || L.kind == W_F0_FINAL) {
+        // a thread per pair of entries 2q, 2q+1 (their gates share operands;
+        // a thread per entry left half of each warp idle on the other path)
+        const u64 q = w;
+        if (2 * q >= Sn) return;
+        u64 P2a, P2b, M2;
+        if (L.kind == W_F0_PAIR) {  // gate 2q = v_2q^2, gate 2q+1 = v_2q+1 v_2q
+            const u64 wg0 = f_mul(ez, eq_at(L.trp, 2 * q)), wg1 = f_mul(ez, eq_at(L.trp, 2 * q + 1));
+            const u64 x = V[2 * q];
+            P2a = f_mul(wg0, x);
+            P2b = f_mul(wg1, x);
+            M2 = f_add(f_mul(wg0, eq_at(L.tr1, 2 * q)), f_mul(wg1, eq_at(L.tr1, 2 * q + 1)));
+        } else {  // gate q = v_2q+1^2: only entry 2q+1 is read
+            const u64 wg = f_mul(ez, eq_at(L.trp, q));
+            P2a = f_mul(wg, V[2 * q + 1]);
+            M2 = f_mul(wg, eq_at(L.tr1, 2 * q + 1));
+        }
+        // PAIR: entry 2q carries the products with in1 = 2q (P2 and, with in1
+        // = in2 = 2q or in1 = 2q+1, in2 = 2q, M2 at 2q); FINAL: all at 2q+1
+        ulonglong2 *P2 = reinterpret_cast<ulonglong2 *>(L.P2), *P3 = reinterpret_cast<ulonglong2 *>(L.P3);
+        if (L.kind == W_F0_PAIR) {
+            P2[q] = make_ulonglong2(P2a, P2b);
+            P3[q] = make_ulonglong2(f_mul(v1, M2), 0);
+        } else {
+            P2[q] = make_ulonglong2(0, P2a);
+            P3[q] = make_ulonglong2(0, f_mul(v1, M2));
+        }
+        return;
+    }
+    if (w >= Sn) return;
     u64 P2 = 0, B2 = 0, A2 = 0, M2 = 0;
     switch (L.kind) {
     case W_SQUARE: {
@@ -480,24 +509,6 @@ __global__ void __launch_bounds__(256) k_build23(const Globals *Gs, const BuildI
         B2 = f_mul(wa, V[w]);
         A2 = f_mul(wa, e1);
         M2 = f_mul(wm, e1);
-        break;
-    }
-    case W_F0_PAIR: {
-        const u64 wg = f_mul(ez, eq_at(L.trp, w));
-        P2 = f_mul(wg, V[w & ~1ull]);
-        if ((w & 1) == 0) {
-            const u64 wg1 = f_mul(ez, eq_at(L.trp, w + 1));
-            M2 = f_add(f_mul(wg, eq_at(L.tr1, w)), f_mul(wg1, eq_at(L.tr1, w + 1)));
-        }
-        break;
-    }
-    case W_F0_FINAL: {
-        if (w & 1) {
-            const u64 g = w >> 1;
-            const u64 wg = f_mul(ez, eq_at(L.trp, g));
-            P2 = f_mul(wg, V[w]);
-            M2 = f_mul(wg, eq_at(L.tr1, w));
-        }
         break;
     }
     case W_MATMULT: {

@@ -611,7 +611,9 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     P.heavy.clear();
     for (u32 i = 0; i < d; i++) {
         if (!needs_tables(c->kind[i])) continue;
-        const u64 blocks = (S(i + 1) + 255) / 256;
+        // F0 pair and final layers: a thread per pair of entries of layer i+1
+        const bool pairs = c->kind[i] == W_F0_PAIR || c->kind[i] == W_F0_FINAL;
+        const u64 blocks = ((pairs ? S(i + 1) / 2 : S(i + 1)) + 255) / 256;
         for (u64 b = 0; b < blocks; b++) P.builds.push_back({0u, i, (u32)b, 0u});
         if (c->kind[i] != W_EXPLICIT) continue;
         for (u64 w = 0; w < S(i + 1); w++)
