@@ -162,8 +162,10 @@ __device__ __forceinline__ void eval_block_smem(u32 kind, const u64 *cur, u64 *n
 }
 
 // Layers whose blocks all fit in one warp (<= 64 entries in and out): warp 0
-// holds the block in registers (two entries per lane) and exchanges operands
-// with shuffles, without block-wide barriers.
+// holds the block in registers (entries l and l + 32 in lane l) and exchanges
+// operands with shuffles, without block-wide barriers.  SQUARE needs no
+// exchange and TREE (at most 32 outputs) only its two operands, so those take
+// no multiply or shuffle they do not use.
 template <class LayerFn>
 __device__ __forceinline__ void eval_warp_layers(LayerFn layer, int hi, int lo, const u64 *cur, u32 B, bool chunked,
                                                  u32 chunk)
@@ -175,17 +177,29 @@ __device__ __forceinline__ void eval_warp_layers(LayerFn layer, int hi, int lo, 
         const u32 Bo = chunked ? ((L.s >= L.sn) ? (B << (L.s - L.sn)) : (B >> (L.sn - L.s))) : (1u << L.s);
         u64 *__restrict__ out = L.V + (chunked ? (u64)chunk * Bo : 0);
         u64 nv[2];
+        if (L.kind == W_SQUARE) {
+            nv[0] = f_mul(v0, v0);
+            nv[1] = f_mul(v1, v1);
+        } else if (L.kind == W_TREE) {  // Bo <= 32: entries 2k, 2k+1 of lane k
+            const u32 a = (2 * lane) & 31;
+            const u64 x0 = __shfl_sync(0xffffffffu, v0, a), y0 = __shfl_sync(0xffffffffu, v0, a + 1);
+            const u64 x1 = __shfl_sync(0xffffffffu, v1, a), y1 = __shfl_sync(0xffffffffu, v1, a + 1);
+            nv[0] = (lane < 16) ? f_add(x0, y0) : f_add(x1, y1);
+            nv[1] = 0;
+        } else {
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const u32 k = lane + 32 * h;
-            u32 a, b, mul;
-            local_gate(L.kind, k < Bo ? k : 0, a, b, mul);
-            const u64 xa0 = __shfl_sync(0xffffffffu, v0, a & 31), xa1 = __shfl_sync(0xffffffffu, v1, a & 31);
-            const u64 xb0 = __shfl_sync(0xffffffffu, v0, b & 31), xb1 = __shfl_sync(0xffffffffu, v1, b & 31);
-            const u64 x = (a < 32) ? xa0 : xa1, y = (b < 32) ? xb0 : xb1;
-            nv[h] = mul ? f_mul(x, y) : f_add(x, y);
-            if (k < Bo) out[k] = nv[h];
+            for (int h = 0; h < 2; h++) {
+                const u32 k = lane + 32 * h;
+                u32 a, b, mul;
+                local_gate(L.kind, k < Bo ? k : 0, a, b, mul);
+                const u64 xa0 = __shfl_sync(0xffffffffu, v0, a & 31), xa1 = __shfl_sync(0xffffffffu, v1, a & 31);
+                const u64 xb0 = __shfl_sync(0xffffffffu, v0, b & 31), xb1 = __shfl_sync(0xffffffffu, v1, b & 31);
+                const u64 x = (a < 32) ? xa0 : xa1, y = (b < 32) ? xb0 : xb1;
+                nv[h] = mul ? f_mul(x, y) : f_add(x, y);
+            }
         }
+        if (lane < Bo) out[lane] = nv[0];
+        if (lane + 32 < Bo) out[lane + 32] = nv[1];
         v0 = (lane < Bo) ? nv[0] : 0;
         v1 = (lane + 32 < Bo) ? nv[1] : 0;
         B = Bo;
