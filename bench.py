@@ -613,10 +613,10 @@ def e2e_pipelined(h, step, xh, n_in, tr_len, side, main, ev_start, nsteps, dist)
     from paper_1202_1350_gb300 import replicas
     copy = torch.cuda.Stream()
     xe = [torch.empty(n_in, dtype=torch.int64, device="cuda") for _ in range(2)]
-    tr = [torch.empty(tr_len, dtype=torch.int64, device="cuda") for _ in range(2)]
-    acc = [torch.zeros(1, dtype=torch.int32, device="cuda") for _ in range(2)]
-    trh = torch.empty((nsteps, tr_len), dtype=torch.int64).pin_memory()
-    acch = torch.zeros(nsteps, dtype=torch.int32).pin_memory()
+    # the accept word sits after the transcript: one read-back per step
+    tr = [torch.empty(tr_len + 1, dtype=torch.int64, device="cuda") for _ in range(2)]
+    acc = [t[tr_len:].view(torch.int32) for t in tr]
+    trh = torch.empty((nsteps, tr_len + 1), dtype=torch.int64).pin_memory()
     up = [torch.cuda.Event() for _ in range(2)]
     free = [torch.cuda.Event() for _ in range(2)]
 
@@ -633,9 +633,8 @@ def e2e_pipelined(h, step, xh, n_in, tr_len, side, main, ev_start, nsteps, dist)
             step(seed0 + k, ev_start, xe[b], tr[b], acc[b])
             free[b].record(main)
             trh[k].copy_(tr[b], non_blocking=True)
-            acch[k:k + 1].copy_(acc[b], non_blocking=True)
         main.synchronize()
-        return int(acch.sum()) == nsteps
+        return int(trh[:, tr_len:].contiguous().view(torch.int32)[:, 0].sum()) == nsteps
 
     assert run(7000)
     torch.cuda.synchronize()
@@ -644,7 +643,7 @@ def e2e_pipelined(h, step, xh, n_in, tr_len, side, main, ev_start, nsteps, dist)
     ms = 1000 * (time.perf_counter() - t0) / nsteps
     assert ok, "a pipelined proof was rejected"
     ms = replicas.max_over_ranks(ms, dist, "cuda")
-    return {"ms_per_step": ms, "steps": nsteps, "h2d_bytes_per_step": n_in * 8, "d2h_bytes_per_step": tr_len * 8 + 4,
+    return {"ms_per_step": ms, "steps": nsteps, "h2d_bytes_per_step": n_in * 8, "d2h_bytes_per_step": (tr_len + 1) * 8,
             "note": "throughput of a stream of proofs with each step's upload overlapping the previous step's "
                     "proof; not the latency of one step (the `modes` above)"}
 
@@ -752,7 +751,11 @@ def run_ours(args):
 
     # end to end through the C ABI with pinned host buffers
     xh = torch.from_numpy(x.view(np.int64).copy()).pin_memory()
-    trh = torch.empty(info["transcript_len"], dtype=torch.int64).pin_memory()
+    # the e2e steps' transcript with the accept word after it: one read-back
+    ntr = info["transcript_len"]
+    trx = torch.empty(ntr + 1, dtype=torch.int64, device="cuda")
+    accx = trx[ntr:].view(torch.int32)
+    trh = torch.empty(ntr + 1, dtype=torch.int64).pin_memory()
     # stage breakdown (diagnostic, outside the timed region): every stage's events
     stage_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * vc.NUM_STAGES)]
     vc.vc_circuit_set_stage_events(h, stage_ev)
@@ -787,7 +790,6 @@ def run_ours(args):
     # second stream, beside the sum-check waves), so the inputs cross the link
     # twice.  The faster is reported; both are measured.
     xe = torch.empty_like(xd)
-    acch = torch.zeros(1, dtype=torch.int32).pin_memory()
     ev_eval = torch.cuda.Event()
     e2e_ev = [None] * (2 * vc.NUM_STAGES)
     e2e_ev[2 * vc.STAGES.index("eval") + 1] = ev_eval
@@ -795,23 +797,22 @@ def run_ours(args):
     def e2e_copy(seed):
         xe.copy_(xh, non_blocking=True)
         ev_start.record(main)
-        step(seed, ev_start, xe, tr, acc)
+        step(seed, ev_start, xe, trx, accx)
 
     def e2e_in_place(seed):
-        vc.vc_prove(h, xh, seed, tr)  # asynchronous: inputs read in place
+        vc.vc_prove(h, xh, seed, trx)  # asynchronous: inputs read in place
         side.wait_event(ev_eval)
         vc.vc_verify_input(h, xh, seed, stream=side)
         ev_input.record(side)
         main.wait_event(ev_input)
-        vc.vc_verify_transcript(h, seed, tr, accept=acc)
+        vc.vc_verify_transcript(h, seed, trx, accept=accx)
 
     def e2e_time(run):
         def one(seed):
             run(seed)
-            trh.copy_(tr, non_blocking=True)
-            acch.copy_(acc, non_blocking=True)
+            trh.copy_(trx, non_blocking=True)
             main.synchronize()
-            return int(acch[0]) == 1
+            return int(trh[ntr:].view(torch.int32)[0]) == 1
         assert one(999) and one(998)
         ms = []
         for k in range(max(3, args.steps // 2)):
@@ -823,7 +824,7 @@ def run_ours(args):
         vc.vc_circuit_sync(h)
         return replicas.max_over_ranks(statistics.mean(ms), dist, "cuda")
 
-    n_in, tr_bytes = 1 << widths[-1], info["transcript_len"] * 8 + 4
+    n_in, tr_bytes = 1 << widths[-1], (ntr + 1) * 8
     modes = {"copy": {"ms_per_step": e2e_time(e2e_copy), "h2d_bytes_per_step": n_in * 8}}
     vc.vc_circuit_set_stage_events(h, e2e_ev)
     modes["in_place"] = {"ms_per_step": e2e_time(e2e_in_place), "h2d_bytes_per_step": 2 * n_in * 8}

@@ -229,9 +229,9 @@ __device__ __forceinline__ void eval_pair_chain(LayerFn layer, int hi, int lo, c
 #pragma unroll
         for (int h = 0; h < PP; h++) {
             const u32 q = threadIdx.x + h * EV_NT;
-            if (q < np) {
-                x1[h] = f_mul(x1[h], x0[h]);
-                x0[h] = f_mul(x0[h], x0[h]);
+            if (q < np) {  // the shorter-latency product: the chain is latency-bound
+                x1[h] = f_mul_wide(x1[h], x0[h]);
+                x0[h] = f_mul_wide(x0[h], x0[h]);
                 out[q] = make_ulonglong2(x0[h], x1[h]);
             }
         }
