@@ -780,19 +780,32 @@ def run_ours(args):
         residency["deep"] = run_residency_deep(flush)
         special = run_special_purpose(flush)
         size_sweep = run_size_sweep(flush)
-    # end to end through the C ABI from page-locked host memory, two ways;
-    # each step ends with the transcript and the accept bit read back into
-    # page-locked host memory.  "copy": the inputs are uploaded once and the
-    # prover and the verifier's input pass both read that device copy.
-    # "in_place": nothing is copied; the prover's first evaluation launch reads
-    # the inputs across the host link where they lie, and the verifier's input
-    # pass reads them again (from the end of the evaluation stage on, on a
-    # second stream, beside the sum-check waves), so the inputs cross the link
-    # twice.  The faster is reported; both are measured.
+    # end to end from page-locked host memory, three ways; each step ends with
+    # the transcript and the accept bit read back into page-locked host
+    # memory.  "upload": the C ABI gets the host inputs and copies them itself
+    # (a circuit created with VC_INPUTS_UPLOAD): the prover's upload comes
+    # first, the verifier's input pass uploads its own copy on a second stream
+    # from the end of the evaluation stage on, beside the sum-check waves.
+    # "copy": the caller uploads the inputs once (torch) and the prover and the
+    # verifier's input pass both read that device copy.  "in_place": nothing
+    # is copied; the prover's first evaluation launch reads the inputs across
+    # the host link where they lie, and the verifier's input pass reads them
+    # again (beside the waves), so the inputs cross the link twice.  The
+    # fastest is reported; all are measured.
     xe = torch.empty_like(xd)
     ev_eval = torch.cuda.Event()
     e2e_ev = [None] * (2 * vc.NUM_STAGES)
     e2e_ev[2 * vc.STAGES.index("eval") + 1] = ev_eval
+    h_up = vc.vc_circuit_create(widths, kinds, upload=True)
+    vc.vc_circuit_set_stage_events(h_up, e2e_ev)
+
+    def e2e_upload(seed):
+        vc.vc_prove(h_up, xh, seed, trx)  # asynchronous: uploads, then proves
+        side.wait_event(ev_eval)
+        vc.vc_verify_input(h_up, xh, seed, stream=side)
+        ev_input.record(side)
+        main.wait_event(ev_input)
+        vc.vc_verify_transcript(h_up, seed, trx, accept=accx)
 
     def e2e_copy(seed):
         xe.copy_(xh, non_blocking=True)
@@ -807,7 +820,7 @@ def run_ours(args):
         main.wait_event(ev_input)
         vc.vc_verify_transcript(h, seed, trx, accept=accx)
 
-    def e2e_time(run):
+    def e2e_time(run, hh=h):
         def one(seed):
             run(seed)
             trh.copy_(trx, non_blocking=True)
@@ -815,17 +828,19 @@ def run_ours(args):
             return int(trh[ntr:].view(torch.int32)[0]) == 1
         assert one(999) and one(998)
         ms = []
-        for k in range(max(3, args.steps // 2)):
+        for k in range(max(5, args.steps)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ok = one(500 + k)
             ms.append(1000 * (time.perf_counter() - t0))
             assert ok
-        vc.vc_circuit_sync(h)
+        vc.vc_circuit_sync(hh)
         return replicas.max_over_ranks(statistics.mean(ms), dist, "cuda")
 
     n_in, tr_bytes = 1 << widths[-1], (ntr + 1) * 8
-    modes = {"copy": {"ms_per_step": e2e_time(e2e_copy), "h2d_bytes_per_step": n_in * 8}}
+    modes = {"upload": {"ms_per_step": e2e_time(e2e_upload, h_up), "h2d_bytes_per_step": 2 * n_in * 8},
+             "copy": {"ms_per_step": e2e_time(e2e_copy), "h2d_bytes_per_step": n_in * 8}}
+    vc.vc_circuit_destroy(h_up)
     vc.vc_circuit_set_stage_events(h, e2e_ev)
     modes["in_place"] = {"ms_per_step": e2e_time(e2e_in_place), "h2d_bytes_per_step": 2 * n_in * 8}
     vc.vc_circuit_set_stage_events(h, None)

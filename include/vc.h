@@ -143,9 +143,21 @@ vc_status vc_circuit_create(const vc_circuit_desc *desc, int device, vc_circuit 
  * `residency` reports the choice.  VC_ENOMEM only when none fits. */
 #define VC_VALUES_AUTO 4u
 
+/* With VC_INPUTS_UPLOAD (device-resident values only: flags ==
+ * VC_INPUTS_UPLOAD) page-locked host inputs given to vc_prove,
+ * vc_verify_input or vc_verify are uploaded by one copy-engine transfer on
+ * the call's stream (the prover's into its input layer, the verifier's into a
+ * device buffer of its own, S_d more u64 of device memory) instead of being
+ * read in place across the host link by the first kernel that needs them.
+ * The calls stay asynchronous: the host buffer must stay unchanged until the
+ * stream has passed the call.  Pageable host inputs are copied as without the
+ * flag. */
+#define VC_INPUTS_UPLOAD 16u
+
 /* vc_circuit_create with residency flags (0, VC_VALUES_IN_HOST_MEMORY,
- * VC_VALUES_STAGED, VC_VALUES_WINDOWED or VC_VALUES_AUTO; VC_EINVAL for any
- * other value; VC_ENOMEM if the device or pinned host allocation fails). */
+ * VC_VALUES_STAGED, VC_VALUES_WINDOWED, VC_VALUES_AUTO, or VC_INPUTS_UPLOAD;
+ * VC_EINVAL for any other value; VC_ENOMEM if the device or pinned host
+ * allocation fails). */
 vc_status vc_circuit_create_ex(const vc_circuit_desc *desc, int device, uint32_t flags, vc_circuit **out);
 
 /* Free the circuit and its device scratch (synchronises its device).  NULL is

@@ -181,6 +181,7 @@ struct vc_circuit {
     Globals *d_G = nullptr;  // device copy (seed and tr written per call)
     std::vector<u64 *> V;
     u64 *d_tr = nullptr;
+    u64 *d_vin = nullptr;  // VC_INPUTS_UPLOAD: the verifier's copy of page-locked host inputs
     u64 *d_result = nullptr;
     std::vector<LayerDev> L;
     LayerDev *d_layers = nullptr;

@@ -507,6 +507,7 @@ static size_t layout(vc_circuit *c, uintptr_t base, uintptr_t hbase)
     P.d_G = c->d_G;
     c->d_result = A.take<u64>(VC_RESULT_WORDS);
     c->d_tr = A.take<u64>(c->tr_len);
+    c->d_vin = (c->flags & VC_INPUTS_UPLOAD) ? A.take<u64>(S(d)) : nullptr;
     G.tr = c->d_tr;
 
     for (EvalSeg &Sg : P.segs) Sg.counter = A.take<u32>(1);
@@ -1520,7 +1521,8 @@ PlanConfig shape_config(const vc_circuit_desc *desc)
 vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **out, const PlanConfig *cfg,
                           u32 flags)
 {
-    if (flags != 0 && flags != VC_VALUES_IN_HOST_MEMORY && flags != VC_VALUES_STAGED && flags != VC_VALUES_WINDOWED)
+    if (flags != 0 && flags != VC_VALUES_IN_HOST_MEMORY && flags != VC_VALUES_STAGED && flags != VC_VALUES_WINDOWED &&
+        flags != VC_INPUTS_UPLOAD)
         return VC_EINVAL;
     if (!desc || !out || desc->n_layers < 1 || desc->n_layers > 4096 || !desc->log_width || !desc->wiring)
         return VC_EINVAL;
@@ -1814,9 +1816,11 @@ extern "C" vc_status vc_prove(vc_circuit *c, const uint64_t *inputs, uint64_t se
     const int ki = ptr_kind(inputs, c->device, &mapped), kt = ptr_kind(transcript, c->device);
     if (ki < 0 || kt < 0) return VC_EINVAL;
     // inputs the device can address are read in place by the first evaluation
-    // launch (which writes the input layer); otherwise they are copied first
+    // launch (which writes the input layer); otherwise they are copied first,
+    // as are page-locked host inputs of a circuit that uploads them
+    const bool upload = (c->flags & VC_INPUTS_UPLOAD) && ki == 0 && mapped;
     const u64 *in = nullptr;
-    if (c->eval_reads_inputs) in = ki ? inputs : static_cast<const u64 *>(mapped);
+    if (c->eval_reads_inputs && !upload) in = ki ? inputs : static_cast<const u64 *>(mapped);
     cudaError_t e = cudaSuccess;
     if (!in) {
         const u64 nin = u64(1) << c->s[c->d];
@@ -1830,7 +1834,7 @@ extern "C" vc_status vc_prove(vc_circuit *c, const uint64_t *inputs, uint64_t se
         e = cudaMemcpyAsync(transcript, c->d_tr, c->tr_len * sizeof(u64), cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return VC_ECUDA;
     }
-    if (kt && (ki || in)) return VC_OK;  // everything read in place: asynchronous, status latched
+    if (kt && (ki || in || upload)) return VC_OK;  // no pageable input copy: asynchronous, status latched
     return read_status_and_clear(c, st);
 }
 
@@ -2034,9 +2038,14 @@ extern "C" vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t s
     const u64 nin = u64(1) << c->s[c->d];
     cudaError_t e = cudaSuccess;
     // the input MLE reads the inputs once: in place when the device can address
-    // them, else from a copy
-    const u64 *din = ki ? inputs : static_cast<const u64 *>(mapped);
-    if (!din) {
+    // them, else from a copy (page-locked ones of a circuit that uploads its
+    // inputs into the verifier's own buffer)
+    const bool upload = (c->flags & VC_INPUTS_UPLOAD) && ki == 0 && mapped;
+    const u64 *din = ki ? inputs : upload ? nullptr : static_cast<const u64 *>(mapped);
+    if (upload) {
+        e = cudaMemcpyAsync(c->d_vin, inputs, nin * sizeof(u64), cudaMemcpyHostToDevice, st);
+        din = c->d_vin;
+    } else if (!din) {
         e = cudaMemcpyAsync(c->V[c->d], inputs, nin * sizeof(u64), cudaMemcpyDefault, st);
         din = c->V[c->d];
     }
@@ -2067,7 +2076,7 @@ extern "C" vc_status vc_verify(vc_circuit *c, const uint64_t *inputs, uint64_t s
     }
     if (e == cudaSuccess) e = cudaGraphLaunch(c->vexec, st);
     if (e != cudaSuccess) return VC_ECUDA;
-    return verifier_finish(c, ka && ki && kt, ka, accept, st);
+    return verifier_finish(c, ka && (ki || upload) && kt, ka, accept, st);
 }
 
 extern "C" vc_status vc_verify_input(vc_circuit *c, const uint64_t *inputs, uint64_t seed, void *stream)
@@ -2077,9 +2086,16 @@ extern "C" vc_status vc_verify_input(vc_circuit *c, const uint64_t *inputs, uint
     cudaStream_t st = (cudaStream_t)stream;
     const void *mapped = nullptr;
     const int ki = ptr_kind(inputs, c->device, &mapped);
-    const u64 *din = ki > 0 ? inputs : static_cast<const u64 *>(mapped);
-    if (ki < 0 || !din) return VC_EINVAL;  // the pass reads its inputs in place
+    // the pass reads its inputs in place, or page-locked ones of a circuit
+    // that uploads its inputs from the verifier's own copy
+    const bool upload = (c->flags & VC_INPUTS_UPLOAD) && ki == 0 && mapped;
+    const u64 *din = ki > 0 ? inputs : upload ? c->d_vin : static_cast<const u64 *>(mapped);
+    if (ki < 0 || !din) return VC_EINVAL;
     cudaError_t e = cudaSuccess;
+    if (upload) {
+        e = cudaMemcpyAsync(c->d_vin, inputs, (u64(1) << c->s[c->d]) * sizeof(u64), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return VC_ECUDA;
+    }
     if (!c->vin_exec) {
         auto enqueue = [&](cudaStream_t cs) {
             launch_vparams_in(c->d_Gv, c->d_vp, 0, nullptr, cs);
@@ -2103,7 +2119,7 @@ extern "C" vc_status vc_verify_input(vc_circuit *c, const uint64_t *inputs, uint
     if (e != cudaSuccess) return VC_ECUDA;
     c->vin_pending = true;
     c->vin_seed = seed;
-    c->vin_sync = ki == 0;
+    c->vin_sync = ki == 0 && !upload;
     return VC_OK;
 }
 
@@ -2163,7 +2179,7 @@ extern "C" vc_status vc_circuit_get_info(const vc_circuit *c, vc_circuit_info *i
     // and wiring (EXPLICIT only), output MLE (many outputs only), checks
     I.verify2_launches = (uint32_t)(4 + (c->explicit_layers.empty() ? 0 : 2) + (c->Vd.mle_out_blocks ? 1 : 0));
     I.wave_tasks = (uint32_t)(c->P.groupsA.empty() ? 0 : c->P.groupsA[0].size());
-    I.residency = c->flags;
+    I.residency = c->flags & ~VC_INPUTS_UPLOAD;
     I.link_bytes = c->P.staged ? c->st_link_bytes : 0;
     *info = I;
     return VC_OK;

@@ -239,17 +239,20 @@ VC_VALUES_IN_HOST_MEMORY = 1
 VC_VALUES_STAGED = 2
 VC_VALUES_AUTO = 4
 VC_VALUES_WINDOWED = 8
+VC_INPUTS_UPLOAD = 16
 
 
 def vc_circuit_create(log_width, wiring, explicit=None, device: int = 0, host_values: bool = False,
-                      staged: bool = False, auto: bool = False, windowed: bool = False):
+                      staged: bool = False, auto: bool = False, windowed: bool = False, upload: bool = False):
     """Returns an opaque handle (int).  explicit: per-layer (type, in1, in2) or
     None.  host_values: keep the layer values in mapped host memory; staged:
     keep the wide layers in host memory and pass them through device slots
     (copy-once-per-layer); windowed: the wide layers through device slots
     only, each iteration run while its layers are there; auto: the first of
     device memory, windowed and mapped host memory whose memory can be had
-    (vc_circuit_get_info's "residency" says which)."""
+    (vc_circuit_get_info's "residency" says which); upload (device-resident
+    values only): page-locked host inputs are copied to the device by one
+    transfer per call instead of being read in place."""
     lw = [int(x) for x in log_width]
     kinds = [int(k) for k in wiring]
     d = len(kinds)
@@ -277,9 +280,10 @@ def vc_circuit_create(log_width, wiring, explicit=None, device: int = 0, host_va
         desc.in1 = i1s
         desc.in2 = i2s
     h = ctypes.c_void_p()
-    if host_values or staged or auto or windowed:
+    if host_values or staged or auto or windowed or upload:
         flags = (VC_VALUES_AUTO if auto else VC_VALUES_WINDOWED if windowed else
-                 VC_VALUES_STAGED if staged else VC_VALUES_IN_HOST_MEMORY)
+                 VC_VALUES_STAGED if staged else VC_VALUES_IN_HOST_MEMORY if host_values else 0)
+        flags |= VC_INPUTS_UPLOAD if upload else 0
         _check(lib().vc_circuit_create_ex(ctypes.byref(desc), device, flags, ctypes.byref(h)),
                "vc_circuit_create_ex")
     else:

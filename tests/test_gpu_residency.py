@@ -105,8 +105,58 @@ def test_bad_flags_rejected():
     w, k = circuits.f2(3)
     desc, keep = vc._desc_struct(w, k)
     h = ctypes.c_void_p()
-    for flags in (6, 3, 5, 16, 10):
+    for flags in (6, 3, 5, 32, 10, 17, 18, 20, 24):
         assert vc.lib().vc_circuit_create_ex(ctypes.byref(desc), 0, flags, ctypes.byref(h)) == vc.VC_EINVAL
+
+
+@pytest.mark.parametrize("family,logn", [("f2", 4), ("f2", 12), ("f0", 6), ("matmult", 3)])
+def test_uploaded_inputs_equal_oracle(family, logn):
+    """VC_INPUTS_UPLOAD: page-locked host inputs are copied to the device by
+    the prover and by the verifier's input pass (each into its own buffer);
+    the transcript equals the oracle's, both verifiers accept it and reject a
+    changed one, a refilled host buffer is picked up by the next proof, and a
+    non-canonical input is still reported."""
+    P = (1 << 61) - 1
+    w, k = circuits.by_name(family, logn)
+    x = I.job_inputs(family, logn, 90 + logn)
+    h = vc.vc_circuit_create(w, k, upload=True)
+    main, side = torch.cuda.current_stream(), torch.cuda.Stream()
+    try:
+        assert vc.vc_circuit_get_info(h)["residency"] == 0
+        xh = torch.from_numpy(np.ascontiguousarray(x, np.uint64).view(np.int64).copy()).pin_memory()
+        n = vc.vc_transcript_len(h)
+        tr = torch.empty(n, dtype=torch.int64, device="cuda")
+        acc = torch.zeros(1, dtype=torch.int32, device="cuda")
+        start = torch.cuda.Event()
+        start.record(main)
+        vc.vc_prove(h, xh, 5, tr)
+        side.wait_event(start)
+        vc.vc_verify_input(h, xh, 5, stream=side)
+        main.wait_stream(side)
+        vc.vc_verify_transcript(h, 5, tr, accept=acc)
+        torch.cuda.synchronize()
+        vc.vc_circuit_sync(h)
+        assert (to_np(tr) == oracle_prove(w, k, x, 5)).all()
+        assert int(acc.item()) == 1
+        assert vc.vc_verify(h, xh, 5, tr)
+        bad = tr.clone()
+        bad[n // 2] = (int(bad[n // 2]) + 1) % P
+        assert not vc.vc_verify(h, xh, 5, bad)
+        x2 = I.job_inputs(family, logn, 190 + logn)
+        xh.copy_(torch.from_numpy(np.ascontiguousarray(x2, np.uint64).view(np.int64).copy()))
+        vc.vc_prove(h, xh, 6, tr)
+        vc.vc_circuit_sync(h)
+        assert (to_np(tr) == oracle_prove(w, k, x2, 6)).all()
+        assert vc.vc_verify(h, xh, 6, tr)
+        xh[0] = -1  # 2^64 - 1: not a field element
+        with pytest.raises(vc.VcError) as e:
+            vc.vc_prove(h, xh, 7, tr)  # asynchronous: latched, reported by the sync
+            vc.vc_circuit_sync(h)
+        assert e.value.status == vc.VC_EINVAL
+        vc.vc_circuit_sync(h)
+    finally:
+        torch.cuda.synchronize()
+        vc.vc_circuit_destroy(h)
 
 
 STAGED = [("f2", 0), ("f2", 1), ("f2", 2), ("f2", 5), ("f2", 13), ("f0", 3), ("f0", 6), ("matmult", 2),
