@@ -269,15 +269,18 @@ typedef enum {
 } vc_stage;
 
 /* Record CUDA events around the stages of every later vc_prove on this
- * circuit: events[2k] when stage k starts and events[2k+1] when it ends, each
- * on the stream that runs the stage; a stage with no work for this circuit
+ * circuit: events[2k] when stage k can start (the work before it is done)
+ * and events[2k+1] when it has ended; a stage with no work for this circuit
  * records nothing.  `events` must hold 2 * VC_NUM_STAGES entries: cudaEvent_t
  * created on the circuit's device and owned by the caller, or NULL to skip
- * that mark (each recorded event costs a little device time: record only the
- * stages you time).  events == NULL turns recording off.  A proof replays a CUDA graph of its launches, captured by
- * the first vc_prove after the circuit's creation or after this call; the
- * events are event-record nodes of that graph.  The call must not overlap a
- * proof in flight on the circuit (it may replace the graph). */
+ * that mark (record only the stages you time: marks of one stream are
+ * recorded in order, so a mark may wait for the one before it).  events ==
+ * NULL turns recording off.  A proof replays a CUDA graph of its launches,
+ * captured by the first vc_prove after the circuit's creation or after this
+ * call; the events are event-record nodes of that graph, on side branches
+ * that no launch waits for (timing a stage adds no step between launches).
+ * The call must not overlap a proof in flight on the circuit (it may replace
+ * the graph). */
 vc_status vc_circuit_set_stage_events(vc_circuit *c, void *const *events);
 
 /* Shape facts of a circuit. */

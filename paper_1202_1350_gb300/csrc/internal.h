@@ -144,6 +144,13 @@ struct Plan {
     cudaStream_t cap = nullptr;  // private stream: graph capture, creation work
     cudaEvent_t ev_fork = nullptr, ev_tables = nullptr;
     cudaEvent_t ev_params = nullptr;  // a batch's parameter table was copied
+    // stage events are recorded on a side branch of the graph (evs), so that
+    // timing a stage adds no node between two launches (and keeps the final
+    // reduction's programmatic dependence on the wave launch)
+    // (one branch per stream whose stages are timed: a branch of its own
+    // keeps the helper stream's marks from waiting for the main stream's)
+    cudaStream_t evs = nullptr, evs_aux = nullptr;
+    cudaEvent_t ev_mark = nullptr;
     struct vc_circuit *staged = nullptr;  // a single staged circuit: its own launch sequence
     cudaGraphExec_t exec = nullptr;
     // own_params: the graph's first node is the per-proof parameter write

@@ -1035,7 +1035,9 @@ cudaError_t plan_resources(Plan &P)
 {
     cudaError_t e = cudaStreamCreateWithFlags(&P.aux, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P.cap, cudaStreamNonBlocking);
-    for (cudaEvent_t *ev : {&P.ev_fork, &P.ev_tables, &P.ev_params})
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P.evs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P.evs_aux, cudaStreamNonBlocking);
+    for (cudaEvent_t *ev : {&P.ev_fork, &P.ev_tables, &P.ev_params, &P.ev_mark})
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     return e;
 }
@@ -1052,11 +1054,11 @@ void plan_drop_graph(Plan &P)
 void plan_release(Plan &P)
 {
     plan_drop_graph(P);
-    for (cudaEvent_t *ev : {&P.ev_fork, &P.ev_tables, &P.ev_params}) {
+    for (cudaEvent_t *ev : {&P.ev_fork, &P.ev_tables, &P.ev_params, &P.ev_mark}) {
         if (*ev) cudaEventDestroy(*ev);
         *ev = nullptr;
     }
-    for (cudaStream_t *s : {&P.aux, &P.cap}) {
+    for (cudaStream_t *s : {&P.aux, &P.cap, &P.evs, &P.evs_aux}) {
         if (*s) cudaStreamDestroy(*s);
         *s = nullptr;
     }
@@ -1166,10 +1168,18 @@ void enqueue_plan(Plan &P, cudaStream_t st)
 {
     cudaStream_t sa = P.aux;
     const Globals *Gs = P.d_G;
-    // stage events become event-record nodes of the captured graph
+    // stage events become event-record nodes of the captured graph, on a
+    // branch (P.evs) that depends on the point of `s` where the stage starts
+    // or ends but that no launch depends on
+    bool marked = false, marked_aux = false;
     auto mark = [&](int k, int end, cudaStream_t s) {
-        if (P.stage_on && P.stage_ev[2 * k + end])
-            cudaEventRecordWithFlags(P.stage_ev[2 * k + end], s, cudaEventRecordExternal);
+        if (!(P.stage_on && P.stage_ev[2 * k + end])) return;
+        const bool aux = s == P.aux;
+        cudaStream_t b = aux ? P.evs_aux : P.evs;
+        cudaEventRecord(P.ev_mark, s);
+        cudaStreamWaitEvent(b, P.ev_mark, 0);
+        cudaEventRecordWithFlags(P.stage_ev[2 * k + end], b, cudaEventRecordExternal);
+        (aux ? marked_aux : marked) = true;
     };
     auto any_tasks = [](const std::vector<std::vector<Task>> &g, size_t from) {
         for (size_t k = from; k < g.size(); k++)
@@ -1228,6 +1238,12 @@ void enqueue_plan(Plan &P, cudaStream_t st)
     launch_final(P.d_G, P.d_rounds, (int)P.rounds.size(), (int)P.nbig, P.d_outs, (int)P.outs.size(), st);
     mark(VC_STAGE_FINAL, 1, st);
     mark(VC_STAGE_PROOF, 1, st);
+    // the branches join the stream at the end
+    for (int k = 0; k < 2; k++)
+        if (k ? marked_aux : marked) {
+            cudaEventRecord(P.ev_mark, k ? P.evs_aux : P.evs);
+            cudaStreamWaitEvent(st, P.ev_mark, 0);
+        }
 }
 
 cudaError_t find_kernel_node(cudaGraph_t g, const void *fn, cudaGraphNode_t *node, cudaKernelNodeParams *kp)
