@@ -22,6 +22,9 @@
 // inputs when the evaluation reads them in place).
 __global__ void k_params(Globals *G, u64 seed, u64 *tr, const u64 *in)
 {
+    // the evaluation launch that follows may start now (it waits for these
+    // writes before it reads them)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     G->seed = seed;
     G->tr = tr;
     G->in = in;
@@ -274,6 +277,9 @@ __global__ void __launch_bounds__(EV_NT, EV_MINB) k_eval_seg(const Globals *Gs, 
         s_V[j] = L.V;
     }
     __shared__ u64 *s_copy;
+    // launched right after the parameter write with a programmatic dependence:
+    // the plan's descriptors above are static, the per-proof fields are not
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (threadIdx.x == 0) {
         // a run over the input layer reads this proof's inputs in place, if
         // given, and writes them to the layer's values
@@ -402,10 +408,27 @@ __global__ void __launch_bounds__(EV_NT, EV_MINB) k_eval_seg(const Globals *Gs, 
 }
 
 void launch_eval_segs(const Globals *Gs, const EvalSeg *segs, const Item *items, int nitems, u32 maxblock,
-                      cudaStream_t st)
+                      cudaStream_t st, bool after_params)
 {
     if (maxblock > EV_MAXB) maxblock = EV_MAXB;
-    if (nitems > 0) k_eval_seg<<<nitems, EV_NT, 2 * maxblock * sizeof(u64), st>>>(Gs, segs, items, maxblock);
+    if (nitems <= 0) return;
+    if (!after_params) {
+        k_eval_seg<<<nitems, EV_NT, 2 * maxblock * sizeof(u64), st>>>(Gs, segs, items, maxblock);
+        return;
+    }
+    // right after k_params: a programmatic dependence lets the CTAs start and
+    // read the plan's descriptors while the parameters are written
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)nitems);
+    cfg.blockDim = dim3(EV_NT);
+    cfg.dynamicSmemBytes = 2 * maxblock * sizeof(u64);
+    cfg.stream = st;
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_eval_seg, Gs, segs, items, maxblock);
 }
 
 __global__ void k_check_canonical(const u64 *x, u64 n, u32 *status)

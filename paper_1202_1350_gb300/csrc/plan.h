@@ -317,7 +317,8 @@ void launch_eval_layers(const Globals *Gs, const LayerEval *le, const Item *item
 // maxblock: the largest block (entries) of any run layer or tail output in
 // the launch (<= 2048); it sizes the two shared-memory buffers.
 void launch_eval_segs(const Globals *Gs, const EvalSeg *segs, const Item *items, int nitems, u32 maxblock,
-                      cudaStream_t st);
+                      cudaStream_t st,
+                      bool after_params = false);
 void launch_check_canonical(const u64 *x, u64 n, u32 *status, cudaStream_t st);
 void launch_check_inputs(const Globals *Gs, const Item *items, int nitems, cudaStream_t st);
 void launch_build23(const Globals *Gs, const BuildItem *items, int nitems, cudaStream_t st);

@@ -1200,7 +1200,8 @@ void enqueue_plan(Plan &P, cudaStream_t st)
     cudaEventRecord(P.ev_fork, st);
     mark(VC_STAGE_EVAL, 0, st);
     for (size_t k = 0; k < P.seg_items.size(); k++) {
-        launch_eval_segs(Gs, P.d_segs, P.d_seg_items[k], (int)P.seg_items[k].size(), P.seg_maxblock[k], st);
+        launch_eval_segs(Gs, P.d_segs, P.d_seg_items[k], (int)P.seg_items[k].size(), P.seg_maxblock[k], st,
+                         P.own_params && k == 0);
         launch_eval_layers(Gs, P.d_levs, P.d_lev_items[k], (int)P.lev_items[k].size(), st);
     }
     // inputs not checked by an evaluation segment: the check only latches a
