@@ -247,6 +247,24 @@ vc_status vc_verify_input(vc_circuit *c, const uint64_t *inputs, uint64_t seed, 
 vc_status vc_verify_transcript(vc_circuit *c, uint64_t seed, const uint64_t *transcript, int *accept,
                                void *stream);
 
+/* Prove and verify in one call (Sec. 3.1's prover and verifier, the
+ * verifier checking the prover's transcript): the proof as vc_prove, the
+ * verifier's input pass (its coins and the inputs' multilinear extension at
+ * its final point, fixed by the seed alone) beside it, and the checks of the
+ * transcript after the proof, all one CUDA graph launch on `stream`.  The
+ * verifier reads the inputs where the prover does: in place, or from the
+ * input layer that the library's own copy filled (pageable host inputs, or
+ * page-locked ones with VC_INPUTS_UPLOAD), which no launch writes.
+ * transcript and accept: device or host memory.  Asynchronous (statuses
+ * latched, read by vc_circuit_sync) when transcript and accept are device
+ * memory and the inputs were not a pageable copy; otherwise it returns after
+ * both are written.  The transcript and the accept bit equal those of
+ * vc_prove followed by vc_verify.  VC_EINVAL for circuits whose values pass
+ * through device slots (VC_VALUES_STAGED, VC_VALUES_WINDOWED) and for an
+ * input >= p (from the call, or latched). */
+vc_status vc_prove_verify(vc_circuit *c, const uint64_t *inputs, uint64_t seed, uint64_t *transcript, int *accept,
+                          void *stream);
+
 /* Stages of a proof, for timing them.  A proof runs on the caller's stream;
  * the coins, eq tables and product weights run on a helper stream owned by
  * the circuit (forked from and joined back to the caller's stream),

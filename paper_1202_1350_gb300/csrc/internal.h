@@ -202,6 +202,14 @@ struct vc_circuit {
     // writes what a proof on the handle reads
     Globals Gv{};
     Globals *d_Gv = nullptr;
+    // vc_prove_verify: the proof and its verification in one captured graph
+    // (the prover's and the verifier's parameter nodes set per call)
+    cudaGraphExec_t pv_exec = nullptr;
+    cudaGraph_t pv_graph = nullptr;
+    cudaGraphNode_t pv_pnode = nullptr, pv_vnode = nullptr;
+    cudaKernelNodeParams pv_pkp{}, pv_vkp{};
+    cudaStream_t pv_vs = nullptr;  // the verifier's branch while the graph is captured
+    cudaEvent_t pv_fork = nullptr, pv_join = nullptr;
     cudaGraphExec_t vexec = nullptr;   // the verifier's captured launches, parameter write first
     cudaGraph_t vgraph = nullptr;
     cudaGraphNode_t vpnode = nullptr;

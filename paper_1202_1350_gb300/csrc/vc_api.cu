@@ -1641,10 +1641,13 @@ vc_status circuit_prepare(const vc_circuit_desc *desc, int device, vc_circuit **
 void circuit_free(vc_circuit *c)
 {
     if (!c) return;
-    for (cudaGraphExec_t x : {c->vexec, c->vin_exec})
+    for (cudaGraphExec_t x : {c->vexec, c->vin_exec, c->pv_exec})
         if (x) cudaGraphExecDestroy(x);
-    for (cudaGraph_t g : {c->vgraph, c->vin_graph})
+    for (cudaGraph_t g : {c->vgraph, c->vin_graph, c->pv_graph})
         if (g) cudaGraphDestroy(g);
+    for (cudaEvent_t ev : {c->pv_fork, c->pv_join})
+        if (ev) cudaEventDestroy(ev);
+    if (c->pv_vs) cudaStreamDestroy(c->pv_vs);
     if (c->pg_exec) cudaGraphExecDestroy(c->pg_exec);
     if (c->pg_arena) lib_free(c->pg_arena);
     for (cudaEvent_t ev : c->st_ev)
@@ -2162,12 +2165,107 @@ extern "C" vc_status vc_verify_transcript(vc_circuit *c, uint64_t seed, const ui
     return verifier_finish(c, ka && kt && !c->vin_sync, ka, accept, st);
 }
 
+// The proof and its verification as one graph: the verifier's branch (its
+// parameters, coins and eq tables, and the inputs' MLE at its final point,
+// all fixed by the seed) forks at the start and runs beside the proof; the
+// checks of the transcript follow the proof's final reduction and join the
+// branch.  Parameters: the prover's k_params node and the verifier's
+// k_vparams node, set before each launch.
+static cudaError_t pv_capture(vc_circuit *c)
+{
+    cudaError_t e = cudaSuccess;
+    if (!c->pv_vs) e = cudaStreamCreateWithFlags(&c->pv_vs, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !c->pv_fork) e = cudaEventCreateWithFlags(&c->pv_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !c->pv_join) e = cudaEventCreateWithFlags(&c->pv_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    cudaStream_t cs = c->P.cap;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    // the proof's launches are captured first, so that the graph starts them
+    // ahead of the verifier's branch, which forks from the start
+    cudaEventRecord(c->pv_fork, cs);
+    enqueue_plan(c->P, cs);
+    cudaStreamWaitEvent(c->pv_vs, c->pv_fork, 0);
+    launch_vparams(c->d_Gv, c->d_vp, 0, nullptr, nullptr, nullptr, c->d_result, c->pv_vs);
+    launch_coins(c->d_Gv, 1, c->d_eq_verify, (int)c->eq_verify.size(), nullptr, nullptr, 0, c->pv_vs);
+    launch_verify_input(c->d_Gv, c->Gv, c->Vd, c->s[c->d], c->s[0], c->pv_vs);
+    cudaEventRecord(c->pv_join, c->pv_vs);
+    cudaStreamWaitEvent(cs, c->pv_join, 0);
+    // transcript and accept pointer from the verifier's parameters
+    launch_verify_transcript(c->d_Gv, c->Gv, c->Vd, c->s[c->d], c->s[0], c->d_vwire, (int)c->vwire.size(), nullptr,
+                             nullptr, cs);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = find_kernel_node(g, params_kernel(), &c->pv_pnode, &c->pv_pkp);
+    if (e == cudaSuccess) e = find_kernel_node(g, vparams_kernel(), &c->pv_vnode, &c->pv_vkp);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->pv_exec, g, 0);
+    if (e != cudaSuccess) {
+        c->pv_exec = nullptr;
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return e;
+    }
+    c->pv_graph = g;
+    return cudaSuccess;
+}
+
+extern "C" vc_status vc_prove_verify(vc_circuit *c, const uint64_t *inputs, uint64_t seed, uint64_t *transcript,
+                                     int *accept, void *stream)
+{
+    if (!c || !inputs || !transcript || !accept) return VC_EINVAL;
+    if (c->P.staged || !c->P.own_params) return VC_EINVAL;  // values through device slots: vc_prove, vc_verify
+    DevGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const void *mapped = nullptr;
+    const int ki = ptr_kind(inputs, c->device, &mapped), kt = ptr_kind(transcript, c->device);
+    const int ka = ptr_kind(accept, c->device);
+    if (ki < 0 || kt < 0 || ka < 0) return VC_EINVAL;
+    if (!ka) *accept = 0;
+    c->vin_pending = false;  // this call reuses the input pass's scratch
+    // the prover's inputs as in vc_prove; the verifier reads them where the
+    // prover does: in place, or in the input layer the library's copy filled
+    // (no launch writes that layer then)
+    const bool upload = (c->flags & VC_INPUTS_UPLOAD) && ki == 0 && mapped;
+    const u64 *in = nullptr;
+    if (c->eval_reads_inputs && !upload) in = ki ? inputs : static_cast<const u64 *>(mapped);
+    cudaError_t e = cudaSuccess;
+    if (!in)
+        e = cudaMemcpyAsync(c->V[c->d], inputs, (u64(1) << c->s[c->d]) * sizeof(u64), cudaMemcpyDefault, st);
+    const u64 *din = in ? in : ki > 0 ? inputs : c->V[c->d];
+    if (e == cudaSuccess && !c->pv_exec) e = pv_capture(c);
+    u64 *tr = kt ? transcript : c->d_tr;
+    const u64 *trc = tr;
+    int *acc = ka ? accept : nullptr;
+    Globals *G = c->P.d_G, *Gv = c->d_Gv;
+    VerifyPtrs *vp = c->d_vp;
+    u64 *res = c->d_result;
+    void *pargs[4] = {&G, &seed, &tr, &in};
+    void *vargs[7] = {&Gv, &vp, &seed, &trc, &din, &acc, &res};
+    if (e == cudaSuccess) e = set_node_args(c->pv_exec, c->pv_pnode, c->pv_pkp, pargs);
+    if (e == cudaSuccess) e = set_node_args(c->pv_exec, c->pv_vnode, c->pv_vkp, vargs);
+    if (e == cudaSuccess) e = cudaGraphLaunch(c->pv_exec, st);
+    if (e == cudaSuccess && !kt)
+        e = cudaMemcpyAsync(transcript, c->d_tr, c->tr_len * sizeof(u64), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return VC_ECUDA;
+    if (kt && ka && (ki || in || upload)) return VC_OK;  // asynchronous, statuses latched
+    const vc_status s = read_status_and_clear(c, st);
+    if (s != VC_OK) return s;
+    return verifier_finish(c, false, ka, accept, st);
+}
+
 extern "C" vc_status vc_circuit_set_stage_events(vc_circuit *c, void *const *events)
 {
     if (!c) return VC_EINVAL;
     DevGuard guard(c->device);
     if (c->P.exec) {  // the events are part of the captured graph: capture again
         plan_drop_graph(c->P);
+    }
+    if (c->pv_exec) {  // and of the proof-and-verification graph
+        cudaGraphExecDestroy(c->pv_exec);
+        cudaGraphDestroy(c->pv_graph);
+        c->pv_exec = nullptr;
+        c->pv_graph = nullptr;
     }
     c->P.stage_on = events != nullptr;
     if (events)

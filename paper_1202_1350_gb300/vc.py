@@ -132,6 +132,7 @@ def lib():
             L.vc_verify.argtypes = [vp, vp, ctypes.c_uint64, vp, ctypes.POINTER(ctypes.c_int), vp]
             L.vc_verify_input.argtypes = [vp, vp, ctypes.c_uint64, vp]
             L.vc_verify_transcript.argtypes = [vp, ctypes.c_uint64, vp, ctypes.POINTER(ctypes.c_int), vp]
+            L.vc_prove_verify.argtypes = [vp, vp, ctypes.c_uint64, vp, ctypes.POINTER(ctypes.c_int), vp]
             L.vc_prove_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), _u64p, ctypes.POINTER(vp),
                                          ctypes.c_int, vp]
             L.vc_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
@@ -175,7 +176,7 @@ def lib():
                          "vc_autotune_batch", "vc_circuit_create_tiles", "vc_circuit_get_tiles", "vc_prove_pergate",
                          "vc_circuit_create_ex", "vc_f2sp_create", "vc_f2sp_destroy", "vc_f2sp_prove",
                          "vc_f2sp_verify_begin", "vc_f2sp_verify_absorb", "vc_f2sp_verify_absorb_async",
-                         "vc_f2sp_verify_end", "vc_verify_input", "vc_verify_transcript"):
+                         "vc_f2sp_verify_end", "vc_verify_input", "vc_verify_transcript", "vc_prove_verify"):
                 getattr(L, name).restype = st
             _lib = L
     return _lib
@@ -447,6 +448,26 @@ def vc_verify_transcript(h, seed: int, transcript, stream=None, device: int = 0,
     acc = ctypes.c_int(0)
     _check(lib().vc_verify_transcript(h, seed & 0xFFFFFFFFFFFFFFFF, _ptr(transcript), ctypes.byref(acc),
                                       _stream(stream, device)), "vc_verify_transcript")
+    return bool(acc.value)
+
+
+def vc_prove_verify(h, inputs, seed: int, transcript, stream=None, device: int = 0, accept=None):
+    """Prove and verify in one graph launch: writes the transcript and returns
+    the accept bit; with `accept` (a CUDA int32 tensor) the call is
+    asynchronous where vc_prove's would be and the bit is written there."""
+    nin, _, ntr = _shapes[h]
+    _need(inputs, nin, "inputs")
+    _need(transcript, ntr, "transcript")
+    if accept is not None:
+        if accept.element_size() != 4 or accept.numel() < 1:
+            raise ValueError("accept must be an int32 tensor")
+        _check(lib().vc_prove_verify(h, _ptr(inputs), seed & 0xFFFFFFFFFFFFFFFF, _ptr(transcript),
+                                     ctypes.cast(ctypes.c_void_p(accept.data_ptr()), ctypes.POINTER(ctypes.c_int)),
+                                     _stream(stream, device)), "vc_prove_verify")
+        return None
+    acc = ctypes.c_int(0)
+    _check(lib().vc_prove_verify(h, _ptr(inputs), seed & 0xFFFFFFFFFFFFFFFF, _ptr(transcript), ctypes.byref(acc),
+                                 _stream(stream, device)), "vc_prove_verify")
     return bool(acc.value)
 
 

@@ -314,3 +314,77 @@ def test_two_pass_at_the_bench_size():
     finally:
         torch.cuda.synchronize()
         vc.vc_circuit_destroy(h)
+
+
+def _oracle_transcript(w, k, x, seed, explicit=None):
+    return oracle.Circuit(w, k, explicit=explicit).prove(np.asarray(x, np.uint64), seed)
+
+
+@pytest.mark.parametrize("family,logn", [("f2", 0), ("f2", 5), ("f2", 12), ("f0", 6), ("matmult", 3)])
+def test_prove_verify_one_call(family, logn):
+    """vc_prove_verify (the proof, the verifier's input pass beside it and its
+    checks after it, one graph): the transcript equals the oracle's and the
+    accept bit is set, with device buffers (asynchronous), with host buffers
+    (synchronous), with page-locked inputs read in place, and twice in a row
+    on one handle; the same handle then verifies with vc_verify."""
+    w, k = circuits.by_name(family, logn)
+    x = I.job_inputs(family, logn, 40 + logn)
+    h = vc.vc_circuit_create(w, k)
+    try:
+        n = vc.vc_transcript_len(h)
+        tr = torch.empty(n, dtype=torch.int64, device="cuda")
+        acc = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for seed in (9, 10, 9):
+            acc.zero_()
+            vc.vc_prove_verify(h, dev(x), seed, tr, accept=acc)
+            vc.vc_circuit_sync(h)
+            assert (to_np(tr) == _oracle_transcript(w, k, x, seed)).all()
+            assert int(acc.item()) == 1
+        trh = np.zeros(n, np.uint64)
+        assert vc.vc_prove_verify(h, np.ascontiguousarray(x, np.uint64), 11, trh) is True
+        assert (trh == _oracle_transcript(w, k, x, 11)).all()
+        xp = torch.from_numpy(np.ascontiguousarray(x, np.uint64).view(np.int64).copy()).pin_memory()
+        acc.zero_()
+        vc.vc_prove_verify(h, xp, 12, tr, accept=acc)
+        vc.vc_circuit_sync(h)
+        assert (to_np(tr) == _oracle_transcript(w, k, x, 12)).all() and int(acc.item()) == 1
+        assert vc.vc_verify(h, dev(x), 12, tr)
+        bad = tr.clone()
+        bad[n - 1] = (int(bad[n - 1]) + 1) % P
+        assert not vc.vc_verify(h, dev(x), 12, bad)
+    finally:
+        torch.cuda.synchronize()
+        vc.vc_circuit_destroy(h)
+
+
+@pytest.mark.parametrize("mode", ["upload", "host_values", "staged"])
+def test_prove_verify_modes(mode):
+    """The one-call form with uploaded inputs (the verifier reads the input
+    layer the library's copy filled) and with layer values in mapped host
+    memory equals the oracle; circuits whose values pass through device slots
+    are refused; a non-canonical input is reported."""
+    w, k = circuits.f2(11)
+    x = I.f2_inputs(11, 1 << 16, 31)
+    h = vc.vc_circuit_create(w, k, **{mode: True})
+    try:
+        n = vc.vc_transcript_len(h)
+        tr = torch.empty(n, dtype=torch.int64, device="cuda")
+        acc = torch.zeros(1, dtype=torch.int32, device="cuda")
+        xp = torch.from_numpy(np.ascontiguousarray(x, np.uint64).view(np.int64).copy()).pin_memory()
+        if mode == "staged":
+            with pytest.raises(vc.VcError) as e:
+                vc.vc_prove_verify(h, xp, 3, tr, accept=acc)
+            assert e.value.status == vc.VC_EINVAL
+            return
+        vc.vc_prove_verify(h, xp, 3, tr, accept=acc)
+        vc.vc_circuit_sync(h)
+        assert (to_np(tr) == _oracle_transcript(w, k, x, 3)).all() and int(acc.item()) == 1
+        xp[5] = P  # not a field element
+        with pytest.raises(vc.VcError) as e:
+            vc.vc_prove_verify(h, xp, 4, tr, accept=acc)
+            vc.vc_circuit_sync(h)
+        assert e.value.status == vc.VC_EINVAL
+        vc.vc_circuit_sync(h)
+    finally:
+        torch.cuda.synchronize()
+        vc.vc_circuit_destroy(h)
