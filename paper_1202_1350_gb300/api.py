@@ -74,6 +74,14 @@ class Circuit:
         x = _as_tensor(inputs, f"cuda:{self.device}")
         return _vc.vc_verify(self.handle, x, seed, transcript, device=self.device)
 
+    def prove_verify(self, inputs, seed: int, transcript=None):
+        """Proof and verification in one graph launch; returns (transcript,
+        accept bit)."""
+        x = _as_tensor(inputs, f"cuda:{self.device}")
+        tr = self.new_transcript() if transcript is None else transcript
+        ok = _vc.vc_prove_verify(self.handle, x, seed, tr, device=self.device)
+        return tr, ok
+
     def verify_input(self, inputs, seed: int, stream=None):
         """The verifier's input pass for `seed` (its coins and the inputs'
         multilinear extension at the final point), queued on `stream` (a torch

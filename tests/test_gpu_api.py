@@ -35,6 +35,8 @@ def test_circuit_roundtrip():
         bad = tr.clone()
         bad[1] = (int(bad[1]) + 1) % P
         assert not c.verify(x, 5, bad)
+        tr2, ok = c.prove_verify(x, 6)
+        assert ok and (to_np(tr2) == oracle_prove(*circuits.f2(9), x, 6)).all()
     finally:
         c.close()
 
