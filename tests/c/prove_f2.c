@@ -1,7 +1,8 @@
 /* A C user of include/vc.h: builds the F2 circuit for 2^n inputs
  * x_i = (i * 2654435761) mod 65537, proves it with host buffers on device 0,
- * verifies the proof, and prints the status, the accept bit and the
- * transcript (one decimal u64 per line).  Usage: prove_f2 n seed */
+ * verifies the proof, proves and verifies it again in one call, and prints
+ * the statuses, the accept bits and the transcript (one decimal u64 per
+ * line).  Usage: prove_f2 n seed */
 #include <inttypes.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -48,6 +49,15 @@ int main(int argc, char **argv)
     vc_verify(c, x, seed, tr, &reject, NULL);
     tr[len - 1] -= 1;
     printf("tampered %d\n", reject);
+    /* the same proof and its verification in one call */
+    uint64_t *tr2 = malloc(len * sizeof(uint64_t));
+    if (!tr2) return 1;
+    int accept2 = -1;
+    st = vc_prove_verify(c, x, seed, tr2, &accept2, NULL);
+    int same = 1;
+    for (uint64_t k = 0; k < len; k++) same &= tr2[k] == tr[k];
+    printf("prove_verify %s %d %d\n", vc_status_string(st), accept2, same);
+    free(tr2);
     for (uint64_t k = 0; k < len; k++) printf("%" PRIu64 "\n", tr[k]);
     vc_circuit_destroy(c);
     free(x);

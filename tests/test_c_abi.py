@@ -1,7 +1,8 @@
 """The C ABI used from C: tests/c/prove_f2.c includes include/vc.h, links
-libvc.so and proves and verifies F2 with host buffers.  On CPU the program
-compiles and links; on the GPU its transcript equals the oracle's, the honest
-proof is accepted and a changed one rejected."""
+libvc.so and proves and verifies F2 with host buffers, separately and in one
+call.  On CPU the program compiles and links; on the GPU its transcript
+equals the oracle's, the honest proof is accepted (both ways) and a changed
+one rejected."""
 import os
 import shutil
 import subprocess
@@ -40,7 +41,8 @@ def test_c_program_proof_equals_oracle(tmp_path, n, seed):
     assert out[:2] == ["prove", "ok"]
     assert out[2:5] == ["verify", "ok", "1"]
     assert out[5:7] == ["tampered", "0"]
-    got = np.array([int(v) for v in out[7:]], dtype=np.uint64)
+    assert out[7:11] == ["prove_verify", "ok", "1", "1"]  # accepted, same transcript
+    got = np.array([int(v) for v in out[11:]], dtype=np.uint64)
     x = np.array([(i * 2654435761) % 65537 for i in range(1 << n)], dtype=np.uint64)
     want = oracle.Circuit(*oracle.f2_layers(n)).prove(x, seed)
     assert len(got) == len(want)
